@@ -1,0 +1,193 @@
+"""Oracle gDC time step (Sec. 3) and Euler-Maruyama step (App. D).  TEST INFRASTRUCTURE ONLY.
+
+Everything is dense FP64 for one suspension: M is assembled, its square root
+is taken by eigendecomposition (the symmetric root that Lanczos converges to)
+or by Cholesky, the saddle point is solved by LU, and step 2 is solved as
+the least-squares problem it is.  The random vectors W (3M normals) and
+W-tilde (6N normals) are inputs, so the same draws can be fed to any
+implementation.
+
+Readings of points the paper leaves open (each is also listed with the design notes):
+
+* Y_p is the blob centroid (templates are centred on it).
+* The Brownian slip velocity is v-breve = sqrt(2 kT / dt) M^(1/2) W with the
+  same W at the start and at the mid-step (Eqs. 17 and 19).
+* RFD (Eq. 16 with the footnote's L_p): the perturbed state is
+  Y + delta L_p W~_t, exp(delta W~_r) * q; the estimator is
+  sum_p [W~_t . (V~_t - V_t) / (delta L_p) + W~_r . (V~_r - V_r) / delta],
+  and nu = 1 + dt/2 * estimator is one scalar for the whole suspension.
+  A single-blob body has L_p = 0; it uses L_p = a instead.
+* FD (Eq. 15): the same sum over unit perturbations of each body coordinate.
+* Background shear u(r) = (shear_rate * y, 0, 0) enters the slip as
+  M lambda - K V = -v-breve - u(r) at the mid-step solve only.
+* Forces are the soft blob repulsion of forces.py evaluated at the mid-step.
+* The update x^(n+1) = x^n + nu dt V^m uses Omega^m directly as du/dt,
+  which is exact because u^n = 0 and D^-1 at 0 is I (App. A).
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+from . import forces, geometry, rigid, rpy
+
+
+@dataclasses.dataclass
+class Params:
+    eta: float = 1.0
+    kT: float = 1.0
+    a: float = 1.0
+    dt: float = 0.01
+    rfd_delta: float = 1e-6
+    rep_A: float = 0.0
+    rep_b: float = 0.1
+    shear_rate: float = 0.0
+    sqrt_mode: str = "sym"      # "sym" (eigh) or "chol"
+
+    @classmethod
+    def from_dict(cls, d: dict) -> "Params":
+        names = {f.name for f in dataclasses.fields(cls)}
+        return cls(**{k: v for k, v in d.items() if k in names})
+
+
+def _lengths(layout: geometry.Layout, a: float) -> np.ndarray:
+    return np.where(layout.L > 0.0, layout.L, a)
+
+
+def sqrt_apply(M: np.ndarray, W: np.ndarray, mode: str) -> np.ndarray:
+    S = rigid.sqrtm_sym(M) if mode == "sym" else rigid.sqrtm_chol(M)
+    return S @ W
+
+
+def brownian_slip(layout, Y, q, W, p: Params):
+    """Blob positions, M, K, B and v-breve = sqrt(2kT/dt) M^(1/2) W at state (Y, q)."""
+    r = geometry.blob_positions(layout, Y, q)
+    M = rpy.rpy_matrix(r, p.a, p.eta)
+    K = rigid.k_matrix(r, Y, layout.blob_body)
+    B = rigid.rigid_basis(K, layout.n_bodies)
+    vb = np.sqrt(2.0 * p.kT / p.dt) * sqrt_apply(M, W, p.sqrt_mode)
+    return r, M, K, B, vb
+
+
+def projected_velocity(layout, Y, q, W, p: Params) -> np.ndarray:
+    """Step 2: the least-squares rigid velocity of v-breve at state (Y, q), shape (N, 6)."""
+    _, _, K, B, vb = brownian_slip(layout, Y, q, W, p)
+    return rigid.lsq_velocity(K, B, vb).reshape(-1, 6)
+
+
+def perturbed_state(layout, Y, q, dY: np.ndarray, du: np.ndarray):
+    """(Y + dY, exp(du) * q) body by body."""
+    Yp = Y + dY
+    qp = np.array([geometry.quat_mul(geometry.quat_exp(du[k]), q[k]) for k in range(Y.shape[0])])
+    return Yp, qp
+
+
+def rfd_divergence(layout, Y, q, W, Wt, calV, p: Params) -> float:
+    """Step 3(b): one-sample random finite difference of div(calV) (Eq. 16 and its footnote)."""
+    d = p.rfd_delta
+    L = _lengths(layout, p.a)
+    Wt = Wt.reshape(-1, 6)
+    Yt, qt = perturbed_state(layout, Y, q, d * L[:, None] * Wt[:, :3], d * Wt[:, 3:])
+    calVt = projected_velocity(layout, Yt, qt, W, p)
+    dV = calVt - calV
+    return float(((Wt[:, :3] * dV[:, :3]).sum(axis=1) / (d * L)).sum()
+                 + (Wt[:, 3:] * dV[:, 3:]).sum() / d)
+
+
+def fd_divergence(layout, Y, q, W, calV, p: Params) -> float:
+    """Step 3(a): one-sided finite differences over every body coordinate (Eq. 15)."""
+    d = p.rfd_delta
+    L = _lengths(layout, p.a)
+    total = 0.0
+    for k in range(layout.n_bodies):
+        for c in range(6):
+            dY = np.zeros((layout.n_bodies, 3))
+            du = np.zeros((layout.n_bodies, 3))
+            if c < 3:
+                dY[k, c] = d * L[k]
+            else:
+                du[k, c - 3] = d
+            Vp = projected_velocity(layout, *perturbed_state(layout, Y, q, dY, du), W, p)
+            total += (Vp[k, c] - calV[k, c]) / (d * L[k] if c < 3 else d)
+    return float(total)
+
+
+def midpoint_solve(layout, Ym, qm, W, p: Params):
+    """Step 5: full mobility solve at the mid-step with the same W (Eq. 19)."""
+    r, M, K, B, vb = brownian_slip(layout, Ym, qm, W, p)
+    f = forces.blob_forces(r, layout.blob_body, p.rep_A, p.rep_b, p.a)
+    FT = forces.body_force_torque(r, Ym, layout.blob_body, f)
+    slip = vb.copy()
+    if p.shear_rate != 0.0:
+        uinf = np.zeros_like(r)
+        uinf[:, 0] = p.shear_rate * r[:, 1]
+        slip = slip + uinf.reshape(-1)
+    lam, V = rigid.saddle_solve(M, K, B, slip, FT)
+    return dict(r=r, M=M, K=K, B=B, vb=vb, FT=FT, slip=slip, lam=lam, V=V.reshape(-1, 6))
+
+
+def gdc_step(layout, Y, q, W, Wt, p: Params, div: str = "rfd") -> dict:
+    """One gDC step (Sec. 3, steps 2-6) from (Y, q) with given W (3M) and W-tilde (6N)."""
+    # step 2
+    r0, M0, K0, B0, vb0 = brownian_slip(layout, Y, q, W, p)
+    calV = rigid.lsq_velocity(K0, B0, vb0).reshape(-1, 6)
+    # step 3
+    if div == "rfd":
+        dv = rfd_divergence(layout, Y, q, W, Wt, calV, p)
+    elif div == "fd":
+        dv = fd_divergence(layout, Y, q, W, calV, p)
+    else:
+        raise ValueError(div)
+    nu = 1.0 + 0.5 * p.dt * dv
+    # step 4
+    Ym, qm = geometry.advance(Y, q, calV, 0.5 * p.dt)
+    # step 5
+    mid = midpoint_solve(layout, Ym, qm, W, p)
+    # step 6
+    Y1, q1 = geometry.advance(Y, q, mid["V"], nu * p.dt)
+    return dict(r0=r0, vb0=vb0, calV=calV, div=dv, nu=nu, Ym=Ym, qm=qm, Y1=Y1, q1=q1, **mid)
+
+
+def em_step(layout, Y, q, W, p: Params) -> dict:
+    """Euler-Maruyama (App. D): one full solve at x^n, then x^(n+1) = x^n + dt V^n."""
+    sol = midpoint_solve(layout, Y, q, W, p)
+    Y1, q1 = geometry.advance(Y, q, sol["V"], p.dt)
+    return dict(Y1=Y1, q1=q1, **sol)
+
+
+def body_mobility_at(layout, Y, q, p: Params) -> np.ndarray:
+    """Dense N(x) = (K^T M^-1 K)^-1 at state (Y, q) (Eq. 12)."""
+    r = geometry.blob_positions(layout, Y, q)
+    M = rpy.rpy_matrix(r, p.a, p.eta)
+    K = rigid.k_matrix(r, Y, layout.blob_body)
+    B = rigid.rigid_basis(K, layout.n_bodies)
+    return rigid.body_mobility(M, K, B)
+
+
+def mobility_divergence(layout, Y, q, p: Params, h: float = 1e-5) -> np.ndarray:
+    """(div N)_i = sum_j d N_ij / d x_j by central differences in x = (Y, u) with u = 0 (App. E)."""
+    n = layout.n_bodies
+    out = np.zeros(6 * n)
+    for k in range(n):
+        for c in range(6):
+            dY = np.zeros((n, 3))
+            du = np.zeros((n, 3))
+            if c < 3:
+                dY[k, c] = h
+            else:
+                du[k, c - 3] = h
+            Np = body_mobility_at(layout, *perturbed_state(layout, Y, q, dY, du), p)
+            Nm = body_mobility_at(layout, *perturbed_state(layout, Y, q, -dY, -du), p)
+            out += (Np[:, 6 * k + c] - Nm[:, 6 * k + c]) / (2.0 * h)
+    return out
+
+
+def draw_W(seed: int, susp: int, step: int, n_blobs: int) -> np.ndarray:
+    from . import philox
+    return philox.normals(seed, susp, step, philox.STREAM_W, 3 * n_blobs)
+
+
+def draw_Wt(seed: int, susp: int, step: int, n_bodies: int) -> np.ndarray:
+    from . import philox
+    return philox.normals(seed, susp, step, philox.STREAM_WTILDE, 6 * n_bodies)

@@ -1,0 +1,119 @@
+"""Oracle rigid-body algebra: K, K^T K, the saddle point, N and step-2 least squares.
+
+TEST INFRASTRUCTURE ONLY.  Dense FP64 restatements of Sec. 2.2 (Eqs. 7-15),
+Sec. 3 step 2 (Eqs. 17-18) and Sec. 5 (the closed form of (K^T K)^(p)).
+
+Rank-deficient bodies.  A body whose blobs are collinear (a rod) cannot be
+spun about its own axis by any blob velocity: K_p has a null vector, so
+K_p^T K_p, K^T M^-1 K and the saddle matrix are singular.  The paper's
+bodies never meet this.  Reading used here: such a body has only the rigid
+motions that move some blob; the axial spin is defined to be zero.  Every
+solve below is therefore done in the reduced basis B_p (the eigenvectors of
+K_p^T K_p with non-zero eigenvalue), and results are mapped back with
+V_p = B_p V_red, which equals applying the Moore-Penrose pseudo-inverse.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .geometry import cross_matrix
+
+
+def k_matrix(r: np.ndarray, Y: np.ndarray, blob_body: np.ndarray) -> np.ndarray:
+    """K (3M x 6N): block (i, p) = [I_3, [x (r_i - Y_p)]] if blob i is in body p, else 0 (Eq. 9).
+
+    [x v] = -[v x], so [x (r_i - Y_p)] Omega = Omega x (r_i - Y_p) (Eq. 6).
+    """
+    m = r.shape[0]
+    n = Y.shape[0]
+    K = np.zeros((3 * m, 6 * n))
+    for i in range(m):
+        p = int(blob_body[i])
+        K[3 * i:3 * i + 3, 6 * p:6 * p + 3] = np.eye(3)
+        K[3 * i:3 * i + 3, 6 * p + 3:6 * p + 6] = -cross_matrix(r[i] - Y[p])
+    return K
+
+
+def ktk_closed_form(r: np.ndarray, Y: np.ndarray, blob_body: np.ndarray, p: int) -> np.ndarray:
+    """(K^T K)^(p) as printed in Sec. 5: [[N_b I, sum [x d]], [sum [d x], -sum [d x]^2]], d = r_i - Y_p."""
+    idx = np.nonzero(blob_body == p)[0]
+    out = np.zeros((6, 6))
+    out[:3, :3] = len(idx) * np.eye(3)
+    for i in idx:
+        c = cross_matrix(r[i] - Y[p])
+        out[:3, 3:] += -c
+        out[3:, :3] += c
+        out[3:, 3:] += -(c @ c)
+    return out
+
+
+def rigid_basis(K: np.ndarray, n_bodies: int, rel_tol: float = 1e-10) -> np.ndarray:
+    """Block-diagonal basis B (6N x n_red) of the rigid motions that move some blob.
+
+    For each body, the eigenvectors of K_p^T K_p whose eigenvalue exceeds
+    rel_tol times the largest one.  B = I for every body that is not collinear.
+    """
+    cols = []
+    for p in range(n_bodies):
+        Kp = K[:, 6 * p:6 * p + 6]
+        g = Kp.T @ Kp
+        w, v = np.linalg.eigh(g)
+        keep = w > rel_tol * w.max()
+        if keep.all():
+            v = np.eye(6)
+        else:
+            v = v[:, keep]
+        blk = np.zeros((6 * n_bodies, v.shape[1]))
+        blk[6 * p:6 * p + 6] = v
+        cols.append(blk)
+    return np.hstack(cols)
+
+
+def saddle_solve(M: np.ndarray, K: np.ndarray, B: np.ndarray, slip: np.ndarray, F: np.ndarray):
+    """Solve [[M, -K], [-K^T, 0]] [lambda; V] = [-slip; -F] by dense LU (Eqs. 10, 14).
+
+    slip is the blob velocity on the right-hand side (the Brownian velocity
+    v-breve, plus the background flow where there is one); F stacks [F_p; T_p]
+    per body.  Returns (lambda, V) with V in the full 6N coordinates.
+    """
+    m3 = M.shape[0]
+    KB = K @ B
+    nr = KB.shape[1]
+    A = np.zeros((m3 + nr, m3 + nr))
+    A[:m3, :m3] = M
+    A[:m3, m3:] = -KB
+    A[m3:, :m3] = -KB.T
+    rhs = np.concatenate([-slip, -(B.T @ F)])
+    sol = np.linalg.solve(A, rhs)
+    return sol[:m3], B @ sol[m3:]
+
+
+def saddle_apply(M: np.ndarray, K: np.ndarray, lam: np.ndarray, V: np.ndarray):
+    """The saddle operator applied to [lambda; V]: [M lambda - K V; -K^T lambda]."""
+    return M @ lam - K @ V, -(K.T @ lam)
+
+
+def body_mobility(M: np.ndarray, K: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """N = (K^T M^-1 K)^-1 (Eq. 12), in the reduced basis: N = B (B^T K^T M^-1 K B)^-1 B^T."""
+    KB = K @ B
+    G = KB.T @ np.linalg.solve(M, KB)
+    return B @ np.linalg.inv(G) @ B.T
+
+
+def lsq_velocity(K: np.ndarray, B: np.ndarray, vb: np.ndarray) -> np.ndarray:
+    """Step 2 (Eq. 18): V = (K^T K)^-1 K^T v-breve, i.e. argmin ||K V - v-breve||."""
+    KB = K @ B
+    return B @ np.linalg.solve(KB.T @ KB, KB.T @ vb)
+
+
+def sqrtm_sym(M: np.ndarray) -> np.ndarray:
+    """Principal (symmetric) square root Q diag(sqrt(mu)) Q^T of the SPD matrix M."""
+    w, Q = np.linalg.eigh(M)
+    if w.min() <= 0.0:
+        raise np.linalg.LinAlgError("M is not positive definite")
+    return (Q * np.sqrt(w)) @ Q.T
+
+
+def sqrtm_chol(M: np.ndarray) -> np.ndarray:
+    """Lower Cholesky factor L with L L^T = M (another valid M^(1/2), Eq. 15)."""
+    return np.linalg.cholesky(M)
