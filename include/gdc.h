@@ -1,0 +1,200 @@
+/*
+ * gdc.h -- C ABI of the GB300 library for the generalised drift-correcting
+ * (gDC) time step of Brownian suspensions of rigid multiblob bodies
+ * (Westwood, Delmotte & Keaveny, arXiv 2106.00449).
+ *
+ * Model (Sec. 2): N rigid bodies, body p at centre Y_p with unit quaternion
+ * q_p = (q0, q1, q2, q3) (scalar first, App. A), made of blobs of radius a
+ * placed at r_i = Y_p + R(q_p) b_i (Eq. 1).  Blobs interact through the
+ * unbounded Rotne-Prager-Yamakawa tensor including its overlapping-blob form
+ * (Sec. 4.1).  lambda (3 per blob) is the force a blob exerts on the fluid
+ * (Eq. 5); V_p = [Ydot_p, Omega_p] (Sec. 2.2); F_p = [force; torque].
+ *
+ * Memory.  Every array argument named "dev" is device memory owned by the
+ * caller; every "host" array is host memory owned by the caller.  The
+ * library allocates no device memory: the caller passes one workspace of
+ * gdc_workspace_bytes() bytes to gdc_init and keeps it alive until
+ * gdc_destroy.  All work is issued on the stream given to gdc_init, in
+ * order; calls that return info structs synchronise that stream first.
+ *
+ * Batching.  One context holds S independent suspensions.  Bodies are
+ * numbered suspension by suspension (susp_body_off), blobs body by body in
+ * template order.  Suspensions never interact; each has its own nu, its
+ * own Krylov spaces and its own random stream.
+ *
+ * Errors.  Every call returns a gdc_status; a non-OK status leaves a one-line
+ * description in gdc_last_error(ctx).  Invalid sizes, non-unit quaternions,
+ * a too-small workspace and out-of-range parameters are rejected on the
+ * host before any launch.  Nothing aborts, traps or hangs: Krylov loops stop
+ * at their iteration limits and report GDC_ERR_NOT_CONVERGED, non-finite
+ * results report GDC_ERR_NONFINITE.
+ */
+#ifndef GDC_H
+#define GDC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GDC_OK = 0,
+    GDC_ERR_INVALID_ARG = 1,
+    GDC_ERR_CUDA = 2,
+    GDC_ERR_NOT_CONVERGED = 3,
+    GDC_ERR_NONFINITE = 4,
+    GDC_ERR_TIMEOUT = 5,
+    GDC_ERR_WORKSPACE = 6
+} gdc_status;
+
+/* Precision of the O(N_b^2) pair evaluations.  GDC_FP64: everything in FP64.
+ * GDC_FP32_MIXED: pair kernels in FP32 (FP64 across tiles); Krylov
+ * recurrences, the preconditioner and the state in FP64; the mobility solve
+ * restarts from an FP64 residual until that residual meets gmres_tol. */
+typedef enum { GDC_FP64 = 0, GDC_FP32_MIXED = 1 } gdc_precision;
+
+/* Divergence estimate of Sec. 3 step 3: random finite differences (Eq. 16)
+ * or finite differences over every body coordinate (Eq. 15). */
+typedef enum { GDC_DIV_RFD = 0, GDC_DIV_FD = 1 } gdc_divmode;
+
+/* Time integrator: the gDC of Sec. 3, or Euler-Maruyama of App. D (no drift). */
+typedef enum { GDC_SCHEME_GDC = 0, GDC_SCHEME_EM = 1 } gdc_scheme;
+
+typedef struct {
+    double eta;            /* fluid viscosity (Sec. 4.2)                               */
+    double kT;             /* thermal energy k_B T (Eq. 4)                             */
+    double a;              /* blob radius (Sec. 4.1)                                   */
+    double dt;             /* time step Delta t (Sec. 3)                               */
+    double gmres_tol;      /* relative residual of the mobility solve (Sec. 2.2, 5)   */
+    int    gmres_max_iter; /* total inner GMRES iterations allowed per solve           */
+    int    gmres_restart;  /* Krylov basis size per cycle, 2..100                      */
+    double lanczos_tol;    /* relative change of M^(1/2) W between iterations (Sec. 4.1) */
+    int    lanczos_max_iter; /* 2..128                                                */
+    double rfd_delta;      /* delta of Eqs. 15-16 (Sec. 6.2 uses 1e-6)                 */
+    int    precision;      /* gdc_precision                                            */
+    int    divmode;        /* gdc_divmode                                              */
+    int    scheme;         /* gdc_scheme                                               */
+    double rep_A;          /* soft repulsion amplitude A (force units), 0 = off        */
+    double rep_b;          /* soft repulsion range b (Eq. 20)                          */
+    double shear_rate;     /* background flow u = (shear_rate * y, 0, 0); 0 = off      */
+    unsigned long long seed; /* Philox4x32-10 key of the W and W-tilde draws            */
+} gdc_params;
+
+typedef struct {
+    int    iterations;     /* inner GMRES iterations (largest over suspensions)        */
+    int    cycles;         /* restart / refinement cycles                              */
+    int    matvecs_fp32;   /* RPY products evaluated in FP32                           */
+    int    matvecs_fp64;   /* RPY products evaluated in FP64                           */
+    double residual;       /* largest relative FP64 residual ||b - A x|| / ||b||        */
+    int    converged;      /* 1 when every suspension met gmres_tol                    */
+} gdc_solve_info;
+
+typedef struct {
+    unsigned long long step;      /* step counter the draws of this step used          */
+    int    lanczos_iters[3];      /* at x^n, at x^n + delta W~ (or all FD states), at x^m */
+    double lanczos_err;           /* largest final Lanczos change estimate             */
+    gdc_solve_info solve;         /* the mid-step mobility solve (Sec. 3 step 5)       */
+    double nu_min, nu_max;        /* range of nu over suspensions (Sec. 3 step 3)      */
+    double pair_evals;            /* ordered blob pairs evaluated by RPY products      */
+} gdc_step_info;
+
+/* Device pointers that gdc_step fills with the intermediates of its LAST
+ * step (any may be NULL).  Layouts: calV, Vm: 6 per body; nu: 1 per
+ * suspension; Ym: 3 per body; qm: 4 per body; vb_n, vb_m: 3 per blob. */
+typedef struct {
+    double* calV;   /* step 2 rigid projection of v-breve at x^n           */
+    double* nu;     /* step 3                                               */
+    double* Ym;     /* step 4 mid-step centres                              */
+    double* qm;     /* step 4 mid-step quaternions                          */
+    double* Vm;     /* step 5 mid-step body velocities                      */
+    double* vb_n;   /* v-breve at x^n                                       */
+    double* vb_m;   /* v-breve at x^m                                       */
+    double* FTm;    /* mid-step body forces and torques, 6 per body         */
+} gdc_trace;
+
+typedef struct gdc_ctx gdc_ctx;
+
+/* Bytes of device workspace gdc_init needs for these sizes and parameters
+ * (0 when an argument is invalid).  tmpl_nblobs: n_templates counts;
+ * susp_body_off: n_susp+1 increasing offsets starting at 0; body_tmpl: one
+ * template index per body (host arrays). */
+size_t gdc_workspace_bytes(const gdc_params* params, int n_templates, const int* tmpl_nblobs,
+                           int n_susp, const long long* susp_body_off, const int* body_tmpl);
+
+/* Create a context.  Templates are body-frame blob coordinates (host,
+ * 3 doubles per blob, templates back to back); the library re-centres each
+ * on its blob centroid, which is then Y_p (Sec. 2).  Y (dev, 3 per body) and
+ * q (dev, 4 per body, unit) are the caller's state arrays; gdc_step updates
+ * them in place.  Precomputes each template's preconditioner block (FP64
+ * Cholesky of its RPY block, Sec. 2.2 and the block-diagonal P that follows
+ * Eq. 15) on the device.  stream is a cudaStream_t (NULL = default stream). */
+gdc_status gdc_init(gdc_ctx** ctx, const gdc_params* params,
+                    int n_templates, const int* tmpl_nblobs, const double* tmpl_xyz,
+                    int n_susp, const long long* susp_body_off, const int* body_tmpl,
+                    double* Y, double* q, void* workspace, size_t workspace_bytes, void* stream);
+
+void        gdc_destroy(gdc_ctx* ctx);
+const char* gdc_last_error(const gdc_ctx* ctx);
+
+/* Change tolerances, precision, divergence mode, scheme, forces or dt of an
+ * existing context (sizes and seed are fixed at init). */
+gdc_status gdc_set_params(gdc_ctx* ctx, const gdc_params* params);
+
+/* The rigid multiblob mobility problem at the current state (Eq. 14):
+ *   [ M  -K ] [lambda]   [ -vbrev - u_inf ]
+ *   [-K^T 0 ] [  V   ] = [ -FT            ]
+ * solved by right-preconditioned GMRES with the block-diagonal P (Sec. 2.2).
+ * FT (dev, 6 per body), vbrev (dev, 3 per blob, NULL = 0), V (dev out, 6 per
+ * body), lambda (dev out, 3 per blob, or NULL).  info (host) may be NULL. */
+gdc_status gdc_mobility_solve(gdc_ctx* ctx, const double* FT, const double* vbrev, double* V,
+                              double* lambda, gdc_solve_info* info);
+
+/* Advance the state by nsteps steps of the configured scheme (Sec. 3 steps
+ * 1-6, or App. D).  Step k draws W and W-tilde from Philox with counter
+ * (index, suspension, step, stream).  info: host array of nsteps entries, or NULL. */
+gdc_status gdc_step(gdc_ctx* ctx, int nsteps, gdc_step_info* info);
+gdc_status gdc_set_trace(gdc_ctx* ctx, const gdc_trace* trace);
+
+/* Checkpoint / resume: copy the state (host arrays, 3 and 4 doubles per body)
+ * and the step counter out of / into the context. */
+gdc_status gdc_get_state(gdc_ctx* ctx, double* Y_host, double* q_host, unsigned long long* step);
+gdc_status gdc_set_state(gdc_ctx* ctx, const double* Y_host, const double* q_host, unsigned long long step);
+
+/* ---- building blocks of the step, exposed for verification -------------- */
+
+/* Blob positions r_i = Y_p + R(q_p) b_i of the current state (dev out, 3 per blob). */
+gdc_status gdc_blob_positions(gdc_ctx* ctx, double* r);
+
+/* u = M lambda at the current state (Eq. 5, RPY of Sec. 4.1); lambda, u dev,
+ * 3 per blob; precision is a gdc_precision. */
+gdc_status gdc_rpy_apply(gdc_ctx* ctx, int precision, const double* lambda, double* u);
+
+/* The saddle operator [M lambda - K V; -K^T lambda] (Eq. 14) on x = [lambda; V]
+ * stored per suspension as [3 per blob | 6 per body] (dev in, dev out). */
+gdc_status gdc_saddle_apply(gdc_ctx* ctx, int precision, const double* x, double* y);
+
+/* z = P^-1 r for the block-diagonal preconditioner (same layout as above). */
+gdc_status gdc_precond_apply(gdc_ctx* ctx, const double* r, double* z);
+
+/* vbrev = sqrt(2 kT / dt) M^(1/2) W by Lanczos (Sec. 4.1); W, vbrev dev, 3 per blob. */
+gdc_status gdc_brownian_slip(gdc_ctx* ctx, const double* W, double* vbrev, int* iters, double* err);
+
+/* Step 2 (Eq. 18): calV = (K^T K)^-1 K^T vbrev per body; vbrev dev 3 per blob, calV dev 6 per body. */
+gdc_status gdc_lsq_velocity(gdc_ctx* ctx, const double* vbrev, double* calV);
+
+/* Soft repulsion between blobs of different bodies, summed per body (dev out, 6 per body). */
+gdc_status gdc_forces(gdc_ctx* ctx, double* FT);
+
+/* The N(0,1) draws of the step counter: stream 0 gives W (3 per blob),
+ * stream 1 gives W-tilde (6 per body). */
+gdc_status gdc_draw_normals(gdc_ctx* ctx, unsigned long long step, int stream, double* out);
+
+/* Layout helper: offset of each suspension's [lambda; V] block in the
+ * vectors of gdc_saddle_apply / gdc_precond_apply (host out, n_susp + 1). */
+gdc_status gdc_saddle_offsets(const gdc_ctx* ctx, long long* off);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GDC_H */

@@ -1,0 +1,627 @@
+// C ABI of the library (include/gdc.h): validation, workspace layout, and the
+// orchestration of the gDC step of Sec. 3 (steps 1-6) and the Euler-Maruyama step of
+// App. D on top of the kernels of the other translation units.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+
+namespace gdc {
+
+gdc_status fail(gdc_ctx* c, gdc_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+gdc_status cuda_check(gdc_ctx* c, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return GDC_OK;
+    return fail(c, GDC_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+static const char* validate_params(const gdc_params* p) {
+    if (!p) return "params is NULL";
+    if (!(p->eta > 0.0) || !std::isfinite(p->eta)) return "eta must be > 0";
+    if (!(p->kT >= 0.0) || !std::isfinite(p->kT)) return "kT must be >= 0";
+    if (!(p->a > 0.0) || !std::isfinite(p->a)) return "a must be > 0";
+    if (!(p->dt > 0.0) || !std::isfinite(p->dt)) return "dt must be > 0";
+    if (!(p->gmres_tol > 0.0) || !(p->gmres_tol < 1.0)) return "gmres_tol must be in (0, 1)";
+    if (p->gmres_max_iter < 1) return "gmres_max_iter must be >= 1";
+    if (p->gmres_restart < 2 || p->gmres_restart > GDC_MAX_RESTART) return "gmres_restart must be in [2, 100]";
+    if (!(p->lanczos_tol > 0.0) || !(p->lanczos_tol < 1.0)) return "lanczos_tol must be in (0, 1)";
+    if (p->lanczos_max_iter < 2 || p->lanczos_max_iter > GDC_MAX_LANCZOS) return "lanczos_max_iter must be in [2, 128]";
+    if (!(p->rfd_delta > 0.0) || !(p->rfd_delta < 1.0)) return "rfd_delta must be in (0, 1)";
+    if (p->precision != GDC_FP64 && p->precision != GDC_FP32_MIXED) return "unknown precision";
+    if (p->divmode != GDC_DIV_RFD && p->divmode != GDC_DIV_FD) return "unknown divmode";
+    if (p->scheme != GDC_SCHEME_GDC && p->scheme != GDC_SCHEME_EM) return "unknown scheme";
+    if (!(p->rep_A >= 0.0) || !std::isfinite(p->rep_A)) return "rep_A must be >= 0";
+    if (p->rep_A > 0.0 && !(p->rep_b > 0.0)) return "rep_b must be > 0 when rep_A > 0";
+    if (!std::isfinite(p->shear_rate)) return "shear_rate must be finite";
+    return nullptr;
+}
+
+// Host-side layout of a context from the user's sizes (no device work).
+static const char* build_host_layout(gdc_ctx* c, const gdc_params* p, int n_templates, const int* tmpl_nblobs,
+                                     int n_susp, const long long* susp_body_off, const int* body_tmpl) {
+    if (const char* m = validate_params(p)) return m;
+    if (n_templates < 1 || !tmpl_nblobs) return "need at least one template";
+    if (n_susp < 1 || !susp_body_off) return "need at least one suspension";
+    if (susp_body_off[0] != 0) return "susp_body_off[0] must be 0";
+    for (int s = 0; s < n_susp; ++s)
+        if (susp_body_off[s + 1] < susp_body_off[s]) return "susp_body_off must be non-decreasing";
+    const long long NB = susp_body_off[n_susp];
+    if (NB < 1) return "no bodies";
+    if (NB > (1LL << 28)) return "too many bodies";
+    if (!body_tmpl) return "body_tmpl is NULL";
+    c->p = *p;
+    c->T = n_templates;
+    c->S = n_susp;
+    c->NB = (int)NB;
+    c->h_tmpl_n.assign(tmpl_nblobs, tmpl_nblobs + n_templates);
+    c->h_tmpl_off.assign(n_templates + 1, 0);
+    c->h_minv_off.assign(n_templates + 1, 0);
+    for (int t = 0; t < n_templates; ++t) {
+        if (tmpl_nblobs[t] < 1 || tmpl_nblobs[t] > GDC_MAX_TMPL_BLOBS) return "template blob count must be in [1, 340]";
+        c->h_tmpl_off[t + 1] = c->h_tmpl_off[t] + tmpl_nblobs[t];
+        c->h_minv_off[t + 1] = c->h_minv_off[t] + 9LL * tmpl_nblobs[t] * tmpl_nblobs[t];
+    }
+    c->h_body_off.assign(susp_body_off, susp_body_off + n_susp + 1);
+    c->h_body_tmpl.assign(body_tmpl, body_tmpl + NB);
+    c->h_body_blob_off.assign(NB + 1, 0);
+    c->h_body_susp.assign(NB, 0);
+    c->max_body_blobs = 0;
+    for (long long b = 0; b < NB; ++b) {
+        const int t = body_tmpl[b];
+        if (t < 0 || t >= n_templates) return "body_tmpl entry out of range";
+        c->h_body_blob_off[b + 1] = c->h_body_blob_off[b] + tmpl_nblobs[t];
+        c->max_body_blobs = std::max(c->max_body_blobs, tmpl_nblobs[t]);
+    }
+    const long long NBL = c->h_body_blob_off[NB];
+    if (3 * NBL + 6 * NB > (1LL << 30)) return "too many blobs";
+    c->NBL = (int)NBL;
+    c->h_blob_off.assign(n_susp + 1, 0);
+    c->h_gm_off.assign(n_susp + 1, 0);
+    for (int s = 0; s < n_susp; ++s) {
+        for (long long b = susp_body_off[s]; b < susp_body_off[s + 1]; ++b) c->h_body_susp[b] = s;
+        c->h_blob_off[s + 1] = c->h_body_blob_off[susp_body_off[s + 1]];
+        const long long nbl = c->h_blob_off[s + 1] - c->h_blob_off[s];
+        const long long nbd = susp_body_off[s + 1] - susp_body_off[s];
+        c->h_gm_off[s + 1] = c->h_gm_off[s] + 3 * nbl + 6 * nbd;
+    }
+    c->ngm = c->h_gm_off[n_susp];
+    c->m = p->gmres_restart;
+    c->kmax = p->lanczos_max_iter;
+    c->red_cols = std::max(c->m + 1, c->kmax + 1);
+    c->red_cols = (c->red_cols + 7) / 8 * 8;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
+    c->device = dev;
+    c->num_sms = sms;
+    build_mv_items(c);
+    setup_segments(c);
+    return nullptr;
+}
+
+// Sequential carving of the caller's workspace with 256-byte alignment.
+struct Carver {
+    char* base;
+    size_t off = 0;
+    explicit Carver(void* b) : base((char*)b) {}
+    template <typename T>
+    T* take(long long count) {
+        off = (off + 255) & ~(size_t)255;
+        T* ptr = base ? (T*)(base + off) : nullptr;
+        off += sizeof(T) * (size_t)std::max<long long>(count, 1);
+        return ptr;
+    }
+};
+
+static size_t carve(gdc_ctx* c, void* base) {
+    Carver w(base);
+    const long long S = c->S, NB = c->NB, NBL = c->NBL, T = c->T;
+    const long long nt = c->h_tmpl_off[T];
+    const long long cols = c->red_cols;
+    c->susp_body_off = w.take<long long>(S + 1);
+    c->susp_blob_off = w.take<long long>(S + 1);
+    c->susp_gm_off = w.take<long long>(S + 1);
+    c->body_blob_off = w.take<long long>(NB + 1);
+    c->minv_off = w.take<long long>(T + 1);
+    c->body_tmpl = w.take<int>(NB);
+    c->body_susp = w.take<int>(NB);
+    c->blob_body = w.take<int>(NBL);
+    c->blob_susp = w.take<int>(NBL);
+    c->tmpl_n = w.take<int>(T);
+    c->tmpl_off = w.take<int>(T + 1);
+    c->blob_gm = w.take<int>(NBL);
+    c->body_gm = w.take<int>(NB);
+    c->tmpl_xyz = w.take<double>(3 * nt);
+    c->tmpl_L = w.take<double>(T);
+    c->tmpl_Minv = w.take<double>(c->h_minv_off[T]);
+    c->tmpl_G = w.take<double>(18 * nt);
+    c->tmpl_N = w.take<double>(36 * T);
+    c->tmpl_KtKp = w.take<double>(36 * T);
+    c->tmpl_work = w.take<double>(2 * c->h_minv_off[T]);
+    c->body_L = w.take<double>(NB);
+    c->Rb = w.take<double>(9 * NB);
+    c->r = w.take<double>(3 * NBL);
+    c->Yc = w.take<double>(3 * NB);
+    c->ref = w.take<double>(3 * S);
+    c->spos = w.take<float4>(NBL);
+    c->slam = w.take<float4>(NBL);
+    c->spos64 = w.take<double4>(NBL);
+    c->slam64 = w.take<double4>(NBL);
+    c->W = w.take<double>(3 * NBL);
+    c->Wt = w.take<double>(6 * NB);
+    c->vb_n = w.take<double>(3 * NBL);
+    c->vb_t = w.take<double>(3 * NBL);
+    c->vb_m = w.take<double>(3 * NBL);
+    c->calV = w.take<double>(6 * NB);
+    c->calVt = w.take<double>(6 * NB);
+    c->Yt = w.take<double>(3 * NB);
+    c->qt = w.take<double>(4 * NB);
+    c->Ym = w.take<double>(3 * NB);
+    c->qm = w.take<double>(4 * NB);
+    c->FT = w.take<double>(6 * NB);
+    c->Vm = w.take<double>(6 * NB);
+    c->nu = w.take<double>(S);
+    c->divp = w.take<double>(S);
+    c->fblob = w.take<double>(3 * NBL);
+    c->u3 = w.take<double>(3 * NBL);
+    const long long m = c->m, n = c->ngm;
+    c->gm_V = w.take<double>((m + 1) * n);
+    c->gm_x = w.take<double>(n);
+    c->gm_b = w.take<double>(n);
+    c->gm_r = w.take<double>(n);
+    c->gm_w = w.take<double>(n);
+    c->gm_z = w.take<double>(n);
+    c->gm_H = w.take<double>(S * (m + 1) * m);
+    c->gm_cs = w.take<double>(S * m);
+    c->gm_sn = w.take<double>(S * m);
+    c->gm_g = w.take<double>(S * (m + 1));
+    c->gm_y = w.take<double>(S * cols);
+    c->gm_h = w.take<double>(S * cols);
+    c->gm_h2 = w.take<double>(S * cols);
+    c->gm_bnorm = w.take<double>(S);
+    c->gm_res = w.take<double>(2 * S);
+    c->gm_scal = w.take<double>(S);
+    c->gm_active = w.take<int>(2 * S);
+    c->gm_j = w.take<int>(S);
+    const long long k = c->kmax, nl = 3 * NBL;
+    c->lz_V = w.take<double>((k + 1) * nl);
+    c->lz_w = w.take<double>(nl);
+    c->lz_alpha = w.take<double>(S * k);
+    c->lz_beta = w.take<double>(S * k);
+    c->lz_c = w.take<double>(S * k);
+    c->lz_cprev = w.take<double>(S * k);
+    c->lz_h = w.take<double>(S * cols);
+    c->lz_Wnorm = w.take<double>(S);
+    c->lz_err = w.take<double>(S);
+    c->lz_scal = w.take<double>(S);
+    c->lz_active = w.take<int>(S);
+    c->lz_k = w.take<int>(S);
+    c->lz_fix = w.take<int>(S);
+    c->seg_gm.chunks = w.take<Chunk>(c->seg_gm.n_chunks);
+    c->seg_gm.seg_chunk_off = w.take<int>(S + 1);
+    c->seg_gm.off = c->susp_gm_off;
+    c->seg_lz.chunks = w.take<Chunk>(c->seg_lz.n_chunks);
+    c->seg_lz.seg_chunk_off = w.take<int>(S + 1);
+    c->red_part = w.take<double>((long long)std::max(c->seg_gm.n_chunks, c->seg_lz.n_chunks) * cols);
+    c->mv_items = w.take<MvItem>(c->mv_n_items);
+    c->mv_nk = w.take<int>(S);
+    c->mv_part = (void*)w.take<double4>((long long)c->mv_kmax * NBL);
+    c->dev_status = w.take<int>(4);
+    return w.off + 256;
+}
+
+template <typename T>
+static cudaError_t up(gdc_ctx* c, T* dst, const T* src, size_t count) {
+    return cudaMemcpyAsync(dst, src, sizeof(T) * count, cudaMemcpyHostToDevice, c->stream);
+}
+
+static gdc_status upload_layout(gdc_ctx* c, const double* tmpl_xyz_centred) {
+    const int S = c->S, NB = c->NB, NBL = c->NBL, T = c->T;
+    std::vector<int> blob_body(NBL), blob_susp(NBL), blob_gm(NBL), body_gm(NB);
+    std::vector<double> body_L(NB);
+    for (int b = 0; b < NB; ++b) {
+        const int s = c->h_body_susp[b];
+        const long long lb = b - c->h_body_off[s];
+        body_gm[b] = (int)(c->h_gm_off[s] + 3 * (c->h_blob_off[s + 1] - c->h_blob_off[s]) + 6 * lb);
+        body_L[b] = c->h_tmpl_L[c->h_body_tmpl[b]];
+        for (long long i = c->h_body_blob_off[b]; i < c->h_body_blob_off[b + 1]; ++i) {
+            blob_body[i] = b;
+            blob_susp[i] = s;
+            blob_gm[i] = (int)(c->h_gm_off[s] + 3 * (i - c->h_blob_off[s]));
+        }
+    }
+    cudaError_t e = cudaSuccess;
+    auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+    chk(up(c, c->susp_body_off, c->h_body_off.data(), S + 1));
+    chk(up(c, c->susp_blob_off, c->h_blob_off.data(), S + 1));
+    chk(up(c, c->susp_gm_off, c->h_gm_off.data(), S + 1));
+    chk(up(c, c->body_blob_off, c->h_body_blob_off.data(), NB + 1));
+    chk(up(c, c->minv_off, c->h_minv_off.data(), T + 1));
+    chk(up(c, c->body_tmpl, c->h_body_tmpl.data(), NB));
+    chk(up(c, c->body_susp, c->h_body_susp.data(), NB));
+    chk(up(c, c->blob_body, blob_body.data(), NBL));
+    chk(up(c, c->blob_susp, blob_susp.data(), NBL));
+    chk(up(c, c->tmpl_n, c->h_tmpl_n.data(), T));
+    chk(up(c, c->tmpl_off, c->h_tmpl_off.data(), T + 1));
+    chk(up(c, c->blob_gm, blob_gm.data(), NBL));
+    chk(up(c, c->body_gm, body_gm.data(), NB));
+    chk(up(c, c->tmpl_xyz, tmpl_xyz_centred, 3 * c->h_tmpl_off[T]));
+    chk(up(c, c->tmpl_L, c->h_tmpl_L.data(), T));
+    chk(up(c, c->body_L, body_L.data(), NB));
+    chk(up(c, c->seg_gm.chunks, c->seg_gm.h_chunks.data(), c->seg_gm.h_chunks.size()));
+    chk(up(c, c->seg_gm.seg_chunk_off, c->seg_gm.h_seg_chunk_off.data(), S + 1));
+    chk(up(c, c->seg_lz.chunks, c->seg_lz.h_chunks.data(), c->seg_lz.h_chunks.size()));
+    chk(up(c, c->seg_lz.seg_chunk_off, c->seg_lz.h_seg_chunk_off.data(), S + 1));
+    chk(up(c, c->mv_items, c->h_mv_items.data(), c->h_mv_items.size()));
+    chk(up(c, c->mv_nk, c->h_mv_nk.data(), S));
+    chk(cudaMemsetAsync(c->dev_status, 0, 4 * sizeof(int), c->stream));
+    chk(cudaStreamSynchronize(c->stream));  // host vectors above go out of scope
+    return cuda_check(c, e, "upload of the layout");
+}
+
+static gdc_status check_state_host(gdc_ctx* c, const double* Y, const double* q) {
+    for (int p = 0; p < c->NB; ++p) {
+        double n2 = 0.0;
+        for (int k = 0; k < 4; ++k) n2 += q[4 * p + k] * q[4 * p + k];
+        if (!(std::fabs(n2 - 1.0) <= 1e-10)) return fail(c, GDC_ERR_INVALID_ARG, "quaternion of body " + std::to_string(p) + " is not unit");
+        for (int k = 0; k < 3; ++k)
+            if (!std::isfinite(Y[3 * p + k])) return fail(c, GDC_ERR_INVALID_ARG, "non-finite body centre");
+    }
+    return GDC_OK;
+}
+
+static gdc_status read_status(gdc_ctx* c) {
+    int st[4] = {0, 0, 0, 0};
+    cudaError_t e = cudaMemcpyAsync(st, c->dev_status, sizeof(st), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "status read");
+    if (st[0] == 1) return fail(c, GDC_ERR_NONFINITE, "template RPY block is not positive definite");
+    if (st[0] == 2) return fail(c, GDC_ERR_NOT_CONVERGED, "tridiagonal eigensolver did not converge");
+    return GDC_OK;
+}
+
+// ---- the steps -------------------------------------------------------------------------
+
+static void load_at(gdc_ctx* c, const double* Y, const double* q) {
+    launch_ref(c, Y);
+    load_config(c, Y, q);
+}
+
+static gdc_status forces_at_loaded(gdc_ctx* c, double* FT) {
+    if (c->p.rep_A > 0.0) {
+        launch_forces_pair(c, c->p.precision, c->fblob);
+        launch_body_KT(c, c->fblob, 0, FT, 0, 1.0);
+    } else {
+        cudaMemsetAsync(FT, 0, sizeof(double) * 6 * c->NB, c->stream);
+    }
+    return GDC_OK;
+}
+
+// v-breve = sqrt(2 kT / dt) M^(1/2) W at the loaded configuration
+static gdc_status slip_at_loaded(gdc_ctx* c, const double* W, double* vb, int fixed, int* iters, double* err) {
+    const double scale = std::sqrt(2.0 * c->p.kT / c->p.dt);
+    if (c->p.kT == 0.0) {
+        if (iters) *iters = 0;
+        if (err) *err = 0.0;
+        return cuda_check(c, cudaMemsetAsync(vb, 0, sizeof(double) * 3 * c->NBL, c->stream), "memset");
+    }
+    return lanczos_sqrt(c, W, vb, scale, fixed, iters, err);
+}
+
+static gdc_status one_step(gdc_ctx* c, gdc_step_info* info) {
+    gdc_step_info inf{};
+    inf.step = c->step;
+    gdc_status st;
+    const double dt = c->p.dt;
+    int matvecs = 0;
+    launch_normals(c, c->step, 0, c->W);
+    launch_normals(c, c->step, 1, c->Wt);
+    if (c->p.scheme == GDC_SCHEME_EM) {
+        // App. D: one full solve at x^n, then x^(n+1) = x^n + dt V^n
+        load_at(c, c->Y, c->q);
+        forces_at_loaded(c, c->FT);
+        if ((st = slip_at_loaded(c, c->W, c->vb_m, 0, &inf.lanczos_iters[2], &inf.lanczos_err)) != GDC_OK) return st;
+        launch_rhs(c, c->vb_m, c->FT, c->gm_b);
+        st = gmres_solve(c, c->gm_b, c->gm_x, &inf.solve);
+        if (st != GDC_OK) return st;
+        launch_scatter_solution(c, c->gm_x, c->Vm, nullptr);
+        launch_advance(c, c->Y, c->q, c->Vm, dt, nullptr, c->Y, c->q);
+        matvecs = inf.lanczos_iters[2] + inf.solve.matvecs_fp32 + inf.solve.matvecs_fp64;
+    } else {
+        // step 2 at x^n
+        load_at(c, c->Y, c->q);
+        if ((st = slip_at_loaded(c, c->W, c->vb_n, 0, &inf.lanczos_iters[0], &inf.lanczos_err)) != GDC_OK) return st;
+        launch_lsq(c, c->vb_n, c->calV);
+        // step 3: divergence of calV
+        double e2 = 0.0;
+        if (c->p.divmode == GDC_DIV_RFD) {
+            launch_perturb(c, c->Y, c->q, c->Wt, c->p.rfd_delta, c->Yt, c->qt);
+            load_config(c, c->Yt, c->qt);  // same reference point as x^n
+            cudaMemcpyAsync(c->lz_fix, c->lz_k, sizeof(int) * c->S, cudaMemcpyDeviceToDevice, c->stream);
+            if ((st = slip_at_loaded(c, c->W, c->vb_t, 1, &inf.lanczos_iters[1], &e2)) != GDC_OK) return st;
+            launch_lsq(c, c->vb_t, c->calVt);
+            launch_rfd_div(c, c->Wt, c->calV, c->calVt, c->p.rfd_delta, dt, c->nu);
+        } else {
+            int maxn = 0;
+            for (int s = 0; s < c->S; ++s) maxn = std::max<int>(maxn, (int)(c->h_body_off[s + 1] - c->h_body_off[s]));
+            cudaMemcpyAsync(c->lz_fix, c->lz_k, sizeof(int) * c->S, cudaMemcpyDeviceToDevice, c->stream);
+            for (int pl = 0; pl < maxn; ++pl)
+                for (int coord = 0; coord < 6; ++coord) {
+                    launch_perturb_one(c, c->Y, c->q, pl, coord, c->p.rfd_delta, c->Yt, c->qt);
+                    load_config(c, c->Yt, c->qt);
+                    int it = 0;
+                    if ((st = slip_at_loaded(c, c->W, c->vb_t, 1, &it, &e2)) != GDC_OK) return st;
+                    inf.lanczos_iters[1] += it;
+                    launch_lsq(c, c->vb_t, c->calVt);
+                    launch_fd_accum(c, c->calV, c->calVt, pl, coord, c->p.rfd_delta, c->divp, pl == 0 && coord == 0);
+                }
+            launch_nu_from_div(c, c->divp, dt, c->nu);
+        }
+        // step 4: mid-step
+        launch_advance(c, c->Y, c->q, c->calV, 0.5 * dt, nullptr, c->Ym, c->qm);
+        // step 5: forces and the full mobility solve at the mid-step, same W
+        load_at(c, c->Ym, c->qm);
+        forces_at_loaded(c, c->FT);
+        double e3 = 0.0;
+        if ((st = slip_at_loaded(c, c->W, c->vb_m, 0, &inf.lanczos_iters[2], &e3)) != GDC_OK) return st;
+        inf.lanczos_err = std::max(inf.lanczos_err, e3);
+        launch_rhs(c, c->vb_m, c->FT, c->gm_b);
+        st = gmres_solve(c, c->gm_b, c->gm_x, &inf.solve);
+        if (st != GDC_OK) return st;
+        launch_scatter_solution(c, c->gm_x, c->Vm, nullptr);
+        // step 6
+        launch_advance(c, c->Y, c->q, c->Vm, dt, c->nu, c->Y, c->q);
+        matvecs = inf.lanczos_iters[0] + inf.lanczos_iters[1] + inf.lanczos_iters[2] + inf.solve.matvecs_fp32 +
+                  inf.solve.matvecs_fp64;
+    }
+    // nu range and a finiteness check
+    std::vector<double> nu(c->S, 1.0);
+    if (c->p.scheme == GDC_SCHEME_GDC) {
+        cudaError_t e = cudaMemcpyAsync(nu.data(), c->nu, sizeof(double) * c->S, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if ((st = cuda_check(c, e, "nu read")) != GDC_OK) return st;
+    }
+    inf.nu_min = *std::min_element(nu.begin(), nu.end());
+    inf.nu_max = *std::max_element(nu.begin(), nu.end());
+    if (!std::isfinite(inf.nu_min) || !std::isfinite(inf.nu_max)) return fail(c, GDC_ERR_NONFINITE, "non-finite nu");
+    inf.pair_evals = (double)matvecs * c->pair_evals_per_matvec;
+    if (c->have_trace) {
+        const gdc_trace& t = c->trace;
+        auto cp = [&](double* dst, const double* src, long long n) {
+            if (dst) cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream);
+        };
+        cp(t.calV, c->calV, 6LL * c->NB);
+        cp(t.nu, c->nu, c->S);
+        cp(t.Ym, c->Ym, 3LL * c->NB);
+        cp(t.qm, c->qm, 4LL * c->NB);
+        cp(t.Vm, c->Vm, 6LL * c->NB);
+        cp(t.vb_n, c->vb_n, 3LL * c->NBL);
+        cp(t.vb_m, c->vb_m, 3LL * c->NBL);
+        cp(t.FTm, c->FT, 6LL * c->NB);
+    }
+    c->step++;
+    if ((st = read_status(c)) != GDC_OK) return st;
+    if (info) *info = inf;
+    return cuda_check(c, cudaGetLastError(), "step launch");
+}
+
+}  // namespace gdc
+
+using namespace gdc;
+
+extern "C" {
+
+size_t gdc_workspace_bytes(const gdc_params* params, int n_templates, const int* tmpl_nblobs, int n_susp,
+                           const long long* susp_body_off, const int* body_tmpl) {
+    gdc_ctx tmp;
+    if (build_host_layout(&tmp, params, n_templates, tmpl_nblobs, n_susp, susp_body_off, body_tmpl)) return 0;
+    return carve(&tmp, nullptr);
+}
+
+gdc_status gdc_init(gdc_ctx** out, const gdc_params* params, int n_templates, const int* tmpl_nblobs,
+                    const double* tmpl_xyz, int n_susp, const long long* susp_body_off, const int* body_tmpl,
+                    double* Y, double* q, void* workspace, size_t workspace_bytes, void* stream) {
+    if (!out) return GDC_ERR_INVALID_ARG;
+    *out = nullptr;
+    gdc_ctx* c = new (std::nothrow) gdc_ctx();
+    if (!c) return GDC_ERR_INVALID_ARG;
+    *out = c;
+    c->stream = (cudaStream_t)stream;
+    if (const char* m = build_host_layout(c, params, n_templates, tmpl_nblobs, n_susp, susp_body_off, body_tmpl))
+        return fail(c, GDC_ERR_INVALID_ARG, m);
+    if (!tmpl_xyz || !Y || !q || !workspace) return fail(c, GDC_ERR_INVALID_ARG, "NULL pointer argument");
+    const size_t need = carve(c, nullptr);
+    if (workspace_bytes < need)
+        return fail(c, GDC_ERR_WORKSPACE, "workspace too small: need " + std::to_string(need) + " bytes");
+    if (((uintptr_t)workspace) & 255) return fail(c, GDC_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    carve(c, workspace);
+    c->Y = Y;
+    c->q = q;
+    // centre the templates on their blob centroids (Y_p is the centroid), body lengths L_p
+    const long long nt = c->h_tmpl_off[c->T];
+    c->h_tmpl_xyz.assign(tmpl_xyz, tmpl_xyz + 3 * nt);
+    c->h_tmpl_L.assign(c->T, 0.0);
+    for (int t = 0; t < c->T; ++t) {
+        const int n = c->h_tmpl_n[t];
+        double* b = c->h_tmpl_xyz.data() + 3LL * c->h_tmpl_off[t];
+        double cen[3] = {0, 0, 0};
+        for (int i = 0; i < n; ++i)
+            for (int k = 0; k < 3; ++k) {
+                if (!std::isfinite(b[3 * i + k])) return fail(c, GDC_ERR_INVALID_ARG, "non-finite template coordinate");
+                cen[k] += b[3 * i + k] / n;
+            }
+        double L = 0.0;
+        for (int i = 0; i < n; ++i) {
+            for (int k = 0; k < 3; ++k) b[3 * i + k] -= cen[k];
+        }
+        for (int i = 0; i < n; ++i)
+            for (int j = i + 1; j < n; ++j) {
+                double d2 = 0.0;
+                for (int k = 0; k < 3; ++k) d2 += (b[3 * i + k] - b[3 * j + k]) * (b[3 * i + k] - b[3 * j + k]);
+                L = std::max(L, std::sqrt(d2));
+            }
+        // L_p scales the translational RFD displacement (footnote to step 3); a single blob uses a
+        c->h_tmpl_L[t] = L > 0.0 ? L : c->p.a;
+    }
+    gdc_status st;
+    if ((st = upload_layout(c, c->h_tmpl_xyz.data())) != GDC_OK) return st;
+    // state check on the host
+    std::vector<double> hY(3LL * c->NB), hq(4LL * c->NB);
+    cudaError_t e = cudaMemcpyAsync(hY.data(), Y, sizeof(double) * hY.size(), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hq.data(), q, sizeof(double) * hq.size(), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if ((st = cuda_check(c, e, "state read")) != GDC_OK) return st;
+    if ((st = check_state_host(c, hY.data(), hq.data())) != GDC_OK) return st;
+    krylov_init_attributes();
+    launch_template_setup(c);
+    if ((st = cuda_check(c, cudaGetLastError(), "template setup")) != GDC_OK) return st;
+    return read_status(c);
+}
+
+void gdc_destroy(gdc_ctx* c) { delete c; }
+
+const char* gdc_last_error(const gdc_ctx* c) { return c ? c->err.c_str() : "NULL context"; }
+
+gdc_status gdc_set_params(gdc_ctx* c, const gdc_params* p) {
+    if (!c) return GDC_ERR_INVALID_ARG;
+    if (const char* m = validate_params(p)) return fail(c, GDC_ERR_INVALID_ARG, m);
+    if (p->gmres_restart != c->p.gmres_restart || p->lanczos_max_iter != c->p.lanczos_max_iter)
+        return fail(c, GDC_ERR_INVALID_ARG, "gmres_restart and lanczos_max_iter are fixed at init");
+    if (p->a != c->p.a || p->eta != c->p.eta)
+        return fail(c, GDC_ERR_INVALID_ARG, "a and eta are fixed at init (they shape the preconditioner)");
+    const unsigned long long seed = c->p.seed;
+    c->p = *p;
+    c->p.seed = seed;
+    return GDC_OK;
+}
+
+gdc_status gdc_mobility_solve(gdc_ctx* c, const double* FT, const double* vbrev, double* V, double* lambda,
+                              gdc_solve_info* info) {
+    if (!c) return GDC_ERR_INVALID_ARG;
+    if (!FT || !V) return fail(c, GDC_ERR_INVALID_ARG, "FT and V are required");
+    load_at(c, c->Y, c->q);
+    launch_rhs(c, vbrev, FT, c->gm_b);
+    gdc_solve_info inf{};
+    gdc_status st = gmres_solve(c, c->gm_b, c->gm_x, &inf);
+    launch_scatter_solution(c, c->gm_x, V, lambda);
+    if (info) *info = inf;
+    gdc_status e2 = cuda_check(c, cudaStreamSynchronize(c->stream), "mobility solve");
+    return st != GDC_OK ? st : e2;
+}
+
+gdc_status gdc_step(gdc_ctx* c, int nsteps, gdc_step_info* info) {
+    if (!c) return GDC_ERR_INVALID_ARG;
+    if (nsteps < 0) return fail(c, GDC_ERR_INVALID_ARG, "nsteps must be >= 0");
+    for (int k = 0; k < nsteps; ++k) {
+        gdc_status st = one_step(c, info ? info + k : nullptr);
+        if (st != GDC_OK) return st;
+    }
+    return GDC_OK;
+}
+
+gdc_status gdc_set_trace(gdc_ctx* c, const gdc_trace* t) {
+    if (!c) return GDC_ERR_INVALID_ARG;
+    if (t) {
+        c->trace = *t;
+        c->have_trace = 1;
+    } else {
+        c->have_trace = 0;
+    }
+    return GDC_OK;
+}
+
+gdc_status gdc_get_state(gdc_ctx* c, double* Y, double* q, unsigned long long* step) {
+    if (!c) return GDC_ERR_INVALID_ARG;
+    cudaError_t e = cudaSuccess;
+    if (Y) e = cudaMemcpyAsync(Y, c->Y, sizeof(double) * 3 * c->NB, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && q) e = cudaMemcpyAsync(q, c->q, sizeof(double) * 4 * c->NB, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (step) *step = c->step;
+    return cuda_check(c, e, "get_state");
+}
+
+gdc_status gdc_set_state(gdc_ctx* c, const double* Y, const double* q, unsigned long long step) {
+    if (!c) return GDC_ERR_INVALID_ARG;
+    if (!Y || !q) return fail(c, GDC_ERR_INVALID_ARG, "Y and q are required");
+    gdc_status st = check_state_host(c, Y, q);
+    if (st != GDC_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(c->Y, Y, sizeof(double) * 3 * c->NB, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->q, q, sizeof(double) * 4 * c->NB, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    c->step = step;
+    return cuda_check(c, e, "set_state");
+}
+
+gdc_status gdc_blob_positions(gdc_ctx* c, double* r) {
+    if (!c || !r) return c ? fail(c, GDC_ERR_INVALID_ARG, "NULL output") : GDC_ERR_INVALID_ARG;
+    load_at(c, c->Y, c->q);
+    cudaMemcpyAsync(r, c->r, sizeof(double) * 3 * c->NBL, cudaMemcpyDeviceToDevice, c->stream);
+    return cuda_check(c, cudaStreamSynchronize(c->stream), "blob positions");
+}
+
+gdc_status gdc_rpy_apply(gdc_ctx* c, int precision, const double* lam, double* u) {
+    if (!c || !lam || !u) return c ? fail(c, GDC_ERR_INVALID_ARG, "NULL pointer") : GDC_ERR_INVALID_ARG;
+    if (precision != GDC_FP64 && precision != GDC_FP32_MIXED) return fail(c, GDC_ERR_INVALID_ARG, "unknown precision");
+    load_at(c, c->Y, c->q);
+    rpy_op(c, precision, lam, u);
+    return cuda_check(c, cudaStreamSynchronize(c->stream), "rpy apply");
+}
+
+gdc_status gdc_saddle_apply(gdc_ctx* c, int precision, const double* x, double* y) {
+    if (!c || !x || !y) return c ? fail(c, GDC_ERR_INVALID_ARG, "NULL pointer") : GDC_ERR_INVALID_ARG;
+    if (precision != GDC_FP64 && precision != GDC_FP32_MIXED) return fail(c, GDC_ERR_INVALID_ARG, "unknown precision");
+    load_at(c, c->Y, c->q);
+    saddle_op(c, precision, x, y);
+    return cuda_check(c, cudaStreamSynchronize(c->stream), "saddle apply");
+}
+
+gdc_status gdc_precond_apply(gdc_ctx* c, const double* r, double* z) {
+    if (!c || !r || !z) return c ? fail(c, GDC_ERR_INVALID_ARG, "NULL pointer") : GDC_ERR_INVALID_ARG;
+    load_at(c, c->Y, c->q);
+    launch_precond(c, r, z);
+    return cuda_check(c, cudaStreamSynchronize(c->stream), "precond apply");
+}
+
+gdc_status gdc_brownian_slip(gdc_ctx* c, const double* W, double* vbrev, int* iters, double* err) {
+    if (!c || !W || !vbrev) return c ? fail(c, GDC_ERR_INVALID_ARG, "NULL pointer") : GDC_ERR_INVALID_ARG;
+    load_at(c, c->Y, c->q);
+    gdc_status st = slip_at_loaded(c, W, vbrev, 0, iters, err);
+    gdc_status e2 = cuda_check(c, cudaStreamSynchronize(c->stream), "brownian slip");
+    return st != GDC_OK ? st : e2;
+}
+
+gdc_status gdc_lsq_velocity(gdc_ctx* c, const double* vbrev, double* calV) {
+    if (!c || !vbrev || !calV) return c ? fail(c, GDC_ERR_INVALID_ARG, "NULL pointer") : GDC_ERR_INVALID_ARG;
+    load_at(c, c->Y, c->q);
+    launch_lsq(c, vbrev, calV);
+    return cuda_check(c, cudaStreamSynchronize(c->stream), "lsq velocity");
+}
+
+gdc_status gdc_forces(gdc_ctx* c, double* FT) {
+    if (!c || !FT) return c ? fail(c, GDC_ERR_INVALID_ARG, "NULL pointer") : GDC_ERR_INVALID_ARG;
+    load_at(c, c->Y, c->q);
+    forces_at_loaded(c, FT);
+    return cuda_check(c, cudaStreamSynchronize(c->stream), "forces");
+}
+
+gdc_status gdc_draw_normals(gdc_ctx* c, unsigned long long step, int stream, double* out) {
+    if (!c || !out) return c ? fail(c, GDC_ERR_INVALID_ARG, "NULL pointer") : GDC_ERR_INVALID_ARG;
+    if (stream != 0 && stream != 1) return fail(c, GDC_ERR_INVALID_ARG, "stream must be 0 (W) or 1 (W-tilde)");
+    launch_normals(c, step, stream, out);
+    return cuda_check(c, cudaStreamSynchronize(c->stream), "normals");
+}
+
+gdc_status gdc_saddle_offsets(const gdc_ctx* c, long long* off) {
+    if (!c || !off) return GDC_ERR_INVALID_ARG;
+    for (int s = 0; s <= c->S; ++s) off[s] = c->h_gm_off[s];
+    return GDC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,421 @@
+// Per-body kernels: the K^T map (Eq. 13), step-2 least squares (Eq. 18 with the
+// closed-form K^T K of Sec. 5), the block-diagonal preconditioner P of Sec. 2.2, and
+// the per-template FP64 setup of P (Cholesky of the template's RPY block).
+//
+// Rigidity makes every intra-body quantity a rotation of a body-frame template
+// quantity: with R-hat = diag(R, ..., R) on blobs and R-tilde = diag(R, R) on
+// [force; torque], K_p = R-hat K_t R-tilde^T and M_pp = R-hat M_t R-hat^T (RPY is
+// rotation covariant and intra-body distances are fixed).  So M_t^-1, G_t = M_t^-1 K_t,
+// N_t = (K_t^T M_t^-1 K_t)^+ and (K_t^T K_t)^+ are computed once per template in the
+// body frame and applied to rotated vectors.  "^+" is the pseudo-inverse: a collinear
+// body (rod) has no axial spin (its K has that null vector), which is then set to 0.
+#include "common.cuh"
+
+namespace gdc {
+
+// ---- K^T: [sum lambda_i; sum (r_i - Y_p) x lambda_i] per body, one warp per body ----
+
+__global__ void k_body_KT(int NB, const long long* __restrict__ body_blob_off, const int* __restrict__ blob_gm,
+                          const int* __restrict__ body_gm, const double* __restrict__ x, int x_gm,
+                          double* __restrict__ y, int y_gm, double scale, const double* __restrict__ r,
+                          const double* __restrict__ Yc) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= NB) return;
+    const int p = warp;
+    const double Y0 = Yc[3 * p], Y1 = Yc[3 * p + 1], Y2 = Yc[3 * p + 2];
+    double f0 = 0, f1 = 0, f2 = 0, t0 = 0, t1 = 0, t2 = 0;
+    for (long long i = body_blob_off[p] + lane; i < body_blob_off[p + 1]; i += 32) {
+        const long long o = x_gm ? (long long)blob_gm[i] : 3 * i;
+        const double l0 = x[o], l1 = x[o + 1], l2 = x[o + 2];
+        const double d0 = r[3 * i] - Y0, d1 = r[3 * i + 1] - Y1, d2 = r[3 * i + 2] - Y2;
+        f0 += l0;
+        f1 += l1;
+        f2 += l2;
+        t0 += d1 * l2 - d2 * l1;
+        t1 += d2 * l0 - d0 * l2;
+        t2 += d0 * l1 - d1 * l0;
+    }
+    f0 = warp_sum(f0);
+    f1 = warp_sum(f1);
+    f2 = warp_sum(f2);
+    t0 = warp_sum(t0);
+    t1 = warp_sum(t1);
+    t2 = warp_sum(t2);
+    if (lane == 0) {
+        const long long o = y_gm ? (long long)body_gm[p] : 6LL * p;
+        y[o] = scale * f0;
+        y[o + 1] = scale * f1;
+        y[o + 2] = scale * f2;
+        y[o + 3] = scale * t0;
+        y[o + 4] = scale * t1;
+        y[o + 5] = scale * t2;
+    }
+}
+
+void launch_body_KT(gdc_ctx* c, const double* x, int x_gm, double* y, int y_gm, double scale) {
+    k_body_KT<<<ceil_div(32LL * c->NB, 256), 256, 0, c->stream>>>(c->NB, c->body_blob_off, c->blob_gm, c->body_gm, x,
+                                                                  x_gm, y, y_gm, scale, c->r, c->Yc);
+}
+
+// ---- step 2: calV_p = (K^T K)_p^+ K_p^T vbrev ----------------------------------------
+
+__device__ inline void rotT(const double* R, const double* v, double* o) {  // o = R^T v
+    o[0] = R[0] * v[0] + R[3] * v[1] + R[6] * v[2];
+    o[1] = R[1] * v[0] + R[4] * v[1] + R[7] * v[2];
+    o[2] = R[2] * v[0] + R[5] * v[1] + R[8] * v[2];
+}
+
+__device__ inline void rot(const double* R, const double* v, double* o) {  // o = R v
+    o[0] = R[0] * v[0] + R[1] * v[1] + R[2] * v[2];
+    o[1] = R[3] * v[0] + R[4] * v[1] + R[5] * v[2];
+    o[2] = R[6] * v[0] + R[7] * v[1] + R[8] * v[2];
+}
+
+__global__ void k_lsq(int NB, const long long* __restrict__ body_blob_off, const int* __restrict__ body_tmpl,
+                      const double* __restrict__ KtKp, const double* __restrict__ vb, const double* __restrict__ r,
+                      const double* __restrict__ Yc, const double* __restrict__ Rb, double* __restrict__ calV) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= NB) return;
+    const int p = warp;
+    const double Y0 = Yc[3 * p], Y1 = Yc[3 * p + 1], Y2 = Yc[3 * p + 2];
+    double g[6] = {0, 0, 0, 0, 0, 0};
+    for (long long i = body_blob_off[p] + lane; i < body_blob_off[p + 1]; i += 32) {
+        const double l0 = vb[3 * i], l1 = vb[3 * i + 1], l2 = vb[3 * i + 2];
+        const double d0 = r[3 * i] - Y0, d1 = r[3 * i + 1] - Y1, d2 = r[3 * i + 2] - Y2;
+        g[0] += l0;
+        g[1] += l1;
+        g[2] += l2;
+        g[3] += d1 * l2 - d2 * l1;
+        g[4] += d2 * l0 - d0 * l2;
+        g[5] += d0 * l1 - d1 * l0;
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) g[k] = warp_sum(g[k]);
+    if (lane == 0) {
+        const double* R = Rb + 9 * p;
+        double gb[6], vbody[6], out[6];
+        rotT(R, g, gb);
+        rotT(R, g + 3, gb + 3);
+        const double* A = KtKp + 36 * body_tmpl[p];
+        for (int a = 0; a < 6; ++a) {
+            double acc = 0.0;
+            for (int b = 0; b < 6; ++b) acc += A[6 * a + b] * gb[b];
+            vbody[a] = acc;
+        }
+        rot(R, vbody, out);
+        rot(R, vbody + 3, out + 3);
+        for (int k = 0; k < 6; ++k) calV[6 * p + k] = out[k];
+    }
+}
+
+void launch_lsq(gdc_ctx* c, const double* vbrev, double* calV) {
+    k_lsq<<<ceil_div(32LL * c->NB, 256), 256, 0, c->stream>>>(c->NB, c->body_blob_off, c->body_tmpl, c->tmpl_KtKp,
+                                                              vbrev, c->r, c->Yc, c->Rb, calV);
+}
+
+// ---- block-diagonal preconditioner, one block per body ---------------------------------
+//
+// Solves [M_pp -K_p; -K_p^T 0][lam; V] = [r_lam; r_V] exactly:
+//   a = M^-1 r_lam,  V = -N (r_V + K^T a),  lam = a + G V   (N = (K^T M^-1 K)^+, G = M^-1 K)
+// in the body frame of the template.
+
+__global__ void __launch_bounds__(128) k_precond(const long long* __restrict__ body_blob_off, const int* __restrict__ body_tmpl,
+                                                 const int* __restrict__ tmpl_n, const int* __restrict__ tmpl_off,
+                                                 const long long* __restrict__ minv_off, const double* __restrict__ Minv,
+                                                 const double* __restrict__ Gt, const double* __restrict__ Nt,
+                                                 const double* __restrict__ tmpl_xyz, const int* __restrict__ blob_gm,
+                                                 const int* __restrict__ body_gm, const double* __restrict__ Rb,
+                                                 const double* __restrict__ rin, double* __restrict__ zout) {
+    extern __shared__ double sh[];
+    const int p = blockIdx.x;
+    const int t = body_tmpl[p];
+    const int n = tmpl_n[t];
+    const int n3 = 3 * n;
+    double* rho = sh;          // n3
+    double* av = sh + n3;      // n3
+    double* misc = sh + 2 * n3;  // 32
+    const double* R = Rb + 9 * p;
+    const long long i0 = body_blob_off[p];
+    for (int b = threadIdx.x; b < n; b += blockDim.x) {
+        const long long o = blob_gm[i0 + b];
+        double v[3] = {rin[o], rin[o + 1], rin[o + 2]}, w[3];
+        rotT(R, v, w);
+        rho[3 * b] = w[0];
+        rho[3 * b + 1] = w[1];
+        rho[3 * b + 2] = w[2];
+    }
+    if (threadIdx.x == 0) {
+        const long long o = body_gm[p];
+        double v[3] = {rin[o], rin[o + 1], rin[o + 2]}, w[3];
+        rotT(R, v, w);
+        misc[0] = w[0];
+        misc[1] = w[1];
+        misc[2] = w[2];
+        double v2[3] = {rin[o + 3], rin[o + 4], rin[o + 5]};
+        rotT(R, v2, w);
+        misc[3] = w[0];
+        misc[4] = w[1];
+        misc[5] = w[2];
+    }
+    __syncthreads();
+    const double* Mi = Minv + minv_off[t];
+    for (int row = threadIdx.x; row < n3; row += blockDim.x) {
+        double acc = 0.0;
+        for (int k = 0; k < n3; ++k) acc = fma(Mi[(long long)k * n3 + row], rho[k], acc);  // symmetric
+        av[row] = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const double* b = tmpl_xyz + 3LL * tmpl_off[t];
+        double g[6] = {0, 0, 0, 0, 0, 0};
+        for (int i = threadIdx.x; i < n; i += 32) {
+            const double a0 = av[3 * i], a1 = av[3 * i + 1], a2 = av[3 * i + 2];
+            const double d0 = b[3 * i], d1 = b[3 * i + 1], d2 = b[3 * i + 2];
+            g[0] += a0;
+            g[1] += a1;
+            g[2] += a2;
+            g[3] += d1 * a2 - d2 * a1;
+            g[4] += d2 * a0 - d0 * a2;
+            g[5] += d0 * a1 - d1 * a0;
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) g[k] = warp_sum(g[k]);
+        if (threadIdx.x == 0) {
+            const double* N = Nt + 36 * t;
+            for (int a = 0; a < 6; ++a) {
+                double acc = 0.0;
+                for (int k = 0; k < 6; ++k) acc += N[6 * a + k] * (misc[k] + g[k]);
+                misc[8 + a] = -acc;
+            }
+        }
+    }
+    __syncthreads();
+    const double* Gtt = Gt + 18LL * tmpl_off[t];  // G_t is 3n x 6, templates back to back
+    for (int b = threadIdx.x; b < n; b += blockDim.x) {
+        double lb[3];
+        for (int a = 0; a < 3; ++a) {
+            const int row = 3 * b + a;
+            double acc = av[row];
+            for (int k = 0; k < 6; ++k) acc = fma(Gtt[6LL * row + k], misc[8 + k], acc);
+            lb[a] = acc;
+        }
+        double w[3];
+        rot(R, lb, w);
+        const long long o = blob_gm[i0 + b];
+        zout[o] = w[0];
+        zout[o + 1] = w[1];
+        zout[o + 2] = w[2];
+    }
+    if (threadIdx.x == 0) {
+        double w[3];
+        const long long o = body_gm[p];
+        rot(R, misc + 8, w);
+        zout[o] = w[0];
+        zout[o + 1] = w[1];
+        zout[o + 2] = w[2];
+        rot(R, misc + 11, w);
+        zout[o + 3] = w[0];
+        zout[o + 4] = w[1];
+        zout[o + 5] = w[2];
+    }
+}
+
+void launch_precond(gdc_ctx* c, const double* r, double* z) {
+    const size_t smem = (size_t)(2 * 3 * c->max_body_blobs + 32) * sizeof(double);
+    k_precond<<<c->NB, 128, smem, c->stream>>>(c->body_blob_off, c->body_tmpl, c->tmpl_n, c->tmpl_off, c->minv_off,
+                                               c->tmpl_Minv, c->tmpl_G, c->tmpl_N, c->tmpl_xyz, c->blob_gm,
+                                               c->body_gm, c->Rb, r, z);
+}
+
+// ---- per-template setup (once, at init) -------------------------------------------------
+
+// Cyclic Jacobi eigendecomposition of a symmetric 6x6 (Golub & Van Loan, Sec. 8.5), then the
+// pseudo-inverse with eigenvalues below rel_tol * max set to zero.  Single thread.
+__device__ void pinv6(const double* A_in, double* P, double rel_tol) {
+    double A[36], V[36];
+    for (int k = 0; k < 36; ++k) {
+        A[k] = A_in[k];
+        V[k] = (k % 7 == 0) ? 1.0 : 0.0;
+    }
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int i = 0; i < 6; ++i)
+            for (int j = 0; j < 6; ++j) {
+                tot += A[6 * i + j] * A[6 * i + j];
+                if (i != j) off += A[6 * i + j] * A[6 * i + j];
+            }
+        if (off <= 1e-30 * tot) break;
+        for (int pp = 0; pp < 5; ++pp)
+            for (int qq = pp + 1; qq < 6; ++qq) {
+                const double apq = A[6 * pp + qq];
+                if (apq == 0.0) continue;
+                const double tau = (A[6 * qq + qq] - A[6 * pp + pp]) / (2.0 * apq);
+                const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                const double cs = 1.0 / sqrt(1.0 + tt * tt), sn = tt * cs;
+                // A <- J^T A J, J = identity with [c s; -s c] in rows/cols (pp, qq)
+                for (int k = 0; k < 6; ++k) {
+                    const double akp = A[6 * k + pp], akq = A[6 * k + qq];
+                    A[6 * k + pp] = cs * akp - sn * akq;
+                    A[6 * k + qq] = sn * akp + cs * akq;
+                }
+                for (int k = 0; k < 6; ++k) {
+                    const double apk = A[6 * pp + k], aqk = A[6 * qq + k];
+                    A[6 * pp + k] = cs * apk - sn * aqk;
+                    A[6 * qq + k] = sn * apk + cs * aqk;
+                }
+                for (int k = 0; k < 6; ++k) {
+                    const double vkp = V[6 * k + pp], vkq = V[6 * k + qq];
+                    V[6 * k + pp] = cs * vkp - sn * vkq;
+                    V[6 * k + qq] = sn * vkp + cs * vkq;
+                }
+            }
+    }
+    double lmax = 0.0;
+    for (int i = 0; i < 6; ++i) lmax = fmax(lmax, fabs(A[7 * i]));
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) {
+            double acc = 0.0;
+            for (int k = 0; k < 6; ++k) {
+                const double lam = A[7 * k];
+                if (lam > rel_tol * lmax) acc += V[6 * i + k] * V[6 * j + k] / lam;
+            }
+            P[6 * i + j] = acc;
+        }
+}
+
+// One block per template.  work: 2 (3n)^2 doubles of scratch per template at minv_off.
+__global__ void k_template_setup(const int* __restrict__ tmpl_n, const int* __restrict__ tmpl_off,
+                                 const long long* __restrict__ minv_off, const double* __restrict__ xyz,
+                                 double a, double eta, double* __restrict__ Minv, double* __restrict__ Gt,
+                                 double* __restrict__ Nt, double* __restrict__ KtKp, double* __restrict__ work,
+                                 int* __restrict__ status) {
+    const int t = blockIdx.x;
+    const int n = tmpl_n[t];
+    const int n3 = 3 * n;
+    const double* b = xyz + 3LL * tmpl_off[t];
+    double* Mi = Minv + minv_off[t];
+    double* L = work + 2 * minv_off[t];
+    double* X = L + (long long)n3 * n3;
+    const double c0 = 1.0 / (8.0 * 3.141592653589793 * eta);
+    // 1. the template's RPY block M_t (Sec. 4.1), row-major in L
+    for (long long e = threadIdx.x; e < (long long)n3 * n3; e += blockDim.x) {
+        const int row = (int)(e / n3), col = (int)(e % n3);
+        const int i = row / 3, al = row % 3, j = col / 3, be = col % 3;
+        const double d0 = b[3 * j] - b[3 * i], d1 = b[3 * j + 1] - b[3 * i + 1], d2 = b[3 * j + 2] - b[3 * i + 2];
+        const double dd[3] = {d0, d1, d2};
+        const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+        double A, B;
+        if (r2 == 0.0) {
+            A = 4.0 / (3.0 * a);
+            B = 0.0;
+        } else if (r2 < 4.0 * a * a) {
+            const double r = sqrt(r2);
+            A = 4.0 / (3.0 * a) * (1.0 - 9.0 * r / (32.0 * a));
+            B = 1.0 / (8.0 * a * a * r);
+        } else {
+            const double r = sqrt(r2);
+            A = 1.0 / r + 2.0 * a * a / (3.0 * r * r2);
+            B = (1.0 - 2.0 * a * a / r2) / (r * r2);
+        }
+        L[e] = c0 * ((al == be ? A : 0.0) + B * dd[al] * dd[be]);
+    }
+    __syncthreads();
+    // 2. Cholesky M = L L^T (right-looking; lower triangle of L overwritten)
+    for (int k = 0; k < n3; ++k) {
+        if (threadIdx.x == 0) {
+            const double dkk = L[(long long)k * n3 + k];
+            if (!(dkk > 0.0)) atomicExch(status, 1);
+            L[(long long)k * n3 + k] = sqrt(fmax(dkk, 1e-300));
+        }
+        __syncthreads();
+        const double lkk = L[(long long)k * n3 + k];
+        for (int i = k + 1 + threadIdx.x; i < n3; i += blockDim.x) L[(long long)i * n3 + k] /= lkk;
+        __syncthreads();
+        const int m = n3 - k - 1;
+        for (long long e = threadIdx.x; e < (long long)m * m; e += blockDim.x) {
+            const int i = k + 1 + (int)(e / m), j = k + 1 + (int)(e % m);
+            if (j <= i) L[(long long)i * n3 + j] -= L[(long long)i * n3 + k] * L[(long long)j * n3 + k];
+        }
+        __syncthreads();
+    }
+    // 3. X = L^-1 column by column (forward substitution), then M^-1 = X^T X
+    for (int col = threadIdx.x; col < n3; col += blockDim.x) {
+        for (int i = 0; i < n3; ++i) X[(long long)i * n3 + col] = 0.0;
+        for (int i = col; i < n3; ++i) {
+            double acc = (i == col) ? 1.0 : 0.0;
+            for (int k = col; k < i; ++k) acc -= L[(long long)i * n3 + k] * X[(long long)k * n3 + col];
+            X[(long long)i * n3 + col] = acc / L[(long long)i * n3 + i];
+        }
+    }
+    __syncthreads();
+    for (long long e = threadIdx.x; e < (long long)n3 * n3; e += blockDim.x) {
+        const int i = (int)(e / n3), j = (int)(e % n3);
+        double acc = 0.0;
+        for (int k = max(i, j); k < n3; ++k) acc += X[(long long)k * n3 + i] * X[(long long)k * n3 + j];
+        Mi[e] = acc;
+    }
+    __syncthreads();
+    // 4. G = M^-1 K_t (3n x 6): K_t columns are unit translations and rotations e_b x b_i
+    double* G = Gt + 18LL * tmpl_off[t];
+    for (long long e = threadIdx.x; e < 6LL * n3; e += blockDim.x) {
+        const int row = (int)(e / 6), col = (int)(e % 6);
+        double acc = 0.0;
+        for (int i = 0; i < n; ++i) {
+            double kc[3];
+            if (col < 3) {
+                kc[0] = col == 0;
+                kc[1] = col == 1;
+                kc[2] = col == 2;
+            } else {
+                const int bb = col - 3;  // e_bb x b_i
+                const double e3[3] = {(double)(bb == 0), (double)(bb == 1), (double)(bb == 2)};
+                kc[0] = e3[1] * b[3 * i + 2] - e3[2] * b[3 * i + 1];
+                kc[1] = e3[2] * b[3 * i] - e3[0] * b[3 * i + 2];
+                kc[2] = e3[0] * b[3 * i + 1] - e3[1] * b[3 * i];
+            }
+            for (int al = 0; al < 3; ++al) acc += Mi[(long long)row * n3 + 3 * i + al] * kc[al];
+        }
+        G[e] = acc;
+    }
+    __syncthreads();
+    // 5. N_t = (K_t^T G)^+ and (K_t^T K_t)^+  (closed form of Sec. 5 for the latter)
+    if (threadIdx.x == 0) {
+        double A6[36], KK[36];
+        for (int k = 0; k < 36; ++k) {
+            A6[k] = 0.0;
+            KK[k] = 0.0;
+        }
+        for (int i = 0; i < n; ++i) {
+            const double bx = b[3 * i], by = b[3 * i + 1], bz = b[3 * i + 2];
+            // K_i = [I, [x b]]: columns e_x, e_y, e_z and e_k x b_i
+            double Kc[6][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {0, -bz, by}, {bz, 0, -bx}, {-by, bx, 0}};
+            for (int u = 0; u < 6; ++u)
+                for (int v = 0; v < 6; ++v) {
+                    double s1 = 0.0, s2 = 0.0;
+                    for (int al = 0; al < 3; ++al) {
+                        s1 += Kc[u][al] * G[6LL * (3 * i + al) + v];
+                        s2 += Kc[u][al] * Kc[v][al];
+                    }
+                    A6[6 * u + v] += s1;
+                    KK[6 * u + v] += s2;
+                }
+        }
+        for (int u = 0; u < 6; ++u)  // symmetrise rounding
+            for (int v = u + 1; v < 6; ++v) {
+                const double m = 0.5 * (A6[6 * u + v] + A6[6 * v + u]);
+                A6[6 * u + v] = A6[6 * v + u] = m;
+            }
+        pinv6(A6, Nt + 36 * t, 1e-10);
+        pinv6(KK, KtKp + 36 * t, 1e-10);
+    }
+}
+
+void launch_template_setup(gdc_ctx* c) {
+    k_template_setup<<<c->T, 256, 0, c->stream>>>(c->tmpl_n, c->tmpl_off, c->minv_off, c->tmpl_xyz, c->p.a, c->p.eta,
+                                                  c->tmpl_Minv, c->tmpl_G, c->tmpl_N, c->tmpl_KtKp, c->tmpl_work,
+                                                  c->dev_status);
+}
+
+}  // namespace gdc

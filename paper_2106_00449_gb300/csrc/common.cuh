@@ -1,0 +1,234 @@
+// Internal definitions shared by the gDC CUDA translation units.
+//
+// Data layout in device memory (all caller-owned, carved from one workspace):
+//   * per suspension s: body range [susp_body_off[s], susp_body_off[s+1]),
+//     blob range [susp_blob_off[s], ...), saddle-vector block at susp_gm_off[s]
+//     holding [lambda: 3 per blob | V: 6 per body] of that suspension;
+//   * blob-indexed vectors (W, v-breve, Lanczos basis) are 3 doubles per blob,
+//     global blob order;
+//   * body-indexed vectors (V, calV, F) are 6 doubles per body;
+//   * the configuration a product is evaluated at ("loaded" configuration):
+//     per-body rotation R (9 doubles), per-blob FP64 position r, and the pair
+//     kernels' source arrays: float4/double4 position relative to the
+//     suspension's reference point (w = body index bits) and float4/double4
+//     lambda.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/gdc.h"
+
+#define GDC_MAX_RESTART 100
+#define GDC_MAX_LANCZOS 128
+#define GDC_MAX_TMPL_BLOBS 340   // 3n <= 1020 rows of a template block
+
+namespace gdc {
+
+struct MvItem {      // one block of the pair kernels: targets [t0, t0+tile) x sources [j0, j1) of suspension s
+    int s;
+    int t0;          // first target, local to the suspension
+    int j0, j1;      // source range, local to the suspension
+    int k;           // source-chunk slot of the partial sums
+    int pad[3];
+};
+
+struct Chunk {       // a contiguous element range inside one segment, for deterministic reductions
+    long long lo, hi;
+    int seg;
+    int pad;
+};
+
+struct Seg {         // a segmented vector space: per-suspension offsets and the chunks covering it
+    long long n = 0;           // total length
+    const long long* off = 0;  // device, S+1
+    std::vector<long long> h_off;
+    Chunk* chunks = 0;         // device
+    int* seg_chunk_off = 0;    // device, S+1
+    std::vector<Chunk> h_chunks;
+    std::vector<int> h_seg_chunk_off;
+    int n_chunks = 0;
+};
+
+struct Config {      // a rigid configuration the kernels evaluate at
+    const double* Y = 0;
+    const double* q = 0;
+};
+
+}  // namespace gdc
+
+struct gdc_ctx {
+    gdc_params p;
+    cudaStream_t stream = 0;
+    int device = 0, num_sms = 0;
+    std::string err;
+
+    // sizes
+    int S = 0, NB = 0, NBL = 0, T = 0;
+    long long ngm = 0;            // saddle-vector length
+    int max_body_blobs = 0;
+    unsigned long long step = 0;
+
+    // host copies of the layout
+    std::vector<long long> h_body_off, h_blob_off, h_gm_off, h_body_blob_off;
+    std::vector<int> h_body_tmpl, h_tmpl_n, h_tmpl_off, h_body_susp;
+    std::vector<long long> h_minv_off;
+    std::vector<double> h_tmpl_xyz, h_tmpl_L;
+
+    // device layout tables
+    long long *susp_body_off = 0, *susp_blob_off = 0, *susp_gm_off = 0, *body_blob_off = 0;
+    long long *minv_off = 0;
+    int *body_tmpl = 0, *body_susp = 0, *blob_body = 0, *blob_susp = 0, *tmpl_n = 0, *tmpl_off = 0;
+    int *blob_gm = 0, *body_gm = 0;
+    double *tmpl_xyz = 0, *tmpl_L = 0;
+    double *tmpl_Minv = 0, *tmpl_G = 0, *tmpl_N = 0, *tmpl_KtKp = 0, *tmpl_work = 0;
+    double *body_L = 0;
+
+    // state (caller arrays)
+    double *Y = 0, *q = 0;
+
+    // loaded configuration
+    double *Rb = 0, *r = 0, *Yc = 0, *ref = 0;
+    float4 *spos = 0, *slam = 0;
+    double4 *spos64 = 0, *slam64 = 0;
+
+    // step buffers
+    double *W = 0, *Wt = 0, *vb_n = 0, *vb_t = 0, *vb_m = 0, *calV = 0, *calVt = 0;
+    double *Yt = 0, *qt = 0, *Ym = 0, *qm = 0, *FT = 0, *Vm = 0, *nu = 0, *divp = 0, *fblob = 0;
+    double *u3 = 0;               // scratch 3 per blob
+
+    // GMRES (saddle layout)
+    int m = 0;
+    double *gm_V = 0, *gm_x = 0, *gm_b = 0, *gm_r = 0, *gm_w = 0, *gm_z = 0;
+    double *gm_H = 0, *gm_cs = 0, *gm_sn = 0, *gm_g = 0, *gm_y = 0, *gm_h = 0, *gm_h2 = 0;
+    double *gm_bnorm = 0, *gm_res = 0, *gm_scal = 0;
+    int *gm_active = 0, *gm_j = 0;
+
+    // Lanczos (blob layout)
+    int kmax = 0;
+    double *lz_V = 0, *lz_w = 0, *lz_alpha = 0, *lz_beta = 0, *lz_c = 0, *lz_cprev = 0;
+    double *lz_h = 0, *lz_Wnorm = 0, *lz_err = 0, *lz_scal = 0;
+    int *lz_active = 0, *lz_k = 0, *lz_fix = 0;
+
+    // reductions
+    gdc::Seg seg_gm, seg_lz, seg_body;
+    double* red_part = 0;         // n_chunks x GDC_MAX_LANCZOS partial sums
+    int red_cols = 0;
+
+    // pair-kernel work lists
+    gdc::MvItem* mv_items = 0;
+    int mv_n_items = 0, mv_tpt = 2, mv_threads = 128, mv_kmax = 1;
+    int* mv_nk = 0;               // chunks per suspension
+    std::vector<gdc::MvItem> h_mv_items;
+    std::vector<int> h_mv_nk;
+    void* mv_part = 0;            // mv_kmax x NBL x (float4 | double4)
+    double pair_evals_per_matvec = 0.0;
+
+    // host mirrors for convergence checks
+    std::vector<int> h_flags;
+    std::vector<double> h_vals;
+
+    // optional trace of the last step
+    gdc_trace trace{};
+    int have_trace = 0;
+
+    // status of device-side loops
+    int* dev_status = 0;
+};
+
+namespace gdc {
+
+// ---- small device helpers -------------------------------------------------
+
+__host__ __device__ inline void quat_to_R(const double* q, double* R) {
+    // Eq. (1) of Sec. 2, q scalar first
+    const double q0 = q[0], q1 = q[1], q2 = q[2], q3 = q[3];
+    R[0] = 1.0 - 2.0 * q2 * q2 - 2.0 * q3 * q3;
+    R[1] = 2.0 * (q1 * q2 - q3 * q0);
+    R[2] = 2.0 * (q1 * q3 + q2 * q0);
+    R[3] = 2.0 * (q1 * q2 + q3 * q0);
+    R[4] = 1.0 - 2.0 * q1 * q1 - 2.0 * q3 * q3;
+    R[5] = 2.0 * (q3 * q2 - q1 * q0);
+    R[6] = 2.0 * (q1 * q3 - q2 * q0);
+    R[7] = 2.0 * (q3 * q2 + q1 * q0);
+    R[8] = 1.0 - 2.0 * q2 * q2 - 2.0 * q1 * q1;
+}
+
+__device__ inline void quat_exp_mul(const double* u, const double* q, double* out) {
+    // out = exp(u) * q: exp of Sec. 2 followed by the Hamilton product of App. A
+    const double th = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    double s, c;
+    if (th < 1e-8) {
+        s = 0.5 - th * th / 48.0;      // sin(th/2)/th near 0
+        c = cos(0.5 * th);
+    } else {
+        double sh, ch;
+        sincos(0.5 * th, &sh, &ch);
+        s = sh / th;
+        c = ch;
+    }
+    const double e0 = c, e1 = s * u[0], e2 = s * u[1], e3 = s * u[2];
+    const double q0 = q[0], q1 = q[1], q2 = q[2], q3 = q[3];
+    out[0] = e0 * q0 - (e1 * q1 + e2 * q2 + e3 * q3);
+    out[1] = e0 * q1 + q0 * e1 + (e2 * q3 - e3 * q2);
+    out[2] = e0 * q2 + q0 * e2 + (e3 * q1 - e1 * q3);
+    out[3] = e0 * q3 + q0 * e3 + (e1 * q2 - e2 * q1);
+}
+
+__device__ inline double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// ---- host-side helpers (defined in api.cu) --------------------------------
+gdc_status fail(gdc_ctx* c, gdc_status s, const std::string& msg);
+gdc_status cuda_check(gdc_ctx* c, cudaError_t e, const char* what);
+
+// ---- kernels launched across translation units ----------------------------
+// geometry.cu
+void load_config(gdc_ctx* c, const double* Y, const double* q);
+void launch_ref(gdc_ctx* c, const double* Y);
+void launch_normals(gdc_ctx* c, unsigned long long step, int stream, double* out);
+void launch_perturb(gdc_ctx* c, const double* Y, const double* q, const double* Wt, double delta,
+                    double* Yo, double* qo);
+void launch_perturb_one(gdc_ctx* c, const double* Y, const double* q, int p_local, int coord,
+                        double delta, double* Yo, double* qo);
+void launch_advance(gdc_ctx* c, const double* Y, const double* q, const double* V, double h,
+                    const double* nu, double* Yo, double* qo);
+void launch_rfd_div(gdc_ctx* c, const double* Wt, const double* calV, const double* calVt,
+                    double delta, double dt, double* nu);
+void launch_fd_accum(gdc_ctx* c, const double* calV, const double* calVp, int p_local, int coord,
+                     double delta, double* div, int first);
+void launch_nu_from_div(gdc_ctx* c, const double* div, double dt, double* nu);
+void launch_rhs(gdc_ctx* c, const double* vbrev, const double* FT, double* b);
+void launch_scatter_solution(gdc_ctx* c, const double* x, double* V, double* lambda);
+
+// rpy.cu
+void launch_pack_lambda(gdc_ctx* c, int prec, const double* x, int gm_layout);
+void launch_rpy(gdc_ctx* c, int prec);
+void launch_rpy_epilogue(gdc_ctx* c, int prec, const double* x, double* y, int gm_layout);
+void launch_forces_pair(gdc_ctx* c, int prec, double* fblob);
+void build_mv_items(gdc_ctx* c);
+
+// body.cu
+void launch_body_KT(gdc_ctx* c, const double* x, int x_gm, double* y, int y_gm, double scale);
+void launch_lsq(gdc_ctx* c, const double* vbrev, double* calV);
+void launch_precond(gdc_ctx* c, const double* r, double* z);
+void launch_template_setup(gdc_ctx* c);
+
+// krylov.cu
+gdc_status saddle_op(gdc_ctx* c, int prec, const double* x, double* y);
+gdc_status rpy_op(gdc_ctx* c, int prec, const double* lam, double* u);
+gdc_status gmres_solve(gdc_ctx* c, const double* b, double* x, gdc_solve_info* info);
+gdc_status lanczos_sqrt(gdc_ctx* c, const double* W, double* out, double scale, int fixed_iters,
+                        int* iters_out, double* err_out);
+void setup_segments(gdc_ctx* c);
+void krylov_init_attributes();
+
+}  // namespace gdc

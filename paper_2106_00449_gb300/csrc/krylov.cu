@@ -1,0 +1,568 @@
+// Batched Krylov solvers of the mobility problem (Sec. 2.2): right-preconditioned
+// GMRES on the saddle-point system of Eq. (14) with the block-diagonal P, and the
+// Lanczos approximation of M^(1/2) W (Sec. 4.1, Chow & Saad).  Every suspension has its
+// own Krylov space; vectors of all suspensions are stored back to back and reductions
+// are segmented per suspension.  Reductions are two-pass (per-chunk partials, then a
+// fixed-order sum per segment), so results are bitwise reproducible run to run.
+//
+// Precision: bases, inner products, Givens/Hessenberg and the small tridiagonal
+// eigenproblem are FP64.  In GDC_FP32_MIXED mode the operator inside the Krylov loop
+// uses the FP32 pair kernel; each GMRES cycle ends with an FP64 residual, and the
+// solver restarts from it until that FP64 residual meets gmres_tol (iterative refinement).
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+
+namespace gdc {
+
+constexpr int RED_CHUNK = 1024;   // elements per reduction chunk
+constexpr int RED_THREADS = 256;
+
+// ---- segment / chunk tables ---------------------------------------------------------
+
+static void build_seg(gdc::Seg& sg, const std::vector<long long>& off) {
+    sg.h_off = off;
+    sg.n = off.back();
+    sg.h_chunks.clear();
+    sg.h_seg_chunk_off.assign(off.size(), 0);
+    for (size_t s = 0; s + 1 < off.size(); ++s) {
+        sg.h_seg_chunk_off[s] = (int)sg.h_chunks.size();
+        for (long long lo = off[s]; lo < off[s + 1]; lo += RED_CHUNK) {
+            Chunk ch{};
+            ch.lo = lo;
+            ch.hi = std::min(off[s + 1], lo + RED_CHUNK);
+            ch.seg = (int)s;
+            sg.h_chunks.push_back(ch);
+        }
+    }
+    sg.h_seg_chunk_off.back() = (int)sg.h_chunks.size();
+    sg.n_chunks = (int)sg.h_chunks.size();
+}
+
+void setup_segments(gdc_ctx* c) {
+    build_seg(c->seg_gm, c->h_gm_off);
+    std::vector<long long> lz(c->S + 1);
+    for (int s = 0; s <= c->S; ++s) lz[s] = 3 * c->h_blob_off[s];
+    build_seg(c->seg_lz, lz);
+}
+
+// ---- reduction kernels -----------------------------------------------------------------
+
+// part[chunk * cols + i] = sum over the chunk of V_i[e] * w[e], i < k  (V_i = V + i * ld)
+__global__ void __launch_bounds__(RED_THREADS) k_mdot(const Chunk* __restrict__ chunks, const double* __restrict__ V,
+                                                      long long ld, int k, const double* __restrict__ w,
+                                                      double* __restrict__ part, int cols) {
+    __shared__ double sh[RED_THREADS / 32][GDC_MAX_LANCZOS + 1];
+    const Chunk ch = chunks[blockIdx.x];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double wv[RED_CHUNK / RED_THREADS];
+#pragma unroll
+    for (int u = 0; u < RED_CHUNK / RED_THREADS; ++u) {
+        const long long e = ch.lo + threadIdx.x + u * RED_THREADS;
+        wv[u] = e < ch.hi ? w[e] : 0.0;
+    }
+    for (int i = 0; i < k; ++i) {
+        const double* Vi = V + (long long)i * ld;
+        double acc = 0.0;
+#pragma unroll
+        for (int u = 0; u < RED_CHUNK / RED_THREADS; ++u) {
+            const long long e = ch.lo + threadIdx.x + u * RED_THREADS;
+            if (e < ch.hi) acc = fma(Vi[e], wv[u], acc);
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) sh[wid][i] = acc;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        double acc = 0.0;
+        for (int q = 0; q < RED_THREADS / 32; ++q) acc += sh[q][i];
+        part[(long long)blockIdx.x * cols + i] = acc;
+    }
+}
+
+// out[s * cols + i] = sum of the chunk partials of segment s, in chunk order
+__global__ void k_seg_sum(int S, const int* __restrict__ seg_chunk_off, const double* __restrict__ part, int cols, int k,
+                          double* __restrict__ out) {
+    const int s = blockIdx.x;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        double acc = 0.0;
+        for (int ch = seg_chunk_off[s]; ch < seg_chunk_off[s + 1]; ++ch) acc += part[(long long)ch * cols + i];
+        out[(long long)s * cols + i] = acc;
+    }
+}
+
+// w[e] -= sum_i h[s * cols + i] * V_i[e] for i < k
+__global__ void k_mupdate(const Chunk* __restrict__ chunks, const double* __restrict__ V, long long ld, int k,
+                          const double* __restrict__ h, int cols, double* __restrict__ w) {
+    const Chunk ch = chunks[blockIdx.x];
+    const double* hs = h + (long long)ch.seg * cols;
+    for (long long e = ch.lo + threadIdx.x; e < ch.hi; e += blockDim.x) {
+        double acc = w[e];
+        for (int i = 0; i < k; ++i) acc = fma(-hs[i], V[(long long)i * ld + e], acc);
+        w[e] = acc;
+    }
+}
+
+// out[e] = scale_s * sum_i y[s * cols + i] * V_i[e] for i < kcount[s]   (+ out[e] when accumulate)
+__global__ void k_combine(const Chunk* __restrict__ chunks, const double* __restrict__ V, long long ld,
+                          const int* __restrict__ kcount, const double* __restrict__ y, int cols,
+                          const double* __restrict__ scale, double* __restrict__ out) {
+    const Chunk ch = chunks[blockIdx.x];
+    const int k = kcount[ch.seg];
+    const double* ys = y + (long long)ch.seg * cols;
+    const double sc = scale ? scale[ch.seg] : 1.0;
+    for (long long e = ch.lo + threadIdx.x; e < ch.hi; e += blockDim.x) {
+        double acc = 0.0;
+        for (int i = 0; i < k; ++i) acc = fma(ys[i], V[(long long)i * ld + e], acc);
+        out[e] = sc * acc;
+    }
+}
+
+// out[e] = w[e] * scal[s]
+__global__ void k_seg_scale(const Chunk* __restrict__ chunks, const double* __restrict__ w,
+                            const double* __restrict__ scal, double* __restrict__ out) {
+    const Chunk ch = chunks[blockIdx.x];
+    const double sc = scal[ch.seg];
+    for (long long e = ch.lo + threadIdx.x; e < ch.hi; e += blockDim.x) out[e] = w[e] * sc;
+}
+
+__global__ void k_axpy_chunks(const Chunk* __restrict__ chunks, double a, const double* __restrict__ x,
+                              double* __restrict__ y) {
+    const Chunk ch = chunks[blockIdx.x];
+    for (long long e = ch.lo + threadIdx.x; e < ch.hi; e += blockDim.x) y[e] += a * x[e];
+}
+
+__global__ void k_sub_chunks(const Chunk* __restrict__ chunks, const double* __restrict__ b,
+                             const double* __restrict__ ax, double* __restrict__ r) {
+    const Chunk ch = chunks[blockIdx.x];
+    for (long long e = ch.lo + threadIdx.x; e < ch.hi; e += blockDim.x) r[e] = b[e] - ax[e];
+}
+
+// per-segment inner products <V_i, w>, i < k  -> out[s * cols + i]
+static void seg_mdot(gdc_ctx* c, const gdc::Seg& sg, const double* V, long long ld, int k, const double* w,
+                     double* out, int cols) {
+    k_mdot<<<sg.n_chunks, RED_THREADS, 0, c->stream>>>(sg.chunks, V, ld, k, w, c->red_part, c->red_cols);
+    k_seg_sum<<<c->S, 128, 0, c->stream>>>(c->S, sg.seg_chunk_off, c->red_part, c->red_cols, k, out);
+    (void)cols;
+}
+
+
+// ---- tiny per-suspension helpers ------------------------------------------------------
+
+__global__ void k_sqrt_col0(int S, const double* __restrict__ v, int cols, double* __restrict__ o) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < S) o[s] = sqrt(fmax(v[(long long)s * cols], 0.0));
+}
+
+__global__ void k_add_cols(int k, double* __restrict__ h, const double* __restrict__ h2, int cols) {
+    const int s = blockIdx.x;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) h[(long long)s * cols + i] += h2[(long long)s * cols + i];
+}
+
+__global__ void k_fill(int S, double v, double* __restrict__ o) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < S) o[s] = v;
+}
+
+// ---- operators ---------------------------------------------------------------------
+
+gdc_status rpy_op(gdc_ctx* c, int prec, const double* lam, double* u) {
+    launch_pack_lambda(c, prec, lam, 0);
+    launch_rpy(c, prec);
+    launch_rpy_epilogue(c, prec, lam, u, 0);
+    return GDC_OK;
+}
+
+gdc_status saddle_op(gdc_ctx* c, int prec, const double* x, double* y) {
+    launch_pack_lambda(c, prec, x, 1);
+    launch_rpy(c, prec);
+    launch_rpy_epilogue(c, prec, x, y, 1);
+    launch_body_KT(c, x, 1, y, 1, -1.0);
+    return GDC_OK;
+}
+
+static gdc_status sync_read(gdc_ctx* c, const void* dev, void* host, size_t bytes) {
+    cudaError_t e = cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return cuda_check(c, e, "device-to-host read");
+}
+
+// ---- GMRES small per-suspension kernels ------------------------------------------------
+
+// Start of a cycle: beta = ||r||, residual check against tol, V_0 scale and g.
+__global__ void k_gm_start(int S, const double* __restrict__ rn2, const double* __restrict__ bnorm, double tol,
+                           int cols, double* __restrict__ res, int* __restrict__ active, double* __restrict__ g,
+                           double* __restrict__ scal, int mp1, int* __restrict__ jcount, int* __restrict__ outer) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    const double beta = sqrt(fmax(rn2[(long long)s * cols], 0.0));
+    const double bn = bnorm[s];
+    const double rr = bn > 0.0 ? beta / bn : 0.0;
+    res[s] = rr;
+    const int go = (bn > 0.0) && (rr > tol) && isfinite(rr);
+    outer[s] = go || !isfinite(rr);
+    active[s] = go;
+    jcount[s] = 0;
+    for (int i = 0; i < mp1; ++i) g[(long long)s * mp1 + i] = 0.0;
+    g[(long long)s * mp1] = beta;
+    scal[s] = (go && beta > 0.0) ? 1.0 / beta : 0.0;
+}
+
+// Column j of the Hessenberg matrix: h (orthogonalisation coefficients), beta = ||w||.
+// Applies the previous Givens rotations, makes a new one, updates g and the residual estimate.
+__global__ void k_gm_arnoldi(int S, int j, int m, const double* __restrict__ h, int cols, const double* __restrict__ wn2,
+                             double* __restrict__ H, double* __restrict__ cs, double* __restrict__ sn,
+                             double* __restrict__ g, const double* __restrict__ bnorm, double inner_tol,
+                             double* __restrict__ est, int* __restrict__ active, int* __restrict__ jcount,
+                             double* __restrict__ scal) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    if (!active[s]) {
+        scal[s] = 0.0;
+        return;
+    }
+    const int mp1 = m + 1;
+    double* Hs = H + (long long)s * mp1 * m;
+    double* css = cs + (long long)s * m;
+    double* sns = sn + (long long)s * m;
+    double* gs = g + (long long)s * mp1;
+    const double beta = sqrt(fmax(wn2[(long long)s * cols], 0.0));
+    for (int i = 0; i <= j; ++i) Hs[i * m + j] = h[(long long)s * cols + i];
+    Hs[(j + 1) * m + j] = beta;
+    for (int i = 0; i < j; ++i) {
+        const double a = Hs[i * m + j], b = Hs[(i + 1) * m + j];
+        Hs[i * m + j] = css[i] * a + sns[i] * b;
+        Hs[(i + 1) * m + j] = -sns[i] * a + css[i] * b;
+    }
+    const double a = Hs[j * m + j], b = Hs[(j + 1) * m + j];
+    const double rr = hypot(a, b);
+    const double cc = rr > 0.0 ? a / rr : 1.0, ss = rr > 0.0 ? b / rr : 0.0;
+    css[j] = cc;
+    sns[j] = ss;
+    Hs[j * m + j] = rr;
+    Hs[(j + 1) * m + j] = 0.0;
+    gs[j + 1] = -ss * gs[j];
+    gs[j] = cc * gs[j];
+    const double e = fabs(gs[j + 1]) / bnorm[s];
+    est[s] = e;
+    jcount[s] = j + 1;
+    scal[s] = beta > 0.0 ? 1.0 / beta : 0.0;
+    if (!(e > inner_tol) || beta == 0.0 || j + 1 == m) active[s] = 0;
+}
+
+// y = H^-1 g (upper triangular, size jcount[s])
+__global__ void k_gm_backsolve(int S, int m, const double* __restrict__ H, const double* __restrict__ g,
+                               const int* __restrict__ jcount, double* __restrict__ y, int cols) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    const int k = jcount[s];
+    const int mp1 = m + 1;
+    const double* Hs = H + (long long)s * mp1 * m;
+    const double* gs = g + (long long)s * mp1;
+    double* ys = y + (long long)s * cols;
+    for (int i = k - 1; i >= 0; --i) {
+        double acc = gs[i];
+        for (int q = i + 1; q < k; ++q) acc -= Hs[i * m + q] * ys[q];
+        ys[i] = Hs[i * m + i] != 0.0 ? acc / Hs[i * m + i] : 0.0;
+    }
+    for (int i = k; i < cols; ++i) ys[i] = 0.0;
+}
+
+gdc_status gmres_solve(gdc_ctx* c, const double* b, double* x, gdc_solve_info* info) {
+    const int prec = c->p.precision;
+    const int m = c->m;
+    const long long n = c->ngm;
+    const gdc::Seg& sg = c->seg_gm;
+    const int cols = c->red_cols;
+    const double tol = c->p.gmres_tol;
+    const double inner_tol = prec == GDC_FP32_MIXED ? 0.5 * tol : tol;
+    gdc_solve_info inf{};
+    // ||b|| per suspension
+    seg_mdot(c, sg, b, 0, 1, b, c->gm_h, cols);
+    double* bn2 = c->gm_h;
+    // bnorm = sqrt(bn2): reuse k_seg_scale-free path via a tiny kernel
+    k_sqrt_col0<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(c->S, bn2, cols, c->gm_bnorm);
+    cudaMemsetAsync(x, 0, sizeof(double) * n, c->stream);
+    cudaMemcpyAsync(c->gm_r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream);
+    int total = 0;
+    gdc_status st = GDC_OK;
+    std::vector<int> outer(c->S), act(c->S);
+    std::vector<double> res(c->S);
+    for (int cycle = 0;; ++cycle) {
+        // beta = ||r|| and the FP64 residual check
+        seg_mdot(c, sg, c->gm_r, 0, 1, c->gm_r, c->gm_h2, cols);
+        k_gm_start<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(c->S, c->gm_h2, c->gm_bnorm, tol, cols, c->gm_res,
+                                                               c->gm_active, c->gm_g, c->gm_scal, m + 1, c->gm_j,
+                                                               c->gm_active + c->S);
+        if ((st = sync_read(c, c->gm_active + c->S, outer.data(), sizeof(int) * c->S)) != GDC_OK) return st;
+        if ((st = sync_read(c, c->gm_res, res.data(), sizeof(double) * c->S)) != GDC_OK) return st;
+        inf.cycles = cycle;
+        double rmax = 0.0;
+        bool any = false, bad = false;
+        for (int s = 0; s < c->S; ++s) {
+            if (!std::isfinite(res[s])) bad = true;
+            rmax = std::max(rmax, res[s]);
+            any = any || outer[s];
+        }
+        inf.residual = rmax;
+        if (bad) {
+            st = fail(c, GDC_ERR_NONFINITE, "mobility solve: non-finite residual");
+            break;
+        }
+        if (!any) {
+            inf.converged = 1;
+            break;
+        }
+        if (total >= c->p.gmres_max_iter) {
+            st = fail(c, GDC_ERR_NOT_CONVERGED, "mobility solve: GMRES reached gmres_max_iter");
+            break;
+        }
+        k_seg_scale<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->gm_r, c->gm_scal, c->gm_V);
+        int j = 0;
+        for (; j < m; ++j) {
+            double* Vj = c->gm_V + (long long)j * n;
+            launch_precond(c, Vj, c->gm_z);
+            saddle_op(c, prec, c->gm_z, c->gm_w);
+            if (prec == GDC_FP32_MIXED) inf.matvecs_fp32++; else inf.matvecs_fp64++;
+            // classical Gram-Schmidt, twice
+            seg_mdot(c, sg, c->gm_V, n, j + 1, c->gm_w, c->gm_h, cols);
+            k_mupdate<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->gm_V, n, j + 1, c->gm_h, cols, c->gm_w);
+            seg_mdot(c, sg, c->gm_V, n, j + 1, c->gm_w, c->gm_h2, cols);
+            k_mupdate<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->gm_V, n, j + 1, c->gm_h2, cols, c->gm_w);
+            k_add_cols<<<c->S, 128, 0, c->stream>>>(j + 1, c->gm_h, c->gm_h2, cols);
+            // ||w||: the column of wn2 lives after the h coefficients
+            seg_mdot(c, sg, c->gm_w, 0, 1, c->gm_w, c->gm_h2, cols);
+            k_gm_arnoldi<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(c->S, j, m, c->gm_h, cols, c->gm_h2, c->gm_H,
+                                                                     c->gm_cs, c->gm_sn, c->gm_g, c->gm_bnorm,
+                                                                     inner_tol, c->gm_res + c->S, c->gm_active,
+                                                                     c->gm_j, c->gm_scal);
+            k_seg_scale<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->gm_w, c->gm_scal, c->gm_V + (long long)(j + 1) * n);
+            ++total;
+            if ((st = sync_read(c, c->gm_active, act.data(), sizeof(int) * c->S)) != GDC_OK) return st;
+            bool still = false;
+            for (int s = 0; s < c->S; ++s) still = still || act[s];
+            if (!still || total >= c->p.gmres_max_iter) {
+                ++j;
+                break;
+            }
+        }
+        inf.iterations = std::max(inf.iterations, total);
+        // x += P^-1 V y
+        k_gm_backsolve<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(c->S, m, c->gm_H, c->gm_g, c->gm_j, c->gm_y, cols);
+        k_combine<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->gm_V, n, c->gm_j, c->gm_y, cols, nullptr, c->gm_w);
+        launch_precond(c, c->gm_w, c->gm_z);
+        k_axpy_chunks<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, 1.0, c->gm_z, x);
+        // FP64 residual r = b - A x
+        saddle_op(c, GDC_FP64, x, c->gm_w);
+        inf.matvecs_fp64++;
+        k_sub_chunks<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, b, c->gm_w, c->gm_r);
+        if ((st = cuda_check(c, cudaGetLastError(), "GMRES launch")) != GDC_OK) return st;
+    }
+    inf.iterations = total;
+    if (info) *info = inf;
+    return st;
+}
+
+// ---- Lanczos square root ------------------------------------------------------------
+
+__global__ void k_lz_start(int S, const double* __restrict__ wn2, int cols, double* __restrict__ Wnorm,
+                           double* __restrict__ scal, int* __restrict__ active, int* __restrict__ kcount,
+                           double* __restrict__ err) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    const double nrm = sqrt(fmax(wn2[(long long)s * cols], 0.0));
+    Wnorm[s] = nrm;
+    scal[s] = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    active[s] = nrm > 0.0;
+    kcount[s] = 0;
+    err[s] = 0.0;
+}
+
+// One block per suspension: T_k (k = j+1) from alpha/beta, its eigendecomposition by
+// implicit symmetric QR steps with Wilkinson shifts (Golub & Van Loan, Sec. 8.3), and
+// c = ||W|| T^(1/2) e_1.  Convergence: ||c_k - [c_{k-1}; 0]|| / ||c_k|| < tol.
+__global__ void k_lz_tridiag(int S, int j, const double* __restrict__ h, int cols, const double* __restrict__ wn2,
+                             double* __restrict__ alpha, double* __restrict__ betav, const double* __restrict__ Wnorm,
+                             double* __restrict__ cvec, double* __restrict__ err, int* __restrict__ active,
+                             int* __restrict__ kcount, double* __restrict__ scal, double tol,
+                             const int* __restrict__ fixed, int kmax, int* __restrict__ status) {
+    const int s = blockIdx.x;
+    if (!active[s]) {
+        if (threadIdx.x == 0) scal[s] = 0.0;
+        return;
+    }
+    extern __shared__ double smem[];
+    const int k = j + 1;
+    double* Q = smem;                 // k x k, row r owned by thread r
+    double* d = Q + k * k;
+    double* e = d + k;
+    double* rc = e + k;               // rotation cosines of one sweep
+    double* rs = rc + k;
+    __shared__ int lo_s, hi_s, done_s;
+    const double beta = sqrt(fmax(wn2[(long long)s * cols], 0.0));
+    if (threadIdx.x == 0) {
+        alpha[(long long)s * kmax + j] = h[(long long)s * cols + j];
+        betav[(long long)s * kmax + j] = beta;
+        for (int i = 0; i < k; ++i) d[i] = alpha[(long long)s * kmax + i];
+        for (int i = 0; i + 1 < k; ++i) e[i] = betav[(long long)s * kmax + i];
+        done_s = 0;
+    }
+    for (int r = threadIdx.x; r < k; r += blockDim.x)
+        for (int q = 0; q < k; ++q) Q[r * k + q] = (r == q) ? 1.0 : 0.0;
+    __syncthreads();
+    int hi_loc = k - 1;
+    for (int sweep = 0; sweep < 60 * k + 60; ++sweep) {
+        if (threadIdx.x == 0) {
+            int hi = hi_loc;
+            while (hi > 0 && fabs(e[hi - 1]) <= 1e-16 * (fabs(d[hi - 1]) + fabs(d[hi]))) {
+                e[hi - 1] = 0.0;
+                --hi;
+            }
+            hi_loc = hi;
+            if (hi == 0) {
+                done_s = 1;
+            } else {
+                int lo = hi - 1;
+                while (lo > 0 && fabs(e[lo - 1]) > 1e-16 * (fabs(d[lo - 1]) + fabs(d[lo]))) --lo;
+                const double da = d[hi - 1], dc = d[hi], bb = e[hi - 1];
+                const double del = 0.5 * (da - dc);
+                const double sg = del >= 0.0 ? 1.0 : -1.0;
+                const double mu = dc - bb * bb / (del + sg * hypot(del, bb));
+                double xx = d[lo] - mu, zz = e[lo];
+                for (int q = lo; q < hi; ++q) {
+                    const double rr = hypot(xx, zz);
+                    const double cq = rr > 0.0 ? xx / rr : 1.0, sq = rr > 0.0 ? zz / rr : 0.0;
+                    if (q > lo) e[q - 1] = rr;
+                    const double a0 = d[q], b0 = d[q + 1], f0 = e[q];
+                    d[q] = cq * cq * a0 + 2.0 * cq * sq * f0 + sq * sq * b0;
+                    d[q + 1] = sq * sq * a0 - 2.0 * cq * sq * f0 + cq * cq * b0;
+                    e[q] = cq * sq * (b0 - a0) + (cq * cq - sq * sq) * f0;
+                    if (q + 1 < hi) {
+                        const double bulge = sq * e[q + 1];
+                        e[q + 1] = cq * e[q + 1];
+                        xx = e[q];
+                        zz = bulge;
+                    }
+                    rc[q] = cq;
+                    rs[q] = sq;
+                }
+                lo_s = lo;
+                hi_s = hi;
+            }
+        }
+        __syncthreads();
+        if (done_s) break;
+        const int lo = lo_s, hi = hi_s;
+        for (int r = threadIdx.x; r < k; r += blockDim.x) {
+            for (int q = lo; q < hi; ++q) {
+                const double a0 = Q[r * k + q], b0 = Q[r * k + q + 1];
+                Q[r * k + q] = rc[q] * a0 + rs[q] * b0;
+                Q[r * k + q + 1] = -rs[q] * a0 + rc[q] * b0;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && !done_s) atomicExch(status, 2);
+    // c_r = ||W|| sum_q Q[r][q] sqrt(theta_q) Q[0][q]
+    const double wn = Wnorm[s];
+    double* cs_ = cvec + (long long)s * kmax;
+    __shared__ double num_s, den_s;
+    if (threadIdx.x == 0) {
+        num_s = 0.0;
+        den_s = 0.0;
+    }
+    __syncthreads();
+    double* cnew = rc;  // reuse
+    for (int r = threadIdx.x; r < k; r += blockDim.x) {
+        double acc = 0.0;
+        for (int q = 0; q < k; ++q) acc += Q[r * k + q] * sqrt(fmax(d[q], 0.0)) * Q[q];
+        cnew[r] = wn * acc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double num = 0.0, den = 0.0;
+        for (int r = 0; r < k; ++r) {
+            const double old = r < k - 1 ? cs_[r] : 0.0;
+            num += (cnew[r] - old) * (cnew[r] - old);
+            den += cnew[r] * cnew[r];
+        }
+        for (int r = 0; r < k; ++r) cs_[r] = cnew[r];
+        const double ee = den > 0.0 ? sqrt(num / den) : 0.0;
+        err[s] = ee;
+        kcount[s] = k;
+        scal[s] = beta > 0.0 ? 1.0 / beta : 0.0;
+        bool stop;
+        if (fixed && fixed[s] > 0)
+            stop = k >= fixed[s];
+        else
+            stop = (k >= 2 && ee < tol) || beta == 0.0;
+        if (k >= kmax) stop = true;
+        if (stop) active[s] = 0;
+    }
+}
+
+void krylov_init_attributes() {
+    cudaFuncSetAttribute(k_lz_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (GDC_MAX_LANCZOS * GDC_MAX_LANCZOS + 4 * GDC_MAX_LANCZOS) * (int)sizeof(double));
+}
+
+gdc_status lanczos_sqrt(gdc_ctx* c, const double* W, double* out, double scale, int fixed_mode,
+                        int* iters_out, double* err_out) {
+    const int prec = c->p.precision;
+    const long long n = 3LL * c->NBL;
+    const gdc::Seg& sg = c->seg_lz;
+    const int cols = c->red_cols;
+    const int kmax = c->kmax;
+    gdc_status st = GDC_OK;
+    seg_mdot(c, sg, W, 0, 1, W, c->lz_h, cols);
+    k_lz_start<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(c->S, c->lz_h, cols, c->lz_Wnorm, c->lz_scal, c->lz_active,
+                                                           c->lz_k, c->lz_err);
+    k_seg_scale<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, W, c->lz_scal, c->lz_V);
+    std::vector<int> act(c->S);
+    int j = 0;
+    for (; j < kmax; ++j) {
+        const double* Vj = c->lz_V + (long long)j * n;
+        rpy_op(c, prec, Vj, c->lz_w);
+        seg_mdot(c, sg, c->lz_V, n, j + 1, c->lz_w, c->lz_h, cols);
+        k_mupdate<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_V, n, j + 1, c->lz_h, cols, c->lz_w);
+        seg_mdot(c, sg, c->lz_V, n, j + 1, c->lz_w, c->gm_h2, cols);
+        k_mupdate<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_V, n, j + 1, c->gm_h2, cols, c->lz_w);
+        k_add_cols<<<c->S, 128, 0, c->stream>>>(j + 1, c->lz_h, c->gm_h2, cols);
+        seg_mdot(c, sg, c->lz_w, 0, 1, c->lz_w, c->gm_h2, cols);
+        const int k = j + 1;
+        const size_t smem = (size_t)(k * k + 4 * k) * sizeof(double);
+        k_lz_tridiag<<<c->S, 128, smem, c->stream>>>(c->S, j, c->lz_h, cols, c->gm_h2, c->lz_alpha, c->lz_beta,
+                                                     c->lz_Wnorm, c->lz_c, c->lz_err, c->lz_active, c->lz_k,
+                                                     c->lz_scal, c->p.lanczos_tol, fixed_mode ? c->lz_fix : nullptr,
+                                                     kmax, c->dev_status);
+        k_seg_scale<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_w, c->lz_scal, c->lz_V + (long long)(j + 1) * n);
+        if ((st = sync_read(c, c->lz_active, act.data(), sizeof(int) * c->S)) != GDC_OK) return st;
+        bool still = false;
+        for (int s = 0; s < c->S; ++s) still = still || act[s];
+        if (!still) {
+            ++j;
+            break;
+        }
+    }
+    // out = scale * V c
+    k_fill<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(c->S, scale, c->lz_scal);
+    k_combine<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_V, n, c->lz_k, c->lz_c, kmax, c->lz_scal, out);
+    std::vector<int> ks(c->S);
+    std::vector<double> errs(c->S);
+    if ((st = sync_read(c, c->lz_k, ks.data(), sizeof(int) * c->S)) != GDC_OK) return st;
+    if ((st = sync_read(c, c->lz_err, errs.data(), sizeof(double) * c->S)) != GDC_OK) return st;
+    int kk = 0;
+    double ee = 0.0;
+    for (int s = 0; s < c->S; ++s) {
+        kk = std::max(kk, ks[s]);
+        ee = std::max(ee, errs[s]);
+    }
+    if (iters_out) *iters_out = kk;
+    if (err_out) *err_out = ee;
+    if (!fixed_mode && ee > c->p.lanczos_tol && kk >= kmax)
+        return fail(c, GDC_ERR_NOT_CONVERGED, "Lanczos reached lanczos_max_iter");
+    return cuda_check(c, cudaGetLastError(), "Lanczos launch");
+}
+
+}  // namespace gdc

@@ -1,0 +1,463 @@
+// On-the-fly tiled N-body kernels: the RPY product u = M lambda (Sec. 4.1, Eq. 5) in
+// FP32 and FP64, and the soft blob repulsion (Eq. 20 form).  Sources are staged in
+// shared memory tile by tile; each thread owns TPT targets.  Work is split into
+// (target tile x source chunk) items so that a launch fills every SM several times
+// over; chunk partial sums are added in FP64, in chunk order, by the epilogue.
+//
+// RPY with c0 = 1/(8 pi eta), d = r_j - r_i, r = |d| (the d d^T term is even in d):
+//   r >= 2a : u_i += c0 [ (1/r + 2a^2/(3 r^3)) lambda_j + (1/r^3)(1 - 2a^2/r^2) (d.lambda_j) d ]
+//   r <  2a : u_i += c0 [ (4/(3a))(1 - 9r/(32a)) lambda_j + (1/(8 a^2 r)) (d.lambda_j) d ]
+//   r == 0  : u_i += c0 (4/(3a)) lambda_j                     (self term 1/(6 pi eta a))
+#include <algorithm>
+#include <numeric>
+
+#include "common.cuh"
+
+namespace gdc {
+
+constexpr int MV_TILE = 256;
+
+// ---- source packing ---------------------------------------------------------
+
+__global__ void k_pack_lam32(int NBL, const int* __restrict__ map, const double* __restrict__ x,
+                             float4* __restrict__ slam) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= NBL) return;
+    const long long o = map ? (long long)map[i] : 3LL * i;
+    slam[i] = make_float4((float)x[o], (float)x[o + 1], (float)x[o + 2], 0.f);
+}
+
+__global__ void k_pack_lam64(int NBL, const int* __restrict__ map, const double* __restrict__ x,
+                             double4* __restrict__ slam) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= NBL) return;
+    const long long o = map ? (long long)map[i] : 3LL * i;
+    slam[i] = make_double4(x[o], x[o + 1], x[o + 2], 0.0);
+}
+
+void launch_pack_lambda(gdc_ctx* c, int prec, const double* x, int gm_layout) {
+    const int* map = gm_layout ? c->blob_gm : nullptr;
+    if (prec == GDC_FP32_MIXED)
+        k_pack_lam32<<<ceil_div(c->NBL, 256), 256, 0, c->stream>>>(c->NBL, map, x, c->slam);
+    else
+        k_pack_lam64<<<ceil_div(c->NBL, 256), 256, 0, c->stream>>>(c->NBL, map, x, c->slam64);
+}
+
+// ---- FP32 RPY pair kernel -----------------------------------------------------
+
+struct RpyConst32 {
+    float c23;     // 2a^2/3
+    float c2;      // 2a^2
+    float four_a2; // 4a^2
+    float cA;      // 4/(3a)
+    float c9;      // 9/(32a)
+    float cB;      // 1/(8a^2)
+};
+
+template <int TPT>
+__global__ void __launch_bounds__(128) k_rpy32(const MvItem* __restrict__ items, const long long* __restrict__ susp_blob_off,
+                                               const float4* __restrict__ spos, const float4* __restrict__ slam,
+                                               float4* __restrict__ part, int NBL, RpyConst32 k) {
+    __shared__ float4 sp[MV_TILE];
+    __shared__ float4 sl[MV_TILE];
+    const MvItem it = items[blockIdx.x];
+    const long long b0 = susp_blob_off[it.s];
+    const int ns = (int)(susp_blob_off[it.s + 1] - b0);
+
+    float xt[TPT], yt[TPT], zt[TPT];
+    float ax[TPT], ay[TPT], az[TPT], cx[TPT], cy[TPT], cz[TPT];
+#pragma unroll
+    for (int t = 0; t < TPT; ++t) {
+        const int ti = it.t0 + threadIdx.x + t * 128;
+        const float4 p = spos[b0 + min(ti, ns - 1)];
+        xt[t] = p.x;
+        yt[t] = p.y;
+        zt[t] = p.z;
+        ax[t] = ay[t] = az[t] = 0.f;
+        cx[t] = cy[t] = cz[t] = 0.f;
+    }
+    for (int j0 = it.j0; j0 < it.j1; j0 += MV_TILE) {
+        const int n = min(MV_TILE, it.j1 - j0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < n; e += 128) {
+            sp[e] = spos[b0 + j0 + e];
+            sl[e] = slam[b0 + j0 + e];
+        }
+        __syncthreads();
+        float tx[TPT], ty[TPT], tz[TPT];
+#pragma unroll
+        for (int t = 0; t < TPT; ++t) tx[t] = ty[t] = tz[t] = 0.f;
+#pragma unroll 4
+        for (int j = 0; j < n; ++j) {
+            const float4 ps = sp[j];
+            const float4 ls = sl[j];
+#pragma unroll
+            for (int t = 0; t < TPT; ++t) {
+                const float dx = ps.x - xt[t], dy = ps.y - yt[t], dz = ps.z - zt[t];
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                const float ri = rsqrtf(r2);
+                const float ri2 = ri * ri;
+                const float ri3 = ri2 * ri;
+                float A = fmaf(k.c23, ri3, ri);
+                float B = ri3 * fmaf(-k.c2, ri2, 1.f);
+                if (r2 < k.four_a2) {
+                    const bool pos = r2 > 0.f;
+                    const float r = pos ? r2 * ri : 0.f;
+                    A = k.cA * fmaf(-k.c9, r, 1.f);
+                    B = pos ? ri * k.cB : 0.f;
+                }
+                const float dl = fmaf(dx, ls.x, fmaf(dy, ls.y, dz * ls.z));
+                const float s = B * dl;
+                tx[t] = fmaf(A, ls.x, fmaf(s, dx, tx[t]));
+                ty[t] = fmaf(A, ls.y, fmaf(s, dy, ty[t]));
+                tz[t] = fmaf(A, ls.z, fmaf(s, dz, tz[t]));
+            }
+        }
+        // compensated (Kahan) addition of the tile sums
+#pragma unroll
+        for (int t = 0; t < TPT; ++t) {
+            float y, u;
+            y = tx[t] - cx[t]; u = ax[t] + y; cx[t] = (u - ax[t]) - y; ax[t] = u;
+            y = ty[t] - cy[t]; u = ay[t] + y; cy[t] = (u - ay[t]) - y; ay[t] = u;
+            y = tz[t] - cz[t]; u = az[t] + y; cz[t] = (u - az[t]) - y; az[t] = u;
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < TPT; ++t) {
+        const int ti = it.t0 + threadIdx.x + t * 128;
+        if (ti < ns) part[(long long)it.k * NBL + b0 + ti] = make_float4(ax[t] - cx[t], ay[t] - cy[t], az[t] - cz[t], 0.f);
+    }
+}
+
+// ---- FP64 RPY pair kernel -----------------------------------------------------
+
+template <int TPT>
+__global__ void __launch_bounds__(128) k_rpy64(const MvItem* __restrict__ items, const long long* __restrict__ susp_blob_off,
+                                               const double4* __restrict__ spos, const double4* __restrict__ slam,
+                                               double4* __restrict__ part, int NBL, double a) {
+    __shared__ double4 sp[MV_TILE];
+    __shared__ double4 sl[MV_TILE];
+    const MvItem it = items[blockIdx.x];
+    const long long b0 = susp_blob_off[it.s];
+    const int ns = (int)(susp_blob_off[it.s + 1] - b0);
+    const double c23 = 2.0 * a * a / 3.0, c2 = 2.0 * a * a, four_a2 = 4.0 * a * a;
+    const double cA = 4.0 / (3.0 * a), c9 = 9.0 / (32.0 * a), cB = 1.0 / (8.0 * a * a);
+    double xt[TPT], yt[TPT], zt[TPT], ax[TPT], ay[TPT], az[TPT];
+#pragma unroll
+    for (int t = 0; t < TPT; ++t) {
+        const int ti = it.t0 + threadIdx.x + t * 128;
+        const double4 p = spos[b0 + min(ti, ns - 1)];
+        xt[t] = p.x;
+        yt[t] = p.y;
+        zt[t] = p.z;
+        ax[t] = ay[t] = az[t] = 0.0;
+    }
+    for (int j0 = it.j0; j0 < it.j1; j0 += MV_TILE) {
+        const int n = min(MV_TILE, it.j1 - j0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < n; e += 128) {
+            sp[e] = spos[b0 + j0 + e];
+            sl[e] = slam[b0 + j0 + e];
+        }
+        __syncthreads();
+        for (int j = 0; j < n; ++j) {
+            const double4 ps = sp[j];
+            const double4 ls = sl[j];
+#pragma unroll
+            for (int t = 0; t < TPT; ++t) {
+                const double dx = ps.x - xt[t], dy = ps.y - yt[t], dz = ps.z - zt[t];
+                const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+                double A, B;
+                if (r2 < four_a2) {
+                    if (r2 > 0.0) {
+                        const double r = sqrt(r2);
+                        A = cA * fma(-c9, r, 1.0);
+                        B = cB / r;
+                    } else {
+                        A = cA;
+                        B = 0.0;
+                    }
+                } else {
+                    const double ri = rsqrt(r2);
+                    const double ri2 = ri * ri, ri3 = ri2 * ri;
+                    A = fma(c23, ri3, ri);
+                    B = ri3 * fma(-c2, ri2, 1.0);
+                }
+                const double dl = fma(dx, ls.x, fma(dy, ls.y, dz * ls.z));
+                const double s = B * dl;
+                ax[t] = fma(A, ls.x, fma(s, dx, ax[t]));
+                ay[t] = fma(A, ls.y, fma(s, dy, ay[t]));
+                az[t] = fma(A, ls.z, fma(s, dz, az[t]));
+            }
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < TPT; ++t) {
+        const int ti = it.t0 + threadIdx.x + t * 128;
+        if (ti < ns) part[(long long)it.k * NBL + b0 + ti] = make_double4(ax[t], ay[t], az[t], 0.0);
+    }
+}
+
+void launch_rpy(gdc_ctx* c, int prec) {
+    if (prec == GDC_FP32_MIXED) {
+        const double a = c->p.a;
+        RpyConst32 k{(float)(2.0 * a * a / 3.0), (float)(2.0 * a * a), (float)(4.0 * a * a),
+                     (float)(4.0 / (3.0 * a)), (float)(9.0 / (32.0 * a)), (float)(1.0 / (8.0 * a * a))};
+        if (c->mv_tpt == 1)
+            k_rpy32<1><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off, c->spos, c->slam,
+                                                             (float4*)c->mv_part, c->NBL, k);
+        else if (c->mv_tpt == 4)
+            k_rpy32<4><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off, c->spos, c->slam,
+                                                             (float4*)c->mv_part, c->NBL, k);
+        else
+            k_rpy32<2><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off, c->spos, c->slam,
+                                                             (float4*)c->mv_part, c->NBL, k);
+    } else {
+        if (c->mv_tpt == 1)
+            k_rpy64<1><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off, c->spos64, c->slam64,
+                                                             (double4*)c->mv_part, c->NBL, c->p.a);
+        else if (c->mv_tpt == 4)
+            k_rpy64<4><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off, c->spos64, c->slam64,
+                                                             (double4*)c->mv_part, c->NBL, c->p.a);
+        else
+            k_rpy64<2><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off, c->spos64, c->slam64,
+                                                             (double4*)c->mv_part, c->NBL, c->p.a);
+    }
+}
+
+// ---- epilogue: chunk sums in FP64, scale, and the -K V part of the saddle operator ----
+
+template <typename P>
+__device__ inline void load_part(const P* part, long long idx, double& x, double& y, double& z) {
+    const P v = part[idx];
+    x = (double)v.x;
+    y = (double)v.y;
+    z = (double)v.z;
+}
+
+template <typename P>
+__global__ void k_rpy_epilogue(int NBL, const P* __restrict__ part, const int* __restrict__ blob_susp,
+                               const int* __restrict__ nk, double c0, const double* __restrict__ x,
+                               double* __restrict__ y, int gm_layout, const int* __restrict__ blob_gm,
+                               const int* __restrict__ body_gm, const int* __restrict__ blob_body,
+                               const double* __restrict__ r, const double* __restrict__ Yc) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= NBL) return;
+    const int n = nk[blob_susp[i]];
+    double ux = 0.0, uy = 0.0, uz = 0.0;
+    for (int k = 0; k < n; ++k) {
+        double a, b, cc;
+        load_part(part, (long long)k * NBL + i, a, b, cc);
+        ux += a;
+        uy += b;
+        uz += cc;
+    }
+    ux *= c0;
+    uy *= c0;
+    uz *= c0;
+    if (!gm_layout) {
+        y[3 * i] = ux;
+        y[3 * i + 1] = uy;
+        y[3 * i + 2] = uz;
+        return;
+    }
+    // saddle operator: M lambda - K V, K V = U_p + Omega_p x (r_i - Y_p)  (Eqs. 6-9)
+    const int p = blob_body[i];
+    const double* V = x + body_gm[p];
+    const double dx = r[3 * i] - Yc[3 * p], dy = r[3 * i + 1] - Yc[3 * p + 1], dz = r[3 * i + 2] - Yc[3 * p + 2];
+    const double kx = V[0] + (V[4] * dz - V[5] * dy);
+    const double ky = V[1] + (V[5] * dx - V[3] * dz);
+    const double kz = V[2] + (V[3] * dy - V[4] * dx);
+    const long long o = blob_gm[i];
+    y[o] = ux - kx;
+    y[o + 1] = uy - ky;
+    y[o + 2] = uz - kz;
+}
+
+static void launch_epilogue(gdc_ctx* c, int prec, double c0, const double* x, double* y, int gm_layout) {
+    if (prec == GDC_FP32_MIXED)
+        k_rpy_epilogue<float4><<<ceil_div(c->NBL, 256), 256, 0, c->stream>>>(
+            c->NBL, (const float4*)c->mv_part, c->blob_susp, c->mv_nk, c0, x, y, gm_layout, c->blob_gm, c->body_gm,
+            c->blob_body, c->r, c->Yc);
+    else
+        k_rpy_epilogue<double4><<<ceil_div(c->NBL, 256), 256, 0, c->stream>>>(
+            c->NBL, (const double4*)c->mv_part, c->blob_susp, c->mv_nk, c0, x, y, gm_layout, c->blob_gm, c->body_gm,
+            c->blob_body, c->r, c->Yc);
+}
+
+void launch_rpy_epilogue(gdc_ctx* c, int prec, const double* x, double* y, int gm_layout) {
+    launch_epilogue(c, prec, 1.0 / (8.0 * 3.141592653589793 * c->p.eta), x, y, gm_layout);
+}
+
+// ---- soft repulsion between blobs of different bodies --------------------------
+
+// f_i = sum_j F(|r_i - r_j|) (r_i - r_j)/|r_i - r_j| over blobs j of other bodies,
+// F(r) = A exp(-(r - 2a)/b) for r >= 2a, A below.  Pairs with (r - 2a)/b > 36 are
+// skipped (their force is below 2.4e-16 A).
+template <int TPT>
+__global__ void __launch_bounds__(128) k_forces32(const MvItem* __restrict__ items, const long long* __restrict__ susp_blob_off,
+                                                  const float4* __restrict__ spos, float4* __restrict__ part, int NBL,
+                                                  float A, float b, float two_a, float rc2) {
+    __shared__ float4 sp[MV_TILE];
+    const MvItem it = items[blockIdx.x];
+    const long long b0 = susp_blob_off[it.s];
+    const int ns = (int)(susp_blob_off[it.s + 1] - b0);
+    const int ti0 = it.t0 + threadIdx.x;
+    float xt[TPT], yt[TPT], zt[TPT], fx[TPT], fy[TPT], fz[TPT];
+    int bt[TPT];
+    const float inv_b = 1.f / b;
+    for (int t = 0; t < TPT; ++t) {
+        fx[t] = fy[t] = fz[t] = 0.f;
+        const float4 p = spos[b0 + min(ti0 + t * 128, ns - 1)];
+        xt[t] = p.x;
+        yt[t] = p.y;
+        zt[t] = p.z;
+        bt[t] = __float_as_int(p.w);
+    }
+    for (int j0 = it.j0; j0 < it.j1; j0 += MV_TILE) {
+        const int n = min(MV_TILE, it.j1 - j0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < n; e += 128) sp[e] = spos[b0 + j0 + e];
+        __syncthreads();
+        for (int j = 0; j < n; ++j) {
+            const float4 ps = sp[j];
+            const int bj = __float_as_int(ps.w);
+#pragma unroll
+            for (int t = 0; t < TPT; ++t) {
+                const float dx = xt[t] - ps.x, dy = yt[t] - ps.y, dz = zt[t] - ps.z;
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                if (bj != bt[t] && r2 < rc2 && r2 > 0.f) {
+                    const float r = sqrtf(r2);
+                    const float F = r >= two_a ? A * expf(-(r - two_a) * inv_b) : A;
+                    const float s = F / r;
+                    fx[t] = fmaf(s, dx, fx[t]);
+                    fy[t] = fmaf(s, dy, fy[t]);
+                    fz[t] = fmaf(s, dz, fz[t]);
+                }
+            }
+        }
+    }
+    for (int t = 0; t < TPT; ++t) {
+        const int ti = ti0 + t * 128;
+        if (ti < ns) part[(long long)it.k * NBL + b0 + ti] = make_float4(fx[t], fy[t], fz[t], 0.f);
+    }
+}
+
+template <int TPT>
+__global__ void __launch_bounds__(128) k_forces64(const MvItem* __restrict__ items, const long long* __restrict__ susp_blob_off,
+                                                  const double4* __restrict__ spos, double4* __restrict__ part, int NBL,
+                                                  double A, double b, double two_a, double rc2) {
+    __shared__ double4 sp[MV_TILE];
+    const MvItem it = items[blockIdx.x];
+    const long long b0 = susp_blob_off[it.s];
+    const int ns = (int)(susp_blob_off[it.s + 1] - b0);
+    const int ti0 = it.t0 + threadIdx.x;
+    double xt[TPT], yt[TPT], zt[TPT], fx[TPT], fy[TPT], fz[TPT];
+    long long bt[TPT];
+    for (int t = 0; t < TPT; ++t) {
+        fx[t] = fy[t] = fz[t] = 0.0;
+        const double4 p = spos[b0 + min(ti0 + t * 128, ns - 1)];
+        xt[t] = p.x;
+        yt[t] = p.y;
+        zt[t] = p.z;
+        bt[t] = (long long)p.w;
+    }
+    for (int j0 = it.j0; j0 < it.j1; j0 += MV_TILE) {
+        const int n = min(MV_TILE, it.j1 - j0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < n; e += 128) sp[e] = spos[b0 + j0 + e];
+        __syncthreads();
+        for (int j = 0; j < n; ++j) {
+            const double4 ps = sp[j];
+            const long long bj = (long long)ps.w;
+#pragma unroll
+            for (int t = 0; t < TPT; ++t) {
+                const double dx = xt[t] - ps.x, dy = yt[t] - ps.y, dz = zt[t] - ps.z;
+                const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+                if (bj != bt[t] && r2 < rc2 && r2 > 0.0) {
+                    const double r = sqrt(r2);
+                    const double F = r >= two_a ? A * exp(-(r - two_a) / b) : A;
+                    const double s = F / r;
+                    fx[t] = fma(s, dx, fx[t]);
+                    fy[t] = fma(s, dy, fy[t]);
+                    fz[t] = fma(s, dz, fz[t]);
+                }
+            }
+        }
+    }
+    for (int t = 0; t < TPT; ++t) {
+        const int ti = ti0 + t * 128;
+        if (ti < ns) part[(long long)it.k * NBL + b0 + ti] = make_double4(fx[t], fy[t], fz[t], 0.0);
+    }
+}
+
+#define GDC_FORCES_LAUNCH(TPT)                                                                         \
+    do {                                                                                               \
+        if (prec == GDC_FP32_MIXED)                                                                    \
+            k_forces32<TPT><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off, c->spos, \
+                (float4*)c->mv_part, c->NBL, (float)A, (float)b, (float)two_a, (float)(rc * rc));           \
+        else                                                                                           \
+            k_forces64<TPT><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off,          \
+                c->spos64, (double4*)c->mv_part, c->NBL, A, b, two_a, rc * rc);                            \
+    } while (0)
+
+void launch_forces_pair(gdc_ctx* c, int prec, double* fblob) {
+    const double A = c->p.rep_A, b = c->p.rep_b, two_a = 2.0 * c->p.a;
+    const double rc = two_a + 36.0 * b;
+    if (c->mv_tpt == 1)
+        GDC_FORCES_LAUNCH(1);
+    else if (c->mv_tpt == 4)
+        GDC_FORCES_LAUNCH(4);
+    else
+        GDC_FORCES_LAUNCH(2);
+    launch_epilogue(c, prec, 1.0, nullptr, fblob, 0);
+}
+
+// ---- work list ------------------------------------------------------------------------
+
+void build_mv_items(gdc_ctx* c) {
+    const int tile_targets = 128 * c->mv_tpt;
+    double P = 0.0;
+    std::vector<long long> ns(c->S);
+    for (int s = 0; s < c->S; ++s) {
+        ns[s] = c->h_blob_off[s + 1] - c->h_blob_off[s];
+        P += (double)ns[s] * (double)ns[s];
+    }
+    c->pair_evals_per_matvec = P;
+    const double target_items = (double)c->num_sms * 4.0 * 8.0;  // ~8 waves of 4 blocks per SM
+    c->h_mv_items.clear();
+    c->h_mv_nk.assign(c->S, 1);
+    int kmax = 1;
+    for (int s = 0; s < c->S; ++s) {
+        const long long n = ns[s];
+        const int nt = ceil_div(n, tile_targets);
+        int nk = (int)std::lround(target_items * (double)n * (double)n / std::max(P, 1.0) / std::max(nt, 1));
+        nk = std::max(1, std::min(nk, std::max(1, ceil_div(n, 512))));
+        nk = std::min(nk, 64);
+        long long csz = (n + nk - 1) / nk;
+        csz = ((csz + 31) / 32) * 32;
+        nk = (int)std::max<long long>(1, (n + csz - 1) / csz);
+        c->h_mv_nk[s] = nk;
+        kmax = std::max(kmax, nk);
+        for (int t = 0; t < nt; ++t)
+            for (int k = 0; k < nk; ++k) {
+                MvItem it{};
+                it.s = s;
+                it.t0 = t * tile_targets;
+                it.j0 = (int)(k * csz);
+                it.j1 = (int)std::min<long long>(n, (k + 1) * csz);
+                it.k = k;
+                if (it.j1 > it.j0) c->h_mv_items.push_back(it);
+            }
+    }
+    // largest items first, so the tail of the launch is made of small ones
+    std::stable_sort(c->h_mv_items.begin(), c->h_mv_items.end(), [&](const MvItem& x, const MvItem& y) {
+        const long long cx = (long long)std::min<long long>(tile_targets, ns[x.s] - x.t0) * (x.j1 - x.j0);
+        const long long cy = (long long)std::min<long long>(tile_targets, ns[y.s] - y.t0) * (y.j1 - y.j0);
+        return cx > cy;
+    });
+    c->mv_n_items = (int)c->h_mv_items.size();
+    c->mv_kmax = kmax;
+}
+
+}  // namespace gdc

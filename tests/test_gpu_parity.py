@@ -1,0 +1,321 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle on seeded inputs.
+
+Tolerances: FP64 paths agree with the oracle to rounding and solver tolerance; the
+FP32-mixed path must meet the target of one-step positions and orientations to
+relative 1e-5 with mobility-solve residual <= 1e-6 (checked with the oracle's
+dense FP64 operator).  Sizes span several 256-target tiles with ragged tails.
+"""
+import numpy as np
+import pytest
+
+from oracle import forces, geometry as G, philox, rigid, rpy
+from oracle import gdc as ogdc
+from synthetic import workloads as WL
+
+from gpu_common import blob_slices, dense_state, oracle_params, rel, rot_err, susp_layout
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def wl_mix():
+    return WL.mixed_small(40, seed=1)
+
+
+@pytest.fixture(scope="module")
+def wl_batch():
+    return WL.batch_small(6, seed=3)
+
+
+@pytest.fixture(scope="module")
+def wl_rod():
+    return WL.c2(seed=2, n_rods=60, box=37.0)
+
+
+@pytest.fixture(scope="module")
+def wl_c1():
+    return WL.c1()
+
+
+def ctx_for(lib, wl, **kw):
+    return lib.context_from_workload(wl, **kw)
+
+
+def _host(t):
+    return t.detach().cpu().numpy()
+
+
+def test_normals_match_oracle(lib, wl_batch):
+    ctx = ctx_for(lib, wl_batch, seed=1234567890123)
+    sl = blob_slices(wl_batch)
+    for step in (0, 7):
+        W = _host(ctx.draw_normals(step, 0))
+        Wt = _host(ctx.draw_normals(step, 1))
+        for s in range(wl_batch.n_susp):
+            lay, _, _ = susp_layout(wl_batch, s)
+            a, b = sl[s]
+            ref = philox.normals(1234567890123, s, step, 0, 3 * lay.n_blobs)
+            np.testing.assert_allclose(W[3 * a:3 * b], ref, rtol=0, atol=1e-13)
+            o = int(wl_batch.susp_body_off[s])
+            ref_t = philox.normals(1234567890123, s, step, 1, 6 * lay.n_bodies)
+            np.testing.assert_allclose(Wt[6 * o:6 * o + 6 * lay.n_bodies], ref_t, rtol=0, atol=1e-13)
+
+
+def test_blob_positions(lib, wl_mix):
+    ctx = ctx_for(lib, wl_mix)
+    lay, Y, q = susp_layout(wl_mix, 0)
+    np.testing.assert_allclose(_host(ctx.blob_positions()).reshape(-1, 3), G.blob_positions(lay, Y, q),
+                               rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("which", ["mix", "batch"])
+def test_rpy_apply(lib, wl_mix, wl_batch, prec, which):
+    wl = wl_mix if which == "mix" else wl_batch
+    ctx = ctx_for(lib, wl)
+    rng = np.random.default_rng(11)
+    lam = rng.standard_normal(3 * wl.n_blobs)
+    u = _host(ctx.rpy_apply(lam, prec))
+    sl = blob_slices(wl)
+    for s in range(wl.n_susp):
+        lay, Y, q = susp_layout(wl, s)
+        a, b = sl[s]
+        r, M, _, _ = dense_state(lay, Y, q)
+        ref = M @ lam[3 * a:3 * b]
+        if prec == 0:
+            assert rel(u[3 * a:3 * b], ref) < 1e-13
+        else:
+            assert rel(u[3 * a:3 * b], ref) < 2e-6
+            assert np.abs(u[3 * a:3 * b] - ref).max() < 1e-5 * np.abs(ref).max()
+
+
+def _oracle_saddle(wl):
+    out = []
+    for s in range(wl.n_susp):
+        lay, Y, q = susp_layout(wl, s)
+        out.append(dense_state(lay, Y, q) + (lay,))
+    return out
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_saddle_apply(lib, wl_batch, prec):
+    ctx = ctx_for(lib, wl_batch)
+    rng = np.random.default_rng(12)
+    n = int(ctx.saddle_off[-1])
+    x = rng.standard_normal(n)
+    y = _host(ctx.saddle_apply(x, prec))
+    for s, (r, M, K, B, lay) in enumerate(_oracle_saddle(wl_batch)):
+        o = int(ctx.saddle_off[s])
+        lam, V = x[o:o + 3 * lay.n_blobs], x[o + 3 * lay.n_blobs:o + 3 * lay.n_blobs + 6 * lay.n_bodies]
+        y1, y2 = rigid.saddle_apply(M, K, lam, V)
+        got = y[o:o + 3 * lay.n_blobs + 6 * lay.n_bodies]
+        tol = 1e-13 if prec == 0 else 2e-6
+        assert rel(got, np.concatenate([y1, y2])) < tol
+
+
+def test_precond_apply(lib, wl_mix, wl_rod):
+    for wl in (wl_mix, wl_rod):
+        ctx = ctx_for(lib, wl)
+        rng = np.random.default_rng(13)
+        n = int(ctx.saddle_off[-1])
+        rvec = rng.standard_normal(n)
+        z = _host(ctx.precond_apply(rvec))
+        lay, Y, q = susp_layout(wl, 0)
+        r, M, K, B = dense_state(lay, Y, q)
+        nl = 3 * lay.n_blobs
+        ref_l = np.zeros(nl)
+        ref_v = np.zeros(6 * lay.n_bodies)
+        for p in range(lay.n_bodies):
+            i0, i1 = lay.blob_off[p], lay.blob_off[p + 1]
+            Mp = M[3 * i0:3 * i1, 3 * i0:3 * i1]
+            Kp = K[3 * i0:3 * i1, 6 * p:6 * p + 6]
+            Bp = rigid.rigid_basis(Kp, 1)
+            rv = Bp @ (Bp.T @ rvec[nl + 6 * p:nl + 6 * p + 6])
+            lp, vp = rigid.saddle_solve(Mp, Kp, Bp, -rvec[3 * i0:3 * i1], -rv)
+            ref_l[3 * i0:3 * i1] = lp
+            ref_v[6 * p:6 * p + 6] = vp
+        # rods: the axial torque component is not in the range of K^T and is dropped
+        assert rel(z[:nl], ref_l) < 1e-10
+        assert rel(z[nl:], ref_v) < 1e-10
+
+
+def test_lsq_velocity(lib, wl_mix, wl_rod):
+    for wl in (wl_mix, wl_rod):
+        ctx = ctx_for(lib, wl)
+        rng = np.random.default_rng(14)
+        vb = rng.standard_normal(3 * wl.n_blobs)
+        got = _host(ctx.lsq_velocity(vb))
+        lay, Y, q = susp_layout(wl, 0)
+        r, M, K, B = dense_state(lay, Y, q)
+        assert rel(got, rigid.lsq_velocity(K, B, vb)) < 1e-12
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_brownian_slip_lanczos(lib, wl_mix, prec):
+    tol = 1e-11 if prec == 0 else 1e-6
+    ctx = ctx_for(lib, wl_mix, precision=prec, lanczos_tol=tol, lanczos_max_iter=128, kT=1.3, dt=0.02)
+    rng = np.random.default_rng(15)
+    W = rng.standard_normal(3 * wl_mix.n_blobs)
+    vb, iters, err = ctx.brownian_slip(W)
+    lay, Y, q = susp_layout(wl_mix, 0)
+    r, M, K, B = dense_state(lay, Y, q)
+    ref = np.sqrt(2 * 1.3 / 0.02) * rigid.sqrtm_sym(M) @ W
+    assert 2 <= iters <= 128
+    assert rel(_host(vb), ref) < (1e-9 if prec == 0 else 2e-5)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_mobility_solve(lib, wl_mix, wl_rod, wl_batch, prec):
+    for wl in (wl_mix, wl_rod, wl_batch):
+        tol = 1e-12 if prec == 0 else 1e-6
+        ctx = ctx_for(lib, wl, precision=prec, gmres_tol=tol, gmres_max_iter=800)
+        rng = np.random.default_rng(16)
+        FT = rng.standard_normal(6 * wl.n_bodies)
+        vb = rng.standard_normal(3 * wl.n_blobs)
+        dense = _oracle_saddle(wl)
+        for s, (r, M, K, B, lay) in enumerate(dense):
+            o = int(wl.susp_body_off[s])
+            # rod axial torques are outside the range of K^T: physical torques never have them
+            FT[6 * o:6 * o + 6 * lay.n_bodies] = B @ (B.T @ FT[6 * o:6 * o + 6 * lay.n_bodies])
+        V, lam, info = ctx.mobility_solve(FT, vb, want_lambda=True)
+        V, lam = _host(V), _host(lam)
+        assert info["converged"] and info["residual"] <= tol
+        sl = blob_slices(wl)
+        for s, (r, M, K, B, lay) in enumerate(dense):
+            a, b = sl[s]
+            o = int(wl.susp_body_off[s])
+            Fs = FT[6 * o:6 * o + 6 * lay.n_bodies]
+            ls, Vs = rigid.saddle_solve(M, K, B, vb[3 * a:3 * b], Fs)
+            Vg = V[6 * o:6 * o + 6 * lay.n_bodies]
+            lg = lam[3 * a:3 * b]
+            # FP64 residual of the GPU solution with the oracle's dense operator
+            y1, y2 = rigid.saddle_apply(M, K, lg, Vg)
+            res = np.linalg.norm(np.concatenate([y1 + vb[3 * a:3 * b], y2 + Fs])) / np.linalg.norm(
+                np.concatenate([vb[3 * a:3 * b], Fs]))
+            assert res <= 2 * tol, res
+            assert rel(Vg, Vs) < (1e-9 if prec == 0 else 1e-4)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_forces(lib, wl_mix, prec):
+    ctx = ctx_for(lib, wl_mix, precision=prec)
+    got = _host(ctx.forces())
+    lay, Y, q = susp_layout(wl_mix, 0)
+    r = G.blob_positions(lay, Y, q)
+    f = forces.blob_forces(r, lay.blob_body, wl_mix.params["rep_A"], wl_mix.params["rep_b"], 1.0)
+    ref = forces.body_force_torque(r, Y, lay.blob_body, f)
+    assert np.abs(ref).max() > 0
+    assert rel(got, ref) < (1e-12 if prec == 0 else 1e-5)
+
+
+def _oracle_step(wl, s, seed, step, op, div="rfd", scheme="gdc"):
+    lay, Y, q = susp_layout(wl, s)
+    W = philox.normals(seed, s, step, 0, 3 * lay.n_blobs)
+    Wt = philox.normals(seed, s, step, 1, 6 * lay.n_bodies)
+    if scheme == "em":
+        return ogdc.em_step(lay, Y, q, W, op)
+    return ogdc.gdc_step(lay, Y, q, W, Wt, op, div=div)
+
+
+def _step_case(lib, wl, prec, div=0, scheme=0):
+    seed = 77
+    delta = 1e-6 if prec == 0 else 1e-3
+    kw = dict(precision=prec, seed=seed, rfd_delta=delta, divmode=div, scheme=scheme, lanczos_max_iter=128)
+    if prec == 0:
+        kw.update(gmres_tol=1e-12, lanczos_tol=1e-11, gmres_max_iter=1000)
+    else:
+        kw.update(gmres_tol=1e-6, lanczos_tol=1e-7, gmres_max_iter=1000)
+    ctx = ctx_for(lib, wl, **kw)
+    tr = ctx.set_trace(True)
+    info = ctx.step(1)[0]
+    Y1, q1, stp = ctx.get_state()
+    assert stp == 1
+    op = oracle_params(wl, rfd_delta=delta)
+    out = []
+    for s in range(wl.n_susp):
+        o, e = int(wl.susp_body_off[s]), int(wl.susp_body_off[s + 1])
+        ora = _oracle_step(wl, s, seed, 0, op, div="rfd" if div == 0 else "fd", scheme="gdc" if scheme == 0 else "em")
+        out.append((s, o, e, ora))
+    return ctx, tr, info, Y1, q1, out
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("which", ["c1", "mix", "rod", "batch"])
+def test_gdc_step_parity(lib, wl_c1, wl_mix, wl_rod, wl_batch, prec, which):
+    wl = dict(c1=wl_c1, mix=wl_mix, rod=wl_rod, batch=wl_batch)[which]
+    ctx, tr, info, Y1, q1, out = _step_case(lib, wl, prec)
+    assert info["solve"]["converged"]
+    nu = _host(tr["nu"])
+    calV = _host(tr["calV"]).reshape(-1, 6)
+    Vm = _host(tr["Vm"]).reshape(-1, 6)
+    for s, o, e, ora in out:
+        Y0 = wl.Y[o:e]
+        pos_err = np.abs(Y1[o:e] - ora["Y1"]).max() / np.abs(ora["Y1"]).max()
+        disp_err = rel(Y1[o:e] - Y0, ora["Y1"] - Y0)
+        r_err = rot_err(q1[o:e], ora["q1"])
+        if prec == 0:
+            assert pos_err < 1e-11 and r_err < 1e-9 and disp_err < 1e-6, (pos_err, r_err, disp_err)
+            assert rel(calV[o:e], ora["calV"]) < 1e-8
+            assert abs(nu[s] - ora["nu"]) < 1e-6
+            assert rel(Vm[o:e], ora["V"]) < 1e-7
+        else:
+            assert pos_err < 1e-5 and r_err < 1e-5, (pos_err, r_err, disp_err)
+            assert disp_err < 1e-3, disp_err
+            assert rel(calV[o:e], ora["calV"]) < 1e-4
+            assert abs(nu[s] - ora["nu"]) < 1e-3
+
+
+def test_em_step_parity(lib, wl_mix):
+    ctx, tr, info, Y1, q1, out = _step_case(lib, wl_mix, 0, scheme=1)
+    for s, o, e, ora in out:
+        assert rel(Y1[o:e] - wl_mix.Y[o:e], ora["Y1"] - wl_mix.Y[o:e]) < 1e-7
+        assert rot_err(q1[o:e], ora["q1"]) < 1e-9
+
+
+def test_fd_divergence_parity(lib, wl_c1):
+    ctx, tr, info, Y1, q1, out = _step_case(lib, wl_c1, 0, div=1)
+    nu = _host(tr["nu"])
+    for s, o, e, ora in out:
+        assert abs(nu[s] - ora["nu"]) < 1e-6
+        assert rel(Y1[o:e] - wl_c1.Y[o:e], ora["Y1"] - wl_c1.Y[o:e]) < 1e-6
+
+
+def test_checkpoint_resume_is_bitwise(lib, wl_batch):
+    ctx = ctx_for(lib, wl_batch, precision=1, rfd_delta=1e-3)
+    Y0, q0, _ = ctx.get_state()
+    ctx.step(2)
+    Ya, qa, sa = ctx.get_state()
+    ctx.set_state(Y0, q0, 0)
+    ctx.step(1)
+    Yh, qh, sh = ctx.get_state()
+    ctx.set_state(Yh, qh, sh)
+    ctx.step(1)
+    Yb, qb, sb = ctx.get_state()
+    assert sa == sb == 2
+    np.testing.assert_array_equal(Ya, Yb)
+    np.testing.assert_array_equal(qa, qb)
+
+
+def test_errors_are_reported(lib, wl_c1):
+    ctx = ctx_for(lib, wl_c1)
+    Y, q, _ = ctx.get_state()
+    bad = q.copy()
+    bad[1] *= 1.5
+    with pytest.raises(lib.GdcError) as ei:
+        ctx.set_state(Y, bad, 0)
+    assert ei.value.status == 1
+    Yn = Y.copy()
+    Yn[0, 0] = np.nan
+    with pytest.raises(lib.GdcError):
+        ctx.set_state(Yn, q, 0)
+    ctx2 = ctx_for(lib, wl_c1, gmres_tol=1e-15, gmres_max_iter=2)
+    with pytest.raises(lib.GdcError) as ei:
+        ctx2.mobility_solve(np.ones(6 * wl_c1.n_bodies))
+    assert ei.value.status == 3
+    ctx3 = ctx_for(lib, wl_c1, lanczos_tol=1e-15, lanczos_max_iter=2)
+    with pytest.raises(lib.GdcError) as ei:
+        ctx3.brownian_slip(np.ones(3 * wl_c1.n_blobs))
+    assert ei.value.status == 3
+    # the context stays usable after an error
+    V, _, info = ctx.mobility_solve(np.ones(6 * wl_c1.n_bodies))
+    assert info["converged"]
