@@ -1,0 +1,316 @@
+#!/usr/bin/env python
+"""Benchmark of the gDC step on GB300: steps/s at 65,520 blobs (FP32-mixed), RPY pair-evals/s.
+
+Workload (seeded, synthetic): 2,520 rigid bodies, a third each 42-blob icosphere shells,
+15-blob rods and 21-blob L-shaped boomerangs, uniform random orientations, 10% volume
+fraction in a 140a cube (65,520 blobs), unbounded overlapping RPY, soft repulsion
+A = 4kT/a, b = 0.1a, dt = 0.005, GMRES tol 1e-6, Lanczos tol 1e-4, RFD delta 1e-3.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank advances its own
+independent suspension of the same size (replicas, weak scaling, no collective on the
+data path); value = total steps of all ranks / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "gDC steps/s at 65k blobs, FP32-mixed vs FP64, residual ≤1e-6; RPY pair-evals/s"
+WORKLOAD = ("c3_65k: 2,520 rigid bodies (840 each of 42-blob icosphere, 15-blob rod, 21-blob boomerang), "
+            "65,520 blobs, 10% volume fraction in a 140a cube, unbounded overlapping RPY, soft repulsion")
+FLOPS_PER_PAIR = 33.0          # algorithmic flops of one far-field RPY pair (FMA = 2), see the design doc
+FP32_LANES_PER_SM = 128
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"sm_max_mhz": 2070.0, "hbm_gbs": 6800.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.gpu = gpu_index
+        self.p = None
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = [s for s, p in zip(sm, power) if p > 0.3 * max(power)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax), "samples": len(sm),
+                "power_w_max": max(power), "reasons": sorted(reasons)}
+
+
+def oracle_sample_step(wl, n_bodies: int, seed: int = 0):
+    """One dense FP64 oracle gDC step on the first n_bodies bodies of the workload (seconds, blobs)."""
+    from oracle import geometry as G, philox
+    from oracle import gdc as ogdc
+    sub = wl.first_bodies(n_bodies)
+    lay = G.Layout(sub.templates, sub.body_tmpl)
+    W = philox.normals(seed, 0, 0, 0, 3 * lay.n_blobs)
+    Wt = philox.normals(seed, 0, 0, 1, 6 * lay.n_bodies)
+    p = ogdc.Params.from_dict(dict(sub.params, rfd_delta=1e-3))
+    t0 = time.perf_counter()
+    ogdc.gdc_step(lay, sub.Y, sub.q, W, Wt, p)
+    return time.perf_counter() - t0, lay.n_blobs
+
+
+def cpu_baseline(wl, budget_s: float = 20.0, n_bodies: int = 48) -> dict:
+    """The dense oracle timed on a bounded sample of the workload, scaled to a full 65k step.
+
+    The oracle's step is dominated by its O(n^3) dense factorisations (three symmetric
+    eigendecompositions and one LU), so the sample's time is scaled by the cube of the
+    blob-count ratio.
+    """
+    times, nbl = [], 0
+    t_start = time.perf_counter()
+    while time.perf_counter() - t_start < budget_s or not times:
+        t, nbl = oracle_sample_step(wl, n_bodies, seed=len(times))
+        times.append(t)
+        if len(times) >= 3:
+            break
+    t_sample = statistics.median(times)
+    scale = (wl.n_blobs / nbl) ** 3
+    t_full = t_sample * scale
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": 1.0 / t_full, "unit": "steps/s", "cores": cores, "kind": "oracle",
+            "sample": (f"dense FP64 oracle gDC step on the first {n_bodies} bodies ({nbl} blobs) of the workload, "
+                       f"median of {len(times)} runs = {t_sample:.3f} s, scaled by ({wl.n_blobs}/{nbl})^3 "
+                       f"for its O(n^3) eigendecompositions and LU"),
+            "sample_seconds": t_sample}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    from synthetic import workloads as WL
+    wl = WL.c3_65k(seed=0)
+    for _ in range(args.warmup):
+        oracle_sample_step(wl, args.ref_bodies)
+    times, nbl = [], 0
+    for k in range(args.steps):
+        t, nbl = oracle_sample_step(wl, args.ref_bodies, seed=k)
+        times.append(t * (wl.n_blobs / nbl) ** 3)
+    total = sum(times)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    value = args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": "fp64 dense oracle (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "steps/s", "cores": cores, "kind": "oracle",
+                             "sample": (f"each step: dense FP64 oracle gDC step on the first {args.ref_bodies} bodies "
+                                        f"({nbl} blobs), scaled by ({wl.n_blobs}/{nbl})^3")},
+            "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=1, help="FP64 steps timed for the comparison (0 = skip)")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--ref-bodies", type=int, default=40)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    world, rank, local = _dist()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import numpy as np
+    import torch
+
+    import paper_2106_00449_gb300 as g
+    from synthetic import workloads as WL
+
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    wl = WL.c3_65k(seed=rank)
+    common = dict(gmres_tol=1e-6, lanczos_tol=1e-4, lanczos_max_iter=128, gmres_restart=50, gmres_max_iter=500,
+                  seed=1000 + rank)
+    ctx = g.context_from_workload(wl, precision=g.FP32_MIXED, rfd_delta=1e-3, **common)
+    stream = ctx.stream
+    infos = []
+    for _ in range(args.warmup):
+        ctx.step(1)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=ctx.device)  # > 129 MB L2
+    sampler = ClockSampler(local)
+    ctx.profile(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.steps):
+        flush.fill_(1)                         # evict L2 between timed steps (outside the events)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        infos.extend(ctx.step(1))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1000.0)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    prof = ctx.profile_read()
+    clocks = sampler.stop()
+    t_local = sum(times)
+    t_max = t_local
+    if dist:
+        t = torch.tensor([t_local], dtype=torch.float64, device=ctx.device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * args.steps / t_max
+    pair_evals = sum(i["pair_evals"] for i in infos)
+    peaks, peak_src = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    n_sm = torch.cuda.get_device_properties(ctx.device).multi_processor_count
+    peak_tf = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    avg_s = prof["rpy32_ms"] / max(prof["rpy32_launches"], 1) / 1000.0
+    achieved_tf = FLOPS_PER_PAIR * prof["pairs_per_product"] / avg_s / 1e12 if avg_s > 0 else None
+    roof = {"bound": "alu", "kernel": "k_rpy32 (FP32 RPY pair kernel)", "achieved": achieved_tf,
+            "peak": peak_tf, "unit": "TFLOP/s", "frac": (achieved_tf / peak_tf) if achieved_tf else None,
+            "traffic": None,
+            "peak_source": (f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flops x {sm_max:.0f} MHz "
+                            f"(sm_max_mhz of MEASURED_PEAKS.json, {peak_src})"),
+            "avg_launch_ms": avg_s * 1000.0, "launches": prof["rpy32_launches"],
+            "flops_per_pair": FLOPS_PER_PAIR, "pairs_per_launch": prof["pairs_per_product"]}
+    if clocks.get("sm_mhz") and achieved_tf:
+        roof["frac_at_sampled_clock"] = achieved_tf / (n_sm * FP32_LANES_PER_SM * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
+    line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 pair kernels, f64 Krylov/state",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_blobs": wl.n_blobs, "n_bodies": wl.n_bodies,
+                       "precision": "fp32-mixed", "dt": wl.params["dt"], "gmres_tol": 1e-6, "lanczos_tol": 1e-4,
+                       "rfd_delta": 1e-3, "l2": "flushed between timed steps (256 MB write outside the events)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "pair_evals_per_s": world * pair_evals / t_max,
+            "residual_max": max(i["solve"]["residual"] for i in infos),
+            "lanczos_iters": [i["lanczos_iters"] for i in infos],
+            "gmres_iters": [i["solve"]["iterations"] for i in infos],
+            "fp64_products_per_step": statistics.mean(i["solve"]["matvecs_fp64"] for i in infos),
+            "nu_range": [min(i["nu_min"] for i in infos), max(i["nu_max"] for i in infos)],
+            "roofline": roof,
+            "gpu_launches": int(prof["launches"]),
+            "clocks": clocks}
+    ctx.profile(False)
+
+    # end to end through the C ABI: host state in, step, host state out
+    hY = torch.empty((wl.n_bodies, 3), dtype=torch.float64).pin_memory()
+    hq = torch.empty((wl.n_bodies, 4), dtype=torch.float64).pin_memory()
+    step0 = ctx.get_state_host_ptr(hY.data_ptr(), hq.data_ptr())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        ctx.set_state_host_ptr(hY.data_ptr(), hq.data_ptr(), step0)
+        ctx.step(1, info=False)
+        step0 = ctx.get_state_host_ptr(hY.data_ptr(), hq.data_ptr())
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    nbytes = 7 * 8 * wl.n_bodies
+    line["e2e"] = {"value": args.e2e_steps / t_e2e, "unit": "steps/s", "h2d_bytes_per_step": nbytes,
+                   "d2h_bytes_per_step": nbytes, "steps": args.e2e_steps}
+
+    # the plain FP64 path on the same workload
+    if args.fp64_steps > 0:
+        del ctx
+        torch.cuda.empty_cache()
+        ctx64 = g.context_from_workload(wl, precision=g.FP64, rfd_delta=1e-6, **common)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(ctx64.stream)
+        inf64 = ctx64.step(args.fp64_steps)
+        e1.record(ctx64.stream)
+        torch.cuda.synchronize()
+        t64 = e0.elapsed_time(e1) / 1000.0
+        line["fp64"] = {"steps_per_s": args.fp64_steps / t64, "steps": args.fp64_steps, "warmup": 0,
+                        "residual_max": max(i["solve"]["residual"] for i in inf64),
+                        "lanczos_iters": [i["lanczos_iters"] for i in inf64],
+                        "gmres_iters": [i["solve"]["iterations"] for i in inf64],
+                        "fp32_mixed_speedup": value / world / (args.fp64_steps / t64)}
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(wl, budget_s=args.cpu_budget, n_bodies=48)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -194,6 +194,23 @@ gdc_status gdc_draw_normals(gdc_ctx* ctx, unsigned long long step, int stream, d
  * vectors of gdc_saddle_apply / gdc_precond_apply (host out, n_susp + 1). */
 gdc_status gdc_saddle_offsets(const gdc_ctx* ctx, long long* off);
 
+/* ---- instrumentation ---------------------------------------------------- */
+
+typedef struct {
+    unsigned long long launches;        /* kernels this context launched since gdc_profile */
+    unsigned long long rpy32_launches;  /* FP32 RPY pair-kernel launches timed            */
+    unsigned long long rpy64_launches;  /* FP64 RPY pair-kernel launches timed            */
+    unsigned long long force_launches;  /* repulsion pair-kernel launches timed           */
+    double rpy32_ms, rpy64_ms, force_ms; /* summed CUDA-event durations of those launches */
+    double pairs_per_product;           /* ordered blob pairs one RPY product evaluates  */
+} gdc_profile_info;
+
+/* Reset the counters; enable != 0 also brackets every pair-kernel launch with
+ * CUDA events recorded on the context's stream (events are created once). */
+gdc_status gdc_profile(gdc_ctx* ctx, int enable);
+/* Synchronise the stream and report the counters (host out). */
+gdc_status gdc_profile_read(gdc_ctx* ctx, gdc_profile_info* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -32,6 +32,7 @@ EXPORTS = [
     "gdc_mobility_solve", "gdc_step", "gdc_set_trace", "gdc_get_state", "gdc_set_state",
     "gdc_blob_positions", "gdc_rpy_apply", "gdc_saddle_apply", "gdc_precond_apply",
     "gdc_brownian_slip", "gdc_lsq_velocity", "gdc_forces", "gdc_draw_normals", "gdc_saddle_offsets",
+    "gdc_profile", "gdc_profile_read",
 ]
 
 
@@ -59,6 +60,13 @@ class _StepInfo(ctypes.Structure):
     _fields_ = [("step", ctypes.c_ulonglong), ("lanczos_iters", ctypes.c_int * 3), ("lanczos_err", ctypes.c_double),
                 ("solve", _SolveInfo), ("nu_min", ctypes.c_double), ("nu_max", ctypes.c_double),
                 ("pair_evals", ctypes.c_double)]
+
+
+class _Profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_ulonglong), ("rpy32_launches", ctypes.c_ulonglong),
+                ("rpy64_launches", ctypes.c_ulonglong), ("force_launches", ctypes.c_ulonglong),
+                ("rpy32_ms", ctypes.c_double), ("rpy64_ms", ctypes.c_double), ("force_ms", ctypes.c_double),
+                ("pairs_per_product", ctypes.c_double)]
 
 
 class _Trace(ctypes.Structure):
@@ -125,6 +133,8 @@ def load_library() -> ctypes.CDLL:
     lib.gdc_forces.argtypes = [vp, dp]
     lib.gdc_draw_normals.argtypes = [vp, ctypes.c_ulonglong, ctypes.c_int, dp]
     lib.gdc_saddle_offsets.argtypes = [vp, llp]
+    lib.gdc_profile.argtypes = [vp, ctypes.c_int]
+    lib.gdc_profile_read.argtypes = [vp, ctypes.POINTER(_Profile)]
     for name in EXPORTS:
         if name not in ("gdc_workspace_bytes", "gdc_destroy", "gdc_last_error"):
             getattr(lib, name).restype = ctypes.c_int
@@ -289,6 +299,15 @@ class Context:
         self._check(self.lib.gdc_set_trace(self._h, ctypes.byref(tr)))
         self._trace_keep = bufs
         return bufs
+
+    # -- instrumentation --
+    def profile(self, enable: bool = True):
+        self._check(self.lib.gdc_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self) -> dict:
+        p = _Profile()
+        self._check(self.lib.gdc_profile_read(self._h, ctypes.byref(p)))
+        return {f[0]: getattr(p, f[0]) for f in _Profile._fields_}
 
     # -- building blocks --
     def blob_positions(self):

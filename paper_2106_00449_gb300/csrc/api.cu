@@ -21,6 +21,35 @@ gdc_status cuda_check(gdc_ctx* c, cudaError_t e, const char* what) {
     return fail(c, GDC_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// ---- pair-kernel timing with CUDA events on the library's stream ----
+
+int prof_begin(gdc_ctx* c, int kind) {
+    if (!c->prof_on) return -1;
+    if (2 * (c->prof_used + 1) > (int)c->prof_ev.size()) prof_flush(c);
+    const int idx = c->prof_used++;
+    c->prof_kind[idx] = kind;
+    cudaEventRecord(c->prof_ev[2 * idx], c->stream);
+    return idx;
+}
+
+void prof_end(gdc_ctx* c, int idx) {
+    if (idx < 0) return;
+    cudaEventRecord(c->prof_ev[2 * idx + 1], c->stream);
+}
+
+void prof_flush(gdc_ctx* c) {
+    if (c->prof_used == 0) return;
+    cudaEventSynchronize(c->prof_ev[2 * (c->prof_used - 1) + 1]);
+    for (int i = 0; i < c->prof_used; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->prof_ev[2 * i], c->prof_ev[2 * i + 1]) == cudaSuccess) {
+            c->prof_ms[c->prof_kind[i]] += ms;
+            c->prof_count[c->prof_kind[i]] += 1;
+        }
+    }
+    c->prof_used = 0;
+}
+
 static const char* validate_params(const gdc_params* p) {
     if (!p) return "params is NULL";
     if (!(p->eta > 0.0) || !std::isfinite(p->eta)) return "eta must be > 0";
@@ -485,7 +514,47 @@ gdc_status gdc_init(gdc_ctx** out, const gdc_params* params, int n_templates, co
     return read_status(c);
 }
 
-void gdc_destroy(gdc_ctx* c) { delete c; }
+void gdc_destroy(gdc_ctx* c) {
+    if (!c) return;
+    for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
+    delete c;
+}
+
+gdc_status gdc_profile(gdc_ctx* c, int enable) {
+    if (!c) return GDC_ERR_INVALID_ARG;
+    gdc_status st = cuda_check(c, cudaStreamSynchronize(c->stream), "profile");
+    if (st != GDC_OK) return st;
+    prof_flush(c);
+    if (enable && c->prof_ev.empty()) {
+        c->prof_ev.resize(2 * 1024);
+        c->prof_kind.resize(1024);
+        for (auto& e : c->prof_ev)
+            if ((st = cuda_check(c, cudaEventCreate(&e), "event create")) != GDC_OK) return st;
+    }
+    c->prof_on = enable ? 1 : 0;
+    c->n_launch = 0;
+    for (int k = 0; k < 3; ++k) {
+        c->prof_ms[k] = 0.0;
+        c->prof_count[k] = 0;
+    }
+    return GDC_OK;
+}
+
+gdc_status gdc_profile_read(gdc_ctx* c, gdc_profile_info* out) {
+    if (!c || !out) return c ? fail(c, GDC_ERR_INVALID_ARG, "NULL output") : GDC_ERR_INVALID_ARG;
+    gdc_status st = cuda_check(c, cudaStreamSynchronize(c->stream), "profile read");
+    if (st != GDC_OK) return st;
+    prof_flush(c);
+    out->launches = c->n_launch;
+    out->rpy32_launches = c->prof_count[0];
+    out->rpy64_launches = c->prof_count[1];
+    out->force_launches = c->prof_count[2];
+    out->rpy32_ms = c->prof_ms[0];
+    out->rpy64_ms = c->prof_ms[1];
+    out->force_ms = c->prof_ms[2];
+    out->pairs_per_product = c->pair_evals_per_matvec;
+    return GDC_OK;
+}
 
 const char* gdc_last_error(const gdc_ctx* c) { return c ? c->err.c_str() : "NULL context"; }
 

@@ -54,7 +54,7 @@ __global__ void k_body_KT(int NB, const long long* __restrict__ body_blob_off, c
 }
 
 void launch_body_KT(gdc_ctx* c, const double* x, int x_gm, double* y, int y_gm, double scale) {
-    k_body_KT<<<ceil_div(32LL * c->NB, 256), 256, 0, c->stream>>>(c->NB, c->body_blob_off, c->blob_gm, c->body_gm, x,
+    ++c->n_launch, k_body_KT<<<ceil_div(32LL * c->NB, 256), 256, 0, c->stream>>>(c->NB, c->body_blob_off, c->blob_gm, c->body_gm, x,
                                                                   x_gm, y, y_gm, scale, c->r, c->Yc);
 }
 
@@ -111,7 +111,7 @@ __global__ void k_lsq(int NB, const long long* __restrict__ body_blob_off, const
 }
 
 void launch_lsq(gdc_ctx* c, const double* vbrev, double* calV) {
-    k_lsq<<<ceil_div(32LL * c->NB, 256), 256, 0, c->stream>>>(c->NB, c->body_blob_off, c->body_tmpl, c->tmpl_KtKp,
+    ++c->n_launch, k_lsq<<<ceil_div(32LL * c->NB, 256), 256, 0, c->stream>>>(c->NB, c->body_blob_off, c->body_tmpl, c->tmpl_KtKp,
                                                               vbrev, c->r, c->Yc, c->Rb, calV);
 }
 
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(128) k_precond(const long long* __restrict__ b
 
 void launch_precond(gdc_ctx* c, const double* r, double* z) {
     const size_t smem = (size_t)(2 * 3 * c->max_body_blobs + 32) * sizeof(double);
-    k_precond<<<c->NB, 128, smem, c->stream>>>(c->body_blob_off, c->body_tmpl, c->tmpl_n, c->tmpl_off, c->minv_off,
+    ++c->n_launch, k_precond<<<c->NB, 128, smem, c->stream>>>(c->body_blob_off, c->body_tmpl, c->tmpl_n, c->tmpl_off, c->minv_off,
                                                c->tmpl_Minv, c->tmpl_G, c->tmpl_N, c->tmpl_xyz, c->blob_gm,
                                                c->body_gm, c->Rb, r, z);
 }
@@ -413,7 +413,7 @@ __global__ void k_template_setup(const int* __restrict__ tmpl_n, const int* __re
 }
 
 void launch_template_setup(gdc_ctx* c) {
-    k_template_setup<<<c->T, 256, 0, c->stream>>>(c->tmpl_n, c->tmpl_off, c->minv_off, c->tmpl_xyz, c->p.a, c->p.eta,
+    ++c->n_launch, k_template_setup<<<c->T, 256, 0, c->stream>>>(c->tmpl_n, c->tmpl_off, c->minv_off, c->tmpl_xyz, c->p.a, c->p.eta,
                                                   c->tmpl_Minv, c->tmpl_G, c->tmpl_N, c->tmpl_KtKp, c->tmpl_work,
                                                   c->dev_status);
 }

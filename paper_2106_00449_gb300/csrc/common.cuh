@@ -137,6 +137,15 @@ struct gdc_ctx {
 
     // status of device-side loops
     int* dev_status = 0;
+
+    // instrumentation: kernel launches issued, and CUDA-event timing of the pair kernels
+    unsigned long long n_launch = 0;
+    int prof_on = 0;
+    std::vector<cudaEvent_t> prof_ev;      // start/stop pairs
+    std::vector<int> prof_kind;            // 0 = FP32 RPY, 1 = FP64 RPY, 2 = forces
+    int prof_used = 0;
+    double prof_ms[3] = {0, 0, 0};
+    unsigned long long prof_count[3] = {0, 0, 0};
 };
 
 namespace gdc {
@@ -189,6 +198,9 @@ inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 // ---- host-side helpers (defined in api.cu) --------------------------------
 gdc_status fail(gdc_ctx* c, gdc_status s, const std::string& msg);
 gdc_status cuda_check(gdc_ctx* c, cudaError_t e, const char* what);
+int prof_begin(gdc_ctx* c, int kind);     // records a start event when timing is on (-1 otherwise)
+void prof_end(gdc_ctx* c, int idx);
+void prof_flush(gdc_ctx* c);
 
 // ---- kernels launched across translation units ----------------------------
 // geometry.cu

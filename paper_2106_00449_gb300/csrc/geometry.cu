@@ -47,8 +47,8 @@ __global__ void k_blob_pos(int NBL, const int* __restrict__ blob_body, const int
 }
 
 void load_config(gdc_ctx* c, const double* Y, const double* q) {
-    k_body_rot<<<ceil_div(c->NB, 128), 128, 0, c->stream>>>(c->NB, Y, q, c->Rb, c->Yc);
-    k_blob_pos<<<ceil_div(c->NBL, 128), 128, 0, c->stream>>>(
+    ++c->n_launch, k_body_rot<<<ceil_div(c->NB, 128), 128, 0, c->stream>>>(c->NB, Y, q, c->Rb, c->Yc);
+    ++c->n_launch, k_blob_pos<<<ceil_div(c->NBL, 128), 128, 0, c->stream>>>(
         c->NBL, c->blob_body, c->blob_susp, c->body_tmpl, c->body_blob_off, c->tmpl_off, c->tmpl_xyz,
         Y, c->Rb, c->ref, c->r, c->spos, c->spos64);
 }
@@ -95,11 +95,11 @@ __global__ void k_normals(long long total, int per, const int* __restrict__ owne
 void launch_normals(gdc_ctx* c, unsigned long long step, int stream, double* out) {
     if (stream == 0) {
         long long total = 3LL * c->NBL;
-        k_normals<<<ceil_div(total, 256), 256, 0, c->stream>>>(total, 3, c->blob_susp, c->susp_blob_off,
+        ++c->n_launch, k_normals<<<ceil_div(total, 256), 256, 0, c->stream>>>(total, 3, c->blob_susp, c->susp_blob_off,
                                                                c->p.seed, step, 0u, out);
     } else {
         long long total = 6LL * c->NB;
-        k_normals<<<ceil_div(total, 256), 256, 0, c->stream>>>(total, 6, c->body_susp, c->susp_body_off,
+        ++c->n_launch, k_normals<<<ceil_div(total, 256), 256, 0, c->stream>>>(total, 6, c->body_susp, c->susp_body_off,
                                                                c->p.seed, step, 1u, out);
     }
 }
@@ -122,7 +122,7 @@ __global__ void k_perturb(int NB, const double* __restrict__ Y, const double* __
 
 void launch_perturb(gdc_ctx* c, const double* Y, const double* q, const double* Wt, double delta,
                     double* Yo, double* qo) {
-    k_perturb<<<ceil_div(c->NB, 128), 128, 0, c->stream>>>(c->NB, Y, q, Wt, c->body_L, delta, Yo, qo);
+    ++c->n_launch, k_perturb<<<ceil_div(c->NB, 128), 128, 0, c->stream>>>(c->NB, Y, q, Wt, c->body_L, delta, Yo, qo);
 }
 
 // FD state of Eq. (15): coordinate `coord` of the body with local index p_local of every suspension.
@@ -147,7 +147,7 @@ __global__ void k_perturb_one(int NB, const double* __restrict__ Y, const double
 
 void launch_perturb_one(gdc_ctx* c, const double* Y, const double* q, int p_local, int coord,
                         double delta, double* Yo, double* qo) {
-    k_perturb_one<<<ceil_div(c->NB, 128), 128, 0, c->stream>>>(c->NB, Y, q, c->body_susp, c->susp_body_off,
+    ++c->n_launch, k_perturb_one<<<ceil_div(c->NB, 128), 128, 0, c->stream>>>(c->NB, Y, q, c->body_susp, c->susp_body_off,
                                                                c->body_L, p_local, coord, delta, Yo, qo);
 }
 
@@ -170,7 +170,7 @@ __global__ void k_advance(int NB, const double* __restrict__ Y, const double* __
 
 void launch_advance(gdc_ctx* c, const double* Y, const double* q, const double* V, double h,
                     const double* nu, double* Yo, double* qo) {
-    k_advance<<<ceil_div(c->NB, 128), 128, 0, c->stream>>>(c->NB, Y, q, V, h, nu, c->body_susp, Yo, qo);
+    ++c->n_launch, k_advance<<<ceil_div(c->NB, 128), 128, 0, c->stream>>>(c->NB, Y, q, V, h, nu, c->body_susp, Yo, qo);
 }
 
 // One block per suspension; fixed-order block reduction (deterministic).
@@ -198,7 +198,7 @@ __global__ void k_rfd_div(const long long* __restrict__ susp_body_off, const dou
 
 void launch_rfd_div(gdc_ctx* c, const double* Wt, const double* calV, const double* calVt,
                     double delta, double dt, double* nu) {
-    k_rfd_div<<<c->S, 256, 0, c->stream>>>(c->susp_body_off, Wt, calV, calVt, c->body_L, delta, dt, nu);
+    ++c->n_launch, k_rfd_div<<<c->S, 256, 0, c->stream>>>(c->susp_body_off, Wt, calV, calVt, c->body_L, delta, dt, nu);
 }
 
 __global__ void k_fd_accum(int S, const long long* __restrict__ susp_body_off, const double* __restrict__ calV,
@@ -217,7 +217,7 @@ __global__ void k_fd_accum(int S, const long long* __restrict__ susp_body_off, c
 
 void launch_fd_accum(gdc_ctx* c, const double* calV, const double* calVp, int p_local, int coord,
                      double delta, double* div, int first) {
-    k_fd_accum<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(c->S, c->susp_body_off, calV, calVp, c->body_L,
+    ++c->n_launch, k_fd_accum<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(c->S, c->susp_body_off, calV, calVp, c->body_L,
                                                            p_local, coord, delta, div, first);
 }
 
@@ -227,7 +227,7 @@ __global__ void k_nu(int S, const double* __restrict__ div, double dt, double* _
 }
 
 void launch_nu_from_div(gdc_ctx* c, const double* div, double dt, double* nu) {
-    k_nu<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(c->S, div, dt, nu);
+    ++c->n_launch, k_nu<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(c->S, div, dt, nu);
 }
 
 // ---- right-hand side and solution layout -----------------------------------------
@@ -254,8 +254,8 @@ __global__ void k_rhs_body(int NB, const int* __restrict__ body_gm, const double
 }
 
 void launch_rhs(gdc_ctx* c, const double* vbrev, const double* FT, double* b) {
-    k_rhs_blob<<<ceil_div(c->NBL, 128), 128, 0, c->stream>>>(c->NBL, c->blob_gm, vbrev, c->r, c->p.shear_rate, b);
-    k_rhs_body<<<ceil_div(c->NB, 128), 128, 0, c->stream>>>(c->NB, c->body_gm, FT, b);
+    ++c->n_launch, k_rhs_blob<<<ceil_div(c->NBL, 128), 128, 0, c->stream>>>(c->NBL, c->blob_gm, vbrev, c->r, c->p.shear_rate, b);
+    ++c->n_launch, k_rhs_body<<<ceil_div(c->NB, 128), 128, 0, c->stream>>>(c->NB, c->body_gm, FT, b);
 }
 
 __global__ void k_scatter_V(int NB, const int* __restrict__ body_gm, const double* __restrict__ x,
@@ -273,8 +273,8 @@ __global__ void k_scatter_lam(int NBL, const int* __restrict__ blob_gm, const do
 }
 
 void launch_scatter_solution(gdc_ctx* c, const double* x, double* V, double* lambda) {
-    if (V) k_scatter_V<<<ceil_div(c->NB, 128), 128, 0, c->stream>>>(c->NB, c->body_gm, x, V);
-    if (lambda) k_scatter_lam<<<ceil_div(c->NBL, 128), 128, 0, c->stream>>>(c->NBL, c->blob_gm, x, lambda);
+    if (V) ++c->n_launch, k_scatter_V<<<ceil_div(c->NB, 128), 128, 0, c->stream>>>(c->NB, c->body_gm, x, V);
+    if (lambda) ++c->n_launch, k_scatter_lam<<<ceil_div(c->NBL, 128), 128, 0, c->stream>>>(c->NBL, c->blob_gm, x, lambda);
 }
 
 }  // namespace gdc
@@ -310,7 +310,7 @@ __global__ void k_ref(const long long* __restrict__ susp_body_off, const double*
 }
 
 void launch_ref(gdc_ctx* c, const double* Y) {
-    k_ref<<<c->S, 256, 0, c->stream>>>(c->susp_body_off, Y, c->ref);
+    ++c->n_launch, k_ref<<<c->S, 256, 0, c->stream>>>(c->susp_body_off, Y, c->ref);
 }
 
 }  // namespace gdc

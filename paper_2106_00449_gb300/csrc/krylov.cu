@@ -142,8 +142,8 @@ __global__ void k_sub_chunks(const Chunk* __restrict__ chunks, const double* __r
 // per-segment inner products <V_i, w>, i < k  -> out[s * cols + i]
 static void seg_mdot(gdc_ctx* c, const gdc::Seg& sg, const double* V, long long ld, int k, const double* w,
                      double* out, int cols) {
-    k_mdot<<<sg.n_chunks, RED_THREADS, 0, c->stream>>>(sg.chunks, V, ld, k, w, c->red_part, c->red_cols);
-    k_seg_sum<<<c->S, 128, 0, c->stream>>>(c->S, sg.seg_chunk_off, c->red_part, c->red_cols, k, out);
+    ++c->n_launch, k_mdot<<<sg.n_chunks, RED_THREADS, 0, c->stream>>>(sg.chunks, V, ld, k, w, c->red_part, c->red_cols);
+    ++c->n_launch, k_seg_sum<<<c->S, 128, 0, c->stream>>>(c->S, sg.seg_chunk_off, c->red_part, c->red_cols, k, out);
     (void)cols;
 }
 
@@ -282,7 +282,7 @@ gdc_status gmres_solve(gdc_ctx* c, const double* b, double* x, gdc_solve_info* i
     seg_mdot(c, sg, b, 0, 1, b, c->gm_h, cols);
     double* bn2 = c->gm_h;
     // bnorm = sqrt(bn2): reuse k_seg_scale-free path via a tiny kernel
-    k_sqrt_col0<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(c->S, bn2, cols, c->gm_bnorm);
+    ++c->n_launch, k_sqrt_col0<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(c->S, bn2, cols, c->gm_bnorm);
     cudaMemsetAsync(x, 0, sizeof(double) * n, c->stream);
     cudaMemcpyAsync(c->gm_r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream);
     int total = 0;
@@ -292,7 +292,7 @@ gdc_status gmres_solve(gdc_ctx* c, const double* b, double* x, gdc_solve_info* i
     for (int cycle = 0;; ++cycle) {
         // beta = ||r|| and the FP64 residual check
         seg_mdot(c, sg, c->gm_r, 0, 1, c->gm_r, c->gm_h2, cols);
-        k_gm_start<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(c->S, c->gm_h2, c->gm_bnorm, tol, cols, c->gm_res,
+        ++c->n_launch, k_gm_start<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(c->S, c->gm_h2, c->gm_bnorm, tol, cols, c->gm_res,
                                                                c->gm_active, c->gm_g, c->gm_scal, m + 1, c->gm_j,
                                                                c->gm_active + c->S);
         if ((st = sync_read(c, c->gm_active + c->S, outer.data(), sizeof(int) * c->S)) != GDC_OK) return st;
@@ -318,7 +318,7 @@ gdc_status gmres_solve(gdc_ctx* c, const double* b, double* x, gdc_solve_info* i
             st = fail(c, GDC_ERR_NOT_CONVERGED, "mobility solve: GMRES reached gmres_max_iter");
             break;
         }
-        k_seg_scale<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->gm_r, c->gm_scal, c->gm_V);
+        ++c->n_launch, k_seg_scale<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->gm_r, c->gm_scal, c->gm_V);
         int j = 0;
         for (; j < m; ++j) {
             double* Vj = c->gm_V + (long long)j * n;
@@ -327,17 +327,17 @@ gdc_status gmres_solve(gdc_ctx* c, const double* b, double* x, gdc_solve_info* i
             if (prec == GDC_FP32_MIXED) inf.matvecs_fp32++; else inf.matvecs_fp64++;
             // classical Gram-Schmidt, twice
             seg_mdot(c, sg, c->gm_V, n, j + 1, c->gm_w, c->gm_h, cols);
-            k_mupdate<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->gm_V, n, j + 1, c->gm_h, cols, c->gm_w);
+            ++c->n_launch, k_mupdate<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->gm_V, n, j + 1, c->gm_h, cols, c->gm_w);
             seg_mdot(c, sg, c->gm_V, n, j + 1, c->gm_w, c->gm_h2, cols);
-            k_mupdate<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->gm_V, n, j + 1, c->gm_h2, cols, c->gm_w);
-            k_add_cols<<<c->S, 128, 0, c->stream>>>(j + 1, c->gm_h, c->gm_h2, cols);
+            ++c->n_launch, k_mupdate<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->gm_V, n, j + 1, c->gm_h2, cols, c->gm_w);
+            ++c->n_launch, k_add_cols<<<c->S, 128, 0, c->stream>>>(j + 1, c->gm_h, c->gm_h2, cols);
             // ||w||: the column of wn2 lives after the h coefficients
             seg_mdot(c, sg, c->gm_w, 0, 1, c->gm_w, c->gm_h2, cols);
-            k_gm_arnoldi<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(c->S, j, m, c->gm_h, cols, c->gm_h2, c->gm_H,
+            ++c->n_launch, k_gm_arnoldi<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(c->S, j, m, c->gm_h, cols, c->gm_h2, c->gm_H,
                                                                      c->gm_cs, c->gm_sn, c->gm_g, c->gm_bnorm,
                                                                      inner_tol, c->gm_res + c->S, c->gm_active,
                                                                      c->gm_j, c->gm_scal);
-            k_seg_scale<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->gm_w, c->gm_scal, c->gm_V + (long long)(j + 1) * n);
+            ++c->n_launch, k_seg_scale<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->gm_w, c->gm_scal, c->gm_V + (long long)(j + 1) * n);
             ++total;
             if ((st = sync_read(c, c->gm_active, act.data(), sizeof(int) * c->S)) != GDC_OK) return st;
             bool still = false;
@@ -349,14 +349,14 @@ gdc_status gmres_solve(gdc_ctx* c, const double* b, double* x, gdc_solve_info* i
         }
         inf.iterations = std::max(inf.iterations, total);
         // x += P^-1 V y
-        k_gm_backsolve<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(c->S, m, c->gm_H, c->gm_g, c->gm_j, c->gm_y, cols);
-        k_combine<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->gm_V, n, c->gm_j, c->gm_y, cols, nullptr, c->gm_w);
+        ++c->n_launch, k_gm_backsolve<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(c->S, m, c->gm_H, c->gm_g, c->gm_j, c->gm_y, cols);
+        ++c->n_launch, k_combine<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->gm_V, n, c->gm_j, c->gm_y, cols, nullptr, c->gm_w);
         launch_precond(c, c->gm_w, c->gm_z);
-        k_axpy_chunks<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, 1.0, c->gm_z, x);
+        ++c->n_launch, k_axpy_chunks<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, 1.0, c->gm_z, x);
         // FP64 residual r = b - A x
         saddle_op(c, GDC_FP64, x, c->gm_w);
         inf.matvecs_fp64++;
-        k_sub_chunks<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, b, c->gm_w, c->gm_r);
+        ++c->n_launch, k_sub_chunks<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, b, c->gm_w, c->gm_r);
         if ((st = cuda_check(c, cudaGetLastError(), "GMRES launch")) != GDC_OK) return st;
     }
     inf.iterations = total;
@@ -516,27 +516,27 @@ gdc_status lanczos_sqrt(gdc_ctx* c, const double* W, double* out, double scale, 
     const int kmax = c->kmax;
     gdc_status st = GDC_OK;
     seg_mdot(c, sg, W, 0, 1, W, c->lz_h, cols);
-    k_lz_start<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(c->S, c->lz_h, cols, c->lz_Wnorm, c->lz_scal, c->lz_active,
+    ++c->n_launch, k_lz_start<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(c->S, c->lz_h, cols, c->lz_Wnorm, c->lz_scal, c->lz_active,
                                                            c->lz_k, c->lz_err);
-    k_seg_scale<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, W, c->lz_scal, c->lz_V);
+    ++c->n_launch, k_seg_scale<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, W, c->lz_scal, c->lz_V);
     std::vector<int> act(c->S);
     int j = 0;
     for (; j < kmax; ++j) {
         const double* Vj = c->lz_V + (long long)j * n;
         rpy_op(c, prec, Vj, c->lz_w);
         seg_mdot(c, sg, c->lz_V, n, j + 1, c->lz_w, c->lz_h, cols);
-        k_mupdate<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_V, n, j + 1, c->lz_h, cols, c->lz_w);
+        ++c->n_launch, k_mupdate<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_V, n, j + 1, c->lz_h, cols, c->lz_w);
         seg_mdot(c, sg, c->lz_V, n, j + 1, c->lz_w, c->gm_h2, cols);
-        k_mupdate<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_V, n, j + 1, c->gm_h2, cols, c->lz_w);
-        k_add_cols<<<c->S, 128, 0, c->stream>>>(j + 1, c->lz_h, c->gm_h2, cols);
+        ++c->n_launch, k_mupdate<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_V, n, j + 1, c->gm_h2, cols, c->lz_w);
+        ++c->n_launch, k_add_cols<<<c->S, 128, 0, c->stream>>>(j + 1, c->lz_h, c->gm_h2, cols);
         seg_mdot(c, sg, c->lz_w, 0, 1, c->lz_w, c->gm_h2, cols);
         const int k = j + 1;
         const size_t smem = (size_t)(k * k + 4 * k) * sizeof(double);
-        k_lz_tridiag<<<c->S, 128, smem, c->stream>>>(c->S, j, c->lz_h, cols, c->gm_h2, c->lz_alpha, c->lz_beta,
+        ++c->n_launch, k_lz_tridiag<<<c->S, 128, smem, c->stream>>>(c->S, j, c->lz_h, cols, c->gm_h2, c->lz_alpha, c->lz_beta,
                                                      c->lz_Wnorm, c->lz_c, c->lz_err, c->lz_active, c->lz_k,
                                                      c->lz_scal, c->p.lanczos_tol, fixed_mode ? c->lz_fix : nullptr,
                                                      kmax, c->dev_status);
-        k_seg_scale<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_w, c->lz_scal, c->lz_V + (long long)(j + 1) * n);
+        ++c->n_launch, k_seg_scale<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_w, c->lz_scal, c->lz_V + (long long)(j + 1) * n);
         if ((st = sync_read(c, c->lz_active, act.data(), sizeof(int) * c->S)) != GDC_OK) return st;
         bool still = false;
         for (int s = 0; s < c->S; ++s) still = still || act[s];
@@ -546,8 +546,8 @@ gdc_status lanczos_sqrt(gdc_ctx* c, const double* W, double* out, double scale, 
         }
     }
     // out = scale * V c
-    k_fill<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(c->S, scale, c->lz_scal);
-    k_combine<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_V, n, c->lz_k, c->lz_c, kmax, c->lz_scal, out);
+    ++c->n_launch, k_fill<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(c->S, scale, c->lz_scal);
+    ++c->n_launch, k_combine<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_V, n, c->lz_k, c->lz_c, kmax, c->lz_scal, out);
     std::vector<int> ks(c->S);
     std::vector<double> errs(c->S);
     if ((st = sync_read(c, c->lz_k, ks.data(), sizeof(int) * c->S)) != GDC_OK) return st;

@@ -38,9 +38,9 @@ __global__ void k_pack_lam64(int NBL, const int* __restrict__ map, const double*
 void launch_pack_lambda(gdc_ctx* c, int prec, const double* x, int gm_layout) {
     const int* map = gm_layout ? c->blob_gm : nullptr;
     if (prec == GDC_FP32_MIXED)
-        k_pack_lam32<<<ceil_div(c->NBL, 256), 256, 0, c->stream>>>(c->NBL, map, x, c->slam);
+        ++c->n_launch, k_pack_lam32<<<ceil_div(c->NBL, 256), 256, 0, c->stream>>>(c->NBL, map, x, c->slam);
     else
-        k_pack_lam64<<<ceil_div(c->NBL, 256), 256, 0, c->stream>>>(c->NBL, map, x, c->slam64);
+        ++c->n_launch, k_pack_lam64<<<ceil_div(c->NBL, 256), 256, 0, c->stream>>>(c->NBL, map, x, c->slam64);
 }
 
 // ---- FP32 RPY pair kernel -----------------------------------------------------
@@ -199,30 +199,32 @@ __global__ void __launch_bounds__(128) k_rpy64(const MvItem* __restrict__ items,
 }
 
 void launch_rpy(gdc_ctx* c, int prec) {
+    const int pe = prof_begin(c, prec == GDC_FP32_MIXED ? 0 : 1);
     if (prec == GDC_FP32_MIXED) {
         const double a = c->p.a;
         RpyConst32 k{(float)(2.0 * a * a / 3.0), (float)(2.0 * a * a), (float)(4.0 * a * a),
                      (float)(4.0 / (3.0 * a)), (float)(9.0 / (32.0 * a)), (float)(1.0 / (8.0 * a * a))};
         if (c->mv_tpt == 1)
-            k_rpy32<1><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off, c->spos, c->slam,
+            ++c->n_launch, k_rpy32<1><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off, c->spos, c->slam,
                                                              (float4*)c->mv_part, c->NBL, k);
         else if (c->mv_tpt == 4)
-            k_rpy32<4><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off, c->spos, c->slam,
+            ++c->n_launch, k_rpy32<4><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off, c->spos, c->slam,
                                                              (float4*)c->mv_part, c->NBL, k);
         else
-            k_rpy32<2><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off, c->spos, c->slam,
+            ++c->n_launch, k_rpy32<2><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off, c->spos, c->slam,
                                                              (float4*)c->mv_part, c->NBL, k);
     } else {
         if (c->mv_tpt == 1)
-            k_rpy64<1><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off, c->spos64, c->slam64,
+            ++c->n_launch, k_rpy64<1><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off, c->spos64, c->slam64,
                                                              (double4*)c->mv_part, c->NBL, c->p.a);
         else if (c->mv_tpt == 4)
-            k_rpy64<4><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off, c->spos64, c->slam64,
+            ++c->n_launch, k_rpy64<4><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off, c->spos64, c->slam64,
                                                              (double4*)c->mv_part, c->NBL, c->p.a);
         else
-            k_rpy64<2><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off, c->spos64, c->slam64,
+            ++c->n_launch, k_rpy64<2><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off, c->spos64, c->slam64,
                                                              (double4*)c->mv_part, c->NBL, c->p.a);
     }
+    prof_end(c, pe);
 }
 
 // ---- epilogue: chunk sums in FP64, scale, and the -K V part of the saddle operator ----
@@ -276,11 +278,11 @@ __global__ void k_rpy_epilogue(int NBL, const P* __restrict__ part, const int* _
 
 static void launch_epilogue(gdc_ctx* c, int prec, double c0, const double* x, double* y, int gm_layout) {
     if (prec == GDC_FP32_MIXED)
-        k_rpy_epilogue<float4><<<ceil_div(c->NBL, 256), 256, 0, c->stream>>>(
+        ++c->n_launch, k_rpy_epilogue<float4><<<ceil_div(c->NBL, 256), 256, 0, c->stream>>>(
             c->NBL, (const float4*)c->mv_part, c->blob_susp, c->mv_nk, c0, x, y, gm_layout, c->blob_gm, c->body_gm,
             c->blob_body, c->r, c->Yc);
     else
-        k_rpy_epilogue<double4><<<ceil_div(c->NBL, 256), 256, 0, c->stream>>>(
+        ++c->n_launch, k_rpy_epilogue<double4><<<ceil_div(c->NBL, 256), 256, 0, c->stream>>>(
             c->NBL, (const double4*)c->mv_part, c->blob_susp, c->mv_nk, c0, x, y, gm_layout, c->blob_gm, c->body_gm,
             c->blob_body, c->r, c->Yc);
 }
@@ -394,22 +396,24 @@ __global__ void __launch_bounds__(128) k_forces64(const MvItem* __restrict__ ite
 #define GDC_FORCES_LAUNCH(TPT)                                                                         \
     do {                                                                                               \
         if (prec == GDC_FP32_MIXED)                                                                    \
-            k_forces32<TPT><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off, c->spos, \
+            ++c->n_launch, k_forces32<TPT><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off, c->spos, \
                 (float4*)c->mv_part, c->NBL, (float)A, (float)b, (float)two_a, (float)(rc * rc));           \
         else                                                                                           \
-            k_forces64<TPT><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off,          \
+            ++c->n_launch, k_forces64<TPT><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off,          \
                 c->spos64, (double4*)c->mv_part, c->NBL, A, b, two_a, rc * rc);                            \
     } while (0)
 
 void launch_forces_pair(gdc_ctx* c, int prec, double* fblob) {
     const double A = c->p.rep_A, b = c->p.rep_b, two_a = 2.0 * c->p.a;
     const double rc = two_a + 36.0 * b;
+    const int pe = prof_begin(c, 2);
     if (c->mv_tpt == 1)
         GDC_FORCES_LAUNCH(1);
     else if (c->mv_tpt == 4)
         GDC_FORCES_LAUNCH(4);
     else
         GDC_FORCES_LAUNCH(2);
+    prof_end(c, pe);
     launch_epilogue(c, prec, 1.0, nullptr, fblob, 0);
 }
 

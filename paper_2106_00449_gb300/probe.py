@@ -1,0 +1,69 @@
+"""Run single building blocks of the library on a synthetic workload, for timing and profiling.
+
+    python -m paper_2106_00449_gb300.probe --op rpy32 --workload c3_65k --reps 5
+
+Ops: rpy32 / rpy64 (one RPY product in FP32 / FP64), saddle32, precond, forces32,
+lanczos32 (one M^(1/2) W), solve32 (one FP32-mixed mobility solve), step32 (one gDC step).
+Prints the mean wall time per call measured with CUDA events on the library's stream.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main(argv=None) -> int:
+    import numpy as np
+    import torch
+
+    import paper_2106_00449_gb300 as g
+    from synthetic import workloads as WL
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--op", default="rpy32")
+    ap.add_argument("--workload", default="c3_65k")
+    ap.add_argument("--bodies", type=int, default=0, help="use only the first N bodies (0 = all)")
+    ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--tpt", type=int, default=0, help="unused placeholder for tile-shape experiments")
+    args = ap.parse_args(argv)
+    wl = WL.BY_NAME[args.workload]()
+    if args.bodies:
+        wl = wl.first_bodies(args.bodies)
+    ctx = g.context_from_workload(wl, precision=g.FP32_MIXED, rfd_delta=1e-3, lanczos_max_iter=128)
+    rng = np.random.default_rng(0)
+    lam = torch.as_tensor(rng.standard_normal(3 * wl.n_blobs), device=ctx.device)
+    x = torch.as_tensor(rng.standard_normal(int(ctx.saddle_off[-1])), device=ctx.device)
+    ops = {
+        "rpy32": lambda: ctx.rpy_apply(lam, g.FP32_MIXED),
+        "rpy64": lambda: ctx.rpy_apply(lam, g.FP64),
+        "saddle32": lambda: ctx.saddle_apply(x, g.FP32_MIXED),
+        "precond": lambda: ctx.precond_apply(x),
+        "forces32": lambda: ctx.forces(),
+        "lanczos32": lambda: ctx.brownian_slip(lam),
+        "solve32": lambda: ctx.mobility_solve(torch.zeros(6 * wl.n_bodies, dtype=torch.float64, device=ctx.device), lam),
+        "step32": lambda: ctx.step(1),
+    }
+    fn = ops[args.op]
+    fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(ctx.stream)
+    for _ in range(args.reps):
+        fn()
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.reps
+    print(json.dumps({"op": args.op, "workload": wl.name, "n_blobs": wl.n_blobs, "ms_per_call": ms,
+                      "pairs": wl.pair_evals_per_matvec()}))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
