@@ -246,6 +246,8 @@ def main(argv=None) -> int:
             "peak_source": (f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flops x {sm_max:.0f} MHz "
                             f"(sm_max_mhz of MEASURED_PEAKS.json, {peak_src})"),
             "avg_launch_ms": avg_s * 1000.0, "launches": prof["rpy32_launches"],
+            "tiling": {"targets_per_thread": prof["targets_per_thread"], "work_waves": prof["work_waves"],
+                       "autotuned": prof["autotune_ms"] > 0},
             "flops_per_pair": FLOPS_PER_PAIR, "pairs_per_launch": prof["pairs_per_product"]}
     if clocks.get("sm_mhz") and achieved_tf:
         roof["frac_at_sampled_clock"] = achieved_tf / (n_sm * FP32_LANES_PER_SM * 2 * clocks["sm_mhz"] * 1e6 / 1e12)

@@ -79,6 +79,8 @@ typedef struct {
     double rep_b;          /* soft repulsion range b (Eq. 20)                          */
     double shear_rate;     /* background flow u = (shear_rate * y, 0, 0); 0 = off      */
     unsigned long long seed; /* Philox4x32-10 key of the W and W-tilde draws            */
+    int    autotune;       /* 1: gdc_init times the FP32 pair kernel's candidate tilings
+                              at the initial configuration and keeps the fastest        */
 } gdc_params;
 
 typedef struct {
@@ -203,6 +205,9 @@ typedef struct {
     unsigned long long force_launches;  /* repulsion pair-kernel launches timed           */
     double rpy32_ms, rpy64_ms, force_ms; /* summed CUDA-event durations of those launches */
     double pairs_per_product;           /* ordered blob pairs one RPY product evaluates  */
+    int    targets_per_thread;          /* pair-kernel tiling in use                     */
+    double work_waves;                  /* work items per launch / (4 x SM count)        */
+    double autotune_ms;                 /* fastest FP32 product found at init (0: none)  */
 } gdc_profile_info;
 
 /* Reset the counters; enable != 0 also brackets every pair-kernel launch with

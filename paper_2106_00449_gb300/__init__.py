@@ -48,7 +48,7 @@ class _Params(ctypes.Structure):
                 ("lanczos_tol", ctypes.c_double), ("lanczos_max_iter", ctypes.c_int), ("rfd_delta", ctypes.c_double),
                 ("precision", ctypes.c_int), ("divmode", ctypes.c_int), ("scheme", ctypes.c_int),
                 ("rep_A", ctypes.c_double), ("rep_b", ctypes.c_double), ("shear_rate", ctypes.c_double),
-                ("seed", ctypes.c_ulonglong)]
+                ("seed", ctypes.c_ulonglong), ("autotune", ctypes.c_int)]
 
 
 class _SolveInfo(ctypes.Structure):
@@ -66,7 +66,8 @@ class _Profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_ulonglong), ("rpy32_launches", ctypes.c_ulonglong),
                 ("rpy64_launches", ctypes.c_ulonglong), ("force_launches", ctypes.c_ulonglong),
                 ("rpy32_ms", ctypes.c_double), ("rpy64_ms", ctypes.c_double), ("force_ms", ctypes.c_double),
-                ("pairs_per_product", ctypes.c_double)]
+                ("pairs_per_product", ctypes.c_double), ("targets_per_thread", ctypes.c_int),
+                ("work_waves", ctypes.c_double), ("autotune_ms", ctypes.c_double)]
 
 
 class _Trace(ctypes.Structure):
@@ -92,6 +93,7 @@ class Params:
     rep_b: float = 0.1
     shear_rate: float = 0.0
     seed: int = 0
+    autotune: int = 1
 
     def _c(self) -> _Params:
         return _Params(**{f.name: getattr(self, f.name) for f in dataclasses.fields(self)})

@@ -130,7 +130,7 @@ static const char* build_host_layout(gdc_ctx* c, const gdc_params* p, int n_temp
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
     c->device = dev;
     c->num_sms = sms;
-    build_mv_items(c);
+    plan_mv_capacity(c);
     setup_segments(c);
     return nullptr;
 }
@@ -225,7 +225,9 @@ static size_t carve(gdc_ctx* c, void* base) {
     c->lz_alpha = w.take<double>(S * k);
     c->lz_beta = w.take<double>(S * k);
     c->lz_c = w.take<double>(S * k);
-    c->lz_cprev = w.take<double>(S * k);
+    c->lz_rot_cap = (int)(3 * k * k + 64);
+    c->lz_rot = (void*)w.take<double>(3LL * S * c->lz_rot_cap);   // 24-byte records
+    c->lz_lastk = w.take<int>(S);
     c->lz_h = w.take<double>(S * cols);
     c->lz_Wnorm = w.take<double>(S);
     c->lz_err = w.take<double>(S);
@@ -239,9 +241,9 @@ static size_t carve(gdc_ctx* c, void* base) {
     c->seg_lz.chunks = w.take<Chunk>(c->seg_lz.n_chunks);
     c->seg_lz.seg_chunk_off = w.take<int>(S + 1);
     c->red_part = w.take<double>((long long)std::max(c->seg_gm.n_chunks, c->seg_lz.n_chunks) * cols);
-    c->mv_items = w.take<MvItem>(c->mv_n_items);
+    c->mv_items = w.take<MvItem>(c->mv_cap_items);
     c->mv_nk = w.take<int>(S);
-    c->mv_part = (void*)w.take<double4>((long long)c->mv_kmax * NBL);
+    c->mv_part = (void*)w.take<double4>((long long)c->mv_cap_kmax * NBL);
     c->dev_status = w.take<int>(4);
     return w.off + 256;
 }
@@ -511,7 +513,12 @@ gdc_status gdc_init(gdc_ctx** out, const gdc_params* params, int n_templates, co
     krylov_init_attributes();
     launch_template_setup(c);
     if ((st = cuda_check(c, cudaGetLastError(), "template setup")) != GDC_OK) return st;
-    return read_status(c);
+    if ((st = read_status(c)) != GDC_OK) return st;
+    if (c->p.autotune) {
+        load_at(c, c->Y, c->q);
+        if ((st = autotune_pair_kernel(c)) != GDC_OK) return st;
+    }
+    return GDC_OK;
 }
 
 void gdc_destroy(gdc_ctx* c) {
@@ -553,6 +560,9 @@ gdc_status gdc_profile_read(gdc_ctx* c, gdc_profile_info* out) {
     out->rpy64_ms = c->prof_ms[1];
     out->force_ms = c->prof_ms[2];
     out->pairs_per_product = c->pair_evals_per_matvec;
+    out->targets_per_thread = c->mv_tpt;
+    out->work_waves = c->mv_waves;
+    out->autotune_ms = c->autotune_ms;
     return GDC_OK;
 }
 

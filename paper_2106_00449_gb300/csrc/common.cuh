@@ -109,9 +109,12 @@ struct gdc_ctx {
 
     // Lanczos (blob layout)
     int kmax = 0;
-    double *lz_V = 0, *lz_w = 0, *lz_alpha = 0, *lz_beta = 0, *lz_c = 0, *lz_cprev = 0;
+    double *lz_V = 0, *lz_w = 0, *lz_alpha = 0, *lz_beta = 0, *lz_c = 0;
     double *lz_h = 0, *lz_Wnorm = 0, *lz_err = 0, *lz_scal = 0;
-    int *lz_active = 0, *lz_k = 0, *lz_fix = 0;
+    int *lz_active = 0, *lz_k = 0, *lz_fix = 0, *lz_lastk = 0;
+    void* lz_rot = 0;             // per suspension: Givens rotations of the tridiagonal QR (24 B each)
+    int lz_rot_cap = 0;           // rotations stored per suspension: 3 kmax^2 + 64
+    int lz_hint = 0;              // iterations the previous unconstrained Lanczos run needed
 
     // reductions
     gdc::Seg seg_gm, seg_lz, seg_body;
@@ -121,6 +124,9 @@ struct gdc_ctx {
     // pair-kernel work lists
     gdc::MvItem* mv_items = 0;
     int mv_n_items = 0, mv_tpt = 2, mv_threads = 128, mv_kmax = 1;
+    double mv_waves = 8.0;
+    int mv_cap_items = 0, mv_cap_kmax = 1;   // workspace capacity over all autotune candidates
+    double autotune_ms = 0.0;                 // best FP32 product time found at init (0 = not tuned)
     int* mv_nk = 0;               // chunks per suspension
     std::vector<gdc::MvItem> h_mv_items;
     std::vector<int> h_mv_nk;
@@ -226,7 +232,9 @@ void launch_pack_lambda(gdc_ctx* c, int prec, const double* x, int gm_layout);
 void launch_rpy(gdc_ctx* c, int prec);
 void launch_rpy_epilogue(gdc_ctx* c, int prec, const double* x, double* y, int gm_layout);
 void launch_forces_pair(gdc_ctx* c, int prec, double* fblob);
-void build_mv_items(gdc_ctx* c);
+void build_mv_items(gdc_ctx* c, int tpt, double waves);
+gdc_status autotune_pair_kernel(gdc_ctx* c);
+void plan_mv_capacity(gdc_ctx* c);
 
 // body.cu
 void launch_body_KT(gdc_ctx* c, const double* x, int x_gm, double* y, int y_gm, double scale);

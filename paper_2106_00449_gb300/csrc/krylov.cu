@@ -276,7 +276,8 @@ gdc_status gmres_solve(gdc_ctx* c, const double* b, double* x, gdc_solve_info* i
     const gdc::Seg& sg = c->seg_gm;
     const int cols = c->red_cols;
     const double tol = c->p.gmres_tol;
-    const double inner_tol = prec == GDC_FP32_MIXED ? 0.5 * tol : tol;
+    // the FP32 cycle aims below tol so that one FP64 residual usually confirms it
+    const double inner_tol = prec == GDC_FP32_MIXED ? 0.1 * tol : tol;
     gdc_solve_info inf{};
     // ||b|| per suspension
     seg_mdot(c, sg, b, 0, 1, b, c->gm_h, cols);
@@ -379,133 +380,152 @@ __global__ void k_lz_start(int S, const double* __restrict__ wn2, int cols, doub
     err[s] = 0.0;
 }
 
-// One block per suspension: T_k (k = j+1) from alpha/beta, its eigendecomposition by
-// implicit symmetric QR steps with Wilkinson shifts (Golub & Van Loan, Sec. 8.3), and
-// c = ||W|| T^(1/2) e_1.  Convergence: ||c_k - [c_{k-1}; 0]|| / ||c_k|| < tol.
-__global__ void k_lz_tridiag(int S, int j, const double* __restrict__ h, int cols, const double* __restrict__ wn2,
-                             double* __restrict__ alpha, double* __restrict__ betav, const double* __restrict__ Wnorm,
-                             double* __restrict__ cvec, double* __restrict__ err, int* __restrict__ active,
-                             int* __restrict__ kcount, double* __restrict__ scal, double tol,
-                             const int* __restrict__ fixed, int kmax, int* __restrict__ status) {
+// Lanczos bookkeeping and, where needed, c = ||W|| T_k^(1/2) e_1 for one suspension
+// (one block per suspension; the eigen-work is sequential and runs on thread 0).
+//
+// T_k = Q diag(theta) Q^T is diagonalised by implicit symmetric QR steps with
+// Wilkinson shifts (Golub & Van Loan, Sec. 8.3).  Q is never formed: the rotations
+// R_1 .. R_N are applied to u = e_1 as they are made (u = Q^T e_1), stored, and
+// replayed transposed in reverse order on g = sqrt(theta) * u, which gives Q g.
+// That is O(k^2) work instead of the O(k^3) of accumulating Q.
+//
+// Convergence: ||c_k - c_{k-1}|| / ||c_k|| < tol, evaluated from iteration kstart on
+// (the previous run's count sets kstart, so early iterations skip the eigen-work);
+// in fixed mode c is formed once, at k = fixed[s].
+struct LzRot {
+    double c, s;
+    int q, pad;
+};
+
+__global__ void __launch_bounds__(32) k_lz_tridiag(int S, int j, const double* __restrict__ h, int cols,
+                                                   const double* __restrict__ wn2, double* __restrict__ alpha,
+                                                   double* __restrict__ betav, const double* __restrict__ Wnorm,
+                                                   double* __restrict__ cvec, double* __restrict__ err,
+                                                   int* __restrict__ active, int* __restrict__ kcount,
+                                                   int* __restrict__ lastk, double* __restrict__ scal, double tol,
+                                                   const int* __restrict__ fixed, int kstart, int kmax,
+                                                   LzRot* __restrict__ rot_all, int rot_cap, int* __restrict__ status) {
     const int s = blockIdx.x;
+    if (threadIdx.x != 0) return;
     if (!active[s]) {
-        if (threadIdx.x == 0) scal[s] = 0.0;
+        scal[s] = 0.0;
         return;
     }
-    extern __shared__ double smem[];
     const int k = j + 1;
-    double* Q = smem;                 // k x k, row r owned by thread r
-    double* d = Q + k * k;
-    double* e = d + k;
-    double* rc = e + k;               // rotation cosines of one sweep
-    double* rs = rc + k;
-    __shared__ int lo_s, hi_s, done_s;
     const double beta = sqrt(fmax(wn2[(long long)s * cols], 0.0));
-    if (threadIdx.x == 0) {
-        alpha[(long long)s * kmax + j] = h[(long long)s * cols + j];
-        betav[(long long)s * kmax + j] = beta;
-        for (int i = 0; i < k; ++i) d[i] = alpha[(long long)s * kmax + i];
-        for (int i = 0; i + 1 < k; ++i) e[i] = betav[(long long)s * kmax + i];
-        done_s = 0;
+    double* al = alpha + (long long)s * kmax;
+    double* be = betav + (long long)s * kmax;
+    al[j] = h[(long long)s * cols + j];
+    be[j] = beta;
+    scal[s] = beta > 0.0 ? 1.0 / beta : 0.0;
+    kcount[s] = k;
+    const bool fixed_mode = fixed != nullptr && fixed[s] > 0;
+    bool compute;
+    if (fixed_mode)
+        compute = k >= fixed[s] || k >= kmax || beta == 0.0;
+    else
+        compute = k >= kstart || k >= kmax || beta == 0.0;
+    if (!compute) return;
+
+    double d[GDC_MAX_LANCZOS], e[GDC_MAX_LANCZOS], u[GDC_MAX_LANCZOS];
+    for (int i = 0; i < k; ++i) {
+        d[i] = al[i];
+        e[i] = i + 1 < k ? be[i] : 0.0;
+        u[i] = i == 0 ? 1.0 : 0.0;
     }
-    for (int r = threadIdx.x; r < k; r += blockDim.x)
-        for (int q = 0; q < k; ++q) Q[r * k + q] = (r == q) ? 1.0 : 0.0;
-    __syncthreads();
-    int hi_loc = k - 1;
-    for (int sweep = 0; sweep < 60 * k + 60; ++sweep) {
-        if (threadIdx.x == 0) {
-            int hi = hi_loc;
-            while (hi > 0 && fabs(e[hi - 1]) <= 1e-16 * (fabs(d[hi - 1]) + fabs(d[hi]))) {
-                e[hi - 1] = 0.0;
-                --hi;
-            }
-            hi_loc = hi;
-            if (hi == 0) {
-                done_s = 1;
-            } else {
-                int lo = hi - 1;
-                while (lo > 0 && fabs(e[lo - 1]) > 1e-16 * (fabs(d[lo - 1]) + fabs(d[lo]))) --lo;
-                const double da = d[hi - 1], dc = d[hi], bb = e[hi - 1];
-                const double del = 0.5 * (da - dc);
-                const double sg = del >= 0.0 ? 1.0 : -1.0;
-                const double mu = dc - bb * bb / (del + sg * hypot(del, bb));
-                double xx = d[lo] - mu, zz = e[lo];
-                for (int q = lo; q < hi; ++q) {
-                    const double rr = hypot(xx, zz);
-                    const double cq = rr > 0.0 ? xx / rr : 1.0, sq = rr > 0.0 ? zz / rr : 0.0;
-                    if (q > lo) e[q - 1] = rr;
-                    const double a0 = d[q], b0 = d[q + 1], f0 = e[q];
-                    d[q] = cq * cq * a0 + 2.0 * cq * sq * f0 + sq * sq * b0;
-                    d[q + 1] = sq * sq * a0 - 2.0 * cq * sq * f0 + cq * cq * b0;
-                    e[q] = cq * sq * (b0 - a0) + (cq * cq - sq * sq) * f0;
-                    if (q + 1 < hi) {
-                        const double bulge = sq * e[q + 1];
-                        e[q + 1] = cq * e[q + 1];
-                        xx = e[q];
-                        zz = bulge;
-                    }
-                    rc[q] = cq;
-                    rs[q] = sq;
-                }
-                lo_s = lo;
-                hi_s = hi;
-            }
+    LzRot* rot = rot_all + (long long)s * rot_cap;
+    int nrot = 0;
+    bool ok = true;
+    int hi = k - 1;
+    for (int sweep = 0; hi > 0; ++sweep) {
+        if (sweep > 40 * k + 40) {
+            ok = false;
+            break;
         }
-        __syncthreads();
-        if (done_s) break;
-        const int lo = lo_s, hi = hi_s;
-        for (int r = threadIdx.x; r < k; r += blockDim.x) {
-            for (int q = lo; q < hi; ++q) {
-                const double a0 = Q[r * k + q], b0 = Q[r * k + q + 1];
-                Q[r * k + q] = rc[q] * a0 + rs[q] * b0;
-                Q[r * k + q + 1] = -rs[q] * a0 + rc[q] * b0;
-            }
+        if (fabs(e[hi - 1]) <= 1e-16 * (fabs(d[hi - 1]) + fabs(d[hi]))) {
+            e[hi - 1] = 0.0;
+            --hi;
+            continue;
         }
-        __syncthreads();
+        int lo = hi - 1;
+        while (lo > 0 && fabs(e[lo - 1]) > 1e-16 * (fabs(d[lo - 1]) + fabs(d[lo]))) --lo;
+        const double del = 0.5 * (d[hi - 1] - d[hi]);
+        const double bb = e[hi - 1];
+        const double sg = del >= 0.0 ? 1.0 : -1.0;
+        const double mu = d[hi] - bb * bb / (del + sg * sqrt(del * del + bb * bb));
+        double xx = d[lo] - mu, zz = e[lo];
+        for (int q = lo; q < hi; ++q) {
+            const double rr = sqrt(xx * xx + zz * zz);
+            double cq = 1.0, sq = 0.0;
+            if (rr > 0.0) {
+                const double ri = 1.0 / rr;
+                cq = xx * ri;
+                sq = zz * ri;
+            }
+            if (q > lo) e[q - 1] = rr;
+            const double a0 = d[q], b0 = d[q + 1], f0 = e[q];
+            const double cc = cq * cq, ss = sq * sq, cs = cq * sq;
+            d[q] = cc * a0 + 2.0 * cs * f0 + ss * b0;
+            d[q + 1] = ss * a0 - 2.0 * cs * f0 + cc * b0;
+            e[q] = cs * (b0 - a0) + (cc - ss) * f0;
+            if (q + 1 < hi) {
+                const double bulge = sq * e[q + 1];
+                e[q + 1] = cq * e[q + 1];
+                xx = e[q];
+                zz = bulge;
+            }
+            const double u0 = u[q], u1 = u[q + 1];
+            u[q] = cq * u0 + sq * u1;
+            u[q + 1] = -sq * u0 + cq * u1;
+            if (nrot < rot_cap) rot[nrot] = LzRot{cq, sq, q, 0};
+            ++nrot;
+        }
     }
-    if (threadIdx.x == 0 && !done_s) atomicExch(status, 2);
-    // c_r = ||W|| sum_q Q[r][q] sqrt(theta_q) Q[0][q]
+    if (nrot > rot_cap) ok = false;
+    if (!ok) {
+        atomicExch(status, 2);
+        active[s] = 0;
+        err[s] = 1.0;
+        return;
+    }
+    // g = sqrt(theta) * u, then Q g by the transposed rotations in reverse order
+    for (int i = 0; i < k; ++i) u[i] *= sqrt(fmax(d[i], 0.0));
+    for (int t = nrot - 1; t >= 0; --t) {
+        const LzRot R = rot[t];
+        const double g0 = u[R.q], g1 = u[R.q + 1];
+        u[R.q] = R.c * g0 - R.s * g1;
+        u[R.q + 1] = R.s * g0 + R.c * g1;
+    }
     const double wn = Wnorm[s];
     double* cs_ = cvec + (long long)s * kmax;
-    __shared__ double num_s, den_s;
-    if (threadIdx.x == 0) {
-        num_s = 0.0;
-        den_s = 0.0;
+    const bool have_prev = lastk[s] == k - 1;
+    double num = 0.0, den = 0.0;
+    for (int r = 0; r < k; ++r) {
+        const double cn = wn * u[r];
+        const double old = (have_prev && r < k - 1) ? cs_[r] : 0.0;
+        num += (cn - old) * (cn - old);
+        den += cn * cn;
+        cs_[r] = cn;
     }
-    __syncthreads();
-    double* cnew = rc;  // reuse
-    for (int r = threadIdx.x; r < k; r += blockDim.x) {
-        double acc = 0.0;
-        for (int q = 0; q < k; ++q) acc += Q[r * k + q] * sqrt(fmax(d[q], 0.0)) * Q[q];
-        cnew[r] = wn * acc;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double num = 0.0, den = 0.0;
-        for (int r = 0; r < k; ++r) {
-            const double old = r < k - 1 ? cs_[r] : 0.0;
-            num += (cnew[r] - old) * (cnew[r] - old);
-            den += cnew[r] * cnew[r];
-        }
-        for (int r = 0; r < k; ++r) cs_[r] = cnew[r];
-        const double ee = den > 0.0 ? sqrt(num / den) : 0.0;
-        err[s] = ee;
-        kcount[s] = k;
-        scal[s] = beta > 0.0 ? 1.0 / beta : 0.0;
-        bool stop;
-        if (fixed && fixed[s] > 0)
-            stop = k >= fixed[s];
-        else
-            stop = (k >= 2 && ee < tol) || beta == 0.0;
-        if (k >= kmax) stop = true;
-        if (stop) active[s] = 0;
-    }
+    lastk[s] = k;
+    const double ee = den > 0.0 ? sqrt(num / den) : 0.0;
+    bool stop;
+    if (fixed_mode)
+        stop = true;
+    else
+        stop = (have_prev && ee < tol) || beta == 0.0;
+    err[s] = have_prev ? ee : 1.0;
+    if (beta == 0.0) err[s] = 0.0;
+    if (k >= kmax) stop = true;
+    if (stop) active[s] = 0;
 }
 
-void krylov_init_attributes() {
-    cudaFuncSetAttribute(k_lz_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (GDC_MAX_LANCZOS * GDC_MAX_LANCZOS + 4 * GDC_MAX_LANCZOS) * (int)sizeof(double));
+__global__ void k_lz_reset(int S, int* __restrict__ lastk) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < S) lastk[s] = -1;
 }
+
+void krylov_init_attributes() {}
 
 gdc_status lanczos_sqrt(gdc_ctx* c, const double* W, double* out, double scale, int fixed_mode,
                         int* iters_out, double* err_out) {
@@ -515,39 +535,40 @@ gdc_status lanczos_sqrt(gdc_ctx* c, const double* W, double* out, double scale, 
     const int cols = c->red_cols;
     const int kmax = c->kmax;
     gdc_status st = GDC_OK;
+    // convergence checks start a little before the previous run's count
+    int kstart = 2;
+    if (!fixed_mode && c->lz_hint > 0) kstart = std::max(2, c->lz_hint - std::max(4, c->lz_hint / 8));
     seg_mdot(c, sg, W, 0, 1, W, c->lz_h, cols);
-    ++c->n_launch, k_lz_start<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(c->S, c->lz_h, cols, c->lz_Wnorm, c->lz_scal, c->lz_active,
-                                                           c->lz_k, c->lz_err);
+    ++c->n_launch, k_lz_start<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(c->S, c->lz_h, cols, c->lz_Wnorm, c->lz_scal,
+                                                                          c->lz_active, c->lz_k, c->lz_err);
+    ++c->n_launch, k_lz_reset<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(c->S, c->lz_lastk);
     ++c->n_launch, k_seg_scale<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, W, c->lz_scal, c->lz_V);
     std::vector<int> act(c->S);
-    int j = 0;
-    for (; j < kmax; ++j) {
+    for (int j = 0; j < kmax; ++j) {
         const double* Vj = c->lz_V + (long long)j * n;
         rpy_op(c, prec, Vj, c->lz_w);
+        // w = M v_j orthogonalised against v_0..v_j twice (full reorthogonalisation)
         seg_mdot(c, sg, c->lz_V, n, j + 1, c->lz_w, c->lz_h, cols);
         ++c->n_launch, k_mupdate<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_V, n, j + 1, c->lz_h, cols, c->lz_w);
         seg_mdot(c, sg, c->lz_V, n, j + 1, c->lz_w, c->gm_h2, cols);
         ++c->n_launch, k_mupdate<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_V, n, j + 1, c->gm_h2, cols, c->lz_w);
         ++c->n_launch, k_add_cols<<<c->S, 128, 0, c->stream>>>(j + 1, c->lz_h, c->gm_h2, cols);
         seg_mdot(c, sg, c->lz_w, 0, 1, c->lz_w, c->gm_h2, cols);
-        const int k = j + 1;
-        const size_t smem = (size_t)(k * k + 4 * k) * sizeof(double);
-        ++c->n_launch, k_lz_tridiag<<<c->S, 128, smem, c->stream>>>(c->S, j, c->lz_h, cols, c->gm_h2, c->lz_alpha, c->lz_beta,
-                                                     c->lz_Wnorm, c->lz_c, c->lz_err, c->lz_active, c->lz_k,
-                                                     c->lz_scal, c->p.lanczos_tol, fixed_mode ? c->lz_fix : nullptr,
-                                                     kmax, c->dev_status);
-        ++c->n_launch, k_seg_scale<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_w, c->lz_scal, c->lz_V + (long long)(j + 1) * n);
+        ++c->n_launch, k_lz_tridiag<<<c->S, 32, 0, c->stream>>>(
+            c->S, j, c->lz_h, cols, c->gm_h2, c->lz_alpha, c->lz_beta, c->lz_Wnorm, c->lz_c, c->lz_err, c->lz_active,
+            c->lz_k, c->lz_lastk, c->lz_scal, c->p.lanczos_tol, fixed_mode ? c->lz_fix : nullptr, kstart, kmax,
+            (LzRot*)c->lz_rot, c->lz_rot_cap, c->dev_status);
+        ++c->n_launch, k_seg_scale<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_w, c->lz_scal,
+                                                                       c->lz_V + (long long)(j + 1) * n);
         if ((st = sync_read(c, c->lz_active, act.data(), sizeof(int) * c->S)) != GDC_OK) return st;
         bool still = false;
         for (int s = 0; s < c->S; ++s) still = still || act[s];
-        if (!still) {
-            ++j;
-            break;
-        }
+        if (!still) break;
     }
     // out = scale * V c
     ++c->n_launch, k_fill<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(c->S, scale, c->lz_scal);
-    ++c->n_launch, k_combine<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_V, n, c->lz_k, c->lz_c, kmax, c->lz_scal, out);
+    ++c->n_launch, k_combine<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_V, n, c->lz_k, c->lz_c, kmax,
+                                                                 c->lz_scal, out);
     std::vector<int> ks(c->S);
     std::vector<double> errs(c->S);
     if ((st = sync_read(c, c->lz_k, ks.data(), sizeof(int) * c->S)) != GDC_OK) return st;
@@ -558,6 +579,7 @@ gdc_status lanczos_sqrt(gdc_ctx* c, const double* W, double* out, double scale, 
         kk = std::max(kk, ks[s]);
         ee = std::max(ee, errs[s]);
     }
+    if (!fixed_mode) c->lz_hint = kk;
     if (iters_out) *iters_out = kk;
     if (err_out) *err_out = ee;
     if (!fixed_mode && ee > c->p.lanczos_tol && kk >= kmax)

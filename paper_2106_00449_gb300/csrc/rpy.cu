@@ -54,6 +54,35 @@ struct RpyConst32 {
     float cB;      // 1/(8a^2)
 };
 
+// Exact pair term (all branches) for the rare tiles that hold a near pair.
+__device__ __forceinline__ void rpy_pair_exact(const RpyConst32& k, float dx, float dy, float dz, const float4& ls,
+                                               float& ox, float& oy, float& oz) {
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    float A, B;
+    if (r2 >= k.four_a2) {
+        const float ri = rsqrtf(r2);
+        const float ri2 = ri * ri, ri3 = ri2 * ri;
+        A = fmaf(k.c23, ri3, ri);
+        B = ri3 * fmaf(-k.c2, ri2, 1.f);
+    } else if (r2 > 0.f) {
+        const float ri = rsqrtf(r2);
+        A = k.cA * fmaf(-k.c9, r2 * ri, 1.f);
+        B = ri * k.cB;
+    } else {
+        A = k.cA;
+        B = 0.f;
+    }
+    const float s = B * fmaf(dx, ls.x, fmaf(dy, ls.y, dz * ls.z));
+    ox = fmaf(A, ls.x, fmaf(s, dx, ox));
+    oy = fmaf(A, ls.y, fmaf(s, dy, oy));
+    oz = fmaf(A, ls.z, fmaf(s, dz, oz));
+}
+
+// Each source tile is first evaluated with the far-field formula only (no branch), while
+// the smallest r^2 of the tile is tracked per target.  A target whose tile held a pair
+// closer than 2a (its own blob included) recomputes that tile with rpy_pair_exact; the
+// far-field values (infinite or NaN for r = 0) are discarded.  Near tiles are the few
+// that hold the target's own body or a touching body.
 template <int TPT>
 __global__ void __launch_bounds__(128) k_rpy32(const MvItem* __restrict__ items, const long long* __restrict__ susp_blob_off,
                                                const float4* __restrict__ spos, const float4* __restrict__ slam,
@@ -84,9 +113,12 @@ __global__ void __launch_bounds__(128) k_rpy32(const MvItem* __restrict__ items,
             sl[e] = slam[b0 + j0 + e];
         }
         __syncthreads();
-        float tx[TPT], ty[TPT], tz[TPT];
+        float tx[TPT], ty[TPT], tz[TPT], mn[TPT];
 #pragma unroll
-        for (int t = 0; t < TPT; ++t) tx[t] = ty[t] = tz[t] = 0.f;
+        for (int t = 0; t < TPT; ++t) {
+            tx[t] = ty[t] = tz[t] = 0.f;
+            mn[t] = 3.0e38f;
+        }
 #pragma unroll 4
         for (int j = 0; j < n; ++j) {
             const float4 ps = sp[j];
@@ -98,19 +130,26 @@ __global__ void __launch_bounds__(128) k_rpy32(const MvItem* __restrict__ items,
                 const float ri = rsqrtf(r2);
                 const float ri2 = ri * ri;
                 const float ri3 = ri2 * ri;
-                float A = fmaf(k.c23, ri3, ri);
-                float B = ri3 * fmaf(-k.c2, ri2, 1.f);
-                if (r2 < k.four_a2) {
-                    const bool pos = r2 > 0.f;
-                    const float r = pos ? r2 * ri : 0.f;
-                    A = k.cA * fmaf(-k.c9, r, 1.f);
-                    B = pos ? ri * k.cB : 0.f;
-                }
-                const float dl = fmaf(dx, ls.x, fmaf(dy, ls.y, dz * ls.z));
-                const float s = B * dl;
+                const float A = fmaf(k.c23, ri3, ri);
+                const float B = ri3 * fmaf(-k.c2, ri2, 1.f);
+                const float s = B * fmaf(dx, ls.x, fmaf(dy, ls.y, dz * ls.z));
                 tx[t] = fmaf(A, ls.x, fmaf(s, dx, tx[t]));
                 ty[t] = fmaf(A, ls.y, fmaf(s, dy, ty[t]));
                 tz[t] = fmaf(A, ls.z, fmaf(s, dz, tz[t]));
+                mn[t] = fminf(mn[t], r2);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < TPT; ++t) {
+            if (mn[t] < k.four_a2) {
+                float ox = 0.f, oy = 0.f, oz = 0.f;
+                for (int j = 0; j < n; ++j) {
+                    const float4 ps = sp[j];
+                    rpy_pair_exact(k, ps.x - xt[t], ps.y - yt[t], ps.z - zt[t], sl[j], ox, oy, oz);
+                }
+                tx[t] = ox;
+                ty[t] = oy;
+                tz[t] = oz;
             }
         }
         // compensated (Kahan) addition of the tile sums
@@ -419,8 +458,10 @@ void launch_forces_pair(gdc_ctx* c, int prec, double* fblob) {
 
 // ---- work list ------------------------------------------------------------------------
 
-void build_mv_items(gdc_ctx* c) {
-    const int tile_targets = 128 * c->mv_tpt;
+void build_mv_items(gdc_ctx* c, int tpt, double waves) {
+    c->mv_tpt = tpt;
+    c->mv_waves = waves;
+    const int tile_targets = 128 * tpt;
     double P = 0.0;
     std::vector<long long> ns(c->S);
     for (int s = 0; s < c->S; ++s) {
@@ -428,7 +469,7 @@ void build_mv_items(gdc_ctx* c) {
         P += (double)ns[s] * (double)ns[s];
     }
     c->pair_evals_per_matvec = P;
-    const double target_items = (double)c->num_sms * 4.0 * 8.0;  // ~8 waves of 4 blocks per SM
+    const double target_items = (double)c->num_sms * 4.0 * waves;  // `waves` launches of 4 blocks per SM
     c->h_mv_items.clear();
     c->h_mv_nk.assign(c->S, 1);
     int kmax = 1;
@@ -462,6 +503,73 @@ void build_mv_items(gdc_ctx* c) {
     });
     c->mv_n_items = (int)c->h_mv_items.size();
     c->mv_kmax = kmax;
+}
+
+}  // namespace gdc
+
+namespace gdc {
+
+// Candidate tilings of the pair kernels: targets per thread x work items per launch.
+static const int kTpt[3] = {1, 2, 4};
+static const double kWaves[3] = {4.0, 8.0, 16.0};
+
+void plan_mv_capacity(gdc_ctx* c) {
+    int cap_items = 0, cap_k = 1;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            build_mv_items(c, kTpt[a], kWaves[b]);
+            cap_items = std::max(cap_items, c->mv_n_items);
+            cap_k = std::max(cap_k, c->mv_kmax);
+        }
+    c->mv_cap_items = cap_items;
+    c->mv_cap_kmax = cap_k;
+    build_mv_items(c, 2, 8.0);
+}
+
+static gdc_status upload_items(gdc_ctx* c) {
+    cudaError_t e = cudaMemcpyAsync(c->mv_items, c->h_mv_items.data(), sizeof(MvItem) * c->h_mv_items.size(),
+                                    cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->mv_nk, c->h_mv_nk.data(), sizeof(int) * c->S, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return cuda_check(c, e, "work-list upload");
+}
+
+// Times three launches of the FP32 RPY kernel per candidate at the loaded configuration
+// (lambda = the current W buffer) and keeps the fastest tiling.
+gdc_status autotune_pair_kernel(gdc_ctx* c) {
+    cudaEvent_t e0, e1;
+    gdc_status st = cuda_check(c, cudaEventCreate(&e0), "event");
+    if (st != GDC_OK) return st;
+    if ((st = cuda_check(c, cudaEventCreate(&e1), "event")) != GDC_OK) return st;
+    launch_normals(c, 0, 0, c->W);
+    launch_pack_lambda(c, GDC_FP32_MIXED, c->W, 0);
+    float best = 1e30f;
+    int bt = 2;
+    double bw = 8.0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            build_mv_items(c, kTpt[a], kWaves[b]);
+            if ((st = upload_items(c)) != GDC_OK) break;
+            launch_rpy(c, GDC_FP32_MIXED);  // warm-up
+            cudaEventRecord(e0, c->stream);
+            for (int r = 0; r < 3; ++r) launch_rpy(c, GDC_FP32_MIXED);
+            cudaEventRecord(e1, c->stream);
+            if ((st = cuda_check(c, cudaEventSynchronize(e1), "autotune")) != GDC_OK) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                bt = kTpt[a];
+                bw = kWaves[b];
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != GDC_OK) return st;
+    build_mv_items(c, bt, bw);
+    c->autotune_ms = best / 3.0;
+    return upload_items(c);
 }
 
 }  // namespace gdc
