@@ -22,10 +22,15 @@ def nvcc() -> str:
     return exe
 
 
+# the pair kernels flush FP32 denormals (their operands are never denormal), which lets
+# rsqrtf map to the bare reciprocal-square-root unit operation
+PER_FILE = {"rpy.cu": ["-ftz=true"]}
+
+
 def _compile(src: str, extra) -> str:
     obj = os.path.join(BUILD, src.replace(".cu", ".o"))
     cmd = [nvcc(), "-c", os.path.join(CSRC, src), "-o", obj, "-O3", "-lineinfo", "-std=c++17",
-           "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", *ARCH, *extra]
+           "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", *ARCH, *PER_FILE.get(src, []), *extra]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")

@@ -222,6 +222,57 @@ __global__ void __launch_bounds__(128) k_precond(const long long* __restrict__ b
     }
 }
 
+// ---- intra-body block of the RPY product in FP64 ---------------------------------------
+//
+// y_p += M_pp lambda_p with M_pp = R M_t R^T (M_t: the template's RPY block, FP64, built at
+// init).  The FP32 pair kernel leaves out same-body pairs, so the large near-field terms of
+// each body are added here exactly.  One block per body; x and y use the saddle layout
+// (gm = 1) or 3 doubles per blob (gm = 0).
+__global__ void __launch_bounds__(128) k_intra_body(const long long* __restrict__ body_blob_off, const int* __restrict__ body_tmpl,
+                                                    const int* __restrict__ tmpl_n, const long long* __restrict__ minv_off,
+                                                    const double* __restrict__ Mt, const int* __restrict__ blob_gm,
+                                                    const double* __restrict__ Rb, const double* __restrict__ x,
+                                                    double* __restrict__ y, int gm) {
+    extern __shared__ double sh[];
+    const int p = blockIdx.x;
+    const int t = body_tmpl[p];
+    const int n3 = 3 * tmpl_n[t];
+    double* rho = sh;
+    const double* R = Rb + 9 * p;
+    const long long i0 = body_blob_off[p];
+    for (int b = threadIdx.x; b < n3 / 3; b += blockDim.x) {
+        const long long o = gm ? (long long)blob_gm[i0 + b] : 3 * (i0 + b);
+        double v[3] = {x[o], x[o + 1], x[o + 2]}, w[3];
+        rotT(R, v, w);
+        rho[3 * b] = w[0];
+        rho[3 * b + 1] = w[1];
+        rho[3 * b + 2] = w[2];
+    }
+    __syncthreads();
+    const double* M = Mt + minv_off[t];
+    double* av = sh + n3;
+    for (int row = threadIdx.x; row < n3; row += blockDim.x) {
+        double acc = 0.0;
+        for (int q = 0; q < n3; ++q) acc = fma(M[(long long)q * n3 + row], rho[q], acc);  // symmetric
+        av[row] = acc;
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < n3 / 3; b += blockDim.x) {
+        double w[3];
+        rot(R, av + 3 * b, w);
+        const long long o = gm ? (long long)blob_gm[i0 + b] : 3 * (i0 + b);
+        y[o] += w[0];
+        y[o + 1] += w[1];
+        y[o + 2] += w[2];
+    }
+}
+
+void launch_intra_body(gdc_ctx* c, const double* x, double* y, int gm) {
+    const size_t smem = (size_t)(2 * 3 * c->max_body_blobs) * sizeof(double);
+    ++c->n_launch, k_intra_body<<<c->NB, 128, smem, c->stream>>>(c->body_blob_off, c->body_tmpl, c->tmpl_n, c->minv_off,
+                                                                 c->tmpl_M, c->blob_gm, c->Rb, x, y, gm);
+}
+
 void launch_precond(gdc_ctx* c, const double* r, double* z) {
     const size_t smem = (size_t)(2 * 3 * c->max_body_blobs + 32) * sizeof(double);
     ++c->n_launch, k_precond<<<c->NB, 128, smem, c->stream>>>(c->body_blob_off, c->body_tmpl, c->tmpl_n, c->tmpl_off, c->minv_off,
@@ -290,7 +341,7 @@ __global__ void k_template_setup(const int* __restrict__ tmpl_n, const int* __re
                                  const long long* __restrict__ minv_off, const double* __restrict__ xyz,
                                  double a, double eta, double* __restrict__ Minv, double* __restrict__ Gt,
                                  double* __restrict__ Nt, double* __restrict__ KtKp, double* __restrict__ work,
-                                 int* __restrict__ status) {
+                                 double* __restrict__ Mt, int* __restrict__ status) {
     const int t = blockIdx.x;
     const int n = tmpl_n[t];
     const int n3 = 3 * n;
@@ -320,6 +371,7 @@ __global__ void k_template_setup(const int* __restrict__ tmpl_n, const int* __re
             B = (1.0 - 2.0 * a * a / r2) / (r * r2);
         }
         L[e] = c0 * ((al == be ? A : 0.0) + B * dd[al] * dd[be]);
+        Mt[minv_off[t] + e] = L[e];
     }
     __syncthreads();
     // 2. Cholesky M = L L^T (right-looking; lower triangle of L overwritten)
@@ -415,7 +467,7 @@ __global__ void k_template_setup(const int* __restrict__ tmpl_n, const int* __re
 void launch_template_setup(gdc_ctx* c) {
     ++c->n_launch, k_template_setup<<<c->T, 256, 0, c->stream>>>(c->tmpl_n, c->tmpl_off, c->minv_off, c->tmpl_xyz, c->p.a, c->p.eta,
                                                   c->tmpl_Minv, c->tmpl_G, c->tmpl_N, c->tmpl_KtKp, c->tmpl_work,
-                                                  c->dev_status);
+                                                  c->tmpl_M, c->dev_status);
 }
 
 }  // namespace gdc

@@ -84,7 +84,7 @@ struct gdc_ctx {
     int *body_tmpl = 0, *body_susp = 0, *blob_body = 0, *blob_susp = 0, *tmpl_n = 0, *tmpl_off = 0;
     int *blob_gm = 0, *body_gm = 0;
     double *tmpl_xyz = 0, *tmpl_L = 0;
-    double *tmpl_Minv = 0, *tmpl_G = 0, *tmpl_N = 0, *tmpl_KtKp = 0, *tmpl_work = 0;
+    double *tmpl_Minv = 0, *tmpl_G = 0, *tmpl_N = 0, *tmpl_KtKp = 0, *tmpl_work = 0, *tmpl_M = 0;
     double *body_L = 0;
 
     // state (caller arrays)
@@ -240,6 +240,7 @@ void plan_mv_capacity(gdc_ctx* c);
 void launch_body_KT(gdc_ctx* c, const double* x, int x_gm, double* y, int y_gm, double scale);
 void launch_lsq(gdc_ctx* c, const double* vbrev, double* calV);
 void launch_precond(gdc_ctx* c, const double* r, double* z);
+void launch_intra_body(gdc_ctx* c, const double* x, double* y, int gm);
 void launch_template_setup(gdc_ctx* c);
 
 // krylov.cu

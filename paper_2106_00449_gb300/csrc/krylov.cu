@@ -397,51 +397,20 @@ struct LzRot {
     int q, pad;
 };
 
-__global__ void __launch_bounds__(32) k_lz_tridiag(int S, int j, const double* __restrict__ h, int cols,
-                                                   const double* __restrict__ wn2, double* __restrict__ alpha,
-                                                   double* __restrict__ betav, const double* __restrict__ Wnorm,
-                                                   double* __restrict__ cvec, double* __restrict__ err,
-                                                   int* __restrict__ active, int* __restrict__ kcount,
-                                                   int* __restrict__ lastk, double* __restrict__ scal, double tol,
-                                                   const int* __restrict__ fixed, int kstart, int kmax,
-                                                   LzRot* __restrict__ rot_all, int rot_cap, int* __restrict__ status) {
-    const int s = blockIdx.x;
-    if (threadIdx.x != 0) return;
-    if (!active[s]) {
-        scal[s] = 0.0;
-        return;
-    }
-    const int k = j + 1;
-    const double beta = sqrt(fmax(wn2[(long long)s * cols], 0.0));
-    double* al = alpha + (long long)s * kmax;
-    double* be = betav + (long long)s * kmax;
-    al[j] = h[(long long)s * cols + j];
-    be[j] = beta;
-    scal[s] = beta > 0.0 ? 1.0 / beta : 0.0;
-    kcount[s] = k;
-    const bool fixed_mode = fixed != nullptr && fixed[s] > 0;
-    bool compute;
-    if (fixed_mode)
-        compute = k >= fixed[s] || k >= kmax || beta == 0.0;
-    else
-        compute = k >= kstart || k >= kmax || beta == 0.0;
-    if (!compute) return;
-
-    double d[GDC_MAX_LANCZOS], e[GDC_MAX_LANCZOS], u[GDC_MAX_LANCZOS];
+// out = wn * T_k^(1/2) e_1 for the k x k tridiagonal (al, be).  Returns false when the
+// QR iteration does not converge or the rotation store overflows.
+__device__ bool lz_sqrt_e1(const double* al, const double* be, int k, double wn, LzRot* rot, int rot_cap,
+                           double* out) {
+    double d[GDC_MAX_LANCZOS], e[GDC_MAX_LANCZOS];
     for (int i = 0; i < k; ++i) {
         d[i] = al[i];
         e[i] = i + 1 < k ? be[i] : 0.0;
-        u[i] = i == 0 ? 1.0 : 0.0;
+        out[i] = i == 0 ? 1.0 : 0.0;   // u = Q^T e_1, built rotation by rotation
     }
-    LzRot* rot = rot_all + (long long)s * rot_cap;
     int nrot = 0;
-    bool ok = true;
     int hi = k - 1;
     for (int sweep = 0; hi > 0; ++sweep) {
-        if (sweep > 40 * k + 40) {
-            ok = false;
-            break;
-        }
+        if (sweep > 40 * k + 40) return false;
         if (fabs(e[hi - 1]) <= 1e-16 * (fabs(d[hi - 1]) + fabs(d[hi]))) {
             e[hi - 1] = 0.0;
             --hi;
@@ -474,55 +443,124 @@ __global__ void __launch_bounds__(32) k_lz_tridiag(int S, int j, const double* _
                 xx = e[q];
                 zz = bulge;
             }
-            const double u0 = u[q], u1 = u[q + 1];
-            u[q] = cq * u0 + sq * u1;
-            u[q + 1] = -sq * u0 + cq * u1;
-            if (nrot < rot_cap) rot[nrot] = LzRot{cq, sq, q, 0};
-            ++nrot;
+            const double u0 = out[q], u1 = out[q + 1];
+            out[q] = cq * u0 + sq * u1;
+            out[q + 1] = -sq * u0 + cq * u1;
+            if (nrot >= rot_cap) return false;
+            rot[nrot++] = LzRot{cq, sq, q, 0};
         }
     }
-    if (nrot > rot_cap) ok = false;
-    if (!ok) {
+    // g = sqrt(theta) * u, then Q g by the transposed rotations in reverse order
+    for (int i = 0; i < k; ++i) out[i] *= sqrt(fmax(d[i], 0.0));
+    for (int t = nrot - 1; t >= 0; --t) {
+        const LzRot R = rot[t];
+        const double g0 = out[R.q], g1 = out[R.q + 1];
+        out[R.q] = R.c * g0 - R.s * g1;
+        out[R.q + 1] = R.s * g0 + R.c * g1;
+    }
+    for (int i = 0; i < k; ++i) out[i] *= wn;
+    return true;
+}
+
+// ||c_k - [c_{k-1}; 0]|| / ||c_k||
+__device__ inline double lz_change(const double* ck, const double* cprev, int k) {
+    double num = 0.0, den = 0.0;
+    for (int r = 0; r < k; ++r) {
+        const double old = r < k - 1 ? cprev[r] : 0.0;
+        num += (ck[r] - old) * (ck[r] - old);
+        den += ck[r] * ck[r];
+    }
+    return den > 0.0 ? sqrt(num / den) : 0.0;
+}
+
+// The stopping index is the smallest k >= 2 with ||c_k - c_{k-1}|| / ||c_k|| < tol
+// whatever the check schedule: when the first check of a run (index firstk + 1) already
+// passes, earlier indices are examined backwards.  lastk[s] is the last index whose c was
+// formed (-1 at the start of a run), lastk[S + s] the first one.
+__global__ void __launch_bounds__(32) k_lz_tridiag(int S, int j, const double* __restrict__ h, int cols,
+                                                   const double* __restrict__ wn2, double* __restrict__ alpha,
+                                                   double* __restrict__ betav, const double* __restrict__ Wnorm,
+                                                   double* __restrict__ cvec, double* __restrict__ err,
+                                                   int* __restrict__ active, int* __restrict__ kcount,
+                                                   int* __restrict__ lastk, double* __restrict__ scal, double tol,
+                                                   const int* __restrict__ fixed, int kstart, int kmax,
+                                                   LzRot* __restrict__ rot_all, int rot_cap, int* __restrict__ status) {
+    const int s = blockIdx.x;
+    if (threadIdx.x != 0) return;
+    if (!active[s]) {
+        scal[s] = 0.0;
+        return;
+    }
+    const int k = j + 1;
+    const double beta = sqrt(fmax(wn2[(long long)s * cols], 0.0));
+    double* al = alpha + (long long)s * kmax;
+    double* be = betav + (long long)s * kmax;
+    al[j] = h[(long long)s * cols + j];
+    be[j] = beta;
+    scal[s] = beta > 0.0 ? 1.0 / beta : 0.0;
+    kcount[s] = k;
+    const bool fixed_mode = fixed != nullptr && fixed[s] > 0;
+    const bool compute = fixed_mode ? (k >= fixed[s] || k >= kmax || beta == 0.0)
+                                    : (k >= kstart || k >= kmax || beta == 0.0);
+    if (!compute) return;
+    LzRot* rot = rot_all + (long long)s * rot_cap;
+    double* cs_ = cvec + (long long)s * kmax;   // c of the last formed index
+    const double wn = Wnorm[s];
+    double cur[GDC_MAX_LANCZOS];
+    if (!lz_sqrt_e1(al, be, k, wn, rot, rot_cap, cur)) {
         atomicExch(status, 2);
         active[s] = 0;
         err[s] = 1.0;
         return;
     }
-    // g = sqrt(theta) * u, then Q g by the transposed rotations in reverse order
-    for (int i = 0; i < k; ++i) u[i] *= sqrt(fmax(d[i], 0.0));
-    for (int t = nrot - 1; t >= 0; --t) {
-        const LzRot R = rot[t];
-        const double g0 = u[R.q], g1 = u[R.q + 1];
-        u[R.q] = R.c * g0 - R.s * g1;
-        u[R.q + 1] = R.s * g0 + R.c * g1;
+    if (fixed_mode) {
+        for (int r = 0; r < k; ++r) cs_[r] = cur[r];
+        err[s] = 0.0;
+        active[s] = 0;
+        return;
     }
-    const double wn = Wnorm[s];
-    double* cs_ = cvec + (long long)s * kmax;
-    const bool have_prev = lastk[s] == k - 1;
-    double num = 0.0, den = 0.0;
-    for (int r = 0; r < k; ++r) {
-        const double cn = wn * u[r];
-        const double old = (have_prev && r < k - 1) ? cs_[r] : 0.0;
-        num += (cn - old) * (cn - old);
-        den += cn * cn;
-        cs_[r] = cn;
+    const int prevk = lastk[s], firstk = lastk[S + s];
+    double ee = beta == 0.0 ? 0.0 : 1.0;
+    bool stop = beta == 0.0;
+    int kstar = k;
+    if (prevk == k - 1) {
+        ee = lz_change(cur, cs_, k);
+        if (ee < tol) {
+            stop = true;
+            if (firstk == k - 1) {   // no check was possible at k - 1: look further back
+                double ck[GDC_MAX_LANCZOS], cm[GDC_MAX_LANCZOS], best[GDC_MAX_LANCZOS];
+                for (int r = 0; r < k; ++r) best[r] = cur[r];
+                for (int r = 0; r < k - 1; ++r) ck[r] = cs_[r];
+                double best_err = ee;
+                for (int kk = k - 1; kk >= 2; --kk) {
+                    if (!lz_sqrt_e1(al, be, kk - 1, wn, rot, rot_cap, cm)) break;
+                    const double e2 = lz_change(ck, cm, kk);
+                    if (!(e2 < tol)) break;
+                    kstar = kk;
+                    best_err = e2;
+                    for (int r = 0; r < kk; ++r) best[r] = ck[r];
+                    for (int r = 0; r < kk - 1; ++r) ck[r] = cm[r];
+                }
+                for (int r = 0; r < kstar; ++r) cur[r] = best[r];
+                ee = best_err;
+            }
+        }
     }
+    if (firstk < 0) lastk[S + s] = k;
     lastk[s] = k;
-    const double ee = den > 0.0 ? sqrt(num / den) : 0.0;
-    bool stop;
-    if (fixed_mode)
-        stop = true;
-    else
-        stop = (have_prev && ee < tol) || beta == 0.0;
-    err[s] = have_prev ? ee : 1.0;
-    if (beta == 0.0) err[s] = 0.0;
+    for (int r = 0; r < kstar; ++r) cs_[r] = cur[r];
+    kcount[s] = kstar;
+    err[s] = ee;
     if (k >= kmax) stop = true;
     if (stop) active[s] = 0;
 }
 
 __global__ void k_lz_reset(int S, int* __restrict__ lastk) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s < S) lastk[s] = -1;
+    if (s < S) {
+        lastk[s] = -1;
+        lastk[S + s] = -1;
+    }
 }
 
 void krylov_init_attributes() {}

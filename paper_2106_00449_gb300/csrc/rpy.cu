@@ -55,8 +55,8 @@ struct RpyConst32 {
 };
 
 // Exact pair term (all branches) for the rare tiles that hold a near pair.
-__device__ __forceinline__ void rpy_pair_exact(const RpyConst32& k, float dx, float dy, float dz, const float4& ls,
-                                               float& ox, float& oy, float& oz) {
+__device__ __forceinline__ void rpy_pair_exact(const RpyConst32& k, float dx, float dy, float dz, float lx, float ly,
+                                               float lz, float& ox, float& oy, float& oz) {
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     float A, B;
     if (r2 >= k.four_a2) {
@@ -72,99 +72,154 @@ __device__ __forceinline__ void rpy_pair_exact(const RpyConst32& k, float dx, fl
         A = k.cA;
         B = 0.f;
     }
-    const float s = B * fmaf(dx, ls.x, fmaf(dy, ls.y, dz * ls.z));
-    ox = fmaf(A, ls.x, fmaf(s, dx, ox));
-    oy = fmaf(A, ls.y, fmaf(s, dy, oy));
-    oz = fmaf(A, ls.z, fmaf(s, dz, oz));
+    const float s = B * fmaf(dx, lx, fmaf(dy, ly, dz * lz));
+    ox = fmaf(A, lx, fmaf(s, dx, ox));
+    oy = fmaf(A, ly, fmaf(s, dy, oy));
+    oz = fmaf(A, lz, fmaf(s, dz, oz));
 }
 
-// Each source tile is first evaluated with the far-field formula only (no branch), while
-// the smallest r^2 of the tile is tracked per target.  A target whose tile held a pair
-// closer than 2a (its own blob included) recomputes that tile with rpy_pair_exact; the
-// far-field values (infinite or NaN for r = 0) are discarded.  Near tiles are the few
-// that hold the target's own body or a touching body.
-template <int TPT>
+// Packed FP32 pairs (Blackwell f32x2 instructions): lane .x and .y of a float2 hold
+// the same quantity for two different targets.
+__device__ __forceinline__ unsigned long long f2u(float2 a) { return *reinterpret_cast<unsigned long long*>(&a); }
+__device__ __forceinline__ float2 u2f(unsigned long long a) { return *reinterpret_cast<float2*>(&a); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(f2u(a)), "l"(f2u(b)), "l"(f2u(c)));
+    return u2f(r);
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2u(a)), "l"(f2u(b)));
+    return u2f(r);
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2u(a)), "l"(f2u(b)));
+    return u2f(r);
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2u(a)), "l"(f2u(b)));
+    return u2f(r);
+}
+
+// Each thread owns 2P targets, evaluated two at a time with packed instructions.  A
+// source tile is first evaluated with the far-field formula only (no branch), while
+// the smallest r^2 per target is tracked; a target whose tile held a pair closer than
+// 2a (its own blob included) recomputes that tile with rpy_pair_exact, discarding the
+// far-field values (infinite or NaN for r = 0).  Shared memory holds each source as
+// (x,x,y,y) (z,z,lx,lx) (ly,ly,lz,lz), so one 16-byte load feeds a packed operand.
+//
+// Same-body pairs are left out (the FP64 intra-body kernel adds them exactly): a tile
+// that overlaps the blob range of a target's own body is also redone, skipping that range.
+template <int P>
 __global__ void __launch_bounds__(128) k_rpy32(const MvItem* __restrict__ items, const long long* __restrict__ susp_blob_off,
                                                const float4* __restrict__ spos, const float4* __restrict__ slam,
+                                               const long long* __restrict__ body_blob_off,
                                                float4* __restrict__ part, int NBL, RpyConst32 k) {
-    __shared__ float4 sp[MV_TILE];
-    __shared__ float4 sl[MV_TILE];
+    __shared__ float4 sh[3 * MV_TILE];
     const MvItem it = items[blockIdx.x];
     const long long b0 = susp_blob_off[it.s];
     const int ns = (int)(susp_blob_off[it.s + 1] - b0);
+    const float2 c23 = make_float2(k.c23, k.c23), mc2 = make_float2(-k.c2, -k.c2), one = make_float2(1.f, 1.f);
 
-    float xt[TPT], yt[TPT], zt[TPT];
-    float ax[TPT], ay[TPT], az[TPT], cx[TPT], cy[TPT], cz[TPT];
+    float2 xt[P], yt[P], zt[P], ax[P], ay[P], az[P], cx[P], cy[P], cz[P];
+    int own_lo[2 * P], own_hi[2 * P];   // suspension-local blob range of each target's body
 #pragma unroll
-    for (int t = 0; t < TPT; ++t) {
-        const int ti = it.t0 + threadIdx.x + t * 128;
-        const float4 p = spos[b0 + min(ti, ns - 1)];
-        xt[t] = p.x;
-        yt[t] = p.y;
-        zt[t] = p.z;
-        ax[t] = ay[t] = az[t] = 0.f;
-        cx[t] = cy[t] = cz[t] = 0.f;
+    for (int p = 0; p < P; ++p) {
+        const float4 pa = spos[b0 + min(it.t0 + (int)threadIdx.x + (2 * p) * 128, ns - 1)];
+        const float4 pb = spos[b0 + min(it.t0 + (int)threadIdx.x + (2 * p + 1) * 128, ns - 1)];
+        xt[p] = make_float2(pa.x, pb.x);
+        yt[p] = make_float2(pa.y, pb.y);
+        zt[p] = make_float2(pa.z, pb.z);
+        const int ba = __float_as_int(pa.w), bb = __float_as_int(pb.w);
+        own_lo[2 * p] = (int)(body_blob_off[ba] - b0);
+        own_hi[2 * p] = (int)(body_blob_off[ba + 1] - b0);
+        own_lo[2 * p + 1] = (int)(body_blob_off[bb] - b0);
+        own_hi[2 * p + 1] = (int)(body_blob_off[bb + 1] - b0);
+        ax[p] = ay[p] = az[p] = make_float2(0.f, 0.f);
+        cx[p] = cy[p] = cz[p] = make_float2(0.f, 0.f);
     }
     for (int j0 = it.j0; j0 < it.j1; j0 += MV_TILE) {
         const int n = min(MV_TILE, it.j1 - j0);
         __syncthreads();
         for (int e = threadIdx.x; e < n; e += 128) {
-            sp[e] = spos[b0 + j0 + e];
-            sl[e] = slam[b0 + j0 + e];
+            const float4 ps = spos[b0 + j0 + e];
+            const float4 ls = slam[b0 + j0 + e];
+            sh[3 * e] = make_float4(ps.x, ps.x, ps.y, ps.y);
+            sh[3 * e + 1] = make_float4(ps.z, ps.z, ls.x, ls.x);
+            sh[3 * e + 2] = make_float4(ls.y, ls.y, ls.z, ls.z);
         }
         __syncthreads();
-        float tx[TPT], ty[TPT], tz[TPT], mn[TPT];
+        float2 tx[P], ty[P], tz[P];
+        float mn[2 * P];
 #pragma unroll
-        for (int t = 0; t < TPT; ++t) {
-            tx[t] = ty[t] = tz[t] = 0.f;
-            mn[t] = 3.0e38f;
+        for (int p = 0; p < P; ++p) {
+            tx[p] = ty[p] = tz[p] = make_float2(0.f, 0.f);
+            mn[2 * p] = mn[2 * p + 1] = 3.0e38f;
         }
-#pragma unroll 4
+#pragma unroll 2
         for (int j = 0; j < n; ++j) {
-            const float4 ps = sp[j];
-            const float4 ls = sl[j];
+            const float4 s0 = sh[3 * j], s1 = sh[3 * j + 1], s2 = sh[3 * j + 2];
+            const float2 xs = make_float2(s0.x, s0.y), ys = make_float2(s0.z, s0.w), zs = make_float2(s1.x, s1.y);
+            const float2 lx = make_float2(s1.z, s1.w), ly = make_float2(s2.x, s2.y), lz = make_float2(s2.z, s2.w);
 #pragma unroll
-            for (int t = 0; t < TPT; ++t) {
-                const float dx = ps.x - xt[t], dy = ps.y - yt[t], dz = ps.z - zt[t];
-                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                const float ri = rsqrtf(r2);
-                const float ri2 = ri * ri;
-                const float ri3 = ri2 * ri;
-                const float A = fmaf(k.c23, ri3, ri);
-                const float B = ri3 * fmaf(-k.c2, ri2, 1.f);
-                const float s = B * fmaf(dx, ls.x, fmaf(dy, ls.y, dz * ls.z));
-                tx[t] = fmaf(A, ls.x, fmaf(s, dx, tx[t]));
-                ty[t] = fmaf(A, ls.y, fmaf(s, dy, ty[t]));
-                tz[t] = fmaf(A, ls.z, fmaf(s, dz, tz[t]));
-                mn[t] = fminf(mn[t], r2);
+            for (int p = 0; p < P; ++p) {
+                const float2 dx = sub2(xs, xt[p]), dy = sub2(ys, yt[p]), dz = sub2(zs, zt[p]);
+                const float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+                const float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+                const float2 ri2 = mul2(ri, ri);
+                const float2 ri3 = mul2(ri2, ri);
+                const float2 A = fma2(c23, ri3, ri);
+                const float2 B = mul2(ri3, fma2(mc2, ri2, one));
+                const float2 s = mul2(B, fma2(dx, lx, fma2(dy, ly, mul2(dz, lz))));
+                tx[p] = fma2(A, lx, fma2(s, dx, tx[p]));
+                ty[p] = fma2(A, ly, fma2(s, dy, ty[p]));
+                tz[p] = fma2(A, lz, fma2(s, dz, tz[p]));
+                mn[2 * p] = fminf(mn[2 * p], r2.x);
+                mn[2 * p + 1] = fminf(mn[2 * p + 1], r2.y);
             }
         }
 #pragma unroll
-        for (int t = 0; t < TPT; ++t) {
-            if (mn[t] < k.four_a2) {
-                float ox = 0.f, oy = 0.f, oz = 0.f;
-                for (int j = 0; j < n; ++j) {
-                    const float4 ps = sp[j];
-                    rpy_pair_exact(k, ps.x - xt[t], ps.y - yt[t], ps.z - zt[t], sl[j], ox, oy, oz);
+        for (int p = 0; p < P; ++p) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int lo = own_lo[2 * p + h] - j0, hi = own_hi[2 * p + h] - j0;   // own body, tile-relative
+                if (mn[2 * p + h] < k.four_a2 || (lo < n && hi > 0)) {
+                    const float xq = h ? xt[p].y : xt[p].x, yq = h ? yt[p].y : yt[p].x, zq = h ? zt[p].y : zt[p].x;
+                    float ox = 0.f, oy = 0.f, oz = 0.f;
+                    for (int j = 0; j < n; ++j) {
+                        if (j >= lo && j < hi) continue;
+                        const float4 s0 = sh[3 * j], s1 = sh[3 * j + 1], s2 = sh[3 * j + 2];
+                        rpy_pair_exact(k, s0.x - xq, s0.z - yq, s1.x - zq, s1.z, s2.x, s2.z, ox, oy, oz);
+                    }
+                    if (h) {
+                        tx[p].y = ox;
+                        ty[p].y = oy;
+                        tz[p].y = oz;
+                    } else {
+                        tx[p].x = ox;
+                        ty[p].x = oy;
+                        tz[p].x = oz;
+                    }
                 }
-                tx[t] = ox;
-                ty[t] = oy;
-                tz[t] = oz;
             }
         }
         // compensated (Kahan) addition of the tile sums
 #pragma unroll
-        for (int t = 0; t < TPT; ++t) {
-            float y, u;
-            y = tx[t] - cx[t]; u = ax[t] + y; cx[t] = (u - ax[t]) - y; ax[t] = u;
-            y = ty[t] - cy[t]; u = ay[t] + y; cy[t] = (u - ay[t]) - y; ay[t] = u;
-            y = tz[t] - cz[t]; u = az[t] + y; cz[t] = (u - az[t]) - y; az[t] = u;
+        for (int p = 0; p < P; ++p) {
+            float2 y, u;
+            y = sub2(tx[p], cx[p]); u = add2(ax[p], y); cx[p] = sub2(sub2(u, ax[p]), y); ax[p] = u;
+            y = sub2(ty[p], cy[p]); u = add2(ay[p], y); cy[p] = sub2(sub2(u, ay[p]), y); ay[p] = u;
+            y = sub2(tz[p], cz[p]); u = add2(az[p], y); cz[p] = sub2(sub2(u, az[p]), y); az[p] = u;
         }
     }
 #pragma unroll
-    for (int t = 0; t < TPT; ++t) {
-        const int ti = it.t0 + threadIdx.x + t * 128;
-        if (ti < ns) part[(long long)it.k * NBL + b0 + ti] = make_float4(ax[t] - cx[t], ay[t] - cy[t], az[t] - cz[t], 0.f);
+    for (int p = 0; p < P; ++p) {
+        const float2 rx = sub2(ax[p], cx[p]), ry = sub2(ay[p], cy[p]), rz = sub2(az[p], cz[p]);
+        const int ta = it.t0 + threadIdx.x + (2 * p) * 128, tb = ta + 128;
+        if (ta < ns) part[(long long)it.k * NBL + b0 + ta] = make_float4(rx.x, ry.x, rz.x, 0.f);
+        if (tb < ns) part[(long long)it.k * NBL + b0 + tb] = make_float4(rx.y, ry.y, rz.y, 0.f);
     }
 }
 
@@ -243,15 +298,15 @@ void launch_rpy(gdc_ctx* c, int prec) {
         const double a = c->p.a;
         RpyConst32 k{(float)(2.0 * a * a / 3.0), (float)(2.0 * a * a), (float)(4.0 * a * a),
                      (float)(4.0 / (3.0 * a)), (float)(9.0 / (32.0 * a)), (float)(1.0 / (8.0 * a * a))};
-        if (c->mv_tpt == 1)
-            ++c->n_launch, k_rpy32<1><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off, c->spos, c->slam,
-                                                             (float4*)c->mv_part, c->NBL, k);
-        else if (c->mv_tpt == 4)
-            ++c->n_launch, k_rpy32<4><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off, c->spos, c->slam,
-                                                             (float4*)c->mv_part, c->NBL, k);
+        // two targets per packed lane pair: tpt 4 -> P = 2, otherwise P = 1
+        if (c->mv_tpt == 4)
+            ++c->n_launch, k_rpy32<2><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off, c->spos,
+                                                                            c->slam, c->body_blob_off,
+                                                                            (float4*)c->mv_part, c->NBL, k);
         else
-            ++c->n_launch, k_rpy32<2><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off, c->spos, c->slam,
-                                                             (float4*)c->mv_part, c->NBL, k);
+            ++c->n_launch, k_rpy32<1><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off, c->spos,
+                                                                            c->slam, c->body_blob_off,
+                                                                            (float4*)c->mv_part, c->NBL, k);
     } else {
         if (c->mv_tpt == 1)
             ++c->n_launch, k_rpy64<1><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off, c->spos64, c->slam64,
@@ -328,6 +383,8 @@ static void launch_epilogue(gdc_ctx* c, int prec, double c0, const double* x, do
 
 void launch_rpy_epilogue(gdc_ctx* c, int prec, const double* x, double* y, int gm_layout) {
     launch_epilogue(c, prec, 1.0 / (8.0 * 3.141592653589793 * c->p.eta), x, y, gm_layout);
+    // the FP32 pair kernel leaves out same-body pairs: add each body's block in FP64
+    if (prec == GDC_FP32_MIXED) launch_intra_body(c, x, y, gm_layout);
 }
 
 // ---- soft repulsion between blobs of different bodies --------------------------
@@ -510,12 +567,12 @@ void build_mv_items(gdc_ctx* c, int tpt, double waves) {
 namespace gdc {
 
 // Candidate tilings of the pair kernels: targets per thread x work items per launch.
-static const int kTpt[3] = {1, 2, 4};
+static const int kTpt[2] = {2, 4};
 static const double kWaves[3] = {4.0, 8.0, 16.0};
 
 void plan_mv_capacity(gdc_ctx* c) {
     int cap_items = 0, cap_k = 1;
-    for (int a = 0; a < 3; ++a)
+    for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 3; ++b) {
             build_mv_items(c, kTpt[a], kWaves[b]);
             cap_items = std::max(cap_items, c->mv_n_items);
@@ -547,7 +604,7 @@ gdc_status autotune_pair_kernel(gdc_ctx* c) {
     float best = 1e30f;
     int bt = 2;
     double bw = 8.0;
-    for (int a = 0; a < 3; ++a)
+    for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 3; ++b) {
             build_mv_items(c, kTpt[a], kWaves[b]);
             if ((st = upload_items(c)) != GDC_OK) break;
