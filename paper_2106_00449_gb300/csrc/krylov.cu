@@ -82,14 +82,18 @@ __global__ void __launch_bounds__(RED_THREADS) k_mdot(const Chunk* __restrict__ 
 }
 
 // out[s * cols + i] = sum of the chunk partials of segment s, in chunk order
+// One warp per (segment, column): lanes take chunks lane, lane+32, ... and the warp sums
+// them with a fixed shuffle tree, so the order is the same on every run.
 __global__ void k_seg_sum(int S, const int* __restrict__ seg_chunk_off, const double* __restrict__ part, int cols, int k,
                           double* __restrict__ out) {
     const int s = blockIdx.x;
-    for (int i = threadIdx.x; i < k; i += blockDim.x) {
-        double acc = 0.0;
-        for (int ch = seg_chunk_off[s]; ch < seg_chunk_off[s + 1]; ++ch) acc += part[(long long)ch * cols + i];
-        out[(long long)s * cols + i] = acc;
-    }
+    const int i = blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= k) return;
+    double acc = 0.0;
+    for (int ch = seg_chunk_off[s] + lane; ch < seg_chunk_off[s + 1]; ch += 32) acc += part[(long long)ch * cols + i];
+    acc = warp_sum(acc);
+    if (lane == 0) out[(long long)s * cols + i] = acc;
 }
 
 // w[e] -= sum_i h[s * cols + i] * V_i[e] for i < k
@@ -143,7 +147,8 @@ __global__ void k_sub_chunks(const Chunk* __restrict__ chunks, const double* __r
 static void seg_mdot(gdc_ctx* c, const gdc::Seg& sg, const double* V, long long ld, int k, const double* w,
                      double* out, int cols) {
     ++c->n_launch, k_mdot<<<sg.n_chunks, RED_THREADS, 0, c->stream>>>(sg.chunks, V, ld, k, w, c->red_part, c->red_cols);
-    ++c->n_launch, k_seg_sum<<<c->S, 128, 0, c->stream>>>(c->S, sg.seg_chunk_off, c->red_part, c->red_cols, k, out);
+    ++c->n_launch, k_seg_sum<<<dim3(c->S, ceil_div(k, 8)), 256, 0, c->stream>>>(c->S, sg.seg_chunk_off, c->red_part,
+                                                                                c->red_cols, k, out);
     (void)cols;
 }
 
