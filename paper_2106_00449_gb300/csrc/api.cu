@@ -229,6 +229,7 @@ static size_t carve(gdc_ctx* c, void* base) {
     c->lz_rot_cap = (int)(3 * k * k + 64);
     c->lz_rot = (void*)w.take<double>(3LL * S * c->lz_rot_cap);   // 24-byte records
     c->lz_lastk = w.take<int>(2 * S);
+    c->lz_hint = w.take<int>(S);
     c->lz_h = w.take<double>(S * cols);
     c->lz_Wnorm = w.take<double>(S);
     c->lz_err = w.take<double>(S);
@@ -294,6 +295,7 @@ static gdc_status upload_layout(gdc_ctx* c, const double* tmpl_xyz_centred) {
     chk(up(c, c->mv_items, c->h_mv_items.data(), c->h_mv_items.size()));
     chk(up(c, c->mv_nk, c->h_mv_nk.data(), S));
     chk(cudaMemsetAsync(c->dev_status, 0, 4 * sizeof(int), c->stream));
+    chk(cudaMemsetAsync(c->lz_hint, 0, sizeof(int) * S, c->stream));
     chk(cudaStreamSynchronize(c->stream));  // host vectors above go out of scope
     return cuda_check(c, e, "upload of the layout");
 }

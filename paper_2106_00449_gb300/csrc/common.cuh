@@ -114,7 +114,7 @@ struct gdc_ctx {
     int *lz_active = 0, *lz_k = 0, *lz_fix = 0, *lz_lastk = 0;
     void* lz_rot = 0;             // per suspension: Givens rotations of the tridiagonal QR (24 B each)
     int lz_rot_cap = 0;           // rotations stored per suspension: 3 kmax^2 + 64
-    int lz_hint = 0;              // iterations the previous unconstrained Lanczos run needed
+    int* lz_hint = 0;             // per suspension: index the previous unconstrained run stopped at (0 = none)
 
     // reductions
     gdc::Seg seg_gm, seg_lz, seg_body;

@@ -394,8 +394,8 @@ __global__ void k_lz_start(int S, const double* __restrict__ wn2, int cols, doub
 // replayed transposed in reverse order on g = sqrt(theta) * u, which gives Q g.
 // That is O(k^2) work instead of the O(k^3) of accumulating Q.
 //
-// Convergence: ||c_k - c_{k-1}|| / ||c_k|| < tol, evaluated from iteration kstart on
-// (the previous run's count sets kstart, so early iterations skip the eigen-work);
+// Convergence: ||c_k - c_{k-1}|| / ||c_k|| < tol, evaluated from a start index set by the
+// suspension's previous count (so early iterations skip the eigen-work);
 // in fixed mode c is formed once, at k = fixed[s].
 struct LzRot {
     double c, s;
@@ -488,7 +488,8 @@ __global__ void __launch_bounds__(32) k_lz_tridiag(int S, int j, const double* _
                                                    double* __restrict__ cvec, double* __restrict__ err,
                                                    int* __restrict__ active, int* __restrict__ kcount,
                                                    int* __restrict__ lastk, double* __restrict__ scal, double tol,
-                                                   const int* __restrict__ fixed, int kstart, int kmax,
+                                                   const int* __restrict__ fixed, int* __restrict__ hint, int kmax,
+                                                   const long long* __restrict__ susp_blob_off,
                                                    LzRot* __restrict__ rot_all, int rot_cap, int* __restrict__ status) {
     const int s = blockIdx.x;
     if (threadIdx.x != 0) return;
@@ -497,14 +498,20 @@ __global__ void __launch_bounds__(32) k_lz_tridiag(int S, int j, const double* _
         return;
     }
     const int k = j + 1;
-    const double beta = sqrt(fmax(wn2[(long long)s * cols], 0.0));
+    double beta = sqrt(fmax(wn2[(long long)s * cols], 0.0));
     double* al = alpha + (long long)s * kmax;
     double* be = betav + (long long)s * kmax;
     al[j] = h[(long long)s * cols + j];
+    // Krylov space exhausted (k reached the dimension) or numerically invariant: exact stop
+    const long long dim = 3 * (susp_blob_off[s + 1] - susp_blob_off[s]);
+    if (k >= dim || beta <= 1e-14 * fmax(fabs(al[0]), fabs(al[j]))) beta = 0.0;
     be[j] = beta;
     scal[s] = beta > 0.0 ? 1.0 / beta : 0.0;
     kcount[s] = k;
     const bool fixed_mode = fixed != nullptr && fixed[s] > 0;
+    // checks start a little before this suspension's previous count (hint[s]; 0 = none)
+    const int hs = fixed_mode ? 0 : hint[s];
+    const int kstart = hs > 0 ? max(2, hs - max(4, hs / 8)) : 2;
     const bool compute = fixed_mode ? (k >= fixed[s] || k >= kmax || beta == 0.0)
                                     : (k >= kstart || k >= kmax || beta == 0.0);
     if (!compute) return;
@@ -557,7 +564,10 @@ __global__ void __launch_bounds__(32) k_lz_tridiag(int S, int j, const double* _
     kcount[s] = kstar;
     err[s] = ee;
     if (k >= kmax) stop = true;
-    if (stop) active[s] = 0;
+    if (stop) {
+        active[s] = 0;
+        hint[s] = kstar;
+    }
 }
 
 __global__ void k_lz_reset(int S, int* __restrict__ lastk) {
@@ -579,8 +589,6 @@ gdc_status lanczos_sqrt(gdc_ctx* c, const double* W, double* out, double scale, 
     const int kmax = c->kmax;
     gdc_status st = GDC_OK;
     // convergence checks start a little before the previous run's count
-    int kstart = 2;
-    if (!fixed_mode && c->lz_hint > 0) kstart = std::max(2, c->lz_hint - std::max(4, c->lz_hint / 8));
     seg_mdot(c, sg, W, 0, 1, W, c->lz_h, cols);
     ++c->n_launch, k_lz_start<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(c->S, c->lz_h, cols, c->lz_Wnorm, c->lz_scal,
                                                                           c->lz_active, c->lz_k, c->lz_err);
@@ -599,7 +607,7 @@ gdc_status lanczos_sqrt(gdc_ctx* c, const double* W, double* out, double scale, 
         seg_mdot(c, sg, c->lz_w, 0, 1, c->lz_w, c->gm_h2, cols);
         ++c->n_launch, k_lz_tridiag<<<c->S, 32, 0, c->stream>>>(
             c->S, j, c->lz_h, cols, c->gm_h2, c->lz_alpha, c->lz_beta, c->lz_Wnorm, c->lz_c, c->lz_err, c->lz_active,
-            c->lz_k, c->lz_lastk, c->lz_scal, c->p.lanczos_tol, fixed_mode ? c->lz_fix : nullptr, kstart, kmax,
+            c->lz_k, c->lz_lastk, c->lz_scal, c->p.lanczos_tol, fixed_mode ? c->lz_fix : nullptr, c->lz_hint, kmax, c->susp_blob_off,
             (LzRot*)c->lz_rot, c->lz_rot_cap, c->dev_status);
         ++c->n_launch, k_seg_scale<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_w, c->lz_scal,
                                                                        c->lz_V + (long long)(j + 1) * n);
@@ -622,7 +630,6 @@ gdc_status lanczos_sqrt(gdc_ctx* c, const double* W, double* out, double scale, 
         kk = std::max(kk, ks[s]);
         ee = std::max(ee, errs[s]);
     }
-    if (!fixed_mode) c->lz_hint = kk;
     if (iters_out) *iters_out = kk;
     if (err_out) *err_out = ee;
     if (!fixed_mode && ee > c->p.lanczos_tol && kk >= kmax)
