@@ -14,7 +14,7 @@ Modules
 geometry   quaternions, rotation matrix, exp map, blob positions (Sec. 2, App. A)
 rpy        dense Rotne-Prager-Yamakawa blob mobility M (Sec. 4.1)
 rigid      K, K^T K, saddle-point solve, body mobility N, least squares (Sec. 2.2, 3, 5)
-forces     soft blob-blob repulsion between different bodies (Eq. 20 form)
+forces     soft blob-blob repulsion between different bodies (Eq. soft_sphere_potential form)
 philox     Philox4x32-10 counter-based generator and Box-Muller normals
 gdc        the gDC step (Sec. 3, RFD and FD divergence) and Euler-Maruyama (App. D)
 matfree    matrix-free selected rows of M lambda for sizes too large to store M

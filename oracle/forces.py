@@ -1,16 +1,16 @@
 """Oracle soft repulsion between blobs of different bodies.  TEST INFRASTRUCTURE ONLY.
 
 The force between two blobs a distance r apart is the (negative) derivative
-of the soft-sphere potential of Sec. 6.3, Eq. (20):
+of the soft-sphere potential of Sec. 6.3, Eq. (soft_sphere_potential):
 
   F(r) = A exp(-(r - 2a)/b)  for r >= 2a,
   F(r) = A                   for r <  2a  (the constant-force continuation
-                                           that the linear branch of Eq. (20) gives),
+                                           that the linear branch of Eq. (soft_sphere_potential) gives),
 
 directed along r_i - r_j (it pushes blob i away from blob j), with A = U0/b.
 Blobs of the same body do not repel (their distances never change).  The
 body force and torque are F_p = sum_i f_i and T_p = sum_i (r_i - Y_p) x f_i
-(the K^T map of Eq. 13 applied to the blob forces).
+(the K^T map of Eq. force_torque_balance_compact applied to the blob forces).
 """
 from __future__ import annotations
 

@@ -11,13 +11,13 @@ Readings of points the paper leaves open (each is also listed with the design no
 
 * Y_p is the blob centroid (templates are centred on it).
 * The Brownian slip velocity is v-breve = sqrt(2 kT / dt) M^(1/2) W with the
-  same W at the start and at the mid-step (Eqs. 17 and 19).
-* RFD (Eq. 16 with the footnote's L_p): the perturbed state is
+  same W at the start and at the mid-step (Eqs. unconst and step5).
+* RFD (Eq. rfd_div with the footnote's L_p): the perturbed state is
   Y + delta L_p W~_t, exp(delta W~_r) * q; the estimator is
   sum_p [W~_t . (V~_t - V_t) / (delta L_p) + W~_r . (V~_r - V_r) / delta],
   and nu = 1 + dt/2 * estimator is one scalar for the whole suspension.
   A single-blob body has L_p = 0; it uses L_p = a instead.
-* FD (Eq. 15): the same sum over unit perturbations of each body coordinate.
+* FD (Eq. FD): the same sum over unit perturbations of each body coordinate.
 * Background shear u(r) = (shear_rate * y, 0, 0) enters the slip as
   M lambda - K V = -v-breve - u(r) at the mid-step solve only.
 * Forces are the soft blob repulsion of forces.py evaluated at the mid-step.
@@ -84,7 +84,7 @@ def perturbed_state(layout, Y, q, dY: np.ndarray, du: np.ndarray):
 
 
 def rfd_divergence(layout, Y, q, W, Wt, calV, p: Params) -> float:
-    """Step 3(b): one-sample random finite difference of div(calV) (Eq. 16 and its footnote)."""
+    """Step 3(b): one-sample random finite difference of div(calV) (Eq. rfd_div and its footnote)."""
     d = p.rfd_delta
     L = _lengths(layout, p.a)
     Wt = Wt.reshape(-1, 6)
@@ -96,7 +96,7 @@ def rfd_divergence(layout, Y, q, W, Wt, calV, p: Params) -> float:
 
 
 def fd_divergence(layout, Y, q, W, calV, p: Params) -> float:
-    """Step 3(a): one-sided finite differences over every body coordinate (Eq. 15)."""
+    """Step 3(a): one-sided finite differences over every body coordinate (Eq. FD)."""
     d = p.rfd_delta
     L = _lengths(layout, p.a)
     total = 0.0
@@ -114,7 +114,7 @@ def fd_divergence(layout, Y, q, W, calV, p: Params) -> float:
 
 
 def midpoint_solve(layout, Ym, qm, W, p: Params):
-    """Step 5: full mobility solve at the mid-step with the same W (Eq. 19)."""
+    """Step 5: full mobility solve at the mid-step with the same W (Eq. step5)."""
     r, M, K, B, vb = brownian_slip(layout, Ym, qm, W, p)
     f = forces.blob_forces(r, layout.blob_body, p.rep_A, p.rep_b, p.a)
     FT = forces.body_force_torque(r, Ym, layout.blob_body, f)
@@ -157,7 +157,7 @@ def em_step(layout, Y, q, W, p: Params) -> dict:
 
 
 def body_mobility_at(layout, Y, q, p: Params) -> np.ndarray:
-    """Dense N(x) = (K^T M^-1 K)^-1 at state (Y, q) (Eq. 12)."""
+    """Dense N(x) = (K^T M^-1 K)^-1 at state (Y, q) (Eq. body_mob)."""
     r = geometry.blob_positions(layout, Y, q)
     M = rpy.rpy_matrix(r, p.a, p.eta)
     K = rigid.k_matrix(r, Y, layout.blob_body)

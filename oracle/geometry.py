@@ -1,7 +1,7 @@
 """Oracle geometry: quaternions, rotations and blob positions.  TEST INFRASTRUCTURE ONLY.
 
 Conventions follow Sec. 2 and App. A: q = (q0, q1, q2, q3) with the scalar
-part first; R(q) is Eq. (1); exp(u) = (cos(|u|/2), sin(|u|/2) u/|u|); the
+part first; R(q) is Eq. (quaternion_rotation_matrix); exp(u) = (cos(|u|/2), sin(|u|/2) u/|u|); the
 Hamilton product composes rotations so that exp(u) * q rotates by q first
 and then by exp(u).
 """
@@ -11,7 +11,7 @@ import numpy as np
 
 
 def rotation_matrix(q: np.ndarray) -> np.ndarray:
-    """R(q) of Sec. 2, Eq. (1), written entry by entry (q scalar first)."""
+    """R(q) of Sec. 2, Eq. (quaternion_rotation_matrix), written entry by entry (q scalar first)."""
     q0, q1, q2, q3 = (float(x) for x in q)
     return np.array([
         [1.0 - 2.0 * q2 * q2 - 2.0 * q3 * q3, 2.0 * (q1 * q2 - q3 * q0), 2.0 * (q1 * q3 + q2 * q0)],

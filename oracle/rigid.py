@@ -1,7 +1,7 @@
 """Oracle rigid-body algebra: K, K^T K, the saddle point, N and step-2 least squares.
 
-TEST INFRASTRUCTURE ONLY.  Dense FP64 restatements of Sec. 2.2 (Eqs. 7-15),
-Sec. 3 step 2 (Eqs. 17-18) and Sec. 5 (the closed form of (K^T K)^(p)).
+TEST INFRASTRUCTURE ONLY.  Dense FP64 restatements of Sec. 2.2 (Eqs. rigid_body_cond to v_brown_RMB),
+Sec. 3 step 2 (Eqs. unconst, sol_unconst) and Sec. 5 (the closed form of (K^T K)^(p)).
 
 Rank-deficient bodies.  A body whose blobs are collinear (a rod) cannot be
 spun about its own axis by any blob velocity: K_p has a null vector, so
@@ -20,9 +20,9 @@ from .geometry import cross_matrix
 
 
 def k_matrix(r: np.ndarray, Y: np.ndarray, blob_body: np.ndarray) -> np.ndarray:
-    """K (3M x 6N): block (i, p) = [I_3, [x (r_i - Y_p)]] if blob i is in body p, else 0 (Eq. 9).
+    """K (3M x 6N): block (i, p) = [I_3, [x (r_i - Y_p)]] if blob i is in body p, else 0 (the K block of Sec. 2.2).
 
-    [x v] = -[v x], so [x (r_i - Y_p)] Omega = Omega x (r_i - Y_p) (Eq. 6).
+    [x v] = -[v x], so [x (r_i - Y_p)] Omega = Omega x (r_i - Y_p) (Eq. rigid_body_cond).
     """
     m = r.shape[0]
     n = Y.shape[0]
@@ -70,7 +70,7 @@ def rigid_basis(K: np.ndarray, n_bodies: int, rel_tol: float = 1e-10) -> np.ndar
 
 
 def saddle_solve(M: np.ndarray, K: np.ndarray, B: np.ndarray, slip: np.ndarray, F: np.ndarray):
-    """Solve [[M, -K], [-K^T, 0]] [lambda; V] = [-slip; -F] by dense LU (Eqs. 10, 14).
+    """Solve [[M, -K], [-K^T, 0]] [lambda; V] = [-slip; -F] by dense LU (Eqs. saddle_point_sys, lin_sys_RMB).
 
     slip is the blob velocity on the right-hand side (the Brownian velocity
     v-breve, plus the background flow where there is one); F stacks [F_p; T_p]
@@ -94,14 +94,14 @@ def saddle_apply(M: np.ndarray, K: np.ndarray, lam: np.ndarray, V: np.ndarray):
 
 
 def body_mobility(M: np.ndarray, K: np.ndarray, B: np.ndarray) -> np.ndarray:
-    """N = (K^T M^-1 K)^-1 (Eq. 12), in the reduced basis: N = B (B^T K^T M^-1 K B)^-1 B^T."""
+    """N = (K^T M^-1 K)^-1 (Eq. body_mob), in the reduced basis: N = B (B^T K^T M^-1 K B)^-1 B^T."""
     KB = K @ B
     G = KB.T @ np.linalg.solve(M, KB)
     return B @ np.linalg.inv(G) @ B.T
 
 
 def lsq_velocity(K: np.ndarray, B: np.ndarray, vb: np.ndarray) -> np.ndarray:
-    """Step 2 (Eq. 18): V = (K^T K)^-1 K^T v-breve, i.e. argmin ||K V - v-breve||."""
+    """Step 2 (Eq. sol_unconst): V = (K^T K)^-1 K^T v-breve, i.e. argmin ||K V - v-breve||."""
     KB = K @ B
     return B @ np.linalg.solve(KB.T @ KB, KB.T @ vb)
 
@@ -115,5 +115,5 @@ def sqrtm_sym(M: np.ndarray) -> np.ndarray:
 
 
 def sqrtm_chol(M: np.ndarray) -> np.ndarray:
-    """Lower Cholesky factor L with L L^T = M (another valid M^(1/2), Eq. 15)."""
+    """Lower Cholesky factor L with L L^T = M (another valid M^(1/2), Eq. v_brown_RMB)."""
     return np.linalg.cholesky(M)

@@ -31,7 +31,7 @@ def rpy_pair(rvec: np.ndarray, a: float, eta: float) -> np.ndarray:
 
 
 def rpy_matrix(r: np.ndarray, a: float, eta: float) -> np.ndarray:
-    """Dense 3M x 3M blob mobility, block (i, j) = rpy_pair(r_i - r_j) (Eq. 5 / Sec. 4.1)."""
+    """Dense 3M x 3M blob mobility, block (i, j) = rpy_pair(r_i - r_j) (Eq. ddof_mob / Sec. 4.1)."""
     r = np.asarray(r, dtype=np.float64)
     m = r.shape[0]
     d = r[:, None, :] - r[None, :, :]

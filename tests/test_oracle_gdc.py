@@ -16,7 +16,7 @@ def _state(templates, body_tmpl, Y, seed=0):
 
 
 def _energy(r, blob_body, A, b, a):
-    """Soft-sphere energy of Eq. (20) with U0 = A b (so that -dU/dr = A e^{-(r-2a)/b})."""
+    """Soft-sphere energy of Eq. (soft_sphere_potential) with U0 = A b (so that -dU/dr = A e^{-(r-2a)/b})."""
     e = 0.0
     for i in range(r.shape[0]):
         for j in range(i + 1, r.shape[0]):
@@ -91,7 +91,7 @@ def test_deterministic_limit_is_forward_euler():
 
 
 def test_rfd_is_unbiased_for_fd():
-    # Eq. (16): averaging the RFD estimator over W-tilde gives the FD divergence of Eq. (15).
+    # Eq. (rfd_div): averaging the RFD estimator over W-tilde gives the FD divergence of Eq. (FD).
     lay, Y, q = _state([shapes.triangle(), shapes.triangle()], [0, 0], [[0, 0, 0], [3.2, 0.8, 0.4]], seed=4)
     p = Params(dt=0.01, rfd_delta=1e-5)
     W = np.random.default_rng(5).standard_normal(3 * lay.n_blobs)

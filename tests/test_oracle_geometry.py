@@ -13,7 +13,7 @@ def _rand_q(rng, n):
 
 
 def test_rotation_matrix_matches_scipy():
-    # Eq. (1) is the standard active rotation of a unit quaternion; scipy is an independent implementation.
+    # Eq. (quaternion_rotation_matrix) is the standard active rotation of a unit quaternion; scipy is an independent implementation.
     rng = np.random.default_rng(1)
     for q in _rand_q(rng, 20):
         R = G.rotation_matrix(q)

@@ -204,7 +204,7 @@ def test_saddle_solve_equals_mobility_and_brute_force():
     a1, a2 = rigid.saddle_apply(M, K, lam, V)
     np.testing.assert_allclose(a1, 0, atol=1e-12)
     np.testing.assert_allclose(a2, -F, atol=1e-12)
-    # Brownian slip: V = N K^T M^-1 v (Eq. 14 and the text after it)
+    # Brownian slip: V = N K^T M^-1 v (Eq. lin_sys_RMB and the text after it)
     vb = rng.standard_normal(3 * lay.n_blobs)
     lam2, V2 = rigid.saddle_solve(M, K, B, vb, np.zeros_like(F))
     np.testing.assert_allclose(V2, N @ K.T @ np.linalg.solve(M, vb), rtol=1e-9, atol=1e-13)
