@@ -5,10 +5,10 @@
  *
  * Model (Sec. 2): N rigid bodies, body p at centre Y_p with unit quaternion
  * q_p = (q0, q1, q2, q3) (scalar first, App. A), made of blobs of radius a
- * placed at r_i = Y_p + R(q_p) b_i (Eq. 1).  Blobs interact through the
+ * placed at r_i = Y_p + R(q_p) b_i (Eq. quaternion_rotation_matrix).  Blobs interact through the
  * unbounded Rotne-Prager-Yamakawa tensor including its overlapping-blob form
  * (Sec. 4.1).  lambda (3 per blob) is the force a blob exerts on the fluid
- * (Eq. 5); V_p = [Ydot_p, Omega_p] (Sec. 2.2); F_p = [force; torque].
+ * (Eq. ddof_mob); V_p = [Ydot_p, Omega_p] (Sec. 2.2); F_p = [force; torque].
  *
  * Memory.  Every array argument named "dev" is device memory owned by the
  * caller; every "host" array is host memory owned by the caller.  The
@@ -54,8 +54,8 @@ typedef enum {
  * restarts from an FP64 residual until that residual meets gmres_tol. */
 typedef enum { GDC_FP64 = 0, GDC_FP32_MIXED = 1 } gdc_precision;
 
-/* Divergence estimate of Sec. 3 step 3: random finite differences (Eq. 16)
- * or finite differences over every body coordinate (Eq. 15). */
+/* Divergence estimate of Sec. 3 step 3: random finite differences (Eq. rfd_div)
+ * or finite differences over every body coordinate (Eq. FD). */
 typedef enum { GDC_DIV_RFD = 0, GDC_DIV_FD = 1 } gdc_divmode;
 
 /* Time integrator: the gDC of Sec. 3, or Euler-Maruyama of App. D (no drift). */
@@ -63,7 +63,7 @@ typedef enum { GDC_SCHEME_GDC = 0, GDC_SCHEME_EM = 1 } gdc_scheme;
 
 typedef struct {
     double eta;            /* fluid viscosity (Sec. 4.2)                               */
-    double kT;             /* thermal energy k_B T (Eq. 4)                             */
+    double kT;             /* thermal energy k_B T (Eq. system_sde)                             */
     double a;              /* blob radius (Sec. 4.1)                                   */
     double dt;             /* time step Delta t (Sec. 3)                               */
     double gmres_tol;      /* relative residual of the mobility solve (Sec. 2.2, 5)   */
@@ -71,12 +71,12 @@ typedef struct {
     int    gmres_restart;  /* Krylov basis size per cycle, 2..100                      */
     double lanczos_tol;    /* relative change of M^(1/2) W between iterations (Sec. 4.1) */
     int    lanczos_max_iter; /* 2..128                                                */
-    double rfd_delta;      /* delta of Eqs. 15-16 (Sec. 6.2 uses 1e-6)                 */
+    double rfd_delta;      /* delta of Eqs. FD and rfd_div (Sec. 6.2 uses 1e-6)                 */
     int    precision;      /* gdc_precision                                            */
     int    divmode;        /* gdc_divmode                                              */
     int    scheme;         /* gdc_scheme                                               */
     double rep_A;          /* soft repulsion amplitude A (force units), 0 = off        */
-    double rep_b;          /* soft repulsion range b (Eq. 20)                          */
+    double rep_b;          /* soft repulsion range b (Eq. soft_sphere_potential)                          */
     double shear_rate;     /* background flow u = (shear_rate * y, 0, 0); 0 = off      */
     unsigned long long seed; /* Philox4x32-10 key of the W and W-tilde draws            */
     int    autotune;       /* 1: gdc_init times the FP32 pair kernel's candidate tilings
@@ -129,8 +129,8 @@ size_t gdc_workspace_bytes(const gdc_params* params, int n_templates, const int*
  * on its blob centroid, which is then Y_p (Sec. 2).  Y (dev, 3 per body) and
  * q (dev, 4 per body, unit) are the caller's state arrays; gdc_step updates
  * them in place.  Precomputes each template's preconditioner block (FP64
- * Cholesky of its RPY block, Sec. 2.2 and the block-diagonal P that follows
- * Eq. 15) on the device.  stream is a cudaStream_t (NULL = default stream). */
+ * Cholesky of its RPY block, Sec. 2.2 and the block-diagonal P described after
+ * Eq. lin_sys_RMB) on the device.  stream is a cudaStream_t (NULL = default stream). */
 gdc_status gdc_init(gdc_ctx** ctx, const gdc_params* params,
                     int n_templates, const int* tmpl_nblobs, const double* tmpl_xyz,
                     int n_susp, const long long* susp_body_off, const int* body_tmpl,
@@ -143,7 +143,7 @@ const char* gdc_last_error(const gdc_ctx* ctx);
  * existing context (sizes and seed are fixed at init). */
 gdc_status gdc_set_params(gdc_ctx* ctx, const gdc_params* params);
 
-/* The rigid multiblob mobility problem at the current state (Eq. 14):
+/* The rigid multiblob mobility problem at the current state (Eq. lin_sys_RMB):
  *   [ M  -K ] [lambda]   [ -vbrev - u_inf ]
  *   [-K^T 0 ] [  V   ] = [ -FT            ]
  * solved by right-preconditioned GMRES with the block-diagonal P (Sec. 2.2).
@@ -168,11 +168,11 @@ gdc_status gdc_set_state(gdc_ctx* ctx, const double* Y_host, const double* q_hos
 /* Blob positions r_i = Y_p + R(q_p) b_i of the current state (dev out, 3 per blob). */
 gdc_status gdc_blob_positions(gdc_ctx* ctx, double* r);
 
-/* u = M lambda at the current state (Eq. 5, RPY of Sec. 4.1); lambda, u dev,
+/* u = M lambda at the current state (Eq. ddof_mob, RPY of Sec. 4.1); lambda, u dev,
  * 3 per blob; precision is a gdc_precision. */
 gdc_status gdc_rpy_apply(gdc_ctx* ctx, int precision, const double* lambda, double* u);
 
-/* The saddle operator [M lambda - K V; -K^T lambda] (Eq. 14) on x = [lambda; V]
+/* The saddle operator [M lambda - K V; -K^T lambda] (Eq. lin_sys_RMB) on x = [lambda; V]
  * stored per suspension as [3 per blob | 6 per body] (dev in, dev out). */
 gdc_status gdc_saddle_apply(gdc_ctx* ctx, int precision, const double* x, double* y);
 
@@ -182,7 +182,7 @@ gdc_status gdc_precond_apply(gdc_ctx* ctx, const double* r, double* z);
 /* vbrev = sqrt(2 kT / dt) M^(1/2) W by Lanczos (Sec. 4.1); W, vbrev dev, 3 per blob. */
 gdc_status gdc_brownian_slip(gdc_ctx* ctx, const double* W, double* vbrev, int* iters, double* err);
 
-/* Step 2 (Eq. 18): calV = (K^T K)^-1 K^T vbrev per body; vbrev dev 3 per blob, calV dev 6 per body. */
+/* Step 2 (Eq. sol_unconst): calV = (K^T K)^-1 K^T vbrev per body; vbrev dev 3 per blob, calV dev 6 per body. */
 gdc_status gdc_lsq_velocity(gdc_ctx* ctx, const double* vbrev, double* calV);
 
 /* Soft repulsion between blobs of different bodies, summed per body (dev out, 6 per body). */

@@ -1,4 +1,4 @@
-// Per-body kernels: the K^T map (Eq. 13), step-2 least squares (Eq. 18 with the
+// Per-body kernels: the K^T map (Eq. force_torque_balance_compact), step-2 least squares (Eq. sol_unconst with the
 // closed-form K^T K of Sec. 5), the block-diagonal preconditioner P of Sec. 2.2, and
 // the per-template FP64 setup of P (Cholesky of the template's RPY block).
 //

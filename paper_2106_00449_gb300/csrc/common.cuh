@@ -159,7 +159,7 @@ namespace gdc {
 // ---- small device helpers -------------------------------------------------
 
 __host__ __device__ inline void quat_to_R(const double* q, double* R) {
-    // Eq. (1) of Sec. 2, q scalar first
+    // Eq. (quaternion_rotation_matrix) of Sec. 2, q scalar first
     const double q0 = q[0], q1 = q[1], q2 = q[2], q3 = q[3];
     R[0] = 1.0 - 2.0 * q2 * q2 - 2.0 * q3 * q3;
     R[1] = 2.0 * (q1 * q2 - q3 * q0);

@@ -1,6 +1,6 @@
 // Rigid-body state kernels: blob positions (Sec. 2), Philox draws (Sec. 3 step 1),
-// the RFD/FD perturbations and divergence (Sec. 3 step 3, Eqs. 15-16), the mid-step
-// and final updates (Sec. 3 steps 4 and 6), and the right-hand side of Eq. (19).
+// the RFD/FD perturbations and divergence (Sec. 3 step 3, Eqs. FD and rfd_div), the mid-step
+// and final updates (Sec. 3 steps 4 and 6), and the right-hand side of Eq. (step5).
 #include "common.cuh"
 
 namespace gdc {
@@ -106,7 +106,7 @@ void launch_normals(gdc_ctx* c, unsigned long long step, int stream, double* out
 
 // ---- perturbations and updates -----------------------------------------------
 
-// RFD state of Eq. (16) with the footnote's length scale: Y + delta L_p W~_t, exp(delta W~_r) * q.
+// RFD state of Eq. (rfd_div) with the footnote's length scale: Y + delta L_p W~_t, exp(delta W~_r) * q.
 __global__ void k_perturb(int NB, const double* __restrict__ Y, const double* __restrict__ q,
                           const double* __restrict__ Wt, const double* __restrict__ L, double delta,
                           double* __restrict__ Yo, double* __restrict__ qo) {
@@ -125,7 +125,7 @@ void launch_perturb(gdc_ctx* c, const double* Y, const double* q, const double* 
     ++c->n_launch, k_perturb<<<ceil_div(c->NB, 128), 128, 0, c->stream>>>(c->NB, Y, q, Wt, c->body_L, delta, Yo, qo);
 }
 
-// FD state of Eq. (15): coordinate `coord` of the body with local index p_local of every suspension.
+// FD state of Eq. (FD): coordinate `coord` of the body with local index p_local of every suspension.
 __global__ void k_perturb_one(int NB, const double* __restrict__ Y, const double* __restrict__ q,
                               const int* __restrict__ body_susp, const long long* __restrict__ susp_body_off,
                               const double* __restrict__ L, int p_local, int coord, double delta,
@@ -232,7 +232,7 @@ void launch_nu_from_div(gdc_ctx* c, const double* div, double dt, double* nu) {
 
 // ---- right-hand side and solution layout -----------------------------------------
 
-// b = [-vbrev - u_inf(r); -FT] in the saddle layout (Eq. 19, with the background flow reading).
+// b = [-vbrev - u_inf(r); -FT] in the saddle layout (Eq. step5, with the background flow reading).
 __global__ void k_rhs_blob(int NBL, const int* __restrict__ blob_gm, const double* __restrict__ vb,
                            const double* __restrict__ r, double shear, double* __restrict__ b) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;

@@ -1,5 +1,5 @@
 // Batched Krylov solvers of the mobility problem (Sec. 2.2): right-preconditioned
-// GMRES on the saddle-point system of Eq. (14) with the block-diagonal P, and the
+// GMRES on the saddle-point system of Eq. (lin_sys_RMB) with the block-diagonal P, and the
 // Lanczos approximation of M^(1/2) W (Sec. 4.1, Chow & Saad).  Every suspension has its
 // own Krylov space; vectors of all suspensions are stored back to back and reductions
 // are segmented per suspension.  Reductions are two-pass (per-chunk partials, then a

@@ -1,5 +1,5 @@
-// On-the-fly tiled N-body kernels: the RPY product u = M lambda (Sec. 4.1, Eq. 5) in
-// FP32 and FP64, and the soft blob repulsion (Eq. 20 form).  Sources are staged in
+// On-the-fly tiled N-body kernels: the RPY product u = M lambda (Sec. 4.1, Eq. ddof_mob) in
+// FP32 and FP64, and the soft blob repulsion (Eq. soft_sphere_potential form).  Sources are staged in
 // shared memory tile by tile; each thread owns TPT targets.  Work is split into
 // (target tile x source chunk) items so that a launch fills every SM several times
 // over; chunk partial sums are added in FP64, in chunk order, by the epilogue.
@@ -357,7 +357,7 @@ __global__ void k_rpy_epilogue(int NBL, const P* __restrict__ part, const int* _
         y[3 * i + 2] = uz;
         return;
     }
-    // saddle operator: M lambda - K V, K V = U_p + Omega_p x (r_i - Y_p)  (Eqs. 6-9)
+    // saddle operator: M lambda - K V, K V = U_p + Omega_p x (r_i - Y_p)  (Eq. rigid_body_cond)
     const int p = blob_body[i];
     const double* V = x + body_gm[p];
     const double dx = r[3 * i] - Yc[3 * p], dy = r[3 * i + 1] - Yc[3 * p + 1], dz = r[3 * i + 2] - Yc[3 * p + 2];
