@@ -196,6 +196,32 @@ gdc_status gdc_draw_normals(gdc_ctx* ctx, unsigned long long step, int stream, d
  * vectors of gdc_saddle_apply / gdc_precond_apply (host out, n_susp + 1). */
 gdc_status gdc_saddle_offsets(const gdc_ctx* ctx, long long* off);
 
+/* ---- allocation-free RPY product ------------------------------------------
+ *
+ * For callers that cannot allocate device memory: for example a host program
+ * that hands out all device memory from its own fixed pool and forbids any
+ * other allocation, or a latency-critical loop that cannot afford the
+ * device-wide synchronisation that cudaMalloc / cudaFree may cause.  The
+ * paper has no counterpart: this entry point only exists for such callers.
+ *
+ * u = M lambda for ONE suspension of n_blobs free blobs (no rigid bodies):
+ * the unbounded RPY product with the overlapping-blob form, pair terms in
+ * FP32 (the library's FP32 pair kernel), chunk sums and the self term in FP64.
+ * r (dev, 3 doubles per blob, lab positions), lambda (dev, 3 per blob) and
+ * u (dev out, 3 per blob) are the caller's; stream is a cudaStream_t.
+ *
+ * It allocates nothing: its scratch (about 4.8 MB) is a fixed device array
+ * inside the library, present on every GPU that loads the library until the
+ * process exits.  The first call on a device looks up that array's device
+ * address, so make the first call on each device before any stream capture.
+ * n_blobs above GDC_NOALLOC_MAX_BLOBS is rejected with GDC_ERR_INVALID_ARG
+ * (message in gdc_last_error(NULL)).  Every call uses the same array: calls
+ * that overlap on the GPU (different streams, or different host threads on
+ * one device) race and must be serialised by the caller. */
+#define GDC_NOALLOC_MAX_BLOBS 16384
+gdc_status gdc_rpy_apply_noalloc(const double* r, const double* lambda, double* u, int n_blobs,
+                                 double a, double eta, void* stream);
+
 /* ---- instrumentation ---------------------------------------------------- */
 
 typedef struct {

@@ -32,8 +32,10 @@ EXPORTS = [
     "gdc_mobility_solve", "gdc_step", "gdc_set_trace", "gdc_get_state", "gdc_set_state",
     "gdc_blob_positions", "gdc_rpy_apply", "gdc_saddle_apply", "gdc_precond_apply",
     "gdc_brownian_slip", "gdc_lsq_velocity", "gdc_forces", "gdc_draw_normals", "gdc_saddle_offsets",
-    "gdc_profile", "gdc_profile_read",
+    "gdc_profile", "gdc_profile_read", "gdc_rpy_apply_noalloc",
 ]
+
+NOALLOC_MAX_BLOBS = 16384   # GDC_NOALLOC_MAX_BLOBS of include/gdc.h
 
 
 class GdcError(RuntimeError):
@@ -137,6 +139,7 @@ def load_library() -> ctypes.CDLL:
     lib.gdc_saddle_offsets.argtypes = [vp, llp]
     lib.gdc_profile.argtypes = [vp, ctypes.c_int]
     lib.gdc_profile_read.argtypes = [vp, ctypes.POINTER(_Profile)]
+    lib.gdc_rpy_apply_noalloc.argtypes = [dp, dp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, vp]
     for name in EXPORTS:
         if name not in ("gdc_workspace_bytes", "gdc_destroy", "gdc_last_error"):
             getattr(lib, name).restype = ctypes.c_int
@@ -359,6 +362,25 @@ class Context:
         out = self._dev(n)
         self._check(self.lib.gdc_draw_normals(self._h, ctypes.c_ulonglong(step), stream, _dptr(out)))
         return out
+
+
+def rpy_apply_noalloc(r, lam, a: float = 1.0, eta: float = 1.0, out=None, stream=None):
+    """u = M lambda for one suspension of free blobs through gdc_rpy_apply_noalloc.
+
+    For callers that must not allocate device memory on the library's behalf: the
+    library uses only its fixed internal scratch array.  r, lam: contiguous float64 CUDA
+    tensors with 3 values per blob; out (optional) receives u.  Returns out.
+    """
+    import torch
+    lib = load_library()
+    n = r.numel() // 3
+    if out is None:
+        out = torch.empty_like(lam)
+    s = stream if stream is not None else torch.cuda.current_stream(r.device)
+    st = lib.gdc_rpy_apply_noalloc(_dptr(r), _dptr(lam), _dptr(out), n, a, eta, ctypes.c_void_p(s.cuda_stream))
+    if st != 0:
+        raise GdcError(st, lib.gdc_last_error(None).decode())
+    return out
 
 
 def context_from_workload(wl, **overrides) -> Context:

@@ -569,7 +569,7 @@ gdc_status gdc_profile_read(gdc_ctx* c, gdc_profile_info* out) {
     return GDC_OK;
 }
 
-const char* gdc_last_error(const gdc_ctx* c) { return c ? c->err.c_str() : "NULL context"; }
+const char* gdc_last_error(const gdc_ctx* c) { return c ? c->err.c_str() : noalloc_last_error(); }
 
 gdc_status gdc_set_params(gdc_ctx* c, const gdc_params* p) {
     if (!c) return GDC_ERR_INVALID_ARG;

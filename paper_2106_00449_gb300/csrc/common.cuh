@@ -235,6 +235,7 @@ void launch_forces_pair(gdc_ctx* c, int prec, double* fblob);
 void build_mv_items(gdc_ctx* c, int tpt, double waves);
 gdc_status autotune_pair_kernel(gdc_ctx* c);
 void plan_mv_capacity(gdc_ctx* c);
+const char* noalloc_last_error();
 
 // body.cu
 void launch_body_KT(gdc_ctx* c, const double* x, int x_gm, double* y, int y_gm, double scale);

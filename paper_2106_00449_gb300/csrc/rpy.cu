@@ -630,3 +630,147 @@ gdc_status autotune_pair_kernel(gdc_ctx* c) {
 }
 
 }  // namespace gdc
+
+// ---- allocation-free RPY product (gdc_rpy_apply_noalloc) ------------------------------
+//
+// For callers that cannot allocate device memory.  All scratch of this variant (packed
+// sources, chunk partial sums, the work list) lives in one file-scope device array of
+// fixed size, so the call allocates nothing; every GPU that loads the library holds the
+// array until the process exits.  It reuses the FP32 pair kernel above on one suspension
+// of free blobs (every blob is its own body, so only the self pair is skipped by the pair
+// kernel and its term I/(6 pi eta a) is added in the epilogue).
+
+#include <mutex>
+
+#define GDC_NOALLOC_MAX_CHUNKS 16
+#define GDC_NOALLOC_TILE 256   // targets per work item (two per thread)
+
+namespace gdc {
+
+struct NoallocScratch {
+    float4 spos[GDC_NOALLOC_MAX_BLOBS];
+    float4 slam[GDC_NOALLOC_MAX_BLOBS];
+    float4 part[GDC_NOALLOC_MAX_CHUNKS * GDC_NOALLOC_MAX_BLOBS];
+    MvItem items[(GDC_NOALLOC_MAX_BLOBS / GDC_NOALLOC_TILE) * GDC_NOALLOC_MAX_CHUNKS];
+    long long body_blob_off[GDC_NOALLOC_MAX_BLOBS + 1];
+    long long susp_blob_off[2];
+};
+
+static __device__ __align__(256) NoallocScratch g_noalloc_scratch;
+
+// Positions relative to the blob centroid (FP32), lambda, identity body table, work list.
+__global__ void k_noalloc_prepare(NoallocScratch* __restrict__ sc, const double* __restrict__ r,
+                                  const double* __restrict__ lam, int n, int nk, int csz) {
+    __shared__ double cen[3];
+    if (threadIdx.x < 3) {
+        double acc = 0.0;
+        for (int i = 0; i < n; ++i) acc += r[3 * i + threadIdx.x];
+        cen[threadIdx.x] = acc / n;
+    }
+    __syncthreads();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += gridDim.x * blockDim.x) {
+        sc->body_blob_off[i] = i;
+        if (i == n) continue;
+        sc->spos[i] = make_float4((float)(r[3 * i] - cen[0]), (float)(r[3 * i + 1] - cen[1]),
+                                  (float)(r[3 * i + 2] - cen[2]), __int_as_float(i));
+        sc->slam[i] = make_float4((float)lam[3 * i], (float)lam[3 * i + 1], (float)lam[3 * i + 2], 0.f);
+    }
+    const int ntile = (n + GDC_NOALLOC_TILE - 1) / GDC_NOALLOC_TILE;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < ntile * nk; b += gridDim.x * blockDim.x) {
+        MvItem it{};
+        it.s = 0;
+        it.t0 = (b / nk) * GDC_NOALLOC_TILE;
+        it.k = b % nk;
+        it.j0 = it.k * csz;
+        it.j1 = min(n, (it.k + 1) * csz);
+        sc->items[b] = it;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        sc->susp_blob_off[0] = 0;
+        sc->susp_blob_off[1] = n;
+    }
+}
+
+// u_i = c0 (sum of chunk partials + (4/(3a)) lambda_i)   (self term M_ii = I/(6 pi eta a))
+__global__ void k_noalloc_epilogue(const NoallocScratch* __restrict__ sc, const double* __restrict__ lam, int n, int nk,
+                                   double c0, double self, double* __restrict__ u) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double x = 0.0, y = 0.0, z = 0.0;
+    for (int k = 0; k < nk; ++k) {
+        const float4 v = sc->part[(long long)k * GDC_NOALLOC_MAX_BLOBS + i];
+        x += v.x;
+        y += v.y;
+        z += v.z;
+    }
+    u[3 * i] = c0 * (x + self * lam[3 * i]);
+    u[3 * i + 1] = c0 * (y + self * lam[3 * i + 1]);
+    u[3 * i + 2] = c0 * (z + self * lam[3 * i + 2]);
+}
+
+// Device address of the scratch array and SM count, looked up once per device.
+static std::mutex g_noalloc_mu;
+static NoallocScratch* g_noalloc_ptr[128] = {};
+static int g_noalloc_sms[128] = {};
+static thread_local std::string g_noalloc_err;
+
+const char* noalloc_last_error() { return g_noalloc_err.c_str(); }
+
+static gdc_status noalloc_fail(gdc_status s, const std::string& m) {
+    g_noalloc_err = m;
+    return s;
+}
+
+}  // namespace gdc
+
+extern "C" gdc_status gdc_rpy_apply_noalloc(const double* r, const double* lambda, double* u, int n_blobs, double a,
+                                            double eta, void* stream) {
+    using namespace gdc;
+    if (!r || !lambda || !u) return noalloc_fail(GDC_ERR_INVALID_ARG, "gdc_rpy_apply_noalloc: NULL pointer");
+    if (n_blobs < 1 || n_blobs > GDC_NOALLOC_MAX_BLOBS)
+        return noalloc_fail(GDC_ERR_INVALID_ARG, "gdc_rpy_apply_noalloc: n_blobs must be in [1, " +
+                                                     std::to_string(GDC_NOALLOC_MAX_BLOBS) + "], got " +
+                                                     std::to_string(n_blobs));
+    if (!(a > 0.0) || !(eta > 0.0)) return noalloc_fail(GDC_ERR_INVALID_ARG, "gdc_rpy_apply_noalloc: a and eta must be > 0");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= 128)
+        return noalloc_fail(GDC_ERR_CUDA, std::string("gdc_rpy_apply_noalloc: no usable device: ") + cudaGetErrorString(e));
+    NoallocScratch* sc;
+    int sms;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {   // first call on this device: look up the array's device address
+            void* p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess)
+                return noalloc_fail(GDC_ERR_CUDA, std::string("gdc_rpy_apply_noalloc: cudaGetSymbolAddress failed: ") +
+                                                      cudaGetErrorString(e));
+            int v = 0;
+            if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 152;
+            g_noalloc_sms[dev] = v;
+            g_noalloc_ptr[dev] = (NoallocScratch*)p;
+        }
+        sc = g_noalloc_ptr[dev];
+        sms = g_noalloc_sms[dev];
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int ntile = (n_blobs + GDC_NOALLOC_TILE - 1) / GDC_NOALLOC_TILE;
+    int nk = std::max(1, std::min(GDC_NOALLOC_MAX_CHUNKS, (8 * sms + ntile - 1) / ntile));
+    nk = std::min(nk, std::max(1, (n_blobs + 255) / 256));
+    int csz = (n_blobs + nk - 1) / nk;
+    csz = (csz + 31) / 32 * 32;
+    nk = (n_blobs + csz - 1) / csz;
+    k_noalloc_prepare<<<std::min(1024, (n_blobs + 255) / 256 + 1), 256, 0, st>>>(sc, r, lambda, n_blobs, nk, csz);
+    RpyConst32 k{(float)(2.0 * a * a / 3.0), (float)(2.0 * a * a), (float)(4.0 * a * a), (float)(4.0 / (3.0 * a)),
+                 (float)(9.0 / (32.0 * a)), (float)(1.0 / (8.0 * a * a))};
+    // the pair kernel addresses partial sums as part[k * NBL + i]: pass the array's row length
+    k_rpy32<1><<<ntile * nk, 128, 0, st>>>(sc->items, sc->susp_blob_off, sc->spos, sc->slam, sc->body_blob_off,
+                                             sc->part, GDC_NOALLOC_MAX_BLOBS, k);
+    k_noalloc_epilogue<<<(n_blobs + 255) / 256, 256, 0, st>>>(sc, lambda, n_blobs, nk,
+                                                              1.0 / (8.0 * 3.141592653589793 * eta), 4.0 / (3.0 * a), u);
+    e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return noalloc_fail(GDC_ERR_CUDA, std::string("gdc_rpy_apply_noalloc: launch failed: ") + cudaGetErrorString(e));
+    return GDC_OK;
+}
