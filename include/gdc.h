@@ -54,6 +54,12 @@ typedef enum {
  * restarts from an FP64 residual until that residual meets gmres_tol. */
 typedef enum { GDC_FP64 = 0, GDC_FP32_MIXED = 1 } gdc_precision;
 
+/* Precision of the accurate product that GDC_FP32_MIXED checks its residuals with,
+ * accepted by gdc_rpy_apply / gdc_saddle_apply: pairs of different bodies in
+ * double-float arithmetic (two floats, about 48 significant bits) on the FP32 pipes,
+ * same-body blocks in FP64. */
+#define GDC_DF64_RESIDUAL 2
+
 /* Divergence estimate of Sec. 3 step 3: random finite differences (Eq. rfd_div)
  * or finite differences over every body coordinate (Eq. FD). */
 typedef enum { GDC_DIV_RFD = 0, GDC_DIV_FD = 1 } gdc_divmode;
@@ -234,6 +240,8 @@ typedef struct {
     int    targets_per_thread;          /* pair-kernel tiling in use                     */
     double work_waves;                  /* work items per launch / (4 x SM count)        */
     double autotune_ms;                 /* fastest FP32 product found at init (0: none)  */
+    unsigned long long rpydf_launches;  /* double-float residual pair-kernel launches     */
+    double rpydf_ms;                    /* their summed CUDA-event durations              */
 } gdc_profile_info;
 
 /* Reset the counters; enable != 0 also brackets every pair-kernel launch with

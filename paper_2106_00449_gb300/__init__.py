@@ -69,7 +69,8 @@ class _Profile(ctypes.Structure):
                 ("rpy64_launches", ctypes.c_ulonglong), ("force_launches", ctypes.c_ulonglong),
                 ("rpy32_ms", ctypes.c_double), ("rpy64_ms", ctypes.c_double), ("force_ms", ctypes.c_double),
                 ("pairs_per_product", ctypes.c_double), ("targets_per_thread", ctypes.c_int),
-                ("work_waves", ctypes.c_double), ("autotune_ms", ctypes.c_double)]
+                ("work_waves", ctypes.c_double), ("autotune_ms", ctypes.c_double),
+                ("rpydf_launches", ctypes.c_ulonglong), ("rpydf_ms", ctypes.c_double)]
 
 
 class _Trace(ctypes.Structure):

@@ -82,7 +82,7 @@ static const char* build_host_layout(gdc_ctx* c, const gdc_params* p, int n_temp
         if (susp_body_off[s + 1] < susp_body_off[s]) return "susp_body_off must be non-decreasing";
     const long long NB = susp_body_off[n_susp];
     if (NB < 1) return "no bodies";
-    if (NB > (1LL << 28)) return "too many bodies";
+    if (NB > (1LL << 24)) return "too many bodies (at most 2^24)";
     if (!body_tmpl) return "body_tmpl is NULL";
     c->p = *p;
     c->T = n_templates;
@@ -543,7 +543,7 @@ gdc_status gdc_profile(gdc_ctx* c, int enable) {
     }
     c->prof_on = enable ? 1 : 0;
     c->n_launch = 0;
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < 4; ++k) {
         c->prof_ms[k] = 0.0;
         c->prof_count[k] = 0;
     }
@@ -562,6 +562,8 @@ gdc_status gdc_profile_read(gdc_ctx* c, gdc_profile_info* out) {
     out->rpy32_ms = c->prof_ms[0];
     out->rpy64_ms = c->prof_ms[1];
     out->force_ms = c->prof_ms[2];
+    out->rpydf_launches = c->prof_count[3];
+    out->rpydf_ms = c->prof_ms[3];
     out->pairs_per_product = c->pair_evals_per_matvec;
     out->targets_per_thread = c->mv_tpt;
     out->work_waves = c->mv_waves;
@@ -650,7 +652,8 @@ gdc_status gdc_blob_positions(gdc_ctx* c, double* r) {
 
 gdc_status gdc_rpy_apply(gdc_ctx* c, int precision, const double* lam, double* u) {
     if (!c || !lam || !u) return c ? fail(c, GDC_ERR_INVALID_ARG, "NULL pointer") : GDC_ERR_INVALID_ARG;
-    if (precision != GDC_FP64 && precision != GDC_FP32_MIXED) return fail(c, GDC_ERR_INVALID_ARG, "unknown precision");
+    if (precision != GDC_FP64 && precision != GDC_FP32_MIXED && precision != GDC_DF64_RESIDUAL)
+        return fail(c, GDC_ERR_INVALID_ARG, "unknown precision");
     load_at(c, c->Y, c->q);
     rpy_op(c, precision, lam, u);
     return cuda_check(c, cudaStreamSynchronize(c->stream), "rpy apply");
@@ -658,7 +661,8 @@ gdc_status gdc_rpy_apply(gdc_ctx* c, int precision, const double* lam, double* u
 
 gdc_status gdc_saddle_apply(gdc_ctx* c, int precision, const double* x, double* y) {
     if (!c || !x || !y) return c ? fail(c, GDC_ERR_INVALID_ARG, "NULL pointer") : GDC_ERR_INVALID_ARG;
-    if (precision != GDC_FP64 && precision != GDC_FP32_MIXED) return fail(c, GDC_ERR_INVALID_ARG, "unknown precision");
+    if (precision != GDC_FP64 && precision != GDC_FP32_MIXED && precision != GDC_DF64_RESIDUAL)
+        return fail(c, GDC_ERR_INVALID_ARG, "unknown precision");
     load_at(c, c->Y, c->q);
     saddle_op(c, precision, x, y);
     return cuda_check(c, cudaStreamSynchronize(c->stream), "saddle apply");

@@ -22,6 +22,10 @@
 
 #include "../../include/gdc.h"
 
+// internal precision of the accurate residual product in FP32-mixed mode: pairs of
+// different bodies in double-float arithmetic on the FP32 pipes, same-body blocks in FP64
+#define GDC_PREC_DF64 2
+
 #define GDC_MAX_RESTART 100
 #define GDC_MAX_LANCZOS 128
 #define GDC_MAX_TMPL_BLOBS 340   // 3n <= 1020 rows of a template block
@@ -148,10 +152,10 @@ struct gdc_ctx {
     unsigned long long n_launch = 0;
     int prof_on = 0;
     std::vector<cudaEvent_t> prof_ev;      // start/stop pairs
-    std::vector<int> prof_kind;            // 0 = FP32 RPY, 1 = FP64 RPY, 2 = forces
+    std::vector<int> prof_kind;            // 0 = FP32 RPY, 1 = FP64 RPY, 2 = forces, 3 = df64 RPY
     int prof_used = 0;
-    double prof_ms[3] = {0, 0, 0};
-    unsigned long long prof_count[3] = {0, 0, 0};
+    double prof_ms[4] = {0, 0, 0, 0};
+    unsigned long long prof_count[4] = {0, 0, 0, 0};
 };
 
 namespace gdc {

@@ -360,7 +360,8 @@ gdc_status gmres_solve(gdc_ctx* c, const double* b, double* x, gdc_solve_info* i
         launch_precond(c, c->gm_w, c->gm_z);
         ++c->n_launch, k_axpy_chunks<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, 1.0, c->gm_z, x);
         // FP64 residual r = b - A x
-        saddle_op(c, GDC_FP64, x, c->gm_w);
+        // accurate residual: FP64 in FP64 mode; double-float pairs + FP64 same-body blocks in mixed mode
+        saddle_op(c, prec == GDC_FP32_MIXED ? GDC_PREC_DF64 : GDC_FP64, x, c->gm_w);
         inf.matvecs_fp64++;
         ++c->n_launch, k_sub_chunks<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, b, c->gm_w, c->gm_r);
         if ((st = cuda_check(c, cudaGetLastError(), "GMRES launch")) != GDC_OK) return st;

@@ -223,6 +223,146 @@ __global__ void __launch_bounds__(128) k_rpy32(const MvItem* __restrict__ items,
     }
 }
 
+// ---- double-float (df64) RPY pair kernel for accurate residuals ----------------------
+//
+// GB300 runs FP64 at a small fraction of its FP32 rate, so the accurate product that
+// the mixed-precision mobility solve checks its residual with evaluates the pairs of
+// different bodies in double-float arithmetic on the FP32 pipes: a value is an
+// unevaluated sum hi + lo of two floats (about 48 significant bits).  The error-free
+// transformations are Knuth's two-sum, Dekker's fast two-sum and the FMA-based exact
+// product.  Same-body pairs are skipped (added exactly in FP64 by k_intra_body).
+
+struct df { float h, l; };
+
+// The _rn intrinsics are never fused into FMAs by the compiler, which the error-free
+// transformations rely on.
+__device__ __forceinline__ df df_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ df df_fast(float a, float b) {   // |a| >= |b|
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ df df_add(df x, df y) {
+    df s = df_two_sum(x.h, y.h);
+    return df_fast(s.h, __fadd_rn(s.l, __fadd_rn(x.l, y.l)));
+}
+__device__ __forceinline__ df df_sub(df x, df y) { return df_add(x, df{-y.h, -y.l}); }
+__device__ __forceinline__ df df_mul(df x, df y) {
+    const float p = __fmul_rn(x.h, y.h);
+    float e = fmaf(x.h, y.h, -p);                 // exact rounding error of the product
+    e = fmaf(x.h, y.l, fmaf(x.l, y.h, e));
+    return df_fast(p, e);
+}
+__device__ __forceinline__ df df_from(double v) {
+    const float h = (float)v;
+    return {h, (float)(v - (double)h)};
+}
+__device__ __forceinline__ double df_to(df x) { return (double)x.h + (double)x.l; }
+
+// 1/sqrt(x) to double-float accuracy: one Newton step from the FP32 estimate,
+// y1 = y (1 - (x y^2 - 1)/2), with the residual x y^2 - 1 formed from exact products.
+__device__ __forceinline__ df df_rsqrt(df x) {
+    const float y = rsqrtf(x.h);
+    const float yy = __fmul_rn(y, y), yye = fmaf(y, y, -yy);
+    const float h = __fadd_rn(fmaf(x.h, yy, -1.f), fmaf(x.h, yye, __fmul_rn(x.l, yy)));
+    return df_fast(y, __fmul_rn(__fmul_rn(-0.5f, y), h));
+}
+
+struct RpyConstDF {
+    df c23, c2, cA, c9, cB;
+    double four_a2;
+};
+
+template <int TPT>
+__global__ void __launch_bounds__(128) k_rpy_df(const MvItem* __restrict__ items, const long long* __restrict__ susp_blob_off,
+                                                const double4* __restrict__ spos, const double4* __restrict__ slam,
+                                                double4* __restrict__ part, int NBL, RpyConstDF k) {
+    __shared__ float4 sh[4 * MV_TILE];
+    const MvItem it = items[blockIdx.x];
+    const long long b0 = susp_blob_off[it.s];
+    const int ns = (int)(susp_blob_off[it.s + 1] - b0);
+    df xt[TPT], yt[TPT], zt[TPT], ux[TPT], uy[TPT], uz[TPT];
+    float bt[TPT];
+#pragma unroll
+    for (int t = 0; t < TPT; ++t) {
+        const double4 p = spos[b0 + min(it.t0 + (int)threadIdx.x + t * 128, ns - 1)];
+        xt[t] = df_from(p.x);
+        yt[t] = df_from(p.y);
+        zt[t] = df_from(p.z);
+        bt[t] = (float)p.w;
+        ux[t] = uy[t] = uz[t] = df{0.f, 0.f};
+    }
+    const df one{1.f, 0.f};
+    for (int j0 = it.j0; j0 < it.j1; j0 += MV_TILE) {
+        const int n = min(MV_TILE, it.j1 - j0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < n; e += 128) {
+            const double4 ps = spos[b0 + j0 + e];
+            const double4 ls = slam[b0 + j0 + e];
+            const df x = df_from(ps.x), y = df_from(ps.y), z = df_from(ps.z);
+            const df lx = df_from(ls.x), ly = df_from(ls.y), lz = df_from(ls.z);
+            sh[4 * e] = make_float4(x.h, y.h, z.h, (float)ps.w);
+            sh[4 * e + 1] = make_float4(x.l, y.l, z.l, 0.f);
+            sh[4 * e + 2] = make_float4(lx.h, ly.h, lz.h, 0.f);
+            sh[4 * e + 3] = make_float4(lx.l, ly.l, lz.l, 0.f);
+        }
+        __syncthreads();
+        for (int j = 0; j < n; ++j) {
+            const float4 s0 = sh[4 * j], s1 = sh[4 * j + 1], s2 = sh[4 * j + 2], s3 = sh[4 * j + 3];
+            const df lx{s2.x, s3.x}, ly{s2.y, s3.y}, lz{s2.z, s3.z};
+#pragma unroll
+            for (int t = 0; t < TPT; ++t) {
+                if (s0.w == bt[t]) continue;   // same body: exact FP64 block elsewhere
+                const df dx = df_sub(df{s0.x, s1.x}, xt[t]);
+                const df dy = df_sub(df{s0.y, s1.y}, yt[t]);
+                const df dz = df_sub(df{s0.z, s1.z}, zt[t]);
+                const df r2 = df_add(df_add(df_mul(dx, dx), df_mul(dy, dy)), df_mul(dz, dz));
+                const df ri = df_rsqrt(r2);
+                df A, B;
+                if ((double)r2.h + (double)r2.l >= k.four_a2) {
+                    const df ri2 = df_mul(ri, ri);
+                    const df ri3 = df_mul(ri2, ri);
+                    A = df_add(ri, df_mul(k.c23, ri3));
+                    B = df_mul(ri3, df_sub(one, df_mul(k.c2, ri2)));
+                } else {   // overlapping blobs of different bodies (r > 0 for distinct blobs)
+                    const df r = df_mul(r2, ri);
+                    A = df_mul(k.cA, df_sub(one, df_mul(k.c9, r)));
+                    B = df_mul(k.cB, ri);
+                }
+                const df dl = df_add(df_add(df_mul(dx, lx), df_mul(dy, ly)), df_mul(dz, lz));
+                const df s = df_mul(B, dl);
+                ux[t] = df_add(ux[t], df_add(df_mul(A, lx), df_mul(s, dx)));
+                uy[t] = df_add(uy[t], df_add(df_mul(A, ly), df_mul(s, dy)));
+                uz[t] = df_add(uz[t], df_add(df_mul(A, lz), df_mul(s, dz)));
+            }
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < TPT; ++t) {
+        const int ti = it.t0 + threadIdx.x + t * 128;
+        if (ti < ns) part[(long long)it.k * NBL + b0 + ti] = make_double4(df_to(ux[t]), df_to(uy[t]), df_to(uz[t]), 0.0);
+    }
+}
+
+static df df_from_host(double v) {
+    const float h = (float)v;
+    return {h, (float)(v - (double)h)};
+}
+
+static RpyConstDF df_constants(double a) {
+    RpyConstDF k;
+    k.c23 = df_from_host(2.0 * a * a / 3.0);
+    k.c2 = df_from_host(2.0 * a * a);
+    k.cA = df_from_host(4.0 / (3.0 * a));
+    k.c9 = df_from_host(9.0 / (32.0 * a));
+    k.cB = df_from_host(1.0 / (8.0 * a * a));
+    k.four_a2 = 4.0 * a * a;
+    return k;
+}
+
 // ---- FP64 RPY pair kernel -----------------------------------------------------
 
 template <int TPT>
@@ -293,7 +433,7 @@ __global__ void __launch_bounds__(128) k_rpy64(const MvItem* __restrict__ items,
 }
 
 void launch_rpy(gdc_ctx* c, int prec) {
-    const int pe = prof_begin(c, prec == GDC_FP32_MIXED ? 0 : 1);
+    const int pe = prof_begin(c, prec == GDC_FP32_MIXED ? 0 : (prec == GDC_PREC_DF64 ? 3 : 1));
     if (prec == GDC_FP32_MIXED) {
         const double a = c->p.a;
         RpyConst32 k{(float)(2.0 * a * a / 3.0), (float)(2.0 * a * a), (float)(4.0 * a * a),
@@ -307,6 +447,14 @@ void launch_rpy(gdc_ctx* c, int prec) {
             ++c->n_launch, k_rpy32<1><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off, c->spos,
                                                                             c->slam, c->body_blob_off,
                                                                             (float4*)c->mv_part, c->NBL, k);
+    } else if (prec == GDC_PREC_DF64) {
+        const RpyConstDF k = df_constants(c->p.a);
+        if (c->mv_tpt == 4)
+            ++c->n_launch, k_rpy_df<4><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off, c->spos64,
+                                                                             c->slam64, (double4*)c->mv_part, c->NBL, k);
+        else
+            ++c->n_launch, k_rpy_df<2><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off, c->spos64,
+                                                                             c->slam64, (double4*)c->mv_part, c->NBL, k);
     } else {
         if (c->mv_tpt == 1)
             ++c->n_launch, k_rpy64<1><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off, c->spos64, c->slam64,
@@ -383,8 +531,8 @@ static void launch_epilogue(gdc_ctx* c, int prec, double c0, const double* x, do
 
 void launch_rpy_epilogue(gdc_ctx* c, int prec, const double* x, double* y, int gm_layout) {
     launch_epilogue(c, prec, 1.0 / (8.0 * 3.141592653589793 * c->p.eta), x, y, gm_layout);
-    // the FP32 pair kernel leaves out same-body pairs: add each body's block in FP64
-    if (prec == GDC_FP32_MIXED) launch_intra_body(c, x, y, gm_layout);
+    // the FP32 and df64 pair kernels leave out same-body pairs: add each body's block in FP64
+    if (prec == GDC_FP32_MIXED || prec == GDC_PREC_DF64) launch_intra_body(c, x, y, gm_layout);
 }
 
 // ---- soft repulsion between blobs of different bodies --------------------------

@@ -68,9 +68,10 @@ def test_blob_positions(lib, wl_mix):
                                rtol=0, atol=1e-12)
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 @pytest.mark.parametrize("which", ["mix", "batch"])
 def test_rpy_apply(lib, wl_mix, wl_batch, prec, which):
+    # prec 2: the double-float product the FP32-mixed solve checks its residuals with
     wl = wl_mix if which == "mix" else wl_batch
     ctx = ctx_for(lib, wl)
     rng = np.random.default_rng(11)
@@ -84,6 +85,9 @@ def test_rpy_apply(lib, wl_mix, wl_batch, prec, which):
         ref = M @ lam[3 * a:3 * b]
         if prec == 0:
             assert rel(u[3 * a:3 * b], ref) < 1e-13
+        elif prec == 2:
+            assert rel(u[3 * a:3 * b], ref) < 1e-11
+            assert np.abs(u[3 * a:3 * b] - ref).max() < 1e-11 * np.abs(ref).max()
         else:
             assert rel(u[3 * a:3 * b], ref) < 2e-6
             assert np.abs(u[3 * a:3 * b] - ref).max() < 1e-5 * np.abs(ref).max()
