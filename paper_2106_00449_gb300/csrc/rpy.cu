@@ -15,7 +15,10 @@
 
 namespace gdc {
 
-constexpr int MV_TILE = 256;
+#ifndef GDC_MV_TILE
+#define GDC_MV_TILE 256
+#endif
+constexpr int MV_TILE = GDC_MV_TILE;   // sources staged in shared memory per tile
 
 // ---- source packing ---------------------------------------------------------
 
