@@ -42,6 +42,7 @@ def main(argv=None) -> int:
     ops = {
         "rpy32": lambda: ctx.rpy_apply(lam, g.FP32_MIXED),
         "rpy64": lambda: ctx.rpy_apply(lam, g.FP64),
+        "rpydf": lambda: ctx.rpy_apply(lam, 2),       # double-float residual product
         "saddle32": lambda: ctx.saddle_apply(x, g.FP32_MIXED),
         "precond": lambda: ctx.precond_apply(x),
         "forces32": lambda: ctx.forces(),
