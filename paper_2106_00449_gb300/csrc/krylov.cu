@@ -5,10 +5,11 @@
 // are segmented per suspension.  Reductions are two-pass (per-chunk partials, then a
 // fixed-order sum per segment), so results are bitwise reproducible run to run.
 //
-// Precision: bases, inner products, Givens/Hessenberg and the small tridiagonal
-// eigenproblem are FP64.  In GDC_FP32_MIXED mode the operator inside the Krylov loop
-// uses the FP32 pair kernel; each GMRES cycle ends with an FP64 residual, and the
-// solver restarts from it until that FP64 residual meets gmres_tol (iterative refinement).
+// Precision: bases, inner products and Givens/Hessenberg are FP64; the small tridiagonal
+// eigenproblem of Lanczos is FP64 for tolerances below 1e-5 and FP32 otherwise.  In
+// GDC_FP32_MIXED mode the operator inside the Krylov loop uses the FP32 pair kernel; each
+// GMRES cycle ends with an accurate residual (double-float pairs, FP64 same-body blocks),
+// and the solver restarts from it until that residual meets gmres_tol (iterative refinement).
 #include <algorithm>
 #include <cmath>
 
@@ -403,69 +404,80 @@ struct LzRot {
     int q, pad;
 };
 
-// out = wn * T_k^(1/2) e_1 for the k x k tridiagonal (al, be).  Returns false when the
-// QR iteration does not converge or the rotation store overflows.
-__device__ bool lz_sqrt_e1(const double* al, const double* be, int k, double wn, LzRot* rot, int rot_cap,
-                           double* out) {
-    double d[GDC_MAX_LANCZOS], e[GDC_MAX_LANCZOS];
+// out = wn * T_k^(1/2) e_1 for the k x k tridiagonal (al, be), computed in precision T.
+// Returns false when the QR iteration does not converge or the rotation store overflows.
+template <typename T>
+__device__ bool lz_sqrt_e1_t(const double* al, const double* be, int k, double wn, LzRot* rot, int rot_cap,
+                             double* out_d) {
+    const T eps = sizeof(T) == 4 ? T(1.2e-7) : T(1e-16);   // deflation threshold (relative)
+    T d[GDC_MAX_LANCZOS], e[GDC_MAX_LANCZOS], out[GDC_MAX_LANCZOS];
     for (int i = 0; i < k; ++i) {
-        d[i] = al[i];
-        e[i] = i + 1 < k ? be[i] : 0.0;
-        out[i] = i == 0 ? 1.0 : 0.0;   // u = Q^T e_1, built rotation by rotation
+        d[i] = (T)al[i];
+        e[i] = i + 1 < k ? (T)be[i] : T(0);
+        out[i] = i == 0 ? T(1) : T(0);   // u = Q^T e_1, built rotation by rotation
     }
     int nrot = 0;
     int hi = k - 1;
     for (int sweep = 0; hi > 0; ++sweep) {
         if (sweep > 40 * k + 40) return false;
-        if (fabs(e[hi - 1]) <= 1e-16 * (fabs(d[hi - 1]) + fabs(d[hi]))) {
-            e[hi - 1] = 0.0;
+        if (fabs(e[hi - 1]) <= eps * (fabs(d[hi - 1]) + fabs(d[hi]))) {
+            e[hi - 1] = T(0);
             --hi;
             continue;
         }
         int lo = hi - 1;
-        while (lo > 0 && fabs(e[lo - 1]) > 1e-16 * (fabs(d[lo - 1]) + fabs(d[lo]))) --lo;
-        const double del = 0.5 * (d[hi - 1] - d[hi]);
-        const double bb = e[hi - 1];
-        const double sg = del >= 0.0 ? 1.0 : -1.0;
-        const double mu = d[hi] - bb * bb / (del + sg * sqrt(del * del + bb * bb));
-        double xx = d[lo] - mu, zz = e[lo];
+        while (lo > 0 && fabs(e[lo - 1]) > eps * (fabs(d[lo - 1]) + fabs(d[lo]))) --lo;
+        const T del = T(0.5) * (d[hi - 1] - d[hi]);
+        const T bb = e[hi - 1];
+        const T sg = del >= T(0) ? T(1) : T(-1);
+        const T mu = d[hi] - bb * bb / (del + sg * sqrt(del * del + bb * bb));
+        T xx = d[lo] - mu, zz = e[lo];
         for (int q = lo; q < hi; ++q) {
-            const double rr = sqrt(xx * xx + zz * zz);
-            double cq = 1.0, sq = 0.0;
-            if (rr > 0.0) {
-                const double ri = 1.0 / rr;
+            const T rr = sqrt(xx * xx + zz * zz);
+            T cq = T(1), sq = T(0);
+            if (rr > T(0)) {
+                const T ri = T(1) / rr;
                 cq = xx * ri;
                 sq = zz * ri;
             }
             if (q > lo) e[q - 1] = rr;
-            const double a0 = d[q], b0 = d[q + 1], f0 = e[q];
-            const double cc = cq * cq, ss = sq * sq, cs = cq * sq;
-            d[q] = cc * a0 + 2.0 * cs * f0 + ss * b0;
-            d[q + 1] = ss * a0 - 2.0 * cs * f0 + cc * b0;
+            const T a0 = d[q], b0 = d[q + 1], f0 = e[q];
+            const T cc = cq * cq, ss = sq * sq, cs = cq * sq;
+            d[q] = cc * a0 + T(2) * cs * f0 + ss * b0;
+            d[q + 1] = ss * a0 - T(2) * cs * f0 + cc * b0;
             e[q] = cs * (b0 - a0) + (cc - ss) * f0;
             if (q + 1 < hi) {
-                const double bulge = sq * e[q + 1];
+                const T bulge = sq * e[q + 1];
                 e[q + 1] = cq * e[q + 1];
                 xx = e[q];
                 zz = bulge;
             }
-            const double u0 = out[q], u1 = out[q + 1];
+            const T u0 = out[q], u1 = out[q + 1];
             out[q] = cq * u0 + sq * u1;
             out[q + 1] = -sq * u0 + cq * u1;
             if (nrot >= rot_cap) return false;
-            rot[nrot++] = LzRot{cq, sq, q, 0};
+            rot[nrot++] = LzRot{(double)cq, (double)sq, q, 0};
         }
     }
     // g = sqrt(theta) * u, then Q g by the transposed rotations in reverse order
-    for (int i = 0; i < k; ++i) out[i] *= sqrt(fmax(d[i], 0.0));
+    for (int i = 0; i < k; ++i) out[i] *= sqrt(d[i] > T(0) ? d[i] : T(0));
     for (int t = nrot - 1; t >= 0; --t) {
         const LzRot R = rot[t];
-        const double g0 = out[R.q], g1 = out[R.q + 1];
-        out[R.q] = R.c * g0 - R.s * g1;
-        out[R.q + 1] = R.s * g0 + R.c * g1;
+        const T c = (T)R.c, s = (T)R.s;
+        const T g0 = out[R.q], g1 = out[R.q + 1];
+        out[R.q] = c * g0 - s * g1;
+        out[R.q + 1] = s * g0 + c * g1;
     }
-    for (int i = 0; i < k; ++i) out[i] *= wn;
+    for (int i = 0; i < k; ++i) out_d[i] = wn * (double)out[i];
     return true;
+}
+
+// FP32 is enough for the small eigenproblem when the Lanczos tolerance is loose (its
+// error, ~1e-6 relative, is far below tol); tight tolerances use FP64.
+__device__ inline bool lz_sqrt_e1(const double* al, const double* be, int k, double wn, LzRot* rot, int rot_cap,
+                                  double* out, bool fp32) {
+    return fp32 ? lz_sqrt_e1_t<float>(al, be, k, wn, rot, rot_cap, out)
+                : lz_sqrt_e1_t<double>(al, be, k, wn, rot, rot_cap, out);
 }
 
 // ||c_k - [c_{k-1}; 0]|| / ||c_k||
@@ -520,7 +532,8 @@ __global__ void __launch_bounds__(32) k_lz_tridiag(int S, int j, const double* _
     double* cs_ = cvec + (long long)s * kmax;   // c of the last formed index
     const double wn = Wnorm[s];
     double cur[GDC_MAX_LANCZOS];
-    if (!lz_sqrt_e1(al, be, k, wn, rot, rot_cap, cur)) {
+    const bool eig32 = tol >= 1e-5;
+    if (!lz_sqrt_e1(al, be, k, wn, rot, rot_cap, cur, eig32)) {
         atomicExch(status, 2);
         active[s] = 0;
         err[s] = 1.0;
@@ -546,7 +559,7 @@ __global__ void __launch_bounds__(32) k_lz_tridiag(int S, int j, const double* _
                 for (int r = 0; r < k - 1; ++r) ck[r] = cs_[r];
                 double best_err = ee;
                 for (int kk = k - 1; kk >= 2; --kk) {
-                    if (!lz_sqrt_e1(al, be, kk - 1, wn, rot, rot_cap, cm)) break;
+                    if (!lz_sqrt_e1(al, be, kk - 1, wn, rot, rot_cap, cm, eig32)) break;
                     const double e2 = lz_change(ck, cm, kk);
                     if (!(e2 < tol)) break;
                     kstar = kk;

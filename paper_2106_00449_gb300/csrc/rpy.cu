@@ -106,15 +106,17 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) {
     return u2f(r);
 }
 
-// Each thread owns 2P targets, evaluated two at a time with packed instructions.  A
-// source tile is first evaluated with the far-field formula only (no branch), while
-// the smallest r^2 per target is tracked; a target whose tile held a pair closer than
-// 2a (its own blob included) recomputes that tile with rpy_pair_exact, discarding the
-// far-field values (infinite or NaN for r = 0).  Shared memory holds each source as
-// (x,x,y,y) (z,z,lx,lx) (ly,ly,lz,lz), so one 16-byte load feeds a packed operand.
+// Each thread owns 2P targets, evaluated two at a time with packed instructions.  Each
+// 32-source sub-chunk of a tile is first evaluated with the far-field formula only (no
+// branch), while the smallest r^2 per target is tracked; a target whose sub-chunk held a
+// pair closer than 2a (its own blob included) recomputes that sub-chunk with
+// rpy_pair_exact, discarding the far-field values (infinite or NaN for r = 0).  Shared
+// memory holds each source as (x,x,y,y) (z,z,lx,lx) (ly,ly,lz,lz), so one 16-byte load
+// feeds a packed operand.
 //
-// Same-body pairs are left out (the FP64 intra-body kernel adds them exactly): a tile
-// that overlaps the blob range of a target's own body is also redone, skipping that range.
+// Same-body pairs are left out (the FP64 intra-body kernel adds them exactly): a
+// sub-chunk that overlaps the blob range of a target's own body is also redone, skipping
+// that range.
 template <int P>
 __global__ void __launch_bounds__(128) k_rpy32(const MvItem* __restrict__ items, const long long* __restrict__ susp_blob_off,
                                                const float4* __restrict__ spos, const float4* __restrict__ slam,
@@ -155,57 +157,67 @@ __global__ void __launch_bounds__(128) k_rpy32(const MvItem* __restrict__ items,
         }
         __syncthreads();
         float2 tx[P], ty[P], tz[P];
-        float mn[2 * P];
 #pragma unroll
-        for (int p = 0; p < P; ++p) {
-            tx[p] = ty[p] = tz[p] = make_float2(0.f, 0.f);
-            mn[2 * p] = mn[2 * p + 1] = 3.0e38f;
-        }
-#pragma unroll 2
-        for (int j = 0; j < n; ++j) {
-            const float4 s0 = sh[3 * j], s1 = sh[3 * j + 1], s2 = sh[3 * j + 2];
-            const float2 xs = make_float2(s0.x, s0.y), ys = make_float2(s0.z, s0.w), zs = make_float2(s1.x, s1.y);
-            const float2 lx = make_float2(s1.z, s1.w), ly = make_float2(s2.x, s2.y), lz = make_float2(s2.z, s2.w);
+        for (int p = 0; p < P; ++p) tx[p] = ty[p] = tz[p] = make_float2(0.f, 0.f);
+        // 32-source sub-chunks: only a sub-chunk that holds a near or same-body pair is redone
+        for (int jc = 0; jc < n; jc += 32) {
+            const int je = min(jc + 32, n);
+            float2 qx[P], qy[P], qz[P];
+            float mn[2 * P];
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                const float2 dx = sub2(xs, xt[p]), dy = sub2(ys, yt[p]), dz = sub2(zs, zt[p]);
-                const float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
-                const float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
-                const float2 ri2 = mul2(ri, ri);
-                const float2 ri3 = mul2(ri2, ri);
-                const float2 A = fma2(c23, ri3, ri);
-                const float2 B = mul2(ri3, fma2(mc2, ri2, one));
-                const float2 s = mul2(B, fma2(dx, lx, fma2(dy, ly, mul2(dz, lz))));
-                tx[p] = fma2(A, lx, fma2(s, dx, tx[p]));
-                ty[p] = fma2(A, ly, fma2(s, dy, ty[p]));
-                tz[p] = fma2(A, lz, fma2(s, dz, tz[p]));
-                mn[2 * p] = fminf(mn[2 * p], r2.x);
-                mn[2 * p + 1] = fminf(mn[2 * p + 1], r2.y);
+                qx[p] = qy[p] = qz[p] = make_float2(0.f, 0.f);
+                mn[2 * p] = mn[2 * p + 1] = 3.0e38f;
             }
-        }
+#pragma unroll 4
+            for (int j = jc; j < je; ++j) {
+                const float4 s0 = sh[3 * j], s1 = sh[3 * j + 1], s2 = sh[3 * j + 2];
+                const float2 xs = make_float2(s0.x, s0.y), ys = make_float2(s0.z, s0.w), zs = make_float2(s1.x, s1.y);
+                const float2 lx = make_float2(s1.z, s1.w), ly = make_float2(s2.x, s2.y), lz = make_float2(s2.z, s2.w);
 #pragma unroll
-        for (int p = 0; p < P; ++p) {
+                for (int p = 0; p < P; ++p) {
+                    const float2 dx = sub2(xs, xt[p]), dy = sub2(ys, yt[p]), dz = sub2(zs, zt[p]);
+                    const float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+                    const float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+                    const float2 ri2 = mul2(ri, ri);
+                    const float2 ri3 = mul2(ri2, ri);
+                    const float2 A = fma2(c23, ri3, ri);
+                    const float2 B = mul2(ri3, fma2(mc2, ri2, one));
+                    const float2 s = mul2(B, fma2(dx, lx, fma2(dy, ly, mul2(dz, lz))));
+                    qx[p] = fma2(A, lx, fma2(s, dx, qx[p]));
+                    qy[p] = fma2(A, ly, fma2(s, dy, qy[p]));
+                    qz[p] = fma2(A, lz, fma2(s, dz, qz[p]));
+                    mn[2 * p] = fminf(mn[2 * p], r2.x);
+                    mn[2 * p + 1] = fminf(mn[2 * p + 1], r2.y);
+                }
+            }
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int lo = own_lo[2 * p + h] - j0, hi = own_hi[2 * p + h] - j0;   // own body, tile-relative
-                if (mn[2 * p + h] < k.four_a2 || (lo < n && hi > 0)) {
-                    const float xq = h ? xt[p].y : xt[p].x, yq = h ? yt[p].y : yt[p].x, zq = h ? zt[p].y : zt[p].x;
-                    float ox = 0.f, oy = 0.f, oz = 0.f;
-                    for (int j = 0; j < n; ++j) {
-                        if (j >= lo && j < hi) continue;
-                        const float4 s0 = sh[3 * j], s1 = sh[3 * j + 1], s2 = sh[3 * j + 2];
-                        rpy_pair_exact(k, s0.x - xq, s0.z - yq, s1.x - zq, s1.z, s2.x, s2.z, ox, oy, oz);
-                    }
-                    if (h) {
-                        tx[p].y = ox;
-                        ty[p].y = oy;
-                        tz[p].y = oz;
-                    } else {
-                        tx[p].x = ox;
-                        ty[p].x = oy;
-                        tz[p].x = oz;
+            for (int p = 0; p < P; ++p) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int lo = own_lo[2 * p + h] - j0, hi = own_hi[2 * p + h] - j0;   // own body, tile-relative
+                    if (mn[2 * p + h] < k.four_a2 || (lo < je && hi > jc)) {
+                        const float xq = h ? xt[p].y : xt[p].x, yq = h ? yt[p].y : yt[p].x, zq = h ? zt[p].y : zt[p].x;
+                        float ox = 0.f, oy = 0.f, oz = 0.f;
+                        for (int j = jc; j < je; ++j) {
+                            if (j >= lo && j < hi) continue;
+                            const float4 s0 = sh[3 * j], s1 = sh[3 * j + 1], s2 = sh[3 * j + 2];
+                            rpy_pair_exact(k, s0.x - xq, s0.z - yq, s1.x - zq, s1.z, s2.x, s2.z, ox, oy, oz);
+                        }
+                        if (h) {
+                            qx[p].y = ox;
+                            qy[p].y = oy;
+                            qz[p].y = oz;
+                        } else {
+                            qx[p].x = ox;
+                            qy[p].x = oy;
+                            qz[p].x = oz;
+                        }
                     }
                 }
+                tx[p] = add2(tx[p], qx[p]);
+                ty[p] = add2(ty[p], qy[p]);
+                tz[p] = add2(tz[p], qz[p]);
             }
         }
         // compensated (Kahan) addition of the tile sums
