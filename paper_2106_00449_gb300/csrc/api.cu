@@ -182,6 +182,7 @@ static size_t carve(gdc_ctx* c, void* base) {
     c->ref = w.take<double>(3 * S);
     c->spos = w.take<float4>(NBL);
     c->slam = w.take<float4>(NBL);
+    c->sdup = w.take<float4>(3 * NBL);
     c->spos64 = w.take<double4>(NBL);
     c->slam64 = w.take<double4>(NBL);
     c->W = w.take<double>(3 * NBL);
@@ -318,6 +319,7 @@ static gdc_status read_status(gdc_ctx* c) {
     if (e != cudaSuccess) return cuda_check(c, e, "status read");
     if (st[0] == 1) return fail(c, GDC_ERR_NONFINITE, "template RPY block is not positive definite");
     if (st[0] == 2) return fail(c, GDC_ERR_NOT_CONVERGED, "tridiagonal eigensolver did not converge");
+    if (st[1] != 0) return fail(c, GDC_ERR_TIMEOUT, "a pair-kernel tile copy did not complete in time");
     return GDC_OK;
 }
 

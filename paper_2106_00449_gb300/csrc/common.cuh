@@ -96,7 +96,7 @@ struct gdc_ctx {
 
     // loaded configuration
     double *Rb = 0, *r = 0, *Yc = 0, *ref = 0;
-    float4 *spos = 0, *slam = 0;
+    float4 *spos = 0, *slam = 0, *sdup = 0;   // sdup: 3 float4 per blob, pair-kernel tile layout
     double4 *spos64 = 0, *slam64 = 0;
 
     // step buffers

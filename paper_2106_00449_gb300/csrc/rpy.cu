@@ -22,12 +22,18 @@ constexpr int MV_TILE = GDC_MV_TILE;   // sources staged in shared memory per ti
 
 // ---- source packing ---------------------------------------------------------
 
+// FP32 sources in the layout the pair kernel's shared-memory tiles use, three float4 per
+// blob: (x,x,y,y) (z,z,lx,lx) (ly,ly,lz,lz) -- each value twice, one per packed lane.
 __global__ void k_pack_lam32(int NBL, const int* __restrict__ map, const double* __restrict__ x,
-                             float4* __restrict__ slam) {
+                             const float4* __restrict__ spos, float4* __restrict__ sdup) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= NBL) return;
     const long long o = map ? (long long)map[i] : 3LL * i;
-    slam[i] = make_float4((float)x[o], (float)x[o + 1], (float)x[o + 2], 0.f);
+    const float lx = (float)x[o], ly = (float)x[o + 1], lz = (float)x[o + 2];
+    const float4 ps = spos[i];
+    sdup[3 * i] = make_float4(ps.x, ps.x, ps.y, ps.y);
+    sdup[3 * i + 1] = make_float4(ps.z, ps.z, lx, lx);
+    sdup[3 * i + 2] = make_float4(ly, ly, lz, lz);
 }
 
 __global__ void k_pack_lam64(int NBL, const int* __restrict__ map, const double* __restrict__ x,
@@ -41,7 +47,7 @@ __global__ void k_pack_lam64(int NBL, const int* __restrict__ map, const double*
 void launch_pack_lambda(gdc_ctx* c, int prec, const double* x, int gm_layout) {
     const int* map = gm_layout ? c->blob_gm : nullptr;
     if (prec == GDC_FP32_MIXED)
-        ++c->n_launch, k_pack_lam32<<<ceil_div(c->NBL, 256), 256, 0, c->stream>>>(c->NBL, map, x, c->slam);
+        ++c->n_launch, k_pack_lam32<<<ceil_div(c->NBL, 256), 256, 0, c->stream>>>(c->NBL, map, x, c->spos, c->sdup);
     else
         ++c->n_launch, k_pack_lam64<<<ceil_div(c->NBL, 256), 256, 0, c->stream>>>(c->NBL, map, x, c->slam64);
 }
@@ -117,16 +123,54 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) {
 // Same-body pairs are left out (the FP64 intra-body kernel adds them exactly): a
 // sub-chunk that overlaps the blob range of a target's own body is also redone, skipping
 // that range.
+//
+// Source tiles are staged by the bulk-copy (TMA) engine: the packed source array already
+// holds the duplicated layout, so a tile is one contiguous cp.async.bulk into shared
+// memory, completed on an mbarrier.  Two buffers: the copy of tile t+1 runs while tile t
+// is evaluated.  Waits are bounded; on a timeout the kernel flags status[1] and returns.
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void bulk_tile_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    unsigned long long state;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
+                 : "=l"(state) : "r"(smem_addr(bar)), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
+    (void)state;
+}
+
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+    for (int i = 0; i < 400000; ++i) {
+        unsigned done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(done) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
 template <int P>
 __global__ void __launch_bounds__(128) k_rpy32(const MvItem* __restrict__ items, const long long* __restrict__ susp_blob_off,
-                                               const float4* __restrict__ spos, const float4* __restrict__ slam,
+                                               const float4* __restrict__ spos, const float4* __restrict__ sdup,
                                                const long long* __restrict__ body_blob_off,
-                                               float4* __restrict__ part, int NBL, RpyConst32 k) {
-    __shared__ float4 sh[3 * MV_TILE];
+                                               float4* __restrict__ part, int NBL, RpyConst32 k,
+                                               int* __restrict__ status) {
+    __shared__ __align__(128) float4 shbuf[2][3 * MV_TILE];
+    __shared__ __align__(8) unsigned long long mbar[2];
     const MvItem it = items[blockIdx.x];
     const long long b0 = susp_blob_off[it.s];
     const int ns = (int)(susp_blob_off[it.s + 1] - b0);
     const float2 c23 = make_float2(k.c23, k.c23), mc2 = make_float2(-k.c2, -k.c2), one = make_float2(1.f, 1.f);
+    const int ntile = (it.j1 - it.j0 + MV_TILE - 1) / MV_TILE;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&mbar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&mbar[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && ntile > 0)
+        bulk_tile_load(shbuf[0], sdup + 3 * (b0 + it.j0), 48u * (unsigned)min(MV_TILE, it.j1 - it.j0), &mbar[0]);
 
     float2 xt[P], yt[P], zt[P], ax[P], ay[P], az[P], cx[P], cy[P], cz[P];
     int own_lo[2 * P], own_hi[2 * P];   // suspension-local blob range of each target's body
@@ -145,17 +189,18 @@ __global__ void __launch_bounds__(128) k_rpy32(const MvItem* __restrict__ items,
         ax[p] = ay[p] = az[p] = make_float2(0.f, 0.f);
         cx[p] = cy[p] = cz[p] = make_float2(0.f, 0.f);
     }
-    for (int j0 = it.j0; j0 < it.j1; j0 += MV_TILE) {
+    for (int t = 0; t < ntile; ++t) {
+        const int j0 = it.j0 + t * MV_TILE;
         const int n = min(MV_TILE, it.j1 - j0);
-        __syncthreads();
-        for (int e = threadIdx.x; e < n; e += 128) {
-            const float4 ps = spos[b0 + j0 + e];
-            const float4 ls = slam[b0 + j0 + e];
-            sh[3 * e] = make_float4(ps.x, ps.x, ps.y, ps.y);
-            sh[3 * e + 1] = make_float4(ps.z, ps.z, ls.x, ls.x);
-            sh[3 * e + 2] = make_float4(ls.y, ls.y, ls.z, ls.z);
+        const float4* sh = shbuf[t & 1];
+        if (threadIdx.x == 0 && t + 1 < ntile) {
+            // buffer (t+1)&1 was last read in iteration t-1, which ended with a barrier
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            const int j1n = j0 + MV_TILE;
+            bulk_tile_load(shbuf[(t + 1) & 1], sdup + 3 * (b0 + j1n), 48u * (unsigned)min(MV_TILE, it.j1 - j1n),
+                           &mbar[(t + 1) & 1]);
         }
-        __syncthreads();
+        const bool ok = mbar_wait(&mbar[t & 1], (unsigned)((t >> 1) & 1));
         float2 tx[P], ty[P], tz[P];
 #pragma unroll
         for (int p = 0; p < P; ++p) tx[p] = ty[p] = tz[p] = make_float2(0.f, 0.f);
@@ -227,6 +272,14 @@ __global__ void __launch_bounds__(128) k_rpy32(const MvItem* __restrict__ items,
             y = sub2(tx[p], cx[p]); u = add2(ax[p], y); cx[p] = sub2(sub2(u, ax[p]), y); ax[p] = u;
             y = sub2(ty[p], cy[p]); u = add2(ay[p], y); cy[p] = sub2(sub2(u, ay[p]), y); ay[p] = u;
             y = sub2(tz[p], cz[p]); u = add2(az[p], y); cz[p] = sub2(sub2(u, az[p]), y); az[p] = u;
+        }
+        // every thread is done with this buffer before it is refilled; a timed-out copy stops the block
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                atomicExch(status + 1, 1);
+                if (t + 1 < ntile) mbar_wait(&mbar[(t + 1) & 1], (unsigned)(((t + 1) >> 1) & 1));   // copy in flight
+            }
+            return;
         }
     }
 #pragma unroll
@@ -456,12 +509,14 @@ void launch_rpy(gdc_ctx* c, int prec) {
         // two targets per packed lane pair: tpt 4 -> P = 2, otherwise P = 1
         if (c->mv_tpt == 4)
             ++c->n_launch, k_rpy32<2><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off, c->spos,
-                                                                            c->slam, c->body_blob_off,
-                                                                            (float4*)c->mv_part, c->NBL, k);
+                                                                            c->sdup, c->body_blob_off,
+                                                                            (float4*)c->mv_part, c->NBL, k,
+                                                                            c->dev_status);
         else
             ++c->n_launch, k_rpy32<1><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off, c->spos,
-                                                                            c->slam, c->body_blob_off,
-                                                                            (float4*)c->mv_part, c->NBL, k);
+                                                                            c->sdup, c->body_blob_off,
+                                                                            (float4*)c->mv_part, c->NBL, k,
+                                                                            c->dev_status);
     } else if (prec == GDC_PREC_DF64) {
         const RpyConstDF k = df_constants(c->p.a);
         if (c->mv_tpt == 4)
@@ -812,11 +867,12 @@ namespace gdc {
 
 struct NoallocScratch {
     float4 spos[GDC_NOALLOC_MAX_BLOBS];
-    float4 slam[GDC_NOALLOC_MAX_BLOBS];
+    float4 sdup[3 * GDC_NOALLOC_MAX_BLOBS];
     float4 part[GDC_NOALLOC_MAX_CHUNKS * GDC_NOALLOC_MAX_BLOBS];
     MvItem items[(GDC_NOALLOC_MAX_BLOBS / GDC_NOALLOC_TILE) * GDC_NOALLOC_MAX_CHUNKS];
     long long body_blob_off[GDC_NOALLOC_MAX_BLOBS + 1];
     long long susp_blob_off[2];
+    int status[4];   // set by the pair kernel if a tile copy times out (u is then incomplete)
 };
 
 static __device__ __align__(256) NoallocScratch g_noalloc_scratch;
@@ -834,9 +890,12 @@ __global__ void k_noalloc_prepare(NoallocScratch* __restrict__ sc, const double*
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += gridDim.x * blockDim.x) {
         sc->body_blob_off[i] = i;
         if (i == n) continue;
-        sc->spos[i] = make_float4((float)(r[3 * i] - cen[0]), (float)(r[3 * i + 1] - cen[1]),
-                                  (float)(r[3 * i + 2] - cen[2]), __int_as_float(i));
-        sc->slam[i] = make_float4((float)lam[3 * i], (float)lam[3 * i + 1], (float)lam[3 * i + 2], 0.f);
+        const float x = (float)(r[3 * i] - cen[0]), y = (float)(r[3 * i + 1] - cen[1]), z = (float)(r[3 * i + 2] - cen[2]);
+        const float lx = (float)lam[3 * i], ly = (float)lam[3 * i + 1], lz = (float)lam[3 * i + 2];
+        sc->spos[i] = make_float4(x, y, z, __int_as_float(i));
+        sc->sdup[3 * i] = make_float4(x, x, y, y);
+        sc->sdup[3 * i + 1] = make_float4(z, z, lx, lx);
+        sc->sdup[3 * i + 2] = make_float4(ly, ly, lz, lz);
     }
     const int ntile = (n + GDC_NOALLOC_TILE - 1) / GDC_NOALLOC_TILE;
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < ntile * nk; b += gridDim.x * blockDim.x) {
@@ -928,8 +987,8 @@ extern "C" gdc_status gdc_rpy_apply_noalloc(const double* r, const double* lambd
     RpyConst32 k{(float)(2.0 * a * a / 3.0), (float)(2.0 * a * a), (float)(4.0 * a * a), (float)(4.0 / (3.0 * a)),
                  (float)(9.0 / (32.0 * a)), (float)(1.0 / (8.0 * a * a))};
     // the pair kernel addresses partial sums as part[k * NBL + i]: pass the array's row length
-    k_rpy32<1><<<ntile * nk, 128, 0, st>>>(sc->items, sc->susp_blob_off, sc->spos, sc->slam, sc->body_blob_off,
-                                             sc->part, GDC_NOALLOC_MAX_BLOBS, k);
+    k_rpy32<1><<<ntile * nk, 128, 0, st>>>(sc->items, sc->susp_blob_off, sc->spos, sc->sdup, sc->body_blob_off,
+                                             sc->part, GDC_NOALLOC_MAX_BLOBS, k, sc->status);
     k_noalloc_epilogue<<<(n_blobs + 255) / 256, 256, 0, st>>>(sc, lambda, n_blobs, nk,
                                                               1.0 / (8.0 * 3.141592653589793 * eta), 4.0 / (3.0 * a), u);
     e = cudaGetLastError();
