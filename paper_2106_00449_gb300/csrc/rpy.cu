@@ -150,8 +150,12 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
     return false;
 }
 
+#ifndef GDC_RPY32_MINB
+#define GDC_RPY32_MINB 1   // minimum resident blocks per SM requested from the register allocator
+#endif
+
 template <int P>
-__global__ void __launch_bounds__(128) k_rpy32(const MvItem* __restrict__ items, const long long* __restrict__ susp_blob_off,
+__global__ void __launch_bounds__(128, GDC_RPY32_MINB) k_rpy32(const MvItem* __restrict__ items, const long long* __restrict__ susp_blob_off,
                                                const float4* __restrict__ spos, const float4* __restrict__ sdup,
                                                const long long* __restrict__ body_blob_off,
                                                float4* __restrict__ part, int NBL, RpyConst32 k,
