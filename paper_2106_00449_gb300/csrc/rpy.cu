@@ -151,7 +151,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
 }
 
 #ifndef GDC_RPY32_MINB
-#define GDC_RPY32_MINB 1   // minimum resident blocks per SM requested from the register allocator
+#define GDC_RPY32_MINB 6   // minimum resident blocks per SM requested from the register allocator
 #endif
 
 template <int P>
