@@ -42,6 +42,34 @@ def _dist():
     return world, rank, local
 
 
+def pair_kernel_fingerprint() -> str:
+    """Hash of the FP32 pair kernel's source and its tiling constants."""
+    import hashlib
+    import re
+    src = open(os.path.join(ROOT, "paper_2106_00449_gb300", "csrc", "rpy.cu")).read()
+    start = src.index("template <int P>\n__global__ void __launch_bounds__(128, GDC_RPY32_MINB) k_rpy32")
+    end = src.index("\n}\n", start) + 3
+    macros = re.findall(r"#define (GDC_MV_TILE|GDC_RPY32_MINB) (\S+)", src)
+    return hashlib.sha256((src[start:end] + repr(macros)).encode()).hexdigest()[:16]
+
+
+def captured_traffic():
+    """DRAM bytes per launch of the FP32 pair kernel from the committed ncu summary.
+
+    None when the kernel's source changed since that capture (the figure would be stale).
+    """
+    import re
+    try:
+        text = open(os.path.join(ROOT, "profiles", "k_rpy32_c3_65k.md")).read()
+        h = re.search(r"kernel_source_sha256: (\w+)", text)
+        b = re.search(r"dram_bytes_per_launch: (\d+)", text)
+        if h and b and h.group(1) == pair_kernel_fingerprint():
+            return int(b.group(1))
+    except (OSError, ValueError):
+        pass
+    return None
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -242,7 +270,9 @@ def main(argv=None) -> int:
     achieved_tf = FLOPS_PER_PAIR * prof["pairs_per_product"] / avg_s / 1e12 if avg_s > 0 else None
     roof = {"bound": "alu", "kernel": "k_rpy32 (FP32 RPY pair kernel)", "achieved": achieved_tf,
             "peak": peak_tf, "unit": "TFLOP/s", "frac": (achieved_tf / peak_tf) if achieved_tf else None,
-            "traffic": None,
+            "traffic": captured_traffic(),
+            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch, "
+                              "profiles/k_rpy32_c3_65k.md (null when the kernel source differs)",
             "peak_source": (f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flops x {sm_max:.0f} MHz "
                             f"(sm_max_mhz of MEASURED_PEAKS.json, {peak_src})"),
             "avg_launch_ms": avg_s * 1000.0, "launches": prof["rpy32_launches"],
