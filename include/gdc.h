@@ -87,6 +87,13 @@ typedef struct {
     unsigned long long seed; /* Philox4x32-10 key of the W and W-tilde draws            */
     int    autotune;       /* 1: gdc_init times the FP32 pair kernel's candidate tilings
                               at the initial configuration and keeps the fastest        */
+    int    graph;          /* 1: gdc_step captures one step as a CUDA graph at its first
+                              call and replays it; the Lanczos and GMRES loops are
+                              conditional WHILE nodes whose conditions the loop kernels
+                              set, so a step makes one device-to-host read instead of one
+                              per Krylov iteration.  Results are identical to graph = 0
+                              (host-driven loops).  Used for the RFD divergence and for
+                              Euler-Maruyama, not while gdc_profile is on.              */
 } gdc_params;
 
 typedef struct {

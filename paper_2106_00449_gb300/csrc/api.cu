@@ -248,6 +248,10 @@ static size_t carve(gdc_ctx* c, void* base) {
     c->mv_nk = w.take<int>(S);
     c->mv_part = (void*)w.take<double4>((long long)c->mv_cap_kmax * NBL);
     c->dev_status = w.take<int>(4);
+    c->ctl = w.take<LoopCtl>(1);
+    c->rep = w.take<StepReport>(1);
+    c->lz_vcur = w.take<double>(nl);
+    c->gm_vcur = w.take<double>(n);
     return w.off + 256;
 }
 
@@ -448,6 +452,222 @@ static gdc_status one_step(gdc_ctx* c, gdc_step_info* info) {
     return cuda_check(c, cudaGetLastError(), "step launch");
 }
 
+// ---- graph mode: one CUDA graph per step ----------------------------------------------
+//
+// The whole step (Sec. 3 steps 1-6, or App. D) is captured once as a CUDA graph; the
+// Lanczos and GMRES loops inside it are WHILE nodes whose conditions the loop kernels set
+// on the device.  A replay needs one device-to-host read (the StepReport) at its end.
+// Values the captured launches take by value (tolerances, dt, the trace pointers) are
+// fixed at capture: gdc_set_params and gdc_set_trace drop the graph.  Profiling with
+// CUDA events around launches, and the FD divergence, use the host-driven path.
+
+__global__ void k_step_begin(StepReport* rep) {
+    int* w = reinterpret_cast<int*>(rep);
+    for (int i = threadIdx.x; i < (int)(sizeof(StepReport) / sizeof(int)); i += blockDim.x) w[i] = 0;
+}
+
+// the state is advanced only when no stage failed (the host-driven path returns early instead)
+__global__ void k_step_ok(StepReport* rep, const int* __restrict__ status) {
+    const bool bad = rep->lz_notconv[0] || rep->lz_notconv[1] || rep->lz_notconv[2] || rep->gm_bad ||
+                     rep->gm_notconv || status[0] != 0 || status[1] != 0;
+    rep->ok = bad ? 0 : 1;
+}
+
+__global__ void __launch_bounds__(32) k_step_finish(int S, const double* __restrict__ nu, int have_nu,
+                                                    const int* __restrict__ status, StepReport* rep, LoopCtl* ctl) {
+    double lo = 1.0, hi = 1.0;
+    if (have_nu) {
+        int bad = 0;
+        for (int s = threadIdx.x; s < S; s += 32) {
+            const double v = nu[s];
+            bad |= !isfinite(v);
+            lo = s == (int)threadIdx.x ? v : fmin(lo, v);
+            hi = s == (int)threadIdx.x ? v : fmax(hi, v);
+        }
+        if ((int)threadIdx.x >= S) lo = hi = nu[0];
+        bad = __any_sync(0xffffffffu, bad);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        }
+        if (bad) lo = hi = NAN;   // reported as a non-finite nu
+    }
+    if (threadIdx.x == 0) {
+        rep->nu_min = lo;
+        rep->nu_max = hi;
+        for (int k = 0; k < 4; ++k) rep->status[k] = status[k];
+        if (rep->ok) ctl->step++;
+    }
+}
+
+static bool graph_usable(const gdc_ctx* c) {
+    return c->p.graph && !c->prof_on && (c->p.scheme == GDC_SCHEME_EM || c->p.divmode == GDC_DIV_RFD);
+}
+
+static void drop_graph(gdc_ctx* c) {
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->graph_exec = nullptr;
+    c->graph = nullptr;
+    c->graph_valid = 0;
+}
+
+static void graph_slip(gdc_ctx* c, const double* W, double* vb, int fixed, int run) {
+    if (c->p.kT == 0.0) {
+        cudaMemsetAsync(vb, 0, sizeof(double) * 3 * c->NBL, c->stream);
+        return;
+    }
+    lanczos_sqrt_graph(c, W, vb, std::sqrt(2.0 * c->p.kT / c->p.dt), fixed, run);
+}
+
+// the launches of one step, in the order of one_step, for capture
+static void enqueue_step_graph(gdc_ctx* c) {
+    const double dt = c->p.dt;
+    const unsigned long long* sd = &c->ctl->step;
+    ++c->n_launch, k_step_begin<<<1, 32, 0, c->stream>>>(c->rep);
+    launch_normals(c, 0, 0, c->W, sd);
+    launch_normals(c, 0, 1, c->Wt, sd);
+    const bool gdc_scheme = c->p.scheme != GDC_SCHEME_EM;
+    if (!gdc_scheme) {
+        load_at(c, c->Y, c->q);
+        forces_at_loaded(c, c->FT);
+        graph_slip(c, c->W, c->vb_m, 0, 2);
+        launch_rhs(c, c->vb_m, c->FT, c->gm_b);
+        gmres_solve_graph(c, c->gm_b, c->gm_x);
+        launch_scatter_solution(c, c->gm_x, c->Vm, nullptr);
+        ++c->n_launch, k_step_ok<<<1, 1, 0, c->stream>>>(c->rep, c->dev_status);
+        launch_advance(c, c->Y, c->q, c->Vm, dt, nullptr, c->Y, c->q, &c->rep->ok);
+    } else {
+        load_at(c, c->Y, c->q);
+        graph_slip(c, c->W, c->vb_n, 0, 0);
+        launch_lsq(c, c->vb_n, c->calV);
+        launch_perturb(c, c->Y, c->q, c->Wt, c->p.rfd_delta, c->Yt, c->qt);
+        load_config(c, c->Yt, c->qt);
+        cudaMemcpyAsync(c->lz_fix, c->lz_k, sizeof(int) * c->S, cudaMemcpyDeviceToDevice, c->stream);
+        graph_slip(c, c->W, c->vb_t, 1, 1);
+        launch_lsq(c, c->vb_t, c->calVt);
+        launch_rfd_div(c, c->Wt, c->calV, c->calVt, c->p.rfd_delta, dt, c->nu);
+        launch_advance(c, c->Y, c->q, c->calV, 0.5 * dt, nullptr, c->Ym, c->qm);
+        load_at(c, c->Ym, c->qm);
+        forces_at_loaded(c, c->FT);
+        graph_slip(c, c->W, c->vb_m, 0, 2);
+        launch_rhs(c, c->vb_m, c->FT, c->gm_b);
+        gmres_solve_graph(c, c->gm_b, c->gm_x);
+        launch_scatter_solution(c, c->gm_x, c->Vm, nullptr);
+        ++c->n_launch, k_step_ok<<<1, 1, 0, c->stream>>>(c->rep, c->dev_status);
+        launch_advance(c, c->Y, c->q, c->Vm, dt, c->nu, c->Y, c->q, &c->rep->ok);
+    }
+    if (c->have_trace) {
+        const gdc_trace& t = c->trace;
+        auto cp = [&](double* dst, const double* src, long long n) {
+            if (dst) cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream);
+        };
+        cp(t.calV, c->calV, 6LL * c->NB);
+        cp(t.nu, c->nu, c->S);
+        cp(t.Ym, c->Ym, 3LL * c->NB);
+        cp(t.qm, c->qm, 4LL * c->NB);
+        cp(t.Vm, c->Vm, 6LL * c->NB);
+        cp(t.vb_n, c->vb_n, 3LL * c->NBL);
+        cp(t.vb_m, c->vb_m, 3LL * c->NBL);
+        cp(t.FTm, c->FT, 6LL * c->NB);
+    }
+    ++c->n_launch, k_step_finish<<<1, 32, 0, c->stream>>>(c->S, c->nu, gdc_scheme ? 1 : 0, c->dev_status, c->rep,
+                                                          c->ctl);
+}
+
+static gdc_status build_graph(gdc_ctx* c) {
+    drop_graph(c);
+    gdc_status st;
+    for (cudaStream_t& s : c->cap_stream)
+        if (!s && (st = cuda_check(c, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "capture stream")) != GDC_OK)
+            return st;
+    c->graph_loops.clear();
+    c->cap_err = cudaSuccess;
+    c->cap_depth = 0;
+    const unsigned long long n0 = c->n_launch;
+    cudaStream_t user = c->stream;
+    c->stream = c->cap_stream[0];
+    cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed);
+    cudaGraph_t g = nullptr;
+    if (e == cudaSuccess) {
+        enqueue_step_graph(c);
+        e = cudaStreamEndCapture(c->stream, &g);
+    }
+    c->stream = user;
+    c->graph_base_launches = c->n_launch - n0;
+    c->n_launch = n0;
+    if (e == cudaSuccess && c->cap_err != cudaSuccess) e = c->cap_err;
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_check(c, e, "step graph capture");
+    }
+    c->graph = g;
+    if ((st = cuda_check(c, cudaGraphInstantiate(&c->graph_exec, g, 0), "step graph instantiate")) != GDC_OK) {
+        drop_graph(c);
+        return st;
+    }
+    c->graph_valid = 1;
+    return GDC_OK;
+}
+
+static gdc_status graph_step(gdc_ctx* c, gdc_step_info* info) {
+    gdc_status st;
+    if (!c->graph_valid && (st = build_graph(c)) != GDC_OK) return st;
+    if (c->d_step_mirror != c->step) {
+        const unsigned long long v = c->step;
+        cudaError_t e = cudaMemcpyAsync(&c->ctl->step, &v, sizeof(v), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if ((st = cuda_check(c, e, "step counter upload")) != GDC_OK) return st;
+        c->d_step_mirror = c->step;
+    }
+    StepReport r{};
+    cudaError_t e = cudaGraphLaunch(c->graph_exec, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&r, c->rep, sizeof(r), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if ((st = cuda_check(c, e, "step graph")) != GDC_OK) return st;
+    // kernels executed: those outside the loops plus each loop body times its iterations
+    unsigned long long launches = c->graph_base_launches;
+    for (const auto& lp : c->graph_loops) {
+        const int slot = lp.first;
+        const long long runs = slot < 3 ? r.lz_exec[slot] : (slot == REP_GM_TOTAL ? r.gm_total : r.gm_outer);
+        launches += lp.second * (unsigned long long)std::max(0LL, runs);
+    }
+    c->n_launch += launches;
+    if (r.ok) c->d_step_mirror = c->step + 1;
+    gdc_step_info inf{};
+    inf.step = c->step;
+    for (int k = 0; k < 3; ++k) inf.lanczos_iters[k] = r.lz_iters[k];
+    inf.lanczos_err = std::max(r.lz_err[0], r.lz_err[2]);
+    inf.solve.iterations = r.gm_total;
+    inf.solve.cycles = r.gm_cycles;
+    inf.solve.residual = r.gm_residual;
+    inf.solve.converged = r.gm_converged;
+    if (c->p.precision == GDC_FP32_MIXED) {
+        inf.solve.matvecs_fp32 = r.gm_total;
+        inf.solve.matvecs_fp64 = r.gm_outer;
+    } else {
+        inf.solve.matvecs_fp64 = r.gm_total + r.gm_outer;
+    }
+    inf.nu_min = r.nu_min;
+    inf.nu_max = r.nu_max;
+    const int matvecs = inf.lanczos_iters[0] + inf.lanczos_iters[1] + inf.lanczos_iters[2] + inf.solve.matvecs_fp32 +
+                        inf.solve.matvecs_fp64;
+    inf.pair_evals = (double)matvecs * c->pair_evals_per_matvec;
+    // the host-driven path's checks, in its order
+    if (r.lz_notconv[0] || r.lz_notconv[2]) return fail(c, GDC_ERR_NOT_CONVERGED, "Lanczos reached lanczos_max_iter");
+    if (r.gm_bad) return fail(c, GDC_ERR_NONFINITE, "mobility solve: non-finite residual");
+    if (r.gm_notconv) return fail(c, GDC_ERR_NOT_CONVERGED, "mobility solve: GMRES reached gmres_max_iter");
+    if (r.status[0] == 1) return fail(c, GDC_ERR_NONFINITE, "template RPY block is not positive definite");
+    if (r.status[0] == 2) return fail(c, GDC_ERR_NOT_CONVERGED, "tridiagonal eigensolver did not converge");
+    if (r.status[1] != 0) return fail(c, GDC_ERR_TIMEOUT, "a pair-kernel tile copy did not complete in time");
+    if (!std::isfinite(inf.nu_min) || !std::isfinite(inf.nu_max)) return fail(c, GDC_ERR_NONFINITE, "non-finite nu");
+    c->step++;
+    if (info) *info = inf;
+    return GDC_OK;
+}
+
 }  // namespace gdc
 
 using namespace gdc;
@@ -528,6 +748,9 @@ gdc_status gdc_init(gdc_ctx** out, const gdc_params* params, int n_templates, co
 
 void gdc_destroy(gdc_ctx* c) {
     if (!c) return;
+    drop_graph(c);
+    for (cudaStream_t s : c->cap_stream)
+        if (s) cudaStreamDestroy(s);
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
     delete c;
 }
@@ -585,6 +808,7 @@ gdc_status gdc_set_params(gdc_ctx* c, const gdc_params* p) {
     const unsigned long long seed = c->p.seed;
     c->p = *p;
     c->p.seed = seed;
+    drop_graph(c);   // parameters are baked into the captured launches
     return GDC_OK;
 }
 
@@ -606,7 +830,7 @@ gdc_status gdc_step(gdc_ctx* c, int nsteps, gdc_step_info* info) {
     if (!c) return GDC_ERR_INVALID_ARG;
     if (nsteps < 0) return fail(c, GDC_ERR_INVALID_ARG, "nsteps must be >= 0");
     for (int k = 0; k < nsteps; ++k) {
-        gdc_status st = one_step(c, info ? info + k : nullptr);
+        gdc_status st = graph_usable(c) ? graph_step(c, info ? info + k : nullptr) : one_step(c, info ? info + k : nullptr);
         if (st != GDC_OK) return st;
     }
     return GDC_OK;
@@ -620,6 +844,7 @@ gdc_status gdc_set_trace(gdc_ctx* c, const gdc_trace* t) {
     } else {
         c->have_trace = 0;
     }
+    drop_graph(c);   // the trace copies are part of the captured step
     return GDC_OK;
 }
 

@@ -57,6 +57,31 @@ struct Seg {         // a segmented vector space: per-suspension offsets and the
     int n_chunks = 0;
 };
 
+// Loop indices of the device-driven Krylov loops (graph mode); lives in the workspace.
+struct LoopCtl {
+    int lz_j;        // Lanczos iteration index
+    int gm_j;        // GMRES inner index within the current cycle
+    int gm_total;    // GMRES inner iterations of the current solve
+    int gm_checks;   // residual checks of the current solve
+    int gm_outer;    // cycles executed (one accurate residual product each)
+    int pad[3];
+    unsigned long long step;   // step counter the draws use
+};
+
+// What one graph-replayed step reports back to the host (one device-to-host read per step).
+struct StepReport {
+    double lz_err[3];
+    double gm_residual;
+    double nu_min, nu_max;
+    int lz_iters[3];
+    int lz_notconv[3];   // stopped at lanczos_max_iter with the change above lanczos_tol
+    int lz_exec[3];      // iterations the WHILE node ran
+    int gm_total, gm_cycles, gm_converged, gm_bad, gm_notconv, gm_outer;
+    int status[4];       // copy of the device status words
+    int ok;              // 1 when the state was advanced
+    int pad;
+};
+
 struct Config {      // a rigid configuration the kernels evaluate at
     const double* Y = 0;
     const double* q = 0;
@@ -148,6 +173,21 @@ struct gdc_ctx {
     // status of device-side loops
     int* dev_status = 0;
 
+    // graph mode: the step replayed as one CUDA graph with WHILE nodes for the Krylov loops
+    gdc::LoopCtl* ctl = 0;        // device
+    gdc::StepReport* rep = 0;     // device
+    double *lz_vcur = 0, *gm_vcur = 0;   // the current Krylov vector, copied out of the basis slot
+    cudaGraph_t graph = 0;
+    cudaGraphExec_t graph_exec = 0;
+    int graph_valid = 0;
+    cudaStream_t cap_stream[3] = {0, 0, 0};   // top-level capture, loop body, nested loop body
+    cudaStream_t cap_saved[3] = {0, 0, 0};
+    int cap_depth = 0;
+    cudaError_t cap_err = cudaSuccess;
+    unsigned long long graph_base_launches = 0;               // kernels outside the loops
+    std::vector<std::pair<int, unsigned long long>> graph_loops;   // (report slot, kernels per iteration)
+    unsigned long long d_step_mirror = ~0ull;                 // value last written to ctl->step
+
     // instrumentation: kernel launches issued, and CUDA-event timing of the pair kernels
     unsigned long long n_launch = 0;
     int prof_on = 0;
@@ -216,13 +256,14 @@ void prof_flush(gdc_ctx* c);
 // geometry.cu
 void load_config(gdc_ctx* c, const double* Y, const double* q);
 void launch_ref(gdc_ctx* c, const double* Y);
-void launch_normals(gdc_ctx* c, unsigned long long step, int stream, double* out);
+void launch_normals(gdc_ctx* c, unsigned long long step, int stream, double* out,
+                    const unsigned long long* step_dev = nullptr);
 void launch_perturb(gdc_ctx* c, const double* Y, const double* q, const double* Wt, double delta,
                     double* Yo, double* qo);
 void launch_perturb_one(gdc_ctx* c, const double* Y, const double* q, int p_local, int coord,
                         double delta, double* Yo, double* qo);
 void launch_advance(gdc_ctx* c, const double* Y, const double* q, const double* V, double h,
-                    const double* nu, double* Yo, double* qo);
+                    const double* nu, double* Yo, double* qo, const int* guard = nullptr);
 void launch_rfd_div(gdc_ctx* c, const double* Wt, const double* calV, const double* calVt,
                     double delta, double dt, double* nu);
 void launch_fd_accum(gdc_ctx* c, const double* calV, const double* calVp, int p_local, int coord,
@@ -256,5 +297,13 @@ gdc_status lanczos_sqrt(gdc_ctx* c, const double* W, double* out, double scale, 
                         int* iters_out, double* err_out);
 void setup_segments(gdc_ctx* c);
 void krylov_init_attributes();
+// graph mode (capture helpers and the device-driven loops)
+cudaGraphConditionalHandle cap_cond(gdc_ctx* c);
+void cap_while_begin(gdc_ctx* c, cudaGraphConditionalHandle h);
+void cap_while_end(gdc_ctx* c, int report_slot, unsigned long long launches_before);
+void lanczos_sqrt_graph(gdc_ctx* c, const double* W, double* out, double scale, int fixed_mode, int run);
+void gmres_solve_graph(gdc_ctx* c, const double* b, double* x);
+// report slots of the loops: Lanczos runs 0..2, GMRES inner iterations, GMRES cycles
+enum { REP_LZ0 = 0, REP_GM_TOTAL = 3, REP_GM_OUTER = 4 };
 
 }  // namespace gdc

@@ -82,9 +82,11 @@ __device__ inline double normal_from(uint4 x, int comp) {
 // stream 0: 3 draws per blob; stream 1: 6 draws per body.  Counter (k/2, s, step, stream).
 __global__ void k_normals(long long total, int per, const int* __restrict__ owner_susp,
                           const long long* __restrict__ susp_off, unsigned long long seed,
-                          unsigned long long step, unsigned int stream, double* __restrict__ out) {
+                          unsigned long long step, const unsigned long long* __restrict__ step_dev,
+                          unsigned int stream, double* __restrict__ out) {
     long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (e >= total) return;
+    if (step_dev) step = *step_dev;   // graph mode: the counter lives in device memory
     const int s = owner_susp[e / per];
     const long long k = e - per * susp_off[s];
     const uint4 ctr = make_uint4((unsigned int)(k >> 1), (unsigned int)s, (unsigned int)(step & 0xffffffffull), stream);
@@ -92,15 +94,15 @@ __global__ void k_normals(long long total, int per, const int* __restrict__ owne
     out[e] = normal_from(philox4x32_10(ctr, key), (int)(k & 1));
 }
 
-void launch_normals(gdc_ctx* c, unsigned long long step, int stream, double* out) {
+void launch_normals(gdc_ctx* c, unsigned long long step, int stream, double* out, const unsigned long long* step_dev) {
     if (stream == 0) {
         long long total = 3LL * c->NBL;
         ++c->n_launch, k_normals<<<ceil_div(total, 256), 256, 0, c->stream>>>(total, 3, c->blob_susp, c->susp_blob_off,
-                                                               c->p.seed, step, 0u, out);
+                                                               c->p.seed, step, step_dev, 0u, out);
     } else {
         long long total = 6LL * c->NB;
         ++c->n_launch, k_normals<<<ceil_div(total, 256), 256, 0, c->stream>>>(total, 6, c->body_susp, c->susp_body_off,
-                                                               c->p.seed, step, 1u, out);
+                                                               c->p.seed, step, step_dev, 1u, out);
     }
 }
 
@@ -152,11 +154,14 @@ void launch_perturb_one(gdc_ctx* c, const double* Y, const double* q, int p_loca
 }
 
 // x -> x + h V with q -> exp(h Omega) * q; h is multiplied by nu[s] when nu is given (Sec. 3 steps 4, 6).
+// guard (graph mode): when given and zero the state is left as it is (an earlier stage failed)
 __global__ void k_advance(int NB, const double* __restrict__ Y, const double* __restrict__ q,
                           const double* __restrict__ V, double h, const double* __restrict__ nu,
-                          const int* __restrict__ body_susp, double* __restrict__ Yo, double* __restrict__ qo) {
+                          const int* __restrict__ body_susp, const int* __restrict__ guard, double* __restrict__ Yo,
+                          double* __restrict__ qo) {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= NB) return;
+    if (guard && *guard == 0) return;
     const double hp = nu ? h * nu[body_susp[p]] : h;
     double y0 = Y[3 * p] + hp * V[6 * p], y1 = Y[3 * p + 1] + hp * V[6 * p + 1], y2 = Y[3 * p + 2] + hp * V[6 * p + 2];
     double u[3] = {hp * V[6 * p + 3], hp * V[6 * p + 4], hp * V[6 * p + 5]};
@@ -169,8 +174,9 @@ __global__ void k_advance(int NB, const double* __restrict__ Y, const double* __
 }
 
 void launch_advance(gdc_ctx* c, const double* Y, const double* q, const double* V, double h,
-                    const double* nu, double* Yo, double* qo) {
-    ++c->n_launch, k_advance<<<ceil_div(c->NB, 128), 128, 0, c->stream>>>(c->NB, Y, q, V, h, nu, c->body_susp, Yo, qo);
+                    const double* nu, double* Yo, double* qo, const int* guard) {
+    ++c->n_launch, k_advance<<<ceil_div(c->NB, 128), 128, 0, c->stream>>>(c->NB, Y, q, V, h, nu, c->body_susp, guard,
+                                                                          Yo, qo);
 }
 
 // One block per suspension; fixed-order block reduction (deterministic).

@@ -51,10 +51,13 @@ void setup_segments(gdc_ctx* c) {
 // ---- reduction kernels -----------------------------------------------------------------
 
 // part[chunk * cols + i] = sum over the chunk of V_i[e] * w[e], i < k  (V_i = V + i * ld)
+// When kdev is given (graph mode) the count is k + *kdev: the loop index lives in device memory.
 __global__ void __launch_bounds__(RED_THREADS) k_mdot(const Chunk* __restrict__ chunks, const double* __restrict__ V,
-                                                      long long ld, int k, const double* __restrict__ w,
-                                                      double* __restrict__ part, int cols) {
+                                                      long long ld, int k, const int* __restrict__ kdev,
+                                                      const double* __restrict__ w, double* __restrict__ part,
+                                                      int cols) {
     __shared__ double sh[RED_THREADS / 32][GDC_MAX_LANCZOS + 1];
+    if (kdev) k += *kdev;
     const Chunk ch = chunks[blockIdx.x];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     double wv[RED_CHUNK / RED_THREADS];
@@ -86,7 +89,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_mdot(const Chunk* __restrict__ 
 // One warp per (segment, column): lanes take chunks lane, lane+32, ... and the warp sums
 // them with a fixed shuffle tree, so the order is the same on every run.
 __global__ void k_seg_sum(int S, const int* __restrict__ seg_chunk_off, const double* __restrict__ part, int cols, int k,
-                          double* __restrict__ out) {
+                          const int* __restrict__ kdev, double* __restrict__ out) {
+    if (kdev) k += *kdev;
     const int s = blockIdx.x;
     const int i = blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -99,7 +103,8 @@ __global__ void k_seg_sum(int S, const int* __restrict__ seg_chunk_off, const do
 
 // w[e] -= sum_i h[s * cols + i] * V_i[e] for i < k
 __global__ void k_mupdate(const Chunk* __restrict__ chunks, const double* __restrict__ V, long long ld, int k,
-                          const double* __restrict__ h, int cols, double* __restrict__ w) {
+                          const int* __restrict__ kdev, const double* __restrict__ h, int cols, double* __restrict__ w) {
+    if (kdev) k += *kdev;
     const Chunk ch = chunks[blockIdx.x];
     const double* hs = h + (long long)ch.seg * cols;
     for (long long e = ch.lo + threadIdx.x; e < ch.hi; e += blockDim.x) {
@@ -132,6 +137,20 @@ __global__ void k_seg_scale(const Chunk* __restrict__ chunks, const double* __re
     for (long long e = ch.lo + threadIdx.x; e < ch.hi; e += blockDim.x) out[e] = w[e] * sc;
 }
 
+// out_base + (jadd + *jdev) * ld  <-  w * scal[s]   (and a copy into also, when given)
+__global__ void k_seg_scale_slot(const Chunk* __restrict__ chunks, const double* __restrict__ w,
+                                 const double* __restrict__ scal, double* __restrict__ out_base, long long ld,
+                                 const int* __restrict__ jdev, int jadd, double* __restrict__ also) {
+    const Chunk ch = chunks[blockIdx.x];
+    const double sc = scal[ch.seg];
+    double* out = out_base + (long long)(jadd + (jdev ? *jdev : 0)) * ld;
+    for (long long e = ch.lo + threadIdx.x; e < ch.hi; e += blockDim.x) {
+        const double v = w[e] * sc;
+        out[e] = v;
+        if (also) also[e] = v;
+    }
+}
+
 __global__ void k_axpy_chunks(const Chunk* __restrict__ chunks, double a, const double* __restrict__ x,
                               double* __restrict__ y) {
     const Chunk ch = chunks[blockIdx.x];
@@ -145,11 +164,13 @@ __global__ void k_sub_chunks(const Chunk* __restrict__ chunks, const double* __r
 }
 
 // per-segment inner products <V_i, w>, i < k  -> out[s * cols + i]
+// kdev (graph mode): the count is k + *kdev, at most kcap; the column grid covers kcap
 static void seg_mdot(gdc_ctx* c, const gdc::Seg& sg, const double* V, long long ld, int k, const double* w,
-                     double* out, int cols) {
-    ++c->n_launch, k_mdot<<<sg.n_chunks, RED_THREADS, 0, c->stream>>>(sg.chunks, V, ld, k, w, c->red_part, c->red_cols);
-    ++c->n_launch, k_seg_sum<<<dim3(c->S, ceil_div(k, 8)), 256, 0, c->stream>>>(c->S, sg.seg_chunk_off, c->red_part,
-                                                                                c->red_cols, k, out);
+                     double* out, int cols, const int* kdev = nullptr, int kcap = 0) {
+    ++c->n_launch, k_mdot<<<sg.n_chunks, RED_THREADS, 0, c->stream>>>(sg.chunks, V, ld, k, kdev, w, c->red_part,
+                                                                      c->red_cols);
+    ++c->n_launch, k_seg_sum<<<dim3(c->S, ceil_div(kdev ? kcap : k, 8)), 256, 0, c->stream>>>(
+        c->S, sg.seg_chunk_off, c->red_part, c->red_cols, k, kdev, out);
     (void)cols;
 }
 
@@ -161,7 +182,9 @@ __global__ void k_sqrt_col0(int S, const double* __restrict__ v, int cols, doubl
     if (s < S) o[s] = sqrt(fmax(v[(long long)s * cols], 0.0));
 }
 
-__global__ void k_add_cols(int k, double* __restrict__ h, const double* __restrict__ h2, int cols) {
+__global__ void k_add_cols(int k, const int* __restrict__ kdev, double* __restrict__ h, const double* __restrict__ h2,
+                           int cols) {
+    if (kdev) k += *kdev;
     const int s = blockIdx.x;
     for (int i = threadIdx.x; i < k; i += blockDim.x) h[(long long)s * cols + i] += h2[(long long)s * cols + i];
 }
@@ -217,13 +240,14 @@ __global__ void k_gm_start(int S, const double* __restrict__ rn2, const double* 
 
 // Column j of the Hessenberg matrix: h (orthogonalisation coefficients), beta = ||w||.
 // Applies the previous Givens rotations, makes a new one, updates g and the residual estimate.
-__global__ void k_gm_arnoldi(int S, int j, int m, const double* __restrict__ h, int cols, const double* __restrict__ wn2,
-                             double* __restrict__ H, double* __restrict__ cs, double* __restrict__ sn,
-                             double* __restrict__ g, const double* __restrict__ bnorm, double inner_tol,
-                             double* __restrict__ est, int* __restrict__ active, int* __restrict__ jcount,
-                             double* __restrict__ scal) {
+__global__ void k_gm_arnoldi(int S, int j, const int* __restrict__ jdev, int m, const double* __restrict__ h, int cols,
+                             const double* __restrict__ wn2, double* __restrict__ H, double* __restrict__ cs,
+                             double* __restrict__ sn, double* __restrict__ g, const double* __restrict__ bnorm,
+                             double inner_tol, double* __restrict__ est, int* __restrict__ active,
+                             int* __restrict__ jcount, double* __restrict__ scal) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S) return;
+    if (jdev) j = *jdev;
     if (!active[s]) {
         scal[s] = 0.0;
         return;
@@ -334,13 +358,13 @@ gdc_status gmres_solve(gdc_ctx* c, const double* b, double* x, gdc_solve_info* i
             if (prec == GDC_FP32_MIXED) inf.matvecs_fp32++; else inf.matvecs_fp64++;
             // classical Gram-Schmidt, twice
             seg_mdot(c, sg, c->gm_V, n, j + 1, c->gm_w, c->gm_h, cols);
-            ++c->n_launch, k_mupdate<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->gm_V, n, j + 1, c->gm_h, cols, c->gm_w);
+            ++c->n_launch, k_mupdate<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->gm_V, n, j + 1, nullptr, c->gm_h, cols, c->gm_w);
             seg_mdot(c, sg, c->gm_V, n, j + 1, c->gm_w, c->gm_h2, cols);
-            ++c->n_launch, k_mupdate<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->gm_V, n, j + 1, c->gm_h2, cols, c->gm_w);
-            ++c->n_launch, k_add_cols<<<c->S, 128, 0, c->stream>>>(j + 1, c->gm_h, c->gm_h2, cols);
+            ++c->n_launch, k_mupdate<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->gm_V, n, j + 1, nullptr, c->gm_h2, cols, c->gm_w);
+            ++c->n_launch, k_add_cols<<<c->S, 128, 0, c->stream>>>(j + 1, nullptr, c->gm_h, c->gm_h2, cols);
             // ||w||: the column of wn2 lives after the h coefficients
             seg_mdot(c, sg, c->gm_w, 0, 1, c->gm_w, c->gm_h2, cols);
-            ++c->n_launch, k_gm_arnoldi<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(c->S, j, m, c->gm_h, cols, c->gm_h2, c->gm_H,
+            ++c->n_launch, k_gm_arnoldi<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(c->S, j, nullptr, m, c->gm_h, cols, c->gm_h2, c->gm_H,
                                                                      c->gm_cs, c->gm_sn, c->gm_g, c->gm_bnorm,
                                                                      inner_tol, c->gm_res + c->S, c->gm_active,
                                                                      c->gm_j, c->gm_scal);
@@ -495,7 +519,7 @@ __device__ inline double lz_change(const double* ck, const double* cprev, int k)
 // whatever the check schedule: when the first check of a run (index firstk + 1) already
 // passes, earlier indices are examined backwards.  lastk[s] is the last index whose c was
 // formed (-1 at the start of a run), lastk[S + s] the first one.
-__global__ void __launch_bounds__(32) k_lz_tridiag(int S, int j, const double* __restrict__ h, int cols,
+__global__ void __launch_bounds__(32) k_lz_tridiag(int S, int j, const int* __restrict__ jdev, const double* __restrict__ h, int cols,
                                                    const double* __restrict__ wn2, double* __restrict__ alpha,
                                                    double* __restrict__ betav, const double* __restrict__ Wnorm,
                                                    double* __restrict__ cvec, double* __restrict__ err,
@@ -510,6 +534,7 @@ __global__ void __launch_bounds__(32) k_lz_tridiag(int S, int j, const double* _
         scal[s] = 0.0;
         return;
     }
+    if (jdev) j = *jdev;
     const int k = j + 1;
     double beta = sqrt(fmax(wn2[(long long)s * cols], 0.0));
     double* al = alpha + (long long)s * kmax;
@@ -614,13 +639,13 @@ gdc_status lanczos_sqrt(gdc_ctx* c, const double* W, double* out, double scale, 
         rpy_op(c, prec, Vj, c->lz_w);
         // w = M v_j orthogonalised against v_0..v_j twice (full reorthogonalisation)
         seg_mdot(c, sg, c->lz_V, n, j + 1, c->lz_w, c->lz_h, cols);
-        ++c->n_launch, k_mupdate<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_V, n, j + 1, c->lz_h, cols, c->lz_w);
+        ++c->n_launch, k_mupdate<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_V, n, j + 1, nullptr, c->lz_h, cols, c->lz_w);
         seg_mdot(c, sg, c->lz_V, n, j + 1, c->lz_w, c->gm_h2, cols);
-        ++c->n_launch, k_mupdate<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_V, n, j + 1, c->gm_h2, cols, c->lz_w);
-        ++c->n_launch, k_add_cols<<<c->S, 128, 0, c->stream>>>(j + 1, c->lz_h, c->gm_h2, cols);
+        ++c->n_launch, k_mupdate<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_V, n, j + 1, nullptr, c->gm_h2, cols, c->lz_w);
+        ++c->n_launch, k_add_cols<<<c->S, 128, 0, c->stream>>>(j + 1, nullptr, c->lz_h, c->gm_h2, cols);
         seg_mdot(c, sg, c->lz_w, 0, 1, c->lz_w, c->gm_h2, cols);
         ++c->n_launch, k_lz_tridiag<<<c->S, 32, 0, c->stream>>>(
-            c->S, j, c->lz_h, cols, c->gm_h2, c->lz_alpha, c->lz_beta, c->lz_Wnorm, c->lz_c, c->lz_err, c->lz_active,
+            c->S, j, nullptr, c->lz_h, cols, c->gm_h2, c->lz_alpha, c->lz_beta, c->lz_Wnorm, c->lz_c, c->lz_err, c->lz_active,
             c->lz_k, c->lz_lastk, c->lz_scal, c->p.lanczos_tol, fixed_mode ? c->lz_fix : nullptr, c->lz_hint, kmax, c->susp_blob_off,
             (LzRot*)c->lz_rot, c->lz_rot_cap, c->dev_status);
         ++c->n_launch, k_seg_scale<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_w, c->lz_scal,
@@ -649,6 +674,290 @@ gdc_status lanczos_sqrt(gdc_ctx* c, const double* W, double* out, double scale, 
     if (!fixed_mode && ee > c->p.lanczos_tol && kk >= kmax)
         return fail(c, GDC_ERR_NOT_CONVERGED, "Lanczos reached lanczos_max_iter");
     return cuda_check(c, cudaGetLastError(), "Lanczos launch");
+}
+
+// ---- graph mode: the Krylov loops as CUDA-graph WHILE nodes ---------------------------
+//
+// The loops above decide convergence on the host, one small device-to-host read per
+// iteration.  In graph mode the same kernels run with their iteration index read from
+// device memory (LoopCtl) and the last kernel of every iteration sets the condition of the
+// WHILE node, so a whole step runs without a host round trip.  The arithmetic, and hence
+// every result, is the same as in the host-driven loops.
+
+// OR of flag[0..S) on one warp
+__device__ inline int warp_any_flag(int S, const int* __restrict__ flag) {
+    int any = 0;
+    for (int s = threadIdx.x; s < S; s += 32) any |= flag[s] != 0;
+    return __any_sync(0xffffffffu, any);
+}
+
+__global__ void __launch_bounds__(32) k_lz_begin(int S, const int* __restrict__ active, LoopCtl* ctl, int kmax,
+                                                 cudaGraphConditionalHandle h) {
+    const int any = warp_any_flag(S, active);
+    if (threadIdx.x == 0) {
+        ctl->lz_j = 0;
+        cudaGraphSetConditional(h, (any && kmax > 0) ? 1u : 0u);
+    }
+}
+
+__global__ void __launch_bounds__(32) k_lz_next(int S, const int* __restrict__ active, LoopCtl* ctl, int kmax,
+                                                cudaGraphConditionalHandle h) {
+    const int any = warp_any_flag(S, active);
+    if (threadIdx.x == 0) {
+        const int j = ++ctl->lz_j;
+        cudaGraphSetConditional(h, (any && j < kmax) ? 1u : 0u);
+    }
+}
+
+// the host-side summary of the eager loop, on the device: largest count and change
+__global__ void __launch_bounds__(32) k_lz_finish(int S, const int* __restrict__ kcount, const double* __restrict__ err,
+                                                  int fixed_mode, double tol, int kmax, const LoopCtl* ctl,
+                                                  StepReport* rep, int run) {
+    int kk = 0;
+    double ee = 0.0;
+    for (int s = threadIdx.x; s < S; s += 32) {
+        kk = max(kk, kcount[s]);
+        ee = fmax(ee, err[s]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        kk = max(kk, __shfl_xor_sync(0xffffffffu, kk, o));
+        ee = fmax(ee, __shfl_xor_sync(0xffffffffu, ee, o));
+    }
+    if (threadIdx.x == 0) {
+        rep->lz_iters[run] = kk;
+        rep->lz_err[run] = ee;
+        rep->lz_notconv[run] = (!fixed_mode && ee > tol && kk >= kmax) ? 1 : 0;
+        rep->lz_exec[run] = ctl->lz_j;
+    }
+}
+
+__global__ void k_gm_reset(LoopCtl* ctl) {
+    ctl->gm_j = 0;
+    ctl->gm_total = 0;
+    ctl->gm_checks = 0;
+    ctl->gm_outer = 0;
+}
+
+// after k_gm_start: the residual check of a cycle boundary, and the outer loop's condition
+__global__ void __launch_bounds__(32) k_gm_check(int S, const int* __restrict__ outer, const double* __restrict__ res,
+                                                 LoopCtl* ctl, int max_iter, StepReport* rep,
+                                                 cudaGraphConditionalHandle h) {
+    int any = 0, bad = 0;
+    double rmax = 0.0;
+    for (int s = threadIdx.x; s < S; s += 32) {
+        const double r = res[s];
+        any |= outer[s] != 0;
+        bad |= !isfinite(r);
+        rmax = fmax(rmax, r);
+    }
+    any = __any_sync(0xffffffffu, any);
+    bad = __any_sync(0xffffffffu, bad);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+    if (threadIdx.x != 0) return;
+    rep->gm_residual = rmax;
+    rep->gm_cycles = ctl->gm_checks++;
+    int go = 0;
+    if (bad)
+        rep->gm_bad = 1;
+    else if (!any)
+        rep->gm_converged = 1;
+    else if (ctl->gm_total >= max_iter)
+        rep->gm_notconv = 1;
+    else
+        go = 1;
+    ctl->gm_j = 0;
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+__global__ void k_gm_inner_begin(LoopCtl* ctl, cudaGraphConditionalHandle h) {
+    ctl->gm_outer++;
+    cudaGraphSetConditional(h, 1u);
+}
+
+__global__ void __launch_bounds__(32) k_gm_inner_next(int S, const int* __restrict__ active, LoopCtl* ctl,
+                                                      int max_iter, cudaGraphConditionalHandle h) {
+    const int any = warp_any_flag(S, active);
+    if (threadIdx.x == 0) {
+        ctl->gm_j++;
+        const int total = ++ctl->gm_total;
+        cudaGraphSetConditional(h, (any && total < max_iter) ? 1u : 0u);
+    }
+}
+
+__global__ void k_gm_finish(const LoopCtl* ctl, StepReport* rep) {
+    rep->gm_total = ctl->gm_total;
+    rep->gm_outer = ctl->gm_outer;
+}
+
+// ---- capture helpers -------------------------------------------------------------
+
+static void cap_chk(gdc_ctx* c, cudaError_t e) {
+    if (e != cudaSuccess && c->cap_err == cudaSuccess) c->cap_err = e;
+}
+
+// a condition handle of the graph the library's stream is capturing into
+cudaGraphConditionalHandle cap_cond(gdc_ctx* c) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    cap_chk(c, cudaStreamGetCaptureInfo(c->stream, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+    cudaGraphConditionalHandle h = 0;
+    if (g) cap_chk(c, cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+    return h;
+}
+
+// Appends a WHILE node on h after the work captured so far and redirects the library's
+// stream into the node's body graph (a capture stream of its own, one per nesting level).
+void cap_while_begin(gdc_ctx* c, cudaGraphConditionalHandle h) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* edges = nullptr;
+    size_t nd = 0;
+    cap_chk(c, cudaStreamGetCaptureInfo(c->stream, &cs, nullptr, &g, &deps, &edges, &nd));
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    cap_chk(c, cudaGraphAddNode(&node, g, deps, edges, nd, &np));
+    cap_chk(c, cudaStreamUpdateCaptureDependencies(c->stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    const int d = ++c->cap_depth;
+    c->cap_saved[d] = c->stream;
+    if (d >= 3 || c->cap_err != cudaSuccess) {
+        cap_chk(c, cudaErrorNotSupported);
+        return;
+    }
+    cap_chk(c, cudaStreamBeginCaptureToGraph(c->cap_stream[d], np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                             cudaStreamCaptureModeRelaxed));
+    c->stream = c->cap_stream[d];
+}
+
+// Ends the body capture; the kernels launched since launches_before run once per
+// iteration, which the report slot counts.
+void cap_while_end(gdc_ctx* c, int report_slot, unsigned long long launches_before) {
+    const int d = c->cap_depth;
+    if (d < 3 && c->stream == c->cap_stream[d]) {
+        cudaGraph_t out = nullptr;
+        cap_chk(c, cudaStreamEndCapture(c->stream, &out));
+    }
+    c->stream = c->cap_saved[d];
+    c->cap_depth = d - 1;
+    c->graph_loops.push_back({report_slot, c->n_launch - launches_before});
+    c->n_launch = launches_before;
+}
+
+// ---- the loops -------------------------------------------------------------------
+
+void lanczos_sqrt_graph(gdc_ctx* c, const double* W, double* out, double scale, int fixed_mode, int run) {
+    const int prec = c->p.precision;
+    const long long n = 3LL * c->NBL;
+    const gdc::Seg& sg = c->seg_lz;
+    const int cols = c->red_cols;
+    const int kmax = c->kmax;
+    int* jd = &c->ctl->lz_j;
+    seg_mdot(c, sg, W, 0, 1, W, c->lz_h, cols);
+    ++c->n_launch, k_lz_start<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(c->S, c->lz_h, cols, c->lz_Wnorm, c->lz_scal,
+                                                                          c->lz_active, c->lz_k, c->lz_err);
+    ++c->n_launch, k_lz_reset<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(c->S, c->lz_lastk);
+    ++c->n_launch, k_seg_scale_slot<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, W, c->lz_scal, c->lz_V, n, nullptr,
+                                                                        0, c->lz_vcur);
+    const cudaGraphConditionalHandle h = cap_cond(c);
+    ++c->n_launch, k_lz_begin<<<1, 32, 0, c->stream>>>(c->S, c->lz_active, c->ctl, kmax, h);
+    cap_while_begin(c, h);
+    const unsigned long long before = c->n_launch;
+    rpy_op(c, prec, c->lz_vcur, c->lz_w);
+    seg_mdot(c, sg, c->lz_V, n, 1, c->lz_w, c->lz_h, cols, jd, kmax);
+    ++c->n_launch, k_mupdate<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_V, n, 1, jd, c->lz_h, cols, c->lz_w);
+    seg_mdot(c, sg, c->lz_V, n, 1, c->lz_w, c->gm_h2, cols, jd, kmax);
+    ++c->n_launch, k_mupdate<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_V, n, 1, jd, c->gm_h2, cols, c->lz_w);
+    ++c->n_launch, k_add_cols<<<c->S, 128, 0, c->stream>>>(1, jd, c->lz_h, c->gm_h2, cols);
+    seg_mdot(c, sg, c->lz_w, 0, 1, c->lz_w, c->gm_h2, cols);
+    ++c->n_launch, k_lz_tridiag<<<c->S, 32, 0, c->stream>>>(
+        c->S, 0, jd, c->lz_h, cols, c->gm_h2, c->lz_alpha, c->lz_beta, c->lz_Wnorm, c->lz_c, c->lz_err, c->lz_active,
+        c->lz_k, c->lz_lastk, c->lz_scal, c->p.lanczos_tol, fixed_mode ? c->lz_fix : nullptr, c->lz_hint, kmax,
+        c->susp_blob_off, (LzRot*)c->lz_rot, c->lz_rot_cap, c->dev_status);
+    ++c->n_launch, k_seg_scale_slot<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_w, c->lz_scal, c->lz_V, n, jd,
+                                                                        1, c->lz_vcur);
+    ++c->n_launch, k_lz_next<<<1, 32, 0, c->stream>>>(c->S, c->lz_active, c->ctl, kmax, h);
+    cap_while_end(c, REP_LZ0 + run, before);
+    ++c->n_launch, k_fill<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(c->S, scale, c->lz_scal);
+    ++c->n_launch, k_combine<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_V, n, c->lz_k, c->lz_c, kmax,
+                                                                 c->lz_scal, out);
+    ++c->n_launch, k_lz_finish<<<1, 32, 0, c->stream>>>(c->S, c->lz_k, c->lz_err, fixed_mode, c->p.lanczos_tol, kmax,
+                                                        c->ctl, c->rep, run);
+}
+
+void gmres_solve_graph(gdc_ctx* c, const double* b, double* x) {
+    const int prec = c->p.precision;
+    const int m = c->m;
+    const long long n = c->ngm;
+    const gdc::Seg& sg = c->seg_gm;
+    const int cols = c->red_cols;
+    const double tol = c->p.gmres_tol;
+    const double inner_tol = prec == GDC_FP32_MIXED ? 0.1 * tol : tol;
+    const int max_iter = c->p.gmres_max_iter;
+    int* jd = &c->ctl->gm_j;
+    seg_mdot(c, sg, b, 0, 1, b, c->gm_h, cols);
+    ++c->n_launch, k_sqrt_col0<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(c->S, c->gm_h, cols, c->gm_bnorm);
+    cap_chk(c, cudaMemsetAsync(x, 0, sizeof(double) * n, c->stream));
+    cap_chk(c, cudaMemcpyAsync(c->gm_r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+    ++c->n_launch, k_gm_reset<<<1, 1, 0, c->stream>>>(c->ctl);
+    // first residual check (r = b)
+    seg_mdot(c, sg, c->gm_r, 0, 1, c->gm_r, c->gm_h2, cols);
+    ++c->n_launch, k_gm_start<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(c->S, c->gm_h2, c->gm_bnorm, tol, cols,
+                                                                          c->gm_res, c->gm_active, c->gm_g, c->gm_scal,
+                                                                          m + 1, c->gm_j, c->gm_active + c->S);
+    const cudaGraphConditionalHandle ho = cap_cond(c);
+    ++c->n_launch, k_gm_check<<<1, 32, 0, c->stream>>>(c->S, c->gm_active + c->S, c->gm_res, c->ctl, max_iter, c->rep, ho);
+    cap_while_begin(c, ho);
+    const unsigned long long before_o = c->n_launch;
+    {
+        // one restart / refinement cycle
+        ++c->n_launch, k_seg_scale_slot<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->gm_r, c->gm_scal, c->gm_V, n,
+                                                                            nullptr, 0, c->gm_vcur);
+        const cudaGraphConditionalHandle hi = cap_cond(c);
+        ++c->n_launch, k_gm_inner_begin<<<1, 1, 0, c->stream>>>(c->ctl, hi);
+        cap_while_begin(c, hi);
+        const unsigned long long before_i = c->n_launch;
+        {
+            launch_precond(c, c->gm_vcur, c->gm_z);
+            saddle_op(c, prec, c->gm_z, c->gm_w);
+            seg_mdot(c, sg, c->gm_V, n, 1, c->gm_w, c->gm_h, cols, jd, m);
+            ++c->n_launch, k_mupdate<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->gm_V, n, 1, jd, c->gm_h, cols, c->gm_w);
+            seg_mdot(c, sg, c->gm_V, n, 1, c->gm_w, c->gm_h2, cols, jd, m);
+            ++c->n_launch, k_mupdate<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->gm_V, n, 1, jd, c->gm_h2, cols, c->gm_w);
+            ++c->n_launch, k_add_cols<<<c->S, 128, 0, c->stream>>>(1, jd, c->gm_h, c->gm_h2, cols);
+            seg_mdot(c, sg, c->gm_w, 0, 1, c->gm_w, c->gm_h2, cols);
+            ++c->n_launch, k_gm_arnoldi<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(
+                c->S, 0, jd, m, c->gm_h, cols, c->gm_h2, c->gm_H, c->gm_cs, c->gm_sn, c->gm_g, c->gm_bnorm, inner_tol,
+                c->gm_res + c->S, c->gm_active, c->gm_j, c->gm_scal);
+            ++c->n_launch, k_seg_scale_slot<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->gm_w, c->gm_scal, c->gm_V,
+                                                                                n, jd, 1, c->gm_vcur);
+            ++c->n_launch, k_gm_inner_next<<<1, 32, 0, c->stream>>>(c->S, c->gm_active, c->ctl, max_iter, hi);
+        }
+        cap_while_end(c, REP_GM_TOTAL, before_i);
+        // x += P^-1 V y
+        ++c->n_launch, k_gm_backsolve<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(c->S, m, c->gm_H, c->gm_g, c->gm_j,
+                                                                                  c->gm_y, cols);
+        ++c->n_launch, k_combine<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->gm_V, n, c->gm_j, c->gm_y, cols,
+                                                                     nullptr, c->gm_w);
+        launch_precond(c, c->gm_w, c->gm_z);
+        ++c->n_launch, k_axpy_chunks<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, 1.0, c->gm_z, x);
+        // accurate residual r = b - A x, then the check of the next cycle boundary
+        saddle_op(c, prec == GDC_FP32_MIXED ? GDC_PREC_DF64 : GDC_FP64, x, c->gm_w);
+        ++c->n_launch, k_sub_chunks<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, b, c->gm_w, c->gm_r);
+        seg_mdot(c, sg, c->gm_r, 0, 1, c->gm_r, c->gm_h2, cols);
+        ++c->n_launch, k_gm_start<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(
+            c->S, c->gm_h2, c->gm_bnorm, tol, cols, c->gm_res, c->gm_active, c->gm_g, c->gm_scal, m + 1, c->gm_j,
+            c->gm_active + c->S);
+        ++c->n_launch, k_gm_check<<<1, 32, 0, c->stream>>>(c->S, c->gm_active + c->S, c->gm_res, c->ctl, max_iter,
+                                                           c->rep, ho);
+    }
+    cap_while_end(c, REP_GM_OUTER, before_o);
+    ++c->n_launch, k_gm_finish<<<1, 1, 0, c->stream>>>(c->ctl, c->rep);
 }
 
 }  // namespace gdc
