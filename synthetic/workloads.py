@@ -106,31 +106,31 @@ class _Grid:
 
     def __init__(self, cell: float):
         self.cell = cell
-        self.cells: Dict[tuple, List[np.ndarray]] = {}
+        self.cells: Dict[tuple, List[tuple]] = {}
 
     def keys(self, pts: np.ndarray) -> np.ndarray:
         return np.floor(pts / self.cell).astype(np.int64)
 
-    def near(self, pts: np.ndarray) -> np.ndarray:
-        ks = self.keys(pts)
-        seen = set()
-        out = []
-        lo, hi = ks.min(axis=0) - 1, ks.max(axis=0) + 1
-        for i in range(lo[0], hi[0] + 1):
-            for j in range(lo[1], hi[1] + 1):
-                for k in range(lo[2], hi[2] + 1):
-                    key = (i, j, k)
-                    if key in self.cells and key not in seen:
-                        seen.add(key)
-                        out.extend(self.cells[key])
-        if not out:
-            return np.zeros((0, 3))
-        return np.vstack(out)
+    def conflict(self, pts: np.ndarray, dmin2: float) -> bool:
+        """True when a stored point lies closer than sqrt(dmin2) to one of pts.
+
+        With cell = sqrt(dmin2) such a point is in one of the 27 cells around the blob's
+        cell; blobs are tested one at a time so that a rejected try usually stops early.
+        """
+        for (x, y, z), (i, j, k) in zip(pts.tolist(), self.keys(pts).tolist()):
+            for di in (-1, 0, 1):
+                for dj in (-1, 0, 1):
+                    for dk in (-1, 0, 1):
+                        got = self.cells.get((i + di, j + dj, k + dk))
+                        if got:
+                            for (u, v, w) in got:
+                                if (u - x) * (u - x) + (v - y) * (v - y) + (w - z) * (w - z) < dmin2:
+                                    return True
+        return False
 
     def add(self, pts: np.ndarray) -> None:
-        ks = self.keys(pts)
-        for p, k in zip(pts, map(tuple, ks)):
-            self.cells.setdefault(k, []).append(p[None, :])
+        for p, k in zip(pts.tolist(), map(tuple, self.keys(pts).tolist())):
+            self.cells.setdefault(k, []).append(tuple(p))
 
 
 def place_bodies(rng: np.random.Generator, templates: Sequence[np.ndarray], body_tmpl: np.ndarray,
@@ -150,11 +150,7 @@ def place_bodies(rng: np.random.Generator, templates: Sequence[np.ndarray], body
             qq = random_unit_quaternions(rng, 1)[0]
             rot = Rotation.from_quat([qq[1], qq[2], qq[3], qq[0]])  # scipy is scalar-last
             pts = y[None, :] + rot.apply(t)
-            nb = grid.near(pts)
-            if nb.shape[0] == 0:
-                break
-            d2 = ((pts[:, None, :] - nb[None, :, :]) ** 2).sum(-1)
-            if d2.min() >= dmin2:
+            if not grid.conflict(pts, dmin2):
                 break
         else:
             raise RuntimeError(f"could not place body {p} in a cube of edge {box}")
