@@ -7,6 +7,13 @@ fraction in a 140a cube (65,520 blobs), unbounded overlapping RPY, soft repulsio
 A = 4kT/a, b = 0.1a, dt = 0.005, GMRES tol 1e-6, Lanczos tol 1e-4, RFD delta 1e-3.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload c3_65k|c4|c5]
+
+--workload c4: 512 independent suspensions (8-128 bodies of 12-blob icosahedra, 10-blob
+rods and 42-blob icospheres, 5% volume fraction each, 772,728 blobs in all) advanced in one
+batched context, against the same suspensions advanced one context (one launch sequence)
+per suspension.  --workload c5: 16,384 rods of 20 blobs (327,680 blobs) at 8% volume
+fraction in linear shear, dt 0.002.  The default is the 65,520-blob workload above.
 
 Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank advances its own
 independent suspension of the same size (replicas, weak scaling, no collective on the
@@ -31,6 +38,11 @@ if ROOT not in sys.path:
 METRIC = "gDC steps/s at 65k blobs, FP32-mixed vs FP64, residual ≤1e-6; RPY pair-evals/s"
 WORKLOAD = ("c3_65k: 2,520 rigid bodies (840 each of 42-blob icosphere, 15-blob rod, 21-blob boomerang), "
             "65,520 blobs, 10% volume fraction in a 140a cube, unbounded overlapping RPY, soft repulsion")
+WORKLOAD_C4 = ("c4: 512 independent suspensions of 8-128 bodies (12-blob icosahedra, 10-blob rods, 42-blob "
+               "icospheres), 5% volume fraction each, 772,728 blobs, batched in one context; a step advances "
+               "every suspension once")
+WORKLOAD_C5 = ("c5: 16,384 rods of 20 collinear blobs, 327,680 blobs, 8% volume fraction in a 257.9a cube, "
+               "linear shear u = (y, 0, 0), dt 0.002, soft repulsion")
 FLOPS_PER_PAIR = 33.0          # algorithmic flops of one far-field RPY pair (FMA = 2), see the design doc
 FP32_LANES_PER_SM = 128
 
@@ -195,6 +207,33 @@ def run_reference(args, world, rank):
     return 0
 
 
+def per_suspension_steps(g, torch, wl, common, rank):
+    """The suspensions of a batch advanced one context per suspension, one after another.
+
+    Each suspension gets its own context (graph replay, autotuned tiling); after one
+    warm-up step its next step is timed with CUDA events.  A step of the whole batch is
+    the sum of those times.
+    """
+    total, evals = 0.0, 0.0
+    for s in range(wl.n_susp):
+        sub = wl.subset([s])
+        c = g.context_from_workload(sub, precision=g.FP32_MIXED, rfd_delta=1e-3, **common)
+        c.step(1)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(c.stream)
+        inf = c.step(1)
+        e1.record(c.stream)
+        torch.cuda.synchronize()
+        total += e0.elapsed_time(e1) / 1000.0
+        evals += inf[0]["pair_evals"]
+        del c
+    return {"steps_per_s": 1.0 / total, "pair_evals_per_s": evals / total, "suspensions": wl.n_susp,
+            "note": "one context per suspension, stepped one after another (one warm-up step each, then one "
+                    "timed step); value = 1 / (sum of the timed steps)"}
+
+
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -206,6 +245,7 @@ def main(argv=None) -> int:
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--ref-bodies", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="c3_65k", choices=["c3_65k", "c4", "c5"])
     args = ap.parse_args(argv)
     world, rank, local = _dist()
     if args.impl == "reference":
@@ -224,7 +264,12 @@ def main(argv=None) -> int:
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    wl = WL.c3_65k(seed=rank)
+    if args.workload == "c4":
+        wl, wl_desc = WL.c4(seed=rank), WORKLOAD_C4
+    elif args.workload == "c5":
+        wl, wl_desc = WL.c5(seed=rank), WORKLOAD_C5
+    else:
+        wl, wl_desc = WL.c3_65k(seed=rank), WORKLOAD
     common = dict(gmres_tol=1e-6, lanczos_tol=1e-4, lanczos_max_iter=128, gmres_restart=50, gmres_max_iter=500,
                   seed=1000 + rank)
     ctx = g.context_from_workload(wl, precision=g.FP32_MIXED, rfd_delta=1e-3, **common)
@@ -300,7 +345,8 @@ def main(argv=None) -> int:
             "warmup": args.warmup, "ms_per_step": 1000.0 * t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 pair kernels, f64 Krylov/state",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_blobs": wl.n_blobs, "n_bodies": wl.n_bodies,
+            "config": {"workload": wl_desc, "n_blobs": wl.n_blobs, "n_bodies": wl.n_bodies,
+                       "n_suspensions": wl.n_susp,
                        "precision": "fp32-mixed", "dt": wl.params["dt"], "gmres_tol": 1e-6, "lanczos_tol": 1e-4,
                        "rfd_delta": 1e-3, "l2": "flushed between timed steps (256 MB write outside the events)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
@@ -316,6 +362,17 @@ def main(argv=None) -> int:
                             "note": "the same steps with host-driven Krylov loops and CUDA events around "
                                     "every pair-kernel launch; the roofline's launch time comes from here"},
             "clocks": clocks}
+
+    if args.workload == "c4":
+        line["one_suspension_per_launch"] = per_suspension_steps(g, torch, wl, common, rank)
+        line["one_suspension_per_launch"]["batched_speedup"] = (
+            value / world / line["one_suspension_per_launch"]["steps_per_s"])
+    if args.workload != "c3_65k":
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        if dist:
+            dist.destroy_process_group()
+        return 0
 
     # end to end through the C ABI: host state in, step, host state out
     hY = torch.empty((wl.n_bodies, 3), dtype=torch.float64).pin_memory()

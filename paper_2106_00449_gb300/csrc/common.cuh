@@ -160,6 +160,7 @@ struct gdc_ctx {
     std::vector<gdc::MvItem> h_mv_items;
     std::vector<int> h_mv_nk;
     void* mv_part = 0;            // mv_kmax x NBL x (float4 | double4)
+    const int* mv_active = 0;     // when set, suspensions flagged 0 are skipped by the pair kernels
     double pair_evals_per_matvec = 0.0;
 
     // host mirrors for convergence checks

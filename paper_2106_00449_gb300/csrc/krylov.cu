@@ -18,7 +18,6 @@
 namespace gdc {
 
 constexpr int RED_CHUNK = 1024;   // elements per reduction chunk
-constexpr int RED_THREADS = 256;
 
 // ---- segment / chunk tables ---------------------------------------------------------
 
@@ -51,38 +50,58 @@ void setup_segments(gdc_ctx* c) {
 // ---- reduction kernels -----------------------------------------------------------------
 
 // part[chunk * cols + i] = sum over the chunk of V_i[e] * w[e], i < k  (V_i = V + i * ld)
+//
+// GB300 issues FP64 FMAs at a small fraction of its FP32 rate, so this kernel is bound by
+// the FP64 pipe, not by HBM: each element of V costs one FMA.  A chunk is taken by two
+// warps with 16 elements per lane, so the per-column warp reduction (5 shuffled adds)
+// is small against the 16 FMAs per lane it follows; blockIdx.y takes MD_COLS columns, so
+// that short vectors still give enough blocks.
 // When kdev is given (graph mode) the count is k + *kdev: the loop index lives in device memory.
-__global__ void __launch_bounds__(RED_THREADS) k_mdot(const Chunk* __restrict__ chunks, const double* __restrict__ V,
-                                                      long long ld, int k, const int* __restrict__ kdev,
-                                                      const double* __restrict__ w, double* __restrict__ part,
-                                                      int cols) {
-    __shared__ double sh[RED_THREADS / 32][GDC_MAX_LANCZOS + 1];
+constexpr int MD_THREADS = 64;
+constexpr int MD_PER = RED_CHUNK / MD_THREADS;
+constexpr int MD_COLS = 8;
+
+__global__ void __launch_bounds__(MD_THREADS) k_mdot(const Chunk* __restrict__ chunks, const double* __restrict__ V,
+                                                     long long ld, int k, const int* __restrict__ kdev,
+                                                     const double* __restrict__ w, double* __restrict__ part,
+                                                     int cols) {
+    __shared__ double sh[MD_THREADS / 32][MD_COLS];
     if (kdev) k += *kdev;
+    const int i0 = blockIdx.y * MD_COLS;
+    if (i0 >= k) return;
+    const int i1 = min(k, i0 + MD_COLS);
     const Chunk ch = chunks[blockIdx.x];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    double wv[RED_CHUNK / RED_THREADS];
+    const long long e0 = ch.lo + threadIdx.x;
+    const bool full = ch.hi - ch.lo == RED_CHUNK;
+    double wv[MD_PER];
 #pragma unroll
-    for (int u = 0; u < RED_CHUNK / RED_THREADS; ++u) {
-        const long long e = ch.lo + threadIdx.x + u * RED_THREADS;
+    for (int u = 0; u < MD_PER; ++u) {
+        const long long e = e0 + u * MD_THREADS;
         wv[u] = e < ch.hi ? w[e] : 0.0;
     }
-    for (int i = 0; i < k; ++i) {
-        const double* Vi = V + (long long)i * ld;
-        double acc = 0.0;
+    for (int i = i0; i < i1; ++i) {
+        const double* Vi = V + (long long)i * ld + e0;
+        double a0 = 0.0, a1 = 0.0;
+        if (full) {
 #pragma unroll
-        for (int u = 0; u < RED_CHUNK / RED_THREADS; ++u) {
-            const long long e = ch.lo + threadIdx.x + u * RED_THREADS;
-            if (e < ch.hi) acc = fma(Vi[e], wv[u], acc);
+            for (int u = 0; u < MD_PER; u += 2) {
+                a0 = fma(Vi[u * MD_THREADS], wv[u], a0);
+                a1 = fma(Vi[(u + 1) * MD_THREADS], wv[u + 1], a1);
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < MD_PER; u += 2) {
+                if (e0 + u * MD_THREADS < ch.hi) a0 = fma(Vi[u * MD_THREADS], wv[u], a0);
+                if (e0 + (u + 1) * MD_THREADS < ch.hi) a1 = fma(Vi[(u + 1) * MD_THREADS], wv[u + 1], a1);
+            }
         }
-        acc = warp_sum(acc);
-        if (lane == 0) sh[wid][i] = acc;
+        const double acc = warp_sum(a0 + a1);
+        if (lane == 0) sh[wid][i - i0] = acc;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < k; i += blockDim.x) {
-        double acc = 0.0;
-        for (int q = 0; q < RED_THREADS / 32; ++q) acc += sh[q][i];
-        part[(long long)blockIdx.x * cols + i] = acc;
-    }
+    for (int i = threadIdx.x; i < i1 - i0; i += blockDim.x)
+        part[(long long)blockIdx.x * cols + i0 + i] = sh[0][i] + sh[1][i];
 }
 
 // out[s * cols + i] = sum of the chunk partials of segment s, in chunk order
@@ -101,17 +120,32 @@ __global__ void k_seg_sum(int S, const int* __restrict__ seg_chunk_off, const do
     if (lane == 0) out[(long long)s * cols + i] = acc;
 }
 
-// w[e] -= sum_i h[s * cols + i] * V_i[e] for i < k
-__global__ void k_mupdate(const Chunk* __restrict__ chunks, const double* __restrict__ V, long long ld, int k,
-                          const int* __restrict__ kdev, const double* __restrict__ h, int cols, double* __restrict__ w) {
+// w[e] -= sum_i h[s * cols + i] * V_i[e] for i < k   (FP64-pipe bound like k_mdot; each thread
+// updates its four elements together so that four loads and FMAs are in flight per column)
+__global__ void __launch_bounds__(256) k_mupdate(const Chunk* __restrict__ chunks, const double* __restrict__ V,
+                                                 long long ld, int k, const int* __restrict__ kdev,
+                                                 const double* __restrict__ h, int cols, double* __restrict__ w) {
     if (kdev) k += *kdev;
     const Chunk ch = chunks[blockIdx.x];
     const double* hs = h + (long long)ch.seg * cols;
-    for (long long e = ch.lo + threadIdx.x; e < ch.hi; e += blockDim.x) {
-        double acc = w[e];
-        for (int i = 0; i < k; ++i) acc = fma(-hs[i], V[(long long)i * ld + e], acc);
-        w[e] = acc;
+    constexpr int PER = RED_CHUNK / 256;
+    const long long e0 = ch.lo + threadIdx.x;
+    double acc[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const long long e = e0 + u * 256;
+        acc[u] = e < ch.hi ? w[e] : 0.0;
     }
+    for (int i = 0; i < k; ++i) {
+        const double hv = -hs[i];
+        const double* Vi = V + (long long)i * ld + e0;
+#pragma unroll
+        for (int u = 0; u < PER; ++u)
+            if (e0 + u * 256 < ch.hi) acc[u] = fma(hv, Vi[u * 256], acc[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u)
+        if (e0 + u * 256 < ch.hi) w[e0 + u * 256] = acc[u];
 }
 
 // out[e] = scale_s * sum_i y[s * cols + i] * V_i[e] for i < kcount[s]   (+ out[e] when accumulate)
@@ -167,8 +201,8 @@ __global__ void k_sub_chunks(const Chunk* __restrict__ chunks, const double* __r
 // kdev (graph mode): the count is k + *kdev, at most kcap; the column grid covers kcap
 static void seg_mdot(gdc_ctx* c, const gdc::Seg& sg, const double* V, long long ld, int k, const double* w,
                      double* out, int cols, const int* kdev = nullptr, int kcap = 0) {
-    ++c->n_launch, k_mdot<<<sg.n_chunks, RED_THREADS, 0, c->stream>>>(sg.chunks, V, ld, k, kdev, w, c->red_part,
-                                                                      c->red_cols);
+    ++c->n_launch, k_mdot<<<dim3(sg.n_chunks, ceil_div(kdev ? kcap : k, MD_COLS)), MD_THREADS, 0, c->stream>>>(
+        sg.chunks, V, ld, k, kdev, w, c->red_part, c->red_cols);
     ++c->n_launch, k_seg_sum<<<dim3(c->S, ceil_div(kdev ? kcap : k, 8)), 256, 0, c->stream>>>(
         c->S, sg.seg_chunk_off, c->red_part, c->red_cols, k, kdev, out);
     (void)cols;
@@ -354,7 +388,9 @@ gdc_status gmres_solve(gdc_ctx* c, const double* b, double* x, gdc_solve_info* i
         for (; j < m; ++j) {
             double* Vj = c->gm_V + (long long)j * n;
             launch_precond(c, Vj, c->gm_z);
+            c->mv_active = c->gm_active;   // suspensions that have converged need no product
             saddle_op(c, prec, c->gm_z, c->gm_w);
+            c->mv_active = nullptr;
             if (prec == GDC_FP32_MIXED) inf.matvecs_fp32++; else inf.matvecs_fp64++;
             // classical Gram-Schmidt, twice
             seg_mdot(c, sg, c->gm_V, n, j + 1, c->gm_w, c->gm_h, cols);
@@ -636,7 +672,9 @@ gdc_status lanczos_sqrt(gdc_ctx* c, const double* W, double* out, double scale, 
     std::vector<int> act(c->S);
     for (int j = 0; j < kmax; ++j) {
         const double* Vj = c->lz_V + (long long)j * n;
+        c->mv_active = c->lz_active;   // suspensions that have stopped need no product
         rpy_op(c, prec, Vj, c->lz_w);
+        c->mv_active = nullptr;
         // w = M v_j orthogonalised against v_0..v_j twice (full reorthogonalisation)
         seg_mdot(c, sg, c->lz_V, n, j + 1, c->lz_w, c->lz_h, cols);
         ++c->n_launch, k_mupdate<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_V, n, j + 1, nullptr, c->lz_h, cols, c->lz_w);
@@ -868,7 +906,9 @@ void lanczos_sqrt_graph(gdc_ctx* c, const double* W, double* out, double scale, 
     ++c->n_launch, k_lz_begin<<<1, 32, 0, c->stream>>>(c->S, c->lz_active, c->ctl, kmax, h);
     cap_while_begin(c, h);
     const unsigned long long before = c->n_launch;
+    c->mv_active = c->lz_active;
     rpy_op(c, prec, c->lz_vcur, c->lz_w);
+    c->mv_active = nullptr;
     seg_mdot(c, sg, c->lz_V, n, 1, c->lz_w, c->lz_h, cols, jd, kmax);
     ++c->n_launch, k_mupdate<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_V, n, 1, jd, c->lz_h, cols, c->lz_w);
     seg_mdot(c, sg, c->lz_V, n, 1, c->lz_w, c->gm_h2, cols, jd, kmax);
@@ -924,7 +964,9 @@ void gmres_solve_graph(gdc_ctx* c, const double* b, double* x) {
         const unsigned long long before_i = c->n_launch;
         {
             launch_precond(c, c->gm_vcur, c->gm_z);
+            c->mv_active = c->gm_active;
             saddle_op(c, prec, c->gm_z, c->gm_w);
+            c->mv_active = nullptr;
             seg_mdot(c, sg, c->gm_V, n, 1, c->gm_w, c->gm_h, cols, jd, m);
             ++c->n_launch, k_mupdate<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->gm_V, n, 1, jd, c->gm_h, cols, c->gm_w);
             seg_mdot(c, sg, c->gm_V, n, 1, c->gm_w, c->gm_h2, cols, jd, m);

@@ -155,7 +155,8 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
 #endif
 
 template <int P>
-__global__ void __launch_bounds__(128, GDC_RPY32_MINB) k_rpy32(const MvItem* __restrict__ items, const long long* __restrict__ susp_blob_off,
+__global__ void __launch_bounds__(128, GDC_RPY32_MINB) k_rpy32(const MvItem* __restrict__ items, const int* __restrict__ active,
+                                               const long long* __restrict__ susp_blob_off,
                                                const float4* __restrict__ spos, const float4* __restrict__ sdup,
                                                const long long* __restrict__ body_blob_off,
                                                float4* __restrict__ part, int NBL, RpyConst32 k,
@@ -165,6 +166,12 @@ __global__ void __launch_bounds__(128, GDC_RPY32_MINB) k_rpy32(const MvItem* __r
     const MvItem it = items[blockIdx.x];
     const long long b0 = susp_blob_off[it.s];
     const int ns = (int)(susp_blob_off[it.s + 1] - b0);
+    if (active && !active[it.s]) {
+        // a suspension whose Krylov loop has stopped: its product is not used; leave zeros
+        for (int t = threadIdx.x; t < 256 * P && it.t0 + t < ns; t += 128)
+            part[(long long)it.k * NBL + b0 + it.t0 + t] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
     const float2 c23 = make_float2(k.c23, k.c23), mc2 = make_float2(-k.c2, -k.c2), one = make_float2(1.f, 1.f);
     const int ntile = (it.j1 - it.j0 + MV_TILE - 1) / MV_TILE;
     if (threadIdx.x == 0) {
@@ -438,7 +445,8 @@ static RpyConstDF df_constants(double a) {
 // ---- FP64 RPY pair kernel -----------------------------------------------------
 
 template <int TPT>
-__global__ void __launch_bounds__(128) k_rpy64(const MvItem* __restrict__ items, const long long* __restrict__ susp_blob_off,
+__global__ void __launch_bounds__(128) k_rpy64(const MvItem* __restrict__ items, const int* __restrict__ active,
+                                               const long long* __restrict__ susp_blob_off,
                                                const double4* __restrict__ spos, const double4* __restrict__ slam,
                                                double4* __restrict__ part, int NBL, double a) {
     __shared__ double4 sp[MV_TILE];
@@ -446,6 +454,11 @@ __global__ void __launch_bounds__(128) k_rpy64(const MvItem* __restrict__ items,
     const MvItem it = items[blockIdx.x];
     const long long b0 = susp_blob_off[it.s];
     const int ns = (int)(susp_blob_off[it.s + 1] - b0);
+    if (active && !active[it.s]) {   // stopped Krylov loop: product unused, leave zeros
+        for (int t = threadIdx.x; t < 128 * TPT && it.t0 + t < ns; t += 128)
+            part[(long long)it.k * NBL + b0 + it.t0 + t] = make_double4(0.0, 0.0, 0.0, 0.0);
+        return;
+    }
     const double c23 = 2.0 * a * a / 3.0, c2 = 2.0 * a * a, four_a2 = 4.0 * a * a;
     const double cA = 4.0 / (3.0 * a), c9 = 9.0 / (32.0 * a), cB = 1.0 / (8.0 * a * a);
     double xt[TPT], yt[TPT], zt[TPT], ax[TPT], ay[TPT], az[TPT];
@@ -512,12 +525,12 @@ void launch_rpy(gdc_ctx* c, int prec) {
                      (float)(4.0 / (3.0 * a)), (float)(9.0 / (32.0 * a)), (float)(1.0 / (8.0 * a * a))};
         // two targets per packed lane pair: tpt 4 -> P = 2, otherwise P = 1
         if (c->mv_tpt == 4)
-            ++c->n_launch, k_rpy32<2><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off, c->spos,
+            ++c->n_launch, k_rpy32<2><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->mv_active, c->susp_blob_off, c->spos,
                                                                             c->sdup, c->body_blob_off,
                                                                             (float4*)c->mv_part, c->NBL, k,
                                                                             c->dev_status);
         else
-            ++c->n_launch, k_rpy32<1><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off, c->spos,
+            ++c->n_launch, k_rpy32<1><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->mv_active, c->susp_blob_off, c->spos,
                                                                             c->sdup, c->body_blob_off,
                                                                             (float4*)c->mv_part, c->NBL, k,
                                                                             c->dev_status);
@@ -531,13 +544,13 @@ void launch_rpy(gdc_ctx* c, int prec) {
                                                                              c->slam64, (double4*)c->mv_part, c->NBL, k);
     } else {
         if (c->mv_tpt == 1)
-            ++c->n_launch, k_rpy64<1><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off, c->spos64, c->slam64,
+            ++c->n_launch, k_rpy64<1><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->mv_active, c->susp_blob_off, c->spos64, c->slam64,
                                                              (double4*)c->mv_part, c->NBL, c->p.a);
         else if (c->mv_tpt == 4)
-            ++c->n_launch, k_rpy64<4><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off, c->spos64, c->slam64,
+            ++c->n_launch, k_rpy64<4><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->mv_active, c->susp_blob_off, c->spos64, c->slam64,
                                                              (double4*)c->mv_part, c->NBL, c->p.a);
         else
-            ++c->n_launch, k_rpy64<2><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off, c->spos64, c->slam64,
+            ++c->n_launch, k_rpy64<2><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->mv_active, c->susp_blob_off, c->spos64, c->slam64,
                                                              (double4*)c->mv_part, c->NBL, c->p.a);
     }
     prof_end(c, pe);
@@ -991,7 +1004,7 @@ extern "C" gdc_status gdc_rpy_apply_noalloc(const double* r, const double* lambd
     RpyConst32 k{(float)(2.0 * a * a / 3.0), (float)(2.0 * a * a), (float)(4.0 * a * a), (float)(4.0 / (3.0 * a)),
                  (float)(9.0 / (32.0 * a)), (float)(1.0 / (8.0 * a * a))};
     // the pair kernel addresses partial sums as part[k * NBL + i]: pass the array's row length
-    k_rpy32<1><<<ntile * nk, 128, 0, st>>>(sc->items, sc->susp_blob_off, sc->spos, sc->sdup, sc->body_blob_off,
+    k_rpy32<1><<<ntile * nk, 128, 0, st>>>(sc->items, nullptr, sc->susp_blob_off, sc->spos, sc->sdup, sc->body_blob_off,
                                              sc->part, GDC_NOALLOC_MAX_BLOBS, k, sc->status);
     k_noalloc_epilogue<<<(n_blobs + 255) / 256, 256, 0, st>>>(sc, lambda, n_blobs, nk,
                                                               1.0 / (8.0 * 3.141592653589793 * eta), 4.0 / (3.0 * a), u);
