@@ -219,11 +219,12 @@ gdc_status gdc_saddle_offsets(const gdc_ctx* ctx, long long* off);
  *
  * u = M lambda for ONE suspension of n_blobs free blobs (no rigid bodies):
  * the unbounded RPY product with the overlapping-blob form, pair terms in
- * FP32 (the library's FP32 pair kernel), chunk sums and the self term in FP64.
+ * FP32 (the library's FP32 pair kernel), chunk sums and the corrections of the
+ * self pair and of pairs closer than 2a in FP64.
  * r (dev, 3 doubles per blob, lab positions), lambda (dev, 3 per blob) and
  * u (dev out, 3 per blob) are the caller's; stream is a cudaStream_t.
  *
- * It allocates nothing: its scratch (about 4.8 MB) is a fixed device array
+ * It allocates nothing: its scratch (about 7 MB) is a fixed device array
  * inside the library, present on every GPU that loads the library until the
  * process exits.  The first call on a device looks up that array's device
  * address, so make the first call on each device before any stream capture.

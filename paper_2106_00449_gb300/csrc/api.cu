@@ -248,6 +248,17 @@ static size_t carve(gdc_ctx* c, void* base) {
     c->mv_nk = w.take<int>(S);
     c->mv_part = (void*)w.take<double4>((long long)c->mv_cap_kmax * NBL);
     c->dev_status = w.take<int>(4);
+    c->h_near_items.clear();
+    for (int s = 0; s < c->S; ++s) {
+        const long long ns = c->h_blob_off[s + 1] - c->h_blob_off[s];
+        for (long long t0 = 0; t0 < ns; t0 += 256)
+            for (long long j0 = 0; j0 < ns; j0 += GDC_NEAR_SRC)
+                c->h_near_items.push_back(make_int4(s, (int)t0, (int)j0, (int)std::min(ns, j0 + GDC_NEAR_SRC)));
+    }
+    c->n_near_items = (int)c->h_near_items.size();
+    c->near_items = w.take<int4>(c->n_near_items);
+    c->near_cnt = w.take<int>(NBL);
+    c->near_idx = w.take<int>((long long)GDC_NEAR_CAP * NBL);
     c->ctl = w.take<LoopCtl>(1);
     c->rep = w.take<StepReport>(1);
     c->lz_vcur = w.take<double>(nl);
@@ -298,6 +309,7 @@ static gdc_status upload_layout(gdc_ctx* c, const double* tmpl_xyz_centred) {
     chk(up(c, c->seg_lz.chunks, c->seg_lz.h_chunks.data(), c->seg_lz.h_chunks.size()));
     chk(up(c, c->seg_lz.seg_chunk_off, c->seg_lz.h_seg_chunk_off.data(), S + 1));
     chk(up(c, c->mv_items, c->h_mv_items.data(), c->h_mv_items.size()));
+    chk(up(c, c->near_items, c->h_near_items.data(), c->h_near_items.size()));
     chk(up(c, c->mv_nk, c->h_mv_nk.data(), S));
     chk(cudaMemsetAsync(c->dev_status, 0, 4 * sizeof(int), c->stream));
     chk(cudaMemsetAsync(c->lz_hint, 0, sizeof(int) * S, c->stream));
@@ -823,6 +835,7 @@ gdc_status gdc_mobility_solve(gdc_ctx* c, const double* FT, const double* vbrev,
     launch_scatter_solution(c, c->gm_x, V, lambda);
     if (info) *info = inf;
     gdc_status e2 = cuda_check(c, cudaStreamSynchronize(c->stream), "mobility solve");
+    if (st == GDC_OK && e2 == GDC_OK) e2 = read_status(c);
     return st != GDC_OK ? st : e2;
 }
 
@@ -883,7 +896,8 @@ gdc_status gdc_rpy_apply(gdc_ctx* c, int precision, const double* lam, double* u
         return fail(c, GDC_ERR_INVALID_ARG, "unknown precision");
     load_at(c, c->Y, c->q);
     rpy_op(c, precision, lam, u);
-    return cuda_check(c, cudaStreamSynchronize(c->stream), "rpy apply");
+    gdc_status st = cuda_check(c, cudaStreamSynchronize(c->stream), "rpy apply");
+    return st != GDC_OK ? st : read_status(c);
 }
 
 gdc_status gdc_saddle_apply(gdc_ctx* c, int precision, const double* x, double* y) {
@@ -892,7 +906,8 @@ gdc_status gdc_saddle_apply(gdc_ctx* c, int precision, const double* x, double* 
         return fail(c, GDC_ERR_INVALID_ARG, "unknown precision");
     load_at(c, c->Y, c->q);
     saddle_op(c, precision, x, y);
-    return cuda_check(c, cudaStreamSynchronize(c->stream), "saddle apply");
+    gdc_status st = cuda_check(c, cudaStreamSynchronize(c->stream), "saddle apply");
+    return st != GDC_OK ? st : read_status(c);
 }
 
 gdc_status gdc_precond_apply(gdc_ctx* c, const double* r, double* z) {
@@ -907,6 +922,7 @@ gdc_status gdc_brownian_slip(gdc_ctx* c, const double* W, double* vbrev, int* it
     load_at(c, c->Y, c->q);
     gdc_status st = slip_at_loaded(c, W, vbrev, 0, iters, err);
     gdc_status e2 = cuda_check(c, cudaStreamSynchronize(c->stream), "brownian slip");
+    if (st == GDC_OK && e2 == GDC_OK) e2 = read_status(c);
     return st != GDC_OK ? st : e2;
 }
 

@@ -29,6 +29,8 @@
 #define GDC_MAX_RESTART 100
 #define GDC_MAX_LANCZOS 128
 #define GDC_MAX_TMPL_BLOBS 340   // 3n <= 1020 rows of a template block
+#define GDC_NEAR_CAP 32          // blobs closer than 2a listed per blob (beyond: a search of the suspension)
+#define GDC_NEAR_SRC 2048        // sources per block of the near-pair search
 
 namespace gdc {
 
@@ -161,6 +163,13 @@ struct gdc_ctx {
     std::vector<int> h_mv_nk;
     void* mv_part = 0;            // mv_kmax x NBL x (float4 | double4)
     const int* mv_active = 0;     // when set, suspensions flagged 0 are skipped by the pair kernels
+
+    // pairs closer than 2a (self pair excluded) of the loaded configuration, for the FP32
+    // products' corrections: per blob a count and up to GDC_NEAR_CAP blob indices
+    int4* near_items = 0;         // (suspension, first target, source range) of each search block
+    int n_near_items = 0;
+    std::vector<int4> h_near_items;
+    int *near_cnt = 0, *near_idx = 0;
     double pair_evals_per_matvec = 0.0;
 
     // host mirrors for convergence checks
@@ -278,6 +287,7 @@ void launch_pack_lambda(gdc_ctx* c, int prec, const double* x, int gm_layout);
 void launch_rpy(gdc_ctx* c, int prec);
 void launch_rpy_epilogue(gdc_ctx* c, int prec, const double* x, double* y, int gm_layout);
 void launch_forces_pair(gdc_ctx* c, int prec, double* fblob);
+void launch_near_build(gdc_ctx* c);
 void build_mv_items(gdc_ctx* c, int tpt, double waves);
 gdc_status autotune_pair_kernel(gdc_ctx* c);
 void plan_mv_capacity(gdc_ctx* c);

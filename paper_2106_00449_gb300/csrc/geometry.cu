@@ -51,6 +51,7 @@ void load_config(gdc_ctx* c, const double* Y, const double* q) {
     ++c->n_launch, k_blob_pos<<<ceil_div(c->NBL, 128), 128, 0, c->stream>>>(
         c->NBL, c->blob_body, c->blob_susp, c->body_tmpl, c->body_blob_off, c->tmpl_off, c->tmpl_xyz,
         Y, c->Rb, c->ref, c->r, c->spos, c->spos64);
+    launch_near_build(c);   // pairs closer than 2a, corrected after every FP32 product
 }
 
 // ---- Philox4x32-10 (Salmon et al., SC'11) + Box-Muller ----------------------

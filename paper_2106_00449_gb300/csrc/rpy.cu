@@ -63,28 +63,9 @@ struct RpyConst32 {
     float cB;      // 1/(8a^2)
 };
 
-// Exact pair term (all branches) for the rare tiles that hold a near pair.
-__device__ __forceinline__ void rpy_pair_exact(const RpyConst32& k, float dx, float dy, float dz, float lx, float ly,
-                                               float lz, float& ox, float& oy, float& oz) {
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    float A, B;
-    if (r2 >= k.four_a2) {
-        const float ri = rsqrtf(r2);
-        const float ri2 = ri * ri, ri3 = ri2 * ri;
-        A = fmaf(k.c23, ri3, ri);
-        B = ri3 * fmaf(-k.c2, ri2, 1.f);
-    } else if (r2 > 0.f) {
-        const float ri = rsqrtf(r2);
-        A = k.cA * fmaf(-k.c9, r2 * ri, 1.f);
-        B = ri * k.cB;
-    } else {
-        A = k.cA;
-        B = 0.f;
-    }
-    const float s = B * fmaf(dx, lx, fmaf(dy, ly, dz * lz));
-    ox = fmaf(A, lx, fmaf(s, dx, ox));
-    oy = fmaf(A, ly, fmaf(s, dy, oy));
-    oz = fmaf(A, lz, fmaf(s, dz, oz));
+static RpyConst32 rpy_const32(double a) {
+    return RpyConst32{(float)(2.0 * a * a / 3.0), (float)(2.0 * a * a), (float)(4.0 * a * a),
+                      (float)(4.0 / (3.0 * a)),   (float)(9.0 / (32.0 * a)), (float)(1.0 / (8.0 * a * a))};
 }
 
 // Packed FP32 pairs (Blackwell f32x2 instructions): lane .x and .y of a float2 hold
@@ -112,17 +93,13 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) {
     return u2f(r);
 }
 
-// Each thread owns 2P targets, evaluated two at a time with packed instructions.  Each
-// 32-source sub-chunk of a tile is first evaluated with the far-field formula only (no
-// branch), while the smallest r^2 per target is tracked; a target whose sub-chunk held a
-// pair closer than 2a (its own blob included) recomputes that sub-chunk with
-// rpy_pair_exact, discarding the far-field values (infinite or NaN for r = 0).  Shared
-// memory holds each source as (x,x,y,y) (z,z,lx,lx) (ly,ly,lz,lz), so one 16-byte load
-// feeds a packed operand.
-//
-// Same-body pairs are left out (the FP64 intra-body kernel adds them exactly): a
-// sub-chunk that overlaps the blob range of a target's own body is also redone, skipping
-// that range.
+// Each thread owns 2P targets, evaluated two at a time with packed instructions.  Every
+// pair of the suspension is evaluated with the far-field form of the RPY tensor at the
+// clamped distance max(r, 2a) (branch free); the self pair and the pairs closer than 2a,
+// for which that is not the RPY tensor, are corrected in FP64 by the epilogue from a list of
+// such pairs built once per configuration.  Shared memory holds each source as
+// (x,x,y,y) (z,z,lx,lx) (ly,ly,lz,lz), so one 16-byte load feeds a packed operand.  Sums run
+// over 32-source sub-chunks, then per tile, then across tiles with compensation.
 //
 // Source tiles are staged by the bulk-copy (TMA) engine: the packed source array already
 // holds the duplicated layout, so a tile is one contiguous cp.async.bulk into shared
@@ -158,7 +135,6 @@ template <int P>
 __global__ void __launch_bounds__(128, GDC_RPY32_MINB) k_rpy32(const MvItem* __restrict__ items, const int* __restrict__ active,
                                                const long long* __restrict__ susp_blob_off,
                                                const float4* __restrict__ spos, const float4* __restrict__ sdup,
-                                               const long long* __restrict__ body_blob_off,
                                                float4* __restrict__ part, int NBL, RpyConst32 k,
                                                int* __restrict__ status) {
     __shared__ __align__(128) float4 shbuf[2][3 * MV_TILE];
@@ -173,6 +149,7 @@ __global__ void __launch_bounds__(128, GDC_RPY32_MINB) k_rpy32(const MvItem* __r
         return;
     }
     const float2 c23 = make_float2(k.c23, k.c23), mc2 = make_float2(-k.c2, -k.c2), one = make_float2(1.f, 1.f);
+    const float four_a2 = k.four_a2;
     const int ntile = (it.j1 - it.j0 + MV_TILE - 1) / MV_TILE;
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&mbar[0])) : "memory");
@@ -184,7 +161,6 @@ __global__ void __launch_bounds__(128, GDC_RPY32_MINB) k_rpy32(const MvItem* __r
         bulk_tile_load(shbuf[0], sdup + 3 * (b0 + it.j0), 48u * (unsigned)min(MV_TILE, it.j1 - it.j0), &mbar[0]);
 
     float2 xt[P], yt[P], zt[P], ax[P], ay[P], az[P], cx[P], cy[P], cz[P];
-    int own_lo[2 * P], own_hi[2 * P];   // suspension-local blob range of each target's body
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         const float4 pa = spos[b0 + min(it.t0 + (int)threadIdx.x + (2 * p) * 128, ns - 1)];
@@ -192,11 +168,6 @@ __global__ void __launch_bounds__(128, GDC_RPY32_MINB) k_rpy32(const MvItem* __r
         xt[p] = make_float2(pa.x, pb.x);
         yt[p] = make_float2(pa.y, pb.y);
         zt[p] = make_float2(pa.z, pb.z);
-        const int ba = __float_as_int(pa.w), bb = __float_as_int(pb.w);
-        own_lo[2 * p] = (int)(body_blob_off[ba] - b0);
-        own_hi[2 * p] = (int)(body_blob_off[ba + 1] - b0);
-        own_lo[2 * p + 1] = (int)(body_blob_off[bb] - b0);
-        own_hi[2 * p + 1] = (int)(body_blob_off[bb + 1] - b0);
         ax[p] = ay[p] = az[p] = make_float2(0.f, 0.f);
         cx[p] = cy[p] = cz[p] = make_float2(0.f, 0.f);
     }
@@ -215,16 +186,11 @@ __global__ void __launch_bounds__(128, GDC_RPY32_MINB) k_rpy32(const MvItem* __r
         float2 tx[P], ty[P], tz[P];
 #pragma unroll
         for (int p = 0; p < P; ++p) tx[p] = ty[p] = tz[p] = make_float2(0.f, 0.f);
-        // 32-source sub-chunks: only a sub-chunk that holds a near or same-body pair is redone
         for (int jc = 0; jc < n; jc += 32) {
             const int je = min(jc + 32, n);
             float2 qx[P], qy[P], qz[P];
-            float mn[2 * P];
 #pragma unroll
-            for (int p = 0; p < P; ++p) {
-                qx[p] = qy[p] = qz[p] = make_float2(0.f, 0.f);
-                mn[2 * p] = mn[2 * p + 1] = 3.0e38f;
-            }
+            for (int p = 0; p < P; ++p) qx[p] = qy[p] = qz[p] = make_float2(0.f, 0.f);
 #pragma unroll 4
             for (int j = jc; j < je; ++j) {
                 const float4 s0 = sh[3 * j], s1 = sh[3 * j + 1], s2 = sh[3 * j + 2];
@@ -234,7 +200,7 @@ __global__ void __launch_bounds__(128, GDC_RPY32_MINB) k_rpy32(const MvItem* __r
                 for (int p = 0; p < P; ++p) {
                     const float2 dx = sub2(xs, xt[p]), dy = sub2(ys, yt[p]), dz = sub2(zs, zt[p]);
                     const float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
-                    const float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+                    const float2 ri = make_float2(rsqrtf(fmaxf(r2.x, four_a2)), rsqrtf(fmaxf(r2.y, four_a2)));
                     const float2 ri2 = mul2(ri, ri);
                     const float2 ri3 = mul2(ri2, ri);
                     const float2 A = fma2(c23, ri3, ri);
@@ -243,34 +209,10 @@ __global__ void __launch_bounds__(128, GDC_RPY32_MINB) k_rpy32(const MvItem* __r
                     qx[p] = fma2(A, lx, fma2(s, dx, qx[p]));
                     qy[p] = fma2(A, ly, fma2(s, dy, qy[p]));
                     qz[p] = fma2(A, lz, fma2(s, dz, qz[p]));
-                    mn[2 * p] = fminf(mn[2 * p], r2.x);
-                    mn[2 * p + 1] = fminf(mn[2 * p + 1], r2.y);
                 }
             }
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int lo = own_lo[2 * p + h] - j0, hi = own_hi[2 * p + h] - j0;   // own body, tile-relative
-                    if (mn[2 * p + h] < k.four_a2 || (lo < je && hi > jc)) {
-                        const float xq = h ? xt[p].y : xt[p].x, yq = h ? yt[p].y : yt[p].x, zq = h ? zt[p].y : zt[p].x;
-                        float ox = 0.f, oy = 0.f, oz = 0.f;
-                        for (int j = jc; j < je; ++j) {
-                            if (j >= lo && j < hi) continue;
-                            const float4 s0 = sh[3 * j], s1 = sh[3 * j + 1], s2 = sh[3 * j + 2];
-                            rpy_pair_exact(k, s0.x - xq, s0.z - yq, s1.x - zq, s1.z, s2.x, s2.z, ox, oy, oz);
-                        }
-                        if (h) {
-                            qx[p].y = ox;
-                            qy[p].y = oy;
-                            qz[p].y = oz;
-                        } else {
-                            qx[p].x = ox;
-                            qy[p].x = oy;
-                            qz[p].x = oz;
-                        }
-                    }
-                }
                 tx[p] = add2(tx[p], qx[p]);
                 ty[p] = add2(ty[p], qy[p]);
                 tz[p] = add2(tz[p], qz[p]);
@@ -521,18 +463,15 @@ void launch_rpy(gdc_ctx* c, int prec) {
     const int pe = prof_begin(c, prec == GDC_FP32_MIXED ? 0 : (prec == GDC_PREC_DF64 ? 3 : 1));
     if (prec == GDC_FP32_MIXED) {
         const double a = c->p.a;
-        RpyConst32 k{(float)(2.0 * a * a / 3.0), (float)(2.0 * a * a), (float)(4.0 * a * a),
-                     (float)(4.0 / (3.0 * a)), (float)(9.0 / (32.0 * a)), (float)(1.0 / (8.0 * a * a))};
+        const RpyConst32 k = rpy_const32(a);
         // two targets per packed lane pair: tpt 4 -> P = 2, otherwise P = 1
         if (c->mv_tpt == 4)
             ++c->n_launch, k_rpy32<2><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->mv_active, c->susp_blob_off, c->spos,
-                                                                            c->sdup, c->body_blob_off,
-                                                                            (float4*)c->mv_part, c->NBL, k,
+                                                                            c->sdup, (float4*)c->mv_part, c->NBL, k,
                                                                             c->dev_status);
         else
             ++c->n_launch, k_rpy32<1><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->mv_active, c->susp_blob_off, c->spos,
-                                                                            c->sdup, c->body_blob_off,
-                                                                            (float4*)c->mv_part, c->NBL, k,
+                                                                            c->sdup, (float4*)c->mv_part, c->NBL, k,
                                                                             c->dev_status);
     } else if (prec == GDC_PREC_DF64) {
         const RpyConstDF k = df_constants(c->p.a);
@@ -566,22 +505,97 @@ __device__ inline void load_part(const P* part, long long idx, double& x, double
     z = (double)v.z;
 }
 
+// Exact minus clamped pair coefficients (units of 1/(8 pi eta)) for a pair at distance r < 2a:
+// the FP32 pair kernel evaluates every pair, the self pair and overlapping pairs included,
+// with the far-field form at r clamped to 2a (A = 7/(12a), B = 1/(16a^3) there); the
+// overlapping branch of the RPY tensor has A = 4/(3a) (1 - 9r/(32a)), B = 1/(8a^2 r).
+// FP32 suffices: the correction joins a product whose pair terms are FP32.
+__device__ inline void near_delta(float a, float r, float& dA, float& dB) {
+    dA = 4.f / (3.f * a) * (1.f - 9.f * r / (32.f * a)) - 7.f / (12.f * a);
+    dB = (r > 0.f ? 1.f / (8.f * a * a * r) : 0.f) - 1.f / (16.f * a * a * a);
+}
+
+// Adds to (ux, uy, uz), in units of 1/(8 pi eta), the exact minus clamped terms of blob i's
+// pairs with blobs of other bodies closer than 2a: from the list when it holds them all, else
+// by a search of the suspension's blobs [so, se) (FP64 distances; blob_body given: skip
+// same-body blobs, else only j = i).  x holds lambda, 3 per blob, or in the saddle layout
+// through gm (blob -> offset) when gm is given.
+__device__ inline void near_pair_correction(long long i, long long so, long long se, const int* __restrict__ near_cnt,
+                                            const int* __restrict__ near_idx, const int* __restrict__ blob_body,
+                                            const double* __restrict__ r, const double* __restrict__ x,
+                                            const int* __restrict__ gm, double a, double& ux, double& uy, double& uz) {
+    const int m = near_cnt[i];
+    const double four_a2 = 4.0 * a * a;
+    const long long cnt = m <= GDC_NEAR_CAP ? m : se - so;
+    for (long long q = 0; q < cnt; ++q) {
+        const long long j = m <= GDC_NEAR_CAP ? (long long)near_idx[i * GDC_NEAR_CAP + q] : so + q;
+        if (j == i || (blob_body && blob_body[j] == blob_body[i])) continue;
+        const double dx = r[3 * j] - r[3 * i], dy = r[3 * j + 1] - r[3 * i + 1], dz = r[3 * j + 2] - r[3 * i + 2];
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        if (!(r2 < four_a2)) continue;   // at or beyond 2a the clamped form is the RPY tensor
+        float dA, dB;
+        near_delta((float)a, sqrtf((float)r2), dA, dB);
+        const long long oj = gm ? (long long)gm[j] : 3LL * j;
+        const double lx = x[oj], ly = x[oj + 1], lz = x[oj + 2];
+        const double s = (double)dB * (dx * lx + dy * ly + dz * lz);
+        ux += (double)dA * lx + s * dx;
+        uy += (double)dA * ly + s * dy;
+        uz += (double)dA * lz + s * dz;
+    }
+}
+
+// Subtracts from (ux, uy, uz) the terms the FP32 pair kernel added for blob i's own body
+// [j0, j1) (self pair included), recomputed from the same FP32 operands with the same
+// operations, so that the FP32 rounding of those near-field terms cancels; the FP64
+// intra-body kernel then adds the exact same-body block.
+__device__ inline void same_body_subtract(const float4 pt, long long j0, long long j1, const float4* __restrict__ sdup,
+                                          const RpyConst32& k, double& ux, double& uy, double& uz) {
+    for (long long j = j0; j < j1; ++j) {
+        const float4 s0 = sdup[3 * j], s1 = sdup[3 * j + 1], s2 = sdup[3 * j + 2];
+        const float dx = __fsub_rn(s0.x, pt.x), dy = __fsub_rn(s0.z, pt.y), dz = __fsub_rn(s1.x, pt.z);
+        const float lx = s1.z, ly = s2.x, lz = s2.z;
+        const float r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
+        const float ri = rsqrtf(fmaxf(r2, k.four_a2));
+        const float ri2 = __fmul_rn(ri, ri), ri3 = __fmul_rn(ri2, ri);
+        const float A = __fmaf_rn(k.c23, ri3, ri);
+        const float B = __fmul_rn(ri3, __fmaf_rn(-k.c2, ri2, 1.f));
+        const float sj = __fmul_rn(B, __fmaf_rn(dx, lx, __fmaf_rn(dy, ly, __fmul_rn(dz, lz))));
+        ux -= (double)__fmaf_rn(A, lx, __fmul_rn(sj, dx));
+        uy -= (double)__fmaf_rn(A, ly, __fmul_rn(sj, dy));
+        uz -= (double)__fmaf_rn(A, lz, __fmul_rn(sj, dz));
+    }
+}
+
+// u_i = c0 (sum of the chunk partial sums [+ near-pair corrections]) [- K V]
+//
+// near_cnt != 0 (FP32 products): corrects the pairs of other bodies closer than 2a and takes
+// out the pair kernel's same-body terms (the intra-body kernel adds them exactly).
 template <typename P>
 __global__ void k_rpy_epilogue(int NBL, const P* __restrict__ part, const int* __restrict__ blob_susp,
                                const int* __restrict__ nk, double c0, const double* __restrict__ x,
                                double* __restrict__ y, int gm_layout, const int* __restrict__ blob_gm,
                                const int* __restrict__ body_gm, const int* __restrict__ blob_body,
-                               const double* __restrict__ r, const double* __restrict__ Yc) {
+                               const double* __restrict__ r, const double* __restrict__ Yc,
+                               const int* __restrict__ near_cnt, const int* __restrict__ near_idx, double a,
+                               const long long* __restrict__ susp_blob_off, const long long* __restrict__ body_blob_off,
+                               const float4* __restrict__ spos, const float4* __restrict__ sdup, RpyConst32 k32) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= NBL) return;
     const int n = nk[blob_susp[i]];
     double ux = 0.0, uy = 0.0, uz = 0.0;
     for (int k = 0; k < n; ++k) {
-        double a, b, cc;
-        load_part(part, (long long)k * NBL + i, a, b, cc);
-        ux += a;
+        double a0, b, cc;
+        load_part(part, (long long)k * NBL + i, a0, b, cc);
+        ux += a0;
         uy += b;
         uz += cc;
+    }
+    if (near_cnt) {
+        const long long so = susp_blob_off[blob_susp[i]], se = susp_blob_off[blob_susp[i] + 1];
+        near_pair_correction(i, so, se, near_cnt, near_idx, blob_body, r, x, gm_layout ? blob_gm : nullptr, a, ux, uy,
+                             uz);
+        const int p = blob_body[i];
+        same_body_subtract(spos[i], body_blob_off[p], body_blob_off[p + 1], sdup, k32, ux, uy, uz);
     }
     ux *= c0;
     uy *= c0;
@@ -605,21 +619,101 @@ __global__ void k_rpy_epilogue(int NBL, const P* __restrict__ part, const int* _
     y[o + 2] = uz - kz;
 }
 
-static void launch_epilogue(gdc_ctx* c, int prec, double c0, const double* x, double* y, int gm_layout) {
+static void launch_epilogue(gdc_ctx* c, int prec, double c0, const double* x, double* y, int gm_layout,
+                            bool near) {
     if (prec == GDC_FP32_MIXED)
         ++c->n_launch, k_rpy_epilogue<float4><<<ceil_div(c->NBL, 256), 256, 0, c->stream>>>(
             c->NBL, (const float4*)c->mv_part, c->blob_susp, c->mv_nk, c0, x, y, gm_layout, c->blob_gm, c->body_gm,
-            c->blob_body, c->r, c->Yc);
+            c->blob_body, c->r, c->Yc, near ? c->near_cnt : nullptr, c->near_idx, c->p.a, c->susp_blob_off,
+            c->body_blob_off, c->spos, c->sdup, rpy_const32(c->p.a));
     else
         ++c->n_launch, k_rpy_epilogue<double4><<<ceil_div(c->NBL, 256), 256, 0, c->stream>>>(
             c->NBL, (const double4*)c->mv_part, c->blob_susp, c->mv_nk, c0, x, y, gm_layout, c->blob_gm, c->body_gm,
-            c->blob_body, c->r, c->Yc);
+            c->blob_body, c->r, c->Yc, nullptr, nullptr, c->p.a, c->susp_blob_off, c->body_blob_off, c->spos, c->sdup,
+            rpy_const32(c->p.a));
 }
 
 void launch_rpy_epilogue(gdc_ctx* c, int prec, const double* x, double* y, int gm_layout) {
-    launch_epilogue(c, prec, 1.0 / (8.0 * 3.141592653589793 * c->p.eta), x, y, gm_layout);
-    // the FP32 and df64 pair kernels leave out same-body pairs: add each body's block in FP64
-    if (prec == GDC_FP32_MIXED || prec == GDC_PREC_DF64) launch_intra_body(c, x, y, gm_layout);
+    launch_epilogue(c, prec, 1.0 / (8.0 * 3.141592653589793 * c->p.eta), x, y, gm_layout, prec == GDC_FP32_MIXED);
+    // same-body blocks in FP64: the df64 pair kernel leaves those pairs out and the FP32
+    // epilogue has taken the FP32 pair kernel's same-body terms out again
+    if (prec == GDC_PREC_DF64 || prec == GDC_FP32_MIXED) launch_intra_body(c, x, y, gm_layout);
+}
+
+// ---- pairs closer than 2a ------------------------------------------------------------
+
+// For every blob i, the blobs j of other bodies of its suspension whose FP32 r_ij^2, computed
+// exactly as the FP32 pair kernel computes it, is below 4a^2 -- the pairs the pair kernel
+// clamps: the pairs whose term the epilogue corrects (same-body pairs are replaced whole).  One block per (256 targets, source chunk) of one
+// suspension, two targets per thread in packed arithmetic; a found pair takes the next slot
+// of its target's list (near_cnt starts at zero), and k_near_sort then orders every list so
+// that the corrections are summed in a fixed order.
+__global__ void __launch_bounds__(128) k_near_build(const int4* __restrict__ items, const long long* __restrict__ susp_blob_off,
+                                                   const float4* __restrict__ spos, float four_a2,
+                                                   int* __restrict__ near_cnt, int* __restrict__ near_idx) {
+    __shared__ float4 sh[2 * 256];
+    const int4 it = items[blockIdx.x];   // (suspension, first target, first source, end source)
+    const long long b0 = susp_blob_off[it.x];
+    const int ns = (int)(susp_blob_off[it.x + 1] - b0);
+    const int ta = it.y + (int)threadIdx.x, tb = ta + 128;
+    const float4 pa = spos[b0 + min(ta, ns - 1)], pb = spos[b0 + min(tb, ns - 1)];
+    const float2 xt = make_float2(pa.x, pb.x), yt = make_float2(pa.y, pb.y), zt = make_float2(pa.z, pb.z);
+    for (int j0 = it.z; j0 < it.w; j0 += 256) {
+        const int n = min(256, it.w - j0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < n; e += 128) {
+            const float4 q = spos[b0 + j0 + e];
+            sh[2 * e] = make_float4(q.x, q.x, q.y, q.y);
+            sh[2 * e + 1] = make_float4(q.z, q.z, q.w, q.w);   // w: body index bits
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int j = 0; j < n; ++j) {
+            const float4 s0 = sh[2 * j], s1 = sh[2 * j + 1];
+            const float2 dx = sub2(make_float2(s0.x, s0.y), xt), dy = sub2(make_float2(s0.z, s0.w), yt),
+                         dz = sub2(make_float2(s1.x, s1.y), zt);
+            const float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+            if (r2.x < four_a2 || r2.y < four_a2) {   // rare
+                const int jg = j0 + j;
+                const int bj = __float_as_int(s1.z);
+                if (r2.x < four_a2 && bj != __float_as_int(pa.w) && ta < ns) {
+                    const int slot = atomicAdd(near_cnt + b0 + ta, 1);
+                    if (slot < GDC_NEAR_CAP) near_idx[(b0 + ta) * GDC_NEAR_CAP + slot] = (int)(b0 + jg);
+                }
+                if (r2.y < four_a2 && bj != __float_as_int(pb.w) && tb < ns) {
+                    const int slot = atomicAdd(near_cnt + b0 + tb, 1);
+                    if (slot < GDC_NEAR_CAP) near_idx[(b0 + tb) * GDC_NEAR_CAP + slot] = (int)(b0 + jg);
+                }
+            }
+        }
+    }
+}
+
+// Orders each blob's near-pair list (insertion sort; lists are short).  A count above
+// GDC_NEAR_CAP leaves the list incomplete: the epilogue then searches the suspension.
+__global__ void k_near_sort(int n, const int* __restrict__ near_cnt, int* __restrict__ near_idx) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int m = near_cnt[i];
+    if (m < 2 || m > GDC_NEAR_CAP) return;
+    int* l = near_idx + i * GDC_NEAR_CAP;
+    for (int a = 1; a < m; ++a) {
+        const int v = l[a];
+        int b = a - 1;
+        while (b >= 0 && l[b] > v) {
+            l[b + 1] = l[b];
+            --b;
+        }
+        l[b + 1] = v;
+    }
+}
+
+void launch_near_build(gdc_ctx* c) {
+    cudaMemsetAsync(c->near_cnt, 0, sizeof(int) * c->NBL, c->stream);
+    ++c->n_launch, k_near_build<<<c->n_near_items, 128, 0, c->stream>>>(c->near_items, c->susp_blob_off, c->spos,
+                                                                        (float)(4.0 * c->p.a * c->p.a), c->near_cnt,
+                                                                        c->near_idx);
+    ++c->n_launch, k_near_sort<<<ceil_div(c->NBL, 256), 256, 0, c->stream>>>(c->NBL, c->near_cnt, c->near_idx);
 }
 
 // ---- soft repulsion between blobs of different bodies --------------------------
@@ -745,7 +839,7 @@ void launch_forces_pair(gdc_ctx* c, int prec, double* fblob) {
     else
         GDC_FORCES_LAUNCH(2);
     prof_end(c, pe);
-    launch_epilogue(c, prec, 1.0, nullptr, fblob, 0);
+    launch_epilogue(c, prec, 1.0, nullptr, fblob, 0, false);
 }
 
 // ---- work list ------------------------------------------------------------------------
@@ -872,8 +966,8 @@ gdc_status autotune_pair_kernel(gdc_ctx* c) {
 // sources, chunk partial sums, the work list) lives in one file-scope device array of
 // fixed size, so the call allocates nothing; every GPU that loads the library holds the
 // array until the process exits.  It reuses the FP32 pair kernel above on one suspension
-// of free blobs (every blob is its own body, so only the self pair is skipped by the pair
-// kernel and its term I/(6 pi eta a) is added in the epilogue).
+// of free blobs, with the same near-pair list and FP64 corrections of the self pair and of
+// the pairs closer than 2a.
 
 #include <mutex>
 
@@ -887,7 +981,9 @@ struct NoallocScratch {
     float4 sdup[3 * GDC_NOALLOC_MAX_BLOBS];
     float4 part[GDC_NOALLOC_MAX_CHUNKS * GDC_NOALLOC_MAX_BLOBS];
     MvItem items[(GDC_NOALLOC_MAX_BLOBS / GDC_NOALLOC_TILE) * GDC_NOALLOC_MAX_CHUNKS];
-    long long body_blob_off[GDC_NOALLOC_MAX_BLOBS + 1];
+    int4 near_items[(GDC_NOALLOC_MAX_BLOBS / 256) * (GDC_NOALLOC_MAX_BLOBS / GDC_NEAR_SRC)];
+    int near_cnt[GDC_NOALLOC_MAX_BLOBS];
+    int near_idx[GDC_NOALLOC_MAX_BLOBS * GDC_NEAR_CAP];
     long long susp_blob_off[2];
     int status[4];   // set by the pair kernel if a tile copy times out (u is then incomplete)
 };
@@ -904,9 +1000,12 @@ __global__ void k_noalloc_prepare(NoallocScratch* __restrict__ sc, const double*
         cen[threadIdx.x] = acc / n;
     }
     __syncthreads();
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += gridDim.x * blockDim.x) {
-        sc->body_blob_off[i] = i;
-        if (i == n) continue;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        sc->near_cnt[i] = 0;
+        if (i % 256 == 0)   // near-pair blocks: 256 targets x source chunks of GDC_NEAR_SRC
+            for (int j0 = 0, q = 0; j0 < n; j0 += GDC_NEAR_SRC, ++q)
+                sc->near_items[(i / 256) * ((n + GDC_NEAR_SRC - 1) / GDC_NEAR_SRC) + q] =
+                    make_int4(0, i, j0, min(n, j0 + GDC_NEAR_SRC));
         const float x = (float)(r[3 * i] - cen[0]), y = (float)(r[3 * i + 1] - cen[1]), z = (float)(r[3 * i + 2] - cen[2]);
         const float lx = (float)lam[3 * i], ly = (float)lam[3 * i + 1], lz = (float)lam[3 * i + 2];
         sc->spos[i] = make_float4(x, y, z, __int_as_float(i));
@@ -930,9 +1029,10 @@ __global__ void k_noalloc_prepare(NoallocScratch* __restrict__ sc, const double*
     }
 }
 
-// u_i = c0 (sum of chunk partials + (4/(3a)) lambda_i)   (self term M_ii = I/(6 pi eta a))
-__global__ void k_noalloc_epilogue(const NoallocScratch* __restrict__ sc, const double* __restrict__ lam, int n, int nk,
-                                   double c0, double self, double* __restrict__ u) {
+// u_i = c0 (sum of chunk partials + self-pair and near-pair corrections)
+__global__ void k_noalloc_epilogue(const NoallocScratch* __restrict__ sc, const double* __restrict__ r,
+                                   const double* __restrict__ lam, int n, int nk, double c0, double a,
+                                   double* __restrict__ u) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double x = 0.0, y = 0.0, z = 0.0;
@@ -942,9 +1042,15 @@ __global__ void k_noalloc_epilogue(const NoallocScratch* __restrict__ sc, const 
         y += v.y;
         z += v.z;
     }
-    u[3 * i] = c0 * (x + self * lam[3 * i]);
-    u[3 * i + 1] = c0 * (y + self * lam[3 * i + 1]);
-    u[3 * i + 2] = c0 * (z + self * lam[3 * i + 2]);
+    // self pair: exact 4/(3a), clamped far field 7/(12a) (d = 0, so FP32 leaves only the rsqrt rounding)
+    const double cs = 4.0 / (3.0 * a) - 7.0 / (12.0 * a);
+    x += cs * lam[3 * i];
+    y += cs * lam[3 * i + 1];
+    z += cs * lam[3 * i + 2];
+    near_pair_correction(i, 0, n, sc->near_cnt, sc->near_idx, nullptr, r, lam, nullptr, a, x, y, z);
+    u[3 * i] = c0 * x;
+    u[3 * i + 1] = c0 * y;
+    u[3 * i + 2] = c0 * z;
 }
 
 // Device address of the scratch array and SM count, looked up once per device.
@@ -1004,10 +1110,14 @@ extern "C" gdc_status gdc_rpy_apply_noalloc(const double* r, const double* lambd
     RpyConst32 k{(float)(2.0 * a * a / 3.0), (float)(2.0 * a * a), (float)(4.0 * a * a), (float)(4.0 / (3.0 * a)),
                  (float)(9.0 / (32.0 * a)), (float)(1.0 / (8.0 * a * a))};
     // the pair kernel addresses partial sums as part[k * NBL + i]: pass the array's row length
-    k_rpy32<1><<<ntile * nk, 128, 0, st>>>(sc->items, nullptr, sc->susp_blob_off, sc->spos, sc->sdup, sc->body_blob_off,
-                                             sc->part, GDC_NOALLOC_MAX_BLOBS, k, sc->status);
-    k_noalloc_epilogue<<<(n_blobs + 255) / 256, 256, 0, st>>>(sc, lambda, n_blobs, nk,
-                                                              1.0 / (8.0 * 3.141592653589793 * eta), 4.0 / (3.0 * a), u);
+    const int near_chunks = (n_blobs + GDC_NEAR_SRC - 1) / GDC_NEAR_SRC;
+    k_near_build<<<((n_blobs + 255) / 256) * near_chunks, 128, 0, st>>>(sc->near_items, sc->susp_blob_off, sc->spos,
+                                                                       (float)(4.0 * a * a), sc->near_cnt, sc->near_idx);
+    k_near_sort<<<(n_blobs + 255) / 256, 256, 0, st>>>(n_blobs, sc->near_cnt, sc->near_idx);
+    k_rpy32<1><<<ntile * nk, 128, 0, st>>>(sc->items, nullptr, sc->susp_blob_off, sc->spos, sc->sdup, sc->part,
+                                             GDC_NOALLOC_MAX_BLOBS, k, sc->status);
+    k_noalloc_epilogue<<<(n_blobs + 255) / 256, 256, 0, st>>>(sc, r, lambda, n_blobs, nk,
+                                                              1.0 / (8.0 * 3.141592653589793 * eta), a, u);
     e = cudaGetLastError();
     if (e != cudaSuccess)
         return noalloc_fail(GDC_ERR_CUDA, std::string("gdc_rpy_apply_noalloc: launch failed: ") + cudaGetErrorString(e));

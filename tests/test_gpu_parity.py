@@ -323,3 +323,57 @@ def test_errors_are_reported(lib, wl_c1):
     # the context stays usable after an error
     V, _, info = ctx.mobility_solve(np.ones(6 * wl_c1.n_bodies))
     assert info["converged"]
+
+
+def _overlapping_workload(kind):
+    """Bodies whose blobs come closer than 2a to blobs of other bodies.
+
+    "pairs": a mixed suspension with a few bodies moved onto their neighbours (a handful of
+    overlapping pairs per blob, held in the near-pair list).  "pile": twelve 42-blob
+    icospheres around nearly the same centre (more than 32 blobs within 2a of most blobs,
+    which the FP32 product corrects by searching the suspension).
+    """
+    if kind == "pairs":
+        wl = WL.mixed_small(40, seed=5)
+        Y = wl.Y.copy()
+        for p in range(0, 12, 2):
+            Y[p + 1] = Y[p] + np.array([0.9, 0.4, -0.3]) * (1 + p / 12)
+        return WL.Workload("overlap_pairs", wl.templates, wl.body_tmpl, wl.susp_body_off, Y, wl.q, wl.params, wl.box)
+    from synthetic import shapes
+    rng = np.random.default_rng(8)
+    n = 12
+    Y = rng.uniform(-0.3, 0.3, size=(n, 3))
+    q = WL.random_unit_quaternions(rng, n)
+    return WL.Workload("overlap_pile", [shapes.icosphere42()], np.zeros(n, dtype=np.int32),
+                       np.array([0, n], dtype=np.int64), Y, q, dict(WL.c1().params), np.array([10.0]))
+
+
+@pytest.mark.parametrize("kind", ["pairs", "pile"])
+def test_rpy32_with_overlapping_bodies(lib, kind):
+    """FP32 product and saddle operator when blobs of different bodies overlap.
+
+    The FP32 kernel evaluates every pair at the clamped distance max(r, 2a); the epilogue
+    corrects the self pair and every pair closer than 2a in FP64.
+    """
+    wl = _overlapping_workload(kind)
+    lay, Y, q = susp_layout(wl, 0)
+    r, M, K, B = dense_state(lay, Y, q)
+    d = np.linalg.norm(r[:, None, :] - r[None, :, :], axis=-1)
+    other = lay.blob_body[:, None] != lay.blob_body[None, :]
+    near_other = ((d < 2.0) & other).sum(axis=1)
+    if kind == "pairs":
+        assert near_other.max() >= 1
+    else:
+        assert (((d < 2.0).sum(axis=1) - 1) > 32).mean() > 0.5
+    ctx = ctx_for(lib, wl, autotune=0)
+    rng = np.random.default_rng(17)
+    lam = rng.standard_normal(3 * wl.n_blobs)
+    u = _host(ctx.rpy_apply(lam, 1))
+    ref = M @ lam
+    assert rel(u, ref) < 2e-6
+    assert np.abs(u - ref).max() < 1e-5 * np.abs(ref).max()
+    n = int(ctx.saddle_off[-1])
+    x = rng.standard_normal(n)
+    y = _host(ctx.saddle_apply(x, 1))
+    y1, y2 = rigid.saddle_apply(M, K, x[:3 * wl.n_blobs], x[3 * wl.n_blobs:])
+    assert rel(y, np.concatenate([y1, y2])) < 2e-6
