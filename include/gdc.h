@@ -94,6 +94,10 @@ typedef struct {
                               per Krylov iteration.  Results are identical to graph = 0
                               (host-driven loops).  Used for the RFD divergence and for
                               Euler-Maruyama, not while gdc_profile is on.              */
+    int    pair_kernel;    /* FP32 RPY pair kernel, fixed at init: 1 ordered (every ordered
+                              pair, target-side sums), 2 symmetric (every unordered pair
+                              once, both sides), 0 the faster of the two as timed by the
+                              autotuner (symmetric when autotune = 0)                    */
 } gdc_params;
 
 typedef struct {

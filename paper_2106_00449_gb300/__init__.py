@@ -50,7 +50,8 @@ class _Params(ctypes.Structure):
                 ("lanczos_tol", ctypes.c_double), ("lanczos_max_iter", ctypes.c_int), ("rfd_delta", ctypes.c_double),
                 ("precision", ctypes.c_int), ("divmode", ctypes.c_int), ("scheme", ctypes.c_int),
                 ("rep_A", ctypes.c_double), ("rep_b", ctypes.c_double), ("shear_rate", ctypes.c_double),
-                ("seed", ctypes.c_ulonglong), ("autotune", ctypes.c_int), ("graph", ctypes.c_int)]
+                ("seed", ctypes.c_ulonglong), ("autotune", ctypes.c_int), ("graph", ctypes.c_int),
+                ("pair_kernel", ctypes.c_int)]
 
 
 class _SolveInfo(ctypes.Structure):
@@ -98,6 +99,7 @@ class Params:
     seed: int = 0
     autotune: int = 1
     graph: int = 1
+    pair_kernel: int = 0
 
     def _c(self) -> _Params:
         return _Params(**{f.name: getattr(self, f.name) for f in dataclasses.fields(self)})

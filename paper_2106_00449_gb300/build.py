@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgdc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "geometry.cu", "rpy.cu", "body.cu", "krylov.cu"]
+SOURCES = ["api.cu", "geometry.cu", "rpy.cu", "sym.cu", "body.cu", "krylov.cu"]
 
 
 def nvcc() -> str:
@@ -24,7 +24,7 @@ def nvcc() -> str:
 
 # the pair kernels flush FP32 denormals (their operands are never denormal), which lets
 # rsqrtf map to the bare reciprocal-square-root unit operation
-PER_FILE = {"rpy.cu": ["-ftz=true"]}
+PER_FILE = {"rpy.cu": ["-ftz=true"], "sym.cu": ["-ftz=true"]}
 
 
 def _compile(src: str, extra) -> str:

@@ -58,6 +58,7 @@ static const char* validate_params(const gdc_params* p) {
     if (!(p->dt > 0.0) || !std::isfinite(p->dt)) return "dt must be > 0";
     if (!(p->gmres_tol > 0.0) || !(p->gmres_tol < 1.0)) return "gmres_tol must be in (0, 1)";
     if (p->gmres_max_iter < 1) return "gmres_max_iter must be >= 1";
+    if (p->pair_kernel < 0 || p->pair_kernel > 2) return "pair_kernel must be 0 (choose), 1 (ordered) or 2 (symmetric)";
     if (p->gmres_restart < 2 || p->gmres_restart > GDC_MAX_RESTART) return "gmres_restart must be in [2, 100]";
     if (!(p->lanczos_tol > 0.0) || !(p->lanczos_tol < 1.0)) return "lanczos_tol must be in (0, 1)";
     if (p->lanczos_max_iter < 2 || p->lanczos_max_iter > GDC_MAX_LANCZOS) return "lanczos_max_iter must be in [2, 128]";
@@ -248,6 +249,12 @@ static size_t carve(gdc_ctx* c, void* base) {
     c->mv_nk = w.take<int>(S);
     c->mv_part = (void*)w.take<double4>((long long)c->mv_cap_kmax * NBL);
     c->dev_status = w.take<int>(4);
+    c->sym_items = w.take<SymItem>(c->sym_cap_items);
+    c->sym_row_nk = w.take<int>(std::max<long long>(1, c->sym_n_tiles));
+    c->sym_tile_base = w.take<long long>(S + 1);
+    c->sym_jbase = w.take<long long>(S + 1);
+    c->sym_part_i = w.take<float4>((long long)c->sym_cap_kmax * NBL);
+    c->sym_part_j = w.take<float4>(std::max<long long>(1, c->sym_n_jslots) * GDC_SYM_TILE);
     c->h_near_items.clear();
     for (int s = 0; s < c->S; ++s) {
         const long long ns = c->h_blob_off[s + 1] - c->h_blob_off[s];
@@ -751,9 +758,12 @@ gdc_status gdc_init(gdc_ctx** out, const gdc_params* params, int n_templates, co
     launch_template_setup(c);
     if ((st = cuda_check(c, cudaGetLastError(), "template setup")) != GDC_OK) return st;
     if ((st = read_status(c)) != GDC_OK) return st;
+    if ((st = sym_init_attributes(c)) != GDC_OK) return st;
     if (c->p.autotune) {
         load_at(c, c->Y, c->q);
         if ((st = autotune_pair_kernel(c)) != GDC_OK) return st;
+    } else if ((st = default_pair_kernel(c)) != GDC_OK) {
+        return st;
     }
     return GDC_OK;
 }
@@ -818,8 +828,10 @@ gdc_status gdc_set_params(gdc_ctx* c, const gdc_params* p) {
     if (p->a != c->p.a || p->eta != c->p.eta)
         return fail(c, GDC_ERR_INVALID_ARG, "a and eta are fixed at init (they shape the preconditioner)");
     const unsigned long long seed = c->p.seed;
+    const int pair_kernel = c->p.pair_kernel;
     c->p = *p;
     c->p.seed = seed;
+    c->p.pair_kernel = pair_kernel;   // the pair kernel is chosen at init
     drop_graph(c);   // parameters are baked into the captured launches
     return GDC_OK;
 }

@@ -31,6 +31,7 @@
 #define GDC_MAX_TMPL_BLOBS 340   // 3n <= 1020 rows of a template block
 #define GDC_NEAR_CAP 32          // blobs closer than 2a listed per blob (beyond: a search of the suspension)
 #define GDC_NEAR_SRC 2048        // sources per block of the near-pair search
+#define GDC_SYM_TILE 512         // blobs per tile of the symmetric FP32 pair kernel
 
 namespace gdc {
 
@@ -39,6 +40,12 @@ struct MvItem {      // one block of the pair kernels: targets [t0, t0+tile) x s
     int t0;          // first target, local to the suspension
     int j0, j1;      // source range, local to the suspension
     int k;           // source-chunk slot of the partial sums
+    int pad[3];
+};
+
+struct SymItem {     // one block of the symmetric pair kernel: target tile I x source tiles [J0, J1) of suspension s
+    int s, I, J0, J1;
+    int k;           // target-side partial-sum slot (the item's index within row I)
     int pad[3];
 };
 
@@ -164,6 +171,18 @@ struct gdc_ctx {
     void* mv_part = 0;            // mv_kmax x NBL x (float4 | double4)
     const int* mv_active = 0;     // when set, suspensions flagged 0 are skipped by the pair kernels
 
+    // symmetric FP32 pair kernel (each unordered pair once) and its work list
+    int use_sym = 0, sym_width = 4, sym_n_items = 0, sym_kmax = 1;
+    int sym_cap_items = 0, sym_cap_kmax = 1;
+    long long sym_n_jslots = 0, sym_n_tiles = 0;
+    gdc::SymItem* sym_items = 0;
+    int* sym_row_nk = 0;                      // target-side slots per tile row
+    long long *sym_tile_base = 0, *sym_jbase = 0;   // per suspension: first tile, first source-side slot
+    float4 *sym_part_i = 0, *sym_part_j = 0;  // target-side [slot][blob], source-side [slot][GDC_SYM_TILE]
+    std::vector<gdc::SymItem> h_sym_items;
+    std::vector<int> h_sym_row_nk;
+    std::vector<long long> h_sym_tile_base, h_sym_jbase;
+
     // pairs closer than 2a (self pair excluded) of the loaded configuration, for the FP32
     // products' corrections: per blob a count and up to GDC_NEAR_CAP blob indices
     int4* near_items = 0;         // (suspension, first target, source range) of each search block
@@ -288,8 +307,14 @@ void launch_rpy(gdc_ctx* c, int prec);
 void launch_rpy_epilogue(gdc_ctx* c, int prec, const double* x, double* y, int gm_layout);
 void launch_forces_pair(gdc_ctx* c, int prec, double* fblob);
 void launch_near_build(gdc_ctx* c);
+// sym.cu
+void build_sym_items(gdc_ctx* c, int width);
+gdc_status sym_upload(gdc_ctx* c);
+gdc_status sym_init_attributes(gdc_ctx* c);
+void launch_rpy32_sym(gdc_ctx* c);
 void build_mv_items(gdc_ctx* c, int tpt, double waves);
 gdc_status autotune_pair_kernel(gdc_ctx* c);
+gdc_status default_pair_kernel(gdc_ctx* c);
 void plan_mv_capacity(gdc_ctx* c);
 const char* noalloc_last_error();
 

@@ -12,6 +12,7 @@
 #include <numeric>
 
 #include "common.cuh"
+#include "pair_common.cuh"
 
 namespace gdc {
 
@@ -54,45 +55,6 @@ void launch_pack_lambda(gdc_ctx* c, int prec, const double* x, int gm_layout) {
 
 // ---- FP32 RPY pair kernel -----------------------------------------------------
 
-struct RpyConst32 {
-    float c23;     // 2a^2/3
-    float c2;      // 2a^2
-    float four_a2; // 4a^2
-    float cA;      // 4/(3a)
-    float c9;      // 9/(32a)
-    float cB;      // 1/(8a^2)
-};
-
-static RpyConst32 rpy_const32(double a) {
-    return RpyConst32{(float)(2.0 * a * a / 3.0), (float)(2.0 * a * a), (float)(4.0 * a * a),
-                      (float)(4.0 / (3.0 * a)),   (float)(9.0 / (32.0 * a)), (float)(1.0 / (8.0 * a * a))};
-}
-
-// Packed FP32 pairs (Blackwell f32x2 instructions): lane .x and .y of a float2 hold
-// the same quantity for two different targets.
-__device__ __forceinline__ unsigned long long f2u(float2 a) { return *reinterpret_cast<unsigned long long*>(&a); }
-__device__ __forceinline__ float2 u2f(unsigned long long a) { return *reinterpret_cast<float2*>(&a); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
-    unsigned long long r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(f2u(a)), "l"(f2u(b)), "l"(f2u(c)));
-    return u2f(r);
-}
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
-    unsigned long long r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2u(a)), "l"(f2u(b)));
-    return u2f(r);
-}
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
-    unsigned long long r;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2u(a)), "l"(f2u(b)));
-    return u2f(r);
-}
-__device__ __forceinline__ float2 add2(float2 a, float2 b) {
-    unsigned long long r;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2u(a)), "l"(f2u(b)));
-    return u2f(r);
-}
-
 // Each thread owns 2P targets, evaluated two at a time with packed instructions.  Every
 // pair of the suspension is evaluated with the far-field form of the RPY tensor at the
 // clamped distance max(r, 2a) (branch free); the self pair and the pairs closer than 2a,
@@ -105,27 +67,6 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) {
 // holds the duplicated layout, so a tile is one contiguous cp.async.bulk into shared
 // memory, completed on an mbarrier.  Two buffers: the copy of tile t+1 runs while tile t
 // is evaluated.  Waits are bounded; on a timeout the kernel flags status[1] and returns.
-
-__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void bulk_tile_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
-    unsigned long long state;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
-                 : "=l"(state) : "r"(smem_addr(bar)), "r"(bytes) : "memory");
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 :: "r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
-    (void)state;
-}
-
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
-    for (int i = 0; i < 400000; ++i) {
-        unsigned done;
-        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-                     : "=r"(done) : "r"(smem_addr(bar)), "r"(parity) : "memory");
-        if (done) return true;
-    }
-    return false;
-}
 
 #ifndef GDC_RPY32_MINB
 #define GDC_RPY32_MINB 6   // minimum resident blocks per SM requested from the register allocator
@@ -465,7 +406,9 @@ void launch_rpy(gdc_ctx* c, int prec) {
         const double a = c->p.a;
         const RpyConst32 k = rpy_const32(a);
         // two targets per packed lane pair: tpt 4 -> P = 2, otherwise P = 1
-        if (c->mv_tpt == 4)
+        if (c->use_sym)
+            launch_rpy32_sym(c);
+        else if (c->mv_tpt == 4)
             ++c->n_launch, k_rpy32<2><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->mv_active, c->susp_blob_off, c->spos,
                                                                             c->sdup, (float4*)c->mv_part, c->NBL, k,
                                                                             c->dev_status);
@@ -578,17 +521,42 @@ __global__ void k_rpy_epilogue(int NBL, const P* __restrict__ part, const int* _
                                const double* __restrict__ r, const double* __restrict__ Yc,
                                const int* __restrict__ near_cnt, const int* __restrict__ near_idx, double a,
                                const long long* __restrict__ susp_blob_off, const long long* __restrict__ body_blob_off,
-                               const float4* __restrict__ spos, const float4* __restrict__ sdup, RpyConst32 k32) {
+                               const float4* __restrict__ spos, const float4* __restrict__ sdup, RpyConst32 k32,
+                               const float4* __restrict__ sym_part_j, const int* __restrict__ sym_row_nk,
+                               const long long* __restrict__ sym_tile_base, const long long* __restrict__ sym_jbase) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= NBL) return;
-    const int n = nk[blob_susp[i]];
     double ux = 0.0, uy = 0.0, uz = 0.0;
-    for (int k = 0; k < n; ++k) {
-        double a0, b, cc;
-        load_part(part, (long long)k * NBL + i, a0, b, cc);
-        ux += a0;
-        uy += b;
-        uz += cc;
+    if (sym_part_j) {
+        // symmetric kernel: the target-side slots of the blob's tile row, then the source-side
+        // slots (I, J) of every tile I before the blob's tile J, in order
+        const int s = blob_susp[i];
+        const long long loc = i - susp_blob_off[s];
+        const int J = (int)(loc / GDC_SYM_TILE), e = (int)(loc % GDC_SYM_TILE);
+        const int n = sym_row_nk[sym_tile_base[s] + J];
+        for (int k = 0; k < n; ++k) {
+            double a0, b, cc;
+            load_part(part, (long long)k * NBL + i, a0, b, cc);
+            ux += a0;
+            uy += b;
+            uz += cc;
+        }
+        const long long s0 = sym_jbase[s] + (long long)J * (J - 1) / 2;
+        for (int I = 0; I < J; ++I) {
+            const float4 v = sym_part_j[(s0 + I) * GDC_SYM_TILE + e];
+            ux += (double)v.x;
+            uy += (double)v.y;
+            uz += (double)v.z;
+        }
+    } else {
+        const int n = nk[blob_susp[i]];
+        for (int k = 0; k < n; ++k) {
+            double a0, b, cc;
+            load_part(part, (long long)k * NBL + i, a0, b, cc);
+            ux += a0;
+            uy += b;
+            uz += cc;
+        }
     }
     if (near_cnt) {
         const long long so = susp_blob_off[blob_susp[i]], se = susp_blob_off[blob_susp[i] + 1];
@@ -621,16 +589,18 @@ __global__ void k_rpy_epilogue(int NBL, const P* __restrict__ part, const int* _
 
 static void launch_epilogue(gdc_ctx* c, int prec, double c0, const double* x, double* y, int gm_layout,
                             bool near) {
+    const bool sym = prec == GDC_FP32_MIXED && near && c->use_sym;   // RPY products only, not forces
     if (prec == GDC_FP32_MIXED)
         ++c->n_launch, k_rpy_epilogue<float4><<<ceil_div(c->NBL, 256), 256, 0, c->stream>>>(
-            c->NBL, (const float4*)c->mv_part, c->blob_susp, c->mv_nk, c0, x, y, gm_layout, c->blob_gm, c->body_gm,
-            c->blob_body, c->r, c->Yc, near ? c->near_cnt : nullptr, c->near_idx, c->p.a, c->susp_blob_off,
-            c->body_blob_off, c->spos, c->sdup, rpy_const32(c->p.a));
+            c->NBL, sym ? c->sym_part_i : (const float4*)c->mv_part, c->blob_susp, c->mv_nk, c0, x, y, gm_layout,
+            c->blob_gm, c->body_gm, c->blob_body, c->r, c->Yc, near ? c->near_cnt : nullptr, c->near_idx, c->p.a,
+            c->susp_blob_off, c->body_blob_off, c->spos, c->sdup, rpy_const32(c->p.a), sym ? c->sym_part_j : nullptr,
+            c->sym_row_nk, c->sym_tile_base, c->sym_jbase);
     else
         ++c->n_launch, k_rpy_epilogue<double4><<<ceil_div(c->NBL, 256), 256, 0, c->stream>>>(
             c->NBL, (const double4*)c->mv_part, c->blob_susp, c->mv_nk, c0, x, y, gm_layout, c->blob_gm, c->body_gm,
             c->blob_body, c->r, c->Yc, nullptr, nullptr, c->p.a, c->susp_blob_off, c->body_blob_off, c->spos, c->sdup,
-            rpy_const32(c->p.a));
+            rpy_const32(c->p.a), nullptr, nullptr, nullptr, nullptr);
 }
 
 void launch_rpy_epilogue(gdc_ctx* c, int prec, const double* x, double* y, int gm_layout) {
@@ -898,6 +868,7 @@ namespace gdc {
 // Candidate tilings of the pair kernels: targets per thread x work items per launch.
 static const int kTpt[2] = {2, 4};
 static const double kWaves[3] = {4.0, 8.0, 16.0};
+static const int kSymWidth[3] = {2, 4, 8};   // source tiles per item of the symmetric kernel
 
 void plan_mv_capacity(gdc_ctx* c) {
     int cap_items = 0, cap_k = 1;
@@ -910,6 +881,17 @@ void plan_mv_capacity(gdc_ctx* c) {
     c->mv_cap_items = cap_items;
     c->mv_cap_kmax = cap_k;
     build_mv_items(c, 2, 8.0);
+    int scap = 0, sk = 1;
+    for (int w : kSymWidth) {
+        build_sym_items(c, w);
+        scap = std::max(scap, c->sym_n_items);
+        sk = std::max(sk, c->sym_kmax);
+    }
+    c->sym_cap_items = scap;
+    c->sym_cap_kmax = sk;
+    c->sym_n_tiles = c->h_sym_tile_base.back();
+    c->sym_n_jslots = c->h_sym_jbase.back();
+    build_sym_items(c, 4);
 }
 
 static gdc_status upload_items(gdc_ctx* c) {
@@ -930,32 +912,66 @@ gdc_status autotune_pair_kernel(gdc_ctx* c) {
     if ((st = cuda_check(c, cudaEventCreate(&e1), "event")) != GDC_OK) return st;
     launch_normals(c, 0, 0, c->W);
     launch_pack_lambda(c, GDC_FP32_MIXED, c->W, 0);
+    const int only = c->p.pair_kernel;   // 0: both kernels, 1: ordered, 2: symmetric
     float best = 1e30f;
-    int bt = 2;
+    int bt = 2, bsym = 0, bwid = 4;
     double bw = 8.0;
-    for (int a = 0; a < 2; ++a)
-        for (int b = 0; b < 3; ++b) {
-            build_mv_items(c, kTpt[a], kWaves[b]);
-            if ((st = upload_items(c)) != GDC_OK) break;
-            launch_rpy(c, GDC_FP32_MIXED);  // warm-up
-            cudaEventRecord(e0, c->stream);
-            for (int r = 0; r < 3; ++r) launch_rpy(c, GDC_FP32_MIXED);
-            cudaEventRecord(e1, c->stream);
-            if ((st = cuda_check(c, cudaEventSynchronize(e1), "autotune")) != GDC_OK) break;
+    auto time3 = [&](float& ms) -> gdc_status {
+        launch_rpy(c, GDC_FP32_MIXED);  // warm-up
+        cudaEventRecord(e0, c->stream);
+        for (int r = 0; r < 3; ++r) launch_rpy(c, GDC_FP32_MIXED);
+        cudaEventRecord(e1, c->stream);
+        gdc_status s2 = cuda_check(c, cudaEventSynchronize(e1), "autotune");
+        if (s2 == GDC_OK) cudaEventElapsedTime(&ms, e0, e1);
+        return s2;
+    };
+    if (only != 2) {
+        c->use_sym = 0;
+        for (int a = 0; a < 2 && st == GDC_OK; ++a)
+            for (int b = 0; b < 3; ++b) {
+                build_mv_items(c, kTpt[a], kWaves[b]);
+                if ((st = upload_items(c)) != GDC_OK) break;
+                float ms = 0.f;
+                if ((st = time3(ms)) != GDC_OK) break;
+                if (ms < best) {
+                    best = ms;
+                    bt = kTpt[a];
+                    bw = kWaves[b];
+                    bsym = 0;
+                }
+            }
+    }
+    if (only != 1 && st == GDC_OK) {
+        c->use_sym = 1;
+        for (int w : kSymWidth) {
+            build_sym_items(c, w);
+            if ((st = sym_upload(c)) != GDC_OK) break;
             float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
+            if ((st = time3(ms)) != GDC_OK) break;
             if (ms < best) {
                 best = ms;
-                bt = kTpt[a];
-                bw = kWaves[b];
+                bwid = w;
+                bsym = 1;
             }
         }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != GDC_OK) return st;
     build_mv_items(c, bt, bw);
+    build_sym_items(c, bwid);
+    c->use_sym = bsym;
     c->autotune_ms = best / 3.0;
-    return upload_items(c);
+    if ((st = upload_items(c)) != GDC_OK) return st;
+    return sym_upload(c);
+}
+
+// Without the autotuner: the kernel params.pair_kernel names (symmetric for 0 and 2) with
+// the default work lists.
+gdc_status default_pair_kernel(gdc_ctx* c) {
+    c->use_sym = c->p.pair_kernel != 1;
+    gdc_status st = upload_items(c);
+    return st != GDC_OK ? st : sym_upload(c);
 }
 
 }  // namespace gdc

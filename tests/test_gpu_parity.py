@@ -377,3 +377,48 @@ def test_rpy32_with_overlapping_bodies(lib, kind):
     y = _host(ctx.saddle_apply(x, 1))
     y1, y2 = rigid.saddle_apply(M, K, x[:3 * wl.n_blobs], x[3 * wl.n_blobs:])
     assert rel(y, np.concatenate([y1, y2])) < 2e-6
+
+
+@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("which", ["mix120", "batch_multi_tile", "overlap_pile"])
+def test_rpy32_ordered_and_symmetric_kernels(lib, kernel, which):
+    """Both FP32 pair kernels against the dense oracle, on suspensions of several 512-blob
+    tiles (diagonal and off-diagonal tiles, ragged last tiles, work items of several tiles)."""
+    if which == "mix120":
+        wl = WL.mixed_small(120, seed=4)
+    elif which == "batch_multi_tile":
+        wl = WL.c4(seed=6, n_susp=5, nmin=20, nmax=70)
+    else:
+        wl = _overlapping_workload("pile")
+    ctx = ctx_for(lib, wl, autotune=0, pair_kernel=kernel)
+    rng = np.random.default_rng(19)
+    lam = rng.standard_normal(3 * wl.n_blobs)
+    u = _host(ctx.rpy_apply(lam, 1))
+    n = int(ctx.saddle_off[-1])
+    x = rng.standard_normal(n)
+    y = _host(ctx.saddle_apply(x, 1))
+    sl = blob_slices(wl)
+    for s in range(wl.n_susp):
+        lay, Y, q = susp_layout(wl, s)
+        a, b = sl[s]
+        r, M, K, B = dense_state(lay, Y, q)
+        ref = M @ lam[3 * a:3 * b]
+        assert rel(u[3 * a:3 * b], ref) < 2e-6, (s, rel(u[3 * a:3 * b], ref))
+        assert np.abs(u[3 * a:3 * b] - ref).max() < 1e-5 * np.abs(ref).max()
+        o = int(ctx.saddle_off[s])
+        lam_s, V_s = x[o:o + 3 * lay.n_blobs], x[o + 3 * lay.n_blobs:o + 3 * lay.n_blobs + 6 * lay.n_bodies]
+        y1, y2 = rigid.saddle_apply(M, K, lam_s, V_s)
+        assert rel(y[o:o + 3 * lay.n_blobs + 6 * lay.n_bodies], np.concatenate([y1, y2])) < 2e-6
+
+
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_fp32_step_parity_each_pair_kernel(lib, wl_mix, kernel):
+    wl = wl_mix
+    _, _, _, _, _, out = _step_case(lib, wl, 1)
+    ctx2 = ctx_for(lib, wl, precision=1, seed=77, rfd_delta=1e-3, lanczos_max_iter=128, gmres_tol=1e-6,
+                   lanczos_tol=1e-7, gmres_max_iter=1000, autotune=0, pair_kernel=kernel)
+    ctx2.step(1)
+    Y2, q2, _ = ctx2.get_state()
+    for s, o, e, ora in out:
+        assert np.abs(Y2[o:e] - ora["Y1"]).max() / np.abs(ora["Y1"]).max() < 1e-5
+        assert rot_err(q2[o:e], ora["q1"]) < 1e-5
