@@ -54,28 +54,42 @@ def _dist():
     return world, rank, local
 
 
-def pair_kernel_fingerprint() -> str:
-    """Hash of the FP32 pair kernel's source and its tiling constants."""
+# the FP32 pair kernels: (source file, start of the kernel, tiling macros, ncu summary)
+PAIR_KERNELS = {
+    1: ("rpy.cu", "template <int P>\n__global__ void __launch_bounds__(128, GDC_RPY32_MINB) k_rpy32",
+        r"#define (GDC_MV_TILE|GDC_RPY32_MINB) (\S+)", "k_rpy32_c3_65k.md", "k_rpy32 (ordered FP32 RPY pair kernel)"),
+    2: ("sym.cu", "__global__ void __launch_bounds__(128, GDC_SYM_MINB) k_rpy32_sym",
+        r"#define (GDC_SYM_MINB|GDC_SYM_TILE) (\S+)", "k_rpy32_sym_c3_65k.md",
+        "k_rpy32_sym (symmetric FP32 RPY pair kernel)"),
+}
+
+
+def pair_kernel_fingerprint(kind: int = 1) -> str:
+    """Hash of an FP32 pair kernel's source and its tiling constants."""
     import hashlib
     import re
-    src = open(os.path.join(ROOT, "paper_2106_00449_gb300", "csrc", "rpy.cu")).read()
-    start = src.index("template <int P>\n__global__ void __launch_bounds__(128, GDC_RPY32_MINB) k_rpy32")
+    fname, head, macro_re, _, _ = PAIR_KERNELS[kind]
+    src = open(os.path.join(ROOT, "paper_2106_00449_gb300", "csrc", fname)).read()
+    start = src.index(head)
     end = src.index("\n}\n", start) + 3
-    macros = re.findall(r"#define (GDC_MV_TILE|GDC_RPY32_MINB) (\S+)", src)
+    macros = re.findall(macro_re, src)
+    if kind == 2:
+        macros += re.findall(r"#define (GDC_SYM_TILE) (\S+)",
+                             open(os.path.join(ROOT, "paper_2106_00449_gb300", "csrc", "common.cuh")).read())
     return hashlib.sha256((src[start:end] + repr(macros)).encode()).hexdigest()[:16]
 
 
-def captured_traffic():
-    """DRAM bytes per launch of the FP32 pair kernel from the committed ncu summary.
+def captured_traffic(kind: int = 1):
+    """DRAM bytes per launch of an FP32 pair kernel from its committed ncu summary.
 
     None when the kernel's source changed since that capture (the figure would be stale).
     """
     import re
     try:
-        text = open(os.path.join(ROOT, "profiles", "k_rpy32_c3_65k.md")).read()
+        text = open(os.path.join(ROOT, "profiles", PAIR_KERNELS[kind][3])).read()
         h = re.search(r"kernel_source_sha256: (\w+)", text)
         b = re.search(r"dram_bytes_per_launch: (\d+)", text)
-        if h and b and h.group(1) == pair_kernel_fingerprint():
+        if h and b and h.group(1) == pair_kernel_fingerprint(kind):
             return int(b.group(1))
     except (OSError, ValueError):
         pass
@@ -326,19 +340,27 @@ def main(argv=None) -> int:
     peak_tf = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     avg_s = prof["rpy32_ms"] / max(prof["rpy32_launches"], 1) / 1000.0
     achieved_tf = FLOPS_PER_PAIR * prof["pairs_per_product"] / avg_s / 1e12 if avg_s > 0 else None
-    roof = {"bound": "alu", "kernel": "k_rpy32 (FP32 RPY pair kernel)", "achieved": achieved_tf,
+    kind = int(prof.get("pair_kernel", 1)) or 1
+    roof = {"bound": "alu", "kernel": PAIR_KERNELS[kind][4], "achieved": achieved_tf,
             "peak": peak_tf, "unit": "TFLOP/s", "frac": (achieved_tf / peak_tf) if achieved_tf else None,
-            "traffic": captured_traffic(),
-            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch, "
-                              "profiles/k_rpy32_c3_65k.md (null when the kernel source differs)",
+            "traffic": captured_traffic(kind),
+            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch, profiles/"
+                              + PAIR_KERNELS[kind][3] + " (null when the kernel source differs)",
             "peak_source": (f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flops x {sm_max:.0f} MHz "
                             f"(sm_max_mhz of MEASURED_PEAKS.json, {peak_src})"),
             "avg_launch_ms": avg_s * 1000.0, "launches": prof["rpy32_launches"],
             "timing": "CUDA events on the library stream around every launch, over a second timed region "
                       "of the same number of steps run host-driven",
-            "tiling": {"targets_per_thread": prof["targets_per_thread"], "work_waves": prof["work_waves"],
+            "tiling": {"pair_kernel": "symmetric" if kind == 2 else "ordered",
+                       "targets_per_thread": 4 if kind == 2 else prof["targets_per_thread"],
+                       "work_waves": None if kind == 2 else prof["work_waves"],
+                       "source_tiles_per_item": prof.get("sym_width") if kind == 2 else None,
                        "autotuned": prof["autotune_ms"] > 0},
-            "flops_per_pair": FLOPS_PER_PAIR, "pairs_per_launch": prof["pairs_per_product"]}
+            "flops_per_pair": FLOPS_PER_PAIR, "pairs_per_launch": prof["pairs_per_product"],
+            "flop_count": ("33 flops per ordered pair (i, j), N_b^2 per launch, whichever kernel runs; the "
+                           "symmetric kernel evaluates each unordered pair once for both blobs "
+                           "(unique_pairs_per_launch), so it executes about 51/66 of those flops"),
+            "unique_pairs_per_launch": prof.get("unique_pairs_per_product")}
     if clocks.get("sm_mhz") and achieved_tf:
         roof["frac_at_sampled_clock"] = achieved_tf / (n_sm * FP32_LANES_PER_SM * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
     line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,

@@ -254,6 +254,9 @@ typedef struct {
     double autotune_ms;                 /* fastest FP32 product found at init (0: none)  */
     unsigned long long rpydf_launches;  /* double-float residual pair-kernel launches     */
     double rpydf_ms;                    /* their summed CUDA-event durations              */
+    int    pair_kernel;                 /* FP32 pair kernel in use: 1 ordered, 2 symmetric */
+    int    sym_width;                   /* source tiles per work item (symmetric kernel)  */
+    double unique_pairs_per_product;    /* unordered pairs incl. self, sum n (n + 1) / 2  */
 } gdc_profile_info;
 
 /* Reset the counters; enable != 0 also brackets every pair-kernel launch with

@@ -71,7 +71,9 @@ class _Profile(ctypes.Structure):
                 ("rpy32_ms", ctypes.c_double), ("rpy64_ms", ctypes.c_double), ("force_ms", ctypes.c_double),
                 ("pairs_per_product", ctypes.c_double), ("targets_per_thread", ctypes.c_int),
                 ("work_waves", ctypes.c_double), ("autotune_ms", ctypes.c_double),
-                ("rpydf_launches", ctypes.c_ulonglong), ("rpydf_ms", ctypes.c_double)]
+                ("rpydf_launches", ctypes.c_ulonglong), ("rpydf_ms", ctypes.c_double),
+                ("pair_kernel", ctypes.c_int), ("sym_width", ctypes.c_int),
+                ("unique_pairs_per_product", ctypes.c_double)]
 
 
 class _Trace(ctypes.Structure):

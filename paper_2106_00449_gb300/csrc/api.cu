@@ -815,6 +815,14 @@ gdc_status gdc_profile_read(gdc_ctx* c, gdc_profile_info* out) {
     out->targets_per_thread = c->mv_tpt;
     out->work_waves = c->mv_waves;
     out->autotune_ms = c->autotune_ms;
+    out->pair_kernel = c->use_sym ? 2 : 1;
+    out->sym_width = c->sym_width;
+    double up = 0.0;
+    for (int s = 0; s < c->S; ++s) {
+        const double n = (double)(c->h_blob_off[s + 1] - c->h_blob_off[s]);
+        up += n * (n + 1.0) / 2.0;
+    }
+    out->unique_pairs_per_product = up;
     return GDC_OK;
 }
 

@@ -493,6 +493,14 @@ __device__ inline void near_pair_correction(long long i, long long so, long long
 // intra-body kernel then adds the exact same-body block.
 __device__ inline void same_body_subtract(const float4 pt, long long j0, long long j1, const float4* __restrict__ sdup,
                                           const RpyConst32& k, double& ux, double& uy, double& uz) {
+    // summed in FP32 with compensation (FP64 adds are slow on GB300), subtracted once
+    float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
+    auto kahan = [](float& sum, float& comp, float v) {
+        const float y = __fsub_rn(v, comp);
+        const float t = __fadd_rn(sum, y);
+        comp = __fsub_rn(__fsub_rn(t, sum), y);
+        sum = t;
+    };
     for (long long j = j0; j < j1; ++j) {
         const float4 s0 = sdup[3 * j], s1 = sdup[3 * j + 1], s2 = sdup[3 * j + 2];
         const float dx = __fsub_rn(s0.x, pt.x), dy = __fsub_rn(s0.z, pt.y), dz = __fsub_rn(s1.x, pt.z);
@@ -503,10 +511,13 @@ __device__ inline void same_body_subtract(const float4 pt, long long j0, long lo
         const float A = __fmaf_rn(k.c23, ri3, ri);
         const float B = __fmul_rn(ri3, __fmaf_rn(-k.c2, ri2, 1.f));
         const float sj = __fmul_rn(B, __fmaf_rn(dx, lx, __fmaf_rn(dy, ly, __fmul_rn(dz, lz))));
-        ux -= (double)__fmaf_rn(A, lx, __fmul_rn(sj, dx));
-        uy -= (double)__fmaf_rn(A, ly, __fmul_rn(sj, dy));
-        uz -= (double)__fmaf_rn(A, lz, __fmul_rn(sj, dz));
+        kahan(sx, cx, __fmaf_rn(A, lx, __fmul_rn(sj, dx)));
+        kahan(sy, cy, __fmaf_rn(A, ly, __fmul_rn(sj, dy)));
+        kahan(sz, cz, __fmaf_rn(A, lz, __fmul_rn(sj, dz)));
     }
+    ux -= (double)sx - (double)cx;
+    uy -= (double)sy - (double)cy;
+    uz -= (double)sz - (double)cz;
 }
 
 // u_i = c0 (sum of the chunk partial sums [+ near-pair corrections]) [- K V]
@@ -529,25 +540,37 @@ __global__ void k_rpy_epilogue(int NBL, const P* __restrict__ part, const int* _
     double ux = 0.0, uy = 0.0, uz = 0.0;
     if (sym_part_j) {
         // symmetric kernel: the target-side slots of the blob's tile row, then the source-side
-        // slots (I, J) of every tile I before the blob's tile J, in order
+        // slots (I, J) of every tile I before the blob's tile J, in order.  FP32 partials are
+        // added with compensation in FP32 (GB300 adds in FP64 at a small fraction of the FP32
+        // rate), then converted once.
         const int s = blob_susp[i];
         const long long loc = i - susp_blob_off[s];
         const int J = (int)(loc / GDC_SYM_TILE), e = (int)(loc % GDC_SYM_TILE);
         const int n = sym_row_nk[sym_tile_base[s] + J];
+        const float4* pi = reinterpret_cast<const float4*>(part);
+        float sx = 0.f, sy = 0.f, sz = 0.f, kx = 0.f, ky = 0.f, kz = 0.f;
+        auto kahan = [](float& sum, float& comp, float v) {
+            const float y = __fsub_rn(v, comp);
+            const float t = __fadd_rn(sum, y);
+            comp = __fsub_rn(__fsub_rn(t, sum), y);
+            sum = t;
+        };
         for (int k = 0; k < n; ++k) {
-            double a0, b, cc;
-            load_part(part, (long long)k * NBL + i, a0, b, cc);
-            ux += a0;
-            uy += b;
-            uz += cc;
+            const float4 v = pi[(long long)k * NBL + i];
+            kahan(sx, kx, v.x);
+            kahan(sy, ky, v.y);
+            kahan(sz, kz, v.z);
         }
         const long long s0 = sym_jbase[s] + (long long)J * (J - 1) / 2;
         for (int I = 0; I < J; ++I) {
             const float4 v = sym_part_j[(s0 + I) * GDC_SYM_TILE + e];
-            ux += (double)v.x;
-            uy += (double)v.y;
-            uz += (double)v.z;
+            kahan(sx, kx, v.x);
+            kahan(sy, ky, v.y);
+            kahan(sz, kz, v.z);
         }
+        ux = (double)sx - (double)kx;
+        uy = (double)sy - (double)ky;
+        uz = (double)sz - (double)kz;
     } else {
         const int n = nk[blob_susp[i]];
         for (int k = 0; k < n; ++k) {

@@ -30,12 +30,13 @@ def main(argv=None) -> int:
     ap.add_argument("--workload", default="c3_65k")
     ap.add_argument("--bodies", type=int, default=0, help="use only the first N bodies (0 = all)")
     ap.add_argument("--reps", type=int, default=5)
-    ap.add_argument("--tpt", type=int, default=0, help="unused placeholder for tile-shape experiments")
+    ap.add_argument("--pair-kernel", type=int, default=0, help="FP32 pair kernel: 0 autotuned, 1 ordered, 2 symmetric")
     args = ap.parse_args(argv)
     wl = WL.BY_NAME[args.workload]()
     if args.bodies:
         wl = wl.first_bodies(args.bodies)
-    ctx = g.context_from_workload(wl, precision=g.FP32_MIXED, rfd_delta=1e-3, lanczos_max_iter=128)
+    ctx = g.context_from_workload(wl, precision=g.FP32_MIXED, rfd_delta=1e-3, lanczos_max_iter=128,
+                                  pair_kernel=args.pair_kernel)
     rng = np.random.default_rng(0)
     lam = torch.as_tensor(rng.standard_normal(3 * wl.n_blobs), device=ctx.device)
     x = torch.as_tensor(rng.standard_normal(int(ctx.saddle_off[-1])), device=ctx.device)
@@ -61,8 +62,9 @@ def main(argv=None) -> int:
     e1.record(ctx.stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.reps
+    prof = ctx.profile_read()
     print(json.dumps({"op": args.op, "workload": wl.name, "n_blobs": wl.n_blobs, "ms_per_call": ms,
-                      "pairs": wl.pair_evals_per_matvec()}))
+                      "pairs": wl.pair_evals_per_matvec(), "pair_kernel": prof["pair_kernel"]}))
     return 0
 
 
