@@ -650,7 +650,11 @@ static gdc_status graph_step(gdc_ctx* c, gdc_step_info* info) {
     unsigned long long launches = c->graph_base_launches;
     for (const auto& lp : c->graph_loops) {
         const int slot = lp.first;
-        const long long runs = slot < 3 ? r.lz_exec[slot] : (slot == REP_GM_TOTAL ? r.gm_total : r.gm_outer);
+        const long long runs = slot < 3 ? r.lz_exec[slot]
+                               : slot == REP_GM_TOTAL ? r.gm_total
+                               : slot == REP_GM_OUTER ? r.gm_outer
+                               : slot == REP_GM_DF    ? r.gm_df
+                                                      : r.gm_outer - r.gm_df;
         launches += lp.second * (unsigned long long)std::max(0LL, runs);
     }
     c->n_launch += launches;
@@ -664,8 +668,8 @@ static gdc_status graph_step(gdc_ctx* c, gdc_step_info* info) {
     inf.solve.residual = r.gm_residual;
     inf.solve.converged = r.gm_converged;
     if (c->p.precision == GDC_FP32_MIXED) {
-        inf.solve.matvecs_fp32 = r.gm_total;
-        inf.solve.matvecs_fp64 = r.gm_outer;
+        inf.solve.matvecs_fp32 = r.gm_total + (r.gm_outer - r.gm_df);
+        inf.solve.matvecs_fp64 = r.gm_df;
     } else {
         inf.solve.matvecs_fp64 = r.gm_total + r.gm_outer;
     }

@@ -86,6 +86,7 @@ struct StepReport {
     int lz_notconv[3];   // stopped at lanczos_max_iter with the change above lanczos_tol
     int lz_exec[3];      // iterations the WHILE node ran
     int gm_total, gm_cycles, gm_converged, gm_bad, gm_notconv, gm_outer;
+    int gm_df;           // accurate residual products (the other cycles updated the residual in FP32)
     int status[4];       // copy of the device status words
     int ok;              // 1 when the state was advanced
     int pad;
@@ -211,6 +212,7 @@ struct gdc_ctx {
     int graph_valid = 0;
     cudaStream_t cap_stream[3] = {0, 0, 0};   // top-level capture, loop body, nested loop body
     cudaStream_t cap_saved[3] = {0, 0, 0};
+    cudaGraph_t cap_bodies[2] = {0, 0};        // the two bodies of the IF/ELSE node being captured
     int cap_depth = 0;
     cudaError_t cap_err = cudaSuccess;
     unsigned long long graph_base_launches = 0;               // kernels outside the loops
@@ -339,7 +341,11 @@ void cap_while_begin(gdc_ctx* c, cudaGraphConditionalHandle h);
 void cap_while_end(gdc_ctx* c, int report_slot, unsigned long long launches_before);
 void lanczos_sqrt_graph(gdc_ctx* c, const double* W, double* out, double scale, int fixed_mode, int run);
 void gmres_solve_graph(gdc_ctx* c, const double* b, double* x);
-// report slots of the loops: Lanczos runs 0..2, GMRES inner iterations, GMRES cycles
-enum { REP_LZ0 = 0, REP_GM_TOTAL = 3, REP_GM_OUTER = 4 };
+void cap_ifelse_begin(gdc_ctx* c, cudaGraphConditionalHandle h);
+void cap_ifelse_next(gdc_ctx* c, int report_slot, unsigned long long launches_before);
+void cap_ifelse_end(gdc_ctx* c, int report_slot, unsigned long long launches_before);
+// report slots of the loops and branches: Lanczos runs 0..2, GMRES inner iterations, GMRES
+// cycles, cycles with an accurate residual product, cycles with an updated residual
+enum { REP_LZ0 = 0, REP_GM_TOTAL = 3, REP_GM_OUTER = 4, REP_GM_DF = 5, REP_GM_UPD = 6 };
 
 }  // namespace gdc

@@ -18,6 +18,9 @@
 namespace gdc {
 
 constexpr int RED_CHUNK = 1024;   // elements per reduction chunk
+// FP32-mixed refinement: once every suspension's relative residual is at most this, the next
+// residual is updated with the FP32 product of the (small) correction instead of recomputed
+#define GDC_RESID_UPDATE 1e-3
 
 // ---- segment / chunk tables ---------------------------------------------------------
 
@@ -418,13 +421,21 @@ gdc_status gmres_solve(gdc_ctx* c, const double* b, double* x, gdc_solve_info* i
         // x += P^-1 V y
         ++c->n_launch, k_gm_backsolve<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(c->S, m, c->gm_H, c->gm_g, c->gm_j, c->gm_y, cols);
         ++c->n_launch, k_combine<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->gm_V, n, c->gm_j, c->gm_y, cols, nullptr, c->gm_w);
-        launch_precond(c, c->gm_w, c->gm_z);
+        launch_precond(c, c->gm_w, c->gm_z);   // the correction e of this cycle
         ++c->n_launch, k_axpy_chunks<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, 1.0, c->gm_z, x);
-        // FP64 residual r = b - A x
-        // accurate residual: FP64 in FP64 mode; double-float pairs + FP64 same-body blocks in mixed mode
-        saddle_op(c, prec == GDC_FP32_MIXED ? GDC_PREC_DF64 : GDC_FP64, x, c->gm_w);
-        inf.matvecs_fp64++;
-        ++c->n_launch, k_sub_chunks<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, b, c->gm_w, c->gm_r);
+        if (prec == GDC_FP32_MIXED && rmax <= GDC_RESID_UPDATE) {
+            // r <- r - A e: the residual is already small, so A e is too, and the FP32 product's
+            // relative error (~3e-7) leaves r accurate to ~3e-7 * rmax, far below gmres_tol
+            saddle_op(c, GDC_FP32_MIXED, c->gm_z, c->gm_w);
+            inf.matvecs_fp32++;
+            ++c->n_launch, k_axpy_chunks<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, -1.0, c->gm_w, c->gm_r);
+        } else {
+            // accurate residual r = b - A x: FP64 in FP64 mode; double-float pairs + FP64
+            // same-body blocks in mixed mode
+            saddle_op(c, prec == GDC_FP32_MIXED ? GDC_PREC_DF64 : GDC_FP64, x, c->gm_w);
+            inf.matvecs_fp64++;
+            ++c->n_launch, k_sub_chunks<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, b, c->gm_w, c->gm_r);
+        }
         if ((st = cuda_check(c, cudaGetLastError(), "GMRES launch")) != GDC_OK) return st;
     }
     inf.iterations = total;
@@ -780,7 +791,8 @@ __global__ void k_gm_reset(LoopCtl* ctl) {
 // after k_gm_start: the residual check of a cycle boundary, and the outer loop's condition
 __global__ void __launch_bounds__(32) k_gm_check(int S, const int* __restrict__ outer, const double* __restrict__ res,
                                                  LoopCtl* ctl, int max_iter, StepReport* rep,
-                                                 cudaGraphConditionalHandle h) {
+                                                 cudaGraphConditionalHandle h, cudaGraphConditionalHandle hacc,
+                                                 int mixed) {
     int any = 0, bad = 0;
     double rmax = 0.0;
     for (int s = threadIdx.x; s < S; s += 32) {
@@ -807,7 +819,11 @@ __global__ void __launch_bounds__(32) k_gm_check(int S, const int* __restrict__ 
         go = 1;
     ctl->gm_j = 0;
     cudaGraphSetConditional(h, go ? 1u : 0u);
+    // the next residual: recomputed accurately, or (mixed precision, small residuals) updated
+    cudaGraphSetConditional(hacc, (!mixed || !(rmax <= GDC_RESID_UPDATE)) ? 1u : 0u);
 }
+
+__global__ void k_count(int* counter) { ++*counter; }
 
 __global__ void k_gm_inner_begin(LoopCtl* ctl, cudaGraphConditionalHandle h) {
     ctl->gm_outer++;
@@ -887,6 +903,54 @@ void cap_while_end(gdc_ctx* c, int report_slot, unsigned long long launches_befo
     c->n_launch = launches_before;
 }
 
+// Appends an IF/ELSE node on h and redirects the library's stream into its first body
+// (run when the condition is non-zero); cap_ifelse_next switches to the second body,
+// cap_ifelse_end returns to the enclosing graph.  Each body's kernels run once per
+// execution of that branch, which the report slot counts.
+void cap_ifelse_begin(gdc_ctx* c, cudaGraphConditionalHandle h) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* edges = nullptr;
+    size_t nd = 0;
+    cap_chk(c, cudaStreamGetCaptureInfo(c->stream, &cs, nullptr, &g, &deps, &edges, &nd));
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeIf;
+    np.conditional.size = 2;
+    cudaGraphNode_t node = nullptr;
+    cap_chk(c, cudaGraphAddNode(&node, g, deps, edges, nd, &np));
+    cap_chk(c, cudaStreamUpdateCaptureDependencies(c->stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    const int d = ++c->cap_depth;
+    c->cap_saved[d] = c->stream;
+    if (d >= 3 || c->cap_err != cudaSuccess) {
+        cap_chk(c, cudaErrorNotSupported);
+        return;
+    }
+    c->cap_bodies[0] = np.conditional.phGraph_out[0];
+    c->cap_bodies[1] = np.conditional.phGraph_out[1];
+    cap_chk(c, cudaStreamBeginCaptureToGraph(c->cap_stream[d], c->cap_bodies[0], nullptr, nullptr, 0,
+                                             cudaStreamCaptureModeRelaxed));
+    c->stream = c->cap_stream[d];
+}
+
+void cap_ifelse_next(gdc_ctx* c, int report_slot, unsigned long long launches_before) {
+    const int d = c->cap_depth;
+    if (d < 3 && c->stream == c->cap_stream[d]) {
+        cudaGraph_t out = nullptr;
+        cap_chk(c, cudaStreamEndCapture(c->stream, &out));
+        cap_chk(c, cudaStreamBeginCaptureToGraph(c->cap_stream[d], c->cap_bodies[1], nullptr, nullptr, 0,
+                                                 cudaStreamCaptureModeRelaxed));
+    }
+    c->graph_loops.push_back({report_slot, c->n_launch - launches_before});
+    c->n_launch = launches_before;
+}
+
+void cap_ifelse_end(gdc_ctx* c, int report_slot, unsigned long long launches_before) {
+    cap_while_end(c, report_slot, launches_before);
+}
+
 // ---- the loops -------------------------------------------------------------------
 
 void lanczos_sqrt_graph(gdc_ctx* c, const double* W, double* out, double scale, int fixed_mode, int run) {
@@ -950,8 +1014,10 @@ void gmres_solve_graph(gdc_ctx* c, const double* b, double* x) {
     ++c->n_launch, k_gm_start<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(c->S, c->gm_h2, c->gm_bnorm, tol, cols,
                                                                           c->gm_res, c->gm_active, c->gm_g, c->gm_scal,
                                                                           m + 1, c->gm_j, c->gm_active + c->S);
-    const cudaGraphConditionalHandle ho = cap_cond(c);
-    ++c->n_launch, k_gm_check<<<1, 32, 0, c->stream>>>(c->S, c->gm_active + c->S, c->gm_res, c->ctl, max_iter, c->rep, ho);
+    const cudaGraphConditionalHandle ho = cap_cond(c), hacc = cap_cond(c);
+    const int mixed = prec == GDC_FP32_MIXED;
+    ++c->n_launch, k_gm_check<<<1, 32, 0, c->stream>>>(c->S, c->gm_active + c->S, c->gm_res, c->ctl, max_iter, c->rep,
+                                                       ho, hacc, mixed);
     cap_while_begin(c, ho);
     const unsigned long long before_o = c->n_launch;
     {
@@ -986,17 +1052,28 @@ void gmres_solve_graph(gdc_ctx* c, const double* b, double* x) {
                                                                                   c->gm_y, cols);
         ++c->n_launch, k_combine<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->gm_V, n, c->gm_j, c->gm_y, cols,
                                                                      nullptr, c->gm_w);
-        launch_precond(c, c->gm_w, c->gm_z);
+        launch_precond(c, c->gm_w, c->gm_z);   // the correction e of this cycle
         ++c->n_launch, k_axpy_chunks<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, 1.0, c->gm_z, x);
-        // accurate residual r = b - A x, then the check of the next cycle boundary
-        saddle_op(c, prec == GDC_FP32_MIXED ? GDC_PREC_DF64 : GDC_FP64, x, c->gm_w);
-        ++c->n_launch, k_sub_chunks<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, b, c->gm_w, c->gm_r);
+        // the residual: recomputed, r = b - A x (accurate product), or updated, r <- r - A e
+        // (FP32 product of the small correction), as k_gm_check decided
+        cap_ifelse_begin(c, hacc);
+        {
+            const unsigned long long before_a = c->n_launch;
+            saddle_op(c, prec == GDC_FP32_MIXED ? GDC_PREC_DF64 : GDC_FP64, x, c->gm_w);
+            ++c->n_launch, k_sub_chunks<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, b, c->gm_w, c->gm_r);
+            ++c->n_launch, k_count<<<1, 1, 0, c->stream>>>(&c->rep->gm_df);
+            cap_ifelse_next(c, REP_GM_DF, before_a);
+            const unsigned long long before_u = c->n_launch;
+            saddle_op(c, GDC_FP32_MIXED, c->gm_z, c->gm_w);
+            ++c->n_launch, k_axpy_chunks<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, -1.0, c->gm_w, c->gm_r);
+            cap_ifelse_end(c, REP_GM_UPD, before_u);
+        }
         seg_mdot(c, sg, c->gm_r, 0, 1, c->gm_r, c->gm_h2, cols);
         ++c->n_launch, k_gm_start<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(
             c->S, c->gm_h2, c->gm_bnorm, tol, cols, c->gm_res, c->gm_active, c->gm_g, c->gm_scal, m + 1, c->gm_j,
             c->gm_active + c->S);
         ++c->n_launch, k_gm_check<<<1, 32, 0, c->stream>>>(c->S, c->gm_active + c->S, c->gm_res, c->ctl, max_iter,
-                                                           c->rep, ho);
+                                                           c->rep, ho, hacc, mixed);
     }
     cap_while_end(c, REP_GM_OUTER, before_o);
     ++c->n_launch, k_gm_finish<<<1, 1, 0, c->stream>>>(c->ctl, c->rep);

@@ -27,7 +27,7 @@ def _same_info(a, b):
         assert a["solve"][k] == b["solve"][k], (k, a["solve"][k], b["solve"][k])
 
 
-@pytest.mark.parametrize("case", ["c1_fp64", "mix_fp32", "batch_fp32", "rod_fp32", "mix_em_fp64"])
+@pytest.mark.parametrize("case", ["c1_fp64", "mix_fp32", "batch_fp32", "rod_fp32", "mix_em_fp64", "mix_fp32_restart4"])
 def test_graph_step_is_bitwise_the_host_driven_step(lib, case):
     if case == "c1_fp64":
         wl, kw = WL.c1(), dict(precision=0, gmres_tol=1e-10, lanczos_tol=1e-8)
@@ -37,8 +37,10 @@ def test_graph_step_is_bitwise_the_host_driven_step(lib, case):
         wl, kw = WL.batch_small(6, seed=3), dict(precision=1, rfd_delta=1e-3)
     elif case == "rod_fp32":
         wl, kw = WL.c2(seed=2, n_rods=60, box=37.0), dict(precision=1, rfd_delta=1e-3)
-    else:
+    elif case == "mix_em_fp64":
         wl, kw = WL.mixed_small(40, seed=1), dict(precision=0, scheme=1)
+    else:   # short restarts: cycles with residual updates (the graph's IF/ELSE node)
+        wl, kw = WL.mixed_small(40, seed=1), dict(precision=1, rfd_delta=1e-3, gmres_restart=4, gmres_max_iter=800)
     g, e = _pair(lib, wl, **kw)
     ig = g.step(3)
     ie = e.step(3)
@@ -112,7 +114,8 @@ def test_graph_kernel_count(lib):
 
     kT = 0 leaves only the GMRES loops: per step 3 step-level kernels (report reset, ok
     flag, report), and for the solve one reset, one finish, a check per cycle boundary
-    (cycles + 1), a cycle start per cycle and a loop-control kernel per inner iteration.
+    (cycles + 1), a cycle start per cycle, a loop-control kernel per inner iteration and a
+    counter per accurate residual product.
     """
     wl = WL.mixed_small(40, seed=1)
     g, e = _pair(lib, wl, precision=1, kT=0.0)
@@ -125,5 +128,5 @@ def test_graph_kernel_count(lib):
         counts.append((ctx.profile_read()["launches"], inf))
     (ng, ig), (ne, ie) = counts
     _same_info(ig, ie)
-    cyc, it = ig["solve"]["cycles"], ig["solve"]["iterations"]
-    assert ng - ne == 3 + 1 + 1 + (cyc + 1) + cyc + it, (ng, ne, cyc, it)
+    cyc, it, acc = ig["solve"]["cycles"], ig["solve"]["iterations"], ig["solve"]["matvecs_fp64"]
+    assert ng - ne == 3 + 1 + 1 + (cyc + 1) + cyc + it + acc, (ng, ne, cyc, it, acc)

@@ -422,3 +422,22 @@ def test_fp32_step_parity_each_pair_kernel(lib, wl_mix, kernel):
     for s, o, e, ora in out:
         assert np.abs(Y2[o:e] - ora["Y1"]).max() / np.abs(ora["Y1"]).max() < 1e-5
         assert rot_err(q2[o:e], ora["q1"]) < 1e-5
+
+
+def test_fp32_refinement_with_residual_updates(lib, wl_mix):
+    """FP32-mixed GMRES with short restarts: cycles that start from a residual below 1e-3 update
+    it with the FP32 product of their correction instead of an accurate product; the final
+    residual, checked with the oracle's dense FP64 operator, still meets gmres_tol."""
+    wl = wl_mix
+    tol = 1e-6
+    ctx = ctx_for(lib, wl, precision=1, gmres_tol=tol, gmres_max_iter=800, gmres_restart=4)
+    rng = np.random.default_rng(21)
+    vb = rng.standard_normal(3 * wl.n_blobs)
+    FT = np.zeros(6 * wl.n_bodies)
+    V, lam, info = ctx.mobility_solve(FT, vb, want_lambda=True)
+    assert info["converged"] and info["residual"] <= tol
+    assert info["cycles"] >= 3 and info["matvecs_fp64"] < info["cycles"] + 1, info   # some updated residuals
+    (r, M, K, B, lay), = _oracle_saddle(wl)
+    y1, y2 = rigid.saddle_apply(M, K, _host(lam), _host(V))
+    res = np.linalg.norm(np.concatenate([y1 + vb, y2])) / np.linalg.norm(vb)
+    assert res <= 1.2 * tol, res
