@@ -31,12 +31,13 @@ def main(argv=None) -> int:
     ap.add_argument("--bodies", type=int, default=0, help="use only the first N bodies (0 = all)")
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--pair-kernel", type=int, default=0, help="FP32 pair kernel: 0 autotuned, 1 ordered, 2 symmetric")
+    ap.add_argument("--graph", type=int, default=1, help="step32: 1 replays the step as a CUDA graph, 0 host-driven")
     args = ap.parse_args(argv)
     wl = WL.BY_NAME[args.workload]()
     if args.bodies:
         wl = wl.first_bodies(args.bodies)
     ctx = g.context_from_workload(wl, precision=g.FP32_MIXED, rfd_delta=1e-3, lanczos_max_iter=128,
-                                  pair_kernel=args.pair_kernel)
+                                  pair_kernel=args.pair_kernel, graph=args.graph)
     rng = np.random.default_rng(0)
     lam = torch.as_tensor(rng.standard_normal(3 * wl.n_blobs), device=ctx.device)
     x = torch.as_tensor(rng.standard_normal(int(ctx.saddle_off[-1])), device=ctx.device)
