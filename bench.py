@@ -96,6 +96,19 @@ def captured_traffic(kind: int = 1):
     return None
 
 
+def replica_throughput(t_local: float, steps: int, world: int, dist=None, device="cpu"):
+    """Whole-job steps/s of `world` independent replicas (one suspension per rank, no data-path
+    collective): every rank ran `steps` steps in t_local seconds and the job takes as long as
+    the slowest rank.  Returns (steps/s of the job, the slowest rank's time)."""
+    t_max = t_local
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([t_local], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    return world * steps / t_max, t_max
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -326,13 +339,7 @@ def main(argv=None) -> int:
     times_ev, infos_ev = timed(args.steps)
     prof = ctx.profile_read()
     ctx.profile(False)
-    t_local = sum(times)
-    t_max = t_local
-    if dist:
-        t = torch.tensor([t_local], dtype=torch.float64, device=ctx.device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * args.steps / t_max
+    value, t_max = replica_throughput(sum(times), args.steps, world, dist, ctx.device)
     pair_evals = sum(i["pair_evals"] for i in infos)
     peaks, peak_src = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
