@@ -28,7 +28,7 @@ constexpr int SYM_TILE = GDC_SYM_TILE;
 constexpr int SYM_SMEM = 3 * SYM_TILE * 16 + 3 * 4 * SYM_TILE * 4 + 16;   // tile, 4 warps' sums, mbarrier
 
 #ifndef GDC_SYM_MINB
-#define GDC_SYM_MINB 4
+#define GDC_SYM_MINB 2   // the fully unrolled sweep wants registers (184) more than warps
 #endif
 
 __device__ __forceinline__ float2 shfl2(float2 v, int src) {
@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(128, GDC_SYM_MINB) k_rpy32_sym(const SymItem* 
 #pragma unroll
                 for (int p = 0; p < 2; ++p) qx[p] = qy[p] = qz[p] = make_float2(0.f, 0.f);
                 float2 jx = make_float2(0.f, 0.f), jy = jx, jz = jx;   // sums of the source this lane holds
-#pragma unroll 2
+#pragma unroll
                 for (int st = 0; st < 32; ++st) {
                     const int j = jc + ((lane + st) & 31);
                     const float4 s0 = sh[3 * j], s1 = sh[3 * j + 1], s2 = sh[3 * j + 2];
