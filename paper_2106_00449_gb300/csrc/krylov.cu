@@ -596,7 +596,7 @@ __global__ void __launch_bounds__(32) k_lz_tridiag(int S, int j, const int* __re
     const bool fixed_mode = fixed != nullptr && fixed[s] > 0;
     // checks start a little before this suspension's previous count (hint[s]; 0 = none)
     const int hs = fixed_mode ? 0 : hint[s];
-    const int kstart = hs > 0 ? max(2, hs - max(4, hs / 8)) : 2;
+    const int kstart = hs > 0 ? max(2, hs - max(4, hs / 16)) : 2;
     const bool compute = fixed_mode ? (k >= fixed[s] || k >= kmax || beta == 0.0)
                                     : (k >= kstart || k >= kmax || beta == 0.0);
     if (!compute) return;
