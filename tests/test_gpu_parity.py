@@ -441,3 +441,26 @@ def test_fp32_refinement_with_residual_updates(lib, wl_mix):
     y1, y2 = rigid.saddle_apply(M, K, _host(lam), _host(V))
     res = np.linalg.norm(np.concatenate([y1 + vb, y2])) / np.linalg.norm(vb)
     assert res <= 1.2 * tol, res
+
+
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_rpy32_ragged_suspension_sizes(lib, kernel):
+    """Both FP32 pair kernels on a batch of free-blob suspensions of 1, 2, 31, 511, 512, 513
+    and 1025 blobs: single-blob and sub-warp suspensions, sizes on both sides of the 256- and
+    512-blob tiles, in one launch; random clouds, so blobs of different bodies overlap."""
+    sizes = [1, 2, 31, 511, 512, 513, 1025]
+    rng = np.random.default_rng(23)
+    Y = np.concatenate([rng.uniform(0.0, 1.8 * n ** (1.0 / 3.0) + 1.0, size=(n, 3)) for n in sizes])
+    nb = sum(sizes)
+    wl = WL.Workload("ragged_free_blobs", [np.zeros((1, 3))], np.zeros(nb, dtype=np.int32),
+                     np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64), Y,
+                     np.tile([1.0, 0.0, 0.0, 0.0], (nb, 1)), dict(WL.c1().params), np.ones(len(sizes)))
+    ctx = ctx_for(lib, wl, autotune=0, pair_kernel=kernel)
+    lam = rng.standard_normal(3 * nb)
+    u = _host(ctx.rpy_apply(lam, 1))
+    off = 0
+    for n in sizes:
+        ref = rpy.rpy_matrix(Y[off:off + n], 1.0, 1.0) @ lam[3 * off:3 * (off + n)]
+        got = u[3 * off:3 * (off + n)]
+        assert rel(got, ref) < 2e-6, (n, rel(got, ref))
+        off += n
