@@ -172,6 +172,7 @@ static size_t carve(gdc_ctx* c, void* base) {
     c->tmpl_L = w.take<double>(T);
     c->tmpl_Minv = w.take<double>(c->h_minv_off[T]);
     c->tmpl_M = w.take<double>(c->h_minv_off[T]);
+    c->tmpl_M32 = w.take<float>(c->h_minv_off[T]);
     c->tmpl_G = w.take<double>(18 * nt);
     c->tmpl_N = w.take<double>(36 * T);
     c->tmpl_KtKp = w.take<double>(36 * T);
@@ -228,8 +229,6 @@ static size_t carve(gdc_ctx* c, void* base) {
     c->lz_alpha = w.take<double>(S * k);
     c->lz_beta = w.take<double>(S * k);
     c->lz_c = w.take<double>(S * k);
-    c->lz_rot_cap = (int)(3 * k * k + 64);
-    c->lz_rot = (void*)w.take<double>(3LL * S * c->lz_rot_cap);   // 24-byte records
     c->lz_lastk = w.take<int>(2 * S);
     c->lz_hint = w.take<int>(S);
     c->lz_h = w.take<double>(S * cols);

@@ -9,6 +9,8 @@
 // N_t = (K_t^T M_t^-1 K_t)^+ and (K_t^T K_t)^+ are computed once per template in the
 // body frame and applied to rotated vectors.  "^+" is the pseudo-inverse: a collinear
 // body (rod) has no axial spin (its K has that null vector), which is then set to 0.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace gdc {
@@ -267,6 +269,67 @@ __global__ void __launch_bounds__(128) k_intra_body(const long long* __restrict_
     }
 }
 
+// The same block for the FP32 products, whose other terms carry FP32 rounding: M_t in FP32
+// (tmpl_M32), rho rounded to FP32, each row sum split into four interleaved FP32 partial
+// sums that are added in FP64; the rotations stay in FP64.  Shared memory: av (n3 doubles),
+// then rho (n3 floats).
+__global__ void __launch_bounds__(128) k_intra_body32(const long long* __restrict__ body_blob_off,
+                                                      const int* __restrict__ body_tmpl, const int* __restrict__ tmpl_n,
+                                                      const long long* __restrict__ minv_off, const float* __restrict__ Mt,
+                                                      const int* __restrict__ blob_gm, const double* __restrict__ Rb,
+                                                      const double* __restrict__ x, double* __restrict__ y, int gm) {
+    extern __shared__ double sh[];
+    const int p = blockIdx.x;
+    const int t = body_tmpl[p];
+    const int n3 = 3 * tmpl_n[t];
+    double* av = sh;
+    float* rho = reinterpret_cast<float*>(sh + n3);
+    const double* R = Rb + 9 * p;
+    const long long i0 = body_blob_off[p];
+    for (int b = threadIdx.x; b < n3 / 3; b += blockDim.x) {
+        const long long o = gm ? (long long)blob_gm[i0 + b] : 3 * (i0 + b);
+        double v[3] = {x[o], x[o + 1], x[o + 2]}, w[3];
+        rotT(R, v, w);
+        rho[3 * b] = (float)w[0];
+        rho[3 * b + 1] = (float)w[1];
+        rho[3 * b + 2] = (float)w[2];
+    }
+    __syncthreads();
+    const float* M = Mt + minv_off[t];
+    for (int row = threadIdx.x; row < n3; row += blockDim.x) {
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        int q = 0;
+        for (; q + 4 <= n3; q += 4) {   // M_t is symmetric: column reads, coalesced over rows
+            a0 = fmaf(M[(long long)q * n3 + row], rho[q], a0);
+            a1 = fmaf(M[(long long)(q + 1) * n3 + row], rho[q + 1], a1);
+            a2 = fmaf(M[(long long)(q + 2) * n3 + row], rho[q + 2], a2);
+            a3 = fmaf(M[(long long)(q + 3) * n3 + row], rho[q + 3], a3);
+        }
+        for (; q < n3; ++q) a0 = fmaf(M[(long long)q * n3 + row], rho[q], a0);
+        av[row] = ((double)a0 + (double)a1) + ((double)a2 + (double)a3);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < n3 / 3; b += blockDim.x) {
+        double w[3];
+        rot(R, av + 3 * b, w);
+        const long long o = gm ? (long long)blob_gm[i0 + b] : 3 * (i0 + b);
+        y[o] += w[0];
+        y[o + 1] += w[1];
+        y[o + 2] += w[2];
+    }
+}
+
+__global__ void k_round_f32(long long n, const double* __restrict__ a, float* __restrict__ b) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+
+void launch_intra_body32(gdc_ctx* c, const double* x, double* y, int gm) {
+    const size_t smem = (size_t)(3 * c->max_body_blobs) * (sizeof(double) + sizeof(float));
+    ++c->n_launch, k_intra_body32<<<c->NB, 128, smem, c->stream>>>(c->body_blob_off, c->body_tmpl, c->tmpl_n, c->minv_off,
+                                                                   c->tmpl_M32, c->blob_gm, c->Rb, x, y, gm);
+}
+
 void launch_intra_body(gdc_ctx* c, const double* x, double* y, int gm) {
     const size_t smem = (size_t)(2 * 3 * c->max_body_blobs) * sizeof(double);
     ++c->n_launch, k_intra_body<<<c->NB, 128, smem, c->stream>>>(c->body_blob_off, c->body_tmpl, c->tmpl_n, c->minv_off,
@@ -468,6 +531,9 @@ void launch_template_setup(gdc_ctx* c) {
     ++c->n_launch, k_template_setup<<<c->T, 256, 0, c->stream>>>(c->tmpl_n, c->tmpl_off, c->minv_off, c->tmpl_xyz, c->p.a, c->p.eta,
                                                   c->tmpl_Minv, c->tmpl_G, c->tmpl_N, c->tmpl_KtKp, c->tmpl_work,
                                                   c->tmpl_M, c->dev_status);
+    const long long nm = c->h_minv_off[c->T];
+    ++c->n_launch, k_round_f32<<<(int)std::min<long long>(ceil_div(nm, 256), 1024), 256, 0, c->stream>>>(nm, c->tmpl_M,
+                                                                                                      c->tmpl_M32);
 }
 
 }  // namespace gdc

@@ -124,6 +124,7 @@ struct gdc_ctx {
     int *blob_gm = 0, *body_gm = 0;
     double *tmpl_xyz = 0, *tmpl_L = 0;
     double *tmpl_Minv = 0, *tmpl_G = 0, *tmpl_N = 0, *tmpl_KtKp = 0, *tmpl_work = 0, *tmpl_M = 0;
+    float* tmpl_M32 = 0;          // tmpl_M rounded to FP32 (intra-body block of the FP32 products)
     double *body_L = 0;
 
     // state (caller arrays)
@@ -151,8 +152,6 @@ struct gdc_ctx {
     double *lz_V = 0, *lz_w = 0, *lz_alpha = 0, *lz_beta = 0, *lz_c = 0;
     double *lz_h = 0, *lz_Wnorm = 0, *lz_err = 0, *lz_scal = 0;
     int *lz_active = 0, *lz_k = 0, *lz_fix = 0, *lz_lastk = 0;
-    void* lz_rot = 0;             // per suspension: Givens rotations of the tridiagonal QR (24 B each)
-    int lz_rot_cap = 0;           // rotations stored per suspension: 3 kmax^2 + 64
     int* lz_hint = 0;             // per suspension: index the previous unconstrained run stopped at (0 = none)
 
     // reductions
@@ -325,6 +324,7 @@ void launch_body_KT(gdc_ctx* c, const double* x, int x_gm, double* y, int y_gm, 
 void launch_lsq(gdc_ctx* c, const double* vbrev, double* calV);
 void launch_precond(gdc_ctx* c, const double* r, double* z);
 void launch_intra_body(gdc_ctx* c, const double* x, double* y, int gm);
+void launch_intra_body32(gdc_ctx* c, const double* x, double* y, int gm);
 void launch_template_setup(gdc_ctx* c);
 
 // krylov.cu

@@ -459,35 +459,72 @@ __global__ void k_lz_start(int S, const double* __restrict__ wn2, int cols, doub
 }
 
 // Lanczos bookkeeping and, where needed, c = ||W|| T_k^(1/2) e_1 for one suspension
-// (one block per suspension; the eigen-work is sequential and runs on thread 0).
+// (one warp per suspension).
 //
 // T_k = Q diag(theta) Q^T is diagonalised by implicit symmetric QR steps with
-// Wilkinson shifts (Golub & Van Loan, Sec. 8.3).  Q is never formed: the rotations
-// R_1 .. R_N are applied to u = e_1 as they are made (u = Q^T e_1), stored, and
-// replayed transposed in reverse order on g = sqrt(theta) * u, which gives Q g.
-// That is O(k^2) work instead of the O(k^3) of accumulating Q.
+// Wilkinson shifts (Golub & Van Loan, Sec. 8.3).  Every lane runs the same sweep on its
+// own copy of the diagonal and off-diagonal (identical arithmetic, so identical values and
+// warp-uniform control flow); the bulge chase keeps its carried entries in registers, so
+// the serial chain per rotation is one Givens rotation and a few fused multiply-adds.
+// Q is accumulated in shared memory, each lane updating the rows it owns (rows lane,
+// lane + 32, ...), off the serial chain.  Then c = wn Q (sqrt(theta) o Q^T e_1), where
+// Q^T e_1 is row 0 of Q.
 //
 // Convergence: ||c_k - c_{k-1}|| / ||c_k|| < tol, evaluated from a start index set by the
 // suspension's previous count (so early iterations skip the eigen-work);
 // in fixed mode c is formed once, at k = fixed[s].
-struct LzRot {
-    double c, s;
-    int q, pad;
-};
+static_assert(GDC_MAX_LANCZOS <= 128, "a lane owns at most 4 rows of Q");
 
-// out = wn * T_k^(1/2) e_1 for the k x k tridiagonal (al, be), computed in precision T.
-// Returns false when the QR iteration does not converge or the rotation store overflows.
+// Row stride of Q in shared memory: odd, so that the lanes' rows fall in distinct banks.
+__host__ __device__ inline int lz_ldq(int kmax) { return kmax | 1; }
+
+// Dynamic shared memory of k_lz_tridiag: four c vectors (doubles), then Q.
+static size_t lz_tridiag_smem(int kmax, bool eig32) {
+    return (size_t)4 * kmax * sizeof(double) + (size_t)kmax * lz_ldq(kmax) * (eig32 ? sizeof(float) : sizeof(double));
+}
+
+// Givens rotation (c, s) with c x + s z = r, -s x + c z = 0.  The FP32 eigen-step takes
+// 1/r from the hardware reciprocal square root (one rounding of about 1 ulp, the size of
+// the correctly rounded quotient's); FP64 divides by the correctly rounded square root.
+__device__ inline void lz_givens(float x, float z, float& c, float& s, float& r) {
+    const float r2 = fmaf(x, x, z * z);
+    if (r2 > 0.f) {
+        const float ri = rsqrtf(r2);
+        c = x * ri;
+        s = z * ri;
+        r = r2 * ri;
+    } else {
+        c = 1.f;
+        s = 0.f;
+        r = 0.f;
+    }
+}
+__device__ inline void lz_givens(double x, double z, double& c, double& s, double& r) {
+    r = sqrt(x * x + z * z);
+    if (r > 0.0) {
+        const double ri = 1.0 / r;
+        c = x * ri;
+        s = z * ri;
+    } else {
+        c = 1.0;
+        s = 0.0;
+    }
+}
+
+// out[0..k) = wn * T_k^(1/2) e_1 for the k x k tridiagonal (al, be), computed in precision T
+// by the whole warp; Q is k x k in shared memory with row stride ldq.  Returns false (on
+// every lane) when the QR iteration does not converge.
 template <typename T>
-__device__ bool lz_sqrt_e1_t(const double* al, const double* be, int k, double wn, LzRot* rot, int rot_cap,
-                             double* out_d) {
+__device__ bool lz_sqrt_e1_t(const double* al, const double* be, int k, double wn, T* Q, int ldq, double* out) {
+    const int lane = threadIdx.x;
     const T eps = sizeof(T) == 4 ? T(1.2e-7) : T(1e-16);   // deflation threshold (relative)
-    T d[GDC_MAX_LANCZOS], e[GDC_MAX_LANCZOS], out[GDC_MAX_LANCZOS];
+    T d[GDC_MAX_LANCZOS], e[GDC_MAX_LANCZOS];
     for (int i = 0; i < k; ++i) {
         d[i] = (T)al[i];
         e[i] = i + 1 < k ? (T)be[i] : T(0);
-        out[i] = i == 0 ? T(1) : T(0);   // u = Q^T e_1, built rotation by rotation
     }
-    int nrot = 0;
+    for (int r = lane; r < k; r += 32)
+        for (int col = 0; col < k; ++col) Q[r * ldq + col] = r == col ? T(1) : T(0);
     int hi = k - 1;
     for (int sweep = 0; hi > 0; ++sweep) {
         if (sweep > 40 * k + 40) return false;
@@ -502,56 +539,71 @@ __device__ bool lz_sqrt_e1_t(const double* al, const double* be, int k, double w
         const T bb = e[hi - 1];
         const T sg = del >= T(0) ? T(1) : T(-1);
         const T mu = d[hi] - bb * bb / (del + sg * sqrt(del * del + bb * bb));
-        T xx = d[lo] - mu, zz = e[lo];
+        // carried: dq = d[q] and eq = e[q] as the previous rotation left them
+        T dq = d[lo], eq = e[lo];
+        T x = dq - mu, z = eq;
+        T qc[4];   // column q of the lane's rows of Q
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int r = lane + 32 * m;
+            qc[m] = r < k ? Q[r * ldq + lo] : T(0);
+        }
         for (int q = lo; q < hi; ++q) {
-            const T rr = sqrt(xx * xx + zz * zz);
-            T cq = T(1), sq = T(0);
-            if (rr > T(0)) {
-                const T ri = T(1) / rr;
-                cq = xx * ri;
-                sq = zz * ri;
-            }
+            const T dq1 = d[q + 1];
+            const T eq1 = q + 1 < hi ? e[q + 1] : T(0);
+            T cq, sq, rr;
+            lz_givens(x, z, cq, sq, rr);
             if (q > lo) e[q - 1] = rr;
-            const T a0 = d[q], b0 = d[q + 1], f0 = e[q];
             const T cc = cq * cq, ss = sq * sq, cs = cq * sq;
-            d[q] = cc * a0 + T(2) * cs * f0 + ss * b0;
-            d[q + 1] = ss * a0 - T(2) * cs * f0 + cc * b0;
-            e[q] = cs * (b0 - a0) + (cc - ss) * f0;
-            if (q + 1 < hi) {
-                const T bulge = sq * e[q + 1];
-                e[q + 1] = cq * e[q + 1];
-                xx = e[q];
-                zz = bulge;
+            d[q] = cc * dq + T(2) * cs * eq + ss * dq1;
+            const T nd1 = ss * dq - T(2) * cs * eq + cc * dq1;
+            const T ne = cs * (dq1 - dq) + (cc - ss) * eq;
+            e[q] = ne;
+            dq = nd1;
+            x = ne;
+            z = sq * eq1;
+            eq = cq * eq1;
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const int r = lane + 32 * m;
+                if (r < k) {
+                    const T qn = Q[r * ldq + q + 1];
+                    Q[r * ldq + q] = cq * qc[m] + sq * qn;
+                    qc[m] = -sq * qc[m] + cq * qn;
+                }
             }
-            const T u0 = out[q], u1 = out[q + 1];
-            out[q] = cq * u0 + sq * u1;
-            out[q + 1] = -sq * u0 + cq * u1;
-            if (nrot >= rot_cap) return false;
-            rot[nrot++] = LzRot{(double)cq, (double)sq, q, 0};
+        }
+        d[hi] = dq;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int r = lane + 32 * m;
+            if (r < k) Q[r * ldq + hi] = qc[m];
         }
     }
-    // g = sqrt(theta) * u, then Q g by the transposed rotations in reverse order
-    for (int i = 0; i < k; ++i) out[i] *= sqrt(d[i] > T(0) ? d[i] : T(0));
-    for (int t = nrot - 1; t >= 0; --t) {
-        const LzRot R = rot[t];
-        const T c = (T)R.c, s = (T)R.s;
-        const T g0 = out[R.q], g1 = out[R.q + 1];
-        out[R.q] = c * g0 - s * g1;
-        out[R.q + 1] = s * g0 + c * g1;
+    __syncwarp();   // row 0 of Q (lane 0's) is read by every lane
+    for (int i = 0; i < k; ++i) e[i] = sqrt(d[i] > T(0) ? d[i] : T(0)) * Q[i];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const int r = lane + 32 * m;
+        if (r < k) {
+            T acc = T(0);
+            for (int i = 0; i < k; ++i) acc += Q[r * ldq + i] * e[i];
+            out[r] = wn * (double)acc;
+        }
     }
-    for (int i = 0; i < k; ++i) out_d[i] = wn * (double)out[i];
+    __syncwarp();   // out complete before any lane reads it, Q free for the next call
     return true;
 }
 
 // FP32 is enough for the small eigenproblem when the Lanczos tolerance is loose (its
 // error, ~1e-6 relative, is far below tol); tight tolerances use FP64.
-__device__ inline bool lz_sqrt_e1(const double* al, const double* be, int k, double wn, LzRot* rot, int rot_cap,
-                                  double* out, bool fp32) {
-    return fp32 ? lz_sqrt_e1_t<float>(al, be, k, wn, rot, rot_cap, out)
-                : lz_sqrt_e1_t<double>(al, be, k, wn, rot, rot_cap, out);
+__device__ inline bool lz_sqrt_e1(const double* al, const double* be, int k, double wn, void* Q, int ldq, double* out,
+                                  bool fp32) {
+    return fp32 ? lz_sqrt_e1_t<float>(al, be, k, wn, (float*)Q, ldq, out)
+                : lz_sqrt_e1_t<double>(al, be, k, wn, (double*)Q, ldq, out);
 }
 
-// ||c_k - [c_{k-1}; 0]|| / ||c_k||
+// ||c_k - [c_{k-1}; 0]|| / ||c_k||, summed in the same order on every lane
 __device__ inline double lz_change(const double* ck, const double* cprev, int k) {
     double num = 0.0, den = 0.0;
     for (int r = 0; r < k; ++r) {
@@ -565,7 +617,9 @@ __device__ inline double lz_change(const double* ck, const double* cprev, int k)
 // The stopping index is the smallest k >= 2 with ||c_k - c_{k-1}|| / ||c_k|| < tol
 // whatever the check schedule: when the first check of a run (index firstk + 1) already
 // passes, earlier indices are examined backwards.  lastk[s] is the last index whose c was
-// formed (-1 at the start of a run), lastk[S + s] the first one.
+// formed (-1 at the start of a run), lastk[S + s] the first one.  Launched with 32 threads
+// and lz_tridiag_smem(kmax, tol >= 1e-5) bytes of dynamic shared memory; every lane
+// follows the same control flow and lane 0 alone writes the per-suspension scalars.
 __global__ void __launch_bounds__(32) k_lz_tridiag(int S, int j, const int* __restrict__ jdev, const double* __restrict__ h, int cols,
                                                    const double* __restrict__ wn2, double* __restrict__ alpha,
                                                    double* __restrict__ betav, const double* __restrict__ Wnorm,
@@ -573,12 +627,13 @@ __global__ void __launch_bounds__(32) k_lz_tridiag(int S, int j, const int* __re
                                                    int* __restrict__ active, int* __restrict__ kcount,
                                                    int* __restrict__ lastk, double* __restrict__ scal, double tol,
                                                    const int* __restrict__ fixed, int* __restrict__ hint, int kmax,
-                                                   const long long* __restrict__ susp_blob_off,
-                                                   LzRot* __restrict__ rot_all, int rot_cap, int* __restrict__ status) {
+                                                   const long long* __restrict__ susp_blob_off, int* __restrict__ status) {
+    extern __shared__ __align__(16) unsigned char lz_smem[];
     const int s = blockIdx.x;
-    if (threadIdx.x != 0) return;
+    const int lane = threadIdx.x;
+    const bool lead = lane == 0;
     if (!active[s]) {
-        scal[s] = 0.0;
+        if (lead) scal[s] = 0.0;
         return;
     }
     if (jdev) j = *jdev;
@@ -586,13 +641,18 @@ __global__ void __launch_bounds__(32) k_lz_tridiag(int S, int j, const int* __re
     double beta = sqrt(fmax(wn2[(long long)s * cols], 0.0));
     double* al = alpha + (long long)s * kmax;
     double* be = betav + (long long)s * kmax;
-    al[j] = h[(long long)s * cols + j];
+    const double aj = h[(long long)s * cols + j];
+    const double a0 = j == 0 ? aj : al[0];
     // Krylov space exhausted (k reached the dimension) or numerically invariant: exact stop
     const long long dim = 3 * (susp_blob_off[s + 1] - susp_blob_off[s]);
-    if (k >= dim || beta <= 1e-14 * fmax(fabs(al[0]), fabs(al[j]))) beta = 0.0;
-    be[j] = beta;
-    scal[s] = beta > 0.0 ? 1.0 / beta : 0.0;
-    kcount[s] = k;
+    if (k >= dim || beta <= 1e-14 * fmax(fabs(a0), fabs(aj))) beta = 0.0;
+    if (lead) {
+        al[j] = aj;
+        be[j] = beta;
+        scal[s] = beta > 0.0 ? 1.0 / beta : 0.0;
+        kcount[s] = k;
+    }
+    __syncwarp();   // al[j], be[j] visible to every lane
     const bool fixed_mode = fixed != nullptr && fixed[s] > 0;
     // checks start a little before this suspension's previous count (hint[s]; 0 = none)
     const int hs = fixed_mode ? 0 : hint[s];
@@ -600,21 +660,29 @@ __global__ void __launch_bounds__(32) k_lz_tridiag(int S, int j, const int* __re
     const bool compute = fixed_mode ? (k >= fixed[s] || k >= kmax || beta == 0.0)
                                     : (k >= kstart || k >= kmax || beta == 0.0);
     if (!compute) return;
-    LzRot* rot = rot_all + (long long)s * rot_cap;
     double* cs_ = cvec + (long long)s * kmax;   // c of the last formed index
     const double wn = Wnorm[s];
-    double cur[GDC_MAX_LANCZOS];
+    double* cur = reinterpret_cast<double*>(lz_smem);
+    double* ck = cur + kmax;
+    double* cm = ck + kmax;
+    double* best = cm + kmax;
+    void* Q = best + kmax;
+    const int ldq = lz_ldq(kmax);
     const bool eig32 = tol >= 1e-5;
-    if (!lz_sqrt_e1(al, be, k, wn, rot, rot_cap, cur, eig32)) {
-        atomicExch(status, 2);
-        active[s] = 0;
-        err[s] = 1.0;
+    if (!lz_sqrt_e1(al, be, k, wn, Q, ldq, cur, eig32)) {
+        if (lead) {
+            atomicExch(status, 2);
+            active[s] = 0;
+            err[s] = 1.0;
+        }
         return;
     }
     if (fixed_mode) {
-        for (int r = 0; r < k; ++r) cs_[r] = cur[r];
-        err[s] = 0.0;
-        active[s] = 0;
+        for (int r = lane; r < k; r += 32) cs_[r] = cur[r];
+        if (lead) {
+            err[s] = 0.0;
+            active[s] = 0;
+        }
         return;
     }
     const int prevk = lastk[s], firstk = lastk[S + s];
@@ -626,36 +694,46 @@ __global__ void __launch_bounds__(32) k_lz_tridiag(int S, int j, const int* __re
         if (ee < tol) {
             stop = true;
             if (firstk == k - 1) {   // no check was possible at k - 1: look further back
-                double ck[GDC_MAX_LANCZOS], cm[GDC_MAX_LANCZOS], best[GDC_MAX_LANCZOS];
-                for (int r = 0; r < k; ++r) best[r] = cur[r];
-                for (int r = 0; r < k - 1; ++r) ck[r] = cs_[r];
+                for (int r = lane; r < k; r += 32) {
+                    best[r] = cur[r];
+                    if (r < k - 1) ck[r] = cs_[r];
+                }
+                __syncwarp();
                 double best_err = ee;
                 for (int kk = k - 1; kk >= 2; --kk) {
-                    if (!lz_sqrt_e1(al, be, kk - 1, wn, rot, rot_cap, cm, eig32)) break;
+                    if (!lz_sqrt_e1(al, be, kk - 1, wn, Q, ldq, cm, eig32)) break;
                     const double e2 = lz_change(ck, cm, kk);
                     if (!(e2 < tol)) break;
                     kstar = kk;
                     best_err = e2;
-                    for (int r = 0; r < kk; ++r) best[r] = ck[r];
-                    for (int r = 0; r < kk - 1; ++r) ck[r] = cm[r];
+                    __syncwarp();   // every lane has read ck and cm
+                    for (int r = lane; r < kk; r += 32) {
+                        best[r] = ck[r];
+                        if (r < kk - 1) ck[r] = cm[r];
+                    }
+                    __syncwarp();
                 }
-                for (int r = 0; r < kstar; ++r) cur[r] = best[r];
+                __syncwarp();
+                for (int r = lane; r < kstar; r += 32) cur[r] = best[r];
+                __syncwarp();
                 ee = best_err;
             }
         }
     }
-    if (firstk < 0) lastk[S + s] = k;
-    lastk[s] = k;
-    for (int r = 0; r < kstar; ++r) cs_[r] = cur[r];
-    kcount[s] = kstar;
-    err[s] = ee;
+    __syncwarp();   // every lane has read lastk and cs_ before they are written
+    for (int r = lane; r < kstar; r += 32) cs_[r] = cur[r];
     if (k >= kmax) stop = true;
-    if (stop) {
-        active[s] = 0;
-        hint[s] = kstar;
+    if (lead) {
+        if (firstk < 0) lastk[S + s] = k;
+        lastk[s] = k;
+        kcount[s] = kstar;
+        err[s] = ee;
+        if (stop) {
+            active[s] = 0;
+            hint[s] = kstar;
+        }
     }
 }
-
 __global__ void k_lz_reset(int S, int* __restrict__ lastk) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s < S) {
@@ -664,7 +742,10 @@ __global__ void k_lz_reset(int S, int* __restrict__ lastk) {
     }
 }
 
-void krylov_init_attributes() {}
+void krylov_init_attributes() {
+    cudaFuncSetAttribute(k_lz_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)lz_tridiag_smem(GDC_MAX_LANCZOS, false));
+}
 
 gdc_status lanczos_sqrt(gdc_ctx* c, const double* W, double* out, double scale, int fixed_mode,
                         int* iters_out, double* err_out) {
@@ -693,10 +774,10 @@ gdc_status lanczos_sqrt(gdc_ctx* c, const double* W, double* out, double scale, 
         ++c->n_launch, k_mupdate<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_V, n, j + 1, nullptr, c->gm_h2, cols, c->lz_w);
         ++c->n_launch, k_add_cols<<<c->S, 128, 0, c->stream>>>(j + 1, nullptr, c->lz_h, c->gm_h2, cols);
         seg_mdot(c, sg, c->lz_w, 0, 1, c->lz_w, c->gm_h2, cols);
-        ++c->n_launch, k_lz_tridiag<<<c->S, 32, 0, c->stream>>>(
+        ++c->n_launch, k_lz_tridiag<<<c->S, 32, lz_tridiag_smem(kmax, c->p.lanczos_tol >= 1e-5), c->stream>>>(
             c->S, j, nullptr, c->lz_h, cols, c->gm_h2, c->lz_alpha, c->lz_beta, c->lz_Wnorm, c->lz_c, c->lz_err, c->lz_active,
             c->lz_k, c->lz_lastk, c->lz_scal, c->p.lanczos_tol, fixed_mode ? c->lz_fix : nullptr, c->lz_hint, kmax, c->susp_blob_off,
-            (LzRot*)c->lz_rot, c->lz_rot_cap, c->dev_status);
+            c->dev_status);
         ++c->n_launch, k_seg_scale<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_w, c->lz_scal,
                                                                        c->lz_V + (long long)(j + 1) * n);
         if ((st = sync_read(c, c->lz_active, act.data(), sizeof(int) * c->S)) != GDC_OK) return st;
@@ -979,10 +1060,10 @@ void lanczos_sqrt_graph(gdc_ctx* c, const double* W, double* out, double scale, 
     ++c->n_launch, k_mupdate<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_V, n, 1, jd, c->gm_h2, cols, c->lz_w);
     ++c->n_launch, k_add_cols<<<c->S, 128, 0, c->stream>>>(1, jd, c->lz_h, c->gm_h2, cols);
     seg_mdot(c, sg, c->lz_w, 0, 1, c->lz_w, c->gm_h2, cols);
-    ++c->n_launch, k_lz_tridiag<<<c->S, 32, 0, c->stream>>>(
+    ++c->n_launch, k_lz_tridiag<<<c->S, 32, lz_tridiag_smem(kmax, c->p.lanczos_tol >= 1e-5), c->stream>>>(
         c->S, 0, jd, c->lz_h, cols, c->gm_h2, c->lz_alpha, c->lz_beta, c->lz_Wnorm, c->lz_c, c->lz_err, c->lz_active,
         c->lz_k, c->lz_lastk, c->lz_scal, c->p.lanczos_tol, fixed_mode ? c->lz_fix : nullptr, c->lz_hint, kmax,
-        c->susp_blob_off, (LzRot*)c->lz_rot, c->lz_rot_cap, c->dev_status);
+        c->susp_blob_off, c->dev_status);
     ++c->n_launch, k_seg_scale_slot<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_w, c->lz_scal, c->lz_V, n, jd,
                                                                         1, c->lz_vcur);
     ++c->n_launch, k_lz_next<<<1, 32, 0, c->stream>>>(c->S, c->lz_active, c->ctl, kmax, h);

@@ -489,8 +489,8 @@ __device__ inline void near_pair_correction(long long i, long long so, long long
 
 // Subtracts from (ux, uy, uz) the terms the FP32 pair kernel added for blob i's own body
 // [j0, j1) (self pair included), recomputed from the same FP32 operands with the same
-// operations, so that the FP32 rounding of those near-field terms cancels; the FP64
-// intra-body kernel then adds the exact same-body block.
+// operations, so that the FP32 rounding of those near-field terms cancels; the intra-body
+// kernel then adds the same-body block of the body's template.
 __device__ inline void same_body_subtract(const float4 pt, long long j0, long long j1, const float4* __restrict__ sdup,
                                           const RpyConst32& k, double& ux, double& uy, double& uz) {
     // summed in FP32 with compensation (FP64 adds are slow on GB300), subtracted once
@@ -523,7 +523,7 @@ __device__ inline void same_body_subtract(const float4 pt, long long j0, long lo
 // u_i = c0 (sum of the chunk partial sums [+ near-pair corrections]) [- K V]
 //
 // near_cnt != 0 (FP32 products): corrects the pairs of other bodies closer than 2a and takes
-// out the pair kernel's same-body terms (the intra-body kernel adds them exactly).
+// out the pair kernel's same-body terms (the intra-body kernel adds the template's block).
 template <typename P>
 __global__ void k_rpy_epilogue(int NBL, const P* __restrict__ part, const int* __restrict__ blob_susp,
                                const int* __restrict__ nk, double c0, const double* __restrict__ x,
@@ -628,9 +628,10 @@ static void launch_epilogue(gdc_ctx* c, int prec, double c0, const double* x, do
 
 void launch_rpy_epilogue(gdc_ctx* c, int prec, const double* x, double* y, int gm_layout) {
     launch_epilogue(c, prec, 1.0 / (8.0 * 3.141592653589793 * c->p.eta), x, y, gm_layout, prec == GDC_FP32_MIXED);
-    // same-body blocks in FP64: the df64 pair kernel leaves those pairs out and the FP32
-    // epilogue has taken the FP32 pair kernel's same-body terms out again
-    if (prec == GDC_PREC_DF64 || prec == GDC_FP32_MIXED) launch_intra_body(c, x, y, gm_layout);
+    // same-body blocks from the template: the df64 pair kernel leaves those pairs out and the
+    // FP32 epilogue has taken the FP32 pair kernel's same-body terms out again
+    if (prec == GDC_PREC_DF64) launch_intra_body(c, x, y, gm_layout);
+    if (prec == GDC_FP32_MIXED) launch_intra_body32(c, x, y, gm_layout);
 }
 
 // ---- pairs closer than 2a ------------------------------------------------------------
