@@ -1,36 +1,63 @@
-"""Oracle soft repulsion between blobs of different bodies.  TEST INFRASTRUCTURE ONLY.
+"""Oracle pair forces between blobs of different bodies.  TEST INFRASTRUCTURE ONLY.
 
-The force between two blobs a distance r apart is the (negative) derivative
-of the soft-sphere potential of Sec. 6.3, Eq. (soft_sphere_potential):
+The force between two blobs a distance r apart is F(r) = -dU_k/dr for one of three pair
+potentials, directed along r_i - r_j (F > 0 pushes blob i away from blob j):
 
-  F(r) = A exp(-(r - 2a)/b)  for r >= 2a,
-  F(r) = A                   for r <  2a  (the constant-force continuation
-                                           that the linear branch of Eq. (soft_sphere_potential) gives),
+  k = 0, soft sphere, Sec. 6.3, Eq. (soft_sphere_potential):
+      U(r) = U0 exp((2a - r)/b) for r >= 2a, so F(r) = A exp(-(r - 2a)/b) with A = U0/b;
+  k = 1, repel-attract, Sec. 6.4:       U_1 = U - phi_{3a};
+  k = 2, repel-attract-repel, Sec. 6.4: U_2 = U - phi_{3a} + phi_{7a/2};
 
-directed along r_i - r_j (it pushes blob i away from blob j), with A = U0/b.
-Blobs of the same body do not repel (their distances never change).  The
-body force and torque are F_p = sum_i f_i and T_p = sum_i (r_i - Y_p) x f_i
-(the K^T map of Eq. force_torque_balance_compact applied to the blob forces).
+with the Gaussian wells phi_c(r) = A_w exp(-((r - c)/lambda)^2), whose force is
+-dphi_c/dr = 2 A_w (r - c)/lambda^2 exp(-((r - c)/lambda)^2).  Below r = 2a every potential
+continues linearly (Eq. soft_sphere_potential's first branch for U; the sentence after
+U_2's definition for U_1 and U_2), so the force there is the force at 2a.
+
+Blobs of the same body do not interact (their distances never change).  The body force
+and torque are F_p = sum_i f_i and T_p = sum_i (r_i - Y_p) x f_i (the K^T map of
+Eq. force_torque_balance_compact applied to the blob forces).
 """
 from __future__ import annotations
 
 import numpy as np
 
 
-def blob_forces(r: np.ndarray, blob_body: np.ndarray, A: float, b: float, a: float) -> np.ndarray:
+SOFT, REPEL_ATTRACT, REPEL_ATTRACT_REPEL = 0, 1, 2
+
+
+def well_force(r: np.ndarray, c: float, well_A: float, well_lambda: float) -> np.ndarray:
+    """-dphi_c/dr for phi_c(r) = well_A exp(-((r - c)/well_lambda)^2) (Sec. 6.4)."""
+    x = (r - c) / well_lambda
+    return 2.0 * well_A * x / well_lambda * np.exp(-x * x)
+
+
+def pair_force(dist: np.ndarray, a: float, A: float, b: float, potential: int = SOFT, well_A: float = 0.0,
+               well_lambda: float = 0.5) -> np.ndarray:
+    """F_k(r) = -dU_k/dr, evaluated at max(r, 2a) (the linear continuation below 2a)."""
+    rr = np.maximum(np.asarray(dist, dtype=float), 2.0 * a)
+    F = A * np.exp(-(rr - 2.0 * a) / b) if A != 0.0 else np.zeros_like(rr)
+    if potential in (REPEL_ATTRACT, REPEL_ATTRACT_REPEL):
+        F = F - well_force(rr, 3.0 * a, well_A, well_lambda * a)
+    if potential == REPEL_ATTRACT_REPEL:
+        F = F + well_force(rr, 3.5 * a, well_A, well_lambda * a)
+    return F
+
+
+def blob_forces(r: np.ndarray, blob_body: np.ndarray, A: float, b: float, a: float, potential: int = SOFT,
+                well_A: float = 0.0, well_lambda: float = 0.5) -> np.ndarray:
+    """Blob forces f_i = sum over blobs j of other bodies of F_k(r_ij) (r_i - r_j)/r_ij.
+
+    well_lambda is in units of a (Sec. 6.4 uses A_w = 5 kT and lambda = 0.5 a)."""
     m = r.shape[0]
     f = np.zeros((m, 3))
-    if A == 0.0:
+    if A == 0.0 and (potential == SOFT or well_A == 0.0):
         return f
     for i in range(m):
         d = r[i][None, :] - r
         dist = np.linalg.norm(d, axis=1)
-        other = blob_body != blob_body[i]
-        mag = np.where(dist >= 2.0 * a, A * np.exp(-(dist - 2.0 * a) / b), A)
-        with np.errstate(invalid="ignore", divide="ignore"):
-            unit = d / dist[:, None]
-        sel = other & (dist > 0.0)
-        f[i] = (mag[sel, None] * unit[sel]).sum(axis=0)
+        sel = (blob_body != blob_body[i]) & (dist > 0.0)
+        mag = pair_force(dist[sel], a, A, b, potential, well_A, well_lambda)
+        f[i] = (mag[:, None] * d[sel] / dist[sel, None]).sum(axis=0)
     return f
 
 

@@ -42,6 +42,9 @@ class Params:
     rfd_delta: float = 1e-6
     rep_A: float = 0.0
     rep_b: float = 0.1
+    potential: int = 0          # forces.py: 0 soft sphere, 1 repel-attract, 2 repel-attract-repel
+    well_A: float = 0.0         # Gaussian well amplitude (Sec. 6.4: 5 kT)
+    well_lambda: float = 0.5    # Gaussian well width in units of a (Sec. 6.4: 0.5)
     shear_rate: float = 0.0
     sqrt_mode: str = "sym"      # "sym" (eigh) or "chol"
 
@@ -116,7 +119,7 @@ def fd_divergence(layout, Y, q, W, calV, p: Params) -> float:
 def midpoint_solve(layout, Ym, qm, W, p: Params):
     """Step 5: full mobility solve at the mid-step with the same W (Eq. step5)."""
     r, M, K, B, vb = brownian_slip(layout, Ym, qm, W, p)
-    f = forces.blob_forces(r, layout.blob_body, p.rep_A, p.rep_b, p.a)
+    f = forces.blob_forces(r, layout.blob_body, p.rep_A, p.rep_b, p.a, p.potential, p.well_A, p.well_lambda)
     FT = forces.body_force_torque(r, Ym, layout.blob_body, f)
     slip = vb.copy()
     if p.shear_rate != 0.0:

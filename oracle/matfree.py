@@ -9,6 +9,8 @@ from __future__ import annotations
 
 import numpy as np
 
+from . import forces
+
 
 def rpy_rows(r: np.ndarray, lam: np.ndarray, rows, a: float, eta: float) -> np.ndarray:
     """u_i for every i in ``rows``; r is (M, 3), lam is (M, 3); returns (len(rows), 3)."""
@@ -33,13 +35,14 @@ def rpy_rows(r: np.ndarray, lam: np.ndarray, rows, a: float, eta: float) -> np.n
     return out
 
 
-def repulsion_rows(r: np.ndarray, blob_body: np.ndarray, rows, A: float, b: float, a: float) -> np.ndarray:
-    """Blob repulsion forces f_i for the listed blobs (forces.py definition)."""
+def repulsion_rows(r: np.ndarray, blob_body: np.ndarray, rows, A: float, b: float, a: float, potential: int = 0,
+                   well_A: float = 0.0, well_lambda: float = 0.5) -> np.ndarray:
+    """Blob pair forces f_i for the listed blobs (forces.py definition)."""
     out = np.zeros((len(rows), 3))
     for k, i in enumerate(rows):
         d = r[i][None, :] - r
         dist = np.linalg.norm(d, axis=1)
         sel = (blob_body != blob_body[i]) & (dist > 0.0)
-        mag = np.where(dist[sel] >= 2.0 * a, A * np.exp(-(dist[sel] - 2.0 * a) / b), A)
+        mag = forces.pair_force(dist[sel], a, A, b, potential, well_A, well_lambda)
         out[k] = (mag[:, None] * d[sel] / dist[sel, None]).sum(axis=0)
     return out
