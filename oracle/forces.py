@@ -37,9 +37,9 @@ def pair_force(dist: np.ndarray, a: float, A: float, b: float, potential: int = 
     rr = np.maximum(np.asarray(dist, dtype=float), 2.0 * a)
     F = A * np.exp(-(rr - 2.0 * a) / b) if A != 0.0 else np.zeros_like(rr)
     if potential in (REPEL_ATTRACT, REPEL_ATTRACT_REPEL):
-        F = F - well_force(rr, 3.0 * a, well_A, well_lambda * a)
+        F = F - well_force(rr, 3.0 * a, well_A, well_lambda)
     if potential == REPEL_ATTRACT_REPEL:
-        F = F + well_force(rr, 3.5 * a, well_A, well_lambda * a)
+        F = F + well_force(rr, 3.5 * a, well_A, well_lambda)
     return F
 
 
@@ -47,7 +47,7 @@ def blob_forces(r: np.ndarray, blob_body: np.ndarray, A: float, b: float, a: flo
                 well_A: float = 0.0, well_lambda: float = 0.5) -> np.ndarray:
     """Blob forces f_i = sum over blobs j of other bodies of F_k(r_ij) (r_i - r_j)/r_ij.
 
-    well_lambda is in units of a (Sec. 6.4 uses A_w = 5 kT and lambda = 0.5 a)."""
+    b and well_lambda are lengths (Sec. 6.4 uses A_w = 5 kT and lambda = 0.5 a)."""
     m = r.shape[0]
     f = np.zeros((m, 3))
     if A == 0.0 and (potential == SOFT or well_A == 0.0):

@@ -44,7 +44,7 @@ class Params:
     rep_b: float = 0.1
     potential: int = 0          # forces.py: 0 soft sphere, 1 repel-attract, 2 repel-attract-repel
     well_A: float = 0.0         # Gaussian well amplitude (Sec. 6.4: 5 kT)
-    well_lambda: float = 0.5    # Gaussian well width in units of a (Sec. 6.4: 0.5)
+    well_lambda: float = 0.5    # Gaussian well width, a length (Sec. 6.4: 0.5 a)
     shear_rate: float = 0.0
     sqrt_mode: str = "sym"      # "sym" (eigh) or "chol"
 

@@ -44,7 +44,7 @@ def _energy(r, blob_body, potential, **kw):
 
 
 def _oracle(r, blob_body, potential, u0=U0, b=B, aw=AW, lam=LAM, a=1.0):
-    return forces.blob_forces(r, blob_body, u0 / b, b, a, potential, aw, lam)
+    return forces.blob_forces(r, blob_body, u0 / b, b, a, potential, aw, lam * a)
 
 
 def _three_bodies(seed):
