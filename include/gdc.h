@@ -67,6 +67,17 @@ typedef enum { GDC_DIV_RFD = 0, GDC_DIV_FD = 1 } gdc_divmode;
 /* Time integrator: the gDC of Sec. 3, or Euler-Maruyama of App. D (no drift). */
 typedef enum { GDC_SCHEME_GDC = 0, GDC_SCHEME_EM = 1 } gdc_scheme;
 
+/* Pair potential between blobs of different bodies (the forces F^m of Sec. 3 step 4):
+ * the soft sphere U of Eq. soft_sphere_potential alone, or with the Gaussian wells
+ * phi_c(r) = A_w exp(-((r - c)/lambda)^2) of Sec. 6.4: U_1 = U - phi_3a (repel-attract)
+ * or U_2 = U - phi_3a + phi_7a/2 (repel-attract-repel).  Each continues linearly below
+ * r = 2a, so overlapping blobs feel the force at 2a. */
+typedef enum { GDC_POT_SOFT = 0, GDC_POT_REPEL_ATTRACT = 1, GDC_POT_REPEL_ATTRACT_REPEL = 2 } gdc_potential;
+
+/* How the pair forces are summed: every pair of a suspension in tiles, or a cell list
+ * whose cells are at least the force cutoff wide (O(N_b) work for bounded density). */
+typedef enum { GDC_FORCES_CHOOSE = 0, GDC_FORCES_ALL_PAIRS = 1, GDC_FORCES_CELL_LIST = 2 } gdc_force_method;
+
 typedef struct {
     double eta;            /* fluid viscosity (Sec. 4.2)                               */
     double kT;             /* thermal energy k_B T (Eq. system_sde)                             */
@@ -98,6 +109,14 @@ typedef struct {
                               pair, target-side sums), 2 symmetric (every unordered pair
                               once, both sides), 0 the faster of the two as timed by the
                               autotuner (symmetric when autotune = 0)                    */
+    int    potential;      /* gdc_potential                                            */
+    double well_A;         /* well amplitude A_w, energy units (Sec. 6.4: 5 kT); 0 = no wells */
+    double well_lambda;    /* well width lambda, a length (Sec. 6.4: 0.5 a)            */
+    int    force_method;   /* gdc_force_method; GDC_FORCES_CHOOSE takes the cell list from
+                              16,384 blobs on and every pair below.  Both sum the pairs
+                              closer than the cutoff (36 b past 2a for the soft sphere,
+                              6 lambda past the outer well centre), each blob's terms in
+                              a fixed order: results are deterministic.                 */
 } gdc_params;
 
 typedef struct {
@@ -202,7 +221,8 @@ gdc_status gdc_brownian_slip(gdc_ctx* ctx, const double* W, double* vbrev, int* 
 /* Step 2 (Eq. sol_unconst): calV = (K^T K)^-1 K^T vbrev per body; vbrev dev 3 per blob, calV dev 6 per body. */
 gdc_status gdc_lsq_velocity(gdc_ctx* ctx, const double* vbrev, double* calV);
 
-/* Soft repulsion between blobs of different bodies, summed per body (dev out, 6 per body). */
+/* Pair forces (gdc_params.potential) between blobs of different bodies, summed per body
+ * as [F_p; T_p] (dev out, 6 per body). */
 gdc_status gdc_forces(gdc_ctx* ctx, double* FT);
 
 /* The N(0,1) draws of the step counter: stream 0 gives W (3 per blob),

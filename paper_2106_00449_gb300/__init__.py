@@ -23,6 +23,12 @@ DIV_RFD = 0
 DIV_FD = 1
 SCHEME_GDC = 0
 SCHEME_EM = 1
+POT_SOFT = 0
+POT_REPEL_ATTRACT = 1
+POT_REPEL_ATTRACT_REPEL = 2
+FORCES_CHOOSE = 0
+FORCES_ALL_PAIRS = 1
+FORCES_CELL_LIST = 2
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "NOT_CONVERGED", 4: "NONFINITE", 5: "TIMEOUT", 6: "WORKSPACE"}
 
@@ -51,7 +57,8 @@ class _Params(ctypes.Structure):
                 ("precision", ctypes.c_int), ("divmode", ctypes.c_int), ("scheme", ctypes.c_int),
                 ("rep_A", ctypes.c_double), ("rep_b", ctypes.c_double), ("shear_rate", ctypes.c_double),
                 ("seed", ctypes.c_ulonglong), ("autotune", ctypes.c_int), ("graph", ctypes.c_int),
-                ("pair_kernel", ctypes.c_int)]
+                ("pair_kernel", ctypes.c_int), ("potential", ctypes.c_int), ("well_A", ctypes.c_double),
+                ("well_lambda", ctypes.c_double), ("force_method", ctypes.c_int)]
 
 
 class _SolveInfo(ctypes.Structure):
@@ -102,6 +109,10 @@ class Params:
     autotune: int = 1
     graph: int = 1
     pair_kernel: int = 0
+    potential: int = 0
+    well_A: float = 0.0
+    well_lambda: float = 0.5
+    force_method: int = 0
 
     def _c(self) -> _Params:
         return _Params(**{f.name: getattr(self, f.name) for f in dataclasses.fields(self)})
@@ -394,6 +405,7 @@ def context_from_workload(wl, **overrides) -> Context:
     pp = wl.params
     kw = dict(eta=pp["eta"], kT=pp["kT"], a=pp["a"], dt=pp["dt"], gmres_tol=pp.get("gmres_tol", 1e-6),
               lanczos_tol=pp.get("lanczos_tol", 1e-4), rfd_delta=pp.get("rfd_delta", 1e-6), rep_A=pp.get("rep_A", 0.0),
-              rep_b=pp.get("rep_b", 0.1), shear_rate=pp.get("shear_rate", 0.0), seed=int(pp.get("seed", 0)))
+              rep_b=pp.get("rep_b", 0.1), shear_rate=pp.get("shear_rate", 0.0), seed=int(pp.get("seed", 0)),
+              potential=int(pp.get("potential", 0)), well_A=pp.get("well_A", 0.0), well_lambda=pp.get("well_lambda", 0.5))
     kw.update(overrides)
     return Context(Params(**kw), wl.templates, wl.body_tmpl, wl.susp_body_off, wl.Y, wl.q)

@@ -8,6 +8,7 @@
 #include <new>
 
 #include "common.cuh"
+#include "forces.cuh"
 
 namespace gdc {
 
@@ -69,6 +70,13 @@ static const char* validate_params(const gdc_params* p) {
     if (!(p->rep_A >= 0.0) || !std::isfinite(p->rep_A)) return "rep_A must be >= 0";
     if (p->rep_A > 0.0 && !(p->rep_b > 0.0)) return "rep_b must be > 0 when rep_A > 0";
     if (!std::isfinite(p->shear_rate)) return "shear_rate must be finite";
+    if (p->potential < 0 || p->potential > 2)
+        return "potential must be 0 (soft sphere), 1 (repel-attract) or 2 (repel-attract-repel)";
+    if (!(p->well_A >= 0.0) || !std::isfinite(p->well_A)) return "well_A must be >= 0";
+    if (p->potential > 0 && p->well_A > 0.0 && !(p->well_lambda > 0.0 && std::isfinite(p->well_lambda)))
+        return "well_lambda must be > 0 when the wells are on";
+    if (p->force_method < 0 || p->force_method > 2)
+        return "force_method must be 0 (choose), 1 (all pairs) or 2 (cell list)";
     return nullptr;
 }
 
@@ -203,6 +211,14 @@ static size_t carve(gdc_ctx* c, void* base) {
     c->nu = w.take<double>(S);
     c->divp = w.take<double>(S);
     c->fblob = w.take<double>(3 * NBL);
+    c->cell_H = cell_buckets(NBL);
+    c->cell_xyz = w.take<int4>(NBL);
+    c->cell_key = w.take<unsigned>(NBL);
+    c->cell_cnt = w.take<int>(c->cell_H);
+    c->cell_start = w.take<int>(c->cell_H);
+    c->cell_fill = w.take<int>(c->cell_H);
+    c->cell_list = w.take<int>(NBL);
+    c->cell_scan = w.take<int>(cell_scan_ints(NBL));
     c->u3 = w.take<double>(3 * NBL);
     const long long m = c->m, n = c->ngm;
     c->gm_V = w.take<double>((m + 1) * n);
@@ -353,8 +369,8 @@ static void load_at(gdc_ctx* c, const double* Y, const double* q) {
 }
 
 static gdc_status forces_at_loaded(gdc_ctx* c, double* FT) {
-    if (c->p.rep_A > 0.0) {
-        launch_forces_pair(c, c->p.precision, c->fblob);
+    if (forces_on(c->p)) {
+        launch_forces(c, c->p.precision, c->fblob);
         launch_body_KT(c, c->fblob, 0, FT, 0, 1.0);
     } else {
         cudaMemsetAsync(FT, 0, sizeof(double) * 6 * c->NB, c->stream);

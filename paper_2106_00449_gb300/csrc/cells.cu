@@ -1,0 +1,219 @@
+// Cell list for the short-range pair forces between blobs of different bodies.
+//
+// The pair force vanishes (below 1e-15 of its scale) beyond the cutoff r_c, so blob i
+// only needs the blobs of the 27 cells around its own when cells are at least r_c wide:
+// O(N_b) work at bounded density instead of the N_b^2 of the all-pairs tiles.  The domain
+// is unbounded and bodies drift, so cells are not stored as a grid: the integer cell
+// coordinates (and the suspension) are hashed into H buckets, H a power of two of at least
+// 2 N_b, and a bucket lists its blobs in ascending index.  A bucket may hold blobs of
+// several cells (hash collisions); a blob is taken only when its own cell is the
+// neighbour cell being visited, so every pair is seen exactly once per direction.
+//
+// Build (every configuration): cell and bucket per blob with a count per bucket; an
+// exclusive scan of the counts; a scatter into the buckets; an insertion sort of each
+// bucket by blob index.  The scatter order is arbitrary, the sorted lists are not, and
+// each blob sums its terms cell by cell in a fixed order: the forces are deterministic.
+#include <algorithm>
+
+#include "common.cuh"
+#include "forces.cuh"
+
+namespace gdc {
+
+constexpr int SCAN_B = 1024;
+
+__device__ __forceinline__ unsigned cell_hash(int ix, int iy, int iz, int s, unsigned mask) {
+    return ((unsigned)ix * 73856093u ^ (unsigned)iy * 19349663u ^ (unsigned)iz * 83492791u ^ (unsigned)s * 2654435761u) &
+           mask;
+}
+
+// floor(x / h) as an int, clamped so that a wild coordinate cannot overflow the cast
+__device__ __forceinline__ int cell_coord(double x, double h_inv) {
+    const double v = fmin(fmax(floor(x * h_inv), -1073741824.0), 1073741823.0);
+    return (int)v;
+}
+
+__global__ void k_cell_assign(int NBL, const double4* __restrict__ spos64, const int* __restrict__ blob_susp,
+                              double h_inv, unsigned mask, int4* __restrict__ cell_xyz, unsigned* __restrict__ cell_key,
+                              int* __restrict__ cnt) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= NBL) return;
+    const double4 p = spos64[i];
+    const int s = blob_susp[i];
+    const int4 cc = make_int4(cell_coord(p.x, h_inv), cell_coord(p.y, h_inv), cell_coord(p.z, h_inv), s);
+    const unsigned key = cell_hash(cc.x, cc.y, cc.z, s, mask);
+    cell_xyz[i] = cc;
+    cell_key[i] = key;
+    atomicAdd(cnt + key, 1);
+}
+
+// Exclusive scan of in[0, n) within blocks of SCAN_B elements; block totals to tot.
+__global__ void __launch_bounds__(SCAN_B) k_scan_block(int n, const int* __restrict__ in, int* __restrict__ out,
+                                                       int* __restrict__ tot) {
+    __shared__ int wsum[SCAN_B / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long i = (long long)blockIdx.x * SCAN_B + threadIdx.x;
+    const int v = i < n ? in[i] : 0;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int w = wsum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    const int excl = x - v + (warp > 0 ? wsum[warp - 1] : 0);
+    if (i < n) out[i] = excl;
+    if (threadIdx.x == SCAN_B - 1) tot[blockIdx.x] = excl + v;
+}
+
+__global__ void k_scan_add(int n, int* __restrict__ out, const int* __restrict__ base) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] += base[i / SCAN_B];
+}
+
+// Scratch ints the scan of n elements needs for its block totals (all levels).
+static long long scan_scratch(long long n) {
+    long long s = 0;
+    while (n > 1) {
+        n = (n + SCAN_B - 1) / SCAN_B;
+        s += 2 * n;
+    }
+    return s + 2;
+}
+
+// out = exclusive scan of in[0, n), with the block totals of every level in scratch
+static void scan_exclusive(gdc_ctx* c, int n, const int* in, int* out, int* scratch) {
+    const int nb = ceil_div(n, SCAN_B);
+    int* tot = scratch;
+    ++c->n_launch, k_scan_block<<<nb, SCAN_B, 0, c->stream>>>(n, in, out, tot);
+    if (nb == 1) return;
+    int* tot_ex = scratch + nb;
+    scan_exclusive(c, nb, tot, tot_ex, scratch + 2 * nb);
+    ++c->n_launch, k_scan_add<<<ceil_div(n, 256), 256, 0, c->stream>>>(n, out, tot_ex);
+}
+
+__global__ void k_cell_scatter(int NBL, const unsigned* __restrict__ cell_key, const int* __restrict__ start,
+                               int* __restrict__ fill, int* __restrict__ list) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= NBL) return;
+    const unsigned key = cell_key[i];
+    list[start[key] + atomicAdd(fill + key, 1)] = i;
+}
+
+__global__ void k_cell_sort(int H, const int* __restrict__ cnt, const int* __restrict__ start, int* __restrict__ list) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= H) return;
+    const int n = cnt[b];
+    if (n < 2) return;
+    int* l = list + start[b];
+    for (int i = 1; i < n; ++i) {
+        const int v = l[i];
+        int j = i - 1;
+        while (j >= 0 && l[j] > v) {
+            l[j + 1] = l[j];
+            --j;
+        }
+        l[j + 1] = v;
+    }
+}
+
+__device__ __forceinline__ long long body_of(float4 p) { return __float_as_int(p.w); }
+__device__ __forceinline__ long long body_of(double4 p) { return (long long)p.w; }
+
+// f_i = sum over blobs j of other bodies within the cutoff of F(r_ij) (r_i - r_j)/r_ij, in
+// precision T from the pair kernels' positions (relative to the suspension's reference
+// point); neighbour cells in z, y, x order, each bucket in ascending blob index.
+template <typename T, typename P4>
+__global__ void __launch_bounds__(128) k_forces_cell(int NBL, const P4* __restrict__ pos, const int4* __restrict__ cell_xyz,
+                                                     const int* __restrict__ cnt, const int* __restrict__ start,
+                                                     const int* __restrict__ list, unsigned mask, ForceK<T> k,
+                                                     double* __restrict__ fblob) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= NBL) return;
+    const P4 pi = pos[i];
+    const long long bi = body_of(pi);
+    const int4 ci = cell_xyz[i];
+    T fx = T(0), fy = T(0), fz = T(0);
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int cx = ci.x + dx, cy = ci.y + dy, cz = ci.z + dz;
+                const unsigned key = cell_hash(cx, cy, cz, ci.w, mask);
+                const int e0 = start[key], e1 = e0 + cnt[key];
+                for (int e = e0; e < e1; ++e) {
+                    const int j = list[e];
+                    const int4 cj = cell_xyz[j];
+                    if (cj.x != cx || cj.y != cy || cj.z != cz || cj.w != ci.w) continue;
+                    const P4 pj = pos[j];
+                    const T ddx = pi.x - pj.x, ddy = pi.y - pj.y, ddz = pi.z - pj.z;
+                    const T r2 = fma(ddx, ddx, fma(ddy, ddy, ddz * ddz));
+                    if (body_of(pj) != bi && r2 < k.rc2 && r2 > T(0)) {
+                        const T r = sqrt(r2);
+                        const T s = pair_force(r, k) / r;
+                        fx = fma(s, ddx, fx);
+                        fy = fma(s, ddy, fy);
+                        fz = fma(s, ddz, fz);
+                    }
+                }
+            }
+    fblob[3LL * i] = (double)fx;
+    fblob[3LL * i + 1] = (double)fy;
+    fblob[3LL * i + 2] = (double)fz;
+}
+
+long long cell_buckets(long long NBL) {
+    long long H = 1024;
+    while (H < 2 * NBL) H *= 2;
+    return H;
+}
+
+long long cell_scan_ints(long long NBL) { return scan_scratch(cell_buckets(NBL)); }
+
+bool forces_use_cells(const gdc_ctx* c) {
+    return c->p.force_method == GDC_FORCES_CELL_LIST ||
+           (c->p.force_method == GDC_FORCES_CHOOSE && c->NBL >= GDC_CELL_MIN_BLOBS);
+}
+
+void launch_forces_cell(gdc_ctx* c, int prec, double* fblob) {
+    const int H = (int)c->cell_H;
+    const unsigned mask = (unsigned)(H - 1);
+    const double h = force_cutoff(c->p) * (1.0 + 1e-4);   // FP32 r^2 < r_c^2 stays within adjacent cells
+    const int pe = prof_begin(c, 2);
+    cudaMemsetAsync(c->cell_cnt, 0, sizeof(int) * H, c->stream);
+    cudaMemsetAsync(c->cell_fill, 0, sizeof(int) * H, c->stream);
+    ++c->n_launch, k_cell_assign<<<ceil_div(c->NBL, 256), 256, 0, c->stream>>>(c->NBL, c->spos64, c->blob_susp, 1.0 / h,
+                                                                               mask, c->cell_xyz, c->cell_key, c->cell_cnt);
+    scan_exclusive(c, H, c->cell_cnt, c->cell_start, c->cell_scan);
+    ++c->n_launch, k_cell_scatter<<<ceil_div(c->NBL, 256), 256, 0, c->stream>>>(c->NBL, c->cell_key, c->cell_start,
+                                                                                c->cell_fill, c->cell_list);
+    ++c->n_launch, k_cell_sort<<<ceil_div(H, 256), 256, 0, c->stream>>>(H, c->cell_cnt, c->cell_start, c->cell_list);
+    if (prec == GDC_FP32_MIXED)
+        ++c->n_launch, k_forces_cell<float, float4><<<ceil_div(c->NBL, 128), 128, 0, c->stream>>>(
+            c->NBL, c->spos, c->cell_xyz, c->cell_cnt, c->cell_start, c->cell_list, mask, force_constants<float>(c->p),
+            fblob);
+    else
+        ++c->n_launch, k_forces_cell<double, double4><<<ceil_div(c->NBL, 128), 128, 0, c->stream>>>(
+            c->NBL, c->spos64, c->cell_xyz, c->cell_cnt, c->cell_start, c->cell_list, mask, force_constants<double>(c->p),
+            fblob);
+    prof_end(c, pe);
+}
+
+void launch_forces(gdc_ctx* c, int prec, double* fblob) {
+    if (forces_use_cells(c))
+        launch_forces_cell(c, prec, fblob);
+    else
+        launch_forces_pair(c, prec, fblob);
+}
+
+}  // namespace gdc

@@ -32,6 +32,7 @@
 #define GDC_NEAR_CAP 32          // blobs closer than 2a listed per blob (beyond: a search of the suspension)
 #define GDC_NEAR_SRC 2048        // sources per block of the near-pair search
 #define GDC_SYM_TILE 512         // blobs per tile of the symmetric FP32 pair kernel
+#define GDC_CELL_MIN_BLOBS 16384 // GDC_FORCES_CHOOSE: the cell list from this many blobs on
 
 namespace gdc {
 
@@ -125,6 +126,15 @@ struct gdc_ctx {
     double *tmpl_xyz = 0, *tmpl_L = 0;
     double *tmpl_Minv = 0, *tmpl_G = 0, *tmpl_N = 0, *tmpl_KtKp = 0, *tmpl_work = 0, *tmpl_M = 0;
     float* tmpl_M32 = 0;          // tmpl_M rounded to FP32 (intra-body block of the FP32 products)
+    // cell list of the pair forces (cells.cu)
+    long long cell_H = 0;         // buckets: a power of two >= 2 NBL
+    int4* cell_xyz = 0;           // per blob: cell coordinates and suspension
+    unsigned* cell_key = 0;       // per blob: bucket
+    int* cell_cnt = 0;            // per bucket: blobs
+    int* cell_start = 0;          // per bucket: first entry of cell_list
+    int* cell_fill = 0;           // per bucket: scatter counter
+    int* cell_list = 0;           // blob indices grouped by bucket, ascending within a bucket
+    int* cell_scan = 0;           // block totals of the bucket-count scan
     double *body_L = 0;
 
     // state (caller arrays)
@@ -307,6 +317,11 @@ void launch_pack_lambda(gdc_ctx* c, int prec, const double* x, int gm_layout);
 void launch_rpy(gdc_ctx* c, int prec);
 void launch_rpy_epilogue(gdc_ctx* c, int prec, const double* x, double* y, int gm_layout);
 void launch_forces_pair(gdc_ctx* c, int prec, double* fblob);
+void launch_forces_cell(gdc_ctx* c, int prec, double* fblob);
+void launch_forces(gdc_ctx* c, int prec, double* fblob);   // cell list or all pairs (force_method)
+bool forces_use_cells(const gdc_ctx* c);
+long long cell_buckets(long long NBL);
+long long cell_scan_ints(long long NBL);
 void launch_near_build(gdc_ctx* c);
 // sym.cu
 void build_sym_items(gdc_ctx* c, int width);

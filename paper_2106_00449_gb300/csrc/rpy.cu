@@ -13,6 +13,7 @@
 
 #include "common.cuh"
 #include "pair_common.cuh"
+#include "forces.cuh"
 
 namespace gdc {
 
@@ -710,15 +711,14 @@ void launch_near_build(gdc_ctx* c) {
     ++c->n_launch, k_near_sort<<<ceil_div(c->NBL, 256), 256, 0, c->stream>>>(c->NBL, c->near_cnt, c->near_idx);
 }
 
-// ---- soft repulsion between blobs of different bodies --------------------------
+// ---- pair forces between blobs of different bodies, every pair in tiles -------------
 
-// f_i = sum_j F(|r_i - r_j|) (r_i - r_j)/|r_i - r_j| over blobs j of other bodies,
-// F(r) = A exp(-(r - 2a)/b) for r >= 2a, A below.  Pairs with (r - 2a)/b > 36 are
-// skipped (their force is below 2.4e-16 A).
+// f_i = sum_j F(|r_i - r_j|) (r_i - r_j)/|r_i - r_j| over blobs j of other bodies with F
+// the pair force of forces.cuh; pairs beyond its cutoff are skipped.
 template <int TPT>
 __global__ void __launch_bounds__(128) k_forces32(const MvItem* __restrict__ items, const long long* __restrict__ susp_blob_off,
                                                   const float4* __restrict__ spos, float4* __restrict__ part, int NBL,
-                                                  float A, float b, float two_a, float rc2) {
+                                                  ForceK<float> k) {
     __shared__ float4 sp[MV_TILE];
     const MvItem it = items[blockIdx.x];
     const long long b0 = susp_blob_off[it.s];
@@ -726,7 +726,6 @@ __global__ void __launch_bounds__(128) k_forces32(const MvItem* __restrict__ ite
     const int ti0 = it.t0 + threadIdx.x;
     float xt[TPT], yt[TPT], zt[TPT], fx[TPT], fy[TPT], fz[TPT];
     int bt[TPT];
-    const float inv_b = 1.f / b;
     for (int t = 0; t < TPT; ++t) {
         fx[t] = fy[t] = fz[t] = 0.f;
         const float4 p = spos[b0 + min(ti0 + t * 128, ns - 1)];
@@ -747,10 +746,9 @@ __global__ void __launch_bounds__(128) k_forces32(const MvItem* __restrict__ ite
             for (int t = 0; t < TPT; ++t) {
                 const float dx = xt[t] - ps.x, dy = yt[t] - ps.y, dz = zt[t] - ps.z;
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                if (bj != bt[t] && r2 < rc2 && r2 > 0.f) {
+                if (bj != bt[t] && r2 < k.rc2 && r2 > 0.f) {
                     const float r = sqrtf(r2);
-                    const float F = r >= two_a ? A * expf(-(r - two_a) * inv_b) : A;
-                    const float s = F / r;
+                    const float s = pair_force(r, k) / r;
                     fx[t] = fmaf(s, dx, fx[t]);
                     fy[t] = fmaf(s, dy, fy[t]);
                     fz[t] = fmaf(s, dz, fz[t]);
@@ -767,7 +765,7 @@ __global__ void __launch_bounds__(128) k_forces32(const MvItem* __restrict__ ite
 template <int TPT>
 __global__ void __launch_bounds__(128) k_forces64(const MvItem* __restrict__ items, const long long* __restrict__ susp_blob_off,
                                                   const double4* __restrict__ spos, double4* __restrict__ part, int NBL,
-                                                  double A, double b, double two_a, double rc2) {
+                                                  ForceK<double> k) {
     __shared__ double4 sp[MV_TILE];
     const MvItem it = items[blockIdx.x];
     const long long b0 = susp_blob_off[it.s];
@@ -795,10 +793,9 @@ __global__ void __launch_bounds__(128) k_forces64(const MvItem* __restrict__ ite
             for (int t = 0; t < TPT; ++t) {
                 const double dx = xt[t] - ps.x, dy = yt[t] - ps.y, dz = zt[t] - ps.z;
                 const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                if (bj != bt[t] && r2 < rc2 && r2 > 0.0) {
+                if (bj != bt[t] && r2 < k.rc2 && r2 > 0.0) {
                     const double r = sqrt(r2);
-                    const double F = r >= two_a ? A * exp(-(r - two_a) / b) : A;
-                    const double s = F / r;
+                    const double s = pair_force(r, k) / r;
                     fx[t] = fma(s, dx, fx[t]);
                     fy[t] = fma(s, dy, fy[t]);
                     fz[t] = fma(s, dz, fz[t]);
@@ -816,15 +813,13 @@ __global__ void __launch_bounds__(128) k_forces64(const MvItem* __restrict__ ite
     do {                                                                                               \
         if (prec == GDC_FP32_MIXED)                                                                    \
             ++c->n_launch, k_forces32<TPT><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off, c->spos, \
-                (float4*)c->mv_part, c->NBL, (float)A, (float)b, (float)two_a, (float)(rc * rc));           \
+                (float4*)c->mv_part, c->NBL, force_constants<float>(c->p));                                \
         else                                                                                           \
             ++c->n_launch, k_forces64<TPT><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off,          \
-                c->spos64, (double4*)c->mv_part, c->NBL, A, b, two_a, rc * rc);                            \
+                c->spos64, (double4*)c->mv_part, c->NBL, force_constants<double>(c->p));                   \
     } while (0)
 
 void launch_forces_pair(gdc_ctx* c, int prec, double* fblob) {
-    const double A = c->p.rep_A, b = c->p.rep_b, two_a = 2.0 * c->p.a;
-    const double rc = two_a + 36.0 * b;
     const int pe = prof_begin(c, 2);
     if (c->mv_tpt == 1)
         GDC_FORCES_LAUNCH(1);

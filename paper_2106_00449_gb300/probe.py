@@ -2,7 +2,8 @@
 
     python -m paper_2106_00449_gb300.probe --op rpy32 --workload c3_65k --reps 5
 
-Ops: rpy32 / rpy64 (one RPY product in FP32 / FP64), saddle32, precond, forces32,
+Ops: rpy32 / rpy64 (one RPY product in FP32 / FP64), saddle32, precond, forces32 (positions
+and pair forces, --force-method, --potential),
 lanczos32 (one M^(1/2) W), solve32 (one FP32-mixed mobility solve), step32 (one gDC step).
 Prints the mean wall time per call measured with CUDA events on the library's stream.
 """
@@ -32,12 +33,16 @@ def main(argv=None) -> int:
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--pair-kernel", type=int, default=0, help="FP32 pair kernel: 0 autotuned, 1 ordered, 2 symmetric")
     ap.add_argument("--graph", type=int, default=1, help="step32: 1 replays the step as a CUDA graph, 0 host-driven")
+    ap.add_argument("--force-method", type=int, default=0, help="pair forces: 0 choose, 1 all pairs, 2 cell list")
+    ap.add_argument("--potential", type=int, default=0,
+                    help="0 soft sphere; 1, 2 with the Gaussian wells of Sec. 6.4 (A_w = 5 kT, lambda = 0.5 a)")
     args = ap.parse_args(argv)
     wl = WL.BY_NAME[args.workload]()
     if args.bodies:
         wl = wl.first_bodies(args.bodies)
     ctx = g.context_from_workload(wl, precision=g.FP32_MIXED, rfd_delta=1e-3, lanczos_max_iter=128,
-                                  pair_kernel=args.pair_kernel, graph=args.graph)
+                                  pair_kernel=args.pair_kernel, graph=args.graph, force_method=args.force_method,
+                                  potential=args.potential, well_A=5.0 if args.potential else 0.0, well_lambda=0.5)
     rng = np.random.default_rng(0)
     lam = torch.as_tensor(rng.standard_normal(3 * wl.n_blobs), device=ctx.device)
     x = torch.as_tensor(rng.standard_normal(int(ctx.saddle_off[-1])), device=ctx.device)
