@@ -74,8 +74,11 @@ typedef enum { GDC_SCHEME_GDC = 0, GDC_SCHEME_EM = 1 } gdc_scheme;
  * r = 2a, so overlapping blobs feel the force at 2a. */
 typedef enum { GDC_POT_SOFT = 0, GDC_POT_REPEL_ATTRACT = 1, GDC_POT_REPEL_ATTRACT_REPEL = 2 } gdc_potential;
 
-/* How the pair forces are summed: every pair of a suspension in tiles, or a cell list
- * whose cells are at least the force cutoff wide (O(N_b) work for bounded density). */
+/* How the short-range pair searches run -- the pair forces, and the list of pairs of
+ * different bodies closer than 2a that the FP32 RPY products correct: every pair of a
+ * suspension in tiles, or a cell list whose cells are at least the search radius wide
+ * (O(N_b) work at bounded density).  Both give the same pairs; the near-pair lists are
+ * identical entry for entry, so FP32 products do not depend on the method. */
 typedef enum { GDC_FORCES_CHOOSE = 0, GDC_FORCES_ALL_PAIRS = 1, GDC_FORCES_CELL_LIST = 2 } gdc_force_method;
 
 typedef struct {

@@ -185,11 +185,46 @@ bool forces_use_cells(const gdc_ctx* c) {
            (c->p.force_method == GDC_FORCES_CHOOSE && c->NBL >= GDC_CELL_MIN_BLOBS);
 }
 
-void launch_forces_cell(gdc_ctx* c, int prec, double* fblob) {
+// For every blob i, the blobs j of other bodies of its suspension whose FP32 r_ij^2, formed
+// with the FP32 pair kernels' operations (source minus target, fma(dx, dx, fma(dy, dy,
+// dz dz))), is below 4a^2, from a cell list of cells at least 2a wide: the list k_near_build
+// makes from every pair, entry for entry (k_near_sort then orders both the same way).
+__global__ void __launch_bounds__(128) k_near_cell(int NBL, const float4* __restrict__ spos,
+                                                   const int4* __restrict__ cell_xyz, const int* __restrict__ cnt,
+                                                   const int* __restrict__ start, const int* __restrict__ list,
+                                                   unsigned mask, float four_a2, int* __restrict__ near_cnt,
+                                                   int* __restrict__ near_idx) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= NBL) return;
+    const float4 pi = spos[i];
+    const int4 ci = cell_xyz[i];
+    int m = 0;
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int cx = ci.x + dx, cy = ci.y + dy, cz = ci.z + dz;
+                const unsigned key = cell_hash(cx, cy, cz, ci.w, mask);
+                const int e0 = start[key], e1 = e0 + cnt[key];
+                for (int e = e0; e < e1; ++e) {
+                    const int j = list[e];
+                    const int4 cj = cell_xyz[j];
+                    if (cj.x != cx || cj.y != cy || cj.z != cz || cj.w != ci.w) continue;
+                    const float4 pj = spos[j];
+                    const float ddx = __fsub_rn(pj.x, pi.x), ddy = __fsub_rn(pj.y, pi.y), ddz = __fsub_rn(pj.z, pi.z);
+                    const float r2 = __fmaf_rn(ddx, ddx, __fmaf_rn(ddy, ddy, __fmul_rn(ddz, ddz)));
+                    if (r2 < four_a2 && __float_as_int(pj.w) != __float_as_int(pi.w)) {
+                        if (m < GDC_NEAR_CAP) near_idx[(long long)i * GDC_NEAR_CAP + m] = j;
+                        ++m;
+                    }
+                }
+            }
+    near_cnt[i] = m;
+}
+
+// Buckets of the cells of edge h (bucket counts, starts and blob lists, sorted within a bucket).
+static void build_cells(gdc_ctx* c, double h) {
     const int H = (int)c->cell_H;
     const unsigned mask = (unsigned)(H - 1);
-    const double h = force_cutoff(c->p) * (1.0 + 1e-4);   // FP32 r^2 < r_c^2 stays within adjacent cells
-    const int pe = prof_begin(c, 2);
     cudaMemsetAsync(c->cell_cnt, 0, sizeof(int) * H, c->stream);
     cudaMemsetAsync(c->cell_fill, 0, sizeof(int) * H, c->stream);
     ++c->n_launch, k_cell_assign<<<ceil_div(c->NBL, 256), 256, 0, c->stream>>>(c->NBL, c->spos64, c->blob_susp, 1.0 / h,
@@ -198,6 +233,20 @@ void launch_forces_cell(gdc_ctx* c, int prec, double* fblob) {
     ++c->n_launch, k_cell_scatter<<<ceil_div(c->NBL, 256), 256, 0, c->stream>>>(c->NBL, c->cell_key, c->cell_start,
                                                                                 c->cell_fill, c->cell_list);
     ++c->n_launch, k_cell_sort<<<ceil_div(H, 256), 256, 0, c->stream>>>(H, c->cell_cnt, c->cell_start, c->cell_list);
+}
+
+void launch_near_cell(gdc_ctx* c) {
+    // cells 2a wide (and a margin): an FP32 r^2 below 4a^2 stays within adjacent cells
+    build_cells(c, 2.0 * c->p.a * (1.0 + 1e-4));
+    ++c->n_launch, k_near_cell<<<ceil_div(c->NBL, 128), 128, 0, c->stream>>>(
+        c->NBL, c->spos, c->cell_xyz, c->cell_cnt, c->cell_start, c->cell_list, (unsigned)(c->cell_H - 1),
+        (float)(4.0 * c->p.a * c->p.a), c->near_cnt, c->near_idx);
+}
+
+void launch_forces_cell(gdc_ctx* c, int prec, double* fblob) {
+    const unsigned mask = (unsigned)(c->cell_H - 1);
+    const int pe = prof_begin(c, 2);
+    build_cells(c, force_cutoff(c->p) * (1.0 + 1e-4));   // FP32 r^2 < r_c^2 stays within adjacent cells
     if (prec == GDC_FP32_MIXED)
         ++c->n_launch, k_forces_cell<float, float4><<<ceil_div(c->NBL, 128), 128, 0, c->stream>>>(
             c->NBL, c->spos, c->cell_xyz, c->cell_cnt, c->cell_start, c->cell_list, mask, force_constants<float>(c->p),

@@ -318,8 +318,9 @@ void launch_rpy(gdc_ctx* c, int prec);
 void launch_rpy_epilogue(gdc_ctx* c, int prec, const double* x, double* y, int gm_layout);
 void launch_forces_pair(gdc_ctx* c, int prec, double* fblob);
 void launch_forces_cell(gdc_ctx* c, int prec, double* fblob);
+void launch_near_cell(gdc_ctx* c);   // near-pair lists from a cell list (cells.cu)
 void launch_forces(gdc_ctx* c, int prec, double* fblob);   // cell list or all pairs (force_method)
-bool forces_use_cells(const gdc_ctx* c);
+bool forces_use_cells(const gdc_ctx* c);   // pair searches (forces, near pairs) on a cell list
 long long cell_buckets(long long NBL);
 long long cell_scan_ints(long long NBL);
 void launch_near_build(gdc_ctx* c);

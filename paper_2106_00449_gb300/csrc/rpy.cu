@@ -704,10 +704,14 @@ __global__ void k_near_sort(int n, const int* __restrict__ near_cnt, int* __rest
 }
 
 void launch_near_build(gdc_ctx* c) {
-    cudaMemsetAsync(c->near_cnt, 0, sizeof(int) * c->NBL, c->stream);
-    ++c->n_launch, k_near_build<<<c->n_near_items, 128, 0, c->stream>>>(c->near_items, c->susp_blob_off, c->spos,
-                                                                        (float)(4.0 * c->p.a * c->p.a), c->near_cnt,
-                                                                        c->near_idx);
+    if (forces_use_cells(c)) {
+        launch_near_cell(c);   // the same lists from a cell list, O(N_b)
+    } else {
+        cudaMemsetAsync(c->near_cnt, 0, sizeof(int) * c->NBL, c->stream);
+        ++c->n_launch, k_near_build<<<c->n_near_items, 128, 0, c->stream>>>(c->near_items, c->susp_blob_off, c->spos,
+                                                                            (float)(4.0 * c->p.a * c->p.a), c->near_cnt,
+                                                                            c->near_idx);
+    }
     ++c->n_launch, k_near_sort<<<ceil_div(c->NBL, 256), 256, 0, c->stream>>>(c->NBL, c->near_cnt, c->near_idx);
 }
 

@@ -13,6 +13,7 @@ import pytest
 
 from oracle import forces, geometry as G, matfree, philox
 from oracle import gdc as ogdc
+from synthetic import shapes
 from synthetic import workloads as WL
 
 from gpu_common import oracle_params, rel, rot_err, susp_layout
@@ -143,3 +144,36 @@ def test_step_with_repel_attract_repel_matches_oracle(lib):
     assert np.abs(f - f_soft).max() > 0.1
     assert rel(Y1 - Y, ora["Y1"] - Y) < 1e-6
     assert rot_err(q1, ora["q1"]) < 1e-9
+
+
+def _pile():
+    """Twelve 42-blob icospheres around nearly one centre: most blobs have more than the
+    list's 32 partners closer than 2a (the FP32 product then searches the suspension)."""
+    rng = np.random.default_rng(8)
+    n = 12
+    return WL.Workload("overlap_pile", [shapes.icosphere42()], np.zeros(n, dtype=np.int32),
+                       np.array([0, n], dtype=np.int64), rng.uniform(-0.3, 0.3, size=(n, 3)),
+                       WL.random_unit_quaternions(rng, n), dict(WL.c1().params), np.array([10.0]))
+
+
+def _overlapping_65k():
+    wl = WL.c3_65k()
+    Y = wl.Y.copy()
+    for p in range(0, 400, 2):
+        Y[p + 1] = Y[p] + np.array([0.9, 0.4, -0.3]) * (1 + p / 400)
+    return dataclasses.replace(wl, Y=Y)
+
+
+@pytest.mark.parametrize("which", ["pairs", "pile", "65k"])
+def test_near_pair_lists_do_not_depend_on_the_search(lib, which):
+    """The FP32 product corrects the pairs closer than 2a from per-blob lists; the cell list
+    must build the lists the all-pairs search builds, so that the products agree bit for bit."""
+    import torch
+    wl = {"pairs": _overlapping, "pile": _pile, "65k": _overlapping_65k}[which]()
+    rng = np.random.default_rng(41)
+    lam = torch.as_tensor(rng.standard_normal(3 * wl.n_blobs), device="cuda")
+    out = []
+    for method in (1, 2):
+        ctx = lib.context_from_workload(wl, precision=lib.FP32_MIXED, autotune=0, pair_kernel=2, force_method=method)
+        out.append(ctx.rpy_apply(lam, lib.FP32_MIXED).clone())
+    assert torch.equal(out[0], out[1])
