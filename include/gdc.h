@@ -263,6 +263,54 @@ gdc_status gdc_saddle_offsets(const gdc_ctx* ctx, long long* off);
 gdc_status gdc_rpy_apply_noalloc(const double* r, const double* lambda, double* u, int n_blobs,
                                  double a, double eta, void* stream);
 
+/* ---- fluctuating force-coupling method (FCM) in a periodic cube ---------------
+ *
+ * Sec. 4.2's other way to apply the mobility: M_FCM = J L^-1 S and the Brownian
+ * velocities v-breve = J L^-1 D W, on a regular grid of N^3 points in a periodic cube of
+ * side L (the implementation Sec. 4.2 and Sec. 6.1 describe):
+ *   S  spreads lambda_i with the Gaussian envelope (2 pi sigma^2)^(-3/2) exp(-|x - r_i|^2
+ *      / (2 sigma^2)) (Eq. spreading; sigma = a / sqrt(pi) gives the RPY self-mobility),
+ *      evaluated at minimum-image distances and cut off beyond R_t (Sec. 6.1: 3a);
+ *   L^-1 solves the Stokes equations (Eqs. fluc_stokes1-2) spectrally: mean flow zero, and
+ *      every mode with a Nyquist wavenumber component set to zero;
+ *   J  averages with the same envelopes by the trapezoidal rule (Eq. averaging, J = S*);
+ *   D W is the divergence of the fluctuating stress: six N(0,1) per grid point (Philox
+ *      stream 2, counter (k/2, owner, step, 2), normals xx, yy, zz, xy, xz, yz of point
+ *      x + N (y + N z)), diagonal entries scaled by 2 sqrt(kT eta / (h^3 dt)) and the others
+ *      by sqrt(2 kT eta / (h^3 dt)), h = L/N (Sec. 6.1), so that v-breve has the
+ *      covariance (2 kT / dt) M_FCM (Eq. fluctu_dissip in the velocity form of Sec. 3).
+ * Grid arithmetic (spreading, FFTs, solve) is FP32; averages are summed in FP32 rows added
+ * in FP64.  Positions may lie anywhere (they are wrapped into the cube).
+ * All arrays are device arrays of 3 doubles per blob, owned by the caller; calls are
+ * asynchronous on the stream given at init and end with a synchronisation.  The context
+ * allocates nothing after init: its grids live in the caller's workspace. */
+typedef struct gdc_fcm gdc_fcm;
+
+typedef struct {
+    int    N;         /* grid points per side: a power of two in [16, 512]          */
+    double L;         /* side of the periodic cube                                  */
+    double sigma;     /* envelope width                                             */
+    double R_t;       /* envelope truncation radius, 0 < R_t < L/2, R_t/(L/N) <= 15  */
+    double eta;       /* viscosity                                                  */
+    int    max_blobs; /* largest blob count of a call                               */
+} gdc_fcm_params;
+
+size_t     gdc_fcm_workspace_bytes(const gdc_fcm_params* params);
+gdc_status gdc_fcm_init(gdc_fcm** fcm, const gdc_fcm_params* params, void* workspace, size_t ws_bytes,
+                        void* stream);
+/* u = M_FCM lambda = J L^-1 S lambda at positions r (n_blobs <= max_blobs). */
+gdc_status gdc_fcm_apply(gdc_fcm* fcm, int n_blobs, const double* r, const double* lambda, double* u);
+/* Draws the stress of (seed, owner, step), keeps u-breve = L^-1 D W on the grid, and
+ * returns v = J u-breve at positions r (kT >= 0, dt > 0). */
+gdc_status gdc_fcm_brownian(gdc_fcm* fcm, unsigned long long seed, unsigned int owner, unsigned long long step,
+                            double kT, double dt, int n_blobs, const double* r, double* v);
+/* v = J u-breve of the last gdc_fcm_brownian at new positions r: the re-averaging that
+ * makes changes of configuration cheap for FCM (Sec. 5). */
+gdc_status gdc_fcm_average(gdc_fcm* fcm, int n_blobs, const double* r, double* v);
+const char* gdc_fcm_last_error(const gdc_fcm* fcm);
+unsigned long long gdc_fcm_launches(const gdc_fcm* fcm);   /* kernels launched since init */
+void       gdc_fcm_destroy(gdc_fcm* fcm);
+
 /* ---- instrumentation ---------------------------------------------------- */
 
 typedef struct {

@@ -50,25 +50,32 @@ class Grid:
         return self.L / self.N
 
 
-def _points(g: Grid) -> np.ndarray:
-    """Grid point coordinates, (N^3, 3) in flat order x + N (y + N z)."""
-    c = np.arange(g.N) * g.h
-    z, y, x = np.meshgrid(c, c, c, indexing="ij")
-    return np.stack([x.ravel(), y.ravel(), z.ravel()], axis=1)
-
-
 def envelopes(g: Grid, r: np.ndarray) -> list:
-    """Per particle: (flat indices, Delta_i values) of the grid points within R_t."""
+    """Per particle: (flat indices, Delta_i values) of the grid points within R_t.
+
+    Distances are minimum-image: for each axis the candidate grid indices are those within
+    R_t of the particle (the whole axis when that covers it), d = x_g - r - L round((x_g - r)/L).
+    """
     assert g.R_t < g.L / 2, "the truncated envelope must not meet its periodic image"
-    X = _points(g)
     norm = (2.0 * np.pi * g.sigma ** 2) ** -1.5
+    xs = np.arange(g.N) * g.h
+    m = int(np.ceil(g.R_t / g.h)) + 1
     out = []
     for ri in np.asarray(r, dtype=float).reshape(-1, 3):
-        d = X - ri
-        d -= g.L * np.round(d / g.L)
-        d2 = (d * d).sum(axis=1)
-        idx = np.flatnonzero(d2 <= g.R_t ** 2)
-        out.append((idx, norm * np.exp(-d2[idx] / (2.0 * g.sigma ** 2))))
+        axes = []
+        for d in range(3):
+            if 2 * m + 2 >= g.N:
+                idx = np.arange(g.N)
+            else:
+                idx = (int(np.floor(ri[d] / g.h)) - m + np.arange(2 * m + 2)) % g.N
+            dd = xs[idx] - ri[d]
+            dd -= g.L * np.round(dd / g.L)
+            axes.append((idx, dd))
+        (ix, dx), (iy, dy), (iz, dz) = axes
+        d2 = (dx[None, None, :] ** 2 + dy[None, :, None] ** 2) + dz[:, None, None] ** 2
+        flat = ix[None, None, :] + g.N * (iy[None, :, None] + g.N * iz[:, None, None])
+        sel = d2 <= g.R_t ** 2
+        out.append((flat[sel], norm * np.exp(-d2[sel] / (2.0 * g.sigma ** 2))))
     return out
 
 

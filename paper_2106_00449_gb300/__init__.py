@@ -39,6 +39,8 @@ EXPORTS = [
     "gdc_blob_positions", "gdc_rpy_apply", "gdc_saddle_apply", "gdc_precond_apply",
     "gdc_brownian_slip", "gdc_lsq_velocity", "gdc_forces", "gdc_draw_normals", "gdc_saddle_offsets",
     "gdc_profile", "gdc_profile_read", "gdc_rpy_apply_noalloc",
+    "gdc_fcm_workspace_bytes", "gdc_fcm_init", "gdc_fcm_apply", "gdc_fcm_brownian", "gdc_fcm_average",
+    "gdc_fcm_last_error", "gdc_fcm_launches", "gdc_fcm_destroy",
 ]
 
 NOALLOC_MAX_BLOBS = 16384   # GDC_NOALLOC_MAX_BLOBS of include/gdc.h
@@ -59,6 +61,11 @@ class _Params(ctypes.Structure):
                 ("seed", ctypes.c_ulonglong), ("autotune", ctypes.c_int), ("graph", ctypes.c_int),
                 ("pair_kernel", ctypes.c_int), ("potential", ctypes.c_int), ("well_A", ctypes.c_double),
                 ("well_lambda", ctypes.c_double), ("force_method", ctypes.c_int)]
+
+
+class _FcmParams(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("L", ctypes.c_double), ("sigma", ctypes.c_double), ("R_t", ctypes.c_double),
+                ("eta", ctypes.c_double), ("max_blobs", ctypes.c_int)]
 
 
 class _SolveInfo(ctypes.Structure):
@@ -157,8 +164,22 @@ def load_library() -> ctypes.CDLL:
     lib.gdc_profile.argtypes = [vp, ctypes.c_int]
     lib.gdc_profile_read.argtypes = [vp, ctypes.POINTER(_Profile)]
     lib.gdc_rpy_apply_noalloc.argtypes = [dp, dp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, vp]
+    lib.gdc_fcm_workspace_bytes.restype = ctypes.c_size_t
+    lib.gdc_fcm_workspace_bytes.argtypes = [ctypes.POINTER(_FcmParams)]
+    lib.gdc_fcm_init.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(_FcmParams), vp, ctypes.c_size_t, vp]
+    lib.gdc_fcm_apply.argtypes = [vp, ctypes.c_int, dp, dp, dp]
+    lib.gdc_fcm_brownian.argtypes = [vp, ctypes.c_ulonglong, ctypes.c_uint, ctypes.c_ulonglong, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_int, dp, dp]
+    lib.gdc_fcm_average.argtypes = [vp, ctypes.c_int, dp, dp]
+    lib.gdc_fcm_last_error.restype = cp
+    lib.gdc_fcm_last_error.argtypes = [vp]
+    lib.gdc_fcm_launches.restype = ctypes.c_ulonglong
+    lib.gdc_fcm_launches.argtypes = [vp]
+    lib.gdc_fcm_destroy.restype = None
+    lib.gdc_fcm_destroy.argtypes = [vp]
     for name in EXPORTS:
-        if name not in ("gdc_workspace_bytes", "gdc_destroy", "gdc_last_error"):
+        if name not in ("gdc_workspace_bytes", "gdc_destroy", "gdc_last_error", "gdc_fcm_workspace_bytes",
+                        "gdc_fcm_last_error", "gdc_fcm_launches", "gdc_fcm_destroy"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -379,6 +400,82 @@ class Context:
         out = self._dev(n)
         self._check(self.lib.gdc_draw_normals(self._h, ctypes.c_ulonglong(step), stream, _dptr(out)))
         return out
+
+
+class Fcm:
+    """Fluctuating FCM in a periodic cube of side L on an N^3 grid (C ABI gdc_fcm_*).
+
+    sigma: envelope width (a / sqrt(pi) matches the RPY self-mobility); R_t: envelope
+    truncation radius (3a in Sec. 6.1).  Positions and forces are (n, 3) float64 tensors on
+    the context's device; every call returns a new (n, 3) tensor.
+    """
+
+    def __init__(self, N: int, L: float, sigma: float, R_t: float, eta: float = 1.0, max_blobs: int = 1,
+                 device: int = 0, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("the gDC library needs a CUDA device")
+        self.torch = torch
+        self.lib = load_library()
+        self.device = torch.device("cuda", device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.params = _FcmParams(int(N), float(L), float(sigma), float(R_t), float(eta), int(max_blobs))
+        nbytes = int(self.lib.gdc_fcm_workspace_bytes(ctypes.byref(self.params)))
+        if nbytes == 0:
+            raise GdcError(1, "invalid FCM parameters")
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        ptr = self.workspace.data_ptr() + (-self.workspace.data_ptr()) % 256
+        h = ctypes.c_void_p(0)
+        st = self.lib.gdc_fcm_init(ctypes.byref(h), ctypes.byref(self.params), ctypes.c_void_p(ptr),
+                                   ctypes.c_size_t(nbytes), ctypes.c_void_p(self.stream.cuda_stream))
+        if st != 0:
+            raise GdcError(st, "gdc_fcm_init failed")
+        self._h = h
+
+    def _vec(self, x):
+        t = self.torch.as_tensor(x, dtype=self.torch.float64, device=self.device).reshape(-1, 3).contiguous()
+        return t
+
+    def _check(self, st):
+        if st != 0:
+            raise GdcError(st, self.lib.gdc_fcm_last_error(self._h).decode())
+
+    def apply(self, r, lam):
+        """u = M_FCM lambda (Sec. 4.2)."""
+        r, lam = self._vec(r), self._vec(lam)
+        u = self.torch.empty_like(r)
+        self._check(self.lib.gdc_fcm_apply(self._h, r.shape[0], _dptr(r), _dptr(lam), _dptr(u)))
+        return u
+
+    def brownian(self, r, seed: int, owner: int, step: int, kT: float, dt: float):
+        """v-breve = J L^-1 D W for the stress of (seed, owner, step); keeps u-breve for average()."""
+        r = self._vec(r)
+        v = self.torch.empty_like(r)
+        self._check(self.lib.gdc_fcm_brownian(self._h, int(seed), int(owner), int(step), float(kT), float(dt),
+                                              r.shape[0], _dptr(r), _dptr(v)))
+        return v
+
+    def average(self, r):
+        """J u-breve of the last brownian() at positions r."""
+        r = self._vec(r)
+        v = self.torch.empty_like(r)
+        self._check(self.lib.gdc_fcm_average(self._h, r.shape[0], _dptr(r), _dptr(v)))
+        return v
+
+    @property
+    def launches(self) -> int:
+        return int(self.lib.gdc_fcm_launches(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self.lib.gdc_fcm_destroy(self._h)
+        self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def rpy_apply_noalloc(r, lam, a: float = 1.0, eta: float = 1.0, out=None, stream=None):

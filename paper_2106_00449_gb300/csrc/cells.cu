@@ -83,7 +83,7 @@ __global__ void k_scan_add(int n, int* __restrict__ out, const int* __restrict__
 }
 
 // Scratch ints the scan of n elements needs for its block totals (all levels).
-static long long scan_scratch(long long n) {
+long long scan_scratch(long long n) {
     long long s = 0;
     while (n > 1) {
         n = (n + SCAN_B - 1) / SCAN_B;
@@ -93,14 +93,19 @@ static long long scan_scratch(long long n) {
 }
 
 // out = exclusive scan of in[0, n), with the block totals of every level in scratch
-static void scan_exclusive(gdc_ctx* c, int n, const int* in, int* out, int* scratch) {
+// (scan_scratch(n) ints); kernels counted in *n_launch
+void scan_exclusive(cudaStream_t st, unsigned long long* n_launch, int n, const int* in, int* out, int* scratch) {
     const int nb = ceil_div(n, SCAN_B);
     int* tot = scratch;
-    ++c->n_launch, k_scan_block<<<nb, SCAN_B, 0, c->stream>>>(n, in, out, tot);
+    ++*n_launch, k_scan_block<<<nb, SCAN_B, 0, st>>>(n, in, out, tot);
     if (nb == 1) return;
     int* tot_ex = scratch + nb;
-    scan_exclusive(c, nb, tot, tot_ex, scratch + 2 * nb);
-    ++c->n_launch, k_scan_add<<<ceil_div(n, 256), 256, 0, c->stream>>>(n, out, tot_ex);
+    scan_exclusive(st, n_launch, nb, tot, tot_ex, scratch + 2 * nb);
+    ++*n_launch, k_scan_add<<<ceil_div(n, 256), 256, 0, st>>>(n, out, tot_ex);
+}
+
+static void scan_exclusive(gdc_ctx* c, int n, const int* in, int* out, int* scratch) {
+    scan_exclusive(c->stream, &c->n_launch, n, in, out, scratch);
 }
 
 __global__ void k_cell_scatter(int NBL, const unsigned* __restrict__ cell_key, const int* __restrict__ start,

@@ -323,6 +323,9 @@ void launch_forces(gdc_ctx* c, int prec, double* fblob);   // cell list or all p
 bool forces_use_cells(const gdc_ctx* c);   // pair searches (forces, near pairs) on a cell list
 long long cell_buckets(long long NBL);
 long long cell_scan_ints(long long NBL);
+long long scan_scratch(long long n);   // ints of block totals an exclusive scan of n needs
+void scan_exclusive(cudaStream_t st, unsigned long long* n_launch, int n, const int* in, int* out, int* scratch);
+__global__ void k_cell_sort(int H, const int* __restrict__ cnt, const int* __restrict__ start, int* __restrict__ list);
 void launch_near_build(gdc_ctx* c);
 // sym.cu
 void build_sym_items(gdc_ctx* c, int width);

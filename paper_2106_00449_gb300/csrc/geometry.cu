@@ -2,6 +2,7 @@
 // the RFD/FD perturbations and divergence (Sec. 3 step 3, Eqs. FD and rfd_div), the mid-step
 // and final updates (Sec. 3 steps 4 and 6), and the right-hand side of Eq. (step5).
 #include "common.cuh"
+#include "philox.cuh"
 
 namespace gdc {
 
@@ -52,32 +53,6 @@ void load_config(gdc_ctx* c, const double* Y, const double* q) {
         c->NBL, c->blob_body, c->blob_susp, c->body_tmpl, c->body_blob_off, c->tmpl_off, c->tmpl_xyz,
         Y, c->Rb, c->ref, c->r, c->spos, c->spos64);
     launch_near_build(c);   // pairs closer than 2a, corrected after every FP32 product
-}
-
-// ---- Philox4x32-10 (Salmon et al., SC'11) + Box-Muller ----------------------
-
-__device__ inline uint4 philox4x32_10(uint4 ctr, uint2 key) {
-    const unsigned int M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
-    const unsigned int W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
-#pragma unroll
-    for (int rnd = 0; rnd < 10; ++rnd) {
-        if (rnd > 0) {
-            key.x += W0;
-            key.y += W1;
-        }
-        const unsigned int hi0 = __umulhi(M0, ctr.x), lo0 = M0 * ctr.x;
-        const unsigned int hi1 = __umulhi(M1, ctr.z), lo1 = M1 * ctr.z;
-        ctr = make_uint4(hi1 ^ ctr.y ^ key.x, lo1, hi0 ^ ctr.w ^ key.y, lo0);
-    }
-    return ctr;
-}
-
-__device__ inline double normal_from(uint4 x, int comp) {
-    const double u = (double)(x.x >> 5) * 7.450580596923828125e-9 + (double)(x.y >> 6) * 1.1102230246251565404e-16;
-    const double v = (double)(x.z >> 5) * 7.450580596923828125e-9 + (double)(x.w >> 6) * 1.1102230246251565404e-16;
-    const double rad = sqrt(-2.0 * log1p(-u));
-    const double ang = 2.0 * 3.141592653589793 * v;
-    return comp == 0 ? rad * cos(ang) : rad * sin(ang);
 }
 
 // stream 0: 3 draws per blob; stream 1: 6 draws per body.  Counter (k/2, s, step, stream).

@@ -1,0 +1,34 @@
+// Philox4x32-10 (Salmon, Moraes, Dror and Shaw, SC'11) and Box-Muller normals, shared by
+// the W / W-tilde draws (geometry.cu) and the FCM stress (fcm.cu).  Counter (k/2, owner,
+// step, stream), key (seed low, seed high); normal k is component k % 2 of counter k / 2.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace gdc {
+
+__device__ inline uint4 philox4x32_10(uint4 ctr, uint2 key) {
+    const unsigned int M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const unsigned int W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int rnd = 0; rnd < 10; ++rnd) {
+        if (rnd > 0) {
+            key.x += W0;
+            key.y += W1;
+        }
+        const unsigned int hi0 = __umulhi(M0, ctr.x), lo0 = M0 * ctr.x;
+        const unsigned int hi1 = __umulhi(M1, ctr.z), lo1 = M1 * ctr.z;
+        ctr = make_uint4(hi1 ^ ctr.y ^ key.x, lo1, hi0 ^ ctr.w ^ key.y, lo0);
+    }
+    return ctr;
+}
+
+__device__ inline double normal_from(uint4 x, int comp) {
+    const double u = (double)(x.x >> 5) * 7.450580596923828125e-9 + (double)(x.y >> 6) * 1.1102230246251565404e-16;
+    const double v = (double)(x.z >> 5) * 7.450580596923828125e-9 + (double)(x.w >> 6) * 1.1102230246251565404e-16;
+    const double rad = sqrt(-2.0 * log1p(-u));
+    const double ang = 2.0 * 3.141592653589793 * v;
+    return comp == 0 ? rad * cos(ang) : rad * sin(ang);
+}
+
+}  // namespace gdc

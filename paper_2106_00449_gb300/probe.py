@@ -4,7 +4,9 @@
 
 Ops: rpy32 / rpy64 (one RPY product in FP32 / FP64), saddle32, precond, forces32 (positions
 and pair forces, --force-method, --potential),
-lanczos32 (one M^(1/2) W), solve32 (one FP32-mixed mobility solve), step32 (one gDC step).
+lanczos32 (one M^(1/2) W), solve32 (one FP32-mixed mobility solve), step32 (one gDC step),
+fcm_apply / fcm_brownian / fcm_average (fluctuating FCM of the workload's blobs in a periodic
+cube of its box side, --fcm-n grid points per side).
 Prints the mean wall time per call measured with CUDA events on the library's stream.
 """
 from __future__ import annotations
@@ -34,12 +36,15 @@ def main(argv=None) -> int:
     ap.add_argument("--pair-kernel", type=int, default=0, help="FP32 pair kernel: 0 autotuned, 1 ordered, 2 symmetric")
     ap.add_argument("--graph", type=int, default=1, help="step32: 1 replays the step as a CUDA graph, 0 host-driven")
     ap.add_argument("--force-method", type=int, default=0, help="pair forces: 0 choose, 1 all pairs, 2 cell list")
+    ap.add_argument("--fcm-n", type=int, default=512, help="fcm_*: grid points per side of the periodic cube")
     ap.add_argument("--potential", type=int, default=0,
                     help="0 soft sphere; 1, 2 with the Gaussian wells of Sec. 6.4 (A_w = 5 kT, lambda = 0.5 a)")
     args = ap.parse_args(argv)
     wl = WL.BY_NAME[args.workload]()
     if args.bodies:
         wl = wl.first_bodies(args.bodies)
+    if args.op.startswith("fcm_"):
+        return _fcm(args, wl)
     ctx = g.context_from_workload(wl, precision=g.FP32_MIXED, rfd_delta=1e-3, lanczos_max_iter=128,
                                   pair_kernel=args.pair_kernel, graph=args.graph, force_method=args.force_method,
                                   potential=args.potential, well_A=5.0 if args.potential else 0.0, well_lambda=0.5)
@@ -71,6 +76,44 @@ def main(argv=None) -> int:
     prof = ctx.profile_read()
     print(json.dumps({"op": args.op, "workload": wl.name, "n_blobs": wl.n_blobs, "ms_per_call": ms,
                       "pairs": wl.pair_evals_per_matvec(), "pair_kernel": prof["pair_kernel"]}))
+    return 0
+
+
+def _fcm(args, wl) -> int:
+    """fcm_apply / fcm_brownian / fcm_average: the workload's blobs in a periodic cube of its
+    box side on an N^3 grid, sigma = a/sqrt(pi), envelopes cut at 3a (Sec. 4.2, Sec. 6.1)."""
+    import numpy as np
+    import torch
+
+    import paper_2106_00449_gb300 as g
+
+    ctx = g.context_from_workload(wl, precision=g.FP32_MIXED, autotune=0)
+    r = ctx.blob_positions().reshape(-1, 3).contiguous()
+    n = r.shape[0]
+    L = float(wl.box[0])
+    a = float(wl.params["a"])
+    F = g.Fcm(args.fcm_n, L, a / np.sqrt(np.pi), 3.0 * a, eta=float(wl.params["eta"]), max_blobs=n, stream=ctx.stream)
+    lam = torch.as_tensor(np.random.default_rng(0).standard_normal((n, 3)), device=r.device)
+    F.brownian(r, 1, 0, 0, 1.0, 0.01)
+    ops = {
+        "fcm_apply": lambda: F.apply(r, lam),
+        "fcm_brownian": lambda: F.brownian(r, 1, 0, 1, 1.0, 0.01),
+        "fcm_average": lambda: F.average(r),
+    }
+    fn = ops[args.op]
+    fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    l0 = F.launches
+    e0.record(ctx.stream)
+    for _ in range(args.reps):
+        fn()
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.reps
+    print(json.dumps({"op": args.op, "workload": wl.name, "n_blobs": n, "grid": args.fcm_n, "L": L,
+                      "ms_per_call": ms, "kernels_per_call": (F.launches - l0) / args.reps}))
     return 0
 
 

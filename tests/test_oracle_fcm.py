@@ -98,3 +98,20 @@ def test_brownian_velocity_is_reproducible_and_zero_mean_field():
     kz, ky, kx, keep = fcm.wavenumbers(g)
     uh = np.fft.fftn(u1, axes=(1, 2, 3))
     assert np.abs(kx * uh[0] + ky * uh[1] + kz * uh[2]).max() < 1e-9 * np.abs(uh).max()
+
+
+def test_envelopes_equal_a_search_of_every_grid_point():
+    g = fcm.Grid(32, 10.0, SIGMA, R_t=3.0)
+    r = np.concatenate([_particles(6, g.L, 6), [[0.0, 9.99, 5.0], [-0.2, 10.3, 20.1]]])   # edges and outside
+    c = np.arange(g.N) * g.h
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    X = np.stack([x.ravel(), y.ravel(), z.ravel()], axis=1)
+    for (idx, w), ri in zip(fcm.envelopes(g, r), r):
+        d = X - ri
+        d -= g.L * np.round(d / g.L)
+        d2 = (d * d).sum(axis=1)
+        want = np.flatnonzero(d2 <= g.R_t ** 2)
+        order = np.argsort(idx)
+        np.testing.assert_array_equal(idx[order], want)
+        ref = (2 * np.pi * g.sigma ** 2) ** -1.5 * np.exp(-d2[want] / (2 * g.sigma ** 2))
+        np.testing.assert_allclose(w[order], ref, rtol=1e-13, atol=0)
