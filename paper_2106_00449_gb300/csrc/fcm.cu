@@ -6,18 +6,20 @@
 // GB300 layout: the grid work is bandwidth-bound, so it runs in FP32 (complex float2 grids,
 // nine of N^3 points: 0-2 the deterministic force / velocity, 3-8 the stress, whose last
 // three slots end up holding the fluctuating velocity u-breve, kept for re-averaging).
-//   * spreading is a gather: each grid point sums the blobs of the 27 periodic binning
-//     cells around it (cells at least R_t wide, blobs in ascending index), so it is
-//     deterministic and needs no atomics on the grid; distances are formed in FP32 from
-//     positions relative to the cells' corners;
+//   * spreading is a gather: a block takes the grid points of one binning cell (cells at
+//     least R_t wide) and stages the blobs of the 27 cells around it (blobs in ascending
+//     index) in shared memory as FP32 offsets from the cell's corner; it is deterministic and
+//     needs no atomics on the grid;
 //   * the 3-D FFT is three passes of radix-2 transforms of whole pencils in shared memory,
-//     16 pencils per block; for the y and z passes the 16 pencils are 16 consecutive x, so
-//     every global access is a coalesced run;
+//     16 pencils per block, three butterfly stages per trip through shared memory; for the
+//     y and z passes the 16 pencils are 16 consecutive x, so every global access is a
+//     coalesced run;
 //   * the solve (projection, 1/(eta k^2), the spectral divergence of the stress and the 1/N^3
 //     of the inverse transform) is one pass over the modes;
-//   * averaging takes one warp per blob, lane = x offset inside the blob's box of at most
-//     31 grid points per side, with separable Gaussian factors; each lane sums its x column
-//     of a z-plane in FP32 and the planes in FP64, and the lanes are added in a fixed order.
+//   * averaging reads the velocity packed per point (one 16-byte load) and takes one warp per
+//     blob, each lane a fixed x offset and every (32 / width)-th row of the blob's box (at
+//     most 31 points per side); each lane sums its points of a z-plane in FP32 and the
+//     planes in FP64, and the lanes are added in a fixed order.
 #include <algorithm>
 #include <cmath>
 #include <new>
@@ -36,7 +38,8 @@ struct gdc_fcm {
     int nc = 2;               // binning cells per side
     float2* tw = nullptr;     // N/2 forward twiddles exp(-2 pi i j / N)
     float2* grid = nullptr;   // 9 complex grids
-    float4* prel = nullptr;   // blob positions relative to their binning cell's corner
+    float4* packed = nullptr; // 2 packed velocity grids: deterministic, fluctuating
+    double4* pw = nullptr;    // blob positions wrapped into the cube
     int* cell_of = nullptr;
     int* cnt = nullptr;
     int* start = nullptr;
@@ -86,7 +89,8 @@ static size_t fcm_carve(gdc_fcm* f, void* base) {
     const long long nc3 = (long long)f->nc * f->nc * f->nc;
     f->tw = w.take<float2>(f->N / 2);
     f->grid = w.take<float2>(9 * f->NG);
-    f->prel = w.take<float4>(f->p.max_blobs);
+    f->packed = w.take<float4>(2 * f->NG);
+    f->pw = w.take<double4>(f->p.max_blobs);
     f->cell_of = w.take<int>(f->p.max_blobs);
     f->cnt = w.take<int>(nc3);
     f->start = w.take<int>(nc3);
@@ -106,27 +110,30 @@ static void fcm_layout(gdc_fcm* f, const gdc_fcm_params& p) {
     f->nc = fcm_cells(p);
 }
 
-static size_t fft_smem(int N) { return (size_t)(FFT_P * (N + 1) + N / 2) * sizeof(float2); }
+// Shared-memory row of a pencil: N points, element i at i + i/16 (the padding spreads the
+// bit-reversed and strided accesses over the banks), rows an odd number of float2 apart.
+__host__ __device__ inline int fft_row(int N) { return N + N / 16 + 1; }
+__device__ __forceinline__ int fft_pad(int i) { return i + (i >> 4); }
+static size_t fft_smem(int N) { return (size_t)(FFT_P * fft_row(N) + N / 2) * sizeof(float2); }
 
 // ---- binning ------------------------------------------------------------------------
 
-// Wraps each blob into the cube, bins it, and keeps its position relative to its binning
-// cell's corner in FP32 (small numbers, so FP32 distances stay accurate at any L).
-__global__ void k_fcm_bin(int n, const double* __restrict__ r, double L, int nc, float4* __restrict__ prel,
+// Wraps each blob into the cube and bins it.
+__global__ void k_fcm_bin(int n, const double* __restrict__ r, double L, int nc, double4* __restrict__ pw,
                           int* __restrict__ cell_of, int* __restrict__ cnt) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double w = L / nc;
-    float x[3];
+    double x[3];
     int c[3];
     for (int d = 0; d < 3; ++d) {
         double v = r[3LL * i + d];
         v -= L * floor(v / L);
         if (!(v < L) || !(v >= 0.0)) v = 0.0;   // v == L after rounding, or not finite
         c[d] = (int)fmin(fmax(floor(v / w), 0.0), nc - 1.0);
-        x[d] = (float)(v - c[d] * w);
+        x[d] = v;
     }
-    prel[i] = make_float4(x[0], x[1], x[2], 0.f);
+    pw[i] = make_double4(x[0], x[1], x[2], 0.0);
     const int id = c[0] + nc * (c[1] + nc * c[2]);
     cell_of[i] = id;
     atomicAdd(cnt + id, 1);
@@ -142,55 +149,121 @@ __global__ void k_fcm_scatter(int n, const int* __restrict__ cell_of, const int*
 
 // ---- spreading (gather) -----------------------------------------------------------------
 
-// f(x_g) = sum of lambda_j Delta_j(x_g) over the blobs of the binning cells around x_g.
-// Distances: d = (x_g - corner of its cell) - (p_j - corner of p_j's cell) - o w for the
-// cell offset o, all small numbers in FP32; then the minimum image (two comparisons).
-__global__ void __launch_bounds__(256) k_fcm_spread(long long NG, int N, double h, double L, int nc,
-                                                    const float4* __restrict__ prel, const int* __restrict__ cnt,
-                                                    const int* __restrict__ start, const int* __restrict__ list,
-                                                    const double* __restrict__ lam, float R2, float inv2s2, float norm,
-                                                    float2* __restrict__ f) {
-    const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (g >= NG) return;
+constexpr int SP_CHUNK = 512;    // blobs staged in shared memory per round
+
+// f(x_g) = sum of lambda_j Delta_j(x_g).  One block per binning cell (cells at least R_t wide):
+// its grid points are those with floor(i nc / N) equal to the cell's index on every axis (an
+// exact integer partition of the grid), and every blob that can reach them lies in the 27
+// cells around it.  Those blobs are staged in shared memory (cells in a fixed order, blobs in
+// ascending index; rounds of SP_CHUNK) as FP32 offsets from the cell's corner, nearest image
+// to the cell's centre, and each thread sums them for its grid points with the minimum image
+// in FP32.  Deterministic, no atomics on the grid.
+template <int PT>   // grid points a thread keeps per round (cells with more points take several rounds)
+__global__ void __launch_bounds__(128) k_fcm_spread(int N, double h, double L, int nc, const double4* __restrict__ pw,
+                                                    const int* __restrict__ cnt, const int* __restrict__ start,
+                                                    const int* __restrict__ list, const double* __restrict__ lam,
+                                                    float R2, float inv2s2, float norm, float2* __restrict__ f,
+                                                    long long NG) {
+    __shared__ float4 sp[SP_CHUNK];
+    __shared__ float4 sl[SP_CHUNK];
+    __shared__ int c_start[27], c_off[28];
+    const int b = blockIdx.x;
+    const int c3[3] = {b % nc, (b / nc) % nc, b / (nc * nc)};
     const double w = L / nc;
-    const float wf = (float)w, Lf = (float)L, hL = 0.5f * (float)L;
-    const int ig[3] = {(int)(g % N), (int)((g / N) % N), (int)(g / ((long long)N * N))};
-    int c[3];
-    float xr[3];
+    int g0[3], gn[3];
+    double corner[3];
     for (int d = 0; d < 3; ++d) {
-        const double x = ig[d] * h;
-        c[d] = min(nc - 1, (int)(x / w));
-        xr[d] = (float)(x - c[d] * w);
+        g0[d] = (c3[d] * N + nc - 1) / nc;                  // first i with floor(i nc / N) = c
+        gn[d] = ((c3[d] + 1) * N + nc - 1) / nc - g0[d];
+        corner[d] = c3[d] * w;
     }
-    const int no = nc >= 3 ? 3 : nc, o0 = nc >= 3 ? -1 : 0;
-    float ax = 0.f, ay = 0.f, az = 0.f;
-    for (int oz = 0; oz < no; ++oz)
-        for (int oy = 0; oy < no; ++oy)
-            for (int ox = 0; ox < no; ++ox) {
-                const int o[3] = {o0 + ox, o0 + oy, o0 + oz};
-                const int cx = (c[0] + o[0] + nc) % nc, cy = (c[1] + o[1] + nc) % nc, cz = (c[2] + o[2] + nc) % nc;
-                const int id = cx + nc * (cy + nc * cz);
-                const float bx = xr[0] - o[0] * wf, by = xr[1] - o[1] * wf, bz = xr[2] - o[2] * wf;
-                const int e1 = start[id] + cnt[id];
-                for (int e = start[id]; e < e1; ++e) {
-                    const int j = list[e];
-                    const float4 p = prel[j];
-                    float dx = bx - p.x, dy = by - p.y, dz = bz - p.z;
+    const int npts = gn[0] * gn[1] * gn[2];
+    if (npts == 0) return;
+    // the neighbour cells (each once when the grid has fewer than 3 cells per side)
+    const int no = nc >= 3 ? 3 : nc, o0 = nc >= 3 ? -1 : 0, ncell = no * no * no;
+    if (threadIdx.x < ncell) {
+        const int k = threadIdx.x;
+        const int ox = o0 + k % no, oy = o0 + (k / no) % no, oz = o0 + k / (no * no);
+        const int id = (c3[0] + ox + nc) % nc + nc * ((c3[1] + oy + nc) % nc + nc * ((c3[2] + oz + nc) % nc));
+        c_start[k] = start[id];
+        c_off[k + 1] = cnt[id];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        c_off[0] = 0;
+        for (int k = 0; k < ncell; ++k) c_off[k + 1] += c_off[k];
+    }
+    __syncthreads();
+    const int total = c_off[ncell];
+    const float Lf = (float)L, hL = 0.5f * Lf;
+    const double mid = 0.5 * w;
+    for (int p0 = 0; p0 < npts; p0 += PT * 128) {
+        float gx[PT], gy[PT], gz[PT], ax[PT], ay[PT], az[PT];
+        long long gi[PT];
+#pragma unroll
+        for (int q = 0; q < PT; ++q) {
+            const int pt = p0 + q * 128 + (int)threadIdx.x;
+            ax[q] = ay[q] = az[q] = 0.f;
+            gi[q] = -1;
+            gx[q] = gy[q] = gz[q] = 0.f;
+            if (pt < npts) {
+                const int ix = g0[0] + pt % gn[0], iy = g0[1] + (pt / gn[0]) % gn[1], iz = g0[2] + pt / (gn[0] * gn[1]);
+                gx[q] = (float)(ix * h - corner[0]);
+                gy[q] = (float)(iy * h - corner[1]);
+                gz[q] = (float)(iz * h - corner[2]);
+                gi[q] = ix + (long long)N * (iy + (long long)N * iz);
+            }
+        }
+        for (int s0 = 0; s0 < total; s0 += SP_CHUNK) {
+            const int take = min(SP_CHUNK, total - s0);
+            __syncthreads();
+            for (int t = threadIdx.x; t < take; t += blockDim.x) {
+                const int e = s0 + t;
+                int k = 0;
+                while (c_off[k + 1] <= e) ++k;
+                const int j = list[c_start[k] + (e - c_off[k])];
+                const double4 p = pw[j];
+                double rx = p.x - corner[0], ry = p.y - corner[1], rz = p.z - corner[2];
+                rx -= L * rint((rx - mid) / L);
+                ry -= L * rint((ry - mid) / L);
+                rz -= L * rint((rz - mid) / L);
+                sp[t] = make_float4((float)rx, (float)ry, (float)rz, 0.f);
+                sl[t] = make_float4((float)lam[3LL * j], (float)lam[3LL * j + 1], (float)lam[3LL * j + 2], 0.f);
+            }
+            __syncthreads();
+            for (int j = 0; j < take; ++j) {
+                const float4 pj = sp[j], lj = sl[j];
+#pragma unroll
+                for (int q = 0; q < PT; ++q) {
+                    float dx = gx[q] - pj.x, dy = gy[q] - pj.y, dz = gz[q] - pj.z;
                     dx = dx > hL ? dx - Lf : (dx < -hL ? dx + Lf : dx);
                     dy = dy > hL ? dy - Lf : (dy < -hL ? dy + Lf : dy);
                     dz = dz > hL ? dz - Lf : (dz < -hL ? dz + Lf : dz);
                     const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                     if (d2 <= R2) {
                         const float wt = norm * expf(-d2 * inv2s2);
-                        ax = fmaf((float)lam[3LL * j], wt, ax);
-                        ay = fmaf((float)lam[3LL * j + 1], wt, ay);
-                        az = fmaf((float)lam[3LL * j + 2], wt, az);
+                        ax[q] = fmaf(lj.x, wt, ax[q]);
+                        ay[q] = fmaf(lj.y, wt, ay[q]);
+                        az[q] = fmaf(lj.z, wt, az[q]);
                     }
                 }
             }
-    f[g] = make_float2(ax, 0.f);
-    f[NG + g] = make_float2(ay, 0.f);
-    f[2 * NG + g] = make_float2(az, 0.f);
+        }
+#pragma unroll
+        for (int q = 0; q < PT; ++q)
+            if (gi[q] >= 0) {
+                f[gi[q]] = make_float2(ax[q], 0.f);
+                f[NG + gi[q]] = make_float2(ay[q], 0.f);
+                f[2 * NG + gi[q]] = make_float2(az[q], 0.f);
+            }
+    }
+}
+
+// The three real parts of a velocity's complex grids packed per point (x, y, z, 0).
+__global__ void k_fcm_pack(long long NG, const float2* __restrict__ u, float4* __restrict__ out) {
+    const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (g >= NG) return;
+    out[g] = make_float4(u[g].x, u[NG + g].x, u[2 * NG + g].x, 0.f);
 }
 
 // ---- FFT: radix-2 transforms of 16 pencils per block, one axis per pass -----------------
@@ -201,7 +274,7 @@ template <int INV>
 __global__ void __launch_bounds__(256) k_fft(float2* __restrict__ data, long long NG, const float2* __restrict__ tw_g,
                                              int N, int logN, int axis) {
     extern __shared__ float2 sm[];
-    const int S = N + 1;
+    const int S = fft_row(N);
     float2* tw = sm + FFT_P * S;
     float2* base = data + blockIdx.y * NG;
     const int groups = N / FFT_P;
@@ -229,28 +302,50 @@ __global__ void __launch_bounds__(256) k_fft(float2* __restrict__ data, long lon
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
         const int t = axis == 0 ? e % N : e / FFT_P;
         const int p = axis == 0 ? e / N : e % FFT_P;
-        sm[p * S + (int)(__brev((unsigned)t) >> (32 - logN))] = base[off + p * sp + t * st];
+        sm[p * S + fft_pad((int)(__brev((unsigned)t) >> (32 - logN)))] = base[off + p * sp + t * st];
     }
-    for (int len = 2; len <= N; len <<= 1) {
-        const int half = len >> 1, tstep = N / len;
+    // log2 N radix-2 stages, fused three at a time: a thread loads the 8 elements
+    // k + m h (m = 0..7) of a group of 8h, applies the stages of half h, 2h, 4h in registers
+    // (the same butterflies, in the same arithmetic, as stage-by-stage), and stores them back.
+    const int first = logN % 3 == 0 ? 3 : logN % 3;
+    for (int s0 = 0, ns = first; s0 < logN; s0 += ns, ns = 3) {
+        const int h = 1 << s0, span = h << ns, per = N >> ns;   // groups x offsets per pencil
         __syncthreads();
-        for (int q = threadIdx.x; q < FFT_P * (N >> 1); q += blockDim.x) {
-            const int p = q / (N >> 1), bb = q % (N >> 1);
-            const int grp = bb / half, k = bb - grp * half;
-            const int i0 = grp * len + k, i1 = i0 + half;
+        for (int q = threadIdx.x; q < FFT_P * per; q += blockDim.x) {
+            const int p = q / per, r = q % per;
+            const int k = r % h, base0 = (r / h) * span + k;
             float2* row = sm + p * S;
-            const float2 w = tw[k * tstep];
-            const float2 x0 = row[i0], x1 = row[i1];
-            const float2 t = make_float2(w.x * x1.x - w.y * x1.y, w.x * x1.y + w.y * x1.x);
-            row[i0] = make_float2(x0.x + t.x, x0.y + t.y);
-            row[i1] = make_float2(x0.x - t.x, x0.y - t.y);
+            float2 x[8];
+#pragma unroll
+            for (int m = 0; m < 8; ++m)
+                if (m < (1 << ns)) x[m] = row[fft_pad(base0 + m * h)];
+#pragma unroll
+            for (int st = 0; st < 3; ++st) {
+                if (st < ns) {
+                    const int hs = h << st, tstep = N / (2 * hs);
+#pragma unroll
+                    for (int m = 0; m < 8; ++m) {
+                        if (m < (1 << ns) && ((m >> st) & 1) == 0) {
+                            const int m2 = m + (1 << st);
+                            const float2 w = tw[(k + (m & ((1 << st) - 1)) * h) * tstep];
+                            const float2 x0 = x[m], x1 = x[m2];
+                            const float2 t = make_float2(w.x * x1.x - w.y * x1.y, w.x * x1.y + w.y * x1.x);
+                            x[m] = make_float2(x0.x + t.x, x0.y + t.y);
+                            x[m2] = make_float2(x0.x - t.x, x0.y - t.y);
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int m = 0; m < 8; ++m)
+                if (m < (1 << ns)) row[fft_pad(base0 + m * h)] = x[m];
         }
     }
     __syncthreads();
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
         const int t = axis == 0 ? e % N : e / FFT_P;
         const int p = axis == 0 ? e / N : e % FFT_P;
-        base[off + p * sp + t * st] = sm[p * S + t];
+        base[off + p * sp + t * st] = sm[p * S + fft_pad(t)];
     }
 }
 
@@ -322,27 +417,28 @@ __global__ void k_fcm_solve_stress(long long NG, int N, float kunit, float scale
 
 // ---- fluctuating stress ---------------------------------------------------------------------
 
-__global__ void k_fcm_stress(long long NG, unsigned long long seed, unsigned owner, unsigned long long step, double sd,
-                             double so, float2* __restrict__ W) {
+// Six normals per grid point (Box-Muller in FP32: the grid is FP32, and FP64 logarithms and
+// sines for 6 N^3 draws would dominate the Brownian velocity on GB300).
+__global__ void k_fcm_stress(long long NG, unsigned long long seed, unsigned owner, unsigned long long step, float sd,
+                             float so, float2* __restrict__ W) {
     const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (g >= NG) return;
     const uint2 key = make_uint2((unsigned)(seed & 0xffffffffull), (unsigned)(seed >> 32));
-    double n[6];
+    float n[6];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
         const uint4 x = philox4x32_10(make_uint4((unsigned)(3 * g + q), owner, (unsigned)(step & 0xffffffffull), 2u), key);
-        n[2 * q] = normal_from(x, 0);
-        n[2 * q + 1] = normal_from(x, 1);
+        normals_f32(x, n[2 * q], n[2 * q + 1]);
     }
 #pragma unroll
-    for (int c = 0; c < 6; ++c) W[c * NG + g] = make_float2((float)((c < 3 ? sd : so) * n[c]), 0.f);
+    for (int c = 0; c < 6; ++c) W[c * NG + g] = make_float2((c < 3 ? sd : so) * n[c], 0.f);
 }
 
 // ---- averaging ------------------------------------------------------------------------------
 
 __global__ void __launch_bounds__(128) k_fcm_average(int n, const double* __restrict__ r, double L, int N, double h,
                                                      double R_t, float inv2s2, double wscale,
-                                                     const float2* __restrict__ u, long long NG, double* __restrict__ v) {
+                                                     const float4* __restrict__ u, double* __restrict__ v) {
     const int i = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (i >= n) return;
@@ -356,28 +452,33 @@ __global__ void __launch_bounds__(128) k_fcm_average(int n, const double* __rest
         lo[d] = (int)ceil((x - R_t) / h);
         cn[d] = min(31, (int)floor((x + R_t) / h) - lo[d] + 1);
     }
-    const double R2 = R_t * R_t;
-    const bool on = lane < cn[0];
-    const int gx = lo[0] + lane;
-    const double dx = gx * h - p[0];
-    const float wx = on ? expf(-(float)(dx * dx) * inv2s2) : 0.f;
-    const int ix = ((gx % N) + N) % N;
+    // offsets from the blob to the first grid point of its box, then steps of h, in FP32
+    // (magnitudes below R_t + h, so FP32 keeps them to ~1e-7 R_t)
+    const float hf = (float)h, R2 = (float)(R_t * R_t);
+    const float d0x = (float)(lo[0] * h - p[0]), d0y = (float)(lo[1] * h - p[1]), d0z = (float)(lo[2] * h - p[2]);
+    const int mask = N - 1;                          // N is a power of two
+    const int rows = cn[0] <= 16 ? 32 / cn[0] : 1;   // box rows a warp covers per pass
+    const int ox = lane % cn[0], oyr = lane / cn[0];
+    const bool on = oyr < rows;
+    const float dx = d0x + ox * hf;
+    const float wx = expf(-dx * dx * inv2s2);
+    const int ix = (lo[0] + ox) & mask;
     double acc[3] = {0.0, 0.0, 0.0};
     for (int oz = 0; oz < cn[2]; ++oz) {
-        const int gz = lo[2] + oz;
-        const double dz = gz * h - p[2];
-        const float wz = expf(-(float)(dz * dz) * inv2s2);
-        const long long zoff = (long long)(((gz % N) + N) % N) * N * N;
+        const float dz = d0z + oz * hf;
+        const float wz = expf(-dz * dz * inv2s2) * wx;
+        const float dxz = fmaf(dx, dx, dz * dz);
+        const long long zoff = (long long)((lo[2] + oz) & mask) * N * N + ix;
         float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-        for (int oy = 0; oy < cn[1]; ++oy) {
-            const int gy = lo[1] + oy;
-            const double dy = gy * h - p[1];
-            if (on && dx * dx + dy * dy + dz * dz <= R2) {
-                const float w = wx * expf(-(float)(dy * dy) * inv2s2) * wz;
-                const long long idx = ix + (long long)(((gy % N) + N) % N) * N + zoff;
-                a0 = fmaf(u[idx].x, w, a0);
-                a1 = fmaf(u[NG + idx].x, w, a1);
-                a2 = fmaf(u[2 * NG + idx].x, w, a2);
+#pragma unroll 4
+        for (int oy = oyr; oy < cn[1]; oy += rows) {
+            const float dy = d0y + oy * hf;
+            if (on && fmaf(dy, dy, dxz) <= R2) {
+                const float wgt = expf(-dy * dy * inv2s2) * wz;
+                const float4 q = __ldg(u + zoff + (long long)((lo[1] + oy) & mask) * N);
+                a0 = fmaf(q.x, wgt, a0);
+                a1 = fmaf(q.y, wgt, a1);
+                a2 = fmaf(q.z, wgt, a2);
             }
         }
         acc[0] += a0;
@@ -416,11 +517,17 @@ static void fft3(gdc_fcm* f, int slot, int ncomp, bool inverse) {
     }
 }
 
-static void fcm_average_launch(gdc_fcm* f, int n, const double* r, int slot, double* v) {
+// which = 0: the deterministic velocity, 1: the fluctuating one
+static void fcm_pack(gdc_fcm* f, int slot, int which) {
+    ++f->n_launch, k_fcm_pack<<<ceil_div(f->NG, 256), 256, 0, f->stream>>>(f->NG, f->grid + slot * f->NG,
+                                                                           f->packed + which * f->NG);
+}
+
+static void fcm_average_launch(gdc_fcm* f, int n, const double* r, int which, double* v) {
     const double s2 = f->p.sigma * f->p.sigma;
     const double norm = std::pow(2.0 * 3.141592653589793 * s2, -1.5);
     ++f->n_launch, k_fcm_average<<<ceil_div(32LL * n, 128), 128, 0, f->stream>>>(
-        n, r, f->p.L, f->N, f->h, f->p.R_t, (float)(0.5 / s2), norm * f->h * f->h * f->h, f->grid + slot * f->NG, f->NG, v);
+        n, r, f->p.L, f->N, f->h, f->p.R_t, (float)(0.5 / s2), norm * f->h * f->h * f->h, f->packed + which * f->NG, v);
 }
 
 static const char* fcm_args(const gdc_fcm* f, int n, const void* a, const void* b) {
@@ -479,19 +586,38 @@ gdc_status gdc_fcm_apply(gdc_fcm* f, int n, const double* r, const double* lambd
     const long long nc3 = (long long)f->nc * f->nc * f->nc;
     cudaMemsetAsync(f->cnt, 0, sizeof(int) * nc3, f->stream);
     cudaMemsetAsync(f->fill, 0, sizeof(int) * nc3, f->stream);
-    ++f->n_launch, k_fcm_bin<<<ceil_div(n, 256), 256, 0, f->stream>>>(n, r, f->p.L, f->nc, f->prel, f->cell_of, f->cnt);
+    ++f->n_launch, k_fcm_bin<<<ceil_div(n, 256), 256, 0, f->stream>>>(n, r, f->p.L, f->nc, f->pw, f->cell_of, f->cnt);
     scan_exclusive(f->stream, &f->n_launch, (int)nc3, f->cnt, f->start, f->scan);
     ++f->n_launch, k_fcm_scatter<<<ceil_div(n, 256), 256, 0, f->stream>>>(n, f->cell_of, f->start, f->fill, f->list);
     ++f->n_launch, k_cell_sort<<<ceil_div(nc3, 256), 256, 0, f->stream>>>((int)nc3, f->cnt, f->start, f->list);
     const double s2 = f->p.sigma * f->p.sigma;
-    ++f->n_launch, k_fcm_spread<<<ceil_div(f->NG, 256), 256, 0, f->stream>>>(
-        f->NG, f->N, f->h, f->p.L, f->nc, f->prel, f->cnt, f->start, f->list, lambda, (float)(f->p.R_t * f->p.R_t),
-        (float)(0.5 / s2),
-        (float)std::pow(2.0 * 3.141592653589793 * s2, -1.5), f->grid);
+    {
+        // grid points of the largest binning cell, per thread of a 128-thread block
+        const long long side = (f->N + f->nc - 1) / f->nc + 1;
+        const long long per = (side * side * side + 127) / 128;
+        const float R2 = (float)(f->p.R_t * f->p.R_t), i2 = (float)(0.5 / s2);
+        const float nrm = (float)std::pow(2.0 * 3.141592653589793 * s2, -1.5);
+#define GDC_FCM_SPREAD(PT)                                                                                          \
+    ++f->n_launch, k_fcm_spread<PT><<<(unsigned)nc3, 128, 0, f->stream>>>(f->N, f->h, f->p.L, f->nc, f->pw, f->cnt, \
+                                                                         f->start, f->list, lambda, R2, i2, nrm,    \
+                                                                         f->grid, f->NG)
+        if (per <= 1)
+            GDC_FCM_SPREAD(1);
+        else if (per <= 2)
+            GDC_FCM_SPREAD(2);
+        else if (per <= 4)
+            GDC_FCM_SPREAD(4);
+        else if (per <= 8)
+            GDC_FCM_SPREAD(8);
+        else
+            GDC_FCM_SPREAD(16);
+#undef GDC_FCM_SPREAD
+    }
     fft3(f, 0, 3, false);
     ++f->n_launch, k_fcm_solve<<<ceil_div(f->NG, 256), 256, 0, f->stream>>>(
         f->NG, f->N, (float)(2.0 * 3.141592653589793 / f->p.L), (float)(1.0 / ((double)f->NG * f->p.eta)), f->grid);
     fft3(f, 0, 3, true);
+    fcm_pack(f, 0, 0);
     fcm_average_launch(f, n, r, 0, u);
     gdc_status st = fcm_check(f, cudaGetLastError(), "FCM launch");
     if (st == GDC_OK) st = fcm_check(f, cudaStreamSynchronize(f->stream), "FCM product");
@@ -506,15 +632,16 @@ gdc_status gdc_fcm_brownian(gdc_fcm* f, unsigned long long seed, unsigned int ow
         return fcm_fail(f, GDC_ERR_INVALID_ARG, "kT must be >= 0 and dt > 0");
     const double dv = f->h * f->h * f->h;
     const double sd = 2.0 * std::sqrt(kT * f->p.eta / (dv * dt)), so = std::sqrt(2.0 * kT * f->p.eta / (dv * dt));
-    ++f->n_launch, k_fcm_stress<<<ceil_div(f->NG, 256), 256, 0, f->stream>>>(f->NG, seed, owner, step, sd, so,
-                                                                             f->grid + 3 * f->NG);
+    ++f->n_launch, k_fcm_stress<<<ceil_div(f->NG, 256), 256, 0, f->stream>>>(f->NG, seed, owner, step, (float)sd,
+                                                                             (float)so, f->grid + 3 * f->NG);
     fft3(f, 3, 6, false);
     ++f->n_launch, k_fcm_solve_stress<<<ceil_div(f->NG, 256), 256, 0, f->stream>>>(
         f->NG, f->N, (float)(2.0 * 3.141592653589793 / f->p.L), (float)(1.0 / ((double)f->NG * f->p.eta)),
         f->grid + 3 * f->NG);
     fft3(f, 6, 3, true);
+    fcm_pack(f, 6, 1);
     f->have_field = true;
-    fcm_average_launch(f, n, r, 6, v);
+    fcm_average_launch(f, n, r, 1, v);
     gdc_status st = fcm_check(f, cudaGetLastError(), "FCM launch");
     if (st == GDC_OK) st = fcm_check(f, cudaStreamSynchronize(f->stream), "FCM Brownian velocity");
     return st;
@@ -524,7 +651,7 @@ gdc_status gdc_fcm_average(gdc_fcm* f, int n, const double* r, double* v) {
     if (!f) return GDC_ERR_INVALID_ARG;
     if (const char* m = fcm_args(f, n, r, v)) return fcm_fail(f, GDC_ERR_INVALID_ARG, m);
     if (!f->have_field) return fcm_fail(f, GDC_ERR_INVALID_ARG, "no fluctuating field yet: call gdc_fcm_brownian first");
-    fcm_average_launch(f, n, r, 6, v);
+    fcm_average_launch(f, n, r, 1, v);
     gdc_status st = fcm_check(f, cudaGetLastError(), "FCM launch");
     if (st == GDC_OK) st = fcm_check(f, cudaStreamSynchronize(f->stream), "FCM average");
     return st;

@@ -31,4 +31,17 @@ __device__ inline double normal_from(uint4 x, int comp) {
     return comp == 0 ? rad * cos(ang) : rad * sin(ang);
 }
 
+// The two normals of a Philox output in FP32: the same uniforms as normal_from, with 1 - u
+// formed from the integer words so that it never rounds to zero (no log(0)).
+__device__ inline void normals_f32(uint4 x, float& n0, float& n1) {
+    const float om = (float)((1u << 27) - 1u - (x.x >> 5)) * 7.450580596923828125e-9f +
+                     (float)((1u << 26) - (x.y >> 6)) * 1.1102230246251565404e-16f;
+    const float v = (float)(x.z >> 5) * 7.450580596923828125e-9f + (float)(x.w >> 6) * 1.1102230246251565404e-16f;
+    const float rad = sqrtf(-2.f * logf(om));
+    float s, c;
+    sincospif(2.f * v, &s, &c);
+    n0 = rad * c;
+    n1 = rad * s;
+}
+
 }  // namespace gdc
