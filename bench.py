@@ -261,6 +261,39 @@ def per_suspension_steps(g, torch, wl, common, rank):
                     "timed step); value = 1 / (sum of the timed steps)"}
 
 
+def fcm_measure(g, torch, wl, ctx, N: int, reps: int = 3) -> dict:
+    """The fluctuating-FCM operators (Sec. 4.2) on the same blobs in a periodic cube of the
+    workload's box side: sigma = a/sqrt(pi), envelopes cut at 3a (Sec. 6.1), N^3 grid."""
+    import numpy as np
+    r = ctx.blob_positions().reshape(-1, 3).contiguous()
+    n = r.shape[0]
+    L, a = float(wl.box[0]), float(wl.params["a"])
+    F = g.Fcm(N, L, a / np.sqrt(np.pi), 3.0 * a, eta=float(wl.params["eta"]), max_blobs=n, stream=ctx.stream)
+    lam = torch.as_tensor(np.random.default_rng(0).standard_normal((n, 3)), device=r.device)
+    out = {"grid": N, "L": L, "sigma": a / np.sqrt(np.pi), "R_t": 3.0 * a, "sigma_over_h": a / np.sqrt(np.pi) / (L / N),
+           "n_blobs": n, "dtype": "f32 grid, f64 positions and results", "reps": reps}
+    F.brownian(r, 1, 0, 0, 1.0, 0.01)
+    for name, fn in (("apply_ms", lambda k: F.apply(r, lam)), ("brownian_ms", lambda k: F.brownian(r, 1, 0, k, 1.0, 0.01)),
+                     ("average_ms", lambda k: F.average(r))):
+        fn(0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        for k in range(reps):
+            fn(k + 1)
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        out[name] = e0.elapsed_time(e1) / reps
+    out["grid_points_per_s_apply"] = N ** 3 / (out["apply_ms"] / 1e3)
+    out["note"] = ("M_FCM lambda, v-breve = J L^-1 D W (stress draw + 6 forward and 3 inverse 3-D FFTs) and the "
+                   "re-averaging J u-breve at the same positions; CUDA events on the library stream, each call "
+                   "ending with a synchronisation; the grids (14 GB at 512^3) exceed L2")
+    F.close()
+    del F
+    torch.cuda.empty_cache()
+    return out
+
+
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -273,6 +306,8 @@ def main(argv=None) -> int:
     ap.add_argument("--ref-bodies", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="c3_65k", choices=["c3_65k", "c4", "c5"])
+    ap.add_argument("--fcm-n", type=int, default=512,
+                    help="grid points per side of the fluctuating-FCM measurement (0 = skip it)")
     args = ap.parse_args(argv)
     world, rank, local = _dist()
     if args.impl == "reference":
@@ -418,6 +453,10 @@ def main(argv=None) -> int:
     nbytes = 7 * 8 * wl.n_bodies
     line["e2e"] = {"value": args.e2e_steps / t_e2e, "unit": "steps/s", "h2d_bytes_per_step": nbytes,
                    "d2h_bytes_per_step": nbytes, "steps": args.e2e_steps}
+
+    # the fluctuating-FCM operators on the same blobs (a second way to apply M, Sec. 4.2)
+    if rank == 0 and world == 1 and args.fcm_n and args.workload == "c3_65k":
+        line["fcm"] = fcm_measure(g, torch, wl, ctx, args.fcm_n)
 
     # the plain FP64 path on the same workload
     if args.fp64_steps > 0:

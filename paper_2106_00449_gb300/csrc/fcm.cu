@@ -53,7 +53,7 @@ struct gdc_fcm {
 
 namespace gdc {
 
-constexpr int FFT_P = 16;     // pencils per FFT block
+constexpr int FFT_P = 16;     // pencils per FFT block (the index arithmetic below assumes 16)
 
 static int fcm_cells(const gdc_fcm_params& p) {
     return (int)std::min(128.0, std::max(2.0, std::floor(p.L / p.R_t)));
@@ -298,10 +298,10 @@ __global__ void __launch_bounds__(256) k_fft(float2* __restrict__ data, long lon
         if (INV) w.y = -w.y;
         tw[j] = w;
     }
-    const int total = FFT_P * N;
+    const int total = FFT_P * N, nmask = N - 1;   // N and FFT_P are powers of two: shifts and masks
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
-        const int t = axis == 0 ? e % N : e / FFT_P;
-        const int p = axis == 0 ? e / N : e % FFT_P;
+        const int t = axis == 0 ? (e & nmask) : (e >> 4);
+        const int p = axis == 0 ? (e >> logN) : (e & (FFT_P - 1));
         sm[p * S + fft_pad((int)(__brev((unsigned)t) >> (32 - logN)))] = base[off + p * sp + t * st];
     }
     // log2 N radix-2 stages, fused three at a time: a thread loads the 8 elements
@@ -309,11 +309,11 @@ __global__ void __launch_bounds__(256) k_fft(float2* __restrict__ data, long lon
     // (the same butterflies, in the same arithmetic, as stage-by-stage), and stores them back.
     const int first = logN % 3 == 0 ? 3 : logN % 3;
     for (int s0 = 0, ns = first; s0 < logN; s0 += ns, ns = 3) {
-        const int h = 1 << s0, span = h << ns, per = N >> ns;   // groups x offsets per pencil
+        const int h = 1 << s0, lper = logN - ns;   // 2^lper groups x offsets per pencil
         __syncthreads();
-        for (int q = threadIdx.x; q < FFT_P * per; q += blockDim.x) {
-            const int p = q / per, r = q % per;
-            const int k = r % h, base0 = (r / h) * span + k;
+        for (int q = threadIdx.x; q < (FFT_P << lper); q += blockDim.x) {
+            const int p = q >> lper, r = q & ((1 << lper) - 1);
+            const int k = r & (h - 1), base0 = ((r >> s0) << (s0 + ns)) + k;
             float2* row = sm + p * S;
             float2 x[8];
 #pragma unroll
@@ -322,12 +322,12 @@ __global__ void __launch_bounds__(256) k_fft(float2* __restrict__ data, long lon
 #pragma unroll
             for (int st = 0; st < 3; ++st) {
                 if (st < ns) {
-                    const int hs = h << st, tstep = N / (2 * hs);
+                    const int lstep = logN - 1 - s0 - st;   // twiddle stride N / (2 h 2^st)
 #pragma unroll
                     for (int m = 0; m < 8; ++m) {
                         if (m < (1 << ns) && ((m >> st) & 1) == 0) {
                             const int m2 = m + (1 << st);
-                            const float2 w = tw[(k + (m & ((1 << st) - 1)) * h) * tstep];
+                            const float2 w = tw[(k + ((m & ((1 << st) - 1)) << s0)) << lstep];
                             const float2 x0 = x[m], x1 = x[m2];
                             const float2 t = make_float2(w.x * x1.x - w.y * x1.y, w.x * x1.y + w.y * x1.x);
                             x[m] = make_float2(x0.x + t.x, x0.y + t.y);
@@ -343,8 +343,8 @@ __global__ void __launch_bounds__(256) k_fft(float2* __restrict__ data, long lon
     }
     __syncthreads();
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
-        const int t = axis == 0 ? e % N : e / FFT_P;
-        const int p = axis == 0 ? e / N : e % FFT_P;
+        const int t = axis == 0 ? (e & nmask) : (e >> 4);
+        const int p = axis == 0 ? (e >> logN) : (e & (FFT_P - 1));
         base[off + p * sp + t * st] = sm[p * S + fft_pad(t)];
     }
 }
