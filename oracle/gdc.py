@@ -86,20 +86,24 @@ def perturbed_state(layout, Y, q, dY: np.ndarray, du: np.ndarray):
     return Yp, qp
 
 
-def rfd_divergence(layout, Y, q, W, Wt, calV, p: Params) -> float:
-    """Step 3(b): one-sample random finite difference of div(calV) (Eq. rfd_div and its footnote)."""
+def rfd_divergence(layout, Y, q, W, Wt, calV, p: Params, project=None) -> float:
+    """Step 3(b): one-sample random finite difference of div(calV) (Eq. rfd_div and its footnote).
+
+    project(Y, q) gives calV at another state (default: step 2 with the RPY slip of W)."""
+    project = project or (lambda Ys, qs: projected_velocity(layout, Ys, qs, W, p))
     d = p.rfd_delta
     L = _lengths(layout, p.a)
     Wt = Wt.reshape(-1, 6)
     Yt, qt = perturbed_state(layout, Y, q, d * L[:, None] * Wt[:, :3], d * Wt[:, 3:])
-    calVt = projected_velocity(layout, Yt, qt, W, p)
+    calVt = project(Yt, qt)
     dV = calVt - calV
     return float(((Wt[:, :3] * dV[:, :3]).sum(axis=1) / (d * L)).sum()
                  + (Wt[:, 3:] * dV[:, 3:]).sum() / d)
 
 
-def fd_divergence(layout, Y, q, W, calV, p: Params) -> float:
+def fd_divergence(layout, Y, q, W, calV, p: Params, project=None) -> float:
     """Step 3(a): one-sided finite differences over every body coordinate (Eq. FD)."""
+    project = project or (lambda Ys, qs: projected_velocity(layout, Ys, qs, W, p))
     d = p.rfd_delta
     L = _lengths(layout, p.a)
     total = 0.0
@@ -111,7 +115,7 @@ def fd_divergence(layout, Y, q, W, calV, p: Params) -> float:
                 dY[k, c] = d * L[k]
             else:
                 du[k, c - 3] = d
-            Vp = projected_velocity(layout, *perturbed_state(layout, Y, q, dY, du), W, p)
+            Vp = project(*perturbed_state(layout, Y, q, dY, du))
             total += (Vp[k, c] - calV[k, c]) / (d * L[k] if c < 3 else d)
     return float(total)
 
@@ -150,6 +154,50 @@ def gdc_step(layout, Y, q, W, Wt, p: Params, div: str = "rfd") -> dict:
     # step 6
     Y1, q1 = geometry.advance(Y, q, mid["V"], nu * p.dt)
     return dict(r0=r0, vb0=vb0, calV=calV, div=dv, nu=nu, Ym=Ym, qm=qm, Y1=Y1, q1=q1, **mid)
+
+
+def gdc_step_fcm(layout, Y, q, Wt, grid, p: Params, seed: int, susp: int, step: int, div: str = "rfd") -> dict:
+    """One gDC step with the fluctuating FCM of Sec. 4.2 in a periodic cube (oracle.fcm.Grid).
+
+    The Brownian slip is v-breve = J L^-1 D W (already in the velocity form): the stress of
+    (seed, susp, step) gives one fluctuating field u-breve per step, averaged at x^n, at the
+    perturbed states of step 3 and at the mid-step x^m -- the same W throughout, and the
+    re-averaging Sec. 5 describes.  The mobility solve of step 5 uses the dense M_FCM at x^m.
+    Forces are left out (pair forces in a periodic cube are not part of this path)."""
+    from . import fcm
+    r0 = geometry.blob_positions(layout, Y, q)
+    vb0, ufield = fcm.brownian_velocity(grid, r0, seed, susp, step, p.kT, p.dt)
+    vb0 = vb0.reshape(-1)
+
+    def project(Ys, qs):
+        rs = geometry.blob_positions(layout, Ys, qs)
+        Ks = rigid.k_matrix(rs, Ys, layout.blob_body)
+        return rigid.lsq_velocity(Ks, rigid.rigid_basis(Ks, layout.n_bodies),
+                                  fcm.average(grid, rs, ufield).reshape(-1)).reshape(-1, 6)
+
+    calV = project(Y, q)
+    if div == "rfd":
+        dv = rfd_divergence(layout, Y, q, None, Wt, calV, p, project)
+    elif div == "fd":
+        dv = fd_divergence(layout, Y, q, None, calV, p, project)
+    else:
+        raise ValueError(div)
+    nu = 1.0 + 0.5 * p.dt * dv
+    Ym, qm = geometry.advance(Y, q, calV, 0.5 * p.dt)
+    rm = geometry.blob_positions(layout, Ym, qm)
+    n3 = rm.size
+    M = np.zeros((n3, n3))
+    for c in range(n3):
+        e = np.zeros(n3)
+        e[c] = 1.0
+        M[:, c] = fcm.mobility_apply(grid, rm, e).reshape(-1)
+    K = rigid.k_matrix(rm, Ym, layout.blob_body)
+    B = rigid.rigid_basis(K, layout.n_bodies)
+    vbm = fcm.average(grid, rm, ufield).reshape(-1)
+    lam, V = rigid.saddle_solve(M, K, B, vbm, np.zeros(6 * layout.n_bodies))
+    Y1, q1 = geometry.advance(Y, q, V.reshape(-1, 6), nu * p.dt)
+    return dict(r0=r0, vb0=vb0, calV=calV, div=dv, nu=nu, Ym=Ym, qm=qm, M=M, vb=vbm, lam=lam, V=V.reshape(-1, 6),
+                Y1=Y1, q1=q1)
 
 
 def em_step(layout, Y, q, W, p: Params) -> dict:

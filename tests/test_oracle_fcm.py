@@ -115,3 +115,36 @@ def test_envelopes_equal_a_search_of_every_grid_point():
         np.testing.assert_array_equal(idx[order], want)
         ref = (2 * np.pi * g.sigma ** 2) ** -1.5 * np.exp(-d2[want] / (2 * g.sigma ** 2))
         np.testing.assert_allclose(w[order], ref, rtol=1e-13, atol=0)
+
+
+def test_fcm_step_divergence_rfd_is_unbiased_for_fd():
+    """Step 3 with FCM re-averages one fluctuating field at perturbed states (Sec. 5): the
+    random finite difference (Eq. rfd_div) at the unit vectors sums to the finite difference
+    over every body coordinate (Eq. FD) of the same field, and over random W-tilde it is
+    unbiased for it."""
+    from oracle import geometry as G, rigid
+    from oracle.gdc import Params, fd_divergence, rfd_divergence
+    from synthetic import shapes
+    grid = fcm.Grid(32, 10.0, SIGMA, R_t=3.0)
+    lay = G.Layout([shapes.icosahedron()], np.array([0]))
+    rng = np.random.default_rng(7)
+    Y = np.array([[4.0, 5.0, 5.0]])
+    g = rng.standard_normal((1, 4))
+    q = g / np.linalg.norm(g, axis=1, keepdims=True)
+    p = Params(dt=0.01, kT=1.0, rfd_delta=1e-4)
+    _, ufield = fcm.brownian_velocity(grid, G.blob_positions(lay, Y, q), seed=5, susp=0, step=0, kT=1.0, dt=0.01)
+
+    def project(Ys, qs):
+        rs = G.blob_positions(lay, Ys, qs)
+        Ks = rigid.k_matrix(rs, Ys, lay.blob_body)
+        return rigid.lsq_velocity(Ks, rigid.rigid_basis(Ks, lay.n_bodies),
+                                  fcm.average(grid, rs, ufield).reshape(-1)).reshape(-1, 6)
+
+    calV = project(Y, q)
+    fd = fd_divergence(lay, Y, q, None, calV, p, project)
+    unit = sum(rfd_divergence(lay, Y, q, None, np.eye(6)[i], calV, p, project) for i in range(6))
+    assert abs(unit - fd) < 1e-10 * abs(fd), (unit, fd)
+    samples = np.array([rfd_divergence(lay, Y, q, None, rng.standard_normal(6), calV, p, project) for _ in range(2000)])
+    se = samples.std() / np.sqrt(samples.size)
+    assert abs(fd) > 5 * se, "the divergence must be resolvable for the test to have power"
+    assert abs(samples.mean() - fd) < 4 * se, (samples.mean(), fd, se)
