@@ -67,6 +67,15 @@ typedef enum { GDC_DIV_RFD = 0, GDC_DIV_FD = 1 } gdc_divmode;
 /* Time integrator: the gDC of Sec. 3, or Euler-Maruyama of App. D (no drift). */
 typedef enum { GDC_SCHEME_GDC = 0, GDC_SCHEME_EM = 1 } gdc_scheme;
 
+/* Mobility of the blobs: the unbounded RPY tensor (Sec. 4.1), or the fluctuating FCM of
+ * Sec. 4.2 in a periodic cube (one suspension, no pair forces).  With FCM the Brownian
+ * slip of a step is J u-breve for one fluctuating field u-breve = L^-1 D W drawn at the
+ * step's start (stress of (seed, 0, step), see gdc_fcm_*) and averaged again at every later
+ * configuration of the step -- the perturbed states of step 3 and the mid-step (Sec. 5);
+ * the RPY-only settings (Lanczos tolerances, pair kernels) are not used, all products use
+ * the FP32-grid FCM operator whatever the precision, and steps run host-driven. */
+typedef enum { GDC_MOB_RPY = 0, GDC_MOB_FCM = 1 } gdc_mobility;
+
 /* Pair potential between blobs of different bodies (the forces F^m of Sec. 3 step 4):
  * the soft sphere U of Eq. soft_sphere_potential alone, or with the Gaussian wells
  * phi_c(r) = A_w exp(-((r - c)/lambda)^2) of Sec. 6.4: U_1 = U - phi_3a (repel-attract)
@@ -120,6 +129,11 @@ typedef struct {
                               closer than the cutoff (36 b past 2a for the soft sphere,
                               6 lambda past the outer well centre), each blob's terms in
                               a fixed order: results are deterministic.                 */
+    int    mobility;       /* gdc_mobility                                             */
+    double box_L;          /* GDC_MOB_FCM: side of the periodic cube                   */
+    int    fcm_N;          /* GDC_MOB_FCM: grid points per side (power of two, 16..512)  */
+    double fcm_sigma;      /* GDC_MOB_FCM: envelope width; 0 = a / sqrt(pi)             */
+    double fcm_R_t;        /* GDC_MOB_FCM: envelope truncation radius; 0 = 3a          */
 } gdc_params;
 
 typedef struct {

@@ -29,6 +29,8 @@ POT_REPEL_ATTRACT_REPEL = 2
 FORCES_CHOOSE = 0
 FORCES_ALL_PAIRS = 1
 FORCES_CELL_LIST = 2
+MOB_RPY = 0
+MOB_FCM = 1
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "NOT_CONVERGED", 4: "NONFINITE", 5: "TIMEOUT", 6: "WORKSPACE"}
 
@@ -60,7 +62,9 @@ class _Params(ctypes.Structure):
                 ("rep_A", ctypes.c_double), ("rep_b", ctypes.c_double), ("shear_rate", ctypes.c_double),
                 ("seed", ctypes.c_ulonglong), ("autotune", ctypes.c_int), ("graph", ctypes.c_int),
                 ("pair_kernel", ctypes.c_int), ("potential", ctypes.c_int), ("well_A", ctypes.c_double),
-                ("well_lambda", ctypes.c_double), ("force_method", ctypes.c_int)]
+                ("well_lambda", ctypes.c_double), ("force_method", ctypes.c_int), ("mobility", ctypes.c_int),
+                ("box_L", ctypes.c_double), ("fcm_N", ctypes.c_int), ("fcm_sigma", ctypes.c_double),
+                ("fcm_R_t", ctypes.c_double)]
 
 
 class _FcmParams(ctypes.Structure):
@@ -120,6 +124,11 @@ class Params:
     well_A: float = 0.0
     well_lambda: float = 0.5
     force_method: int = 0
+    mobility: int = 0        # 0 unbounded RPY, 1 fluctuating FCM in a periodic cube
+    box_L: float = 0.0
+    fcm_N: int = 0
+    fcm_sigma: float = 0.0   # 0: a / sqrt(pi)
+    fcm_R_t: float = 0.0     # 0: 3a
 
     def _c(self) -> _Params:
         return _Params(**{f.name: getattr(self, f.name) for f in dataclasses.fields(self)})

@@ -77,6 +77,15 @@ static const char* validate_params(const gdc_params* p) {
         return "well_lambda must be > 0 when the wells are on";
     if (p->force_method < 0 || p->force_method > 2)
         return "force_method must be 0 (choose), 1 (all pairs) or 2 (cell list)";
+    if (p->mobility != GDC_MOB_RPY && p->mobility != GDC_MOB_FCM) return "mobility must be 0 (RPY) or 1 (FCM)";
+    if (p->mobility == GDC_MOB_FCM) {
+        const gdc_fcm_params fp = fcm_params_of(*p, 1);
+        if (gdc_fcm_workspace_bytes(&fp) == 0)
+            return "FCM needs box_L > 0 and a valid grid: fcm_N a power of two in [16, 512], 0 < R_t < box_L/2, "
+                   "R_t within 15 grid spacings";
+        if (p->rep_A > 0.0 || (p->potential > 0 && p->well_A > 0.0))
+            return "pair forces are not available with the periodic FCM mobility";
+    }
     return nullptr;
 }
 
@@ -87,6 +96,7 @@ static const char* build_host_layout(gdc_ctx* c, const gdc_params* p, int n_temp
     if (n_templates < 1 || !tmpl_nblobs) return "need at least one template";
     if (n_susp < 1 || !susp_body_off) return "need at least one suspension";
     if (susp_body_off[0] != 0) return "susp_body_off[0] must be 0";
+    if (p->mobility == GDC_MOB_FCM && n_susp != 1) return "the FCM mobility takes one suspension";
     for (int s = 0; s < n_susp; ++s)
         if (susp_body_off[s + 1] < susp_body_off[s]) return "susp_body_off must be non-decreasing";
     const long long NB = susp_body_off[n_susp];
@@ -211,6 +221,12 @@ static size_t carve(gdc_ctx* c, void* base) {
     c->nu = w.take<double>(S);
     c->divp = w.take<double>(S);
     c->fblob = w.take<double>(3 * NBL);
+    if (c->p.mobility == GDC_MOB_FCM) {
+        const gdc_fcm_params fp = fcm_params_of(c->p, NBL);
+        c->fcm_ws_bytes = gdc_fcm_workspace_bytes(&fp);
+        c->fcm_u = w.take<double>(3 * NBL);
+        c->fcm_ws = (void*)w.take<char>((long long)c->fcm_ws_bytes);
+    }
     c->cell_H = cell_buckets(NBL);
     c->cell_xyz = w.take<int4>(NBL);
     c->cell_key = w.take<unsigned>(NBL);
@@ -378,13 +394,26 @@ static gdc_status forces_at_loaded(gdc_ctx* c, double* FT) {
     return GDC_OK;
 }
 
-// v-breve = sqrt(2 kT / dt) M^(1/2) W at the loaded configuration
+// v-breve = sqrt(2 kT / dt) M^(1/2) W at the loaded configuration.  FCM: the step's
+// fluctuating field is drawn at the step's first slip and averaged again at later ones.
 static gdc_status slip_at_loaded(gdc_ctx* c, const double* W, double* vb, int fixed, int* iters, double* err) {
     const double scale = std::sqrt(2.0 * c->p.kT / c->p.dt);
     if (c->p.kT == 0.0) {
         if (iters) *iters = 0;
         if (err) *err = 0.0;
         return cuda_check(c, cudaMemsetAsync(vb, 0, sizeof(double) * 3 * c->NBL, c->stream), "memset");
+    }
+    if (c->fcm) {
+        if (iters) *iters = 0;
+        if (err) *err = 0.0;
+        gdc_status st;
+        if (c->fcm_field_step != c->step) {
+            st = gdc_fcm_brownian(c->fcm, c->p.seed, 0u, c->step, c->p.kT, c->p.dt, (int)c->NBL, c->r, vb);
+            if (st == GDC_OK) c->fcm_field_step = c->step;
+        } else {
+            st = gdc_fcm_average(c->fcm, (int)c->NBL, c->r, vb);
+        }
+        return st == GDC_OK ? st : fail(c, st, std::string("FCM: ") + gdc_fcm_last_error(c->fcm));
     }
     return lanczos_sqrt(c, W, vb, scale, fixed, iters, err);
 }
@@ -536,7 +565,7 @@ __global__ void __launch_bounds__(32) k_step_finish(int S, const double* __restr
 }
 
 static bool graph_usable(const gdc_ctx* c) {
-    return c->p.graph && !c->prof_on && (c->p.scheme == GDC_SCHEME_EM || c->p.divmode == GDC_DIV_RFD);
+    return c->p.graph && !c->prof_on && !c->fcm && (c->p.scheme == GDC_SCHEME_EM || c->p.divmode == GDC_DIV_RFD);
 }
 
 static void drop_graph(gdc_ctx* c) {
@@ -778,6 +807,11 @@ gdc_status gdc_init(gdc_ctx** out, const gdc_params* params, int n_templates, co
     if ((st = cuda_check(c, cudaGetLastError(), "template setup")) != GDC_OK) return st;
     if ((st = read_status(c)) != GDC_OK) return st;
     if ((st = sym_init_attributes(c)) != GDC_OK) return st;
+    if (c->p.mobility == GDC_MOB_FCM) {
+        const gdc_fcm_params fp = fcm_params_of(c->p, c->NBL);
+        if ((st = gdc_fcm_init(&c->fcm, &fp, c->fcm_ws, c->fcm_ws_bytes, c->stream)) != GDC_OK)
+            return fail(c, st, "FCM context setup failed");
+    }
     if (c->p.autotune) {
         load_at(c, c->Y, c->q);
         if ((st = autotune_pair_kernel(c)) != GDC_OK) return st;
@@ -790,6 +824,7 @@ gdc_status gdc_init(gdc_ctx** out, const gdc_params* params, int n_templates, co
 void gdc_destroy(gdc_ctx* c) {
     if (!c) return;
     drop_graph(c);
+    gdc_fcm_destroy(c->fcm);
     for (cudaStream_t s : c->cap_stream)
         if (s) cudaStreamDestroy(s);
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
@@ -854,6 +889,9 @@ gdc_status gdc_set_params(gdc_ctx* c, const gdc_params* p) {
         return fail(c, GDC_ERR_INVALID_ARG, "gmres_restart and lanczos_max_iter are fixed at init");
     if (p->a != c->p.a || p->eta != c->p.eta)
         return fail(c, GDC_ERR_INVALID_ARG, "a and eta are fixed at init (they shape the preconditioner)");
+    if (p->mobility != c->p.mobility || p->box_L != c->p.box_L || p->fcm_N != c->p.fcm_N ||
+        p->fcm_sigma != c->p.fcm_sigma || p->fcm_R_t != c->p.fcm_R_t)
+        return fail(c, GDC_ERR_INVALID_ARG, "the mobility and its FCM grid are fixed at init");
     const unsigned long long seed = c->p.seed;
     const int pair_kernel = c->p.pair_kernel;
     c->p = *p;

@@ -126,6 +126,12 @@ struct gdc_ctx {
     double *tmpl_xyz = 0, *tmpl_L = 0;
     double *tmpl_Minv = 0, *tmpl_G = 0, *tmpl_N = 0, *tmpl_KtKp = 0, *tmpl_work = 0, *tmpl_M = 0;
     float* tmpl_M32 = 0;          // tmpl_M rounded to FP32 (intra-body block of the FP32 products)
+    // fluctuating FCM mobility (fcm.cu), GDC_MOB_FCM only
+    gdc_fcm* fcm = nullptr;
+    double* fcm_u = nullptr;      // M_FCM lambda, 3 per blob
+    void* fcm_ws = nullptr;
+    size_t fcm_ws_bytes = 0;
+    unsigned long long fcm_field_step = ~0ULL;   // step whose fluctuating field the grid holds
     // cell list of the pair forces (cells.cu)
     long long cell_H = 0;         // buckets: a power of two >= 2 NBL
     int4* cell_xyz = 0;           // per blob: cell coordinates and suspension
@@ -319,6 +325,8 @@ void launch_rpy_epilogue(gdc_ctx* c, int prec, const double* x, double* y, int g
 void launch_forces_pair(gdc_ctx* c, int prec, double* fblob);
 void launch_forces_cell(gdc_ctx* c, int prec, double* fblob);
 void launch_near_cell(gdc_ctx* c);   // near-pair lists from a cell list (cells.cu)
+gdc_fcm_params fcm_params_of(const gdc_params& p, long long n_blobs);
+void launch_fcm_saddle_rows(gdc_ctx* c, const double* x, double* y);
 void launch_forces(gdc_ctx* c, int prec, double* fblob);   // cell list or all pairs (force_method)
 bool forces_use_cells(const gdc_ctx* c);   // pair searches (forces, near pairs) on a cell list
 long long cell_buckets(long long NBL);

@@ -530,6 +530,18 @@ static void fcm_average_launch(gdc_fcm* f, int n, const double* r, int which, do
         n, r, f->p.L, f->N, f->h, f->p.R_t, (float)(0.5 / s2), norm * f->h * f->h * f->h, f->packed + which * f->NG, v);
 }
 
+// The grid of a gDC context with the FCM mobility (defaults: sigma = a/sqrt(pi), R_t = 3a).
+gdc_fcm_params fcm_params_of(const gdc_params& p, long long n_blobs) {
+    gdc_fcm_params f{};
+    f.N = p.fcm_N;
+    f.L = p.box_L;
+    f.sigma = p.fcm_sigma > 0.0 ? p.fcm_sigma : p.a / std::sqrt(3.141592653589793);
+    f.R_t = p.fcm_R_t > 0.0 ? p.fcm_R_t : 3.0 * p.a;
+    f.eta = p.eta;
+    f.max_blobs = (int)std::max(1LL, n_blobs);
+    return f;
+}
+
 static const char* fcm_args(const gdc_fcm* f, int n, const void* a, const void* b) {
     if (!a || !b) return "NULL pointer";
     if (n < 1 || n > f->p.max_blobs) return "n_blobs must be in [1, max_blobs]";

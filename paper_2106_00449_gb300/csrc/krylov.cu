@@ -234,6 +234,10 @@ __global__ void k_fill(int S, double v, double* __restrict__ o) {
 // ---- operators ---------------------------------------------------------------------
 
 gdc_status rpy_op(gdc_ctx* c, int prec, const double* lam, double* u) {
+    if (c->fcm) {   // the periodic FCM mobility (one suspension, lambda and u 3 per blob)
+        const gdc_status st = gdc_fcm_apply(c->fcm, (int)c->NBL, c->r, lam, u);
+        return st == GDC_OK ? st : fail(c, st, std::string("FCM: ") + gdc_fcm_last_error(c->fcm));
+    }
     launch_pack_lambda(c, prec, lam, 0);
     launch_rpy(c, prec);
     launch_rpy_epilogue(c, prec, lam, u, 0);
@@ -241,6 +245,13 @@ gdc_status rpy_op(gdc_ctx* c, int prec, const double* lam, double* u) {
 }
 
 gdc_status saddle_op(gdc_ctx* c, int prec, const double* x, double* y) {
+    if (c->fcm) {   // one suspension: lambda is the first 3 N_b entries of the saddle vector
+        const gdc_status st = gdc_fcm_apply(c->fcm, (int)c->NBL, c->r, x, c->fcm_u);
+        if (st != GDC_OK) return fail(c, st, std::string("FCM: ") + gdc_fcm_last_error(c->fcm));
+        launch_fcm_saddle_rows(c, x, y);
+        launch_body_KT(c, x, 1, y, 1, -1.0);
+        return GDC_OK;
+    }
     launch_pack_lambda(c, prec, x, 1);
     launch_rpy(c, prec);
     launch_rpy_epilogue(c, prec, x, y, 1);

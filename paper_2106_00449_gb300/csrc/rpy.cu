@@ -611,6 +611,28 @@ __global__ void k_rpy_epilogue(int NBL, const P* __restrict__ part, const int* _
     y[o + 2] = uz - kz;
 }
 
+// Blob rows of the saddle operator with the FCM mobility: y_i = (M_FCM lambda)_i - (K V)_i,
+// K V = U_p + Omega_p x (r_i - Y_p) (Eq. rigid_body_cond), u = M_FCM lambda given 3 per blob.
+__global__ void k_fcm_saddle_rows(int NBL, const double* __restrict__ u, const double* __restrict__ x,
+                                  double* __restrict__ y, const int* __restrict__ blob_gm, const int* __restrict__ body_gm,
+                                  const int* __restrict__ blob_body, const double* __restrict__ r,
+                                  const double* __restrict__ Yc) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= NBL) return;
+    const int p = blob_body[i];
+    const double* V = x + body_gm[p];
+    const double dx = r[3 * i] - Yc[3 * p], dy = r[3 * i + 1] - Yc[3 * p + 1], dz = r[3 * i + 2] - Yc[3 * p + 2];
+    const long long o = blob_gm[i];
+    y[o] = u[3LL * i] - (V[0] + (V[4] * dz - V[5] * dy));
+    y[o + 1] = u[3LL * i + 1] - (V[1] + (V[5] * dx - V[3] * dz));
+    y[o + 2] = u[3LL * i + 2] - (V[2] + (V[3] * dy - V[4] * dx));
+}
+
+void launch_fcm_saddle_rows(gdc_ctx* c, const double* x, double* y) {
+    ++c->n_launch, k_fcm_saddle_rows<<<ceil_div(c->NBL, 256), 256, 0, c->stream>>>(
+        c->NBL, c->fcm_u, x, y, c->blob_gm, c->body_gm, c->blob_body, c->r, c->Yc);
+}
+
 static void launch_epilogue(gdc_ctx* c, int prec, double c0, const double* x, double* y, int gm_layout,
                             bool near) {
     const bool sym = prec == GDC_FP32_MIXED && near && c->use_sym;   // RPY products only, not forces

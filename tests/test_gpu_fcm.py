@@ -76,3 +76,44 @@ def test_fcm_rejects_bad_input(lib):
     before = F.launches
     F.apply(np.ones((3, 3)), np.ones((3, 3)))
     assert F.launches > before
+
+
+# ---- the gDC step with the FCM mobility (Sec. 3 with Sec. 4.2, periodic cube) ----------
+
+def _fcm_case(lib, div, graph=0, oracle=True):
+    from oracle import gdc as ogdc, philox
+    from synthetic import workloads as WL
+    from gpu_common import oracle_params, rot_err, susp_layout
+    wl = WL.c1()                       # four icosahedra, 48 blobs, no pair forces
+    L, N, seed = 20.0, 64, 77          # sigma / h = 1.80
+    ctx = lib.context_from_workload(wl, precision=0, mobility=1, box_L=L, fcm_N=N, seed=seed, rfd_delta=1e-3,
+                                    gmres_tol=1e-7, gmres_max_iter=1000, divmode=div, graph=graph)
+    tr = ctx.set_trace(True)
+    info = ctx.step(1)[0]
+    Y1, q1, _ = ctx.get_state()
+    lay, Y, q = susp_layout(wl, 0)
+    if not oracle:
+        return ctx, tr, info, Y, Y1, q1, None, rot_err
+    Wt = philox.normals(seed, 0, 0, 1, 6 * lay.n_bodies)
+    ora = ogdc.gdc_step_fcm(lay, Y, q, Wt, fcm.Grid(N, L, SIGMA, 3.0), oracle_params(wl, rfd_delta=1e-3), seed, 0, 0,
+                            div="rfd" if div == 0 else "fd")
+    return ctx, tr, info, Y, Y1, q1, ora, rot_err
+
+
+@pytest.mark.parametrize("div", [0, 1])
+def test_fcm_gdc_step_matches_oracle(lib, div):
+    ctx, tr, info, Y, Y1, q1, ora, rot_err = _fcm_case(lib, div)
+    assert info["solve"]["converged"] and info["lanczos_iters"] == [0, 0, 0]
+    assert rel(_host(tr["vb_n"]), ora["vb0"]) < TOL
+    assert rel(_host(tr["calV"]).reshape(-1, 6), ora["calV"]) < TOL
+    assert abs(_host(tr["nu"])[0] - ora["nu"]) < 1e-3
+    assert rel(_host(tr["vb_m"]), ora["vb"]) < TOL          # the same field, averaged at x^m
+    assert rel(Y1 - Y, ora["Y1"] - Y) < 1e-4
+    assert rot_err(q1, ora["q1"]) < 1e-6
+
+
+def test_fcm_step_runs_host_driven_with_graph_requested(lib):
+    a = _fcm_case(lib, 0, graph=1, oracle=False)
+    b = _fcm_case(lib, 0, graph=0, oracle=False)
+    np.testing.assert_array_equal(a[4], b[4])
+    np.testing.assert_array_equal(a[5], b[5])
