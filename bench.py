@@ -285,11 +285,28 @@ def fcm_measure(g, torch, wl, ctx, N: int, reps: int = 3) -> dict:
         torch.cuda.synchronize()
         out[name] = e0.elapsed_time(e1) / reps
     out["grid_points_per_s_apply"] = N ** 3 / (out["apply_ms"] / 1e3)
+    F.close()
+    del F
+    torch.cuda.empty_cache()
+    # one gDC step with the FCM mobility on the same bodies (no pair forces in the periodic cube)
+    fctx = g.context_from_workload(wl, precision=g.FP32_MIXED, rfd_delta=1e-3, gmres_tol=1e-6, gmres_max_iter=500,
+                                   mobility=g.MOB_FCM, box_L=L, fcm_N=N, rep_A=0.0, autotune=0)
+    fctx.step(1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(fctx.stream)
+    inf = fctx.step(1)[0]
+    e1.record(fctx.stream)
+    torch.cuda.synchronize()
+    out["gdc_step"] = {"steps_per_s": 1e3 / e0.elapsed_time(e1), "gmres_iters": inf["solve"]["iterations"],
+                       "residual": inf["solve"]["residual"], "nu": inf["nu_min"],
+                       "note": "one timed step after one warm-up, host-driven (FCM steps are not graph-captured); "
+                               "the soft repulsion is off (pair forces are not periodic)"}
+    fctx.close()
+    del fctx
     out["note"] = ("M_FCM lambda, v-breve = J L^-1 D W (stress draw + 6 forward and 3 inverse 3-D FFTs) and the "
                    "re-averaging J u-breve at the same positions; CUDA events on the library stream, each call "
                    "ending with a synchronisation; the grids (14 GB at 512^3) exceed L2")
-    F.close()
-    del F
     torch.cuda.empty_cache()
     return out
 
