@@ -49,3 +49,49 @@ def test_workspace_rejects_bad_input_without_gpu(libpath):
     assert lib.gdc_workspace_bytes(ctypes.byref(p2), 1, g._np_ptr(n), 1, g._np_ptr(off), g._np_ptr(bt)) == 0
     empty = np.array([0, 0], dtype=np.int64)
     assert lib.gdc_workspace_bytes(ctypes.byref(p), 1, g._np_ptr(n), 1, g._np_ptr(empty), g._np_ptr(bt)) == 0
+
+
+def test_workspace_checks_the_mobility_and_force_options_without_gpu(libpath):
+    import numpy as np
+    import paper_2106_00449_gb300 as g
+    lib = g.load_library()
+    n = np.array([3], dtype=np.int32)
+    off1, bt1 = np.array([0, 2], dtype=np.int64), np.array([0, 0], dtype=np.int32)
+    off2, bt2 = np.array([0, 1, 2], dtype=np.int64), np.array([0, 0], dtype=np.int32)
+
+    def ws(params, off=off1, bt=bt1):
+        c = params._c()
+        return lib.gdc_workspace_bytes(ctypes.byref(c), 1, g._np_ptr(n), len(off) - 1, g._np_ptr(off), g._np_ptr(bt))
+
+    fcm = dict(mobility=g.MOB_FCM, box_L=20.0, fcm_N=64)
+    assert ws(g.Params(**fcm)) > ws(g.Params())                     # the FCM grids live in the workspace
+    assert ws(g.Params(**fcm), off2, bt2) == 0                      # one suspension only
+    assert ws(g.Params(rep_A=4.0, **fcm)) == 0                      # no pair forces in the periodic cube
+    assert ws(g.Params(potential=1, well_A=5.0, **fcm)) == 0
+    assert ws(g.Params(**dict(fcm, fcm_N=48))) == 0                 # not a power of two
+    assert ws(g.Params(**dict(fcm, box_L=5.0))) == 0                # 3a truncation reaches the image
+    assert ws(g.Params(mobility=2)) == 0
+    # pair potentials and the pair search
+    assert ws(g.Params(potential=2, well_A=5.0, well_lambda=0.5, force_method=2)) > 0
+    assert ws(g.Params(potential=3)) == 0
+    assert ws(g.Params(potential=1, well_A=5.0, well_lambda=0.0)) == 0
+    assert ws(g.Params(force_method=3)) == 0
+    assert ws(g.Params(well_A=-1.0)) == 0
+
+
+def test_fcm_workspace_checks_the_grid_without_gpu(libpath):
+    import paper_2106_00449_gb300 as g
+    lib = g.load_library()
+
+    def ws(*a):
+        p = g._FcmParams(*a)
+        return lib.gdc_fcm_workspace_bytes(ctypes.byref(p))
+
+    good = ws(64, 20.0, 0.5642, 3.0, 1.0, 100)
+    assert good > 13 * 64 ** 3 * 8                   # nine complex and two packed grids
+    assert ws(63, 20.0, 0.5642, 3.0, 1.0, 100) == 0
+    assert ws(1024, 20.0, 0.5642, 3.0, 1.0, 100) == 0
+    assert ws(64, 20.0, 0.5642, 10.0, 1.0, 100) == 0    # R_t >= L/2
+    assert ws(512, 20.0, 0.5642, 3.0, 1.0, 100) == 0    # R_t beyond 15 grid spacings (h = L/512)
+    assert ws(64, 20.0, 0.5642, 3.0, 0.0, 100) == 0
+    assert ws(64, 20.0, 0.5642, 3.0, 1.0, 0) == 0
