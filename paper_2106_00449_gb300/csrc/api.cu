@@ -225,6 +225,7 @@ static size_t carve(gdc_ctx* c, void* base) {
         const gdc_fcm_params fp = fcm_params_of(c->p, NBL);
         c->fcm_ws_bytes = gdc_fcm_workspace_bytes(&fp);
         c->fcm_u = w.take<double>(3 * NBL);
+        c->fcm_Mt = w.take<double>(c->h_minv_off[T]);
         c->fcm_ws = (void*)w.take<char>((long long)c->fcm_ws_bytes);
     }
     c->cell_H = cell_buckets(NBL);
@@ -375,6 +376,41 @@ static gdc_status read_status(gdc_ctx* c) {
     if (st[0] == 2) return fail(c, GDC_ERR_NOT_CONVERGED, "tridiagonal eigensolver did not converge");
     if (st[1] != 0) return fail(c, GDC_ERR_TIMEOUT, "a pair-kernel tile copy did not complete in time");
     return GDC_OK;
+}
+
+// FCM mode: each template's block of M_FCM for the template alone at the centre of the
+// periodic cube (3 n_t FCM products on unit vectors), symmetrised (J = S*).  It replaces the
+// RPY template block in the block-diagonal preconditioner; R M_t R^T matches a body's block
+// up to the small anisotropy of its periodic images.
+static gdc_status fcm_template_blocks(gdc_ctx* c) {
+    std::vector<double> M(c->h_minv_off[c->T]);
+    for (int t = 0; t < c->T; ++t) {
+        const int n = c->h_tmpl_n[t], n3 = 3 * n;
+        std::vector<double> r(n3), e(n3, 0.0), u(n3);
+        for (int i = 0; i < n3; ++i) r[i] = 0.5 * c->p.box_L + c->h_tmpl_xyz[3LL * c->h_tmpl_off[t] + i];
+        cudaError_t ce = cudaMemcpyAsync(c->vb_n, r.data(), sizeof(double) * n3, cudaMemcpyHostToDevice, c->stream);
+        if (ce != cudaSuccess) return cuda_check(c, ce, "FCM template blocks");
+        double* Mb = M.data() + c->h_minv_off[t];
+        for (int k = 0; k < n3; ++k) {
+            e[k] = 1.0;
+            ce = cudaMemcpyAsync(c->W, e.data(), sizeof(double) * n3, cudaMemcpyHostToDevice, c->stream);
+            e[k] = 0.0;
+            if (ce != cudaSuccess) return cuda_check(c, ce, "FCM template blocks");
+            const gdc_status st = gdc_fcm_apply(c->fcm, n, c->vb_n, c->W, c->vb_t);
+            if (st != GDC_OK) return fail(c, st, std::string("FCM: ") + gdc_fcm_last_error(c->fcm));
+            ce = cudaMemcpyAsync(u.data(), c->vb_t, sizeof(double) * n3, cudaMemcpyDeviceToHost, c->stream);
+            if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
+            if (ce != cudaSuccess) return cuda_check(c, ce, "FCM template blocks");
+            for (int row = 0; row < n3; ++row) Mb[(long long)row * n3 + k] = u[row];
+        }
+        for (int i = 0; i < n3; ++i)
+            for (int j = i + 1; j < n3; ++j) {
+                const double m = 0.5 * (Mb[(long long)i * n3 + j] + Mb[(long long)j * n3 + i]);
+                Mb[(long long)i * n3 + j] = Mb[(long long)j * n3 + i] = m;
+            }
+    }
+    return cuda_check(c, cudaMemcpyAsync(c->fcm_Mt, M.data(), sizeof(double) * M.size(), cudaMemcpyHostToDevice,
+                                         c->stream), "FCM template blocks");
 }
 
 // ---- the steps -------------------------------------------------------------------------
@@ -803,15 +839,17 @@ gdc_status gdc_init(gdc_ctx** out, const gdc_params* params, int n_templates, co
     if ((st = cuda_check(c, e, "state read")) != GDC_OK) return st;
     if ((st = check_state_host(c, hY.data(), hq.data())) != GDC_OK) return st;
     krylov_init_attributes();
-    launch_template_setup(c);
-    if ((st = cuda_check(c, cudaGetLastError(), "template setup")) != GDC_OK) return st;
-    if ((st = read_status(c)) != GDC_OK) return st;
-    if ((st = sym_init_attributes(c)) != GDC_OK) return st;
     if (c->p.mobility == GDC_MOB_FCM) {
+        // the FCM grid first: the preconditioner's template blocks are FCM blocks
         const gdc_fcm_params fp = fcm_params_of(c->p, c->NBL);
         if ((st = gdc_fcm_init(&c->fcm, &fp, c->fcm_ws, c->fcm_ws_bytes, c->stream)) != GDC_OK)
             return fail(c, st, "FCM context setup failed");
+        if ((st = fcm_template_blocks(c)) != GDC_OK) return st;
     }
+    launch_template_setup(c, c->fcm ? c->fcm_Mt : nullptr);
+    if ((st = cuda_check(c, cudaGetLastError(), "template setup")) != GDC_OK) return st;
+    if ((st = read_status(c)) != GDC_OK) return st;
+    if ((st = sym_init_attributes(c)) != GDC_OK) return st;
     if (c->p.autotune) {
         load_at(c, c->Y, c->q);
         if ((st = autotune_pair_kernel(c)) != GDC_OK) return st;

@@ -404,7 +404,7 @@ __global__ void k_template_setup(const int* __restrict__ tmpl_n, const int* __re
                                  const long long* __restrict__ minv_off, const double* __restrict__ xyz,
                                  double a, double eta, double* __restrict__ Minv, double* __restrict__ Gt,
                                  double* __restrict__ Nt, double* __restrict__ KtKp, double* __restrict__ work,
-                                 double* __restrict__ Mt, int* __restrict__ status) {
+                                 double* __restrict__ Mt, const double* __restrict__ Mext, int* __restrict__ status) {
     const int t = blockIdx.x;
     const int n = tmpl_n[t];
     const int n3 = 3 * n;
@@ -413,8 +413,13 @@ __global__ void k_template_setup(const int* __restrict__ tmpl_n, const int* __re
     double* L = work + 2 * minv_off[t];
     double* X = L + (long long)n3 * n3;
     const double c0 = 1.0 / (8.0 * 3.141592653589793 * eta);
-    // 1. the template's RPY block M_t (Sec. 4.1), row-major in L
-    for (long long e = threadIdx.x; e < (long long)n3 * n3; e += blockDim.x) {
+    // 1. the template's mobility block M_t, row-major in L: given (Mext: the FCM block of the
+    //    template alone in the periodic cube), or the RPY block (Sec. 4.1)
+    for (long long e = threadIdx.x; Mext && e < (long long)n3 * n3; e += blockDim.x) {
+        L[e] = Mext[minv_off[t] + e];
+        Mt[minv_off[t] + e] = L[e];
+    }
+    for (long long e = threadIdx.x; !Mext && e < (long long)n3 * n3; e += blockDim.x) {
         const int row = (int)(e / n3), col = (int)(e % n3);
         const int i = row / 3, al = row % 3, j = col / 3, be = col % 3;
         const double d0 = b[3 * j] - b[3 * i], d1 = b[3 * j + 1] - b[3 * i + 1], d2 = b[3 * j + 2] - b[3 * i + 2];
@@ -527,10 +532,10 @@ __global__ void k_template_setup(const int* __restrict__ tmpl_n, const int* __re
     }
 }
 
-void launch_template_setup(gdc_ctx* c) {
+void launch_template_setup(gdc_ctx* c, const double* Mext) {
     ++c->n_launch, k_template_setup<<<c->T, 256, 0, c->stream>>>(c->tmpl_n, c->tmpl_off, c->minv_off, c->tmpl_xyz, c->p.a, c->p.eta,
                                                   c->tmpl_Minv, c->tmpl_G, c->tmpl_N, c->tmpl_KtKp, c->tmpl_work,
-                                                  c->tmpl_M, c->dev_status);
+                                                  c->tmpl_M, Mext, c->dev_status);
     const long long nm = c->h_minv_off[c->T];
     ++c->n_launch, k_round_f32<<<(int)std::min<long long>(ceil_div(nm, 256), 1024), 256, 0, c->stream>>>(nm, c->tmpl_M,
                                                                                                       c->tmpl_M32);

@@ -129,6 +129,7 @@ struct gdc_ctx {
     // fluctuating FCM mobility (fcm.cu), GDC_MOB_FCM only
     gdc_fcm* fcm = nullptr;
     double* fcm_u = nullptr;      // M_FCM lambda, 3 per blob
+    double* fcm_Mt = nullptr;     // the templates' FCM blocks (preconditioner), like tmpl_M
     void* fcm_ws = nullptr;
     size_t fcm_ws_bytes = 0;
     unsigned long long fcm_field_step = ~0ULL;   // step whose fluctuating field the grid holds
@@ -352,7 +353,7 @@ void launch_lsq(gdc_ctx* c, const double* vbrev, double* calV);
 void launch_precond(gdc_ctx* c, const double* r, double* z);
 void launch_intra_body(gdc_ctx* c, const double* x, double* y, int gm);
 void launch_intra_body32(gdc_ctx* c, const double* x, double* y, int gm);
-void launch_template_setup(gdc_ctx* c);
+void launch_template_setup(gdc_ctx* c, const double* Mext = nullptr);   // Mext: given template blocks
 
 // krylov.cu
 gdc_status saddle_op(gdc_ctx* c, int prec, const double* x, double* y);
