@@ -271,7 +271,7 @@ __global__ void k_fcm_pack(long long NG, const float2* __restrict__ u, float4* _
 // INV = 0: X_k = sum_n x_n exp(-2 pi i k n / N); INV = 1: the same with +i, unscaled.
 // blockIdx.y picks the component grid (NG points apart).
 template <int INV>
-__global__ void __launch_bounds__(256) k_fft(float2* __restrict__ data, long long NG, const float2* __restrict__ tw_g,
+__global__ void __launch_bounds__(512) k_fft(float2* __restrict__ data, long long NG, const float2* __restrict__ tw_g,
                                              int N, int logN, int axis) {
     extern __shared__ float2 sm[];
     const int S = fft_row(N);
@@ -509,11 +509,16 @@ static gdc_status fcm_check(gdc_fcm* f, cudaError_t e, const char* what) {
 static void fft3(gdc_fcm* f, int slot, int ncomp, bool inverse) {
     const dim3 grid((unsigned)(f->N * f->N / FFT_P), (unsigned)ncomp);
     const size_t smem = fft_smem(f->N);
+    // 512-point pencils take 72 KB of shared memory per block (3 blocks per SM): twice the
+    // threads keep as many warps resident as the 256-point case
+    const int threads = f->N >= 512 ? 512 : 256;
     for (int axis = 0; axis < 3; ++axis) {
         if (inverse)
-            ++f->n_launch, k_fft<1><<<grid, 256, smem, f->stream>>>(f->grid + slot * f->NG, f->NG, f->tw, f->N, f->logN, axis);
+            ++f->n_launch, k_fft<1><<<grid, threads, smem, f->stream>>>(f->grid + slot * f->NG, f->NG, f->tw, f->N, f->logN,
+                                                                       axis);
         else
-            ++f->n_launch, k_fft<0><<<grid, 256, smem, f->stream>>>(f->grid + slot * f->NG, f->NG, f->tw, f->N, f->logN, axis);
+            ++f->n_launch, k_fft<0><<<grid, threads, smem, f->stream>>>(f->grid + slot * f->NG, f->NG, f->tw, f->N, f->logN,
+                                                                       axis);
     }
 }
 
