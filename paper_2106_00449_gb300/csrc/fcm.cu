@@ -53,7 +53,7 @@ struct gdc_fcm {
 
 namespace gdc {
 
-constexpr int FFT_P = 16;     // pencils per FFT block (the index arithmetic below assumes 16)
+// pencils per FFT block: 2^LP (16 up to 256-point pencils, 8 for 512-point ones)
 
 static int fcm_cells(const gdc_fcm_params& p) {
     return (int)std::min(128.0, std::max(2.0, std::floor(p.L / p.R_t)));
@@ -114,7 +114,8 @@ static void fcm_layout(gdc_fcm* f, const gdc_fcm_params& p) {
 // bit-reversed and strided accesses over the banks), rows an odd number of float2 apart.
 __host__ __device__ inline int fft_row(int N) { return N + N / 16 + 1; }
 __device__ __forceinline__ int fft_pad(int i) { return i + (i >> 4); }
-static size_t fft_smem(int N) { return (size_t)(FFT_P * fft_row(N) + N / 2) * sizeof(float2); }
+static int fft_lp(int N) { return N >= 512 ? 3 : 4; }
+static size_t fft_smem(int N) { return (size_t)(((size_t)1 << fft_lp(N)) * fft_row(N) + N / 2) * sizeof(float2); }
 
 // ---- binning ------------------------------------------------------------------------
 
@@ -151,10 +152,10 @@ __global__ void k_fcm_scatter(int n, const int* __restrict__ cell_of, const int*
 
 constexpr int SP_CHUNK = 512;    // blobs staged in shared memory per round
 
-// f(x_g) = sum of lambda_j Delta_j(x_g).  One block per binning cell (cells at least R_t wide):
-// its grid points are those with floor(i nc / N) equal to the cell's index on every axis (an
-// exact integer partition of the grid), and every blob that can reach them lies in the 27
-// cells around it.  Those blobs are staged in shared memory (cells in a fixed order, blobs in
+// f(x_g) = sum of lambda_j Delta_j(x_g).  One block per binning cell (cells at least R_t wide)
+// and chunk of 128 PT of its grid points (blockIdx.y): the cell's grid points are those with
+// floor(i nc / N) equal to its index on every axis (an exact integer partition of the grid),
+// and every blob that can reach them lies in the 27 cells around it.  Those blobs are staged in shared memory (cells in a fixed order, blobs in
 // ascending index; rounds of SP_CHUNK) as FP32 offsets from the cell's corner, nearest image
 // to the cell's centre, and each thread sums them for its grid points with the minimum image
 // in FP32.  Deterministic, no atomics on the grid.
@@ -178,7 +179,7 @@ __global__ void __launch_bounds__(128) k_fcm_spread(int N, double h, double L, i
         corner[d] = c3[d] * w;
     }
     const int npts = gn[0] * gn[1] * gn[2];
-    if (npts == 0) return;
+    if (npts <= (int)blockIdx.y * PT * 128) return;   // whole block: no points in this chunk
     // the neighbour cells (each once when the grid has fewer than 3 cells per side)
     const int no = nc >= 3 ? 3 : nc, o0 = nc >= 3 ? -1 : 0, ncell = no * no * no;
     if (threadIdx.x < ncell) {
@@ -197,7 +198,8 @@ __global__ void __launch_bounds__(128) k_fcm_spread(int N, double h, double L, i
     const int total = c_off[ncell];
     const float Lf = (float)L, hL = 0.5f * Lf;
     const double mid = 0.5 * w;
-    for (int p0 = 0; p0 < npts; p0 += PT * 128) {
+    {
+        const int p0 = blockIdx.y * PT * 128;   // this block's chunk of the cell's grid points
         float gx[PT], gy[PT], gz[PT], ax[PT], ay[PT], az[PT];
         long long gi[PT];
 #pragma unroll
@@ -270,26 +272,27 @@ __global__ void k_fcm_pack(long long NG, const float2* __restrict__ u, float4* _
 
 // INV = 0: X_k = sum_n x_n exp(-2 pi i k n / N); INV = 1: the same with +i, unscaled.
 // blockIdx.y picks the component grid (NG points apart).
-template <int INV>
-__global__ void __launch_bounds__(512) k_fft(float2* __restrict__ data, long long NG, const float2* __restrict__ tw_g,
+template <int INV, int LP>
+__global__ void __launch_bounds__(256) k_fft(float2* __restrict__ data, long long NG, const float2* __restrict__ tw_g,
                                              int N, int logN, int axis) {
+    constexpr int P = 1 << LP;
     extern __shared__ float2 sm[];
     const int S = fft_row(N);
-    float2* tw = sm + FFT_P * S;
+    float2* tw = sm + P * S;
     float2* base = data + blockIdx.y * NG;
-    const int groups = N / FFT_P;
+    const int groups = N / P;
     const int b = blockIdx.x;
     long long off, sp, st;   // first element, pencil stride, element stride
     if (axis == 0) {
-        off = (long long)N * ((b % groups) * FFT_P + (long long)N * (b / groups));
+        off = (long long)N * ((b % groups) * P + (long long)N * (b / groups));
         sp = N;
         st = 1;
     } else if (axis == 1) {
-        off = (b % groups) * FFT_P + (long long)N * N * (b / groups);
+        off = (b % groups) * P + (long long)N * N * (b / groups);
         sp = 1;
         st = N;
     } else {
-        off = (b % groups) * FFT_P + (long long)N * (b / groups);
+        off = (b % groups) * P + (long long)N * (b / groups);
         sp = 1;
         st = (long long)N * N;
     }
@@ -298,10 +301,10 @@ __global__ void __launch_bounds__(512) k_fft(float2* __restrict__ data, long lon
         if (INV) w.y = -w.y;
         tw[j] = w;
     }
-    const int total = FFT_P * N, nmask = N - 1;   // N and FFT_P are powers of two: shifts and masks
+    const int total = P * N, nmask = N - 1;   // N and P are powers of two: shifts and masks
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
-        const int t = axis == 0 ? (e & nmask) : (e >> 4);
-        const int p = axis == 0 ? (e >> logN) : (e & (FFT_P - 1));
+        const int t = axis == 0 ? (e & nmask) : (e >> LP);
+        const int p = axis == 0 ? (e >> logN) : (e & (P - 1));
         sm[p * S + fft_pad((int)(__brev((unsigned)t) >> (32 - logN)))] = base[off + p * sp + t * st];
     }
     // log2 N radix-2 stages, fused three at a time: a thread loads the 8 elements
@@ -311,7 +314,7 @@ __global__ void __launch_bounds__(512) k_fft(float2* __restrict__ data, long lon
     for (int s0 = 0, ns = first; s0 < logN; s0 += ns, ns = 3) {
         const int h = 1 << s0, lper = logN - ns;   // 2^lper groups x offsets per pencil
         __syncthreads();
-        for (int q = threadIdx.x; q < (FFT_P << lper); q += blockDim.x) {
+        for (int q = threadIdx.x; q < (P << lper); q += blockDim.x) {
             const int p = q >> lper, r = q & ((1 << lper) - 1);
             const int k = r & (h - 1), base0 = ((r >> s0) << (s0 + ns)) + k;
             float2* row = sm + p * S;
@@ -343,8 +346,8 @@ __global__ void __launch_bounds__(512) k_fft(float2* __restrict__ data, long lon
     }
     __syncthreads();
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
-        const int t = axis == 0 ? (e & nmask) : (e >> 4);
-        const int p = axis == 0 ? (e >> logN) : (e & (FFT_P - 1));
+        const int t = axis == 0 ? (e & nmask) : (e >> LP);
+        const int p = axis == 0 ? (e >> logN) : (e & (P - 1));
         base[off + p * sp + t * st] = sm[p * S + fft_pad(t)];
     }
 }
@@ -507,18 +510,24 @@ static gdc_status fcm_check(gdc_fcm* f, cudaError_t e, const char* what) {
 }
 
 static void fft3(gdc_fcm* f, int slot, int ncomp, bool inverse) {
-    const dim3 grid((unsigned)(f->N * f->N / FFT_P), (unsigned)ncomp);
+    // 512-point pencils go 8 to a block, so that a block's shared memory (37 KB) leaves room
+    // for as many resident blocks as the 16 pencils of shorter transforms
+    const int lp = fft_lp(f->N);
+    const dim3 grid((unsigned)(f->N * f->N >> lp), (unsigned)ncomp);
     const size_t smem = fft_smem(f->N);
-    // 512-point pencils take 72 KB of shared memory per block (3 blocks per SM): twice the
-    // threads keep as many warps resident as the 256-point case
-    const int threads = f->N >= 512 ? 512 : 256;
+    float2* d = f->grid + slot * f->NG;
     for (int axis = 0; axis < 3; ++axis) {
-        if (inverse)
-            ++f->n_launch, k_fft<1><<<grid, threads, smem, f->stream>>>(f->grid + slot * f->NG, f->NG, f->tw, f->N, f->logN,
-                                                                       axis);
-        else
-            ++f->n_launch, k_fft<0><<<grid, threads, smem, f->stream>>>(f->grid + slot * f->NG, f->NG, f->tw, f->N, f->logN,
-                                                                       axis);
+        if (lp == 3) {
+            if (inverse)
+                ++f->n_launch, k_fft<1, 3><<<grid, 256, smem, f->stream>>>(d, f->NG, f->tw, f->N, f->logN, axis);
+            else
+                ++f->n_launch, k_fft<0, 3><<<grid, 256, smem, f->stream>>>(d, f->NG, f->tw, f->N, f->logN, axis);
+        } else {
+            if (inverse)
+                ++f->n_launch, k_fft<1, 4><<<grid, 256, smem, f->stream>>>(d, f->NG, f->tw, f->N, f->logN, axis);
+            else
+                ++f->n_launch, k_fft<0, 4><<<grid, 256, smem, f->stream>>>(d, f->NG, f->tw, f->N, f->logN, axis);
+        }
     }
 }
 
@@ -585,8 +594,11 @@ gdc_status gdc_fcm_init(gdc_fcm** out, const gdc_fcm_params* params, void* works
         tw[j] = make_float2((float)std::cos(a), (float)-std::sin(a));
     }
     cudaError_t e = cudaMemcpyAsync(f->tw, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice, f->stream);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem(512));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem(512));
+    const int fsm = (int)std::max(fft_smem(256), fft_smem(512));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft<0, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft<1, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft<0, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft<1, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm);
     if (e == cudaSuccess) e = cudaStreamSynchronize(f->stream);
     if (e != cudaSuccess) {
         delete f;
@@ -609,26 +621,13 @@ gdc_status gdc_fcm_apply(gdc_fcm* f, int n, const double* r, const double* lambd
     ++f->n_launch, k_cell_sort<<<ceil_div(nc3, 256), 256, 0, f->stream>>>((int)nc3, f->cnt, f->start, f->list);
     const double s2 = f->p.sigma * f->p.sigma;
     {
-        // grid points of the largest binning cell, per thread of a 128-thread block
-        const long long side = (f->N + f->nc - 1) / f->nc + 1;
-        const long long per = (side * side * side + 127) / 128;
+        // 4 grid points per thread, 512 per block; the largest binning cell has side^3 points
+        const long long side = (f->N + f->nc - 1) / f->nc;
+        const unsigned chunks = (unsigned)((side * side * side + 511) / 512);
         const float R2 = (float)(f->p.R_t * f->p.R_t), i2 = (float)(0.5 / s2);
         const float nrm = (float)std::pow(2.0 * 3.141592653589793 * s2, -1.5);
-#define GDC_FCM_SPREAD(PT)                                                                                          \
-    ++f->n_launch, k_fcm_spread<PT><<<(unsigned)nc3, 128, 0, f->stream>>>(f->N, f->h, f->p.L, f->nc, f->pw, f->cnt, \
-                                                                         f->start, f->list, lambda, R2, i2, nrm,    \
-                                                                         f->grid, f->NG)
-        if (per <= 1)
-            GDC_FCM_SPREAD(1);
-        else if (per <= 2)
-            GDC_FCM_SPREAD(2);
-        else if (per <= 4)
-            GDC_FCM_SPREAD(4);
-        else if (per <= 8)
-            GDC_FCM_SPREAD(8);
-        else
-            GDC_FCM_SPREAD(16);
-#undef GDC_FCM_SPREAD
+        ++f->n_launch, k_fcm_spread<4><<<dim3((unsigned)nc3, chunks), 128, 0, f->stream>>>(
+            f->N, f->h, f->p.L, f->nc, f->pw, f->cnt, f->start, f->list, lambda, R2, i2, nrm, f->grid, f->NG);
     }
     fft3(f, 0, 3, false);
     ++f->n_launch, k_fcm_solve<<<ceil_div(f->NG, 256), 256, 0, f->stream>>>(
