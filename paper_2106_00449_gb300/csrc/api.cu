@@ -203,8 +203,8 @@ static size_t carve(gdc_ctx* c, void* base) {
     c->spos = w.take<float4>(NBL);
     c->slam = w.take<float4>(NBL);
     c->sdup = w.take<float4>(3 * NBL);
-    c->spos64 = w.take<double4>(NBL);
-    c->slam64 = w.take<double4>(NBL);
+    c->spos64 = w.take<double4_32a>(NBL);
+    c->slam64 = w.take<double4_32a>(NBL);
     c->W = w.take<double>(3 * NBL);
     c->Wt = w.take<double>(6 * NB);
     c->vb_n = w.take<double>(3 * NBL);
@@ -279,7 +279,7 @@ static size_t carve(gdc_ctx* c, void* base) {
     c->red_part = w.take<double>((long long)std::max(c->seg_gm.n_chunks, c->seg_lz.n_chunks) * cols);
     c->mv_items = w.take<MvItem>(c->mv_cap_items);
     c->mv_nk = w.take<int>(S);
-    c->mv_part = (void*)w.take<double4>((long long)c->mv_cap_kmax * NBL);
+    c->mv_part = (void*)w.take<double4_32a>((long long)c->mv_cap_kmax * NBL);
     c->dev_status = w.take<int>(4);
     c->sym_items = w.take<SymItem>(c->sym_cap_items);
     c->sym_row_nk = w.take<int>(std::max<long long>(1, c->sym_n_tiles));

@@ -33,12 +33,12 @@ __device__ __forceinline__ int cell_coord(double x, double h_inv) {
     return (int)v;
 }
 
-__global__ void k_cell_assign(int NBL, const double4* __restrict__ spos64, const int* __restrict__ blob_susp,
+__global__ void k_cell_assign(int NBL, const double4_32a* __restrict__ spos64, const int* __restrict__ blob_susp,
                               double h_inv, unsigned mask, int4* __restrict__ cell_xyz, unsigned* __restrict__ cell_key,
                               int* __restrict__ cnt) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= NBL) return;
-    const double4 p = spos64[i];
+    const double4_32a p = spos64[i];
     const int s = blob_susp[i];
     const int4 cc = make_int4(cell_coord(p.x, h_inv), cell_coord(p.y, h_inv), cell_coord(p.z, h_inv), s);
     const unsigned key = cell_hash(cc.x, cc.y, cc.z, s, mask);
@@ -134,7 +134,7 @@ __global__ void k_cell_sort(int H, const int* __restrict__ cnt, const int* __res
 }
 
 __device__ __forceinline__ long long body_of(float4 p) { return __float_as_int(p.w); }
-__device__ __forceinline__ long long body_of(double4 p) { return (long long)p.w; }
+__device__ __forceinline__ long long body_of(double4_32a p) { return (long long)p.w; }
 
 // f_i = sum over blobs j of other bodies within the cutoff of F(r_ij) (r_i - r_j)/r_ij, in
 // precision T from the pair kernels' positions (relative to the suspension's reference
@@ -257,7 +257,7 @@ void launch_forces_cell(gdc_ctx* c, int prec, double* fblob) {
             c->NBL, c->spos, c->cell_xyz, c->cell_cnt, c->cell_start, c->cell_list, mask, force_constants<float>(c->p),
             fblob);
     else
-        ++c->n_launch, k_forces_cell<double, double4><<<ceil_div(c->NBL, 128), 128, 0, c->stream>>>(
+        ++c->n_launch, k_forces_cell<double, double4_32a><<<ceil_div(c->NBL, 128), 128, 0, c->stream>>>(
             c->NBL, c->spos64, c->cell_xyz, c->cell_cnt, c->cell_start, c->cell_list, mask, force_constants<double>(c->p),
             fblob);
     prof_end(c, pe);

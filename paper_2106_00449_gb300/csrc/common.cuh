@@ -9,7 +9,7 @@
 //   * body-indexed vectors (V, calV, F) are 6 doubles per body;
 //   * the configuration a product is evaluated at ("loaded" configuration):
 //     per-body rotation R (9 doubles), per-blob FP64 position r, and the pair
-//     kernels' source arrays: float4/double4 position relative to the
+//     kernels' source arrays: float4/double4_32a position relative to the
 //     suspension's reference point (w = body index bits) and float4/double4
 //     lambda.
 #pragma once
@@ -150,7 +150,7 @@ struct gdc_ctx {
     // loaded configuration
     double *Rb = 0, *r = 0, *Yc = 0, *ref = 0;
     float4 *spos = 0, *slam = 0, *sdup = 0;   // sdup: 3 float4 per blob, pair-kernel tile layout
-    double4 *spos64 = 0, *slam64 = 0;
+    double4_32a *spos64 = 0, *slam64 = 0;
 
     // step buffers
     double *W = 0, *Wt = 0, *vb_n = 0, *vb_t = 0, *vb_m = 0, *calV = 0, *calVt = 0;
@@ -185,7 +185,7 @@ struct gdc_ctx {
     int* mv_nk = 0;               // chunks per suspension
     std::vector<gdc::MvItem> h_mv_items;
     std::vector<int> h_mv_nk;
-    void* mv_part = 0;            // mv_kmax x NBL x (float4 | double4)
+    void* mv_part = 0;            // mv_kmax x NBL x (float4 | double4_32a)
     const int* mv_active = 0;     // when set, suspensions flagged 0 are skipped by the pair kernels
 
     // symmetric FP32 pair kernel (each unordered pair once) and its work list

@@ -39,7 +39,7 @@ struct gdc_fcm {
     float2* tw = nullptr;     // N/2 forward twiddles exp(-2 pi i j / N)
     float2* grid = nullptr;   // 9 complex grids
     float4* packed = nullptr; // 2 packed velocity grids: deterministic, fluctuating
-    double4* pw = nullptr;    // blob positions wrapped into the cube
+    double4_32a* pw = nullptr;    // blob positions wrapped into the cube
     int* cell_of = nullptr;
     int* cnt = nullptr;
     int* start = nullptr;
@@ -90,7 +90,7 @@ static size_t fcm_carve(gdc_fcm* f, void* base) {
     f->tw = w.take<float2>(f->N / 2);
     f->grid = w.take<float2>(9 * f->NG);
     f->packed = w.take<float4>(2 * f->NG);
-    f->pw = w.take<double4>(f->p.max_blobs);
+    f->pw = w.take<double4_32a>(f->p.max_blobs);
     f->cell_of = w.take<int>(f->p.max_blobs);
     f->cnt = w.take<int>(nc3);
     f->start = w.take<int>(nc3);
@@ -120,7 +120,7 @@ static size_t fft_smem(int N) { return (size_t)(((size_t)1 << fft_lp(N)) * fft_r
 // ---- binning ------------------------------------------------------------------------
 
 // Wraps each blob into the cube and bins it.
-__global__ void k_fcm_bin(int n, const double* __restrict__ r, double L, int nc, double4* __restrict__ pw,
+__global__ void k_fcm_bin(int n, const double* __restrict__ r, double L, int nc, double4_32a* __restrict__ pw,
                           int* __restrict__ cell_of, int* __restrict__ cnt) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -134,7 +134,7 @@ __global__ void k_fcm_bin(int n, const double* __restrict__ r, double L, int nc,
         c[d] = (int)fmin(fmax(floor(v / w), 0.0), nc - 1.0);
         x[d] = v;
     }
-    pw[i] = make_double4(x[0], x[1], x[2], 0.0);
+    pw[i] = make_double4_32a(x[0], x[1], x[2], 0.0);
     const int id = c[0] + nc * (c[1] + nc * c[2]);
     cell_of[i] = id;
     atomicAdd(cnt + id, 1);
@@ -160,7 +160,7 @@ constexpr int SP_CHUNK = 512;    // blobs staged in shared memory per round
 // to the cell's centre, and each thread sums them for its grid points with the minimum image
 // in FP32.  Deterministic, no atomics on the grid.
 template <int PT>   // grid points a thread keeps per round (cells with more points take several rounds)
-__global__ void __launch_bounds__(128) k_fcm_spread(int N, double h, double L, int nc, const double4* __restrict__ pw,
+__global__ void __launch_bounds__(128) k_fcm_spread(int N, double h, double L, int nc, const double4_32a* __restrict__ pw,
                                                     const int* __restrict__ cnt, const int* __restrict__ start,
                                                     const int* __restrict__ list, const double* __restrict__ lam,
                                                     float R2, float inv2s2, float norm, float2* __restrict__ f,
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(128) k_fcm_spread(int N, double h, double L, i
                 int k = 0;
                 while (c_off[k + 1] <= e) ++k;
                 const int j = list[c_start[k] + (e - c_off[k])];
-                const double4 p = pw[j];
+                const double4_32a p = pw[j];
                 double rx = p.x - corner[0], ry = p.y - corner[1], rz = p.z - corner[2];
                 rx -= L * rint((rx - mid) / L);
                 ry -= L * rint((ry - mid) / L);

@@ -26,7 +26,7 @@ __global__ void k_blob_pos(int NBL, const int* __restrict__ blob_body, const int
                            const int* __restrict__ tmpl_off, const double* __restrict__ tmpl_xyz,
                            const double* __restrict__ Y, const double* __restrict__ Rb,
                            const double* __restrict__ ref, double* __restrict__ r,
-                           float4* __restrict__ spos, double4* __restrict__ spos64) {
+                           float4* __restrict__ spos, double4_32a* __restrict__ spos64) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= NBL) return;
     const int p = blob_body[i];
@@ -44,7 +44,7 @@ __global__ void k_blob_pos(int NBL, const int* __restrict__ blob_body, const int
     const double rx = x - ref[3 * s], ry = y - ref[3 * s + 1], rz = z - ref[3 * s + 2];
     const float pb = __int_as_float(p);
     spos[i] = make_float4((float)rx, (float)ry, (float)rz, pb);
-    spos64[i] = make_double4(rx, ry, rz, (double)p);
+    spos64[i] = make_double4_32a(rx, ry, rz, (double)p);
 }
 
 void load_config(gdc_ctx* c, const double* Y, const double* q) {

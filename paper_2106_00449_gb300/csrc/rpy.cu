@@ -39,11 +39,11 @@ __global__ void k_pack_lam32(int NBL, const int* __restrict__ map, const double*
 }
 
 __global__ void k_pack_lam64(int NBL, const int* __restrict__ map, const double* __restrict__ x,
-                             double4* __restrict__ slam) {
+                             double4_32a* __restrict__ slam) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= NBL) return;
     const long long o = map ? (long long)map[i] : 3LL * i;
-    slam[i] = make_double4(x[o], x[o + 1], x[o + 2], 0.0);
+    slam[i] = make_double4_32a(x[o], x[o + 1], x[o + 2], 0.0);
 }
 
 void launch_pack_lambda(gdc_ctx* c, int prec, const double* x, int gm_layout) {
@@ -241,8 +241,8 @@ struct RpyConstDF {
 
 template <int TPT>
 __global__ void __launch_bounds__(128) k_rpy_df(const MvItem* __restrict__ items, const long long* __restrict__ susp_blob_off,
-                                                const double4* __restrict__ spos, const double4* __restrict__ slam,
-                                                double4* __restrict__ part, int NBL, RpyConstDF k) {
+                                                const double4_32a* __restrict__ spos, const double4_32a* __restrict__ slam,
+                                                double4_32a* __restrict__ part, int NBL, RpyConstDF k) {
     __shared__ float4 sh[4 * MV_TILE];
     const MvItem it = items[blockIdx.x];
     const long long b0 = susp_blob_off[it.s];
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(128) k_rpy_df(const MvItem* __restrict__ items
     float bt[TPT];
 #pragma unroll
     for (int t = 0; t < TPT; ++t) {
-        const double4 p = spos[b0 + min(it.t0 + (int)threadIdx.x + t * 128, ns - 1)];
+        const double4_32a p = spos[b0 + min(it.t0 + (int)threadIdx.x + t * 128, ns - 1)];
         xt[t] = df_from(p.x);
         yt[t] = df_from(p.y);
         zt[t] = df_from(p.z);
@@ -263,8 +263,8 @@ __global__ void __launch_bounds__(128) k_rpy_df(const MvItem* __restrict__ items
         const int n = min(MV_TILE, it.j1 - j0);
         __syncthreads();
         for (int e = threadIdx.x; e < n; e += 128) {
-            const double4 ps = spos[b0 + j0 + e];
-            const double4 ls = slam[b0 + j0 + e];
+            const double4_32a ps = spos[b0 + j0 + e];
+            const double4_32a ls = slam[b0 + j0 + e];
             const df x = df_from(ps.x), y = df_from(ps.y), z = df_from(ps.z);
             const df lx = df_from(ls.x), ly = df_from(ls.y), lz = df_from(ls.z);
             sh[4 * e] = make_float4(x.h, y.h, z.h, (float)ps.w);
@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(128) k_rpy_df(const MvItem* __restrict__ items
 #pragma unroll
     for (int t = 0; t < TPT; ++t) {
         const int ti = it.t0 + threadIdx.x + t * 128;
-        if (ti < ns) part[(long long)it.k * NBL + b0 + ti] = make_double4(df_to(ux[t]), df_to(uy[t]), df_to(uz[t]), 0.0);
+        if (ti < ns) part[(long long)it.k * NBL + b0 + ti] = make_double4_32a(df_to(ux[t]), df_to(uy[t]), df_to(uz[t]), 0.0);
     }
 }
 
@@ -331,16 +331,16 @@ static RpyConstDF df_constants(double a) {
 template <int TPT>
 __global__ void __launch_bounds__(128) k_rpy64(const MvItem* __restrict__ items, const int* __restrict__ active,
                                                const long long* __restrict__ susp_blob_off,
-                                               const double4* __restrict__ spos, const double4* __restrict__ slam,
-                                               double4* __restrict__ part, int NBL, double a) {
-    __shared__ double4 sp[MV_TILE];
-    __shared__ double4 sl[MV_TILE];
+                                               const double4_32a* __restrict__ spos, const double4_32a* __restrict__ slam,
+                                               double4_32a* __restrict__ part, int NBL, double a) {
+    __shared__ double4_32a sp[MV_TILE];
+    __shared__ double4_32a sl[MV_TILE];
     const MvItem it = items[blockIdx.x];
     const long long b0 = susp_blob_off[it.s];
     const int ns = (int)(susp_blob_off[it.s + 1] - b0);
     if (active && !active[it.s]) {   // stopped Krylov loop: product unused, leave zeros
         for (int t = threadIdx.x; t < 128 * TPT && it.t0 + t < ns; t += 128)
-            part[(long long)it.k * NBL + b0 + it.t0 + t] = make_double4(0.0, 0.0, 0.0, 0.0);
+            part[(long long)it.k * NBL + b0 + it.t0 + t] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
         return;
     }
     const double c23 = 2.0 * a * a / 3.0, c2 = 2.0 * a * a, four_a2 = 4.0 * a * a;
@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(128) k_rpy64(const MvItem* __restrict__ items,
 #pragma unroll
     for (int t = 0; t < TPT; ++t) {
         const int ti = it.t0 + threadIdx.x + t * 128;
-        const double4 p = spos[b0 + min(ti, ns - 1)];
+        const double4_32a p = spos[b0 + min(ti, ns - 1)];
         xt[t] = p.x;
         yt[t] = p.y;
         zt[t] = p.z;
@@ -364,8 +364,8 @@ __global__ void __launch_bounds__(128) k_rpy64(const MvItem* __restrict__ items,
         }
         __syncthreads();
         for (int j = 0; j < n; ++j) {
-            const double4 ps = sp[j];
-            const double4 ls = sl[j];
+            const double4_32a ps = sp[j];
+            const double4_32a ls = sl[j];
 #pragma unroll
             for (int t = 0; t < TPT; ++t) {
                 const double dx = ps.x - xt[t], dy = ps.y - yt[t], dz = ps.z - zt[t];
@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(128) k_rpy64(const MvItem* __restrict__ items,
 #pragma unroll
     for (int t = 0; t < TPT; ++t) {
         const int ti = it.t0 + threadIdx.x + t * 128;
-        if (ti < ns) part[(long long)it.k * NBL + b0 + ti] = make_double4(ax[t], ay[t], az[t], 0.0);
+        if (ti < ns) part[(long long)it.k * NBL + b0 + ti] = make_double4_32a(ax[t], ay[t], az[t], 0.0);
     }
 }
 
@@ -421,20 +421,20 @@ void launch_rpy(gdc_ctx* c, int prec) {
         const RpyConstDF k = df_constants(c->p.a);
         if (c->mv_tpt == 4)
             ++c->n_launch, k_rpy_df<4><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off, c->spos64,
-                                                                             c->slam64, (double4*)c->mv_part, c->NBL, k);
+                                                                             c->slam64, (double4_32a*)c->mv_part, c->NBL, k);
         else
             ++c->n_launch, k_rpy_df<2><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off, c->spos64,
-                                                                             c->slam64, (double4*)c->mv_part, c->NBL, k);
+                                                                             c->slam64, (double4_32a*)c->mv_part, c->NBL, k);
     } else {
         if (c->mv_tpt == 1)
             ++c->n_launch, k_rpy64<1><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->mv_active, c->susp_blob_off, c->spos64, c->slam64,
-                                                             (double4*)c->mv_part, c->NBL, c->p.a);
+                                                             (double4_32a*)c->mv_part, c->NBL, c->p.a);
         else if (c->mv_tpt == 4)
             ++c->n_launch, k_rpy64<4><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->mv_active, c->susp_blob_off, c->spos64, c->slam64,
-                                                             (double4*)c->mv_part, c->NBL, c->p.a);
+                                                             (double4_32a*)c->mv_part, c->NBL, c->p.a);
         else
             ++c->n_launch, k_rpy64<2><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->mv_active, c->susp_blob_off, c->spos64, c->slam64,
-                                                             (double4*)c->mv_part, c->NBL, c->p.a);
+                                                             (double4_32a*)c->mv_part, c->NBL, c->p.a);
     }
     prof_end(c, pe);
 }
@@ -643,8 +643,8 @@ static void launch_epilogue(gdc_ctx* c, int prec, double c0, const double* x, do
             c->susp_blob_off, c->body_blob_off, c->spos, c->sdup, rpy_const32(c->p.a), sym ? c->sym_part_j : nullptr,
             c->sym_row_nk, c->sym_tile_base, c->sym_jbase);
     else
-        ++c->n_launch, k_rpy_epilogue<double4><<<ceil_div(c->NBL, 256), 256, 0, c->stream>>>(
-            c->NBL, (const double4*)c->mv_part, c->blob_susp, c->mv_nk, c0, x, y, gm_layout, c->blob_gm, c->body_gm,
+        ++c->n_launch, k_rpy_epilogue<double4_32a><<<ceil_div(c->NBL, 256), 256, 0, c->stream>>>(
+            c->NBL, (const double4_32a*)c->mv_part, c->blob_susp, c->mv_nk, c0, x, y, gm_layout, c->blob_gm, c->body_gm,
             c->blob_body, c->r, c->Yc, nullptr, nullptr, c->p.a, c->susp_blob_off, c->body_blob_off, c->spos, c->sdup,
             rpy_const32(c->p.a), nullptr, nullptr, nullptr, nullptr);
 }
@@ -790,9 +790,9 @@ __global__ void __launch_bounds__(128) k_forces32(const MvItem* __restrict__ ite
 
 template <int TPT>
 __global__ void __launch_bounds__(128) k_forces64(const MvItem* __restrict__ items, const long long* __restrict__ susp_blob_off,
-                                                  const double4* __restrict__ spos, double4* __restrict__ part, int NBL,
+                                                  const double4_32a* __restrict__ spos, double4_32a* __restrict__ part, int NBL,
                                                   ForceK<double> k) {
-    __shared__ double4 sp[MV_TILE];
+    __shared__ double4_32a sp[MV_TILE];
     const MvItem it = items[blockIdx.x];
     const long long b0 = susp_blob_off[it.s];
     const int ns = (int)(susp_blob_off[it.s + 1] - b0);
@@ -801,7 +801,7 @@ __global__ void __launch_bounds__(128) k_forces64(const MvItem* __restrict__ ite
     long long bt[TPT];
     for (int t = 0; t < TPT; ++t) {
         fx[t] = fy[t] = fz[t] = 0.0;
-        const double4 p = spos[b0 + min(ti0 + t * 128, ns - 1)];
+        const double4_32a p = spos[b0 + min(ti0 + t * 128, ns - 1)];
         xt[t] = p.x;
         yt[t] = p.y;
         zt[t] = p.z;
@@ -813,7 +813,7 @@ __global__ void __launch_bounds__(128) k_forces64(const MvItem* __restrict__ ite
         for (int e = threadIdx.x; e < n; e += 128) sp[e] = spos[b0 + j0 + e];
         __syncthreads();
         for (int j = 0; j < n; ++j) {
-            const double4 ps = sp[j];
+            const double4_32a ps = sp[j];
             const long long bj = (long long)ps.w;
 #pragma unroll
             for (int t = 0; t < TPT; ++t) {
@@ -831,7 +831,7 @@ __global__ void __launch_bounds__(128) k_forces64(const MvItem* __restrict__ ite
     }
     for (int t = 0; t < TPT; ++t) {
         const int ti = ti0 + t * 128;
-        if (ti < ns) part[(long long)it.k * NBL + b0 + ti] = make_double4(fx[t], fy[t], fz[t], 0.0);
+        if (ti < ns) part[(long long)it.k * NBL + b0 + ti] = make_double4_32a(fx[t], fy[t], fz[t], 0.0);
     }
 }
 
@@ -842,7 +842,7 @@ __global__ void __launch_bounds__(128) k_forces64(const MvItem* __restrict__ ite
                 (float4*)c->mv_part, c->NBL, force_constants<float>(c->p));                                \
         else                                                                                           \
             ++c->n_launch, k_forces64<TPT><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->susp_blob_off,          \
-                c->spos64, (double4*)c->mv_part, c->NBL, force_constants<double>(c->p));                   \
+                c->spos64, (double4_32a*)c->mv_part, c->NBL, force_constants<double>(c->p));                   \
     } while (0)
 
 void launch_forces_pair(gdc_ctx* c, int prec, double* fblob) {
