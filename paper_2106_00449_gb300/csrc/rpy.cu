@@ -236,7 +236,7 @@ __device__ __forceinline__ df df_rsqrt(df x) {
 
 struct RpyConstDF {
     df c23, c2, cA, c9, cB;
-    double four_a2;
+    df four_a2;   // 4a^2
 };
 
 template <int TPT>
@@ -285,7 +285,8 @@ __global__ void __launch_bounds__(128) k_rpy_df(const MvItem* __restrict__ items
                 const df r2 = df_add(df_add(df_mul(dx, dx), df_mul(dy, dy)), df_mul(dz, dz));
                 const df ri = df_rsqrt(r2);
                 df A, B;
-                if ((double)r2.h + (double)r2.l >= k.four_a2) {
+                // r^2 >= 4a^2 compared in double-float (both normalised: high parts first)
+                if (r2.h > k.four_a2.h || (r2.h == k.four_a2.h && r2.l >= k.four_a2.l)) {
                     const df ri2 = df_mul(ri, ri);
                     const df ri3 = df_mul(ri2, ri);
                     A = df_add(ri, df_mul(k.c23, ri3));
@@ -322,7 +323,7 @@ static RpyConstDF df_constants(double a) {
     k.cA = df_from_host(4.0 / (3.0 * a));
     k.c9 = df_from_host(9.0 / (32.0 * a));
     k.cB = df_from_host(1.0 / (8.0 * a * a));
-    k.four_a2 = 4.0 * a * a;
+    k.four_a2 = df_from_host(4.0 * a * a);
     return k;
 }
 
