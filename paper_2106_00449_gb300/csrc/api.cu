@@ -936,6 +936,7 @@ gdc_status gdc_set_params(gdc_ctx* c, const gdc_params* p) {
     c->p.seed = seed;
     c->p.pair_kernel = pair_kernel;   // the pair kernel is chosen at init
     drop_graph(c);   // parameters are baked into the captured launches
+    c->fcm_field_step = ~0ULL;   // an FCM field drawn with the old kT and dt is not reused
     return GDC_OK;
 }
 

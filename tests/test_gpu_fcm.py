@@ -117,3 +117,19 @@ def test_fcm_step_runs_host_driven_with_graph_requested(lib):
     b = _fcm_case(lib, 0, graph=0, oracle=False)
     np.testing.assert_array_equal(a[4], b[4])
     np.testing.assert_array_equal(a[5], b[5])
+
+
+def test_fcm_slip_follows_parameter_changes(lib):
+    """v-breve at a fixed step scales as sqrt(kT/dt): a parameter change between two slips of
+    the same step draws the field again with the new scale."""
+    import dataclasses
+    from synthetic import workloads as WL
+    wl = WL.c1()
+    ctx = lib.context_from_workload(wl, precision=0, mobility=1, box_L=20.0, fcm_N=32, seed=3)
+    W = np.zeros(3 * wl.n_blobs)      # unused with FCM: the stress is drawn on the grid
+    v1 = _host(ctx.brownian_slip(W)[0])
+    again = _host(ctx.brownian_slip(W)[0])       # same step: the stored field, averaged again
+    np.testing.assert_array_equal(again, v1)
+    ctx.set_params(dataclasses.replace(ctx.params, kT=4.0 * ctx.params.kT))
+    v2 = _host(ctx.brownian_slip(W)[0])
+    np.testing.assert_allclose(v2, 2.0 * v1, rtol=1e-5, atol=1e-12 * np.abs(v1).max())
