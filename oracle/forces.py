@@ -44,16 +44,21 @@ def pair_force(dist: np.ndarray, a: float, A: float, b: float, potential: int = 
 
 
 def blob_forces(r: np.ndarray, blob_body: np.ndarray, A: float, b: float, a: float, potential: int = SOFT,
-                well_A: float = 0.0, well_lambda: float = 0.5) -> np.ndarray:
+                well_A: float = 0.0, well_lambda: float = 0.5, box: float | None = None) -> np.ndarray:
     """Blob forces f_i = sum over blobs j of other bodies of F_k(r_ij) (r_i - r_j)/r_ij.
 
-    b and well_lambda are lengths (Sec. 6.4 uses A_w = 5 kT and lambda = 0.5 a)."""
+    b and well_lambda are lengths (Sec. 6.4 uses A_w = 5 kT and lambda = 0.5 a).  In a
+    periodic cube of side ``box`` (the FCM setting of Sec. 4.2) r_i - r_j is the minimum
+    image: every other image of a blob is farther than box/2, where the forces have vanished
+    for the cubes this is used with."""
     m = r.shape[0]
     f = np.zeros((m, 3))
     if A == 0.0 and (potential == SOFT or well_A == 0.0):
         return f
     for i in range(m):
         d = r[i][None, :] - r
+        if box is not None:
+            d -= box * np.round(d / box)
         dist = np.linalg.norm(d, axis=1)
         sel = (blob_body != blob_body[i]) & (dist > 0.0)
         mag = pair_force(dist[sel], a, A, b, potential, well_A, well_lambda)

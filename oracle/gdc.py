@@ -162,8 +162,8 @@ def gdc_step_fcm(layout, Y, q, Wt, grid, p: Params, seed: int, susp: int, step: 
     The Brownian slip is v-breve = J L^-1 D W (already in the velocity form): the stress of
     (seed, susp, step) gives one fluctuating field u-breve per step, averaged at x^n, at the
     perturbed states of step 3 and at the mid-step x^m -- the same W throughout, and the
-    re-averaging Sec. 5 describes.  The mobility solve of step 5 uses the dense M_FCM at x^m.
-    Forces are left out (pair forces in a periodic cube are not part of this path)."""
+    re-averaging Sec. 5 describes.  The mobility solve of step 5 uses the dense M_FCM at x^m,
+    with the pair forces of forces.py at x^m at minimum-image distances in the cube."""
     from . import fcm
     r0 = geometry.blob_positions(layout, Y, q)
     vb0, ufield = fcm.brownian_velocity(grid, r0, seed, susp, step, p.kT, p.dt)
@@ -194,10 +194,13 @@ def gdc_step_fcm(layout, Y, q, Wt, grid, p: Params, seed: int, susp: int, step: 
     K = rigid.k_matrix(rm, Ym, layout.blob_body)
     B = rigid.rigid_basis(K, layout.n_bodies)
     vbm = fcm.average(grid, rm, ufield).reshape(-1)
-    lam, V = rigid.saddle_solve(M, K, B, vbm, np.zeros(6 * layout.n_bodies))
+    f = forces.blob_forces(rm, layout.blob_body, p.rep_A, p.rep_b, p.a, p.potential, p.well_A, p.well_lambda,
+                           box=grid.L)
+    FT = forces.body_force_torque(rm, Ym, layout.blob_body, f)
+    lam, V = rigid.saddle_solve(M, K, B, vbm, FT)
     Y1, q1 = geometry.advance(Y, q, V.reshape(-1, 6), nu * p.dt)
-    return dict(r0=r0, vb0=vb0, calV=calV, div=dv, nu=nu, Ym=Ym, qm=qm, M=M, vb=vbm, lam=lam, V=V.reshape(-1, 6),
-                Y1=Y1, q1=q1)
+    return dict(r0=r0, vb0=vb0, calV=calV, div=dv, nu=nu, Ym=Ym, qm=qm, M=M, vb=vbm, FT=FT, lam=lam,
+                V=V.reshape(-1, 6), Y1=Y1, q1=q1)
 
 
 def em_step(layout, Y, q, W, p: Params) -> dict:

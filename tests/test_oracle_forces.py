@@ -121,3 +121,29 @@ def test_special_cases_reduce_to_the_soft_sphere():
     f = _oracle(r, lay.blob_body, 1, u0=0.0)
     g = _oracle(r, lay.blob_body, 1) - soft
     np.testing.assert_allclose(f, g, atol=1e-12)
+
+
+def test_periodic_forces_are_the_sum_over_images():
+    """In a periodic cube the minimum-image forces equal the sum over every image shift of
+    -1, 0, 1 cube sides (all nearer images), computed by brute force."""
+    lay, Y, q, r = _three_bodies(seed=4)
+    box = 16.0                                     # force range ~6.5a < box / 2
+    r = r + np.array([7.0, -9.0, 15.0])            # bodies straddle the cube's faces
+    f = forces.blob_forces(r, lay.blob_body, U0 / B, B, 1.0, 2, AW, LAM, box=box)
+    shifts = np.array([[i, j, k] for i in (-1, 0, 1) for j in (-1, 0, 1) for k in (-1, 0, 1)]) * box
+    ref = np.zeros_like(r)
+    for i in range(r.shape[0]):
+        for j in range(r.shape[0]):
+            if lay.blob_body[i] == lay.blob_body[j]:
+                continue
+            d = r[i] - r[j] - shifts
+            dist = np.linalg.norm(d, axis=1)
+            mag = forces.pair_force(dist, 1.0, U0 / B, B, 2, AW, LAM)
+            mag[dist > 8.0] = 0.0                  # beyond the range: below 1e-15
+            ref[i] += (mag[:, None] * d / dist[:, None]).sum(axis=0)
+    np.testing.assert_allclose(f, ref, atol=1e-12 * np.abs(ref).max())
+    # and translating one body by a cube side changes nothing
+    r2 = r.copy()
+    r2[lay.blob_body == 1] += np.array([box, -box, 0.0])
+    np.testing.assert_allclose(forces.blob_forces(r2, lay.blob_body, U0 / B, B, 1.0, 2, AW, LAM, box=box), f,
+                               atol=1e-12 * np.abs(f).max())
