@@ -68,7 +68,8 @@ typedef enum { GDC_DIV_RFD = 0, GDC_DIV_FD = 1 } gdc_divmode;
 typedef enum { GDC_SCHEME_GDC = 0, GDC_SCHEME_EM = 1 } gdc_scheme;
 
 /* Mobility of the blobs: the unbounded RPY tensor (Sec. 4.1), or the fluctuating FCM of
- * Sec. 4.2 in a periodic cube (one suspension, no pair forces).  With FCM the Brownian
+ * Sec. 4.2 in a periodic cube (one suspension; pair forces at minimum-image distances on a
+ * periodic cell list, which needs box_L of at least 3 force cutoffs).  With FCM the Brownian
  * slip of a step is J u-breve for one fluctuating field u-breve = L^-1 D W drawn at the
  * step's start (stress of (seed, 0, step), see gdc_fcm_*) and averaged again at every later
  * configuration of the step -- the perturbed states of step 3 and the mid-step (Sec. 5);

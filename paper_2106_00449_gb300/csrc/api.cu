@@ -83,8 +83,8 @@ static const char* validate_params(const gdc_params* p) {
         if (gdc_fcm_workspace_bytes(&fp) == 0)
             return "FCM needs box_L > 0 and a valid grid: fcm_N a power of two in [16, 512], 0 < R_t < box_L/2, "
                    "R_t within 15 grid spacings";
-        if (p->rep_A > 0.0 || (p->potential > 0 && p->well_A > 0.0))
-            return "pair forces are not available with the periodic FCM mobility";
+        if (forces_on(*p) && std::floor(p->box_L / (force_cutoff(*p) * (1.0 + 1e-4))) < 3.0)
+            return "with the periodic FCM mobility the pair-force cutoff must fit 3 times in box_L";
     }
     return nullptr;
 }
@@ -850,7 +850,7 @@ gdc_status gdc_init(gdc_ctx** out, const gdc_params* params, int n_templates, co
     if ((st = cuda_check(c, cudaGetLastError(), "template setup")) != GDC_OK) return st;
     if ((st = read_status(c)) != GDC_OK) return st;
     if ((st = sym_init_attributes(c)) != GDC_OK) return st;
-    if (c->p.autotune) {
+    if (c->p.autotune && c->p.mobility == GDC_MOB_RPY) {   // the RPY pair kernels only
         load_at(c, c->Y, c->q);
         if ((st = autotune_pair_kernel(c)) != GDC_OK) return st;
     } else if ((st = default_pair_kernel(c)) != GDC_OK) {

@@ -33,14 +33,28 @@ __device__ __forceinline__ int cell_coord(double x, double h_inv) {
     return (int)v;
 }
 
-__global__ void k_cell_assign(int NBL, const double4_32a* __restrict__ spos64, const int* __restrict__ blob_susp,
-                              double h_inv, unsigned mask, int4* __restrict__ cell_xyz, unsigned* __restrict__ cell_key,
-                              int* __restrict__ cnt) {
+// Cells of the blobs.  box > 0 (a periodic cube, the FCM mobility): positions r wrapped into
+// the cube, nc cells of side box / nc per axis; otherwise cells of side 1 / h_inv from the
+// positions relative to the suspension's reference point.
+__global__ void k_cell_assign(int NBL, const double4_32a* __restrict__ spos64, const double* __restrict__ r,
+                              const int* __restrict__ blob_susp, double h_inv, double box, int nc, unsigned mask,
+                              int4* __restrict__ cell_xyz, unsigned* __restrict__ cell_key, int* __restrict__ cnt) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= NBL) return;
-    const double4_32a p = spos64[i];
     const int s = blob_susp[i];
-    const int4 cc = make_int4(cell_coord(p.x, h_inv), cell_coord(p.y, h_inv), cell_coord(p.z, h_inv), s);
+    int4 cc;
+    if (box > 0.0) {
+        int c[3];
+        for (int d = 0; d < 3; ++d) {
+            double v = r[3LL * i + d];
+            v -= box * floor(v / box);
+            c[d] = (int)fmin(fmax(floor(v * nc / box), 0.0), nc - 1.0);
+        }
+        cc = make_int4(c[0], c[1], c[2], s);
+    } else {
+        const double4_32a p = spos64[i];
+        cc = make_int4(cell_coord(p.x, h_inv), cell_coord(p.y, h_inv), cell_coord(p.z, h_inv), s);
+    }
     const unsigned key = cell_hash(cc.x, cc.y, cc.z, s, mask);
     cell_xyz[i] = cc;
     cell_key[i] = key;
@@ -139,11 +153,13 @@ __device__ __forceinline__ long long body_of(double4_32a p) { return (long long)
 // f_i = sum over blobs j of other bodies within the cutoff of F(r_ij) (r_i - r_j)/r_ij, in
 // precision T from the pair kernels' positions (relative to the suspension's reference
 // point); neighbour cells in z, y, x order, each bucket in ascending blob index.
+// box > 0: a periodic cube of nc >= 3 cells per axis; neighbour cells wrap and distances
+// are minimum images.
 template <typename T, typename P4>
 __global__ void __launch_bounds__(128) k_forces_cell(int NBL, const P4* __restrict__ pos, const int4* __restrict__ cell_xyz,
                                                      const int* __restrict__ cnt, const int* __restrict__ start,
                                                      const int* __restrict__ list, unsigned mask, ForceK<T> k,
-                                                     double* __restrict__ fblob) {
+                                                     T box, int nc, double* __restrict__ fblob) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= NBL) return;
     const P4 pi = pos[i];
@@ -153,7 +169,12 @@ __global__ void __launch_bounds__(128) k_forces_cell(int NBL, const P4* __restri
     for (int dz = -1; dz <= 1; ++dz)
         for (int dy = -1; dy <= 1; ++dy)
             for (int dx = -1; dx <= 1; ++dx) {
-                const int cx = ci.x + dx, cy = ci.y + dy, cz = ci.z + dz;
+                int cx = ci.x + dx, cy = ci.y + dy, cz = ci.z + dz;
+                if (box > T(0)) {
+                    cx = (cx + nc) % nc;
+                    cy = (cy + nc) % nc;
+                    cz = (cz + nc) % nc;
+                }
                 const unsigned key = cell_hash(cx, cy, cz, ci.w, mask);
                 const int e0 = start[key], e1 = e0 + cnt[key];
                 for (int e = e0; e < e1; ++e) {
@@ -161,7 +182,12 @@ __global__ void __launch_bounds__(128) k_forces_cell(int NBL, const P4* __restri
                     const int4 cj = cell_xyz[j];
                     if (cj.x != cx || cj.y != cy || cj.z != cz || cj.w != ci.w) continue;
                     const P4 pj = pos[j];
-                    const T ddx = pi.x - pj.x, ddy = pi.y - pj.y, ddz = pi.z - pj.z;
+                    T ddx = pi.x - pj.x, ddy = pi.y - pj.y, ddz = pi.z - pj.z;
+                    if (box > T(0)) {
+                        ddx -= box * rint(ddx / box);
+                        ddy -= box * rint(ddy / box);
+                        ddz -= box * rint(ddz / box);
+                    }
                     const T r2 = fma(ddx, ddx, fma(ddy, ddy, ddz * ddz));
                     if (body_of(pj) != bi && r2 < k.rc2 && r2 > T(0)) {
                         const T r = sqrt(r2);
@@ -186,8 +212,14 @@ long long cell_buckets(long long NBL) {
 long long cell_scan_ints(long long NBL) { return scan_scratch(cell_buckets(NBL)); }
 
 bool forces_use_cells(const gdc_ctx* c) {
-    return c->p.force_method == GDC_FORCES_CELL_LIST ||
+    return c->p.mobility == GDC_MOB_FCM || c->p.force_method == GDC_FORCES_CELL_LIST ||
            (c->p.force_method == GDC_FORCES_CHOOSE && c->NBL >= GDC_CELL_MIN_BLOBS);
+}
+
+// Periodic cells of the FCM cube for the pair forces: as many per axis as fit at least the
+// cutoff (with margin); validation requires 3 or more.
+static int periodic_cells(const gdc_ctx* c) {
+    return (int)std::floor(c->p.box_L / (force_cutoff(c->p) * (1.0 + 1e-4)));
 }
 
 // For every blob i, the blobs j of other bodies of its suspension whose FP32 r_ij^2, formed
@@ -226,14 +258,15 @@ __global__ void __launch_bounds__(128) k_near_cell(int NBL, const float4* __rest
     near_cnt[i] = m;
 }
 
-// Buckets of the cells of edge h (bucket counts, starts and blob lists, sorted within a bucket).
-static void build_cells(gdc_ctx* c, double h) {
+// Buckets of the cells of edge h, or of nc periodic cells per axis of a cube of side box > 0
+// (bucket counts, starts and blob lists, sorted within a bucket).
+static void build_cells(gdc_ctx* c, double h, double box = 0.0, int nc = 0) {
     const int H = (int)c->cell_H;
     const unsigned mask = (unsigned)(H - 1);
     cudaMemsetAsync(c->cell_cnt, 0, sizeof(int) * H, c->stream);
     cudaMemsetAsync(c->cell_fill, 0, sizeof(int) * H, c->stream);
-    ++c->n_launch, k_cell_assign<<<ceil_div(c->NBL, 256), 256, 0, c->stream>>>(c->NBL, c->spos64, c->blob_susp, 1.0 / h,
-                                                                               mask, c->cell_xyz, c->cell_key, c->cell_cnt);
+    ++c->n_launch, k_cell_assign<<<ceil_div(c->NBL, 256), 256, 0, c->stream>>>(
+        c->NBL, c->spos64, c->r, c->blob_susp, 1.0 / h, box, nc, mask, c->cell_xyz, c->cell_key, c->cell_cnt);
     scan_exclusive(c, H, c->cell_cnt, c->cell_start, c->cell_scan);
     ++c->n_launch, k_cell_scatter<<<ceil_div(c->NBL, 256), 256, 0, c->stream>>>(c->NBL, c->cell_key, c->cell_start,
                                                                                 c->cell_fill, c->cell_list);
@@ -251,15 +284,18 @@ void launch_near_cell(gdc_ctx* c) {
 void launch_forces_cell(gdc_ctx* c, int prec, double* fblob) {
     const unsigned mask = (unsigned)(c->cell_H - 1);
     const int pe = prof_begin(c, 2);
-    build_cells(c, force_cutoff(c->p) * (1.0 + 1e-4));   // FP32 r^2 < r_c^2 stays within adjacent cells
+    const bool periodic = c->p.mobility == GDC_MOB_FCM;
+    const double box = periodic ? c->p.box_L : 0.0;
+    const int nc = periodic ? periodic_cells(c) : 0;
+    build_cells(c, force_cutoff(c->p) * (1.0 + 1e-4), box, nc);   // FP32 r^2 < r_c^2 stays within adjacent cells
     if (prec == GDC_FP32_MIXED)
         ++c->n_launch, k_forces_cell<float, float4><<<ceil_div(c->NBL, 128), 128, 0, c->stream>>>(
             c->NBL, c->spos, c->cell_xyz, c->cell_cnt, c->cell_start, c->cell_list, mask, force_constants<float>(c->p),
-            fblob);
+            (float)box, nc, fblob);
     else
         ++c->n_launch, k_forces_cell<double, double4_32a><<<ceil_div(c->NBL, 128), 128, 0, c->stream>>>(
             c->NBL, c->spos64, c->cell_xyz, c->cell_cnt, c->cell_start, c->cell_list, mask, force_constants<double>(c->p),
-            fblob);
+            box, nc, fblob);
     prof_end(c, pe);
 }
 

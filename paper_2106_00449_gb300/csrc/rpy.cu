@@ -727,6 +727,7 @@ __global__ void k_near_sort(int n, const int* __restrict__ near_cnt, int* __rest
 }
 
 void launch_near_build(gdc_ctx* c) {
+    if (c->p.mobility == GDC_MOB_FCM) return;   // the lists serve the RPY products only
     if (forces_use_cells(c)) {
         launch_near_cell(c);   // the same lists from a cell list, O(N_b)
     } else {

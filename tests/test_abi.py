@@ -66,8 +66,10 @@ def test_workspace_checks_the_mobility_and_force_options_without_gpu(libpath):
     fcm = dict(mobility=g.MOB_FCM, box_L=20.0, fcm_N=64)
     assert ws(g.Params(**fcm)) > ws(g.Params())                     # the FCM grids live in the workspace
     assert ws(g.Params(**fcm), off2, bt2) == 0                      # one suspension only
-    assert ws(g.Params(rep_A=4.0, **fcm)) == 0                      # no pair forces in the periodic cube
-    assert ws(g.Params(potential=1, well_A=5.0, **fcm)) == 0
+    # pair forces in the periodic cube need a side of 3 cutoffs (soft sphere 2a + 36 b = 5.6a here)
+    assert ws(g.Params(rep_A=4.0, **fcm)) > 0
+    assert ws(g.Params(rep_A=4.0, **dict(fcm, box_L=15.0))) == 0
+    assert ws(g.Params(potential=1, well_A=5.0, **fcm)) > 0          # wells: 3a + 6 lambda = 6a
     assert ws(g.Params(**dict(fcm, fcm_N=48))) == 0                 # not a power of two
     assert ws(g.Params(**dict(fcm, box_L=5.0))) == 0                # 3a truncation reaches the image
     assert ws(g.Params(mobility=2)) == 0

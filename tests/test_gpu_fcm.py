@@ -133,3 +133,51 @@ def test_fcm_slip_follows_parameter_changes(lib):
     ctx.set_params(dataclasses.replace(ctx.params, kT=4.0 * ctx.params.kT))
     v2 = _host(ctx.brownian_slip(W)[0])
     np.testing.assert_allclose(v2, 2.0 * v1, rtol=1e-5, atol=1e-12 * np.abs(v1).max())
+
+
+def _periodic_workload(**params):
+    import dataclasses
+    from synthetic import workloads as WL
+    wl = WL.c1()
+    Y = wl.Y.copy()
+    Y[0] += np.array([20.0, 0.0, 0.0])          # one cube side away: forces need the minimum image
+    Y[1] += np.array([0.0, -20.0, 20.0])
+    return dataclasses.replace(wl, Y=Y, params=dict(wl.params, **params))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_fcm_mode_forces_use_minimum_images(lib, prec):
+    from oracle import forces, geometry as G
+    from gpu_common import susp_layout
+    wl = _periodic_workload(rep_A=4.0, rep_b=0.1, potential=2, well_A=5.0, well_lambda=0.5)
+    ctx = lib.context_from_workload(wl, precision=prec, mobility=1, box_L=20.0, fcm_N=32)
+    got = _host(ctx.forces())
+    lay, Y, q = susp_layout(wl, 0)
+    r = G.blob_positions(lay, Y, q)
+    pp = wl.params
+    f = forces.blob_forces(r, lay.blob_body, pp["rep_A"], pp["rep_b"], 1.0, 2, 5.0, 0.5, box=20.0)
+    ref = forces.body_force_torque(r, Y, lay.blob_body, f)
+    unwrapped = forces.body_force_torque(r, Y, lay.blob_body, forces.blob_forces(r, lay.blob_body, pp["rep_A"],
+                                                                                 pp["rep_b"], 1.0, 2, 5.0, 0.5))
+    assert rel(unwrapped, ref) > 0.1                 # the images matter in this configuration
+    assert rel(got, ref) < (1e-12 if prec == 0 else 1e-5), rel(got, ref)
+
+
+def test_fcm_gdc_step_with_wells_matches_oracle(lib):
+    from oracle import gdc as ogdc, philox
+    from gpu_common import oracle_params, rot_err, susp_layout
+    wl = _periodic_workload(rep_A=4.0, rep_b=0.1, potential=1, well_A=5.0, well_lambda=0.5)
+    L, N, seed = 20.0, 64, 91
+    ctx = lib.context_from_workload(wl, precision=0, mobility=1, box_L=L, fcm_N=N, seed=seed, rfd_delta=1e-3,
+                                    gmres_tol=1e-7, gmres_max_iter=1000)
+    tr = ctx.set_trace(True)
+    info = ctx.step(1)[0]
+    assert info["solve"]["converged"]
+    Y1, q1, _ = ctx.get_state()
+    lay, Y, q = susp_layout(wl, 0)
+    Wt = philox.normals(seed, 0, 0, 1, 6 * lay.n_bodies)
+    ora = ogdc.gdc_step_fcm(lay, Y, q, Wt, fcm.Grid(N, L, SIGMA, 3.0), oracle_params(wl, rfd_delta=1e-3), seed, 0, 0)
+    assert np.abs(ora["FT"]).max() > 0.1
+    assert rel(_host(tr["FTm"]), ora["FT"]) < 1e-6      # x^m carries the FP32 grid's rounding through calV
+    assert rel(Y1 - Y, ora["Y1"] - Y) < 1e-4
+    assert rot_err(q1, ora["q1"]) < 1e-6
