@@ -288,9 +288,9 @@ def fcm_measure(g, torch, wl, ctx, N: int, reps: int = 3) -> dict:
     F.close()
     del F
     torch.cuda.empty_cache()
-    # one gDC step with the FCM mobility on the same bodies (no pair forces in the periodic cube)
+    # one gDC step with the FCM mobility on the same bodies in the periodic cube
     fctx = g.context_from_workload(wl, precision=g.FP64, rfd_delta=1e-3, gmres_tol=1e-4, gmres_max_iter=500,
-                                   mobility=g.MOB_FCM, box_L=L, fcm_N=N, rep_A=0.0, autotune=0)
+                                   mobility=g.MOB_FCM, box_L=L, fcm_N=N, autotune=0)
     fctx.step(1)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -302,8 +302,8 @@ def fcm_measure(g, torch, wl, ctx, N: int, reps: int = 3) -> dict:
                        "residual": inf["solve"]["residual"], "nu": inf["nu_min"],
                        "gmres_tol": 1e-4,
                        "note": "one timed step after one warm-up, host-driven (FCM steps are not graph-captured); "
-                               "the soft repulsion is off (pair forces are not periodic); GMRES to 1e-4 as in "
-                               "Sec. 6.2 (the FP32 grid's rounding, a few 1e-7 of the operator, sets the floor)"}
+                               "the workload's soft repulsion at minimum-image distances in the cube; GMRES to 1e-4 "
+                               "as in Sec. 6.2 (the FP32 grid's rounding, a few 1e-7 of the operator, sets the floor)"}
     fctx.close()
     del fctx
     out["note"] = ("M_FCM lambda, v-breve = J L^-1 D W (stress draw + 6 forward and 3 inverse 3-D FFTs) and the "

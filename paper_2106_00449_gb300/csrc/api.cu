@@ -85,6 +85,7 @@ static const char* validate_params(const gdc_params* p) {
                    "R_t within 15 grid spacings";
         if (forces_on(*p) && std::floor(p->box_L / (force_cutoff(*p) * (1.0 + 1e-4))) < 3.0)
             return "with the periodic FCM mobility the pair-force cutoff must fit 3 times in box_L";
+        if (p->shear_rate != 0.0) return "a background shear is not periodic: not available with the FCM mobility";
     }
     return nullptr;
 }

@@ -70,6 +70,7 @@ def test_workspace_checks_the_mobility_and_force_options_without_gpu(libpath):
     assert ws(g.Params(rep_A=4.0, **fcm)) > 0
     assert ws(g.Params(rep_A=4.0, **dict(fcm, box_L=15.0))) == 0
     assert ws(g.Params(potential=1, well_A=5.0, **fcm)) > 0          # wells: 3a + 6 lambda = 6a
+    assert ws(g.Params(shear_rate=1.0, **fcm)) == 0                 # linear shear is not periodic
     assert ws(g.Params(**dict(fcm, fcm_N=48))) == 0                 # not a power of two
     assert ws(g.Params(**dict(fcm, box_L=5.0))) == 0                # 3a truncation reaches the image
     assert ws(g.Params(mobility=2)) == 0
