@@ -74,7 +74,8 @@ typedef enum { GDC_SCHEME_GDC = 0, GDC_SCHEME_EM = 1 } gdc_scheme;
  * step's start (stress of (seed, 0, step), see gdc_fcm_*) and averaged again at every later
  * configuration of the step -- the perturbed states of step 3 and the mid-step (Sec. 5);
  * the RPY-only settings (Lanczos tolerances, pair kernels) are not used, all products use
- * the FP32-grid FCM operator whatever the precision (relative rounding a few 1e-7, so
+ * the FP32-grid FCM operator whatever the precision (GMRES then runs without refinement
+ * cycles and counts its products as matvecs_fp64; relative rounding a few 1e-7, so
  * gmres_tol should be 1e-5 or looser; Sec. 6.2 uses 1e-4), the block preconditioner uses
  * each template's FCM block (computed at init from 3 n_t FCM products), and steps run
  * host-driven. */

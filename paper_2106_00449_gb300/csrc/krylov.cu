@@ -348,7 +348,8 @@ __global__ void k_gm_backsolve(int S, int m, const double* __restrict__ H, const
 }
 
 gdc_status gmres_solve(gdc_ctx* c, const double* b, double* x, gdc_solve_info* info) {
-    const int prec = c->p.precision;
+    // FCM: one operator whatever the precision, so no refinement against a second product
+    const int prec = c->fcm ? GDC_FP64 : c->p.precision;
     const int m = c->m;
     const long long n = c->ngm;
     const gdc::Seg& sg = c->seg_gm;
