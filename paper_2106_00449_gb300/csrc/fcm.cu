@@ -3,9 +3,11 @@
 // envelopes on an N^3 grid cut off beyond R_t, a Fourier spectral Stokes solve, trapezoidal
 // averaging, and a fluctuating stress of six independent normals per grid point.
 //
-// GB300 layout: the grid work is bandwidth-bound, so it runs in FP32 (complex float2 grids,
-// nine of N^3 points: 0-2 the deterministic force / velocity, 3-8 the stress, whose last
-// three slots end up holding the fluctuating velocity u-breve, kept for re-averaging).
+// GB300 layout: the grid work is bandwidth-bound, so it runs in FP32 on complex float2 grids
+// of N^3 points, each holding two real fields as a + i b (their transforms are separated by
+// conjugate symmetry in the solve): 0-1 the force density, 2-3 its velocity, 4-6 the six
+// stress components, 7-8 the fluctuating velocity; the two velocities are then packed per
+// point (float4), and the fluctuating one is kept there for re-averaging.
 //   * spreading is a gather: a block takes the grid points of one binning cell (cells at
 //     least R_t wide) and stages the blobs of the 27 cells around it (blobs in ascending
 //     index) in shared memory as FP32 offsets from the cell's corner; it is deterministic and
@@ -254,18 +256,19 @@ __global__ void __launch_bounds__(128) k_fcm_spread(int N, double h, double L, i
 #pragma unroll
         for (int q = 0; q < PT; ++q)
             if (gi[q] >= 0) {
-                f[gi[q]] = make_float2(ax[q], 0.f);
-                f[NG + gi[q]] = make_float2(ay[q], 0.f);
-                f[2 * NG + gi[q]] = make_float2(az[q], 0.f);
+                f[gi[q]] = make_float2(ax[q], ay[q]);      // two real fields in one complex grid
+                f[NG + gi[q]] = make_float2(az[q], 0.f);
             }
     }
 }
 
 // The three real parts of a velocity's complex grids packed per point (x, y, z, 0).
+// The velocity (x, y, z, 0) per point from its packed complex grids (u_x + i u_y, u_z).
 __global__ void k_fcm_pack(long long NG, const float2* __restrict__ u, float4* __restrict__ out) {
     const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (g >= NG) return;
-    out[g] = make_float4(u[g].x, u[NG + g].x, u[2 * NG + g].x, 0.f);
+    const float2 a = u[g];
+    out[g] = make_float4(a.x, a.y, u[NG + g].x, 0.f);
 }
 
 // ---- FFT: radix-2 transforms of 16 pencils per block, one axis per pass -----------------
@@ -382,40 +385,70 @@ __device__ __forceinline__ void fcm_project(const Mode& m, float scale_eta, floa
     uz = make_float2((fz.x - m.kz * kfr) * inv, (fz.y - m.kz * kfi) * inv);
 }
 
-__global__ void k_fcm_solve(long long NG, int N, float kunit, float scale_eta, float2* __restrict__ u) {
+// Index of the mode -k.
+__device__ __forceinline__ long long fcm_mirror(long long g, int N) {
+    const int m = N - 1;
+    const int ix = (int)(g % N), iy = (int)((g / N) % N), iz = (int)(g / ((long long)N * N));
+    return ((N - ix) & m) + (long long)N * (((N - iy) & m) + (long long)N * ((N - iz) & m));
+}
+
+// The transforms A, B of two real fields from Z = FFT(a + i b) at k and -k:
+// A(k) = (Z(k) + conj Z(-k)) / 2, B(k) = (Z(k) - conj Z(-k)) / (2i).
+__device__ __forceinline__ void fcm_split(float2 zk, float2 zm, float2& A, float2& B) {
+    A = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+    B = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+}
+
+// A + i B for two transforms of real fields: the inverse transform gives a + i b.
+__device__ __forceinline__ float2 fcm_join(float2 A, float2 B) { return make_float2(A.x - B.y, A.y + B.x); }
+
+// f: FFT(f_x + i f_y), FFT(f_z); u: (u_x + i u_y, u_z) transforms, scaled for the inverse.
+__global__ void k_fcm_solve(long long NG, int N, float kunit, float scale_eta, const float2* __restrict__ f,
+                            float2* __restrict__ u) {
     const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (g >= NG) return;
     const Mode m = fcm_mode(g, N, kunit);
-    float2 ux = make_float2(0.f, 0.f), uy = ux, uz = ux;
-    if (m.keep) fcm_project(m, scale_eta, u[g], u[NG + g], u[2 * NG + g], ux, uy, uz);
-    u[g] = ux;
-    u[NG + g] = uy;
-    u[2 * NG + g] = uz;
+    float2 o0 = make_float2(0.f, 0.f), o1 = o0;
+    if (m.keep) {   // kept modes come in pairs k, -k (no Nyquist component)
+        const long long gm = fcm_mirror(g, N);
+        float2 fx, fy, ux, uy, uz;
+        fcm_split(f[g], f[gm], fx, fy);
+        fcm_project(m, scale_eta, fx, fy, f[NG + g], ux, uy, uz);
+        o0 = fcm_join(ux, uy);
+        o1 = uz;
+    }
+    u[g] = o0;
+    u[NG + g] = o1;
 }
 
 __device__ __forceinline__ float2 cadd3(float a, float2 x, float b, float2 y, float c, float2 z) {
     return make_float2(a * x.x + b * y.x + c * z.x, a * x.y + b * y.y + c * z.y);
 }
 
-// W: the six stress grids (xx, yy, zz, xy, xz, yz); the velocity goes to the last three.
-__global__ void k_fcm_solve_stress(long long NG, int N, float kunit, float scale_eta, float2* __restrict__ W) {
+// Z: FFT(W_xx + i W_yy), FFT(W_zz + i W_xy), FFT(W_xz + i W_yz); u as for k_fcm_solve.
+__global__ void k_fcm_solve_stress(long long NG, int N, float kunit, float scale_eta, const float2* __restrict__ Z,
+                                   float2* __restrict__ u) {
     const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (g >= NG) return;
     const Mode m = fcm_mode(g, N, kunit);
-    float2 ux = make_float2(0.f, 0.f), uy = ux, uz = ux;
+    float2 o0 = make_float2(0.f, 0.f), o1 = o0;
     if (m.keep) {
-        const float2 xx = W[g], yy = W[NG + g], zz = W[2 * NG + g];
-        const float2 xy = W[3 * NG + g], xz = W[4 * NG + g], yz = W[5 * NG + g];
+        const long long gm = fcm_mirror(g, N);
+        float2 xx, yy, zz, xy, xz, yz, ux, uy, uz;
+        fcm_split(Z[g], Z[gm], xx, yy);
+        fcm_split(Z[NG + g], Z[NG + gm], zz, xy);
+        fcm_split(Z[2 * NG + g], Z[2 * NG + gm], xz, yz);
         // (D W)_a = i k_b W_ab
         const float2 dx = cadd3(m.kx, xx, m.ky, xy, m.kz, xz);
         const float2 dy = cadd3(m.kx, xy, m.ky, yy, m.kz, yz);
         const float2 dz = cadd3(m.kx, xz, m.ky, yz, m.kz, zz);
         fcm_project(m, scale_eta, make_float2(-dx.y, dx.x), make_float2(-dy.y, dy.x), make_float2(-dz.y, dz.x), ux, uy,
                     uz);
+        o0 = fcm_join(ux, uy);
+        o1 = uz;
     }
-    W[3 * NG + g] = ux;
-    W[4 * NG + g] = uy;
-    W[5 * NG + g] = uz;
+    u[g] = o0;
+    u[NG + g] = o1;
 }
 
 // ---- fluctuating stress ---------------------------------------------------------------------
@@ -433,8 +466,10 @@ __global__ void k_fcm_stress(long long NG, unsigned long long seed, unsigned own
         const uint4 x = philox4x32_10(make_uint4((unsigned)(3 * g + q), owner, (unsigned)(step & 0xffffffffull), 2u), key);
         normals_f32(x, n[2 * q], n[2 * q + 1]);
     }
-#pragma unroll
-    for (int c = 0; c < 6; ++c) W[c * NG + g] = make_float2((c < 3 ? sd : so) * n[c], 0.f);
+    // three complex grids, two real components each: xx + i yy, zz + i xy, xz + i yz
+    W[g] = make_float2(sd * n[0], sd * n[1]);
+    W[NG + g] = make_float2(sd * n[2], so * n[3]);
+    W[2 * NG + g] = make_float2(so * n[4], so * n[5]);
 }
 
 // ---- averaging ------------------------------------------------------------------------------
@@ -629,11 +664,13 @@ gdc_status gdc_fcm_apply(gdc_fcm* f, int n, const double* r, const double* lambd
         ++f->n_launch, k_fcm_spread<4><<<dim3((unsigned)nc3, chunks), 128, 0, f->stream>>>(
             f->N, f->h, f->p.L, f->nc, f->pw, f->cnt, f->start, f->list, lambda, R2, i2, nrm, f->grid, f->NG);
     }
-    fft3(f, 0, 3, false);
+    // grids 0-1: FFT(f_x + i f_y), FFT(f_z); grids 2-3: the velocity's (u_x + i u_y, u_z)
+    fft3(f, 0, 2, false);
     ++f->n_launch, k_fcm_solve<<<ceil_div(f->NG, 256), 256, 0, f->stream>>>(
-        f->NG, f->N, (float)(2.0 * 3.141592653589793 / f->p.L), (float)(1.0 / ((double)f->NG * f->p.eta)), f->grid);
-    fft3(f, 0, 3, true);
-    fcm_pack(f, 0, 0);
+        f->NG, f->N, (float)(2.0 * 3.141592653589793 / f->p.L), (float)(1.0 / ((double)f->NG * f->p.eta)), f->grid,
+        f->grid + 2 * f->NG);
+    fft3(f, 2, 2, true);
+    fcm_pack(f, 2, 0);
     fcm_average_launch(f, n, r, 0, u);
     gdc_status st = fcm_check(f, cudaGetLastError(), "FCM launch");
     if (st == GDC_OK) st = fcm_check(f, cudaStreamSynchronize(f->stream), "FCM product");
@@ -648,14 +685,15 @@ gdc_status gdc_fcm_brownian(gdc_fcm* f, unsigned long long seed, unsigned int ow
         return fcm_fail(f, GDC_ERR_INVALID_ARG, "kT must be >= 0 and dt > 0");
     const double dv = f->h * f->h * f->h;
     const double sd = 2.0 * std::sqrt(kT * f->p.eta / (dv * dt)), so = std::sqrt(2.0 * kT * f->p.eta / (dv * dt));
+    // grids 4-6: the stress, two real components per complex grid; grids 7-8: (u_x + i u_y, u_z)
     ++f->n_launch, k_fcm_stress<<<ceil_div(f->NG, 256), 256, 0, f->stream>>>(f->NG, seed, owner, step, (float)sd,
-                                                                             (float)so, f->grid + 3 * f->NG);
-    fft3(f, 3, 6, false);
+                                                                             (float)so, f->grid + 4 * f->NG);
+    fft3(f, 4, 3, false);
     ++f->n_launch, k_fcm_solve_stress<<<ceil_div(f->NG, 256), 256, 0, f->stream>>>(
         f->NG, f->N, (float)(2.0 * 3.141592653589793 / f->p.L), (float)(1.0 / ((double)f->NG * f->p.eta)),
-        f->grid + 3 * f->NG);
-    fft3(f, 6, 3, true);
-    fcm_pack(f, 6, 1);
+        f->grid + 4 * f->NG, f->grid + 7 * f->NG);
+    fft3(f, 7, 2, true);
+    fcm_pack(f, 7, 1);
     f->have_field = true;
     fcm_average_launch(f, n, r, 1, v);
     gdc_status st = fcm_check(f, cudaGetLastError(), "FCM launch");
