@@ -147,3 +147,15 @@ def test_periodic_forces_are_the_sum_over_images():
     r2[lay.blob_body == 1] += np.array([box, -box, 0.0])
     np.testing.assert_allclose(forces.blob_forces(r2, lay.blob_body, U0 / B, B, 1.0, 2, AW, LAM, box=box), f,
                                atol=1e-12 * np.abs(f).max())
+
+
+@pytest.mark.parametrize("potential", [0, 1, 2])
+def test_matrix_free_rows_equal_the_dense_forces(potential):
+    """oracle.matfree.repulsion_rows (the sampled-row oracle of the full-size tests) gives the
+    rows of blob_forces, which the energy-gradient tests pin."""
+    from oracle import matfree
+    lay, Y, q, r = _three_bodies(seed=6 + potential)
+    f = _oracle(r, lay.blob_body, potential)
+    rows = np.array([0, 3, 5, r.shape[0] - 1])
+    got = matfree.repulsion_rows(r, lay.blob_body, rows, U0 / B, B, 1.0, potential, AW, LAM)
+    np.testing.assert_allclose(got, f[rows], atol=1e-13 * np.abs(f).max())
