@@ -43,7 +43,7 @@ WORKLOAD_C4 = ("c4: 512 independent suspensions of 8-128 bodies (12-blob icosahe
                "every suspension once")
 WORKLOAD_C5 = ("c5: 16,384 rods of 20 collinear blobs, 327,680 blobs, 8% volume fraction in a 257.9a cube, "
                "linear shear u = (y, 0, 0), dt 0.002, soft repulsion")
-FLOPS_PER_PAIR = 33.0          # algorithmic flops of one far-field RPY pair (FMA = 2), see the design doc
+FLOPS_PER_PAIR = 33.0          # algorithmic flops of one far-field RPY pair (FMA = 2): d 3, r^2 5, r^-2 1, r^-3 1, A 2, B 3, d.lambda 5, s 1, sums 12
 FP32_LANES_PER_SM = 128
 
 
