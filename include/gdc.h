@@ -139,6 +139,13 @@ typedef struct {
     int    fcm_N;          /* GDC_MOB_FCM: grid points per side (power of two, 16..512)  */
     double fcm_sigma;      /* GDC_MOB_FCM: envelope width; 0 = a / sqrt(pi)             */
     double fcm_R_t;        /* GDC_MOB_FCM: envelope truncation radius; 0 = 3a          */
+    int    lanczos_precond; /* M^(1/2) W by Lanczos (Sec. 4.1): 1 builds the Krylov space of the
+                              block-preconditioned operator A = L^-1 M L^-T of Chow & Saad, with
+                              L = diag_p(R(q_p)-hat L_t) and L_t the Cholesky factor of the
+                              template's RPY block (L L^T = the body blocks of M), and
+                              returns L A^(1/2) W; 0 uses M itself and returns its symmetric
+                              root M^(1/2) W.  Both roots S satisfy S S^T = M, so v-breve has
+                              the covariance (2 kT / dt) M either way; 1 needs fewer products */
 } gdc_params;
 
 typedef struct {

@@ -1,8 +1,10 @@
 """Oracle gDC time step (Sec. 3) and Euler-Maruyama step (App. D).  TEST INFRASTRUCTURE ONLY.
 
 Everything is dense FP64 for one suspension: M is assembled, its square root
-is taken by eigendecomposition (the symmetric root that Lanczos converges to)
-or by Cholesky, the saddle point is solved by LU, and step 2 is solved as
+is taken densely -- by default L (L^-1 M L^-T)^(1/2) with the body-block Cholesky
+factor L (the root that block-preconditioned Lanczos converges to), or the
+symmetric root (eigendecomposition, the limit of unpreconditioned Lanczos), or
+the Cholesky factor of M -- the saddle point is solved by LU, and step 2 is solved as
 the least-squares problem it is.  The random vectors W (3M normals) and
 W-tilde (6N normals) are inputs, so the same draws can be fed to any
 implementation.
@@ -12,6 +14,10 @@ Readings of points the paper leaves open (each is also listed with the design no
 * Y_p is the blob centroid (templates are centred on it).
 * The Brownian slip velocity is v-breve = sqrt(2 kT / dt) M^(1/2) W with the
   same W at the start and at the mid-step (Eqs. unconst and step5).
+* M^(1/2) W (Eq. v_brown_RMB) is taken, as Sec. 4.1 does, by Lanczos in the
+  preconditioned form of Chow & Saad, whose limit is L (L^-1 M L^-T)^(1/2) W with
+  L the body-block Cholesky factor of rigid.block_factor: a square root of M
+  (S S^T = M) that moves with each body's rotation.
 * RFD (Eq. rfd_div with the footnote's L_p): the perturbed state is
   Y + delta L_p W~_t, exp(delta W~_r) * q; the estimator is
   sum_p [W~_t . (V~_t - V_t) / (delta L_p) + W~_r . (V~_r - V_r) / delta],
@@ -30,7 +36,7 @@ import dataclasses
 
 import numpy as np
 
-from . import forces, geometry, rigid, rpy
+from . import forces, geometry, lanczos, rigid, rpy
 
 
 @dataclasses.dataclass
@@ -46,7 +52,9 @@ class Params:
     well_A: float = 0.0         # Gaussian well amplitude (Sec. 6.4: 5 kT)
     well_lambda: float = 0.5    # Gaussian well width, a length (Sec. 6.4: 0.5 a)
     shear_rate: float = 0.0
-    sqrt_mode: str = "sym"      # "sym" (eigh) or "chol"
+    sqrt_mode: str = "block"    # "block" (preconditioned Lanczos root), "sym" (eigh) or "chol"
+    lanczos_tol: float = 0.0    # 0: the dense root of sqrt_mode; > 0: the Lanczos iterate at that tolerance
+    lanczos_max_iter: int = 128
 
     @classmethod
     def from_dict(cls, d: dict) -> "Params":
@@ -58,24 +66,55 @@ def _lengths(layout: geometry.Layout, a: float) -> np.ndarray:
     return np.where(layout.L > 0.0, layout.L, a)
 
 
-def sqrt_apply(M: np.ndarray, W: np.ndarray, mode: str) -> np.ndarray:
-    S = rigid.sqrtm_sym(M) if mode == "sym" else rigid.sqrtm_chol(M)
+def sqrt_apply(M: np.ndarray, W: np.ndarray, mode: str, L: np.ndarray = None) -> np.ndarray:
+    """S W for the square root S of M named by mode (S S^T = M in every mode)."""
+    if mode == "sym":
+        S = rigid.sqrtm_sym(M)
+    elif mode == "chol":
+        S = rigid.sqrtm_chol(M)
+    elif mode == "block":
+        S = rigid.sqrtm_block(M, L)
+    else:
+        raise ValueError(mode)
     return S @ W
 
 
-def brownian_slip(layout, Y, q, W, p: Params):
-    """Blob positions, M, K, B and v-breve = sqrt(2kT/dt) M^(1/2) W at state (Y, q)."""
+def brownian_slip_k(layout, Y, q, W, p: Params, fixed_k: int = None):
+    """Blob positions, M, K, B, v-breve = sqrt(2kT/dt) M^(1/2) W at state (Y, q), and the
+    Lanczos iteration count (None for a dense root).
+
+    With p.lanczos_tol > 0 the root is the Lanczos iterate of lanczos.py at that tolerance
+    (or with exactly fixed_k iterations) on the operator of sqrt_mode: A = L^-1 M L^-T with
+    the result multiplied by L ("block"), or M itself ("sym")."""
     r = geometry.blob_positions(layout, Y, q)
     M = rpy.rpy_matrix(r, p.a, p.eta)
     K = rigid.k_matrix(r, Y, layout.blob_body)
     B = rigid.rigid_basis(K, layout.n_bodies)
-    vb = np.sqrt(2.0 * p.kT / p.dt) * sqrt_apply(M, W, p.sqrt_mode)
-    return r, M, K, B, vb
+    L = rigid.block_factor(layout, q, p.a, p.eta) if p.sqrt_mode == "block" else None
+    scale = np.sqrt(2.0 * p.kT / p.dt)
+    k = None
+    if p.lanczos_tol > 0.0 and p.sqrt_mode in ("block", "sym"):
+        if p.sqrt_mode == "block":
+            Linv = np.linalg.inv(L)
+            A = Linv @ M @ Linv.T
+            y, k, _ = lanczos.lanczos_sqrt(0.5 * (A + A.T), W, p.lanczos_tol, p.lanczos_max_iter, fixed_k)
+            vb = scale * (L @ y)
+        else:
+            y, k, _ = lanczos.lanczos_sqrt(M, W, p.lanczos_tol, p.lanczos_max_iter, fixed_k)
+            vb = scale * y
+    else:
+        vb = scale * sqrt_apply(M, W, p.sqrt_mode, L)
+    return r, M, K, B, vb, k
 
 
-def projected_velocity(layout, Y, q, W, p: Params) -> np.ndarray:
+def brownian_slip(layout, Y, q, W, p: Params):
+    """Blob positions, M, K, B and v-breve = sqrt(2kT/dt) M^(1/2) W at state (Y, q)."""
+    return brownian_slip_k(layout, Y, q, W, p)[:5]
+
+
+def projected_velocity(layout, Y, q, W, p: Params, fixed_k: int = None) -> np.ndarray:
     """Step 2: the least-squares rigid velocity of v-breve at state (Y, q), shape (N, 6)."""
-    _, _, K, B, vb = brownian_slip(layout, Y, q, W, p)
+    _, _, K, B, vb, _ = brownian_slip_k(layout, Y, q, W, p, fixed_k)
     return rigid.lsq_velocity(K, B, vb).reshape(-1, 6)
 
 
@@ -122,7 +161,7 @@ def fd_divergence(layout, Y, q, W, calV, p: Params, project=None) -> float:
 
 def midpoint_solve(layout, Ym, qm, W, p: Params):
     """Step 5: full mobility solve at the mid-step with the same W (Eq. step5)."""
-    r, M, K, B, vb = brownian_slip(layout, Ym, qm, W, p)
+    r, M, K, B, vb, k = brownian_slip_k(layout, Ym, qm, W, p)
     f = forces.blob_forces(r, layout.blob_body, p.rep_A, p.rep_b, p.a, p.potential, p.well_A, p.well_lambda)
     FT = forces.body_force_torque(r, Ym, layout.blob_body, f)
     slip = vb.copy()
@@ -131,19 +170,23 @@ def midpoint_solve(layout, Ym, qm, W, p: Params):
         uinf[:, 0] = p.shear_rate * r[:, 1]
         slip = slip + uinf.reshape(-1)
     lam, V = rigid.saddle_solve(M, K, B, slip, FT)
-    return dict(r=r, M=M, K=K, B=B, vb=vb, FT=FT, slip=slip, lam=lam, V=V.reshape(-1, 6))
+    return dict(r=r, M=M, K=K, B=B, vb=vb, FT=FT, slip=slip, lam=lam, V=V.reshape(-1, 6), k_mid=k)
 
 
 def gdc_step(layout, Y, q, W, Wt, p: Params, div: str = "rfd") -> dict:
     """One gDC step (Sec. 3, steps 2-6) from (Y, q) with given W (3M) and W-tilde (6N)."""
     # step 2
-    r0, M0, K0, B0, vb0 = brownian_slip(layout, Y, q, W, p)
+    r0, M0, K0, B0, vb0, k0 = brownian_slip_k(layout, Y, q, W, p)
     calV = rigid.lsq_velocity(K0, B0, vb0).reshape(-1, 6)
-    # step 3
+    # step 3: the perturbed Lanczos runs take the iteration count of the run at x^n
+
+    def project(Ys, qs):
+        return projected_velocity(layout, Ys, qs, W, p, fixed_k=k0)
+
     if div == "rfd":
-        dv = rfd_divergence(layout, Y, q, W, Wt, calV, p)
+        dv = rfd_divergence(layout, Y, q, W, Wt, calV, p, project)
     elif div == "fd":
-        dv = fd_divergence(layout, Y, q, W, calV, p)
+        dv = fd_divergence(layout, Y, q, W, calV, p, project)
     else:
         raise ValueError(div)
     nu = 1.0 + 0.5 * p.dt * dv
@@ -153,7 +196,7 @@ def gdc_step(layout, Y, q, W, Wt, p: Params, div: str = "rfd") -> dict:
     mid = midpoint_solve(layout, Ym, qm, W, p)
     # step 6
     Y1, q1 = geometry.advance(Y, q, mid["V"], nu * p.dt)
-    return dict(r0=r0, vb0=vb0, calV=calV, div=dv, nu=nu, Ym=Ym, qm=qm, Y1=Y1, q1=q1, **mid)
+    return dict(r0=r0, vb0=vb0, calV=calV, div=dv, nu=nu, Ym=Ym, qm=qm, Y1=Y1, q1=q1, k0=k0, **mid)
 
 
 def gdc_step_fcm(layout, Y, q, Wt, grid, p: Params, seed: int, susp: int, step: int, div: str = "rfd") -> dict:

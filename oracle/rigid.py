@@ -16,7 +16,8 @@ from __future__ import annotations
 
 import numpy as np
 
-from .geometry import cross_matrix
+from . import rpy
+from .geometry import cross_matrix, rotation_matrix
 
 
 def k_matrix(r: np.ndarray, Y: np.ndarray, blob_body: np.ndarray) -> np.ndarray:
@@ -117,3 +118,42 @@ def sqrtm_sym(M: np.ndarray) -> np.ndarray:
 def sqrtm_chol(M: np.ndarray) -> np.ndarray:
     """Lower Cholesky factor L with L L^T = M (another valid M^(1/2), Eq. v_brown_RMB)."""
     return np.linalg.cholesky(M)
+
+
+def block_factor(layout, q: np.ndarray, a: float, eta: float) -> np.ndarray:
+    """The block-diagonal factor L = diag_p(R-hat_p L_t(p)) of the body blocks of M.
+
+    L_t is the lower Cholesky factor of the template's RPY block in the body frame
+    (L_t L_t^T = M_t, Sec. 4.1 blob mobility at the template's own blob positions) and
+    R-hat_p = diag(R(q_p), ..., R(q_p)) rotates each blob of body p (Eq.
+    quaternion_rotation_matrix).  Because RPY is rotation covariant and intra-body
+    distances are fixed, L_p L_p^T = R-hat_p M_t R-hat_p^T is body p's diagonal block of M:
+    L L^T is the block-diagonal preconditioner matrix of Sec. 2.2 (without the K rows).
+    """
+    n3 = 3 * layout.n_blobs
+    L = np.zeros((n3, n3))
+    chol = {}
+    for p in range(layout.n_bodies):
+        t = int(layout.body_tmpl[p])
+        if t not in chol:
+            chol[t] = np.linalg.cholesky(rpy.rpy_matrix(layout.templates[t], a, eta))
+        nb = layout.templates[t].shape[0]
+        Rhat = np.kron(np.eye(nb), rotation_matrix(q[p]))
+        i0, i1 = 3 * layout.blob_off[p], 3 * layout.blob_off[p + 1]
+        L[i0:i1, i0:i1] = Rhat @ chol[t]
+    return L
+
+
+def sqrtm_block(M: np.ndarray, L: np.ndarray) -> np.ndarray:
+    """S = L (L^-1 M L^-T)^(1/2): the square root that preconditioned Lanczos converges to.
+
+    Sec. 4.1 takes M^(1/2) W by the Lanczos method of Chow & Saad, who precondition the
+    Krylov space with a factor L of an approximation L L^T of M: Lanczos then builds the
+    Krylov space of A = L^-1 M L^-T from W and returns L A^(1/2) W.  S S^T = L A L^T = M,
+    so v-breve has the covariance of Eq. v_brown_RMB whatever L is.  Here L is
+    block_factor's body-block factor.
+    """
+    Linv = np.linalg.inv(L)
+    A = Linv @ M @ Linv.T
+    A = 0.5 * (A + A.T)
+    return L @ sqrtm_sym(A)

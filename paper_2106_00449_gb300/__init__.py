@@ -64,7 +64,7 @@ class _Params(ctypes.Structure):
                 ("pair_kernel", ctypes.c_int), ("potential", ctypes.c_int), ("well_A", ctypes.c_double),
                 ("well_lambda", ctypes.c_double), ("force_method", ctypes.c_int), ("mobility", ctypes.c_int),
                 ("box_L", ctypes.c_double), ("fcm_N", ctypes.c_int), ("fcm_sigma", ctypes.c_double),
-                ("fcm_R_t", ctypes.c_double)]
+                ("fcm_R_t", ctypes.c_double), ("lanczos_precond", ctypes.c_int)]
 
 
 class _FcmParams(ctypes.Structure):
@@ -129,6 +129,7 @@ class Params:
     fcm_N: int = 0
     fcm_sigma: float = 0.0   # 0: a / sqrt(pi)
     fcm_R_t: float = 0.0     # 0: 3a
+    lanczos_precond: int = 1  # 1: block-preconditioned Lanczos (root L (L^-1 M L^-T)^(1/2)), 0: M^(1/2)
 
     def _c(self) -> _Params:
         return _Params(**{f.name: getattr(self, f.name) for f in dataclasses.fields(self)})

@@ -63,6 +63,7 @@ static const char* validate_params(const gdc_params* p) {
     if (p->gmres_restart < 2 || p->gmres_restart > GDC_MAX_RESTART) return "gmres_restart must be in [2, 100]";
     if (!(p->lanczos_tol > 0.0) || !(p->lanczos_tol < 1.0)) return "lanczos_tol must be in (0, 1)";
     if (p->lanczos_max_iter < 2 || p->lanczos_max_iter > GDC_MAX_LANCZOS) return "lanczos_max_iter must be in [2, 128]";
+    if (p->lanczos_precond != 0 && p->lanczos_precond != 1) return "lanczos_precond must be 0 or 1";
     if (!(p->rfd_delta > 0.0) || !(p->rfd_delta < 1.0)) return "rfd_delta must be in (0, 1)";
     if (p->precision != GDC_FP64 && p->precision != GDC_FP32_MIXED) return "unknown precision";
     if (p->divmode != GDC_DIV_RFD && p->divmode != GDC_DIV_FD) return "unknown divmode";
@@ -196,6 +197,9 @@ static size_t carve(gdc_ctx* c, void* base) {
     c->tmpl_N = w.take<double>(36 * T);
     c->tmpl_KtKp = w.take<double>(36 * T);
     c->tmpl_work = w.take<double>(2 * c->h_minv_off[T]);
+    c->tmpl_LT = w.take<double>(c->h_minv_off[T]);
+    c->tmpl_X = w.take<double>(c->h_minv_off[T]);
+    c->tmpl_XT = w.take<double>(c->h_minv_off[T]);
     c->body_L = w.take<double>(NB);
     c->Rb = w.take<double>(9 * NB);
     c->r = w.take<double>(3 * NBL);
@@ -272,6 +276,8 @@ static size_t carve(gdc_ctx* c, void* base) {
     c->lz_active = w.take<int>(S);
     c->lz_k = w.take<int>(S);
     c->lz_fix = w.take<int>(S);
+    c->lz_z = w.take<double>(nl);
+    c->lz_u = w.take<double>(nl);
     c->seg_gm.chunks = w.take<Chunk>(c->seg_gm.n_chunks);
     c->seg_gm.seg_chunk_off = w.take<int>(S + 1);
     c->seg_gm.off = c->susp_gm_off;

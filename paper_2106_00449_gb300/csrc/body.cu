@@ -343,6 +343,92 @@ void launch_precond(gdc_ctx* c, const double* r, double* z) {
                                                c->body_gm, c->Rb, r, z);
 }
 
+// ---- factors of the body blocks: block-preconditioned Lanczos (Sec. 4.1, Chow & Saad) ----
+//
+// With L_t the Cholesky factor of the template block (M_t = L_t L_t^T), L_p = R-hat_p L_t
+// factors body p's block of M (M_pp = R-hat_p M_t R-hat_p^T), and the Lanczos operator of
+// Chow & Saad is A = L^-1 M L^-T with L = diag_p(L_p):
+//   TRI_LINV_T: out_p = L_p^-T x_p = R-hat_p (L_t^-T x_p)
+//   TRI_LINV:   out_p = L_p^-1 x_p (+ add_p) = L_t^-1 (R-hat_p^T x_p) (+ add_p)
+//   TRI_L:      out_p = L_p x_p = R-hat_p (L_t x_p)
+// F is the template's factor stored so that out_i = sum_k F[k n3 + i] in_k (coalesced over
+// the rows i); the triangular structure limits k to [i, n3) (TRI_LINV_T) or [0, i].  FP64.
+// One block per body; x, add and out hold 3 doubles per blob.  Shared memory: 2 x 3n doubles.
+template <int MODE>
+__global__ void __launch_bounds__(128) k_body_tri(const long long* __restrict__ body_blob_off,
+                                                  const int* __restrict__ body_tmpl, const int* __restrict__ tmpl_n,
+                                                  const long long* __restrict__ minv_off, const double* __restrict__ F,
+                                                  const double* __restrict__ Rb, const double* __restrict__ x,
+                                                  const double* __restrict__ add, double* __restrict__ out) {
+    extern __shared__ double sh[];
+    const int p = blockIdx.x;
+    const int t = body_tmpl[p];
+    const int n = tmpl_n[t], n3 = 3 * n;
+    double* in = sh;
+    double* res = sh + n3;
+    const double* R = Rb + 9 * p;
+    const long long i0 = body_blob_off[p];
+    for (int b = threadIdx.x; b < n; b += blockDim.x) {
+        double v[3] = {x[3 * (i0 + b)], x[3 * (i0 + b) + 1], x[3 * (i0 + b) + 2]};
+        if (MODE == TRI_LINV) {
+            double w[3];
+            rotT(R, v, w);
+            v[0] = w[0];
+            v[1] = w[1];
+            v[2] = w[2];
+        }
+        in[3 * b] = v[0];
+        in[3 * b + 1] = v[1];
+        in[3 * b + 2] = v[2];
+    }
+    __syncthreads();
+    const double* Ft = F + minv_off[t];
+    for (int i = threadIdx.x; i < n3; i += blockDim.x) {
+        const int k0 = MODE == TRI_LINV_T ? i : 0, k1 = MODE == TRI_LINV_T ? n3 : i + 1;
+        double a0 = 0.0, a1 = 0.0;
+        int k = k0;
+        for (; k + 1 < k1; k += 2) {
+            a0 = fma(Ft[(long long)k * n3 + i], in[k], a0);
+            a1 = fma(Ft[(long long)(k + 1) * n3 + i], in[k + 1], a1);
+        }
+        if (k < k1) a0 = fma(Ft[(long long)k * n3 + i], in[k], a0);
+        res[i] = a0 + a1;
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < n; b += blockDim.x) {
+        double w[3] = {res[3 * b], res[3 * b + 1], res[3 * b + 2]};
+        if (MODE != TRI_LINV) {
+            double v[3];
+            rot(R, w, v);
+            w[0] = v[0];
+            w[1] = v[1];
+            w[2] = v[2];
+        }
+        const long long o = 3 * (i0 + b);
+        if (add) {
+            w[0] += add[o];
+            w[1] += add[o + 1];
+            w[2] += add[o + 2];
+        }
+        out[o] = w[0];
+        out[o + 1] = w[1];
+        out[o + 2] = w[2];
+    }
+}
+
+void launch_body_tri(gdc_ctx* c, int mode, const double* x, const double* add, double* out) {
+    const size_t smem = (size_t)(2 * 3 * c->max_body_blobs) * sizeof(double);
+    if (mode == TRI_LINV_T)
+        ++c->n_launch, k_body_tri<TRI_LINV_T><<<c->NB, 128, smem, c->stream>>>(
+            c->body_blob_off, c->body_tmpl, c->tmpl_n, c->minv_off, c->tmpl_X, c->Rb, x, add, out);
+    else if (mode == TRI_LINV)
+        ++c->n_launch, k_body_tri<TRI_LINV><<<c->NB, 128, smem, c->stream>>>(
+            c->body_blob_off, c->body_tmpl, c->tmpl_n, c->minv_off, c->tmpl_XT, c->Rb, x, add, out);
+    else
+        ++c->n_launch, k_body_tri<TRI_L><<<c->NB, 128, smem, c->stream>>>(
+            c->body_blob_off, c->body_tmpl, c->tmpl_n, c->minv_off, c->tmpl_LT, c->Rb, x, add, out);
+}
+
 // ---- per-template setup (once, at init) -------------------------------------------------
 
 // Cyclic Jacobi eigendecomposition of a symmetric 6x6 (Golub & Van Loan, Sec. 8.5), then the
@@ -404,7 +490,8 @@ __global__ void k_template_setup(const int* __restrict__ tmpl_n, const int* __re
                                  const long long* __restrict__ minv_off, const double* __restrict__ xyz,
                                  double a, double eta, double* __restrict__ Minv, double* __restrict__ Gt,
                                  double* __restrict__ Nt, double* __restrict__ KtKp, double* __restrict__ work,
-                                 double* __restrict__ Mt, const double* __restrict__ Mext, int* __restrict__ status) {
+                                 double* __restrict__ Mt, const double* __restrict__ Mext, int* __restrict__ status,
+                                 double* __restrict__ LT, double* __restrict__ Xo, double* __restrict__ XT) {
     const int t = blockIdx.x;
     const int n = tmpl_n[t];
     const int n3 = 3 * n;
@@ -475,6 +562,12 @@ __global__ void k_template_setup(const int* __restrict__ tmpl_n, const int* __re
         double acc = 0.0;
         for (int k = max(i, j); k < n3; ++k) acc += X[(long long)k * n3 + i] * X[(long long)k * n3 + j];
         Mi[e] = acc;
+        // the factors for the preconditioned Lanczos operator (L lower; its upper part still
+        // holds M and is not part of the factor; X = L^-1 is lower with zeros above)
+        const long long o = minv_off[t] + e;
+        LT[o] = j >= i ? L[(long long)j * n3 + i] : 0.0;
+        Xo[o] = X[e];
+        XT[o] = X[(long long)j * n3 + i];
     }
     __syncthreads();
     // 4. G = M^-1 K_t (3n x 6): K_t columns are unit translations and rotations e_b x b_i
@@ -535,7 +628,7 @@ __global__ void k_template_setup(const int* __restrict__ tmpl_n, const int* __re
 void launch_template_setup(gdc_ctx* c, const double* Mext) {
     ++c->n_launch, k_template_setup<<<c->T, 256, 0, c->stream>>>(c->tmpl_n, c->tmpl_off, c->minv_off, c->tmpl_xyz, c->p.a, c->p.eta,
                                                   c->tmpl_Minv, c->tmpl_G, c->tmpl_N, c->tmpl_KtKp, c->tmpl_work,
-                                                  c->tmpl_M, Mext, c->dev_status);
+                                                  c->tmpl_M, Mext, c->dev_status, c->tmpl_LT, c->tmpl_X, c->tmpl_XT);
     const long long nm = c->h_minv_off[c->T];
     ++c->n_launch, k_round_f32<<<(int)std::min<long long>(ceil_div(nm, 256), 1024), 256, 0, c->stream>>>(nm, c->tmpl_M,
                                                                                                       c->tmpl_M32);

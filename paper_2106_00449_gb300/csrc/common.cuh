@@ -126,6 +126,10 @@ struct gdc_ctx {
     double *tmpl_xyz = 0, *tmpl_L = 0;
     double *tmpl_Minv = 0, *tmpl_G = 0, *tmpl_N = 0, *tmpl_KtKp = 0, *tmpl_work = 0, *tmpl_M = 0;
     float* tmpl_M32 = 0;          // tmpl_M rounded to FP32 (intra-body block of the FP32 products)
+    // factors of the template blocks M_t = L_t L_t^T for the block-preconditioned Lanczos
+    // operator, each stored as F with (F-product)_i = sum_k F[k n3 + i] x_k (reads along rows):
+    // tmpl_LT = L_t^T (products with L_t), tmpl_X = L_t^-1 (with L_t^-T), tmpl_XT = L_t^-T (with L_t^-1)
+    double *tmpl_LT = 0, *tmpl_X = 0, *tmpl_XT = 0;
     // fluctuating FCM mobility (fcm.cu), GDC_MOB_FCM only
     gdc_fcm* fcm = nullptr;
     double* fcm_u = nullptr;      // M_FCM lambda, 3 per blob
@@ -170,6 +174,7 @@ struct gdc_ctx {
     double *lz_h = 0, *lz_Wnorm = 0, *lz_err = 0, *lz_scal = 0;
     int *lz_active = 0, *lz_k = 0, *lz_fix = 0, *lz_lastk = 0;
     int* lz_hint = 0;             // per suspension: index the previous unconstrained run stopped at (0 = none)
+    double *lz_z = 0, *lz_u = 0;  // preconditioned operator: L^-T x and the product at it (3 per blob)
 
     // reductions
     gdc::Seg seg_gm, seg_lz, seg_body;
@@ -322,7 +327,8 @@ void launch_scatter_solution(gdc_ctx* c, const double* x, double* V, double* lam
 // rpy.cu
 void launch_pack_lambda(gdc_ctx* c, int prec, const double* x, int gm_layout);
 void launch_rpy(gdc_ctx* c, int prec);
-void launch_rpy_epilogue(gdc_ctx* c, int prec, const double* x, double* y, int gm_layout);
+void launch_rpy_epilogue(gdc_ctx* c, int prec, const double* x, double* y, int gm_layout,
+                         bool same_body = true);   // same_body = false: blocks between different bodies only (FP32)
 void launch_forces_pair(gdc_ctx* c, int prec, double* fblob);
 void launch_forces_cell(gdc_ctx* c, int prec, double* fblob);
 void launch_near_cell(gdc_ctx* c);   // near-pair lists from a cell list (cells.cu)
@@ -354,6 +360,10 @@ void launch_precond(gdc_ctx* c, const double* r, double* z);
 void launch_intra_body(gdc_ctx* c, const double* x, double* y, int gm);
 void launch_intra_body32(gdc_ctx* c, const double* x, double* y, int gm);
 void launch_template_setup(gdc_ctx* c, const double* Mext = nullptr);   // Mext: given template blocks
+// per-body products with the template-block factors L_p = R-hat_p L_t (block-preconditioned
+// Lanczos): mode 0 out = L_p^-T x, mode 1 out = L_p^-1 x (+ add), mode 2 out = L_p x
+enum { TRI_LINV_T = 0, TRI_LINV = 1, TRI_L = 2 };
+void launch_body_tri(gdc_ctx* c, int mode, const double* x, const double* add, double* out);
 
 // krylov.cu
 gdc_status saddle_op(gdc_ctx* c, int prec, const double* x, double* y);

@@ -5,8 +5,8 @@
 // are segmented per suspension.  Reductions are two-pass (per-chunk partials, then a
 // fixed-order sum per segment), so results are bitwise reproducible run to run.
 //
-// Precision: bases, inner products and Givens/Hessenberg are FP64; the small tridiagonal
-// eigenproblem of Lanczos is FP64 for tolerances below 1e-5 and FP32 otherwise.  In
+// Precision: bases, inner products, Givens/Hessenberg and the small tridiagonal
+// eigenproblem of Lanczos are FP64.  In
 // GDC_FP32_MIXED mode the operator inside the Krylov loop uses the FP32 pair kernel; each
 // GMRES cycle ends with an accurate residual (double-float pairs, FP64 same-body blocks),
 // and the solver restarts from it until that residual meets gmres_tol (iterative refinement).
@@ -259,6 +259,39 @@ gdc_status saddle_op(gdc_ctx* c, int prec, const double* x, double* y) {
     return GDC_OK;
 }
 
+// The operator whose Krylov space Lanczos builds (Sec. 4.1): M, or with lanczos_precond the
+// block-preconditioned A = L^-1 M L^-T of Chow & Saad, L = diag_p(L_p) with L_p L_p^T = M_pp.
+// Since L_p^-1 M_pp L_p^-T = I, an FP32 product takes A x = x + L^-1 M_off L^-T x with M_off
+// the blocks between different bodies (the FP32 product without its same-body blocks), so
+// the body blocks of A are the identity exactly; FP64 forms L^-1 (M (L^-T x)).
+static void lz_operator(gdc_ctx* c, int prec, const double* x, double* w) {
+    if (!c->p.lanczos_precond) {
+        rpy_op(c, prec, x, w);
+        return;
+    }
+    launch_body_tri(c, TRI_LINV_T, x, nullptr, c->lz_z);
+    if (prec == GDC_FP32_MIXED) {
+        launch_pack_lambda(c, prec, c->lz_z, 0);
+        launch_rpy(c, prec);
+        launch_rpy_epilogue(c, prec, c->lz_z, c->lz_u, 0, false);
+        launch_body_tri(c, TRI_LINV, c->lz_u, x, w);
+    } else {
+        rpy_op(c, prec, c->lz_z, c->lz_u);
+        launch_body_tri(c, TRI_LINV, c->lz_u, nullptr, w);
+    }
+}
+
+// out = scale * V c, and with lanczos_precond the factor L applied to it: L A^(1/2) W
+static void lz_result(gdc_ctx* c, double scale, double* out) {
+    const gdc::Seg& sg = c->seg_lz;
+    const long long n = 3LL * c->NBL;
+    double* comb = c->p.lanczos_precond ? c->lz_w : out;
+    ++c->n_launch, k_fill<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(c->S, scale, c->lz_scal);
+    ++c->n_launch, k_combine<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_V, n, c->lz_k, c->lz_c, c->kmax,
+                                                                 c->lz_scal, comb);
+    if (c->p.lanczos_precond) launch_body_tri(c, TRI_L, comb, nullptr, out);
+}
+
 static gdc_status sync_read(gdc_ctx* c, const void* dev, void* host, size_t bytes) {
     cudaError_t e = cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -490,27 +523,13 @@ static_assert(GDC_MAX_LANCZOS <= 128, "a lane owns at most 4 rows of Q");
 // Row stride of Q in shared memory: odd, so that the lanes' rows fall in distinct banks.
 __host__ __device__ inline int lz_ldq(int kmax) { return kmax | 1; }
 
-// Dynamic shared memory of k_lz_tridiag: four c vectors (doubles), then Q.
-static size_t lz_tridiag_smem(int kmax, bool eig32) {
-    return (size_t)4 * kmax * sizeof(double) + (size_t)kmax * lz_ldq(kmax) * (eig32 ? sizeof(float) : sizeof(double));
+// Dynamic shared memory of k_lz_tridiag: four c vectors, then Q (all FP64).
+static size_t lz_tridiag_smem(int kmax) {
+    return (size_t)4 * kmax * sizeof(double) + (size_t)kmax * lz_ldq(kmax) * sizeof(double);
 }
 
-// Givens rotation (c, s) with c x + s z = r, -s x + c z = 0.  The FP32 eigen-step takes
-// 1/r from the hardware reciprocal square root (one rounding of about 1 ulp, the size of
-// the correctly rounded quotient's); FP64 divides by the correctly rounded square root.
-__device__ inline void lz_givens(float x, float z, float& c, float& s, float& r) {
-    const float r2 = fmaf(x, x, z * z);
-    if (r2 > 0.f) {
-        const float ri = rsqrtf(r2);
-        c = x * ri;
-        s = z * ri;
-        r = r2 * ri;
-    } else {
-        c = 1.f;
-        s = 0.f;
-        r = 0.f;
-    }
-}
+// Givens rotation (c, s) with c x + s z = r, -s x + c z = 0, dividing by the correctly
+// rounded square root.
 __device__ inline void lz_givens(double x, double z, double& c, double& s, double& r) {
     r = sqrt(x * x + z * z);
     if (r > 0.0) {
@@ -523,13 +542,13 @@ __device__ inline void lz_givens(double x, double z, double& c, double& s, doubl
     }
 }
 
-// out[0..k) = wn * T_k^(1/2) e_1 for the k x k tridiagonal (al, be), computed in precision T
-// by the whole warp; Q is k x k in shared memory with row stride ldq.  Returns false (on
-// every lane) when the QR iteration does not converge.
-template <typename T>
-__device__ bool lz_sqrt_e1_t(const double* al, const double* be, int k, double wn, T* Q, int ldq, double* out) {
+// out[0..k) = wn * T_k^(1/2) e_1 for the k x k tridiagonal (al, be), computed in FP64 by
+// the whole warp; Q is k x k in shared memory with row stride ldq.  Returns false (on every
+// lane) when the QR iteration does not converge.
+__device__ bool lz_sqrt_e1(const double* al, const double* be, int k, double wn, double* Q, int ldq, double* out) {
+    using T = double;
     const int lane = threadIdx.x;
-    const T eps = sizeof(T) == 4 ? T(1.2e-7) : T(1e-16);   // deflation threshold (relative)
+    const T eps = T(1e-16);   // deflation threshold (relative)
     T d[GDC_MAX_LANCZOS], e[GDC_MAX_LANCZOS];
     for (int i = 0; i < k; ++i) {
         d[i] = (T)al[i];
@@ -607,14 +626,6 @@ __device__ bool lz_sqrt_e1_t(const double* al, const double* be, int k, double w
     return true;
 }
 
-// FP32 is enough for the small eigenproblem when the Lanczos tolerance is loose (its
-// error, ~1e-6 relative, is far below tol); tight tolerances use FP64.
-__device__ inline bool lz_sqrt_e1(const double* al, const double* be, int k, double wn, void* Q, int ldq, double* out,
-                                  bool fp32) {
-    return fp32 ? lz_sqrt_e1_t<float>(al, be, k, wn, (float*)Q, ldq, out)
-                : lz_sqrt_e1_t<double>(al, be, k, wn, (double*)Q, ldq, out);
-}
-
 // ||c_k - [c_{k-1}; 0]|| / ||c_k||, summed in the same order on every lane
 __device__ inline double lz_change(const double* ck, const double* cprev, int k) {
     double num = 0.0, den = 0.0;
@@ -630,7 +641,7 @@ __device__ inline double lz_change(const double* ck, const double* cprev, int k)
 // whatever the check schedule: when the first check of a run (index firstk + 1) already
 // passes, earlier indices are examined backwards.  lastk[s] is the last index whose c was
 // formed (-1 at the start of a run), lastk[S + s] the first one.  Launched with 32 threads
-// and lz_tridiag_smem(kmax, tol >= 1e-5) bytes of dynamic shared memory; every lane
+// and lz_tridiag_smem(kmax) bytes of dynamic shared memory; every lane
 // follows the same control flow and lane 0 alone writes the per-suspension scalars.
 __global__ void __launch_bounds__(32) k_lz_tridiag(int S, int j, const int* __restrict__ jdev, const double* __restrict__ h, int cols,
                                                    const double* __restrict__ wn2, double* __restrict__ alpha,
@@ -678,10 +689,9 @@ __global__ void __launch_bounds__(32) k_lz_tridiag(int S, int j, const int* __re
     double* ck = cur + kmax;
     double* cm = ck + kmax;
     double* best = cm + kmax;
-    void* Q = best + kmax;
+    double* Q = best + kmax;
     const int ldq = lz_ldq(kmax);
-    const bool eig32 = tol >= 1e-5;
-    if (!lz_sqrt_e1(al, be, k, wn, Q, ldq, cur, eig32)) {
+    if (!lz_sqrt_e1(al, be, k, wn, Q, ldq, cur)) {
         if (lead) {
             atomicExch(status, 2);
             active[s] = 0;
@@ -713,7 +723,7 @@ __global__ void __launch_bounds__(32) k_lz_tridiag(int S, int j, const int* __re
                 __syncwarp();
                 double best_err = ee;
                 for (int kk = k - 1; kk >= 2; --kk) {
-                    if (!lz_sqrt_e1(al, be, kk - 1, wn, Q, ldq, cm, eig32)) break;
+                    if (!lz_sqrt_e1(al, be, kk - 1, wn, Q, ldq, cm)) break;
                     const double e2 = lz_change(ck, cm, kk);
                     if (!(e2 < tol)) break;
                     kstar = kk;
@@ -756,7 +766,7 @@ __global__ void k_lz_reset(int S, int* __restrict__ lastk) {
 
 void krylov_init_attributes() {
     cudaFuncSetAttribute(k_lz_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)lz_tridiag_smem(GDC_MAX_LANCZOS, false));
+                         (int)lz_tridiag_smem(GDC_MAX_LANCZOS));
 }
 
 gdc_status lanczos_sqrt(gdc_ctx* c, const double* W, double* out, double scale, int fixed_mode,
@@ -777,7 +787,7 @@ gdc_status lanczos_sqrt(gdc_ctx* c, const double* W, double* out, double scale, 
     for (int j = 0; j < kmax; ++j) {
         const double* Vj = c->lz_V + (long long)j * n;
         c->mv_active = c->lz_active;   // suspensions that have stopped need no product
-        rpy_op(c, prec, Vj, c->lz_w);
+        lz_operator(c, prec, Vj, c->lz_w);
         c->mv_active = nullptr;
         // w = M v_j orthogonalised against v_0..v_j twice (full reorthogonalisation)
         seg_mdot(c, sg, c->lz_V, n, j + 1, c->lz_w, c->lz_h, cols);
@@ -786,7 +796,7 @@ gdc_status lanczos_sqrt(gdc_ctx* c, const double* W, double* out, double scale, 
         ++c->n_launch, k_mupdate<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_V, n, j + 1, nullptr, c->gm_h2, cols, c->lz_w);
         ++c->n_launch, k_add_cols<<<c->S, 128, 0, c->stream>>>(j + 1, nullptr, c->lz_h, c->gm_h2, cols);
         seg_mdot(c, sg, c->lz_w, 0, 1, c->lz_w, c->gm_h2, cols);
-        ++c->n_launch, k_lz_tridiag<<<c->S, 32, lz_tridiag_smem(kmax, c->p.lanczos_tol >= 1e-5), c->stream>>>(
+        ++c->n_launch, k_lz_tridiag<<<c->S, 32, lz_tridiag_smem(kmax), c->stream>>>(
             c->S, j, nullptr, c->lz_h, cols, c->gm_h2, c->lz_alpha, c->lz_beta, c->lz_Wnorm, c->lz_c, c->lz_err, c->lz_active,
             c->lz_k, c->lz_lastk, c->lz_scal, c->p.lanczos_tol, fixed_mode ? c->lz_fix : nullptr, c->lz_hint, kmax, c->susp_blob_off,
             c->dev_status);
@@ -797,10 +807,7 @@ gdc_status lanczos_sqrt(gdc_ctx* c, const double* W, double* out, double scale, 
         for (int s = 0; s < c->S; ++s) still = still || act[s];
         if (!still) break;
     }
-    // out = scale * V c
-    ++c->n_launch, k_fill<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(c->S, scale, c->lz_scal);
-    ++c->n_launch, k_combine<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_V, n, c->lz_k, c->lz_c, kmax,
-                                                                 c->lz_scal, out);
+    lz_result(c, scale, out);
     std::vector<int> ks(c->S);
     std::vector<double> errs(c->S);
     if ((st = sync_read(c, c->lz_k, ks.data(), sizeof(int) * c->S)) != GDC_OK) return st;
@@ -1064,7 +1071,7 @@ void lanczos_sqrt_graph(gdc_ctx* c, const double* W, double* out, double scale, 
     cap_while_begin(c, h);
     const unsigned long long before = c->n_launch;
     c->mv_active = c->lz_active;
-    rpy_op(c, prec, c->lz_vcur, c->lz_w);
+    lz_operator(c, prec, c->lz_vcur, c->lz_w);
     c->mv_active = nullptr;
     seg_mdot(c, sg, c->lz_V, n, 1, c->lz_w, c->lz_h, cols, jd, kmax);
     ++c->n_launch, k_mupdate<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_V, n, 1, jd, c->lz_h, cols, c->lz_w);
@@ -1072,7 +1079,7 @@ void lanczos_sqrt_graph(gdc_ctx* c, const double* W, double* out, double scale, 
     ++c->n_launch, k_mupdate<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_V, n, 1, jd, c->gm_h2, cols, c->lz_w);
     ++c->n_launch, k_add_cols<<<c->S, 128, 0, c->stream>>>(1, jd, c->lz_h, c->gm_h2, cols);
     seg_mdot(c, sg, c->lz_w, 0, 1, c->lz_w, c->gm_h2, cols);
-    ++c->n_launch, k_lz_tridiag<<<c->S, 32, lz_tridiag_smem(kmax, c->p.lanczos_tol >= 1e-5), c->stream>>>(
+    ++c->n_launch, k_lz_tridiag<<<c->S, 32, lz_tridiag_smem(kmax), c->stream>>>(
         c->S, 0, jd, c->lz_h, cols, c->gm_h2, c->lz_alpha, c->lz_beta, c->lz_Wnorm, c->lz_c, c->lz_err, c->lz_active,
         c->lz_k, c->lz_lastk, c->lz_scal, c->p.lanczos_tol, fixed_mode ? c->lz_fix : nullptr, c->lz_hint, kmax,
         c->susp_blob_off, c->dev_status);
@@ -1080,9 +1087,7 @@ void lanczos_sqrt_graph(gdc_ctx* c, const double* W, double* out, double scale, 
                                                                         1, c->lz_vcur);
     ++c->n_launch, k_lz_next<<<1, 32, 0, c->stream>>>(c->S, c->lz_active, c->ctl, kmax, h);
     cap_while_end(c, REP_LZ0 + run, before);
-    ++c->n_launch, k_fill<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(c->S, scale, c->lz_scal);
-    ++c->n_launch, k_combine<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_V, n, c->lz_k, c->lz_c, kmax,
-                                                                 c->lz_scal, out);
+    lz_result(c, scale, out);
     ++c->n_launch, k_lz_finish<<<1, 32, 0, c->stream>>>(c->S, c->lz_k, c->lz_err, fixed_mode, c->p.lanczos_tol, kmax,
                                                         c->ctl, c->rep, run);
 }

@@ -650,12 +650,13 @@ static void launch_epilogue(gdc_ctx* c, int prec, double c0, const double* x, do
             rpy_const32(c->p.a), nullptr, nullptr, nullptr, nullptr);
 }
 
-void launch_rpy_epilogue(gdc_ctx* c, int prec, const double* x, double* y, int gm_layout) {
+void launch_rpy_epilogue(gdc_ctx* c, int prec, const double* x, double* y, int gm_layout, bool same_body) {
     launch_epilogue(c, prec, 1.0 / (8.0 * 3.141592653589793 * c->p.eta), x, y, gm_layout, prec == GDC_FP32_MIXED);
     // same-body blocks from the template: the df64 pair kernel leaves those pairs out and the
-    // FP32 epilogue has taken the FP32 pair kernel's same-body terms out again
+    // FP32 epilogue has taken the FP32 pair kernel's same-body terms out again (so without
+    // them an FP32 product is exactly the blocks between different bodies)
     if (prec == GDC_PREC_DF64) launch_intra_body(c, x, y, gm_layout);
-    if (prec == GDC_FP32_MIXED) launch_intra_body32(c, x, y, gm_layout);
+    if (prec == GDC_FP32_MIXED && same_body) launch_intra_body32(c, x, y, gm_layout);
 }
 
 // ---- pairs closer than 2a ------------------------------------------------------------

@@ -154,16 +154,21 @@ def test_lsq_velocity(lib, wl_mix, wl_rod):
         assert rel(got, rigid.lsq_velocity(K, B, vb)) < 1e-12
 
 
+@pytest.mark.parametrize("precond", [0, 1])
 @pytest.mark.parametrize("prec", [0, 1])
-def test_brownian_slip_lanczos(lib, wl_mix, prec):
+def test_brownian_slip_lanczos(lib, wl_mix, prec, precond):
+    """Lanczos converges to the symmetric root M^(1/2) W (precond 0) or to the block-preconditioned
+    root L (L^-1 M L^-T)^(1/2) W of Chow & Saad (precond 1), computed densely by the oracle."""
     tol = 1e-11 if prec == 0 else 1e-6
-    ctx = ctx_for(lib, wl_mix, precision=prec, lanczos_tol=tol, lanczos_max_iter=128, kT=1.3, dt=0.02)
+    ctx = ctx_for(lib, wl_mix, precision=prec, lanczos_tol=tol, lanczos_max_iter=128, kT=1.3, dt=0.02,
+                  lanczos_precond=precond)
     rng = np.random.default_rng(15)
     W = rng.standard_normal(3 * wl_mix.n_blobs)
     vb, iters, err = ctx.brownian_slip(W)
     lay, Y, q = susp_layout(wl_mix, 0)
     r, M, K, B = dense_state(lay, Y, q)
-    ref = np.sqrt(2 * 1.3 / 0.02) * rigid.sqrtm_sym(M) @ W
+    S = rigid.sqrtm_block(M, rigid.block_factor(lay, q, 1.0, 1.0)) if precond else rigid.sqrtm_sym(M)
+    ref = np.sqrt(2 * 1.3 / 0.02) * S @ W
     assert 2 <= iters <= 128
     assert rel(_host(vb), ref) < (1e-9 if prec == 0 else 2e-5)
 

@@ -92,8 +92,10 @@ def test_deterministic_limit_is_forward_euler():
 
 def test_rfd_is_unbiased_for_fd():
     # Eq. (rfd_div): averaging the RFD estimator over W-tilde gives the FD divergence of Eq. (FD).
+    # The identity holds for any smooth map x -> calV(x); the symmetric root of M gives this
+    # W a divergence large enough for 400 draws to resolve it.
     lay, Y, q = _state([shapes.triangle(), shapes.triangle()], [0, 0], [[0, 0, 0], [3.2, 0.8, 0.4]], seed=4)
-    p = Params(dt=0.01, rfd_delta=1e-5)
+    p = Params(dt=0.01, rfd_delta=1e-5, sqrt_mode="sym")
     W = np.random.default_rng(5).standard_normal(3 * lay.n_blobs)
     calV = projected_velocity(lay, Y, q, W, p)
     fd = fd_divergence(lay, Y, q, W, calV, p)
