@@ -8,12 +8,21 @@ A = 4kT/a, b = 0.1a, dt = 0.005, GMRES tol 1e-6, Lanczos tol 1e-4, RFD delta 1e-
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload c3_65k|c4|c5]
+    python bench.py --op NAME [--workload W] [--reps R] ...   (one building block, for profiling)
 
 --workload c4: 512 independent suspensions (8-128 bodies of 12-blob icosahedra, 10-blob
 rods and 42-blob icospheres, 5% volume fraction each, 772,728 blobs in all) advanced in one
 batched context, against the same suspensions advanced one context (one launch sequence)
 per suspension.  --workload c5: 16,384 rods of 20 blobs (327,680 blobs) at 8% volume
 fraction in linear shear, dt 0.002.  The default is the 65,520-blob workload above.
+
+--op runs one building block of the library on a workload instead of the step benchmark and
+prints its mean time per call (CUDA events on the library's stream): rpy32 / rpy64 / rpydf
+(one RPY product in FP32 / FP64 / double-float), saddle32, precond, forces32 (positions and
+pair forces), lanczos32 (one v-breve), solve32 (one FP32-mixed mobility solve), step32 (one
+gDC step, --graph 0|1), fcm_apply / fcm_brownian / fcm_average (fluctuating FCM of the
+workload's blobs in a periodic cube of its box side, --fcm-n grid points per side).  This is
+the command the ncu captures under profiles/ run.
 
 Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank advances its own
 independent suspension of the same size (replicas, weak scaling, no collective on the
@@ -56,10 +65,10 @@ def _dist():
 
 # the FP32 pair kernels: (source file, start of the kernel, tiling macros, ncu summary)
 PAIR_KERNELS = {
-    1: ("rpy.cu", "template <int P>\n__global__ void __launch_bounds__(128, GDC_RPY32_MINB) k_rpy32",
-        r"#define (GDC_MV_TILE|GDC_RPY32_MINB) (\S+)", "k_rpy32_c3_65k.md", "k_rpy32 (ordered FP32 RPY pair kernel)"),
-    2: ("sym.cu", "__global__ void __launch_bounds__(128, GDC_SYM_MINB) k_rpy32_sym",
-        r"#define (GDC_SYM_MINB|GDC_SYM_TILE) (\S+)", "k_rpy32_sym_c3_65k.md",
+    1: ("rpy.cu", "template <int P, int MINB>\n__global__ void __launch_bounds__(128, MINB) k_rpy32",
+        r"#define (GDC_MV_TILE) (\S+)", "k_rpy32_c3_65k.md", "k_rpy32 (ordered FP32 RPY pair kernel)"),
+    2: ("sym.cu", "template <int MINB>\n__global__ void __launch_bounds__(128, MINB) k_rpy32_sym",
+        r"#define (GDC_SYM_TILE) (\S+)", "k_rpy32_sym_c3_65k.md",
         "k_rpy32_sym (symmetric FP32 RPY pair kernel)"),
 }
 
@@ -169,66 +178,91 @@ class ClockSampler:
                 "power_w_max": max(power), "reasons": sorted(reasons)}
 
 
-def oracle_sample_step(wl, n_bodies: int, seed: int = 0):
-    """One dense FP64 oracle gDC step on the first n_bodies bodies of the workload (seconds, blobs)."""
-    from oracle import geometry as G, philox
-    from oracle import gdc as ogdc
-    sub = wl.first_bodies(n_bodies)
-    lay = G.Layout(sub.templates, sub.body_tmpl)
-    W = philox.normals(seed, 0, 0, 0, 3 * lay.n_blobs)
-    Wt = philox.normals(seed, 0, 0, 1, 6 * lay.n_bodies)
-    p = ogdc.Params.from_dict(dict(sub.params, rfd_delta=1e-3))
+TWIN_RECORD = os.path.join(ROOT, "profiles", "cpu_twin_step_c3_65k.md")
+
+
+def twin_record() -> dict:
+    """The CPU twin's full step on the 65,520-blob workload, measured once on the GPU machine's
+    host cores (oracle/twin_record.py): its RPY product count and the time it spends outside
+    the products.  None when the record is missing."""
+    import re
+    try:
+        text = open(TWIN_RECORD).read()
+    except OSError:
+        return None
+    rec = {k: float(v) for k, v in re.findall(r"^(\w+): ([-0-9.eE+]+)\s*$", text, flags=re.M)}
+    return rec if "products" in rec and "non_product_seconds" in rec else None
+
+
+def twin_products(wl, n: int):
+    """Seconds per full-size FP64 RPY product of the CPU twin (mean of n after one untimed),
+    and the OpenMP threads it used."""
+    import numpy as np
+
+    from oracle import geometry as G, twin
+    lay = G.Layout(wl.templates, wl.body_tmpl)
+    r = G.blob_positions(lay, wl.Y, wl.q)
+    lam = np.random.default_rng(0).standard_normal(3 * lay.n_blobs)
+    twin.rpy_product(r, lam, wl.params["a"], wl.params["eta"])
     t0 = time.perf_counter()
-    ogdc.gdc_step(lay, sub.Y, sub.q, W, Wt, p)
-    return time.perf_counter() - t0, lay.n_blobs
+    for _ in range(n):
+        twin.rpy_product(r, lam, wl.params["a"], wl.params["eta"])
+    return (time.perf_counter() - t0) / n, twin.threads()
 
 
-def cpu_baseline(wl, budget_s: float = 20.0, n_bodies: int = 48) -> dict:
-    """The dense oracle timed on a bounded sample of the workload, scaled to a full 65k step.
+def cpu_baseline(wl, n_products: int = 3) -> dict:
+    """The oracle's matrix-free FP64 twin of the step (oracle/twin.py) on the host cores.
 
-    The oracle's step is dominated by its O(n^3) dense factorisations (three symmetric
-    eigendecompositions and one LU), so the sample's time is scaled by the cube of the
-    blob-count ratio.
-    """
-    times, nbl = [], 0
-    t_start = time.perf_counter()
-    while time.perf_counter() - t_start < budget_s or not times:
-        t, nbl = oracle_sample_step(wl, n_bodies, seed=len(times))
-        times.append(t)
-        if len(times) >= 3:
-            break
-    t_sample = statistics.median(times)
-    scale = (wl.n_blobs / nbl) ** 3
-    t_full = t_sample * scale
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    return {"value": 1.0 / t_full, "unit": "steps/s", "cores": cores, "kind": "oracle",
-            "sample": (f"dense FP64 oracle gDC step on the first {n_bodies} bodies ({nbl} blobs) of the workload, "
-                       f"median of {len(times)} runs = {t_sample:.3f} s, scaled by ({wl.n_blobs}/{nbl})^3 "
-                       f"for its O(n^3) eigendecompositions and LU"),
-            "sample_seconds": t_sample}
+    The sample: n_products full-size RPY products (all 65,520 blobs, pair by pair in FP64, one
+    OpenMP loop), timed; a step is that product time times the products of one full twin step
+    plus the step's time outside its products, both from the twin's full-size step measured
+    once (profiles/cpu_twin_step_c3_65k.md)."""
+    rec = twin_record()
+    t_prod, threads = twin_products(wl, n_products)
+    out = {"unit": "steps/s", "cores": threads, "kind": "oracle", "product_seconds": t_prod}
+    if rec is None:
+        out.update(value=None, sample=f"{n_products} full-size FP64 twin products, {t_prod:.2f} s each; no full-step "
+                                      f"record, so no step rate")
+        return out
+    t_step = t_prod * rec["products"] + max(rec["non_product_seconds"], 0.0)
+    out.update(value=1.0 / t_step, step_seconds=t_step,
+               sample=(f"{n_products} full-size FP64 RPY products of the matrix-free twin (65,520 blobs, "
+                       f"{threads} threads), {t_prod:.2f} s each, times the {int(rec['products'])} products of one "
+                       f"full twin step, plus that step's {max(rec['non_product_seconds'], 0.0):.1f} s outside its "
+                       f"products (both measured once on the full step: profiles/cpu_twin_step_c3_65k.md)"))
+    return out
 
 
 def run_reference(args, world, rank):
+    """The reference arm: the oracle's matrix-free FP64 twin of the step on the host cores,
+    each step one full-size product timed and scaled by the products of a full twin step."""
     if rank != 0:
         return 0
     from synthetic import workloads as WL
     wl = WL.c3_65k(seed=0)
+    rec = twin_record()
+    if rec is None:
+        print(json.dumps({"impl": "reference", "unavailable": "no full-step record of the CPU twin "
+                                                              "(profiles/cpu_twin_step_c3_65k.md)"}), flush=True)
+        return 0
     for _ in range(args.warmup):
-        oracle_sample_step(wl, args.ref_bodies)
-    times, nbl = [], 0
-    for k in range(args.steps):
-        t, nbl = oracle_sample_step(wl, args.ref_bodies, seed=k)
-        times.append(t * (wl.n_blobs / nbl) ** 3)
-    total = sum(times)
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+        twin_products(wl, 1)
+    steps, threads = [], 1
+    for _ in range(args.steps):
+        t_prod, threads = twin_products(wl, 1)
+        steps.append(t_prod * rec["products"] + max(rec["non_product_seconds"], 0.0))
+    total = sum(steps)
     value = args.steps / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "precision": "fp64 dense oracle (CPU)"},
-            "cpu_baseline": {"value": value, "unit": "steps/s", "cores": cores, "kind": "oracle",
-                             "sample": (f"each step: dense FP64 oracle gDC step on the first {args.ref_bodies} bodies "
-                                        f"({nbl} blobs), scaled by ({wl.n_blobs}/{nbl})^3")},
+            "config": {"workload": WORKLOAD, "precision": "fp64 matrix-free CPU twin of the oracle"},
+            "cpu_baseline": {"value": value, "unit": "steps/s", "cores": threads, "kind": "oracle",
+                             "sample": (f"each step: one full-size FP64 RPY product of the matrix-free twin "
+                                        f"(65,520 blobs, {threads} threads) timed, times the "
+                                        f"{int(rec['products'])} products of one full twin step, plus its "
+                                        f"{max(rec['non_product_seconds'], 0.0):.1f} s outside the products "
+                                        f"(profiles/cpu_twin_step_c3_65k.md)")},
             "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -313,6 +347,76 @@ def fcm_measure(g, torch, wl, ctx, N: int, reps: int = 3) -> dict:
     return out
 
 
+def run_op(args) -> int:
+    """One building block of the library, timed with CUDA events (see --op in the module doc)."""
+    import numpy as np
+    import torch
+
+    import paper_2106_00449_gb300 as g
+    from synthetic import workloads as WL
+
+    wl = WL.BY_NAME[args.workload]()
+    if args.bodies:
+        wl = wl.first_bodies(args.bodies)
+    if args.op.startswith("fcm_"):
+        ctx = g.context_from_workload(wl, precision=g.FP32_MIXED, autotune=0)
+        r = ctx.blob_positions().reshape(-1, 3).contiguous()
+        n = r.shape[0]
+        L, a = float(wl.box[0]), float(wl.params["a"])
+        F = g.Fcm(args.fcm_n, L, a / np.sqrt(np.pi), 3.0 * a, eta=float(wl.params["eta"]), max_blobs=n,
+                  stream=ctx.stream)
+        lam = torch.as_tensor(np.random.default_rng(0).standard_normal((n, 3)), device=r.device)
+        F.brownian(r, 1, 0, 0, 1.0, 0.01)
+        ops = {"fcm_apply": lambda: F.apply(r, lam),
+               "fcm_brownian": lambda: F.brownian(r, 1, 0, 1, 1.0, 0.01),
+               "fcm_average": lambda: F.average(r)}
+        stream, extra = ctx.stream, {"grid": args.fcm_n, "L": L}
+    else:
+        ctx = g.context_from_workload(wl, precision=g.FP32_MIXED, rfd_delta=1e-3, lanczos_max_iter=128,
+                                      pair_kernel=args.pair_kernel, graph=args.graph,
+                                      force_method=args.force_method, potential=args.potential,
+                                      well_A=5.0 if args.potential else 0.0, well_lambda=0.5)
+        rng = np.random.default_rng(0)
+        n = wl.n_blobs
+        lam = torch.as_tensor(rng.standard_normal(3 * n), device=ctx.device)
+        x = torch.as_tensor(rng.standard_normal(int(ctx.saddle_off[-1])), device=ctx.device)
+        zero_ft = torch.zeros(6 * wl.n_bodies, dtype=torch.float64, device=ctx.device)
+        ops = {"rpy32": lambda: ctx.rpy_apply(lam, g.FP32_MIXED),
+               "rpy64": lambda: ctx.rpy_apply(lam, g.FP64),
+               "rpydf": lambda: ctx.rpy_apply(lam, 2),
+               "saddle32": lambda: ctx.saddle_apply(x, g.FP32_MIXED),
+               "precond": lambda: ctx.precond_apply(x),
+               "forces32": lambda: ctx.forces(),
+               "lanczos32": lambda: ctx.brownian_slip(lam),
+               "solve32": lambda: ctx.mobility_solve(zero_ft, lam),
+               "step32": lambda: ctx.step(1)}
+        stream, extra = ctx.stream, {"pair_kernel": None}
+    if args.op not in ops:
+        raise SystemExit(f"unknown --op {args.op}; one of {sorted(ops)}")
+    fn = ops[args.op]
+
+    def launched():   # the library's own kernels launched so far (all named k_*)
+        return F.launches if args.op.startswith("fcm_") else ctx.profile_read()["launches"]
+
+    fn()
+    torch.cuda.synchronize()
+    before = launched()   # kernels of the set-up and the warm-up call: what an ncu capture skips
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out = {"op": args.op, "workload": wl.name, "n_blobs": n, "ms_per_call": e0.elapsed_time(e1) / args.reps,
+           "reps": args.reps, "kernels_before_timed_calls": before,
+           "kernels_per_call": (launched() - before) / args.reps, **extra}
+    if "pair_kernel" in extra:
+        out["pair_kernel"] = ctx.profile_read()["pair_kernel"]
+        out["pairs"] = wl.pair_evals_per_matvec()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -321,13 +425,24 @@ def main(argv=None) -> int:
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=1, help="FP64 steps timed for the comparison (0 = skip)")
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--cpu-budget", type=float, default=20.0)
-    ap.add_argument("--ref-bodies", type=int, default=40)
+    ap.add_argument("--cpu-products", type=int, default=3, help="full-size twin products timed for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="c3_65k", choices=["c3_65k", "c4", "c5"])
+    ap.add_argument("--workload", default="c3_65k",
+                    help="c3_65k (default), c4 or c5 for the step benchmark; any synthetic workload for --op")
     ap.add_argument("--fcm-n", type=int, default=512,
                     help="grid points per side of the fluctuating-FCM measurement (0 = skip it)")
+    ap.add_argument("--op", default=None, help="time one building block instead of the step (see the module doc)")
+    ap.add_argument("--bodies", type=int, default=0, help="--op: only the first N bodies of the workload (0 = all)")
+    ap.add_argument("--reps", type=int, default=5, help="--op: timed calls")
+    ap.add_argument("--pair-kernel", type=int, default=0, help="--op: 0 autotuned, 1 ordered, 2 symmetric")
+    ap.add_argument("--graph", type=int, default=1, help="--op step32: 1 graph replay, 0 host-driven")
+    ap.add_argument("--force-method", type=int, default=0, help="--op: 0 choose, 1 all pairs, 2 cell list")
+    ap.add_argument("--potential", type=int, default=0, help="--op: 0 soft sphere, 1 and 2 the Sec. 6.4 wells")
     args = ap.parse_args(argv)
+    if args.op:
+        return run_op(args)
+    if args.workload not in ("c3_65k", "c4", "c5"):
+        raise SystemExit("the step benchmark runs --workload c3_65k, c4 or c5")
     world, rank, local = _dist()
     if args.impl == "reference":
         return run_reference(args, world, rank)
@@ -416,6 +531,7 @@ def main(argv=None) -> int:
                        "targets_per_thread": 4 if kind == 2 else prof["targets_per_thread"],
                        "work_waves": None if kind == 2 else prof["work_waves"],
                        "source_tiles_per_item": prof.get("sym_width") if kind == 2 else None,
+                       "min_blocks_per_sm": prof.get("min_blocks_per_sm"),
                        "autotuned": prof["autotune_ms"] > 0},
             "flops_per_pair": FLOPS_PER_PAIR, "pairs_per_launch": prof["pairs_per_product"],
             "flop_count": ("33 flops per ordered pair (i, j), N_b^2 per launch, whichever kernel runs; the "
@@ -496,7 +612,7 @@ def main(argv=None) -> int:
                         "gmres_iters": [i["solve"]["iterations"] for i in inf64],
                         "fp32_mixed_speedup": value / world / (args.fp64_steps / t64)}
     if rank == 0 and not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(wl, budget_s=args.cpu_budget, n_bodies=48)
+        line["cpu_baseline"] = cpu_baseline(wl, n_products=args.cpu_products)
     if dist:
         dist.barrier()
         dist.destroy_process_group()

@@ -113,8 +113,9 @@ typedef struct {
     double rep_b;          /* soft repulsion range b (Eq. soft_sphere_potential)                          */
     double shear_rate;     /* background flow u = (shear_rate * y, 0, 0); 0 = off      */
     unsigned long long seed; /* Philox4x32-10 key of the W and W-tilde draws            */
-    int    autotune;       /* 1: gdc_init times the FP32 pair kernel's candidate tilings
-                              at the initial configuration and keeps the fastest        */
+    int    autotune;       /* 1: gdc_init times the FP32 pair kernels' candidates at the
+                              initial configuration and keeps the fastest: kernel, work-
+                              item shape and the resident blocks per SM it is compiled for */
     int    graph;          /* 1: gdc_step captures one step as a CUDA graph at its first
                               call and replays it; the Lanczos and GMRES loops are
                               conditional WHILE nodes whose conditions the loop kernels
@@ -284,10 +285,26 @@ gdc_status gdc_saddle_offsets(const gdc_ctx* ctx, long long* off);
  * n_blobs above GDC_NOALLOC_MAX_BLOBS is rejected with GDC_ERR_INVALID_ARG
  * (message in gdc_last_error(NULL)).  Every call uses the same array: calls
  * that overlap on the GPU (different streams, or different host threads on
- * one device) race and must be serialised by the caller. */
+ * one device) race and must be serialised by the caller.  The call is
+ * asynchronous and returns before the kernels finish, so a failure on the GPU
+ * cannot be returned as a status: if a tile copy of the pair kernel does not
+ * complete within its bounded wait, every entry of u is set to NaN instead.
+ * Each call starts by clearing that flag, so the next call is unaffected. */
 #define GDC_NOALLOC_MAX_BLOBS 16384
 gdc_status gdc_rpy_apply_noalloc(const double* r, const double* lambda, double* u, int n_blobs,
                                  double a, double eta, void* stream);
+
+/* ---- testing the bounded waits ----------------------------------------------
+ *
+ * The FP32 pair kernels stage source tiles with bulk copies and wait for each on an
+ * mbarrier for at most a bounded number of polls; a wait that gives up makes the kernel
+ * wait (again bounded) for its copies in flight and return early, and the call reports
+ * GDC_ERR_TIMEOUT (gdc_rpy_apply_noalloc: u set to NaN).  This process-wide setting
+ * changes that bound for the pair-kernel launches issued after it (a step graph captured
+ * before keeps its bound): polls > 0 sets it, 0 restores the default (400,000 polls), and
+ * polls < 0 makes every first wait give up without polling, which exercises the timeout
+ * path on purpose.  It is meant for tests of that path, not for production use. */
+void gdc_debug_wait_polls(int polls);
 
 /* ---- fluctuating force-coupling method (FCM) in a periodic cube ---------------
  *
@@ -354,6 +371,8 @@ typedef struct {
     int    pair_kernel;                 /* FP32 pair kernel in use: 1 ordered, 2 symmetric */
     int    sym_width;                   /* source tiles per work item (symmetric kernel)  */
     double unique_pairs_per_product;    /* unordered pairs incl. self, sum n (n + 1) / 2  */
+    int    min_blocks_per_sm;           /* resident blocks per SM the FP32 pair kernel in use
+                                           was compiled for (chosen by the autotuner)     */
 } gdc_profile_info;
 
 /* Reset the counters; enable != 0 also brackets every pair-kernel launch with

@@ -53,8 +53,10 @@ class Params:
     well_lambda: float = 0.5    # Gaussian well width, a length (Sec. 6.4: 0.5 a)
     shear_rate: float = 0.0
     sqrt_mode: str = "block"    # "block" (preconditioned Lanczos root), "sym" (eigh) or "chol"
-    lanczos_tol: float = 0.0    # 0: the dense root of sqrt_mode; > 0: the Lanczos iterate at that tolerance
-    lanczos_max_iter: int = 128
+    # 0: the dense root of sqrt_mode; > 0: the Lanczos iterate at that tolerance (named apart
+    # from a workload's lanczos_tol, which configures the library, not the oracle)
+    sqrt_lanczos_tol: float = 0.0
+    sqrt_lanczos_max_iter: int = 128
 
     @classmethod
     def from_dict(cls, d: dict) -> "Params":
@@ -83,7 +85,7 @@ def brownian_slip_k(layout, Y, q, W, p: Params, fixed_k: int = None):
     """Blob positions, M, K, B, v-breve = sqrt(2kT/dt) M^(1/2) W at state (Y, q), and the
     Lanczos iteration count (None for a dense root).
 
-    With p.lanczos_tol > 0 the root is the Lanczos iterate of lanczos.py at that tolerance
+    With p.sqrt_lanczos_tol > 0 the root is the Lanczos iterate of lanczos.py at that tolerance
     (or with exactly fixed_k iterations) on the operator of sqrt_mode: A = L^-1 M L^-T with
     the result multiplied by L ("block"), or M itself ("sym")."""
     r = geometry.blob_positions(layout, Y, q)
@@ -93,14 +95,14 @@ def brownian_slip_k(layout, Y, q, W, p: Params, fixed_k: int = None):
     L = rigid.block_factor(layout, q, p.a, p.eta) if p.sqrt_mode == "block" else None
     scale = np.sqrt(2.0 * p.kT / p.dt)
     k = None
-    if p.lanczos_tol > 0.0 and p.sqrt_mode in ("block", "sym"):
+    if p.sqrt_lanczos_tol > 0.0 and p.sqrt_mode in ("block", "sym"):
         if p.sqrt_mode == "block":
             Linv = np.linalg.inv(L)
             A = Linv @ M @ Linv.T
-            y, k, _ = lanczos.lanczos_sqrt(0.5 * (A + A.T), W, p.lanczos_tol, p.lanczos_max_iter, fixed_k)
+            y, k, _ = lanczos.lanczos_sqrt(0.5 * (A + A.T), W, p.sqrt_lanczos_tol, p.sqrt_lanczos_max_iter, fixed_k)
             vb = scale * (L @ y)
         else:
-            y, k, _ = lanczos.lanczos_sqrt(M, W, p.lanczos_tol, p.lanczos_max_iter, fixed_k)
+            y, k, _ = lanczos.lanczos_sqrt(M, W, p.sqrt_lanczos_tol, p.sqrt_lanczos_max_iter, fixed_k)
             vb = scale * y
     else:
         vb = scale * sqrt_apply(M, W, p.sqrt_mode, L)

@@ -26,8 +26,10 @@ from __future__ import annotations
 import numpy as np
 
 
-def lanczos_sqrt(A: np.ndarray, W: np.ndarray, tol: float, kmax: int = 128, fixed_k: int = None):
-    """(y, k, change): the Lanczos approximation y of A^(1/2) W for the SPD matrix A."""
+def lanczos_sqrt(A, W: np.ndarray, tol: float, kmax: int = 128, fixed_k: int = None):
+    """(y, k, change): the Lanczos approximation y of A^(1/2) W for the SPD operator A, a
+    matrix or a function that returns A x."""
+    apply = A if callable(A) else (lambda x: A @ x)
     W = np.asarray(W, dtype=np.float64)
     n = W.size
     wn = float(np.linalg.norm(W))
@@ -38,7 +40,7 @@ def lanczos_sqrt(A: np.ndarray, W: np.ndarray, tol: float, kmax: int = 128, fixe
     c_prev = None
     for k in range(1, kmax + 1):
         Vk = np.array(basis).T
-        w = A @ basis[-1]
+        w = apply(basis[-1])
         h = Vk.T @ w
         w = w - Vk @ h
         h2 = Vk.T @ w

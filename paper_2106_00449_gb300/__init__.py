@@ -40,7 +40,7 @@ EXPORTS = [
     "gdc_mobility_solve", "gdc_step", "gdc_set_trace", "gdc_get_state", "gdc_set_state",
     "gdc_blob_positions", "gdc_rpy_apply", "gdc_saddle_apply", "gdc_precond_apply",
     "gdc_brownian_slip", "gdc_lsq_velocity", "gdc_forces", "gdc_draw_normals", "gdc_saddle_offsets",
-    "gdc_profile", "gdc_profile_read", "gdc_rpy_apply_noalloc",
+    "gdc_profile", "gdc_profile_read", "gdc_rpy_apply_noalloc", "gdc_debug_wait_polls",
     "gdc_fcm_workspace_bytes", "gdc_fcm_init", "gdc_fcm_apply", "gdc_fcm_brownian", "gdc_fcm_average",
     "gdc_fcm_last_error", "gdc_fcm_launches", "gdc_fcm_destroy",
 ]
@@ -91,7 +91,7 @@ class _Profile(ctypes.Structure):
                 ("work_waves", ctypes.c_double), ("autotune_ms", ctypes.c_double),
                 ("rpydf_launches", ctypes.c_ulonglong), ("rpydf_ms", ctypes.c_double),
                 ("pair_kernel", ctypes.c_int), ("sym_width", ctypes.c_int),
-                ("unique_pairs_per_product", ctypes.c_double)]
+                ("unique_pairs_per_product", ctypes.c_double), ("min_blocks_per_sm", ctypes.c_int)]
 
 
 class _Trace(ctypes.Structure):
@@ -174,6 +174,8 @@ def load_library() -> ctypes.CDLL:
     lib.gdc_profile.argtypes = [vp, ctypes.c_int]
     lib.gdc_profile_read.argtypes = [vp, ctypes.POINTER(_Profile)]
     lib.gdc_rpy_apply_noalloc.argtypes = [dp, dp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, vp]
+    lib.gdc_debug_wait_polls.restype = None
+    lib.gdc_debug_wait_polls.argtypes = [ctypes.c_int]
     lib.gdc_fcm_workspace_bytes.restype = ctypes.c_size_t
     lib.gdc_fcm_workspace_bytes.argtypes = [ctypes.POINTER(_FcmParams)]
     lib.gdc_fcm_init.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(_FcmParams), vp, ctypes.c_size_t, vp]
@@ -189,7 +191,7 @@ def load_library() -> ctypes.CDLL:
     lib.gdc_fcm_destroy.argtypes = [vp]
     for name in EXPORTS:
         if name not in ("gdc_workspace_bytes", "gdc_destroy", "gdc_last_error", "gdc_fcm_workspace_bytes",
-                        "gdc_fcm_last_error", "gdc_fcm_launches", "gdc_fcm_destroy"):
+                        "gdc_fcm_last_error", "gdc_fcm_launches", "gdc_fcm_destroy", "gdc_debug_wait_polls"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -493,18 +495,34 @@ def rpy_apply_noalloc(r, lam, a: float = 1.0, eta: float = 1.0, out=None, stream
 
     For callers that must not allocate device memory on the library's behalf: the
     library uses only its fixed internal scratch array.  r, lam: contiguous float64 CUDA
-    tensors with 3 values per blob; out (optional) receives u.  Returns out.
+    tensors of the same length, 3 values per blob, on one device; out (optional, same
+    kind) receives u.  Returns out.  A pair-kernel timeout shows as NaN in out.
     """
     import torch
     lib = load_library()
+    tensors = [r, lam] + ([out] if out is not None else [])
+    for t in tensors:
+        if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+            raise ValueError("r, lam and out must be contiguous float64 CUDA tensors")
+        if t.numel() != r.numel() or t.device != r.device:
+            raise ValueError("r, lam and out must have the same length and device")
+    if r.numel() % 3 != 0 or r.numel() == 0:
+        raise ValueError("r holds 3 values per blob")
     n = r.numel() // 3
-    if out is None:
-        out = torch.empty_like(lam)
-    s = stream if stream is not None else torch.cuda.current_stream(r.device)
-    st = lib.gdc_rpy_apply_noalloc(_dptr(r), _dptr(lam), _dptr(out), n, a, eta, ctypes.c_void_p(s.cuda_stream))
+    with torch.cuda.device(r.device):
+        if out is None:
+            out = torch.empty_like(lam)
+        s = stream if stream is not None else torch.cuda.current_stream(r.device)
+        st = lib.gdc_rpy_apply_noalloc(_dptr(r), _dptr(lam), _dptr(out), n, a, eta, ctypes.c_void_p(s.cuda_stream))
     if st != 0:
         raise GdcError(st, lib.gdc_last_error(None).decode())
     return out
+
+
+def debug_wait_polls(polls: int) -> None:
+    """Bound of the pair kernels' waits for a tile copy (gdc_debug_wait_polls): 0 restores
+    the default; a negative value makes every first wait give up (tests of the timeout path)."""
+    load_library().gdc_debug_wait_polls(int(polls))
 
 
 def context_from_workload(wl, **overrides) -> Context:

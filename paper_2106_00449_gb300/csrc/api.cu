@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <new>
 
 #include "common.cuh"
@@ -15,6 +16,14 @@ namespace gdc {
 gdc_status fail(gdc_ctx* c, gdc_status s, const std::string& msg) {
     if (c) c->err = msg;
     return s;
+}
+
+// the bound of the pair kernels' waits for a tile copy (gdc_debug_wait_polls): 0 = default
+static std::atomic<int> g_wait_polls{0};
+
+int first_wait_polls() {
+    const int v = g_wait_polls.load();
+    return v == 0 ? GDC_WAIT_POLLS : (v < 0 ? 0 : v);
 }
 
 gdc_status cuda_check(gdc_ctx* c, cudaError_t e, const char* what) {
@@ -374,15 +383,35 @@ static gdc_status check_state_host(gdc_ctx* c, const double* Y, const double* q)
     return GDC_OK;
 }
 
+// Clears the device status words once a failure they flagged has been reported, so that the
+// next call of the context starts clean.
+static gdc_status clear_status(gdc_ctx* c) {
+    cudaError_t e = cudaMemsetAsync(c->dev_status, 0, 4 * sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return cuda_check(c, e, "status reset");
+}
+
 static gdc_status read_status(gdc_ctx* c) {
     int st[4] = {0, 0, 0, 0};
     cudaError_t e = cudaMemcpyAsync(st, c->dev_status, sizeof(st), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_check(c, e, "status read");
+    if ((st[0] != 0 || st[1] != 0) && clear_status(c) != GDC_OK) return GDC_ERR_CUDA;
+    // a timed-out tile copy first: an incomplete product explains any later failure
+    if (st[1] != 0) return fail(c, GDC_ERR_TIMEOUT, "a pair-kernel tile copy did not complete in time");
     if (st[0] == 1) return fail(c, GDC_ERR_NONFINITE, "template RPY block is not positive definite");
     if (st[0] == 2) return fail(c, GDC_ERR_NOT_CONVERGED, "tridiagonal eigensolver did not converge");
-    if (st[1] != 0) return fail(c, GDC_ERR_TIMEOUT, "a pair-kernel tile copy did not complete in time");
     return GDC_OK;
+}
+
+// The outcome of a call that failed on the host side: a failure the kernels flagged in the
+// status words (a timed-out tile copy, a failed eigen-step) is the cause of the later
+// symptom (a Krylov loop that did not converge on an incomplete product), so it takes
+// precedence.  The words are cleared once read.
+static gdc_status settle(gdc_ctx* c, gdc_status st) {
+    if (st == GDC_ERR_CUDA) return st;   // the stream may not be usable
+    const gdc_status s2 = read_status(c);
+    return s2 != GDC_OK ? s2 : st;
 }
 
 // FCM mode: each template's block of M_FCM for the template alone at the centre of the
@@ -478,6 +507,7 @@ static gdc_status one_step(gdc_ctx* c, gdc_step_info* info) {
         st = gmres_solve(c, c->gm_b, c->gm_x, &inf.solve);
         if (st != GDC_OK) return st;
         launch_scatter_solution(c, c->gm_x, c->Vm, nullptr);
+        if ((st = read_status(c)) != GDC_OK) return st;   // no advance on a flagged failure
         launch_advance(c, c->Y, c->q, c->Vm, dt, nullptr, c->Y, c->q);
         matvecs = inf.lanczos_iters[2] + inf.solve.matvecs_fp32 + inf.solve.matvecs_fp64;
     } else {
@@ -522,6 +552,7 @@ static gdc_status one_step(gdc_ctx* c, gdc_step_info* info) {
         st = gmres_solve(c, c->gm_b, c->gm_x, &inf.solve);
         if (st != GDC_OK) return st;
         launch_scatter_solution(c, c->gm_x, c->Vm, nullptr);
+        if ((st = read_status(c)) != GDC_OK) return st;   // no advance on a flagged failure
         // step 6
         launch_advance(c, c->Y, c->q, c->Vm, dt, c->nu, c->Y, c->q);
         matvecs = inf.lanczos_iters[0] + inf.lanczos_iters[1] + inf.lanczos_iters[2] + inf.solve.matvecs_fp32 +
@@ -766,6 +797,8 @@ static gdc_status graph_step(gdc_ctx* c, gdc_step_info* info) {
                         inf.solve.matvecs_fp64;
     inf.pair_evals = (double)matvecs * c->pair_evals_per_matvec;
     // the host-driven path's checks, in its order
+    if ((r.status[0] != 0 || r.status[1] != 0) && clear_status(c) != GDC_OK) return GDC_ERR_CUDA;
+    if (r.status[1] != 0) return fail(c, GDC_ERR_TIMEOUT, "a pair-kernel tile copy did not complete in time");
     if (r.lz_notconv[0] || r.lz_notconv[2]) return fail(c, GDC_ERR_NOT_CONVERGED, "Lanczos reached lanczos_max_iter");
     if (r.gm_bad) return fail(c, GDC_ERR_NONFINITE, "mobility solve: non-finite residual");
     if (r.gm_notconv) return fail(c, GDC_ERR_NOT_CONVERGED, "mobility solve: GMRES reached gmres_max_iter");
@@ -783,6 +816,8 @@ static gdc_status graph_step(gdc_ctx* c, gdc_step_info* info) {
 using namespace gdc;
 
 extern "C" {
+
+void gdc_debug_wait_polls(int polls) { g_wait_polls.store(polls); }
 
 size_t gdc_workspace_bytes(const gdc_params* params, int n_templates, const int* tmpl_nblobs, int n_susp,
                            const long long* susp_body_off, const int* body_tmpl) {
@@ -916,6 +951,7 @@ gdc_status gdc_profile_read(gdc_ctx* c, gdc_profile_info* out) {
     out->autotune_ms = c->autotune_ms;
     out->pair_kernel = c->use_sym ? 2 : 1;
     out->sym_width = c->sym_width;
+    out->min_blocks_per_sm = c->use_sym ? c->sym_minb : c->mv_minb;
     double up = 0.0;
     for (int s = 0; s < c->S; ++s) {
         const double n = (double)(c->h_blob_off[s + 1] - c->h_blob_off[s]);
@@ -957,17 +993,17 @@ gdc_status gdc_mobility_solve(gdc_ctx* c, const double* FT, const double* vbrev,
     gdc_status st = gmres_solve(c, c->gm_b, c->gm_x, &inf);
     launch_scatter_solution(c, c->gm_x, V, lambda);
     if (info) *info = inf;
-    gdc_status e2 = cuda_check(c, cudaStreamSynchronize(c->stream), "mobility solve");
-    if (st == GDC_OK && e2 == GDC_OK) e2 = read_status(c);
-    return st != GDC_OK ? st : e2;
+    const gdc_status e2 = cuda_check(c, cudaStreamSynchronize(c->stream), "mobility solve");
+    return e2 != GDC_OK ? e2 : settle(c, st);
 }
 
 gdc_status gdc_step(gdc_ctx* c, int nsteps, gdc_step_info* info) {
     if (!c) return GDC_ERR_INVALID_ARG;
     if (nsteps < 0) return fail(c, GDC_ERR_INVALID_ARG, "nsteps must be >= 0");
     for (int k = 0; k < nsteps; ++k) {
-        gdc_status st = graph_usable(c) ? graph_step(c, info ? info + k : nullptr) : one_step(c, info ? info + k : nullptr);
-        if (st != GDC_OK) return st;
+        const bool graph = graph_usable(c);
+        gdc_status st = graph ? graph_step(c, info ? info + k : nullptr) : one_step(c, info ? info + k : nullptr);
+        if (st != GDC_OK) return graph ? st : settle(c, st);
     }
     return GDC_OK;
 }
@@ -1044,9 +1080,8 @@ gdc_status gdc_brownian_slip(gdc_ctx* c, const double* W, double* vbrev, int* it
     if (!c || !W || !vbrev) return c ? fail(c, GDC_ERR_INVALID_ARG, "NULL pointer") : GDC_ERR_INVALID_ARG;
     load_at(c, c->Y, c->q);
     gdc_status st = slip_at_loaded(c, W, vbrev, 0, iters, err);
-    gdc_status e2 = cuda_check(c, cudaStreamSynchronize(c->stream), "brownian slip");
-    if (st == GDC_OK && e2 == GDC_OK) e2 = read_status(c);
-    return st != GDC_OK ? st : e2;
+    const gdc_status e2 = cuda_check(c, cudaStreamSynchronize(c->stream), "brownian slip");
+    return e2 != GDC_OK ? e2 : settle(c, st);
 }
 
 gdc_status gdc_lsq_velocity(gdc_ctx* c, const double* vbrev, double* calV) {

@@ -33,6 +33,7 @@
 #define GDC_NEAR_SRC 2048        // sources per block of the near-pair search
 #define GDC_SYM_TILE 512         // blobs per tile of the symmetric FP32 pair kernel
 #define GDC_CELL_MIN_BLOBS 16384 // GDC_FORCES_CHOOSE: the cell list from this many blobs on
+#define GDC_WAIT_POLLS 400000    // default bound of a pair kernel's wait for a tile copy (polls)
 
 namespace gdc {
 
@@ -184,6 +185,7 @@ struct gdc_ctx {
     // pair-kernel work lists
     gdc::MvItem* mv_items = 0;
     int mv_n_items = 0, mv_tpt = 2, mv_threads = 128, mv_kmax = 1;
+    int mv_minb = 6;                          // resident blocks per SM the ordered kernel was compiled for (4, 6)
     double mv_waves = 8.0;
     int mv_cap_items = 0, mv_cap_kmax = 1;   // workspace capacity over all autotune candidates
     double autotune_ms = 0.0;                 // best FP32 product time found at init (0 = not tuned)
@@ -195,6 +197,7 @@ struct gdc_ctx {
 
     // symmetric FP32 pair kernel (each unordered pair once) and its work list
     int use_sym = 0, sym_width = 4, sym_n_items = 0, sym_kmax = 1;
+    int sym_minb = 2;                         // resident blocks per SM the kernel was compiled for (2, 3, 4)
     int sym_cap_items = 0, sym_cap_kmax = 1;
     long long sym_n_jslots = 0, sym_n_tiles = 0;
     gdc::SymItem* sym_items = 0;
@@ -298,6 +301,7 @@ __device__ inline double warp_sum(double v) {
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 // ---- host-side helpers (defined in api.cu) --------------------------------
+int first_wait_polls();   // poll bound of the pair kernels' waits for a tile copy (gdc_debug_wait_polls)
 gdc_status fail(gdc_ctx* c, gdc_status s, const std::string& msg);
 gdc_status cuda_check(gdc_ctx* c, cudaError_t e, const char* what);
 int prof_begin(gdc_ctx* c, int kind);     // records a start event when timing is on (-1 otherwise)

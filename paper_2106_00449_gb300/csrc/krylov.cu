@@ -5,8 +5,9 @@
 // are segmented per suspension.  Reductions are two-pass (per-chunk partials, then a
 // fixed-order sum per segment), so results are bitwise reproducible run to run.
 //
-// Precision: bases, inner products, Givens/Hessenberg and the small tridiagonal
-// eigenproblem of Lanczos are FP64.  In
+// Precision: bases, inner products, Givens/Hessenberg and the square root of the small
+// tridiagonal matrix of Lanczos are FP64 (at loose tolerances the stopping test alone runs
+// on FP32 eigen-steps).  In
 // GDC_FP32_MIXED mode the operator inside the Krylov loop uses the FP32 pair kernel; each
 // GMRES cycle ends with an accurate residual (double-float pairs, FP64 same-body blocks),
 // and the solver restarts from it until that residual meets gmres_tol (iterative refinement).
@@ -528,8 +529,22 @@ static size_t lz_tridiag_smem(int kmax) {
     return (size_t)4 * kmax * sizeof(double) + (size_t)kmax * lz_ldq(kmax) * sizeof(double);
 }
 
-// Givens rotation (c, s) with c x + s z = r, -s x + c z = 0, dividing by the correctly
-// rounded square root.
+// Givens rotation (c, s) with c x + s z = r, -s x + c z = 0.  FP32 (the stopping test at
+// loose tolerances) takes 1/r from the hardware reciprocal square root; FP64 divides by the
+// correctly rounded square root.
+__device__ inline void lz_givens(float x, float z, float& c, float& s, float& r) {
+    const float r2 = fmaf(x, x, z * z);
+    if (r2 > 0.f) {
+        const float ri = rsqrtf(r2);
+        c = x * ri;
+        s = z * ri;
+        r = r2 * ri;
+    } else {
+        c = 1.f;
+        s = 0.f;
+        r = 0.f;
+    }
+}
 __device__ inline void lz_givens(double x, double z, double& c, double& s, double& r) {
     r = sqrt(x * x + z * z);
     if (r > 0.0) {
@@ -542,13 +557,13 @@ __device__ inline void lz_givens(double x, double z, double& c, double& s, doubl
     }
 }
 
-// out[0..k) = wn * T_k^(1/2) e_1 for the k x k tridiagonal (al, be), computed in FP64 by
-// the whole warp; Q is k x k in shared memory with row stride ldq.  Returns false (on every
-// lane) when the QR iteration does not converge.
-__device__ bool lz_sqrt_e1(const double* al, const double* be, int k, double wn, double* Q, int ldq, double* out) {
-    using T = double;
+// out[0..k) = wn * T_k^(1/2) e_1 for the k x k tridiagonal (al, be), computed in precision T
+// by the whole warp; Q is k x k in shared memory with row stride ldq.  Returns false (on
+// every lane) when the QR iteration does not converge.
+template <typename T>
+__device__ bool lz_sqrt_e1_t(const double* al, const double* be, int k, double wn, T* Q, int ldq, double* out) {
     const int lane = threadIdx.x;
-    const T eps = T(1e-16);   // deflation threshold (relative)
+    const T eps = sizeof(T) == 4 ? T(1.2e-7) : T(1e-16);   // deflation threshold (relative)
     T d[GDC_MAX_LANCZOS], e[GDC_MAX_LANCZOS];
     for (int i = 0; i < k; ++i) {
         d[i] = (T)al[i];
@@ -626,6 +641,15 @@ __device__ bool lz_sqrt_e1(const double* al, const double* be, int k, double wn,
     return true;
 }
 
+// The square root that enters v-breve is always formed in FP64.  At loose tolerances
+// (lanczos_tol >= 1e-5) the stopping test alone compares FP32 iterates: their relative
+// error, about 1e-6, is far below the tolerance the change is compared with.
+__device__ inline bool lz_sqrt_e1(const double* al, const double* be, int k, double wn, double* Q, int ldq, double* out,
+                                  bool fp32) {
+    return fp32 ? lz_sqrt_e1_t<float>(al, be, k, wn, reinterpret_cast<float*>(Q), ldq, out)
+                : lz_sqrt_e1_t<double>(al, be, k, wn, Q, ldq, out);
+}
+
 // ||c_k - [c_{k-1}; 0]|| / ||c_k||, summed in the same order on every lane
 __device__ inline double lz_change(const double* ck, const double* cprev, int k) {
     double num = 0.0, den = 0.0;
@@ -691,7 +715,8 @@ __global__ void __launch_bounds__(32) k_lz_tridiag(int S, int j, const int* __re
     double* best = cm + kmax;
     double* Q = best + kmax;
     const int ldq = lz_ldq(kmax);
-    if (!lz_sqrt_e1(al, be, k, wn, Q, ldq, cur)) {
+    const bool check32 = !fixed_mode && tol >= 1e-5;   // FP32 stopping test, FP64 result
+    if (!lz_sqrt_e1(al, be, k, wn, Q, ldq, cur, check32)) {
         if (lead) {
             atomicExch(status, 2);
             active[s] = 0;
@@ -723,7 +748,7 @@ __global__ void __launch_bounds__(32) k_lz_tridiag(int S, int j, const int* __re
                 __syncwarp();
                 double best_err = ee;
                 for (int kk = k - 1; kk >= 2; --kk) {
-                    if (!lz_sqrt_e1(al, be, kk - 1, wn, Q, ldq, cm)) break;
+                    if (!lz_sqrt_e1(al, be, kk - 1, wn, Q, ldq, cm, check32)) break;
                     const double e2 = lz_change(ck, cm, kk);
                     if (!(e2 < tol)) break;
                     kstar = kk;
@@ -742,9 +767,20 @@ __global__ void __launch_bounds__(32) k_lz_tridiag(int S, int j, const int* __re
             }
         }
     }
+    if (k >= kmax) stop = true;
+    if (stop && check32) {   // the result at the stopping index, in FP64
+        __syncwarp();
+        if (!lz_sqrt_e1(al, be, kstar, wn, Q, ldq, cur, false)) {
+            if (lead) {
+                atomicExch(status, 2);
+                active[s] = 0;
+                err[s] = 1.0;
+            }
+            return;
+        }
+    }
     __syncwarp();   // every lane has read lastk and cs_ before they are written
     for (int r = lane; r < kstar; r += 32) cs_[r] = cur[r];
-    if (k >= kmax) stop = true;
     if (lead) {
         if (firstk < 0) lastk[S + s] = k;
         lastk[s] = k;

@@ -57,8 +57,10 @@ __device__ __forceinline__ void bulk_tile_load(void* dst, const void* src, unsig
     (void)state;
 }
 
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
-    for (int i = 0; i < 400000; ++i) {
+// Bounded wait for the phase `parity` of an mbarrier: false after `polls` unsuccessful
+// polls (none at all when polls <= 0).
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, int polls = GDC_WAIT_POLLS) {
+    for (int i = 0; i < polls; ++i) {
         unsigned done;
         asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
                      : "=r"(done) : "r"(smem_addr(bar)), "r"(parity) : "memory");

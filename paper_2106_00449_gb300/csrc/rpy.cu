@@ -69,16 +69,15 @@ void launch_pack_lambda(gdc_ctx* c, int prec, const double* x, int gm_layout) {
 // memory, completed on an mbarrier.  Two buffers: the copy of tile t+1 runs while tile t
 // is evaluated.  Waits are bounded; on a timeout the kernel flags status[1] and returns.
 
-#ifndef GDC_RPY32_MINB
-#define GDC_RPY32_MINB 6   // minimum resident blocks per SM requested from the register allocator
-#endif
-
-template <int P>
-__global__ void __launch_bounds__(128, GDC_RPY32_MINB) k_rpy32(const MvItem* __restrict__ items, const int* __restrict__ active,
+// MINB: resident blocks per SM the register allocator is asked to allow, 4 (112 / 124
+// registers for P = 1 / 2) or 6 (76 / 80, the latter with a few spilled bytes); the
+// autotuner times both.
+template <int P, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_rpy32(const MvItem* __restrict__ items, const int* __restrict__ active,
                                                const long long* __restrict__ susp_blob_off,
                                                const float4* __restrict__ spos, const float4* __restrict__ sdup,
                                                float4* __restrict__ part, int NBL, RpyConst32 k,
-                                               int* __restrict__ status) {
+                                               int* __restrict__ status, int first_polls) {
     __shared__ __align__(128) float4 shbuf[2][3 * MV_TILE];
     __shared__ __align__(8) unsigned long long mbar[2];
     const MvItem it = items[blockIdx.x];
@@ -124,7 +123,7 @@ __global__ void __launch_bounds__(128, GDC_RPY32_MINB) k_rpy32(const MvItem* __r
             bulk_tile_load(shbuf[(t + 1) & 1], sdup + 3 * (b0 + j1n), 48u * (unsigned)min(MV_TILE, it.j1 - j1n),
                            &mbar[(t + 1) & 1]);
         }
-        const bool ok = mbar_wait(&mbar[t & 1], (unsigned)((t >> 1) & 1));
+        const bool ok = mbar_wait(&mbar[t & 1], (unsigned)((t >> 1) & 1), first_polls);
         float2 tx[P], ty[P], tz[P];
 #pragma unroll
         for (int p = 0; p < P; ++p) tx[p] = ty[p] = tz[p] = make_float2(0.f, 0.f);
@@ -169,10 +168,12 @@ __global__ void __launch_bounds__(128, GDC_RPY32_MINB) k_rpy32(const MvItem* __r
             y = sub2(tz[p], cz[p]); u = add2(az[p], y); cz[p] = sub2(sub2(u, az[p]), y); az[p] = u;
         }
         // every thread is done with this buffer before it is refilled; a timed-out copy stops the block
+        // after its copies in flight have landed: tile t's (whose wait gave up) and tile t+1's
         if (__syncthreads_or(!ok)) {
             if (threadIdx.x == 0) {
                 atomicExch(status + 1, 1);
-                if (t + 1 < ntile) mbar_wait(&mbar[(t + 1) & 1], (unsigned)(((t + 1) >> 1) & 1));   // copy in flight
+                mbar_wait(&mbar[t & 1], (unsigned)((t >> 1) & 1));
+                if (t + 1 < ntile) mbar_wait(&mbar[(t + 1) & 1], (unsigned)(((t + 1) >> 1) & 1));
             }
             return;
         }
@@ -408,16 +409,27 @@ void launch_rpy(gdc_ctx* c, int prec) {
         const double a = c->p.a;
         const RpyConst32 k = rpy_const32(a);
         // two targets per packed lane pair: tpt 4 -> P = 2, otherwise P = 1
-        if (c->use_sym)
+#define GDC_RPY32_LAUNCH(PP, MB)                                                                             \
+    k_rpy32<PP, MB><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->mv_active, c->susp_blob_off, c->spos, \
+                                                          c->sdup, (float4*)c->mv_part, c->NBL, k, c->dev_status, \
+                                                          first_wait_polls())
+        if (c->use_sym) {
             launch_rpy32_sym(c);
-        else if (c->mv_tpt == 4)
-            ++c->n_launch, k_rpy32<2><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->mv_active, c->susp_blob_off, c->spos,
-                                                                            c->sdup, (float4*)c->mv_part, c->NBL, k,
-                                                                            c->dev_status);
-        else
-            ++c->n_launch, k_rpy32<1><<<c->mv_n_items, 128, 0, c->stream>>>(c->mv_items, c->mv_active, c->susp_blob_off, c->spos,
-                                                                            c->sdup, (float4*)c->mv_part, c->NBL, k,
-                                                                            c->dev_status);
+        } else {
+            ++c->n_launch;
+            if (c->mv_tpt == 4) {
+                if (c->mv_minb == 4)
+                    GDC_RPY32_LAUNCH(2, 4);
+                else
+                    GDC_RPY32_LAUNCH(2, 6);
+            } else {
+                if (c->mv_minb == 4)
+                    GDC_RPY32_LAUNCH(1, 4);
+                else
+                    GDC_RPY32_LAUNCH(1, 6);
+            }
+        }
+#undef GDC_RPY32_LAUNCH
     } else if (prec == GDC_PREC_DF64) {
         const RpyConstDF k = df_constants(c->p.a);
         if (c->mv_tpt == 4)
@@ -917,6 +929,8 @@ namespace gdc {
 static const int kTpt[2] = {2, 4};
 static const double kWaves[3] = {4.0, 8.0, 16.0};
 static const int kSymWidth[3] = {2, 4, 8};   // source tiles per item of the symmetric kernel
+static const int kSymMinBlocks[3] = {2, 3, 4};   // resident blocks per SM of the symmetric kernel
+static const int kMvMinBlocks[2] = {4, 6};       // resident blocks per SM of the ordered kernel
 
 void plan_mv_capacity(gdc_ctx* c) {
     int cap_items = 0, cap_k = 1;
@@ -973,34 +987,45 @@ gdc_status autotune_pair_kernel(gdc_ctx* c) {
         if (s2 == GDC_OK) cudaEventElapsedTime(&ms, e0, e1);
         return s2;
     };
+    int bmv_minb = 6;
     if (only != 2) {
         c->use_sym = 0;
         for (int a = 0; a < 2 && st == GDC_OK; ++a)
-            for (int b = 0; b < 3; ++b) {
+            for (int b = 0; b < 3 && st == GDC_OK; ++b) {
                 build_mv_items(c, kTpt[a], kWaves[b]);
                 if ((st = upload_items(c)) != GDC_OK) break;
-                float ms = 0.f;
-                if ((st = time3(ms)) != GDC_OK) break;
-                if (ms < best) {
-                    best = ms;
-                    bt = kTpt[a];
-                    bw = kWaves[b];
-                    bsym = 0;
+                for (int mb : kMvMinBlocks) {
+                    c->mv_minb = mb;
+                    float ms = 0.f;
+                    if ((st = time3(ms)) != GDC_OK) break;
+                    if (ms < best) {
+                        best = ms;
+                        bt = kTpt[a];
+                        bw = kWaves[b];
+                        bmv_minb = mb;
+                        bsym = 0;
+                    }
                 }
             }
     }
+    int bminb = 2;
     if (only != 1 && st == GDC_OK) {
         c->use_sym = 1;
         for (int w : kSymWidth) {
             build_sym_items(c, w);
             if ((st = sym_upload(c)) != GDC_OK) break;
-            float ms = 0.f;
-            if ((st = time3(ms)) != GDC_OK) break;
-            if (ms < best) {
-                best = ms;
-                bwid = w;
-                bsym = 1;
+            for (int mb : kSymMinBlocks) {
+                c->sym_minb = mb;
+                float ms = 0.f;
+                if ((st = time3(ms)) != GDC_OK) break;
+                if (ms < best) {
+                    best = ms;
+                    bwid = w;
+                    bminb = mb;
+                    bsym = 1;
+                }
             }
+            if (st != GDC_OK) break;
         }
     }
     cudaEventDestroy(e0);
@@ -1009,6 +1034,8 @@ gdc_status autotune_pair_kernel(gdc_ctx* c) {
     build_mv_items(c, bt, bw);
     build_sym_items(c, bwid);
     c->use_sym = bsym;
+    c->sym_minb = bminb;
+    c->mv_minb = bmv_minb;
     c->autotune_ms = best / 3.0;
     if ((st = upload_items(c)) != GDC_OK) return st;
     return sym_upload(c);
@@ -1049,28 +1076,42 @@ struct NoallocScratch {
     int near_cnt[GDC_NOALLOC_MAX_BLOBS];
     int near_idx[GDC_NOALLOC_MAX_BLOBS * GDC_NEAR_CAP];
     long long susp_blob_off[2];
+    double cen[3];   // blob centroid of the call (the FP32 positions are taken relative to it)
     int status[4];   // set by the pair kernel if a tile copy times out (u is then incomplete)
 };
 
 static __device__ __align__(256) NoallocScratch g_noalloc_scratch;
 
+// Start of a call: the blob centroid (one block; per-thread strided sums added in a fixed
+// tree order, so the result does not depend on timing) and the status words cleared.
+__global__ void __launch_bounds__(256) k_noalloc_begin(NoallocScratch* __restrict__ sc, const double* __restrict__ r,
+                                                       int n) {
+    __shared__ double part[3][256];
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int i = threadIdx.x; i < n; i += 256)
+        for (int d = 0; d < 3; ++d) acc[d] += r[3 * i + d];
+    for (int d = 0; d < 3; ++d) part[d][threadIdx.x] = acc[d];
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h)
+            for (int d = 0; d < 3; ++d) part[d][threadIdx.x] += part[d][threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) sc->cen[threadIdx.x] = part[threadIdx.x][0] / n;
+    if (threadIdx.x < 4) sc->status[threadIdx.x] = 0;
+}
+
 // Positions relative to the blob centroid (FP32), lambda, identity body table, work list.
 __global__ void k_noalloc_prepare(NoallocScratch* __restrict__ sc, const double* __restrict__ r,
                                   const double* __restrict__ lam, int n, int nk, int csz) {
-    __shared__ double cen[3];
-    if (threadIdx.x < 3) {
-        double acc = 0.0;
-        for (int i = 0; i < n; ++i) acc += r[3 * i + threadIdx.x];
-        cen[threadIdx.x] = acc / n;
-    }
-    __syncthreads();
+    const double c0 = sc->cen[0], c1 = sc->cen[1], c2 = sc->cen[2];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         sc->near_cnt[i] = 0;
         if (i % 256 == 0)   // near-pair blocks: 256 targets x source chunks of GDC_NEAR_SRC
             for (int j0 = 0, q = 0; j0 < n; j0 += GDC_NEAR_SRC, ++q)
                 sc->near_items[(i / 256) * ((n + GDC_NEAR_SRC - 1) / GDC_NEAR_SRC) + q] =
                     make_int4(0, i, j0, min(n, j0 + GDC_NEAR_SRC));
-        const float x = (float)(r[3 * i] - cen[0]), y = (float)(r[3 * i + 1] - cen[1]), z = (float)(r[3 * i + 2] - cen[2]);
+        const float x = (float)(r[3 * i] - c0), y = (float)(r[3 * i + 1] - c1), z = (float)(r[3 * i + 2] - c2);
         const float lx = (float)lam[3 * i], ly = (float)lam[3 * i + 1], lz = (float)lam[3 * i + 2];
         sc->spos[i] = make_float4(x, y, z, __int_as_float(i));
         sc->sdup[3 * i] = make_float4(x, x, y, y);
@@ -1099,6 +1140,10 @@ __global__ void k_noalloc_epilogue(const NoallocScratch* __restrict__ sc, const 
                                    double* __restrict__ u) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    if (sc->status[1] != 0) {   // a tile copy of the pair kernel timed out: u would be incomplete
+        u[3 * i] = u[3 * i + 1] = u[3 * i + 2] = __longlong_as_double(0x7ff8000000000000LL);
+        return;
+    }
     double x = 0.0, y = 0.0, z = 0.0;
     for (int k = 0; k < nk; ++k) {
         const float4 v = sc->part[(long long)k * GDC_NOALLOC_MAX_BLOBS + i];
@@ -1170,6 +1215,7 @@ extern "C" gdc_status gdc_rpy_apply_noalloc(const double* r, const double* lambd
     int csz = (n_blobs + nk - 1) / nk;
     csz = (csz + 31) / 32 * 32;
     nk = (n_blobs + csz - 1) / csz;
+    k_noalloc_begin<<<1, 256, 0, st>>>(sc, r, n_blobs);
     k_noalloc_prepare<<<std::min(1024, (n_blobs + 255) / 256 + 1), 256, 0, st>>>(sc, r, lambda, n_blobs, nk, csz);
     RpyConst32 k{(float)(2.0 * a * a / 3.0), (float)(2.0 * a * a), (float)(4.0 * a * a), (float)(4.0 / (3.0 * a)),
                  (float)(9.0 / (32.0 * a)), (float)(1.0 / (8.0 * a * a))};
@@ -1178,8 +1224,8 @@ extern "C" gdc_status gdc_rpy_apply_noalloc(const double* r, const double* lambd
     k_near_build<<<((n_blobs + 255) / 256) * near_chunks, 128, 0, st>>>(sc->near_items, sc->susp_blob_off, sc->spos,
                                                                        (float)(4.0 * a * a), sc->near_cnt, sc->near_idx);
     k_near_sort<<<(n_blobs + 255) / 256, 256, 0, st>>>(n_blobs, sc->near_cnt, sc->near_idx);
-    k_rpy32<1><<<ntile * nk, 128, 0, st>>>(sc->items, nullptr, sc->susp_blob_off, sc->spos, sc->sdup, sc->part,
-                                             GDC_NOALLOC_MAX_BLOBS, k, sc->status);
+    k_rpy32<1, 6><<<ntile * nk, 128, 0, st>>>(sc->items, nullptr, sc->susp_blob_off, sc->spos, sc->sdup, sc->part,
+                                             GDC_NOALLOC_MAX_BLOBS, k, sc->status, first_wait_polls());
     k_noalloc_epilogue<<<(n_blobs + 255) / 256, 256, 0, st>>>(sc, r, lambda, n_blobs, nk,
                                                               1.0 / (8.0 * 3.141592653589793 * eta), a, u);
     e = cudaGetLastError();

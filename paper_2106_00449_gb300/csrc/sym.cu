@@ -27,22 +27,23 @@ namespace gdc {
 constexpr int SYM_TILE = GDC_SYM_TILE;
 constexpr int SYM_SMEM = 3 * SYM_TILE * 16 + 3 * 4 * SYM_TILE * 4 + 16;   // tile, 4 warps' sums, mbarrier
 
-#ifndef GDC_SYM_MINB
-#define GDC_SYM_MINB 2   // the fully unrolled sweep wants registers (184) more than warps
-#endif
+// Resident blocks per SM the register allocator is asked to allow (MINB): 2 (184 registers),
+// 3 (165) or 4 (126), none spilling; the autotuner times each with each work-item width.
 
 __device__ __forceinline__ float2 shfl2(float2 v, int src) {
     return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
 }
 
-__global__ void __launch_bounds__(128, GDC_SYM_MINB) k_rpy32_sym(const SymItem* __restrict__ items,
+template <int MINB>
+__global__ void __launch_bounds__(128, MINB) k_rpy32_sym(const SymItem* __restrict__ items,
                                                                  const int* __restrict__ active,
                                                                  const long long* __restrict__ susp_blob_off,
                                                                  const long long* __restrict__ jbase,
                                                                  const float4* __restrict__ spos,
                                                                  const float4* __restrict__ sdup,
                                                                  float4* __restrict__ part_i, float4* __restrict__ part_j,
-                                                                 int NBL, RpyConst32 k, int* __restrict__ status) {
+                                                                 int NBL, RpyConst32 k, int* __restrict__ status,
+                                                                 int first_polls) {
     extern __shared__ __align__(128) float4 dsm[];
     float4* sh = dsm;                                             // the source tile, sdup layout
     float* jsx = reinterpret_cast<float*>(dsm + 3 * SYM_TILE);    // [warp][source] source-side sums
@@ -101,7 +102,7 @@ __global__ void __launch_bounds__(128, GDC_SYM_MINB) k_rpy32_sym(const SymItem* 
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             bulk_tile_load(sh, sdup + 3 * (b0 + j0), 48u * (unsigned)n, mbar);
         }
-        const bool ok = mbar_wait(mbar, phase);
+        const bool ok = mbar_wait(mbar, phase, first_polls);
         phase ^= 1u;
         // sources past the end of the suspension: position 0, lambda 0 (they add nothing)
         for (int e = n + threadIdx.x; e < nr; e += 128)
@@ -272,14 +273,26 @@ gdc_status sym_upload(gdc_ctx* c) {
 }
 
 gdc_status sym_init_attributes(gdc_ctx* c) {
-    return cuda_check(c, cudaFuncSetAttribute(k_rpy32_sym, cudaFuncAttributeMaxDynamicSharedMemorySize, SYM_SMEM),
-                      "symmetric pair kernel attributes");
+    cudaError_t e = cudaFuncSetAttribute(k_rpy32_sym<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SYM_SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rpy32_sym<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, SYM_SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rpy32_sym<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, SYM_SMEM);
+    return cuda_check(c, e, "symmetric pair kernel attributes");
 }
 
 void launch_rpy32_sym(gdc_ctx* c) {
-    ++c->n_launch, k_rpy32_sym<<<c->sym_n_items, 128, SYM_SMEM, c->stream>>>(
-        c->sym_items, c->mv_active, c->susp_blob_off, c->sym_jbase, c->spos, c->sdup, c->sym_part_i, c->sym_part_j,
-        c->NBL, rpy_const32(c->p.a), c->dev_status);
+#define GDC_SYM_LAUNCH(MB)                                                                                         \
+    k_rpy32_sym<MB><<<c->sym_n_items, 128, SYM_SMEM, c->stream>>>(c->sym_items, c->mv_active, c->susp_blob_off,     \
+                                                                  c->sym_jbase, c->spos, c->sdup, c->sym_part_i,   \
+                                                                  c->sym_part_j, c->NBL, rpy_const32(c->p.a),      \
+                                                                  c->dev_status, first_wait_polls())
+    ++c->n_launch;
+    if (c->sym_minb == 3)
+        GDC_SYM_LAUNCH(3);
+    else if (c->sym_minb == 4)
+        GDC_SYM_LAUNCH(4);
+    else
+        GDC_SYM_LAUNCH(2);
+#undef GDC_SYM_LAUNCH
 }
 
 }  // namespace gdc

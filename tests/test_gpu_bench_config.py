@@ -79,7 +79,7 @@ def test_gdc_step_at_bench_config(lib, which):
     Y1, q1, _ = ctx.get_state()
     assert info["solve"]["converged"] and info["solve"]["residual"] <= 1e-6, info
     assert info["lanczos_err"] < LZ_TOL
-    op = oracle_params(wl, rfd_delta=1e-3, lanczos_tol=LZ_TOL, sqrt_mode="block")
+    op = oracle_params(wl, rfd_delta=1e-3, sqrt_lanczos_tol=LZ_TOL, sqrt_mode="block")
     vbn, vbm = _host(tr["vb_n"]), _host(tr["vb_m"])
     calV, nu, Vm = _host(tr["calV"]).reshape(-1, 6), _host(tr["nu"]), _host(tr["Vm"]).reshape(-1, 6)
     k_ora = [0, 0]
