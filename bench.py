@@ -268,6 +268,30 @@ def run_reference(args, world, rank):
     return 0
 
 
+def c4_batching(g, torch, WL, common, n_susp: int) -> dict:
+    """The batching leg on a sample of the c4 workload (its first n_susp suspensions, 8-128
+    bodies each): steps/s of the batched context (graph replay, 3 timed steps after 3
+    warm-ups) against the same suspensions one context per suspension, stepped one after
+    another."""
+    wl4 = WL.c4(seed=0, n_susp=n_susp)
+    ctx = g.context_from_workload(wl4, precision=g.FP32_MIXED, rfd_delta=1e-3, **common)
+    for _ in range(3):
+        ctx.step(1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(ctx.stream)
+    ctx.step(3)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    batched = 3.0 / (e0.elapsed_time(e1) / 1000.0)
+    del ctx
+    torch.cuda.empty_cache()
+    single = per_suspension_steps(g, torch, wl4, common, 0)
+    return {"workload": f"the first {n_susp} suspensions of c4 ({wl4.n_blobs} blobs, {wl4.n_bodies} bodies)",
+            "batched_steps_per_s": batched, "one_context_per_suspension_steps_per_s": single["steps_per_s"],
+            "batched_speedup": batched / single["steps_per_s"], "note": single["note"]}
+
+
 def per_suspension_steps(g, torch, wl, common, rank):
     """The suspensions of a batch advanced one context per suspension, one after another.
 
@@ -426,6 +450,8 @@ def main(argv=None) -> int:
     ap.add_argument("--fp64-steps", type=int, default=1, help="FP64 steps timed for the comparison (0 = skip)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-products", type=int, default=3, help="full-size twin products timed for cpu_baseline")
+    ap.add_argument("--c4-suspensions", type=int, default=64,
+                    help="suspensions of the c4 batching leg of the default run (0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="c3_65k",
                     help="c3_65k (default), c4 or c5 for the step benchmark; any synthetic workload for --op")
@@ -566,6 +592,8 @@ def main(argv=None) -> int:
         line["one_suspension_per_launch"] = per_suspension_steps(g, torch, wl, common, rank)
         line["one_suspension_per_launch"]["batched_speedup"] = (
             value / world / line["one_suspension_per_launch"]["steps_per_s"])
+    elif rank == 0 and world == 1 and args.c4_suspensions > 0:
+        line["c4_batching"] = c4_batching(g, torch, WL, common, args.c4_suspensions)
     if args.workload != "c3_65k":
         if rank == 0:
             print(json.dumps(line), flush=True)
@@ -598,6 +626,7 @@ def main(argv=None) -> int:
         del ctx
         torch.cuda.empty_cache()
         ctx64 = g.context_from_workload(wl, precision=g.FP64, rfd_delta=1e-6, **common)
+        ctx64.step(1)          # warm-up: the graph capture of the FP64 step
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -606,7 +635,7 @@ def main(argv=None) -> int:
         e1.record(ctx64.stream)
         torch.cuda.synchronize()
         t64 = e0.elapsed_time(e1) / 1000.0
-        line["fp64"] = {"steps_per_s": args.fp64_steps / t64, "steps": args.fp64_steps, "warmup": 0,
+        line["fp64"] = {"steps_per_s": args.fp64_steps / t64, "steps": args.fp64_steps, "warmup": 1,
                         "residual_max": max(i["solve"]["residual"] for i in inf64),
                         "lanczos_iters": [i["lanczos_iters"] for i in inf64],
                         "gmres_iters": [i["solve"]["iterations"] for i in inf64],

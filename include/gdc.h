@@ -147,6 +147,19 @@ typedef struct {
                               returns L A^(1/2) W; 0 uses M itself and returns its symmetric
                               root M^(1/2) W.  Both roots S satisfy S S^T = M, so v-breve has
                               the covariance (2 kT / dt) M either way; 1 needs fewer products */
+    int    wall;           /* 1: the blobs move above a no-slip wall at z = 0 (the setting of the
+                              paper's RPY runs, Sec. 4.1 and 6.2): M is the RPY tensor plus its
+                              wall correction (the Rotne-Prager regularisation of the image system
+                              of a point force above a wall), every blob centre must stay above
+                              z = a (a blob reaching it stops the call with GDC_ERR_NONFINITE and
+                              leaves the state unchanged), and the per-body blocks of both
+                              preconditioners are set up for each body at every configuration
+                              (FP64 Cholesky per body); RPY mobility only, no background shear */
+    double wall_V0;        /* with wall: every blob at height h feels -dV/dh of
+                              V(h) = wall_V0 a exp(-(h - a)/wall_b) / (h - a) (Sec. 6.2: 23 kT) */
+    double wall_b;         /* its range, a length (Sec. 6.2: 0.5 a)                    */
+    double body_weight;    /* with wall: a force body_weight along -z on every body, shared
+                              equally by its blobs (Sec. 6.2: mg = 0.18 kT/a)            */
 } gdc_params;
 
 typedef struct {

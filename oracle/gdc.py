@@ -26,7 +26,10 @@ Readings of points the paper leaves open (each is also listed with the design no
 * FD (Eq. FD): the same sum over unit perturbations of each body coordinate.
 * Background shear u(r) = (shear_rate * y, 0, 0) enters the slip as
   M lambda - K V = -v-breve - u(r) at the mid-step solve only.
-* Forces are the soft blob repulsion of forces.py evaluated at the mid-step.
+* Forces are the soft blob repulsion of forces.py evaluated at the mid-step (and, above a
+  wall, the wall repulsion and the body weights of wall.py).
+* Above a wall (Params.wall) M is the wall-corrected mobility of wall.py and the
+  block-preconditioned root uses the lab-frame Cholesky factor of each body's block.
 * The update x^(n+1) = x^n + nu dt V^m uses Omega^m directly as du/dt,
   which is exact because u^n = 0 and D^-1 at 0 is I (App. A).
 """
@@ -36,7 +39,7 @@ import dataclasses
 
 import numpy as np
 
-from . import forces, geometry, lanczos, rigid, rpy
+from . import forces, geometry, lanczos, rigid, rpy, wall
 
 
 @dataclasses.dataclass
@@ -57,6 +60,10 @@ class Params:
     # from a workload's lanczos_tol, which configures the library, not the oracle)
     sqrt_lanczos_tol: float = 0.0
     sqrt_lanczos_max_iter: int = 128
+    wall: bool = False          # blobs above a no-slip wall at z = 0 (wall.py)
+    wall_V0: float = 0.0        # wall repulsion strength V0 (Sec. 6.2: 23 kT), 0 = off
+    wall_b: float = 0.5         # its range b, a length (Sec. 6.2: 0.5 a)
+    body_weight: float = 0.0    # mg of every body, along -z (Sec. 6.2: 0.18 kT/a)
 
     @classmethod
     def from_dict(cls, d: dict) -> "Params":
@@ -81,6 +88,11 @@ def sqrt_apply(M: np.ndarray, W: np.ndarray, mode: str, L: np.ndarray = None) ->
     return S @ W
 
 
+def mobility_matrix(r: np.ndarray, p: Params) -> np.ndarray:
+    """The dense blob mobility M: unbounded RPY (Sec. 4.1), or wall-corrected (wall.py)."""
+    return wall.wall_matrix(r, p.a, p.eta) if p.wall else rpy.rpy_matrix(r, p.a, p.eta)
+
+
 def brownian_slip_k(layout, Y, q, W, p: Params, fixed_k: int = None):
     """Blob positions, M, K, B, v-breve = sqrt(2kT/dt) M^(1/2) W at state (Y, q), and the
     Lanczos iteration count (None for a dense root).
@@ -89,10 +101,12 @@ def brownian_slip_k(layout, Y, q, W, p: Params, fixed_k: int = None):
     (or with exactly fixed_k iterations) on the operator of sqrt_mode: A = L^-1 M L^-T with
     the result multiplied by L ("block"), or M itself ("sym")."""
     r = geometry.blob_positions(layout, Y, q)
-    M = rpy.rpy_matrix(r, p.a, p.eta)
+    M = mobility_matrix(r, p)
     K = rigid.k_matrix(r, Y, layout.blob_body)
     B = rigid.rigid_basis(K, layout.n_bodies)
-    L = rigid.block_factor(layout, q, p.a, p.eta) if p.sqrt_mode == "block" else None
+    L = None
+    if p.sqrt_mode == "block":
+        L = rigid.block_factor_lab(layout, M) if p.wall else rigid.block_factor(layout, q, p.a, p.eta)
     scale = np.sqrt(2.0 * p.kT / p.dt)
     k = None
     if p.sqrt_lanczos_tol > 0.0 and p.sqrt_mode in ("block", "sym"):
@@ -165,6 +179,8 @@ def midpoint_solve(layout, Ym, qm, W, p: Params):
     """Step 5: full mobility solve at the mid-step with the same W (Eq. step5)."""
     r, M, K, B, vb, k = brownian_slip_k(layout, Ym, qm, W, p)
     f = forces.blob_forces(r, layout.blob_body, p.rep_A, p.rep_b, p.a, p.potential, p.well_A, p.well_lambda)
+    if p.wall:
+        f = f + wall.blob_wall_forces(r, layout.blob_body, layout.n_bodies, p.wall_V0, p.wall_b, p.a, p.body_weight)
     FT = forces.body_force_torque(r, Ym, layout.blob_body, f)
     slip = vb.copy()
     if p.shear_rate != 0.0:
@@ -258,7 +274,7 @@ def em_step(layout, Y, q, W, p: Params) -> dict:
 def body_mobility_at(layout, Y, q, p: Params) -> np.ndarray:
     """Dense N(x) = (K^T M^-1 K)^-1 at state (Y, q) (Eq. body_mob)."""
     r = geometry.blob_positions(layout, Y, q)
-    M = rpy.rpy_matrix(r, p.a, p.eta)
+    M = mobility_matrix(r, p)
     K = rigid.k_matrix(r, Y, layout.blob_body)
     B = rigid.rigid_basis(K, layout.n_bodies)
     return rigid.body_mobility(M, K, B)

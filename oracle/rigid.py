@@ -144,6 +144,17 @@ def block_factor(layout, q: np.ndarray, a: float, eta: float) -> np.ndarray:
     return L
 
 
+def block_factor_lab(layout, M: np.ndarray) -> np.ndarray:
+    """diag_p(chol(M_pp)): the lower Cholesky factor of each body's diagonal block of M, in the
+    lab frame.  Used when M_pp is not a rotated template block (above a wall, where the
+    mobility of a body depends on its height and orientation)."""
+    L = np.zeros_like(M)
+    for p in range(layout.n_bodies):
+        i0, i1 = 3 * layout.blob_off[p], 3 * layout.blob_off[p + 1]
+        L[i0:i1, i0:i1] = np.linalg.cholesky(M[i0:i1, i0:i1])
+    return L
+
+
 def sqrtm_block(M: np.ndarray, L: np.ndarray) -> np.ndarray:
     """S = L (L^-1 M L^-T)^(1/2): the square root that preconditioned Lanczos converges to.
 

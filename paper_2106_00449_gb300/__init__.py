@@ -64,7 +64,8 @@ class _Params(ctypes.Structure):
                 ("pair_kernel", ctypes.c_int), ("potential", ctypes.c_int), ("well_A", ctypes.c_double),
                 ("well_lambda", ctypes.c_double), ("force_method", ctypes.c_int), ("mobility", ctypes.c_int),
                 ("box_L", ctypes.c_double), ("fcm_N", ctypes.c_int), ("fcm_sigma", ctypes.c_double),
-                ("fcm_R_t", ctypes.c_double), ("lanczos_precond", ctypes.c_int)]
+                ("fcm_R_t", ctypes.c_double), ("lanczos_precond", ctypes.c_int), ("wall", ctypes.c_int),
+                ("wall_V0", ctypes.c_double), ("wall_b", ctypes.c_double), ("body_weight", ctypes.c_double)]
 
 
 class _FcmParams(ctypes.Structure):
@@ -130,6 +131,10 @@ class Params:
     fcm_sigma: float = 0.0   # 0: a / sqrt(pi)
     fcm_R_t: float = 0.0     # 0: 3a
     lanczos_precond: int = 1  # 1: block-preconditioned Lanczos (root L (L^-1 M L^-T)^(1/2)), 0: M^(1/2)
+    wall: int = 0            # 1: blobs above a no-slip wall at z = 0 (wall-corrected RPY)
+    wall_V0: float = 0.0     # wall repulsion strength (Sec. 6.2: 23 kT)
+    wall_b: float = 0.5      # its range (Sec. 6.2: 0.5 a)
+    body_weight: float = 0.0  # mg per body along -z (Sec. 6.2: 0.18 kT/a)
 
     def _c(self) -> _Params:
         return _Params(**{f.name: getattr(self, f.name) for f in dataclasses.fields(self)})
@@ -531,6 +536,8 @@ def context_from_workload(wl, **overrides) -> Context:
     kw = dict(eta=pp["eta"], kT=pp["kT"], a=pp["a"], dt=pp["dt"], gmres_tol=pp.get("gmres_tol", 1e-6),
               lanczos_tol=pp.get("lanczos_tol", 1e-4), rfd_delta=pp.get("rfd_delta", 1e-6), rep_A=pp.get("rep_A", 0.0),
               rep_b=pp.get("rep_b", 0.1), shear_rate=pp.get("shear_rate", 0.0), seed=int(pp.get("seed", 0)),
-              potential=int(pp.get("potential", 0)), well_A=pp.get("well_A", 0.0), well_lambda=pp.get("well_lambda", 0.5))
+              potential=int(pp.get("potential", 0)), well_A=pp.get("well_A", 0.0), well_lambda=pp.get("well_lambda", 0.5),
+              wall=int(pp.get("wall", 0)), wall_V0=pp.get("wall_V0", 0.0), wall_b=pp.get("wall_b", 0.5),
+              body_weight=pp.get("body_weight", 0.0))
     kw.update(overrides)
     return Context(Params(**kw), wl.templates, wl.body_tmpl, wl.susp_body_off, wl.Y, wl.q)

@@ -97,6 +97,16 @@ static const char* validate_params(const gdc_params* p) {
             return "with the periodic FCM mobility the pair-force cutoff must fit 3 times in box_L";
         if (p->shear_rate != 0.0) return "a background shear is not periodic: not available with the FCM mobility";
     }
+    if (p->wall != 0 && p->wall != 1) return "wall must be 0 or 1";
+    if (p->wall) {
+        if (p->mobility != GDC_MOB_RPY) return "the wall-corrected mobility is an RPY mobility (mobility 0)";
+        if (p->shear_rate != 0.0) return "a background shear is not available above a wall";
+        if (!(p->wall_V0 >= 0.0) || !std::isfinite(p->wall_V0)) return "wall_V0 must be >= 0";
+        if (p->wall_V0 > 0.0 && !(p->wall_b > 0.0 && std::isfinite(p->wall_b))) return "wall_b must be > 0";
+        if (!std::isfinite(p->body_weight)) return "body_weight must be finite";
+    } else if (p->wall_V0 != 0.0 || p->body_weight != 0.0) {
+        return "wall_V0 and body_weight need wall = 1";
+    }
     return nullptr;
 }
 
@@ -162,6 +172,12 @@ static const char* build_host_layout(gdc_ctx* c, const gdc_params* p, int n_temp
     c->num_sms = sms;
     plan_mv_capacity(c);
     setup_segments(c);
+    c->h_blk_off.assign(NB + 1, 0);
+    for (long long b = 0; b < NB; ++b) {
+        const long long n3 = 3 * (c->h_body_blob_off[b + 1] - c->h_body_blob_off[b]);
+        c->h_blk_off[b + 1] = c->h_blk_off[b] + (p->wall ? n3 * n3 : 0);
+    }
+    if (p->wall) build_wall_items(c);
     return nullptr;
 }
 
@@ -318,6 +334,18 @@ static size_t carve(gdc_ctx* c, void* base) {
     c->rep = w.take<StepReport>(1);
     c->lz_vcur = w.take<double>(nl);
     c->gm_vcur = w.take<double>(n);
+    if (c->p.wall) {
+        const long long tot = c->h_blk_off[NB];
+        c->blk_off = w.take<long long>(NB + 1);
+        c->blk_work = w.take<double>(2 * tot);
+        c->blk_Minv = w.take<double>(tot);
+        c->blk_LT = w.take<double>(tot);
+        c->blk_X = w.take<double>(tot);
+        c->blk_XT = w.take<double>(tot);
+        c->blk_G = w.take<double>(18 * NBL);
+        c->blk_N = w.take<double>(36 * NB);
+        c->wall_items = w.take<int2>((long long)c->h_wall_items.size());
+    }
     return w.off + 256;
 }
 
@@ -366,6 +394,10 @@ static gdc_status upload_layout(gdc_ctx* c, const double* tmpl_xyz_centred) {
     chk(up(c, c->mv_items, c->h_mv_items.data(), c->h_mv_items.size()));
     chk(up(c, c->near_items, c->h_near_items.data(), c->h_near_items.size()));
     chk(up(c, c->mv_nk, c->h_mv_nk.data(), S));
+    if (c->p.wall) {
+        chk(up(c, c->blk_off, c->h_blk_off.data(), NB + 1));
+        chk(up(c, c->wall_items, c->h_wall_items.data(), c->h_wall_items.size()));
+    }
     chk(cudaMemsetAsync(c->dev_status, 0, 4 * sizeof(int), c->stream));
     chk(cudaMemsetAsync(c->lz_hint, 0, sizeof(int) * S, c->stream));
     chk(cudaStreamSynchronize(c->stream));  // host vectors above go out of scope
@@ -396,9 +428,10 @@ static gdc_status read_status(gdc_ctx* c) {
     cudaError_t e = cudaMemcpyAsync(st, c->dev_status, sizeof(st), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_check(c, e, "status read");
-    if ((st[0] != 0 || st[1] != 0) && clear_status(c) != GDC_OK) return GDC_ERR_CUDA;
+    if ((st[0] != 0 || st[1] != 0 || st[2] != 0) && clear_status(c) != GDC_OK) return GDC_ERR_CUDA;
     // a timed-out tile copy first: an incomplete product explains any later failure
     if (st[1] != 0) return fail(c, GDC_ERR_TIMEOUT, "a pair-kernel tile copy did not complete in time");
+    if (st[2] != 0) return fail(c, GDC_ERR_NONFINITE, "a blob centre reached the wall (height <= a)");
     if (st[0] == 1) return fail(c, GDC_ERR_NONFINITE, "template RPY block is not positive definite");
     if (st[0] == 2) return fail(c, GDC_ERR_NOT_CONVERGED, "tridiagonal eigensolver did not converge");
     return GDC_OK;
@@ -457,8 +490,12 @@ static void load_at(gdc_ctx* c, const double* Y, const double* q) {
 }
 
 static gdc_status forces_at_loaded(gdc_ctx* c, double* FT) {
-    if (forces_on(c->p)) {
-        launch_forces(c, c->p.precision, c->fblob);
+    if (forces_on(c->p) || c->p.wall) {
+        if (forces_on(c->p))
+            launch_forces(c, c->p.precision, c->fblob);
+        else
+            cudaMemsetAsync(c->fblob, 0, sizeof(double) * 3 * c->NBL, c->stream);
+        if (c->p.wall) launch_wall_forces(c, c->fblob);   // Sec. 6.2: wall repulsion and weight
         launch_body_KT(c, c->fblob, 0, FT, 0, 1.0);
     } else {
         cudaMemsetAsync(FT, 0, sizeof(double) * 6 * c->NB, c->stream);
@@ -606,7 +643,7 @@ __global__ void k_step_begin(StepReport* rep) {
 // the state is advanced only when no stage failed (the host-driven path returns early instead)
 __global__ void k_step_ok(StepReport* rep, const int* __restrict__ status) {
     const bool bad = rep->lz_notconv[0] || rep->lz_notconv[1] || rep->lz_notconv[2] || rep->gm_bad ||
-                     rep->gm_notconv || status[0] != 0 || status[1] != 0;
+                     rep->gm_notconv || status[0] != 0 || status[1] != 0 || status[2] != 0;
     rep->ok = bad ? 0 : 1;
 }
 
@@ -797,8 +834,9 @@ static gdc_status graph_step(gdc_ctx* c, gdc_step_info* info) {
                         inf.solve.matvecs_fp64;
     inf.pair_evals = (double)matvecs * c->pair_evals_per_matvec;
     // the host-driven path's checks, in its order
-    if ((r.status[0] != 0 || r.status[1] != 0) && clear_status(c) != GDC_OK) return GDC_ERR_CUDA;
+    if ((r.status[0] != 0 || r.status[1] != 0 || r.status[2] != 0) && clear_status(c) != GDC_OK) return GDC_ERR_CUDA;
     if (r.status[1] != 0) return fail(c, GDC_ERR_TIMEOUT, "a pair-kernel tile copy did not complete in time");
+    if (r.status[2] != 0) return fail(c, GDC_ERR_NONFINITE, "a blob centre reached the wall (height <= a)");
     if (r.lz_notconv[0] || r.lz_notconv[2]) return fail(c, GDC_ERR_NOT_CONVERGED, "Lanczos reached lanczos_max_iter");
     if (r.gm_bad) return fail(c, GDC_ERR_NONFINITE, "mobility solve: non-finite residual");
     if (r.gm_notconv) return fail(c, GDC_ERR_NOT_CONVERGED, "mobility solve: GMRES reached gmres_max_iter");
@@ -892,6 +930,10 @@ gdc_status gdc_init(gdc_ctx** out, const gdc_params* params, int n_templates, co
     if ((st = cuda_check(c, cudaGetLastError(), "template setup")) != GDC_OK) return st;
     if ((st = read_status(c)) != GDC_OK) return st;
     if ((st = sym_init_attributes(c)) != GDC_OK) return st;
+    if (c->p.wall) {   // every blob must start above z = a
+        load_at(c, c->Y, c->q);
+        if ((st = read_status(c)) != GDC_OK) return st;
+    }
     if (c->p.autotune && c->p.mobility == GDC_MOB_RPY) {   // the RPY pair kernels only
         load_at(c, c->Y, c->q);
         if ((st = autotune_pair_kernel(c)) != GDC_OK) return st;

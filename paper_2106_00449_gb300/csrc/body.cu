@@ -12,6 +12,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "wall_pair.cuh"
 
 namespace gdc {
 
@@ -123,23 +124,33 @@ void launch_lsq(gdc_ctx* c, const double* vbrev, double* calV) {
 //   a = M^-1 r_lam,  V = -N (r_V + K^T a),  lam = a + G V   (N = (K^T M^-1 K)^+, G = M^-1 K)
 // in the body frame of the template.
 
+// LAB = false: the template's FP64 blocks in the body frame, applied to rotated vectors.
+// LAB = true (blobs above a wall): each body's own blocks in the lab frame (set up by
+// k_wall_blocks at every configuration), blob offsets d_i = r_i - Y_p, no rotation.
+template <bool LAB>
 __global__ void __launch_bounds__(128) k_precond(const long long* __restrict__ body_blob_off, const int* __restrict__ body_tmpl,
                                                  const int* __restrict__ tmpl_n, const int* __restrict__ tmpl_off,
                                                  const long long* __restrict__ minv_off, const double* __restrict__ Minv,
                                                  const double* __restrict__ Gt, const double* __restrict__ Nt,
                                                  const double* __restrict__ tmpl_xyz, const int* __restrict__ blob_gm,
                                                  const int* __restrict__ body_gm, const double* __restrict__ Rb,
-                                                 const double* __restrict__ rin, double* __restrict__ zout) {
+                                                 const double* __restrict__ rin, double* __restrict__ zout,
+                                                 const long long* __restrict__ blk_off, const double* __restrict__ r,
+                                                 const double* __restrict__ Yc) {
     extern __shared__ double sh[];
     const int p = blockIdx.x;
-    const int t = body_tmpl[p];
-    const int n = tmpl_n[t];
+    const int t = LAB ? p : body_tmpl[p];
+    const int n = LAB ? (int)(body_blob_off[p + 1] - body_blob_off[p]) : tmpl_n[t];
     const int n3 = 3 * n;
     double* rho = sh;          // n3
     double* av = sh + n3;      // n3
     double* misc = sh + 2 * n3;  // 32
-    const double* R = Rb + 9 * p;
+    double* bl = misc + 32;      // LAB: blob offsets d (n3)
+    const double ident[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    const double* R = LAB ? ident : Rb + 9 * p;
     const long long i0 = body_blob_off[p];
+    if (LAB)
+        for (int e = threadIdx.x; e < n3; e += blockDim.x) bl[e] = r[3 * i0 + e] - Yc[3 * p + e % 3];
     for (int b = threadIdx.x; b < n; b += blockDim.x) {
         const long long o = blob_gm[i0 + b];
         double v[3] = {rin[o], rin[o + 1], rin[o + 2]}, w[3];
@@ -162,7 +173,7 @@ __global__ void __launch_bounds__(128) k_precond(const long long* __restrict__ b
         misc[5] = w[2];
     }
     __syncthreads();
-    const double* Mi = Minv + minv_off[t];
+    const double* Mi = Minv + (LAB ? blk_off[p] : minv_off[t]);
     for (int row = threadIdx.x; row < n3; row += blockDim.x) {
         double acc = 0.0;
         for (int k = 0; k < n3; ++k) acc = fma(Mi[(long long)k * n3 + row], rho[k], acc);  // symmetric
@@ -170,7 +181,7 @@ __global__ void __launch_bounds__(128) k_precond(const long long* __restrict__ b
     }
     __syncthreads();
     if (threadIdx.x < 32) {
-        const double* b = tmpl_xyz + 3LL * tmpl_off[t];
+        const double* b = LAB ? bl : tmpl_xyz + 3LL * tmpl_off[t];
         double g[6] = {0, 0, 0, 0, 0, 0};
         for (int i = threadIdx.x; i < n; i += 32) {
             const double a0 = av[3 * i], a1 = av[3 * i + 1], a2 = av[3 * i + 2];
@@ -194,7 +205,8 @@ __global__ void __launch_bounds__(128) k_precond(const long long* __restrict__ b
         }
     }
     __syncthreads();
-    const double* Gtt = Gt + 18LL * tmpl_off[t];  // G_t is 3n x 6, templates back to back
+    // G is 3n x 6, blocks back to back (templates, or LAB bodies in blob order)
+    const double* Gtt = Gt + 18LL * (LAB ? body_blob_off[p] : (long long)tmpl_off[t]);
     for (int b = threadIdx.x; b < n; b += blockDim.x) {
         double lb[3];
         for (int a = 0; a < 3; ++a) {
@@ -337,10 +349,15 @@ void launch_intra_body(gdc_ctx* c, const double* x, double* y, int gm) {
 }
 
 void launch_precond(gdc_ctx* c, const double* r, double* z) {
-    const size_t smem = (size_t)(2 * 3 * c->max_body_blobs + 32) * sizeof(double);
-    ++c->n_launch, k_precond<<<c->NB, 128, smem, c->stream>>>(c->body_blob_off, c->body_tmpl, c->tmpl_n, c->tmpl_off, c->minv_off,
-                                               c->tmpl_Minv, c->tmpl_G, c->tmpl_N, c->tmpl_xyz, c->blob_gm,
-                                               c->body_gm, c->Rb, r, z);
+    const size_t smem = (size_t)(3 * 3 * c->max_body_blobs + 32) * sizeof(double);
+    if (c->p.wall)
+        ++c->n_launch, k_precond<true><<<c->NB, 128, smem, c->stream>>>(
+            c->body_blob_off, c->body_tmpl, c->tmpl_n, c->tmpl_off, c->minv_off, c->blk_Minv, c->blk_G, c->blk_N,
+            c->tmpl_xyz, c->blob_gm, c->body_gm, c->Rb, r, z, c->blk_off, c->r, c->Yc);
+    else
+        ++c->n_launch, k_precond<false><<<c->NB, 128, smem, c->stream>>>(
+            c->body_blob_off, c->body_tmpl, c->tmpl_n, c->tmpl_off, c->minv_off, c->tmpl_Minv, c->tmpl_G, c->tmpl_N,
+            c->tmpl_xyz, c->blob_gm, c->body_gm, c->Rb, r, z, nullptr, nullptr, nullptr);
 }
 
 // ---- factors of the body blocks: block-preconditioned Lanczos (Sec. 4.1, Chow & Saad) ----
@@ -354,7 +371,9 @@ void launch_precond(gdc_ctx* c, const double* r, double* z) {
 // F is the template's factor stored so that out_i = sum_k F[k n3 + i] in_k (coalesced over
 // the rows i); the triangular structure limits k to [i, n3) (TRI_LINV_T) or [0, i].  FP64.
 // One block per body; x, add and out hold 3 doubles per blob.  Shared memory: 2 x 3n doubles.
-template <int MODE>
+// LAB (blobs above a wall): body p's own factor of its lab-frame block (L_p from
+// k_wall_blocks, at blk_off[p]), no rotation.
+template <int MODE, bool LAB>
 __global__ void __launch_bounds__(128) k_body_tri(const long long* __restrict__ body_blob_off,
                                                   const int* __restrict__ body_tmpl, const int* __restrict__ tmpl_n,
                                                   const long long* __restrict__ minv_off, const double* __restrict__ F,
@@ -362,11 +381,12 @@ __global__ void __launch_bounds__(128) k_body_tri(const long long* __restrict__ 
                                                   const double* __restrict__ add, double* __restrict__ out) {
     extern __shared__ double sh[];
     const int p = blockIdx.x;
-    const int t = body_tmpl[p];
-    const int n = tmpl_n[t], n3 = 3 * n;
+    const int t = LAB ? p : body_tmpl[p];
+    const int n = LAB ? (int)(body_blob_off[p + 1] - body_blob_off[p]) : tmpl_n[t], n3 = 3 * n;
     double* in = sh;
     double* res = sh + n3;
-    const double* R = Rb + 9 * p;
+    const double ident[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    const double* R = LAB ? ident : Rb + 9 * p;
     const long long i0 = body_blob_off[p];
     for (int b = threadIdx.x; b < n; b += blockDim.x) {
         double v[3] = {x[3 * (i0 + b)], x[3 * (i0 + b) + 1], x[3 * (i0 + b) + 2]};
@@ -418,15 +438,20 @@ __global__ void __launch_bounds__(128) k_body_tri(const long long* __restrict__ 
 
 void launch_body_tri(gdc_ctx* c, int mode, const double* x, const double* add, double* out) {
     const size_t smem = (size_t)(2 * 3 * c->max_body_blobs) * sizeof(double);
-    if (mode == TRI_LINV_T)
-        ++c->n_launch, k_body_tri<TRI_LINV_T><<<c->NB, 128, smem, c->stream>>>(
-            c->body_blob_off, c->body_tmpl, c->tmpl_n, c->minv_off, c->tmpl_X, c->Rb, x, add, out);
-    else if (mode == TRI_LINV)
-        ++c->n_launch, k_body_tri<TRI_LINV><<<c->NB, 128, smem, c->stream>>>(
-            c->body_blob_off, c->body_tmpl, c->tmpl_n, c->minv_off, c->tmpl_XT, c->Rb, x, add, out);
-    else
-        ++c->n_launch, k_body_tri<TRI_L><<<c->NB, 128, smem, c->stream>>>(
-            c->body_blob_off, c->body_tmpl, c->tmpl_n, c->minv_off, c->tmpl_LT, c->Rb, x, add, out);
+    const bool lab = c->p.wall != 0;
+    const long long* off = lab ? c->blk_off : c->minv_off;
+#define GDC_TRI(MODE, LAB, F)                                                                                    \
+    k_body_tri<MODE, LAB><<<c->NB, 128, smem, c->stream>>>(c->body_blob_off, c->body_tmpl, c->tmpl_n, off, F, c->Rb, \
+                                                          x, add, out)
+    ++c->n_launch;
+    if (mode == TRI_LINV_T) {
+        if (lab) GDC_TRI(TRI_LINV_T, true, c->blk_X); else GDC_TRI(TRI_LINV_T, false, c->tmpl_X);
+    } else if (mode == TRI_LINV) {
+        if (lab) GDC_TRI(TRI_LINV, true, c->blk_XT); else GDC_TRI(TRI_LINV, false, c->tmpl_XT);
+    } else {
+        if (lab) GDC_TRI(TRI_L, true, c->blk_LT); else GDC_TRI(TRI_L, false, c->tmpl_LT);
+    }
+#undef GDC_TRI
 }
 
 // ---- per-template setup (once, at init) -------------------------------------------------
@@ -632,6 +657,155 @@ void launch_template_setup(gdc_ctx* c, const double* Mext) {
     const long long nm = c->h_minv_off[c->T];
     ++c->n_launch, k_round_f32<<<(int)std::min<long long>(ceil_div(nm, 256), 1024), 256, 0, c->stream>>>(nm, c->tmpl_M,
                                                                                                       c->tmpl_M32);
+}
+
+// ---- per-body blocks above a wall (Sec. 4.1, Sec. 6.2) ---------------------------------
+//
+// A wall makes a body's block of M depend on its height and orientation, so the blocks of
+// the preconditioner (the exact per-body saddle solve) and the factors of the
+// preconditioned Lanczos operator are set up for every body at every configuration.  One
+// block per body: M_pp = unbounded RPY + wall correction (wall_pair.cuh) from the blob
+// offsets d_i = r_i - Y_p and the heights, in FP64; its Cholesky factor L, X = L^-1,
+// M_pp^-1 = X^T X, G = M_pp^-1 K_p (K_p from d), N = (K_p^T G)^+, and LT = L^T, X, XT = X^T
+// stored for k_body_tri<LAB>.  A blob at or below z = a (overlapping the wall, where the
+// correction is not a mobility) sets status[2]; a block that is not positive definite sets
+// status[0] = 1.  Shared memory: 3n doubles.
+__global__ void __launch_bounds__(256) k_wall_blocks(const long long* __restrict__ body_blob_off,
+                                                     const long long* __restrict__ blk_off, const double* __restrict__ r,
+                                                     const double* __restrict__ Yc, double a, double eta,
+                                                     double* __restrict__ work, double* __restrict__ Minv,
+                                                     double* __restrict__ Gb, double* __restrict__ Nb,
+                                                     double* __restrict__ LT, double* __restrict__ Xo,
+                                                     double* __restrict__ XT, int* __restrict__ status) {
+    extern __shared__ double dsh[];
+    const int p = blockIdx.x;
+    const long long i0 = body_blob_off[p];
+    const int n = (int)(body_blob_off[p + 1] - i0), n3 = 3 * n;
+    double* d = dsh;
+    const double zc = Yc[3 * p + 2];
+    for (int e = threadIdx.x; e < n3; e += blockDim.x) d[e] = r[3 * i0 + e] - Yc[3 * p + e % 3];
+    for (int b = threadIdx.x; b < n; b += blockDim.x)
+        if (!(r[3 * (i0 + b) + 2] > a)) atomicExch(status + 2, 1);
+    __syncthreads();
+    const long long mo = blk_off[p];
+    double* L = work + 2 * mo;
+    double* X = L + (long long)n3 * n3;
+    const double c0 = 1.0 / (8.0 * 3.141592653589793 * eta);
+    // 1. M_pp row-major in L: RPY entry (units of 1/(8 pi eta)) + wall correction of column be
+    for (long long e = threadIdx.x; e < (long long)n3 * n3; e += blockDim.x) {
+        const int row = (int)(e / n3), col = (int)(e % n3);
+        const int i = row / 3, al = row % 3, j = col / 3, be = col % 3;
+        const double dx = d[3 * j] - d[3 * i], dy = d[3 * j + 1] - d[3 * i + 1], dz = d[3 * j + 2] - d[3 * i + 2];
+        const double dd[3] = {dx, dy, dz};
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        double A, B;
+        if (r2 == 0.0) {
+            A = 4.0 / (3.0 * a);
+            B = 0.0;
+        } else if (r2 < 4.0 * a * a) {
+            const double rr = sqrt(r2);
+            A = 4.0 / (3.0 * a) * (1.0 - 9.0 * rr / (32.0 * a));
+            B = 1.0 / (8.0 * a * a * rr);
+        } else {
+            const double rr = sqrt(r2);
+            A = 1.0 / rr + 2.0 * a * a / (3.0 * rr * r2);
+            B = (1.0 - 2.0 * a * a / r2) / (rr * r2);
+        }
+        double w[3] = {0.0, 0.0, 0.0};
+        wall_pair<double>(d[3 * i] - d[3 * j], d[3 * i + 1] - d[3 * j + 1], d[3 * i + 2] + d[3 * j + 2] + 2.0 * zc,
+                          d[3 * j + 2] + zc, a * a, be == 0 ? 1.0 : 0.0, be == 1 ? 1.0 : 0.0, be == 2 ? 1.0 : 0.0,
+                          w[0], w[1], w[2]);
+        L[e] = c0 * ((al == be ? A : 0.0) + B * dd[al] * dd[be] + w[al]);
+    }
+    __syncthreads();
+    // 2. Cholesky M = L L^T (right-looking; lower triangle of L overwritten)
+    for (int k = 0; k < n3; ++k) {
+        if (threadIdx.x == 0) {
+            const double dkk = L[(long long)k * n3 + k];
+            if (!(dkk > 0.0)) atomicExch(status, 1);
+            L[(long long)k * n3 + k] = sqrt(fmax(dkk, 1e-300));
+        }
+        __syncthreads();
+        const double lkk = L[(long long)k * n3 + k];
+        for (int i = k + 1 + threadIdx.x; i < n3; i += blockDim.x) L[(long long)i * n3 + k] /= lkk;
+        __syncthreads();
+        const int m = n3 - k - 1;
+        for (long long e = threadIdx.x; e < (long long)m * m; e += blockDim.x) {
+            const int i = k + 1 + (int)(e / m), j = k + 1 + (int)(e % m);
+            if (j <= i) L[(long long)i * n3 + j] -= L[(long long)i * n3 + k] * L[(long long)j * n3 + k];
+        }
+        __syncthreads();
+    }
+    // 3. X = L^-1 (forward substitution per column), M^-1 = X^T X and the factor layouts
+    for (int col = threadIdx.x; col < n3; col += blockDim.x) {
+        for (int i = 0; i < n3; ++i) X[(long long)i * n3 + col] = 0.0;
+        for (int i = col; i < n3; ++i) {
+            double acc = (i == col) ? 1.0 : 0.0;
+            for (int k = col; k < i; ++k) acc -= L[(long long)i * n3 + k] * X[(long long)k * n3 + col];
+            X[(long long)i * n3 + col] = acc / L[(long long)i * n3 + i];
+        }
+    }
+    __syncthreads();
+    for (long long e = threadIdx.x; e < (long long)n3 * n3; e += blockDim.x) {
+        const int i = (int)(e / n3), j = (int)(e % n3);
+        double acc = 0.0;
+        for (int k = max(i, j); k < n3; ++k) acc += X[(long long)k * n3 + i] * X[(long long)k * n3 + j];
+        Minv[mo + e] = acc;
+        LT[mo + e] = j >= i ? L[(long long)j * n3 + i] : 0.0;
+        Xo[mo + e] = X[e];
+        XT[mo + e] = X[(long long)j * n3 + i];
+    }
+    __syncthreads();
+    // 4. G = M^-1 K (3n x 6), K columns: unit translations and e_c x d_i
+    double* G = Gb + 18LL * i0;
+    for (long long e = threadIdx.x; e < 6LL * n3; e += blockDim.x) {
+        const int row = (int)(e / 6), col = (int)(e % 6);
+        double acc = 0.0;
+        for (int i = 0; i < n; ++i) {
+            double kc[3];
+            if (col < 3) {
+                kc[0] = col == 0;
+                kc[1] = col == 1;
+                kc[2] = col == 2;
+            } else {
+                const int bb = col - 3;
+                const double e3[3] = {(double)(bb == 0), (double)(bb == 1), (double)(bb == 2)};
+                kc[0] = e3[1] * d[3 * i + 2] - e3[2] * d[3 * i + 1];
+                kc[1] = e3[2] * d[3 * i] - e3[0] * d[3 * i + 2];
+                kc[2] = e3[0] * d[3 * i + 1] - e3[1] * d[3 * i];
+            }
+            for (int al = 0; al < 3; ++al) acc += Minv[mo + (long long)row * n3 + 3 * i + al] * kc[al];
+        }
+        G[e] = acc;
+    }
+    __syncthreads();
+    // 5. N = (K^T G)^+ (symmetrised, pseudo-inverse for collinear bodies)
+    if (threadIdx.x == 0) {
+        double A6[36];
+        for (int k = 0; k < 36; ++k) A6[k] = 0.0;
+        for (int i = 0; i < n; ++i) {
+            const double bx = d[3 * i], by = d[3 * i + 1], bz = d[3 * i + 2];
+            double Kc[6][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {0, -bz, by}, {bz, 0, -bx}, {-by, bx, 0}};
+            for (int u = 0; u < 6; ++u)
+                for (int v = 0; v < 6; ++v) {
+                    double s1 = 0.0;
+                    for (int al = 0; al < 3; ++al) s1 += Kc[u][al] * G[6LL * (3 * i + al) + v];
+                    A6[6 * u + v] += s1;
+                }
+        }
+        for (int u = 0; u < 6; ++u)
+            for (int v = u + 1; v < 6; ++v) {
+                const double m = 0.5 * (A6[6 * u + v] + A6[6 * v + u]);
+                A6[6 * u + v] = A6[6 * v + u] = m;
+            }
+        pinv6(A6, Nb + 36LL * p, 1e-10);
+    }
+}
+
+void launch_wall_blocks(gdc_ctx* c) {
+    ++c->n_launch, k_wall_blocks<<<c->NB, 256, (size_t)3 * c->max_body_blobs * sizeof(double), c->stream>>>(
+        c->body_blob_off, c->blk_off, c->r, c->Yc, c->p.a, c->p.eta, c->blk_work, c->blk_Minv, c->blk_G, c->blk_N,
+        c->blk_LT, c->blk_X, c->blk_XT, c->dev_status);
 }
 
 }  // namespace gdc

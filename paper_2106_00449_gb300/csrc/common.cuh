@@ -177,6 +177,13 @@ struct gdc_ctx {
     int* lz_hint = 0;             // per suspension: index the previous unconstrained run stopped at (0 = none)
     double *lz_z = 0, *lz_u = 0;  // preconditioned operator: L^-T x and the product at it (3 per blob)
 
+    // blobs above a wall (gdc_params.wall): per-body blocks set up at every configuration
+    std::vector<long long> h_blk_off;          // offsets of the (3 n_p)^2 blocks, NB + 1
+    long long* blk_off = 0;
+    double *blk_work = 0, *blk_Minv = 0, *blk_G = 0, *blk_N = 0, *blk_LT = 0, *blk_X = 0, *blk_XT = 0;
+    std::vector<int2> h_wall_items;            // (suspension, first target) of the wall product
+    int2* wall_items = 0;
+
     // reductions
     gdc::Seg seg_gm, seg_lz, seg_body;
     double* red_part = 0;         // n_chunks x GDC_MAX_LANCZOS partial sums
@@ -368,6 +375,12 @@ void launch_template_setup(gdc_ctx* c, const double* Mext = nullptr);   // Mext:
 // Lanczos): mode 0 out = L_p^-T x, mode 1 out = L_p^-1 x (+ add), mode 2 out = L_p x
 enum { TRI_LINV_T = 0, TRI_LINV = 1, TRI_L = 2 };
 void launch_body_tri(gdc_ctx* c, int mode, const double* x, const double* add, double* out);
+void launch_wall_blocks(gdc_ctx* c);   // per-body blocks above a wall (at every configuration)
+
+// wall.cu (blobs above a no-slip wall)
+void build_wall_items(gdc_ctx* c);
+void launch_wall_apply(gdc_ctx* c, int prec, const double* x, double* y, int gm);   // y += W x
+void launch_wall_forces(gdc_ctx* c, double* fblob);                                 // fblob += wall + weight
 
 // krylov.cu
 gdc_status saddle_op(gdc_ctx* c, int prec, const double* x, double* y);

@@ -53,6 +53,7 @@ void load_config(gdc_ctx* c, const double* Y, const double* q) {
         c->NBL, c->blob_body, c->blob_susp, c->body_tmpl, c->body_blob_off, c->tmpl_off, c->tmpl_xyz,
         Y, c->Rb, c->ref, c->r, c->spos, c->spos64);
     launch_near_build(c);   // pairs closer than 2a, corrected after every FP32 product
+    if (c->p.wall) launch_wall_blocks(c);   // a wall: per-body blocks depend on the configuration
 }
 
 // stream 0: 3 draws per blob; stream 1: 6 draws per body.  Counter (k/2, s, step, stream).

@@ -242,6 +242,7 @@ gdc_status rpy_op(gdc_ctx* c, int prec, const double* lam, double* u) {
     launch_pack_lambda(c, prec, lam, 0);
     launch_rpy(c, prec);
     launch_rpy_epilogue(c, prec, lam, u, 0);
+    if (c->p.wall) launch_wall_apply(c, prec, lam, u, 0);   // + the wall correction of every pair
     return GDC_OK;
 }
 
@@ -256,6 +257,7 @@ gdc_status saddle_op(gdc_ctx* c, int prec, const double* x, double* y) {
     launch_pack_lambda(c, prec, x, 1);
     launch_rpy(c, prec);
     launch_rpy_epilogue(c, prec, x, y, 1);
+    if (c->p.wall) launch_wall_apply(c, prec, x, y, 1);
     launch_body_KT(c, x, 1, y, 1, -1.0);
     return GDC_OK;
 }
@@ -264,14 +266,15 @@ gdc_status saddle_op(gdc_ctx* c, int prec, const double* x, double* y) {
 // block-preconditioned A = L^-1 M L^-T of Chow & Saad, L = diag_p(L_p) with L_p L_p^T = M_pp.
 // Since L_p^-1 M_pp L_p^-T = I, an FP32 product takes A x = x + L^-1 M_off L^-T x with M_off
 // the blocks between different bodies (the FP32 product without its same-body blocks), so
-// the body blocks of A are the identity exactly; FP64 forms L^-1 (M (L^-T x)).
+// the body blocks of A are the identity exactly; FP64, and every product above a wall (whose
+// correction couples a body's blobs too), forms L^-1 (M (L^-T x)).
 static void lz_operator(gdc_ctx* c, int prec, const double* x, double* w) {
     if (!c->p.lanczos_precond) {
         rpy_op(c, prec, x, w);
         return;
     }
     launch_body_tri(c, TRI_LINV_T, x, nullptr, c->lz_z);
-    if (prec == GDC_FP32_MIXED) {
+    if (prec == GDC_FP32_MIXED && !c->p.wall) {
         launch_pack_lambda(c, prec, c->lz_z, 0);
         launch_rpy(c, prec);
         launch_rpy_epilogue(c, prec, c->lz_z, c->lz_u, 0, false);

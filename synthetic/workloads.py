@@ -25,6 +25,8 @@ Workloads (a = eta = kT = 1):
              42-blob icosphere}, 5% volume fraction each, seeds per suspension.
 ``c5``       16,384 rods of 20 blobs (327,680 blobs) at 8% in a 257.9a cube,
              linear shear rate 1, dt 0.002.
+``boomerang_wall``  15-blob boomerangs above a no-slip wall (the setting of Sec. 6.2),
+             independent suspensions, with the wall repulsion and the weight of Sec. 6.2.
 """
 from __future__ import annotations
 
@@ -241,6 +243,42 @@ def c5(seed: int = 0, n_rods: int = 16384) -> Workload:
                     params, np.array([box]))
 
 
+def boomerang_wall(n_susp: int = 36, bodies_per_susp: int = 1, seed: int = 0, spread: float = 12.0) -> Workload:
+    """Boomerangs of 15 blobs at spacing a (two 8-blob arms sharing the corner, Sec. 6.2)
+    above a no-slip wall at z = 0: n_susp independent suspensions (Sec. 6.2 runs 36) of
+    bodies_per_susp boomerangs each, uniform random orientations, centres uniform in a
+    spread x spread square at a height that keeps every blob at least 0.5a above z = a, no
+    two bodies closer than 2a.  Wall repulsion V0 = 23 kT, b = 0.5a, weight mg = 0.18 kT/a,
+    dt = 0.1 tau_D with tau_D = 6 pi eta a^3 / kT, GMRES and Lanczos tolerance 1e-4."""
+    tmpl = shapes.boomerang(8, 1.0)
+    cen = _centred(tmpl)
+    reach = float(np.linalg.norm(cen, axis=1).max())
+    rng = np.random.default_rng(seed)
+    Ys, qs = [], []
+    for s in range(n_susp):
+        placed_Y, placed_pts = [], []
+        for _ in range(bodies_per_susp):
+            for _try in range(10000):
+                y = np.array([*rng.uniform(0.0, spread, 2), 1.5 + reach + rng.uniform(0.0, 2.0)])
+                qq = random_unit_quaternions(rng, 1)[0]
+                pts = y[None, :] + Rotation.from_quat([qq[1], qq[2], qq[3], qq[0]]).apply(cen)
+                if all(np.min(np.linalg.norm(pts[:, None, :] - o[None, :, :], axis=-1)) >= 2.0 for o in placed_pts):
+                    break
+            else:
+                raise RuntimeError("could not place a boomerang")
+            placed_Y.append(y)
+            placed_pts.append(pts)
+            qs.append(qq)
+        Ys.extend(placed_Y)
+    n = n_susp * bodies_per_susp
+    tau_d = 6.0 * math.pi
+    params = dict(_BASE, dt=0.1 * tau_d, steps=100, seed=seed, gmres_tol=1e-4, lanczos_tol=1e-4, rfd_delta=1e-6,
+                  wall=1, wall_V0=23.0, wall_b=0.5, body_weight=0.18)
+    return Workload(f"boomerang_wall_{n_susp}x{bodies_per_susp}", [tmpl], np.zeros(n, dtype=np.int32),
+                    (np.arange(n_susp + 1) * bodies_per_susp).astype(np.int64), np.array(Ys), np.array(qs), params,
+                    np.full(n_susp, spread))
+
+
 def mixed_small(n_bodies: int, seed: int = 0, phi: float = 0.10) -> Workload:
     """Small version of the c3 mix (same shapes and volume fraction) for parity tests."""
     return _mixed(n_bodies, seed, phi=phi, name=f"mixed{n_bodies}")
@@ -251,6 +289,6 @@ def batch_small(n_susp: int = 6, seed: int = 0, nmin: int = 2, nmax: int = 9) ->
     return c4(seed=seed, n_susp=n_susp, nmin=nmin, nmax=nmax)
 
 
-BY_NAME = {"c1": c1, "c2": c2, "c3": c3, "c3_65k": c3_65k, "c4": c4, "c5": c5,
+BY_NAME = {"c1": c1, "c2": c2, "c3": c3, "c3_65k": c3_65k, "c4": c4, "c5": c5, "boomerang_wall": boomerang_wall,
            # half of c5's rods (163,840 blobs): a Lanczos basis of ~30 vectors already exceeds L2
            "c5_half": lambda seed=0: c5(seed=seed, n_rods=8192)}

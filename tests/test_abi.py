@@ -80,6 +80,15 @@ def test_workspace_checks_the_mobility_and_force_options_without_gpu(libpath):
     assert ws(g.Params(potential=1, well_A=5.0, well_lambda=0.0)) == 0
     assert ws(g.Params(force_method=3)) == 0
     assert ws(g.Params(well_A=-1.0)) == 0
+    # blobs above a wall: per-body blocks enlarge the workspace; RPY only, no shear
+    wall = dict(wall=1, wall_V0=23.0, wall_b=0.5, body_weight=0.18)
+    assert ws(g.Params(**wall)) > ws(g.Params())
+    assert ws(g.Params(**dict(wall, wall_b=0.0))) == 0
+    assert ws(g.Params(**dict(wall, wall_V0=-1.0))) == 0
+    assert ws(g.Params(**dict(wall, shear_rate=1.0))) == 0
+    assert ws(g.Params(**dict(wall, **fcm))) == 0
+    assert ws(g.Params(wall_V0=23.0)) == 0                        # wall forces without the wall
+    assert ws(g.Params(lanczos_precond=2)) == 0
 
 
 def test_fcm_workspace_checks_the_grid_without_gpu(libpath):
