@@ -292,6 +292,30 @@ def c4_batching(g, torch, WL, common, n_susp: int) -> dict:
             "batched_speedup": batched / single["steps_per_s"], "note": single["note"]}
 
 
+def boomerang_wall_leg(g, torch, WL, n_susp: int, steps: int = 20) -> dict:
+    """Sec. 6.2's setting: n_susp independent suspensions of one 15-blob boomerang above a
+    no-slip wall (wall repulsion 23 kT, b = 0.5a, weight 0.18 kT/a, dt = 0.1 tau_D, GMRES and
+    Lanczos tolerance 1e-4), advanced together in one batched context, FP64 (as the paper's
+    runs) and FP32-mixed; steps/s of the whole batch by CUDA events after 3 warm-up steps."""
+    wl = WL.boomerang_wall(n_susp, 1, seed=0)
+    out = {"workload": f"{n_susp} suspensions of one 15-blob boomerang above a wall ({wl.n_blobs} blobs)",
+           "steps": steps}
+    for name, prec, delta in (("fp64", g.FP64, 1e-6), ("fp32_mixed", g.FP32_MIXED, 1e-3)):
+        ctx = g.context_from_workload(wl, precision=prec, rfd_delta=delta, seed=11)
+        ctx.step(3)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        inf = ctx.step(steps)
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        out[name] = {"steps_per_s": steps / (e0.elapsed_time(e1) / 1000.0),
+                     "lanczos_iters": inf[-1]["lanczos_iters"], "gmres_iters": inf[-1]["solve"]["iterations"],
+                     "residual_max": max(i["solve"]["residual"] for i in inf)}
+        del ctx
+    return out
+
+
 def per_suspension_steps(g, torch, wl, common, rank):
     """The suspensions of a batch advanced one context per suspension, one after another.
 
@@ -452,6 +476,8 @@ def main(argv=None) -> int:
     ap.add_argument("--cpu-products", type=int, default=3, help="full-size twin products timed for cpu_baseline")
     ap.add_argument("--c4-suspensions", type=int, default=64,
                     help="suspensions of the c4 batching leg of the default run (0 = skip)")
+    ap.add_argument("--wall-suspensions", type=int, default=36,
+                    help="boomerang-above-a-wall suspensions of the default run's wall leg (0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="c3_65k",
                     help="c3_65k (default), c4 or c5 for the step benchmark; any synthetic workload for --op")
@@ -594,6 +620,8 @@ def main(argv=None) -> int:
             value / world / line["one_suspension_per_launch"]["steps_per_s"])
     elif rank == 0 and world == 1 and args.c4_suspensions > 0:
         line["c4_batching"] = c4_batching(g, torch, WL, common, args.c4_suspensions)
+    if args.workload == "c3_65k" and rank == 0 and world == 1 and args.wall_suspensions > 0:
+        line["boomerang_wall"] = boomerang_wall_leg(g, torch, WL, args.wall_suspensions)
     if args.workload != "c3_65k":
         if rank == 0:
             print(json.dumps(line), flush=True)

@@ -116,8 +116,17 @@ static void fcm_layout(gdc_fcm* f, const gdc_fcm_params& p) {
 // bit-reversed and strided accesses over the banks), rows an odd number of float2 apart.
 __host__ __device__ inline int fft_row(int N) { return N + N / 16 + 1; }
 __device__ __forceinline__ int fft_pad(int i) { return i + (i >> 4); }
-static int fft_lp(int N) { return N >= 512 ? 3 : 4; }
-static size_t fft_smem(int N) { return (size_t)(((size_t)1 << fft_lp(N)) * fft_row(N) + N / 2) * sizeof(float2); }
+// Pencils per block: 16 (16 consecutive x: 128-byte runs in the strided y and z passes),
+// except for 512-point pencils of the contiguous x pass, 8 to a block.
+#ifndef GDC_FFT512_LP_YZ
+#define GDC_FFT512_LP_YZ 3
+#endif
+#ifndef GDC_FFT512_TH_YZ
+#define GDC_FFT512_TH_YZ 256
+#endif
+static int fft_lp(int N, int axis) { return N >= 512 ? (axis == 0 ? 3 : GDC_FFT512_LP_YZ) : 4; }
+static size_t fft_smem_lp(int N, int lp) { return (size_t)(((size_t)1 << lp) * fft_row(N) + N / 2) * sizeof(float2); }
+static size_t fft_smem(int N) { return std::max(fft_smem_lp(N, fft_lp(N, 0)), fft_smem_lp(N, fft_lp(N, 1))); }
 
 // ---- binning ------------------------------------------------------------------------
 
@@ -275,8 +284,8 @@ __global__ void k_fcm_pack(long long NG, const float2* __restrict__ u, float4* _
 
 // INV = 0: X_k = sum_n x_n exp(-2 pi i k n / N); INV = 1: the same with +i, unscaled.
 // blockIdx.y picks the component grid (NG points apart).
-template <int INV, int LP>
-__global__ void __launch_bounds__(256) k_fft(float2* __restrict__ data, long long NG, const float2* __restrict__ tw_g,
+template <int INV, int LP, int TH>
+__global__ void __launch_bounds__(TH) k_fft(float2* __restrict__ data, long long NG, const float2* __restrict__ tw_g,
                                              int N, int logN, int axis) {
     constexpr int P = 1 << LP;
     extern __shared__ float2 sm[];
@@ -545,24 +554,29 @@ static gdc_status fcm_check(gdc_fcm* f, cudaError_t e, const char* what) {
 }
 
 static void fft3(gdc_fcm* f, int slot, int ncomp, bool inverse) {
-    // 512-point pencils go 8 to a block, so that a block's shared memory (37 KB) leaves room
-    // for as many resident blocks as the 16 pencils of shorter transforms
-    const int lp = fft_lp(f->N);
-    const dim3 grid((unsigned)(f->N * f->N >> lp), (unsigned)ncomp);
-    const size_t smem = fft_smem(f->N);
+    // 512-point pencils go 8 to a block in the contiguous x pass, so that a block's shared
+    // memory (37 KB) leaves room for as many resident blocks as the 16 pencils of shorter
+    // transforms
     float2* d = f->grid + slot * f->NG;
     for (int axis = 0; axis < 3; ++axis) {
-        if (lp == 3) {
-            if (inverse)
-                ++f->n_launch, k_fft<1, 3><<<grid, 256, smem, f->stream>>>(d, f->NG, f->tw, f->N, f->logN, axis);
-            else
-                ++f->n_launch, k_fft<0, 3><<<grid, 256, smem, f->stream>>>(d, f->NG, f->tw, f->N, f->logN, axis);
-        } else {
-            if (inverse)
-                ++f->n_launch, k_fft<1, 4><<<grid, 256, smem, f->stream>>>(d, f->NG, f->tw, f->N, f->logN, axis);
-            else
-                ++f->n_launch, k_fft<0, 4><<<grid, 256, smem, f->stream>>>(d, f->NG, f->tw, f->N, f->logN, axis);
-        }
+        const int lp = fft_lp(f->N, axis);
+        const dim3 grid((unsigned)(f->N * f->N >> lp), (unsigned)ncomp);
+        const size_t smem = fft_smem_lp(f->N, lp);
+#define GDC_FFT(LP_, TH_)                                                                              \
+    do {                                                                                               \
+        if (inverse)                                                                                   \
+            k_fft<1, LP_, TH_><<<grid, TH_, smem, f->stream>>>(d, f->NG, f->tw, f->N, f->logN, axis);  \
+        else                                                                                           \
+            k_fft<0, LP_, TH_><<<grid, TH_, smem, f->stream>>>(d, f->NG, f->tw, f->N, f->logN, axis);  \
+    } while (0)
+        ++f->n_launch;
+        if (lp == 3)
+            GDC_FFT(3, 256);
+        else if (f->N >= 512)
+            GDC_FFT(4, GDC_FFT512_TH_YZ);
+        else
+            GDC_FFT(4, 256);
+#undef GDC_FFT
     }
 }
 
@@ -630,10 +644,16 @@ gdc_status gdc_fcm_init(gdc_fcm** out, const gdc_fcm_params* params, void* works
     }
     cudaError_t e = cudaMemcpyAsync(f->tw, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice, f->stream);
     const int fsm = (int)std::max(fft_smem(256), fft_smem(512));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft<0, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft<1, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft<0, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft<1, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft<0, 3, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft<1, 3, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft<0, 4, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft<1, 4, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm);
+    if (GDC_FFT512_TH_YZ != 256) {
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_fft<0, 4, GDC_FFT512_TH_YZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_fft<1, 4, GDC_FFT512_TH_YZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(f->stream);
     if (e != cudaSuccess) {
         delete f;
