@@ -22,7 +22,9 @@ prints its mean time per call (CUDA events on the library's stream): rpy32 / rpy
 pair forces), lanczos32 (one v-breve), solve32 (one FP32-mixed mobility solve), step32 (one
 gDC step, --graph 0|1), fcm_apply / fcm_brownian / fcm_average (fluctuating FCM of the
 workload's blobs in a periodic cube of its box side, --fcm-n grid points per side).  This is
-the command the ncu captures under profiles/ run.
+the command the ncu captures under profiles/ run: its kernels_before_timed_calls counts the
+library's kernels (all named k_*) launched before the timed calls, so `ncu -k regex:^k_ -s`
+that count starts at the first timed call.
 
 Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank advances its own
 independent suspension of the same size (replicas, weak scaling, no collective on the
@@ -421,7 +423,7 @@ def run_op(args) -> int:
         stream, extra = ctx.stream, {"grid": args.fcm_n, "L": L}
     else:
         ctx = g.context_from_workload(wl, precision=g.FP32_MIXED, rfd_delta=1e-3, lanczos_max_iter=128,
-                                      pair_kernel=args.pair_kernel, graph=args.graph,
+                                      pair_kernel=args.pair_kernel, df_kernel=args.df_kernel, graph=args.graph,
                                       force_method=args.force_method, potential=args.potential,
                                       well_A=5.0 if args.potential else 0.0, well_lambda=0.5)
         rng = np.random.default_rng(0)
@@ -443,8 +445,8 @@ def run_op(args) -> int:
         raise SystemExit(f"unknown --op {args.op}; one of {sorted(ops)}")
     fn = ops[args.op]
 
-    def launched():   # the library's own kernels launched so far (all named k_*)
-        return F.launches if args.op.startswith("fcm_") else ctx.profile_read()["launches"]
+    def launched():   # the library's own kernels launched so far (all named k_*), context and grid
+        return ctx.profile_read()["launches"] + (F.launches if args.op.startswith("fcm_") else 0)
 
     fn()
     torch.cuda.synchronize()
@@ -459,7 +461,8 @@ def run_op(args) -> int:
            "reps": args.reps, "kernels_before_timed_calls": before,
            "kernels_per_call": (launched() - before) / args.reps, **extra}
     if "pair_kernel" in extra:
-        out["pair_kernel"] = ctx.profile_read()["pair_kernel"]
+        prof = ctx.profile_read()
+        out["pair_kernel"], out["df_kernel"] = prof["pair_kernel"], prof["df_kernel"]
         out["pairs"] = wl.pair_evals_per_matvec()
     print(json.dumps(out), flush=True)
     return 0
@@ -487,6 +490,8 @@ def main(argv=None) -> int:
     ap.add_argument("--bodies", type=int, default=0, help="--op: only the first N bodies of the workload (0 = all)")
     ap.add_argument("--reps", type=int, default=5, help="--op: timed calls")
     ap.add_argument("--pair-kernel", type=int, default=0, help="--op: 0 autotuned, 1 ordered, 2 symmetric")
+    ap.add_argument("--df-kernel", type=int, default=0,
+                    help="--op: double-float kernel, 0 autotuned, 1 ordered, 3/4 symmetric at 3/4 blocks per SM")
     ap.add_argument("--graph", type=int, default=1, help="--op step32: 1 graph replay, 0 host-driven")
     ap.add_argument("--force-method", type=int, default=0, help="--op: 0 choose, 1 all pairs, 2 cell list")
     ap.add_argument("--potential", type=int, default=0, help="--op: 0 soft sphere, 1 and 2 the Sec. 6.4 wells")
@@ -584,6 +589,7 @@ def main(argv=None) -> int:
                        "work_waves": None if kind == 2 else prof["work_waves"],
                        "source_tiles_per_item": prof.get("sym_width") if kind == 2 else None,
                        "min_blocks_per_sm": prof.get("min_blocks_per_sm"),
+                       "df_kernel": prof.get("df_kernel"),
                        "autotuned": prof["autotune_ms"] > 0},
             "flops_per_pair": FLOPS_PER_PAIR, "pairs_per_launch": prof["pairs_per_product"],
             "flop_count": ("33 flops per ordered pair (i, j), N_b^2 per launch, whichever kernel runs; the "

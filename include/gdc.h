@@ -115,7 +115,9 @@ typedef struct {
     unsigned long long seed; /* Philox4x32-10 key of the W and W-tilde draws            */
     int    autotune;       /* 1: gdc_init times the FP32 pair kernels' candidates at the
                               initial configuration and keeps the fastest: kernel, work-
-                              item shape and the resident blocks per SM it is compiled for */
+                              item shape and the resident blocks per SM it is compiled for;
+                              then the double-float residual kernels (ordered, symmetric
+                              at 3 or 4 blocks per SM) the same way                      */
     int    graph;          /* 1: gdc_step captures one step as a CUDA graph at its first
                               call and replays it; the Lanczos and GMRES loops are
                               conditional WHILE nodes whose conditions the loop kernels
@@ -126,7 +128,9 @@ typedef struct {
     int    pair_kernel;    /* FP32 RPY pair kernel, fixed at init: 1 ordered (every ordered
                               pair, target-side sums), 2 symmetric (every unordered pair
                               once, both sides), 0 the faster of the two as timed by the
-                              autotuner (symmetric when autotune = 0)                    */
+                              autotuner (symmetric when autotune = 0).  The double-float
+                              residual kernel is ordered for 1, symmetric for 2, and for
+                              0 the autotuner's pick (symmetric when autotune = 0)        */
     int    potential;      /* gdc_potential                                            */
     double well_A;         /* well amplitude A_w, energy units (Sec. 6.4: 5 kT); 0 = no wells */
     double well_lambda;    /* well width lambda, a length (Sec. 6.4: 0.5 a)            */
@@ -160,6 +164,10 @@ typedef struct {
     double wall_b;         /* its range, a length (Sec. 6.2: 0.5 a)                    */
     double body_weight;    /* with wall: a force body_weight along -z on every body, shared
                               equally by its blobs (Sec. 6.2: mg = 0.18 kT/a)            */
+    int    df_kernel;      /* double-float residual kernel, fixed at init: 0 as pair_kernel
+                              says, 1 ordered, 3 or 4 symmetric compiled for that many
+                              resident blocks per SM; all give the same product up to
+                              summation order                                           */
 } gdc_params;
 
 typedef struct {
@@ -386,6 +394,9 @@ typedef struct {
     double unique_pairs_per_product;    /* unordered pairs incl. self, sum n (n + 1) / 2  */
     int    min_blocks_per_sm;           /* resident blocks per SM the FP32 pair kernel in use
                                            was compiled for (chosen by the autotuner)     */
+    int    df_kernel;                   /* double-float residual kernel in use: 0 ordered,
+                                           else the resident blocks per SM (3 or 4) of the
+                                           symmetric one (chosen by the autotuner)        */
 } gdc_profile_info;
 
 /* Reset the counters; enable != 0 also brackets every pair-kernel launch with

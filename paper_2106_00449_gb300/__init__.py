@@ -65,7 +65,8 @@ class _Params(ctypes.Structure):
                 ("well_lambda", ctypes.c_double), ("force_method", ctypes.c_int), ("mobility", ctypes.c_int),
                 ("box_L", ctypes.c_double), ("fcm_N", ctypes.c_int), ("fcm_sigma", ctypes.c_double),
                 ("fcm_R_t", ctypes.c_double), ("lanczos_precond", ctypes.c_int), ("wall", ctypes.c_int),
-                ("wall_V0", ctypes.c_double), ("wall_b", ctypes.c_double), ("body_weight", ctypes.c_double)]
+                ("wall_V0", ctypes.c_double), ("wall_b", ctypes.c_double), ("body_weight", ctypes.c_double),
+                ("df_kernel", ctypes.c_int)]
 
 
 class _FcmParams(ctypes.Structure):
@@ -92,7 +93,8 @@ class _Profile(ctypes.Structure):
                 ("work_waves", ctypes.c_double), ("autotune_ms", ctypes.c_double),
                 ("rpydf_launches", ctypes.c_ulonglong), ("rpydf_ms", ctypes.c_double),
                 ("pair_kernel", ctypes.c_int), ("sym_width", ctypes.c_int),
-                ("unique_pairs_per_product", ctypes.c_double), ("min_blocks_per_sm", ctypes.c_int)]
+                ("unique_pairs_per_product", ctypes.c_double), ("min_blocks_per_sm", ctypes.c_int),
+                ("df_kernel", ctypes.c_int)]
 
 
 class _Trace(ctypes.Structure):
@@ -135,6 +137,7 @@ class Params:
     wall_V0: float = 0.0     # wall repulsion strength (Sec. 6.2: 23 kT)
     wall_b: float = 0.5      # its range (Sec. 6.2: 0.5 a)
     body_weight: float = 0.0  # mg per body along -z (Sec. 6.2: 0.18 kT/a)
+    df_kernel: int = 0       # double-float residual kernel: 0 as pair_kernel, 1 ordered, 3/4 symmetric
 
     def _c(self) -> _Params:
         return _Params(**{f.name: getattr(self, f.name) for f in dataclasses.fields(self)})

@@ -73,6 +73,8 @@ static const char* validate_params(const gdc_params* p) {
     if (!(p->lanczos_tol > 0.0) || !(p->lanczos_tol < 1.0)) return "lanczos_tol must be in (0, 1)";
     if (p->lanczos_max_iter < 2 || p->lanczos_max_iter > GDC_MAX_LANCZOS) return "lanczos_max_iter must be in [2, 128]";
     if (p->lanczos_precond != 0 && p->lanczos_precond != 1) return "lanczos_precond must be 0 or 1";
+    if (p->df_kernel != 0 && p->df_kernel != 1 && p->df_kernel != 3 && p->df_kernel != 4)
+        return "df_kernel must be 0 (as pair_kernel), 1 (ordered), 3 or 4 (symmetric, blocks per SM)";
     if (!(p->rfd_delta > 0.0) || !(p->rfd_delta < 1.0)) return "rfd_delta must be in (0, 1)";
     if (p->precision != GDC_FP64 && p->precision != GDC_FP32_MIXED) return "unknown precision";
     if (p->divmode != GDC_DIV_RFD && p->divmode != GDC_DIV_FD) return "unknown divmode";
@@ -225,6 +227,8 @@ static size_t carve(gdc_ctx* c, void* base) {
     c->tmpl_LT = w.take<double>(c->h_minv_off[T]);
     c->tmpl_X = w.take<double>(c->h_minv_off[T]);
     c->tmpl_XT = w.take<double>(c->h_minv_off[T]);
+    c->tmpl_X32 = w.take<float>(c->h_minv_off[T]);
+    c->tmpl_XT32 = w.take<float>(c->h_minv_off[T]);
     c->body_L = w.take<double>(NB);
     c->Rb = w.take<double>(9 * NB);
     c->r = w.take<double>(3 * NBL);
@@ -319,6 +323,10 @@ static size_t carve(gdc_ctx* c, void* base) {
     c->sym_jbase = w.take<long long>(S + 1);
     c->sym_part_i = w.take<float4>((long long)c->sym_cap_kmax * NBL);
     c->sym_part_j = w.take<float4>(std::max<long long>(1, c->sym_n_jslots) * GDC_SYM_TILE);
+    c->dfs_items = w.take<SymItem>(c->dfs_n_items);
+    c->dfs_row_nk = w.take<int>(std::max<long long>(1, c->sym_n_tiles));
+    c->dfs_part_i = w.take<double4_32a>((long long)c->dfs_kmax * NBL);
+    c->dfs_part_j = w.take<double4_32a>(std::max<long long>(1, c->sym_n_jslots) * GDC_SYM_TILE);
     c->h_near_items.clear();
     for (int s = 0; s < c->S; ++s) {
         const long long ns = c->h_blob_off[s + 1] - c->h_blob_off[s];
@@ -394,6 +402,8 @@ static gdc_status upload_layout(gdc_ctx* c, const double* tmpl_xyz_centred) {
     chk(up(c, c->mv_items, c->h_mv_items.data(), c->h_mv_items.size()));
     chk(up(c, c->near_items, c->h_near_items.data(), c->h_near_items.size()));
     chk(up(c, c->mv_nk, c->h_mv_nk.data(), S));
+    chk(up(c, c->dfs_items, c->h_dfs_items.data(), c->h_dfs_items.size()));
+    chk(up(c, c->dfs_row_nk, c->h_dfs_row_nk.data(), c->h_dfs_row_nk.size()));
     if (c->p.wall) {
         chk(up(c, c->blk_off, c->h_blk_off.data(), NB + 1));
         chk(up(c, c->wall_items, c->h_wall_items.data(), c->h_wall_items.size()));
@@ -930,6 +940,7 @@ gdc_status gdc_init(gdc_ctx** out, const gdc_params* params, int n_templates, co
     if ((st = cuda_check(c, cudaGetLastError(), "template setup")) != GDC_OK) return st;
     if ((st = read_status(c)) != GDC_OK) return st;
     if ((st = sym_init_attributes(c)) != GDC_OK) return st;
+    if ((st = dfsym_init_attributes(c)) != GDC_OK) return st;
     if (c->p.wall) {   // every blob must start above z = a
         load_at(c, c->Y, c->q);
         if ((st = read_status(c)) != GDC_OK) return st;
@@ -994,6 +1005,7 @@ gdc_status gdc_profile_read(gdc_ctx* c, gdc_profile_info* out) {
     out->pair_kernel = c->use_sym ? 2 : 1;
     out->sym_width = c->sym_width;
     out->min_blocks_per_sm = c->use_sym ? c->sym_minb : c->mv_minb;
+    out->df_kernel = c->dfs_minb;
     double up = 0.0;
     for (int s = 0; s < c->S; ++s) {
         const double n = (double)(c->h_blob_off[s + 1] - c->h_blob_off[s]);
@@ -1016,10 +1028,11 @@ gdc_status gdc_set_params(gdc_ctx* c, const gdc_params* p) {
         p->fcm_sigma != c->p.fcm_sigma || p->fcm_R_t != c->p.fcm_R_t)
         return fail(c, GDC_ERR_INVALID_ARG, "the mobility and its FCM grid are fixed at init");
     const unsigned long long seed = c->p.seed;
-    const int pair_kernel = c->p.pair_kernel;
+    const int pair_kernel = c->p.pair_kernel, df_kernel = c->p.df_kernel;
     c->p = *p;
     c->p.seed = seed;
-    c->p.pair_kernel = pair_kernel;   // the pair kernel is chosen at init
+    c->p.pair_kernel = pair_kernel;   // the pair kernels are chosen at init
+    c->p.df_kernel = df_kernel;
     drop_graph(c);   // parameters are baked into the captured launches
     c->fcm_field_step = ~0ULL;   // an FCM field drawn with the old kT and dt is not reused
     return GDC_OK;

@@ -372,19 +372,21 @@ void launch_precond(gdc_ctx* c, const double* r, double* z) {
 // the rows i); the triangular structure limits k to [i, n3) (TRI_LINV_T) or [0, i].  FP64.
 // One block per body; x, add and out hold 3 doubles per blob.  Shared memory: 2 x 3n doubles.
 // LAB (blobs above a wall): body p's own factor of its lab-frame block (L_p from
-// k_wall_blocks, at blk_off[p]), no rotation.
-template <int MODE, bool LAB>
+// k_wall_blocks, at blk_off[p]), no rotation.  T: the type of the factor and of the sums
+// (float for the FP32 products of the FP32-mixed Lanczos, whose other terms carry FP32
+// rounding; the rotations and the added vector stay FP64).
+template <int MODE, bool LAB, typename T>
 __global__ void __launch_bounds__(128) k_body_tri(const long long* __restrict__ body_blob_off,
                                                   const int* __restrict__ body_tmpl, const int* __restrict__ tmpl_n,
-                                                  const long long* __restrict__ minv_off, const double* __restrict__ F,
+                                                  const long long* __restrict__ minv_off, const T* __restrict__ F,
                                                   const double* __restrict__ Rb, const double* __restrict__ x,
                                                   const double* __restrict__ add, double* __restrict__ out) {
     extern __shared__ double sh[];
     const int p = blockIdx.x;
     const int t = LAB ? p : body_tmpl[p];
     const int n = LAB ? (int)(body_blob_off[p + 1] - body_blob_off[p]) : tmpl_n[t], n3 = 3 * n;
-    double* in = sh;
-    double* res = sh + n3;
+    double* res = sh;
+    T* in = reinterpret_cast<T*>(sh + n3);
     const double ident[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
     const double* R = LAB ? ident : Rb + 9 * p;
     const long long i0 = body_blob_off[p];
@@ -397,22 +399,22 @@ __global__ void __launch_bounds__(128) k_body_tri(const long long* __restrict__ 
             v[1] = w[1];
             v[2] = w[2];
         }
-        in[3 * b] = v[0];
-        in[3 * b + 1] = v[1];
-        in[3 * b + 2] = v[2];
+        in[3 * b] = (T)v[0];
+        in[3 * b + 1] = (T)v[1];
+        in[3 * b + 2] = (T)v[2];
     }
     __syncthreads();
-    const double* Ft = F + minv_off[t];
+    const T* Ft = F + minv_off[t];
     for (int i = threadIdx.x; i < n3; i += blockDim.x) {
         const int k0 = MODE == TRI_LINV_T ? i : 0, k1 = MODE == TRI_LINV_T ? n3 : i + 1;
-        double a0 = 0.0, a1 = 0.0;
+        T a0 = T(0), a1 = T(0);
         int k = k0;
         for (; k + 1 < k1; k += 2) {
             a0 = fma(Ft[(long long)k * n3 + i], in[k], a0);
             a1 = fma(Ft[(long long)(k + 1) * n3 + i], in[k + 1], a1);
         }
         if (k < k1) a0 = fma(Ft[(long long)k * n3 + i], in[k], a0);
-        res[i] = a0 + a1;
+        res[i] = (double)a0 + (double)a1;
     }
     __syncthreads();
     for (int b = threadIdx.x; b < n; b += blockDim.x) {
@@ -436,20 +438,24 @@ __global__ void __launch_bounds__(128) k_body_tri(const long long* __restrict__ 
     }
 }
 
-void launch_body_tri(gdc_ctx* c, int mode, const double* x, const double* add, double* out) {
+void launch_body_tri(gdc_ctx* c, int mode, const double* x, const double* add, double* out, bool fp32) {
     const size_t smem = (size_t)(2 * 3 * c->max_body_blobs) * sizeof(double);
     const bool lab = c->p.wall != 0;
     const long long* off = lab ? c->blk_off : c->minv_off;
-#define GDC_TRI(MODE, LAB, F)                                                                                    \
-    k_body_tri<MODE, LAB><<<c->NB, 128, smem, c->stream>>>(c->body_blob_off, c->body_tmpl, c->tmpl_n, off, F, c->Rb, \
-                                                          x, add, out)
+#define GDC_TRI(MODE, LAB, T, F)                                                                                  \
+    k_body_tri<MODE, LAB, T><<<c->NB, 128, smem, c->stream>>>(c->body_blob_off, c->body_tmpl, c->tmpl_n, off, F, \
+                                                             c->Rb, x, add, out)
     ++c->n_launch;
-    if (mode == TRI_LINV_T) {
-        if (lab) GDC_TRI(TRI_LINV_T, true, c->blk_X); else GDC_TRI(TRI_LINV_T, false, c->tmpl_X);
+    if (fp32 && !lab && mode == TRI_LINV_T)
+        GDC_TRI(TRI_LINV_T, false, float, c->tmpl_X32);
+    else if (fp32 && !lab && mode == TRI_LINV)
+        GDC_TRI(TRI_LINV, false, float, c->tmpl_XT32);
+    else if (mode == TRI_LINV_T) {
+        if (lab) GDC_TRI(TRI_LINV_T, true, double, c->blk_X); else GDC_TRI(TRI_LINV_T, false, double, c->tmpl_X);
     } else if (mode == TRI_LINV) {
-        if (lab) GDC_TRI(TRI_LINV, true, c->blk_XT); else GDC_TRI(TRI_LINV, false, c->tmpl_XT);
+        if (lab) GDC_TRI(TRI_LINV, true, double, c->blk_XT); else GDC_TRI(TRI_LINV, false, double, c->tmpl_XT);
     } else {
-        if (lab) GDC_TRI(TRI_L, true, c->blk_LT); else GDC_TRI(TRI_L, false, c->tmpl_LT);
+        if (lab) GDC_TRI(TRI_L, true, double, c->blk_LT); else GDC_TRI(TRI_L, false, double, c->tmpl_LT);
     }
 #undef GDC_TRI
 }
@@ -655,8 +661,10 @@ void launch_template_setup(gdc_ctx* c, const double* Mext) {
                                                   c->tmpl_Minv, c->tmpl_G, c->tmpl_N, c->tmpl_KtKp, c->tmpl_work,
                                                   c->tmpl_M, Mext, c->dev_status, c->tmpl_LT, c->tmpl_X, c->tmpl_XT);
     const long long nm = c->h_minv_off[c->T];
-    ++c->n_launch, k_round_f32<<<(int)std::min<long long>(ceil_div(nm, 256), 1024), 256, 0, c->stream>>>(nm, c->tmpl_M,
-                                                                                                      c->tmpl_M32);
+    const int gr = (int)std::min<long long>(ceil_div(nm, 256), 1024);
+    ++c->n_launch, k_round_f32<<<gr, 256, 0, c->stream>>>(nm, c->tmpl_M, c->tmpl_M32);
+    ++c->n_launch, k_round_f32<<<gr, 256, 0, c->stream>>>(nm, c->tmpl_X, c->tmpl_X32);
+    ++c->n_launch, k_round_f32<<<gr, 256, 0, c->stream>>>(nm, c->tmpl_XT, c->tmpl_XT32);
 }
 
 // ---- per-body blocks above a wall (Sec. 4.1, Sec. 6.2) ---------------------------------

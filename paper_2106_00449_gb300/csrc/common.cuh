@@ -32,6 +32,7 @@
 #define GDC_NEAR_CAP 32          // blobs closer than 2a listed per blob (beyond: a search of the suspension)
 #define GDC_NEAR_SRC 2048        // sources per block of the near-pair search
 #define GDC_SYM_TILE 512         // blobs per tile of the symmetric FP32 pair kernel
+#define GDC_DFS_WIDTH 8          // source tiles per item of the symmetric double-float kernel
 #define GDC_CELL_MIN_BLOBS 16384 // GDC_FORCES_CHOOSE: the cell list from this many blobs on
 #define GDC_WAIT_POLLS 400000    // default bound of a pair kernel's wait for a tile copy (polls)
 
@@ -131,6 +132,7 @@ struct gdc_ctx {
     // operator, each stored as F with (F-product)_i = sum_k F[k n3 + i] x_k (reads along rows):
     // tmpl_LT = L_t^T (products with L_t), tmpl_X = L_t^-1 (with L_t^-T), tmpl_XT = L_t^-T (with L_t^-1)
     double *tmpl_LT = 0, *tmpl_X = 0, *tmpl_XT = 0;
+    float *tmpl_X32 = 0, *tmpl_XT32 = 0;   // L_t^-1 and L_t^-T rounded to FP32 (FP32-mixed Lanczos operator)
     // fluctuating FCM mobility (fcm.cu), GDC_MOB_FCM only
     gdc_fcm* fcm = nullptr;
     double* fcm_u = nullptr;      // M_FCM lambda, 3 per blob
@@ -213,6 +215,14 @@ struct gdc_ctx {
     float4 *sym_part_i = 0, *sym_part_j = 0;  // target-side [slot][blob], source-side [slot][GDC_SYM_TILE]
     std::vector<gdc::SymItem> h_sym_items;
     std::vector<int> h_sym_row_nk;
+    // symmetric double-float residual kernel (dfsym.cu): its own work list (wider items), FP64 slots
+    gdc::SymItem* dfs_items = 0;
+    int dfs_n_items = 0, dfs_kmax = 1;
+    int dfs_minb = 4;   // 0: the ordered double-float kernel; 3 or 4: symmetric, blocks per SM
+    int* dfs_row_nk = 0;
+    std::vector<gdc::SymItem> h_dfs_items;
+    std::vector<int> h_dfs_row_nk;
+    double4_32a *dfs_part_i = 0, *dfs_part_j = 0;
     std::vector<long long> h_sym_tile_base, h_sym_jbase;
 
     // pairs closer than 2a (self pair excluded) of the loaded configuration, for the FP32
@@ -355,6 +365,11 @@ __global__ void k_cell_sort(int H, const int* __restrict__ cnt, const int* __res
 void launch_near_build(gdc_ctx* c);
 // sym.cu
 void build_sym_items(gdc_ctx* c, int width);
+void build_sym_list(const gdc_ctx* c, int width, std::vector<SymItem>& items, std::vector<int>& row_nk, int& kmax);
+// dfsym.cu
+gdc_status dfsym_init_attributes(gdc_ctx* c);
+void launch_rpy_df_sym_pairs(gdc_ctx* c);
+void launch_rpy_df_sym_epilogue(gdc_ctx* c, const double* x, double* y, int gm_layout);
 gdc_status sym_upload(gdc_ctx* c);
 gdc_status sym_init_attributes(gdc_ctx* c);
 void launch_rpy32_sym(gdc_ctx* c);
@@ -374,7 +389,7 @@ void launch_template_setup(gdc_ctx* c, const double* Mext = nullptr);   // Mext:
 // per-body products with the template-block factors L_p = R-hat_p L_t (block-preconditioned
 // Lanczos): mode 0 out = L_p^-T x, mode 1 out = L_p^-1 x (+ add), mode 2 out = L_p x
 enum { TRI_LINV_T = 0, TRI_LINV = 1, TRI_L = 2 };
-void launch_body_tri(gdc_ctx* c, int mode, const double* x, const double* add, double* out);
+void launch_body_tri(gdc_ctx* c, int mode, const double* x, const double* add, double* out, bool fp32 = false);
 void launch_wall_blocks(gdc_ctx* c);   // per-body blocks above a wall (at every configuration)
 
 // wall.cu (blobs above a no-slip wall)

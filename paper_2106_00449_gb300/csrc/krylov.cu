@@ -273,13 +273,15 @@ static void lz_operator(gdc_ctx* c, int prec, const double* x, double* w) {
         rpy_op(c, prec, x, w);
         return;
     }
-    launch_body_tri(c, TRI_LINV_T, x, nullptr, c->lz_z);
     if (prec == GDC_FP32_MIXED && !c->p.wall) {
+        // the factor products in FP32 too: the coupling term they feed carries FP32 rounding
+        launch_body_tri(c, TRI_LINV_T, x, nullptr, c->lz_z, true);
         launch_pack_lambda(c, prec, c->lz_z, 0);
         launch_rpy(c, prec);
         launch_rpy_epilogue(c, prec, c->lz_z, c->lz_u, 0, false);
-        launch_body_tri(c, TRI_LINV, c->lz_u, x, w);
+        launch_body_tri(c, TRI_LINV, c->lz_u, x, w, true);
     } else {
+        launch_body_tri(c, TRI_LINV_T, x, nullptr, c->lz_z);
         rpy_op(c, prec, c->lz_z, c->lz_u);
         launch_body_tri(c, TRI_LINV, c->lz_u, nullptr, w);
     }
@@ -527,9 +529,22 @@ static_assert(GDC_MAX_LANCZOS <= 128, "a lane owns at most 4 rows of Q");
 // Row stride of Q in shared memory: odd, so that the lanes' rows fall in distinct banks.
 __host__ __device__ inline int lz_ldq(int kmax) { return kmax | 1; }
 
-// Dynamic shared memory of k_lz_tridiag: four c vectors, then Q (all FP64).
+// The FP64 root at the stopping index is refined from the FP32 eigendecomposition up to
+// this many Lanczos vectors (its scratch grows as k^2), formed by FP64 QR beyond.
+#define GDC_LZ_REFINE_MAX 64
+
+// Doubles of scratch the refined root needs for k vectors: Q in FP32, Z and W in FP64, two
+// vectors (see lz_sqrt_e1_refined).
+__host__ __device__ inline int lz_refine_doubles(int k) {
+    const int ldk = k | 1;
+    return (k * ldk + 1) / 2 + 2 * k * ldk + 2 * k;
+}
+
+// Dynamic shared memory of k_lz_tridiag: four c vectors, then Q (FP64) or the scratch of the
+// refined root, whichever is larger.
 static size_t lz_tridiag_smem(int kmax) {
-    return (size_t)4 * kmax * sizeof(double) + (size_t)kmax * lz_ldq(kmax) * sizeof(double);
+    const int q = kmax * lz_ldq(kmax), r = lz_refine_doubles(std::min(kmax, GDC_LZ_REFINE_MAX));
+    return (size_t)4 * kmax * sizeof(double) + (size_t)std::max(q, r) * sizeof(double);
 }
 
 // Givens rotation (c, s) with c x + s z = r, -s x + c z = 0.  FP32 (the stopping test at
@@ -653,6 +668,74 @@ __device__ inline bool lz_sqrt_e1(const double* al, const double* be, int k, dou
                 : lz_sqrt_e1_t<double>(al, be, k, wn, Q, ldq, out);
 }
 
+// out = wn T^(1/2) e_1 in FP64 from the FP32 eigendecomposition T ~ Q diag(theta) Q^T, refined
+// once (k <= GDC_LZ_REFINE_MAX): Z = Q (3I - Q^T Q)/2 is orthogonal to O(|Q^T Q - I|^2), and
+// in B = Z^T T Z = D + E (D its diagonal, E of the size of the FP32 rounding) the root
+// X = D^(1/2) + Y with Y_ij = E_ij / (sqrt(d_i) + sqrt(d_j)) satisfies X^2 = B + O(|E|^2),
+// so T^(1/2) e_1 = Z X Z^T e_1 to about 1e-12 relative.  The denominators are sums of square
+// roots, never small differences, so close eigenvalues are no difficulty.  All sums in FP64,
+// spread over the warp.  buf holds lz_refine_doubles(k) doubles.
+__device__ bool lz_sqrt_e1_refined(const double* al, const double* be, int k, double wn, double* buf, double* out) {
+    const int lane = threadIdx.x, ldk = k | 1;
+    float* Qf = reinterpret_cast<float*>(buf);
+    double* Z = buf + (k * ldk + 1) / 2;
+    double* Wm = Z + k * ldk;
+    double* sv = Wm + k * ldk;   // sqrt(d_j)
+    double* hv = sv + k;         // X Z^T e_1
+    if (!lz_sqrt_e1_t<float>(al, be, k, wn, Qf, ldk, out)) return false;
+    // G = Q^T Q into Wm
+    for (int e = lane; e < k * k; e += 32) {
+        const int i = e / k, j = e % k;
+        double acc = 0.0;
+        for (int r = 0; r < k; ++r) acc = fma((double)Qf[r * ldk + i], (double)Qf[r * ldk + j], acc);
+        Wm[i * ldk + j] = acc;
+    }
+    __syncwarp();
+    // Z = Q (3I - G) / 2
+    for (int e = lane; e < k * k; e += 32) {
+        const int r = e / k, j = e % k;
+        double acc = 0.0;
+        for (int i = 0; i < k; ++i) acc = fma((double)Qf[r * ldk + i], Wm[i * ldk + j], acc);
+        Z[r * ldk + j] = 1.5 * (double)Qf[r * ldk + j] - 0.5 * acc;
+    }
+    __syncwarp();
+    // Wm = T Z (T tridiagonal: alpha on the diagonal, beta_r between r and r + 1)
+    for (int e = lane; e < k * k; e += 32) {
+        const int r = e / k, j = e % k;
+        double acc = al[r] * Z[r * ldk + j];
+        if (r > 0) acc = fma(be[r - 1], Z[(r - 1) * ldk + j], acc);
+        if (r + 1 < k) acc = fma(be[r], Z[(r + 1) * ldk + j], acc);
+        Wm[r * ldk + j] = acc;
+    }
+    __syncwarp();
+    for (int i = lane; i < k; i += 32) {   // d_i = B_ii = z_i . (T z_i)
+        double acc = 0.0;
+        for (int r = 0; r < k; ++r) acc = fma(Z[r * ldk + i], Wm[r * ldk + i], acc);
+        sv[i] = sqrt(fmax(acc, 0.0));
+    }
+    __syncwarp();
+    for (int i = lane; i < k; i += 32) {   // h_i = sqrt(d_i) g_i + sum_j E_ij g_j / (sqrt(d_i) + sqrt(d_j))
+        double h = sv[i] * Z[i];            // g_j = Z[0][j]
+        for (int j = 0; j < k; ++j) {
+            if (j == i) continue;
+            const double den = sv[i] + sv[j];
+            if (!(den > 0.0)) continue;
+            double eij = 0.0;
+            for (int r = 0; r < k; ++r) eij = fma(Z[r * ldk + i], Wm[r * ldk + j], eij);
+            h = fma(eij * Z[j], 1.0 / den, h);
+        }
+        hv[i] = h;
+    }
+    __syncwarp();
+    for (int r = lane; r < k; r += 32) {
+        double acc = 0.0;
+        for (int i = 0; i < k; ++i) acc = fma(Z[r * ldk + i], hv[i], acc);
+        out[r] = wn * acc;
+    }
+    __syncwarp();
+    return true;
+}
+
 // ||c_k - [c_{k-1}; 0]|| / ||c_k||, summed in the same order on every lane
 __device__ inline double lz_change(const double* ck, const double* cprev, int k) {
     double num = 0.0, den = 0.0;
@@ -773,7 +856,9 @@ __global__ void __launch_bounds__(32) k_lz_tridiag(int S, int j, const int* __re
     if (k >= kmax) stop = true;
     if (stop && check32) {   // the result at the stopping index, in FP64
         __syncwarp();
-        if (!lz_sqrt_e1(al, be, kstar, wn, Q, ldq, cur, false)) {
+        const bool ok = kstar <= GDC_LZ_REFINE_MAX ? lz_sqrt_e1_refined(al, be, kstar, wn, Q, cur)
+                                                   : lz_sqrt_e1(al, be, kstar, wn, Q, ldq, cur, false);
+        if (!ok) {
             if (lead) {
                 atomicExch(status, 2);
                 active[s] = 0;

@@ -13,6 +13,7 @@
 
 #include "common.cuh"
 #include "pair_common.cuh"
+#include "df.cuh"
 #include "forces.cuh"
 
 namespace gdc {
@@ -196,50 +197,6 @@ __global__ void __launch_bounds__(128, MINB) k_rpy32(const MvItem* __restrict__ 
 // transformations are Knuth's two-sum, Dekker's fast two-sum and the FMA-based exact
 // product.  Same-body pairs are skipped (added exactly in FP64 by k_intra_body).
 
-struct df { float h, l; };
-
-// The _rn intrinsics are never fused into FMAs by the compiler, which the error-free
-// transformations rely on.
-__device__ __forceinline__ df df_two_sum(float a, float b) {
-    const float s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
-}
-__device__ __forceinline__ df df_fast(float a, float b) {   // |a| >= |b|
-    const float s = __fadd_rn(a, b);
-    return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-__device__ __forceinline__ df df_add(df x, df y) {
-    df s = df_two_sum(x.h, y.h);
-    return df_fast(s.h, __fadd_rn(s.l, __fadd_rn(x.l, y.l)));
-}
-__device__ __forceinline__ df df_sub(df x, df y) { return df_add(x, df{-y.h, -y.l}); }
-__device__ __forceinline__ df df_mul(df x, df y) {
-    const float p = __fmul_rn(x.h, y.h);
-    float e = fmaf(x.h, y.h, -p);                 // exact rounding error of the product
-    e = fmaf(x.h, y.l, fmaf(x.l, y.h, e));
-    return df_fast(p, e);
-}
-__device__ __forceinline__ df df_from(double v) {
-    const float h = (float)v;
-    return {h, (float)(v - (double)h)};
-}
-__device__ __forceinline__ double df_to(df x) { return (double)x.h + (double)x.l; }
-
-// 1/sqrt(x) to double-float accuracy: one Newton step from the FP32 estimate,
-// y1 = y (1 - (x y^2 - 1)/2), with the residual x y^2 - 1 formed from exact products.
-__device__ __forceinline__ df df_rsqrt(df x) {
-    const float y = rsqrtf(x.h);
-    const float yy = __fmul_rn(y, y), yye = fmaf(y, y, -yy);
-    const float h = __fadd_rn(fmaf(x.h, yy, -1.f), fmaf(x.h, yye, __fmul_rn(x.l, yy)));
-    return df_fast(y, __fmul_rn(__fmul_rn(-0.5f, y), h));
-}
-
-struct RpyConstDF {
-    df c23, c2, cA, c9, cB;
-    df four_a2;   // 4a^2
-};
-
 template <int TPT>
 __global__ void __launch_bounds__(128) k_rpy_df(const MvItem* __restrict__ items, const long long* __restrict__ susp_blob_off,
                                                 const double4_32a* __restrict__ spos, const double4_32a* __restrict__ slam,
@@ -311,24 +268,6 @@ __global__ void __launch_bounds__(128) k_rpy_df(const MvItem* __restrict__ items
         if (ti < ns) part[(long long)it.k * NBL + b0 + ti] = make_double4_32a(df_to(ux[t]), df_to(uy[t]), df_to(uz[t]), 0.0);
     }
 }
-
-static df df_from_host(double v) {
-    const float h = (float)v;
-    return {h, (float)(v - (double)h)};
-}
-
-static RpyConstDF df_constants(double a) {
-    RpyConstDF k;
-    k.c23 = df_from_host(2.0 * a * a / 3.0);
-    k.c2 = df_from_host(2.0 * a * a);
-    k.cA = df_from_host(4.0 / (3.0 * a));
-    k.c9 = df_from_host(9.0 / (32.0 * a));
-    k.cB = df_from_host(1.0 / (8.0 * a * a));
-    k.four_a2 = df_from_host(4.0 * a * a);
-    return k;
-}
-
-// ---- FP64 RPY pair kernel -----------------------------------------------------
 
 template <int TPT>
 __global__ void __launch_bounds__(128) k_rpy64(const MvItem* __restrict__ items, const int* __restrict__ active,
@@ -430,6 +369,8 @@ void launch_rpy(gdc_ctx* c, int prec) {
             }
         }
 #undef GDC_RPY32_LAUNCH
+    } else if (prec == GDC_PREC_DF64 && c->dfs_minb) {
+        launch_rpy_df_sym_pairs(c);   // its epilogue runs in launch_rpy_epilogue
     } else if (prec == GDC_PREC_DF64) {
         const RpyConstDF k = df_constants(c->p.a);
         if (c->mv_tpt == 4)
@@ -663,7 +604,10 @@ static void launch_epilogue(gdc_ctx* c, int prec, double c0, const double* x, do
 }
 
 void launch_rpy_epilogue(gdc_ctx* c, int prec, const double* x, double* y, int gm_layout, bool same_body) {
-    launch_epilogue(c, prec, 1.0 / (8.0 * 3.141592653589793 * c->p.eta), x, y, gm_layout, prec == GDC_FP32_MIXED);
+    if (prec == GDC_PREC_DF64 && c->dfs_minb)
+        launch_rpy_df_sym_epilogue(c, x, y, gm_layout);
+    else
+        launch_epilogue(c, prec, 1.0 / (8.0 * 3.141592653589793 * c->p.eta), x, y, gm_layout, prec == GDC_FP32_MIXED);
     // same-body blocks from the template: the df64 pair kernel leaves those pairs out and the
     // FP32 epilogue has taken the FP32 pair kernel's same-body terms out again (so without
     // them an FP32 product is exactly the blocks between different bodies)
@@ -931,6 +875,7 @@ static const double kWaves[3] = {4.0, 8.0, 16.0};
 static const int kSymWidth[3] = {2, 4, 8};   // source tiles per item of the symmetric kernel
 static const int kSymMinBlocks[3] = {2, 3, 4};   // resident blocks per SM of the symmetric kernel
 static const int kMvMinBlocks[2] = {4, 6};       // resident blocks per SM of the ordered kernel
+static const int kDfsMinBlocks[3] = {0, 3, 4};   // double-float kernel: ordered, symmetric at 3 or 4 per SM
 
 void plan_mv_capacity(gdc_ctx* c) {
     int cap_items = 0, cap_k = 1;
@@ -954,6 +899,10 @@ void plan_mv_capacity(gdc_ctx* c) {
     c->sym_n_tiles = c->h_sym_tile_base.back();
     c->sym_n_jslots = c->h_sym_jbase.back();
     build_sym_items(c, 4);
+    // the symmetric double-float kernel: items of up to 8 source tiles (its per-pair work is
+    // ~8x the FP32 kernel's, so fewer, longer items balance as well)
+    build_sym_list(c, GDC_DFS_WIDTH, c->h_dfs_items, c->h_dfs_row_nk, c->dfs_kmax);
+    c->dfs_n_items = (int)c->h_dfs_items.size();
 }
 
 static gdc_status upload_items(gdc_ctx* c) {
@@ -966,7 +915,8 @@ static gdc_status upload_items(gdc_ctx* c) {
 }
 
 // Times three launches of the FP32 RPY kernel per candidate at the loaded configuration
-// (lambda = the current W buffer) and keeps the fastest tiling.
+// (lambda = the current W buffer) and keeps the fastest tiling; then one launch of each
+// double-float residual kernel.
 gdc_status autotune_pair_kernel(gdc_ctx* c) {
     cudaEvent_t e0, e1;
     gdc_status st = cuda_check(c, cudaEventCreate(&e0), "event");
@@ -1028,23 +978,52 @@ gdc_status autotune_pair_kernel(gdc_ctx* c) {
             if (st != GDC_OK) break;
         }
     }
+    if (st == GDC_OK) {
+        build_mv_items(c, bt, bw);
+        build_sym_items(c, bwid);
+        c->use_sym = bsym;
+        c->sym_minb = bminb;
+        c->mv_minb = bmv_minb;
+        c->autotune_ms = best / 3.0;
+        st = upload_items(c);
+        if (st == GDC_OK) st = sym_upload(c);
+    }
+    // the double-float residual kernel, one timed launch each after a warm-up (about 40 ms
+    // per product at 65k blobs): ordered unless the FP32 kernel is pinned to symmetric
+    c->dfs_minb = only == 1 ? 0 : 4;
+    if (c->p.df_kernel) {
+        c->dfs_minb = c->p.df_kernel == 1 ? 0 : c->p.df_kernel;
+    } else if (only != 1 && st == GDC_OK) {
+        launch_pack_lambda(c, GDC_PREC_DF64, c->W, 0);
+        float dbest = 1e30f;
+        int bdf = 4;
+        for (int mb : kDfsMinBlocks) {
+            if (mb == 0 && only == 2) continue;
+            c->dfs_minb = mb;
+            float ms = 0.f;
+            launch_rpy(c, GDC_PREC_DF64);   // warm-up
+            cudaEventRecord(e0, c->stream);
+            launch_rpy(c, GDC_PREC_DF64);
+            cudaEventRecord(e1, c->stream);
+            if ((st = cuda_check(c, cudaEventSynchronize(e1), "autotune")) != GDC_OK) break;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < dbest) {
+                dbest = ms;
+                bdf = mb;
+            }
+        }
+        c->dfs_minb = bdf;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (st != GDC_OK) return st;
-    build_mv_items(c, bt, bw);
-    build_sym_items(c, bwid);
-    c->use_sym = bsym;
-    c->sym_minb = bminb;
-    c->mv_minb = bmv_minb;
-    c->autotune_ms = best / 3.0;
-    if ((st = upload_items(c)) != GDC_OK) return st;
-    return sym_upload(c);
+    return st;
 }
 
 // Without the autotuner: the kernel params.pair_kernel names (symmetric for 0 and 2) with
-// the default work lists.
+// the default work lists, and the double-float kernel of the same kind.
 gdc_status default_pair_kernel(gdc_ctx* c) {
     c->use_sym = c->p.pair_kernel != 1;
+    c->dfs_minb = c->p.df_kernel ? (c->p.df_kernel == 1 ? 0 : c->p.df_kernel) : (c->use_sym ? 4 : 0);
     gdc_status st = upload_items(c);
     return st != GDC_OK ? st : sym_upload(c);
 }

@@ -223,18 +223,13 @@ __global__ void __launch_bounds__(128, MINB) k_rpy32_sym(const SymItem* __restri
 // into items of at most `width` tiles (the first of a row holds the diagonal).  Fills the
 // per-tile item counts (i-side slots), the per-suspension first j-side slot, and orders
 // the items largest first.
-void build_sym_items(gdc_ctx* c, int width) {
-    c->sym_width = width;
-    c->h_sym_items.clear();
-    c->h_sym_row_nk.clear();
-    c->h_sym_tile_base.assign(c->S + 1, 0);
-    c->h_sym_jbase.assign(c->S + 1, 0);
-    int kmax = 1;
+void build_sym_list(const gdc_ctx* c, int width, std::vector<SymItem>& items, std::vector<int>& row_nk, int& kmax) {
+    items.clear();
+    row_nk.clear();
+    kmax = 1;
     for (int s = 0; s < c->S; ++s) {
         const long long n = c->h_blob_off[s + 1] - c->h_blob_off[s];
         const int T = (int)((n + SYM_TILE - 1) / SYM_TILE);
-        c->h_sym_tile_base[s + 1] = c->h_sym_tile_base[s] + T;
-        c->h_sym_jbase[s + 1] = c->h_sym_jbase[s] + (long long)T * (T - 1) / 2;
         for (int I = 0; I < T; ++I) {
             int kk = 0;
             for (int J0 = I; J0 < T; J0 += width, ++kk) {
@@ -244,16 +239,28 @@ void build_sym_items(gdc_ctx* c, int width) {
                 it.J0 = J0;
                 it.J1 = std::min(T, J0 + width);
                 it.k = kk;
-                c->h_sym_items.push_back(it);
+                items.push_back(it);
             }
-            c->h_sym_row_nk.push_back(kk);
+            row_nk.push_back(kk);
             kmax = std::max(kmax, kk);
         }
     }
-    std::stable_sort(c->h_sym_items.begin(), c->h_sym_items.end(),
+    std::stable_sort(items.begin(), items.end(),
                      [](const SymItem& x, const SymItem& y) { return x.J1 - x.J0 > y.J1 - y.J0; });
+}
+
+void build_sym_items(gdc_ctx* c, int width) {
+    c->sym_width = width;
+    build_sym_list(c, width, c->h_sym_items, c->h_sym_row_nk, c->sym_kmax);
+    c->h_sym_tile_base.assign(c->S + 1, 0);
+    c->h_sym_jbase.assign(c->S + 1, 0);
+    for (int s = 0; s < c->S; ++s) {
+        const long long n = c->h_blob_off[s + 1] - c->h_blob_off[s];
+        const int T = (int)((n + SYM_TILE - 1) / SYM_TILE);
+        c->h_sym_tile_base[s + 1] = c->h_sym_tile_base[s] + T;
+        c->h_sym_jbase[s + 1] = c->h_sym_jbase[s] + (long long)T * (T - 1) / 2;
+    }
     c->sym_n_items = (int)c->h_sym_items.size();
-    c->sym_kmax = kmax;
 }
 
 gdc_status sym_upload(gdc_ctx* c) {

@@ -89,6 +89,10 @@ def test_workspace_checks_the_mobility_and_force_options_without_gpu(libpath):
     assert ws(g.Params(**dict(wall, **fcm))) == 0
     assert ws(g.Params(wall_V0=23.0)) == 0                        # wall forces without the wall
     assert ws(g.Params(lanczos_precond=2)) == 0
+    # the double-float residual kernel: ordered (1) or symmetric at 3 or 4 blocks per SM
+    for k in (0, 1, 3, 4):
+        assert ws(g.Params(df_kernel=k)) > 0
+    assert ws(g.Params(df_kernel=2)) == 0
 
 
 def test_fcm_workspace_checks_the_grid_without_gpu(libpath):

@@ -100,3 +100,25 @@ def test_gdc_step_at_bench_config(lib, which):
         assert pos_err < 1e-5 and rot_err(q1[o:e], ora["q1"]) < 1e-5
         assert rel(Y1[o:e] - Y, ora["Y1"] - Y) < 1e-3
     assert info["lanczos_iters"] == [k_ora[0], k_ora[0], k_ora[1]]
+
+
+@pytest.mark.parametrize("which", ["mix40", "mix60"])
+def test_fp64_root_at_the_bench_tolerance(lib, which):
+    """At lanczos_tol >= 1e-5 the stopping test runs on FP32 eigen-steps and the square root at
+    the stopping index is formed in FP64 by refining the FP32 eigendecomposition once; in FP64
+    products v-breve then equals the oracle's Lanczos iterate at the same tolerance to FP64
+    accuracy (the refinement leaves about 1e-12)."""
+    wl = _workload(which)
+    ctx = lib.context_from_workload(wl, precision=0, lanczos_tol=LZ_TOL, lanczos_max_iter=128, lanczos_precond=1)
+    W = np.random.default_rng(37).standard_normal(3 * wl.n_blobs)
+    vb, iters, err = ctx.brownian_slip(W)
+    vb = _host(vb)
+    lay, Y, q = susp_layout(wl, 0)
+    r, M, K, B = dense_state(lay, Y, q)
+    L = rigid.block_factor(lay, q, 1.0, 1.0)
+    Linv = np.linalg.inv(L)
+    A = Linv @ M @ Linv.T
+    y, k, _ = lanczos.lanczos_sqrt(0.5 * (A + A.T), W, LZ_TOL)
+    ref = np.sqrt(2 * wl.params["kT"] / wl.params["dt"]) * (L @ y)
+    assert iters == k
+    assert rel(vb, ref) < 1e-10, rel(vb, ref)

@@ -45,6 +45,19 @@ def test_fcm_product_matches_oracle(lib, N, L, R_t, n):
     np.testing.assert_array_equal(_host(F.apply(r, lam)), u)
 
 
+def test_fcm_product_matches_oracle_at_512(lib):
+    """The 512-point transforms (8 pencils per block in the contiguous pass, the benchmark's
+    grid) against the oracle on a 512^3 grid (about 30 s of numpy FFTs on the host)."""
+    N, L, R_t, n = 512, 150.0, 3.0, 60
+    rng = np.random.default_rng(512)
+    r = rng.uniform(0.0, L, size=(n, 3))
+    lam = rng.standard_normal((n, 3))
+    F = lib.Fcm(N, L, SIGMA, R_t, max_blobs=n)
+    u = _host(F.apply(r, lam))
+    ref = fcm.mobility_apply(fcm.Grid(N, L, SIGMA, R_t), r, lam)
+    assert rel(u, ref) < TOL, rel(u, ref)
+
+
 @pytest.mark.parametrize("N,L,R_t,n", CASES[:3])
 def test_fcm_brownian_matches_oracle(lib, N, L, R_t, n):
     g = fcm.Grid(N, L, SIGMA, R_t)

@@ -402,6 +402,9 @@ def test_rpy32_ordered_and_symmetric_kernels(lib, kernel, which):
     n = int(ctx.saddle_off[-1])
     x = rng.standard_normal(n)
     y = _host(ctx.saddle_apply(x, 1))
+    # the double-float residual product of the same kernel family (ordered or symmetric)
+    udf = _host(ctx.rpy_apply(lam, 2))
+    ydf = _host(ctx.saddle_apply(x, 2))
     sl = blob_slices(wl)
     for s in range(wl.n_susp):
         lay, Y, q = susp_layout(wl, s)
@@ -410,10 +413,47 @@ def test_rpy32_ordered_and_symmetric_kernels(lib, kernel, which):
         ref = M @ lam[3 * a:3 * b]
         assert rel(u[3 * a:3 * b], ref) < 2e-6, (s, rel(u[3 * a:3 * b], ref))
         assert np.abs(u[3 * a:3 * b] - ref).max() < 1e-5 * np.abs(ref).max()
+        assert rel(udf[3 * a:3 * b], ref) < 1e-11, (s, rel(udf[3 * a:3 * b], ref))
         o = int(ctx.saddle_off[s])
         lam_s, V_s = x[o:o + 3 * lay.n_blobs], x[o + 3 * lay.n_blobs:o + 3 * lay.n_blobs + 6 * lay.n_bodies]
         y1, y2 = rigid.saddle_apply(M, K, lam_s, V_s)
         assert rel(y[o:o + 3 * lay.n_blobs + 6 * lay.n_bodies], np.concatenate([y1, y2])) < 2e-6
+        assert rel(ydf[o:o + 3 * lay.n_blobs + 6 * lay.n_bodies], np.concatenate([y1, y2])) < 1e-11
+
+
+@pytest.mark.parametrize("which", ["mix120", "batch_multi_tile", "overlap_pile"])
+def test_double_float_kernels(lib, which):
+    """The double-float residual product by each of its kernels (ordered; symmetric compiled
+    for 3 and for 4 blocks per SM) against the dense oracle; the two symmetric builds run the
+    same arithmetic in the same order, so they agree bit for bit."""
+    if which == "mix120":
+        wl = WL.mixed_small(120, seed=4)
+    elif which == "batch_multi_tile":
+        wl = WL.c4(seed=6, n_susp=5, nmin=20, nmax=70)
+    else:
+        wl = _overlapping_workload("pile")
+    rng = np.random.default_rng(23)
+    lam = rng.standard_normal(3 * wl.n_blobs)
+    out = {}
+    for dk in (1, 3, 4):
+        ctx = ctx_for(lib, wl, autotune=0, pair_kernel=2, df_kernel=dk)
+        assert ctx.profile_read()["df_kernel"] == (0 if dk == 1 else dk)
+        n = int(ctx.saddle_off[-1])
+        x = np.random.default_rng(29).standard_normal(n)
+        out[dk] = (_host(ctx.rpy_apply(lam, 2)), _host(ctx.saddle_apply(x, 2)), x)
+    assert np.array_equal(out[3][0], out[4][0]) and np.array_equal(out[3][1], out[4][1])
+    sl = blob_slices(wl)
+    for s in range(wl.n_susp):
+        lay, Y, q = susp_layout(wl, s)
+        a, b = sl[s]
+        r, M, K, B = dense_state(lay, Y, q)
+        ref = M @ lam[3 * a:3 * b]
+        for dk, (udf, ydf, x) in out.items():
+            assert rel(udf[3 * a:3 * b], ref) < 1e-11, (dk, s, rel(udf[3 * a:3 * b], ref))
+            o = int(ctx.saddle_off[s])
+            m = 3 * lay.n_blobs + 6 * lay.n_bodies
+            y1, y2 = rigid.saddle_apply(M, K, x[o:o + 3 * lay.n_blobs], x[o + 3 * lay.n_blobs:o + m])
+            assert rel(ydf[o:o + m], np.concatenate([y1, y2])) < 1e-11, (dk, s)
 
 
 @pytest.mark.parametrize("kernel", [1, 2])
