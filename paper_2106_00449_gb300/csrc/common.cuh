@@ -32,7 +32,9 @@
 #define GDC_NEAR_CAP 32          // blobs closer than 2a listed per blob (beyond: a search of the suspension)
 #define GDC_NEAR_SRC 2048        // sources per block of the near-pair search
 #define GDC_SYM_TILE 512         // blobs per tile of the symmetric FP32 pair kernel
-#define GDC_DFS_WIDTH 8          // source tiles per item of the symmetric double-float kernel
+#ifndef GDC_DFS_WIDTH
+#define GDC_DFS_WIDTH 2          // source tiles per item of the symmetric double-float kernel
+#endif
 #define GDC_CELL_MIN_BLOBS 16384 // GDC_FORCES_CHOOSE: the cell list from this many blobs on
 #define GDC_WAIT_POLLS 400000    // default bound of a pair kernel's wait for a tile copy (polls)
 

@@ -23,7 +23,8 @@
 namespace gdc {
 
 constexpr int DFS_TILE = GDC_SYM_TILE;
-// dynamic shared memory: the source tile (4 float4 per source), then two buffers of the four
+// dynamic shared memory: the source tile (four planes of one float4 per source: the lanes'
+// rotated reads hit consecutive 16-byte words), then two buffers of the four
 // warps' source sums of one 32-source sub-chunk (3 doubles per source each)
 constexpr int DFS_SMEM = DFS_TILE * 4 * 16 + 2 * 4 * 3 * 32 * 8;
 
@@ -76,7 +77,7 @@ __global__ void __launch_bounds__(128, MINB) k_rpy_df_sym(const SymItem* __restr
                                                        double4_32a* __restrict__ part_i, double4_32a* __restrict__ part_j,
                                                        int NBL, RpyConstDF k) {
     extern __shared__ __align__(16) unsigned char dfs_smem[];
-    float4* sh = reinterpret_cast<float4*>(dfs_smem);                       // 4 per source
+    float4* sh = reinterpret_cast<float4*>(dfs_smem);                       // [plane][source]
     double* ws = reinterpret_cast<double*>(dfs_smem + DFS_TILE * 4 * 16);  // [buffer][warp][3][32]
     const SymItem it = items[blockIdx.x];
     const long long b0 = susp_blob_off[it.s];
@@ -112,20 +113,20 @@ __global__ void __launch_bounds__(128, MINB) k_rpy_df_sym(const SymItem* __restr
                 const double4_32a ps = spos[b0 + j0 + e], ls = slam[b0 + j0 + e];
                 const df x = df_from(ps.x), y = df_from(ps.y), z = df_from(ps.z);
                 const df lx = df_from(ls.x), ly = df_from(ls.y), lz = df_from(ls.z);
-                sh[4 * e] = make_float4(x.h, y.h, z.h, (float)ps.w);
-                sh[4 * e + 1] = make_float4(x.l, y.l, z.l, 0.f);
-                sh[4 * e + 2] = make_float4(lx.h, ly.h, lz.h, 0.f);
-                sh[4 * e + 3] = make_float4(lx.l, ly.l, lz.l, 0.f);
+                sh[e] = make_float4(x.h, y.h, z.h, (float)ps.w);
+                sh[DFS_TILE + e] = make_float4(x.l, y.l, z.l, 0.f);
+                sh[2 * DFS_TILE + e] = make_float4(lx.h, ly.h, lz.h, 0.f);
+                sh[3 * DFS_TILE + e] = make_float4(lx.l, ly.l, lz.l, 0.f);
             } else {   // padding: body -2 matches no target, lambda 0
-                sh[4 * e] = make_float4(0.f, 0.f, 0.f, -2.f);
-                sh[4 * e + 1] = sh[4 * e + 2] = sh[4 * e + 3] = make_float4(0.f, 0.f, 0.f, 0.f);
+                sh[e] = make_float4(0.f, 0.f, 0.f, -2.f);
+                sh[DFS_TILE + e] = sh[2 * DFS_TILE + e] = sh[3 * DFS_TILE + e] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
         }
         __syncthreads();
         if (J == it.I) {
             // diagonal tile: every ordered pair of different bodies, target side only
             for (int j = 0; j < n; ++j) {
-                const float4 s0 = sh[4 * j], s1 = sh[4 * j + 1], s2 = sh[4 * j + 2], s3 = sh[4 * j + 3];
+                const float4 s0 = sh[j], s1 = sh[DFS_TILE + j], s2 = sh[2 * DFS_TILE + j], s3 = sh[3 * DFS_TILE + j];
                 const df lx{s2.x, s3.x}, ly{s2.y, s3.y}, lz{s2.z, s3.z};
 #pragma unroll
                 for (int m = 0; m < 4; ++m) {
@@ -140,7 +141,7 @@ __global__ void __launch_bounds__(128, MINB) k_rpy_df_sym(const SymItem* __restr
                 df jx{0.f, 0.f}, jy{0.f, 0.f}, jz{0.f, 0.f};   // sums of the source this lane holds
                 for (int st = 0; st < 32; ++st) {
                     const int j = jc + ((lane + st) & 31);
-                    const float4 s0 = sh[4 * j], s1 = sh[4 * j + 1], s2 = sh[4 * j + 2], s3 = sh[4 * j + 3];
+                    const float4 s0 = sh[j], s1 = sh[DFS_TILE + j], s2 = sh[2 * DFS_TILE + j], s3 = sh[3 * DFS_TILE + j];
                     const df xs{s0.x, s1.x}, ys{s0.y, s1.y}, zs{s0.z, s1.z};
                     const df lx{s2.x, s3.x}, ly{s2.y, s3.y}, lz{s2.z, s3.z};
                     const bool pad = s0.w < -1.5f;   // past the end of the suspension

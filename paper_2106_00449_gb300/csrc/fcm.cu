@@ -12,10 +12,11 @@
 //     least R_t wide) and stages the blobs of the 27 cells around it (blobs in ascending
 //     index) in shared memory as FP32 offsets from the cell's corner; it is deterministic and
 //     needs no atomics on the grid;
-//   * the 3-D FFT is three passes of radix-2 transforms of whole pencils in shared memory,
-//     16 pencils per block, three butterfly stages per trip through shared memory; for the
-//     y and z passes the 16 pencils are 16 consecutive x, so every global access is a
-//     coalesced run;
+//   * the 3-D FFT is one launch per axis of self-sorting (Stockham) passes of radix 8 (then
+//     4 or 2) with 8 points of a pencil per thread in registers, exchanged through shared
+//     memory between passes (two exchanges for 512-point pencils); points are read once and
+//     written once per axis, along x in the x pass and P consecutive x at a time in the y and
+//     z passes;
 //   * the solve (projection, 1/(eta k^2), the spectral divergence of the stress and the 1/N^3
 //     of the inverse transform) is one pass over the modes;
 //   * averaging reads the velocity packed per point (one 16-byte load) and takes one warp per
@@ -112,21 +113,33 @@ static void fcm_layout(gdc_fcm* f, const gdc_fcm_params& p) {
     f->nc = fcm_cells(p);
 }
 
-// Shared-memory row of a pencil: N points, element i at i + i/16 (the padding spreads the
-// bit-reversed and strided accesses over the banks), rows an odd number of float2 apart.
-__host__ __device__ inline int fft_row(int N) { return N + N / 16 + 1; }
-__device__ __forceinline__ int fft_pad(int i) { return i + (i >> 4); }
-// Pencils per block: 16 (16 consecutive x: 128-byte runs in the strided y and z passes),
-// except for 512-point pencils of the contiguous x pass, 8 to a block.
-#ifndef GDC_FFT512_LP_YZ
-#define GDC_FFT512_LP_YZ 3
+// FFT blocks: TH threads (256; 512 or 1024 in the strided passes of 256- and 512-point
+// pencils), each holding 8 points of one pencil, so a block transforms P = 8 TH / N pencils.
+// Between passes the points go through shared memory, one row of fft_stride(N, P) float2 per
+// pencil, point t of a row at fft_swz(t) = t ^ ((t >> 3) & 15) (a bijection of [0, N)): with
+// these strides the 16 float2 of every half-warp (stride-8 writes of the first pass, grouped
+// writes of the second, unit-stride reads) fall in distinct bank pairs for N >= 128,
+// whichever way the threads map to pencils.
+__host__ __device__ constexpr int fft_stride(int N, int P) {
+    return N >= 128 ? N + (P >= 16 ? 1 : 16 / P) : (N == 32 ? 35 : N + 1);
+}
+__device__ __forceinline__ int fft_swz(int t) { return t ^ ((t >> 3) & 15); }
+static size_t fft_smem(int N, int TH) {
+    const int P = 8 * TH / N;
+    return (size_t)(P * fft_stride(N, P) + N) * sizeof(float2);
+}
+// Threads per block of the y and z passes for 256- and 512-point pencils (P consecutive x
+// per warp row: 4 x 8 bytes = 32-byte runs at 256 threads and N = 512, 64 at 512, 128 at
+// 1024).  Measured at 512^3 (M_FCM lambda / v-breve): 256 and 256 threads 16.6 / 15.6 ms,
+// 512 and 512 15.0 / 13.6, 1024 and 1024 15.1 / 13.7, 256 and 1024 14.8 / 13.4, 512 and
+// 1024 14.8 / 13.3: the z pass, whose points are N^2 apart, wants the longest runs.
+#ifndef GDC_FFT_TH_Y
+#define GDC_FFT_TH_Y 512
 #endif
-#ifndef GDC_FFT512_TH_YZ
-#define GDC_FFT512_TH_YZ 256
+#ifndef GDC_FFT_TH_Z
+#define GDC_FFT_TH_Z 1024
 #endif
-static int fft_lp(int N, int axis) { return N >= 512 ? (axis == 0 ? 3 : GDC_FFT512_LP_YZ) : 4; }
-static size_t fft_smem_lp(int N, int lp) { return (size_t)(((size_t)1 << lp) * fft_row(N) + N / 2) * sizeof(float2); }
-static size_t fft_smem(int N) { return std::max(fft_smem_lp(N, fft_lp(N, 0)), fft_smem_lp(N, fft_lp(N, 1))); }
+static int fft_threads(int N, int axis) { return N < 256 || axis == 0 ? 256 : (axis == 1 ? GDC_FFT_TH_Y : GDC_FFT_TH_Z); }
 
 // ---- binning ------------------------------------------------------------------------
 
@@ -280,88 +293,154 @@ __global__ void k_fcm_pack(long long NG, const float2* __restrict__ u, float4* _
     out[g] = make_float4(a.x, a.y, u[NG + g].x, 0.f);
 }
 
-// ---- FFT: radix-2 transforms of 16 pencils per block, one axis per pass -----------------
-
+// ---- FFT: self-sorting (Stockham) passes of radix 8, then 4 or 2; one axis per launch ----
+//
 // INV = 0: X_k = sum_n x_n exp(-2 pi i k n / N); INV = 1: the same with +i, unscaled.
-// blockIdx.y picks the component grid (NG points apart).
-template <int INV, int LP, int TH>
-__global__ void __launch_bounds__(TH) k_fft(float2* __restrict__ data, long long NG, const float2* __restrict__ tw_g,
-                                             int N, int logN, int axis) {
-    constexpr int P = 1 << LP;
-    extern __shared__ float2 sm[];
-    const int S = fft_row(N);
-    float2* tw = sm + P * S;
-    float2* base = data + blockIdx.y * NG;
-    const int groups = N / P;
-    const int b = blockIdx.x;
-    long long off, sp, st;   // first element, pencil stride, element stride
-    if (axis == 0) {
-        off = (long long)N * ((b % groups) * P + (long long)N * (b / groups));
-        sp = N;
-        st = 1;
-    } else if (axis == 1) {
-        off = (b % groups) * P + (long long)N * N * (b / groups);
-        sp = 1;
-        st = N;
+// blockIdx.y picks the component grid (NG points apart).  Thread i of a pencil holds the
+// points i + m T (m = 0..7, T = N/8) in registers.  A pass of radix R that follows
+// sub-transforms of length p treats 8/R virtual threads v = i + u T: with k = v mod p it
+// multiplies its inputs v + j N/R (j < R) by w^(j k), w = exp(-+2 pi i / (p R)), takes their
+// R-point DFT and writes output j to (v - k) R + k + j p, so the points end in natural order
+// after the last pass (Stockham's self-sorting order, no bit reversal).  The first pass
+// reads straight from global memory and the last writes straight back, both at i + m T
+// (coalesced along x in the x pass; P consecutive x per warp row in the y and z passes);
+// in between the block exchanges its points through shared memory.
+
+// x w (INV: x conj(w)), w a forward twiddle exp(-2 pi i m / N)
+template <int INV>
+__device__ __forceinline__ float2 fft_twiddle(float2 x, float2 w) {
+    if (INV) w.y = -w.y;
+    return make_float2(x.x * w.x - x.y * w.y, x.x * w.y + x.y * w.x);
+}
+
+// z times exp(-+2 pi i / 4) = -+i
+template <int INV>
+__device__ __forceinline__ float2 fft_rot4(float2 z) {
+    return INV ? make_float2(-z.y, z.x) : make_float2(z.y, -z.x);
+}
+
+__device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+
+// In-place R-point DFT of z[0..R-1] (R = 2, 4, 8), outputs in natural order.
+template <int R, int INV>
+__device__ __forceinline__ void fft_dft(float2* z) {
+    if (R == 2) {
+        const float2 a = z[0], b = z[1];
+        z[0] = c_add(a, b);
+        z[1] = c_sub(a, b);
+    } else if (R == 4) {
+        const float2 t0 = c_add(z[0], z[2]), t1 = c_sub(z[0], z[2]);
+        const float2 t2 = c_add(z[1], z[3]), t3 = fft_rot4<INV>(c_sub(z[1], z[3]));
+        z[0] = c_add(t0, t2);
+        z[2] = c_sub(t0, t2);
+        z[1] = c_add(t1, t3);
+        z[3] = c_sub(t1, t3);
     } else {
-        off = (b % groups) * P + (long long)N * (b / groups);
-        sp = 1;
-        st = (long long)N * N;
-    }
-    for (int j = threadIdx.x; j < N / 2; j += blockDim.x) {
-        float2 w = tw_g[j];
-        if (INV) w.y = -w.y;
-        tw[j] = w;
-    }
-    const int total = P * N, nmask = N - 1;   // N and P are powers of two: shifts and masks
-    for (int e = threadIdx.x; e < total; e += blockDim.x) {
-        const int t = axis == 0 ? (e & nmask) : (e >> LP);
-        const int p = axis == 0 ? (e >> logN) : (e & (P - 1));
-        sm[p * S + fft_pad((int)(__brev((unsigned)t) >> (32 - logN)))] = base[off + p * sp + t * st];
-    }
-    // log2 N radix-2 stages, fused three at a time: a thread loads the 8 elements
-    // k + m h (m = 0..7) of a group of 8h, applies the stages of half h, 2h, 4h in registers
-    // (the same butterflies, in the same arithmetic, as stage-by-stage), and stores them back.
-    const int first = logN % 3 == 0 ? 3 : logN % 3;
-    for (int s0 = 0, ns = first; s0 < logN; s0 += ns, ns = 3) {
-        const int h = 1 << s0, lper = logN - ns;   // 2^lper groups x offsets per pencil
-        __syncthreads();
-        for (int q = threadIdx.x; q < (P << lper); q += blockDim.x) {
-            const int p = q >> lper, r = q & ((1 << lper) - 1);
-            const int k = r & (h - 1), base0 = ((r >> s0) << (s0 + ns)) + k;
-            float2* row = sm + p * S;
-            float2 x[8];
+        // even and odd halves by 4-point DFTs, then the radix-2 step with exp(-+2 pi i j / 8)
+        float2 e[4] = {z[0], z[2], z[4], z[6]}, o[4] = {z[1], z[3], z[5], z[7]};
+        fft_dft<4, INV>(e);
+        fft_dft<4, INV>(o);
+        const float r = 0.70710678118654752f;   // 1/sqrt(2)
+        o[1] = fft_twiddle<INV>(o[1], make_float2(r, -r));
+        o[2] = fft_rot4<INV>(o[2]);
+        o[3] = fft_twiddle<INV>(o[3], make_float2(-r, -r));
 #pragma unroll
-            for (int m = 0; m < 8; ++m)
-                if (m < (1 << ns)) x[m] = row[fft_pad(base0 + m * h)];
-#pragma unroll
-            for (int st = 0; st < 3; ++st) {
-                if (st < ns) {
-                    const int lstep = logN - 1 - s0 - st;   // twiddle stride N / (2 h 2^st)
-#pragma unroll
-                    for (int m = 0; m < 8; ++m) {
-                        if (m < (1 << ns) && ((m >> st) & 1) == 0) {
-                            const int m2 = m + (1 << st);
-                            const float2 w = tw[(k + ((m & ((1 << st) - 1)) << s0)) << lstep];
-                            const float2 x0 = x[m], x1 = x[m2];
-                            const float2 t = make_float2(w.x * x1.x - w.y * x1.y, w.x * x1.y + w.y * x1.x);
-                            x[m] = make_float2(x0.x + t.x, x0.y + t.y);
-                            x[m2] = make_float2(x0.x - t.x, x0.y - t.y);
-                        }
-                    }
-                }
-            }
-#pragma unroll
-            for (int m = 0; m < 8; ++m)
-                if (m < (1 << ns)) row[fft_pad(base0 + m * h)] = x[m];
+        for (int j = 0; j < 4; ++j) {
+            z[j] = c_add(e[j], o[j]);
+            z[j + 4] = c_sub(e[j], o[j]);
         }
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < total; e += blockDim.x) {
-        const int t = axis == 0 ? (e & nmask) : (e >> LP);
-        const int p = axis == 0 ? (e >> logN) : (e & (P - 1));
-        base[off + p * sp + t * st] = sm[p * S + fft_pad(t)];
+}
+
+// One pass of radix R after sub-transforms of length PL; LAST leaves the outputs in x at
+// i + m T, the others write them to the pencil's shared-memory row and read the next pass's
+// inputs back.
+template <int INV, int LOGN, int R, int PL, bool LAST>
+__device__ __forceinline__ void fft_pass(float2 (&x)[8], float2* row, const float2* tw, int i) {
+    constexpr int N = 1 << LOGN, T = N / 8, V = 8 / R;
+    float2 y[8];
+#pragma unroll
+    for (int u = 0; u < V; ++u) {
+        const int v = i + u * T, k = v & (PL - 1);
+        float2 z[8];
+#pragma unroll
+        for (int j = 0; j < R; ++j) z[j] = x[u + j * V];
+        if (PL > 1) {
+#pragma unroll
+            for (int j = 1; j < R; ++j) z[j] = fft_twiddle<INV>(z[j], tw[(j * k * (N / (PL * R))) & (N - 1)]);
+        }
+        fft_dft<R, INV>(z);
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            if (LAST)
+                y[u + j * V] = z[j];
+            else
+                row[fft_swz((v - k) * R + k + j * PL)] = z[j];
+        }
     }
+    if (LAST) {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) x[m] = y[m];
+    } else {
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < 8; ++m) x[m] = row[fft_swz(i + m * T)];
+        __syncthreads();   // the row is rewritten by the next pass
+    }
+}
+
+template <int INV, int LOGN, int PASS>
+__device__ __forceinline__ void fft_passes(float2 (&x)[8], float2* row, const float2* tw, int i) {
+    constexpr int NP8 = LOGN / 3, REM = LOGN % 3, NPASS = NP8 + (REM ? 1 : 0);
+    if constexpr (PASS < NPASS) {
+        constexpr int R = PASS < NP8 ? 8 : (REM == 1 ? 2 : 4);
+        fft_pass<INV, LOGN, R, (1 << (3 * PASS)), PASS == NPASS - 1>(x, row, tw, i);
+        fft_passes<INV, LOGN, PASS + 1>(x, row, tw, i);
+    }
+}
+
+template <int INV, int LOGN, int TH>
+__global__ void __launch_bounds__(TH) k_fft(float2* __restrict__ data, long long NG, const float2* __restrict__ tw_g,
+                                              int axis) {
+    constexpr int N = 1 << LOGN, T = N / 8, P = TH / T, S = fft_stride(N, P);
+    extern __shared__ float2 sm[];
+    float2* tw = sm + P * S;   // exp(-2 pi i m / N), m = 0..N-1
+    for (int j = threadIdx.x; j < N / 2; j += TH) {
+        const float2 w = tw_g[j];
+        tw[j] = w;
+        tw[j + N / 2] = make_float2(-w.x, -w.y);
+    }
+    // pencil pid = blockIdx.x P + q of the N^2 along the axis; in the x pass a pencil's T
+    // threads are consecutive, in the y and z passes the P pencils (consecutive x) are
+    int q, i;
+    if (axis == 0) {
+        q = threadIdx.x / T;
+        i = threadIdx.x % T;
+    } else {
+        q = threadIdx.x % P;
+        i = threadIdx.x / P;
+    }
+    const long long pid = (long long)blockIdx.x * P + q;
+    long long o, st;
+    if (axis == 0) {
+        o = pid << LOGN;
+        st = 1;
+    } else if (axis == 1) {
+        o = (pid & (N - 1)) + ((pid >> LOGN) << (2 * LOGN));
+        st = N;
+    } else {
+        o = (pid & (N - 1)) + ((pid >> LOGN) << LOGN);
+        st = (long long)N * N;
+    }
+    float2* g = data + blockIdx.y * NG + o;
+    float2 x[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) x[m] = g[(long long)(i + m * T) * st];
+    __syncthreads();   // twiddle table complete
+    fft_passes<INV, LOGN, 0>(x, sm + q * S, tw, i);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) g[(long long)(i + m * T) * st] = x[m];
 }
 
 // ---- Fourier-space solve ------------------------------------------------------------------
@@ -554,28 +633,34 @@ static gdc_status fcm_check(gdc_fcm* f, cudaError_t e, const char* what) {
 }
 
 static void fft3(gdc_fcm* f, int slot, int ncomp, bool inverse) {
-    // 512-point pencils go 8 to a block in the contiguous x pass, so that a block's shared
-    // memory (37 KB) leaves room for as many resident blocks as the 16 pencils of shorter
-    // transforms
     float2* d = f->grid + slot * f->NG;
     for (int axis = 0; axis < 3; ++axis) {
-        const int lp = fft_lp(f->N, axis);
-        const dim3 grid((unsigned)(f->N * f->N >> lp), (unsigned)ncomp);
-        const size_t smem = fft_smem_lp(f->N, lp);
-#define GDC_FFT(LP_, TH_)                                                                              \
-    do {                                                                                               \
-        if (inverse)                                                                                   \
-            k_fft<1, LP_, TH_><<<grid, TH_, smem, f->stream>>>(d, f->NG, f->tw, f->N, f->logN, axis);  \
-        else                                                                                           \
-            k_fft<0, LP_, TH_><<<grid, TH_, smem, f->stream>>>(d, f->NG, f->tw, f->N, f->logN, axis);  \
+        const int th = fft_threads(f->N, axis);
+        const dim3 grid((unsigned)(f->NG / (8LL * th)), (unsigned)ncomp);   // N^2 pencils, 8 TH / N per block
+        const size_t smem = fft_smem(f->N, th);
+#define GDC_FFT(L, TH_)                                                                         \
+    do {                                                                                        \
+        if (inverse)                                                                            \
+            k_fft<1, L, TH_><<<grid, TH_, smem, f->stream>>>(d, f->NG, f->tw, axis);            \
+        else                                                                                    \
+            k_fft<0, L, TH_><<<grid, TH_, smem, f->stream>>>(d, f->NG, f->tw, axis);            \
     } while (0)
         ++f->n_launch;
-        if (lp == 3)
-            GDC_FFT(3, 256);
-        else if (f->N >= 512)
-            GDC_FFT(4, GDC_FFT512_TH_YZ);
-        else
-            GDC_FFT(4, 256);
+        switch (f->logN) {
+            case 4: GDC_FFT(4, 256); break;
+            case 5: GDC_FFT(5, 256); break;
+            case 6: GDC_FFT(6, 256); break;
+            case 7: GDC_FFT(7, 256); break;
+            case 8:
+                if (th == 1024) GDC_FFT(8, 1024);
+                else if (th == 512) GDC_FFT(8, 512);
+                else GDC_FFT(8, 256);
+                break;
+            default:
+                if (th == 1024) GDC_FFT(9, 1024);
+                else if (th == 512) GDC_FFT(9, 512);
+                else GDC_FFT(9, 256);
+        }
 #undef GDC_FFT
     }
 }
@@ -643,17 +728,12 @@ gdc_status gdc_fcm_init(gdc_fcm** out, const gdc_fcm_params* params, void* works
         tw[j] = make_float2((float)std::cos(a), (float)-std::sin(a));
     }
     cudaError_t e = cudaMemcpyAsync(f->tw, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice, f->stream);
-    const int fsm = (int)std::max(fft_smem(256), fft_smem(512));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft<0, 3, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft<1, 3, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft<0, 4, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft<1, 4, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm);
-    if (GDC_FFT512_TH_YZ != 256) {
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_fft<0, 4, GDC_FFT512_TH_YZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_fft<1, 4, GDC_FFT512_TH_YZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm);
-    }
+    // 1024-thread blocks of 256- and 512-point pencils take 66 and 68 KB of shared memory
+    const int fsm = (int)std::max(fft_smem(256, 1024), fft_smem(512, 1024));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft<0, 8, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft<1, 8, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft<0, 9, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft<1, 9, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm);
     if (e == cudaSuccess) e = cudaStreamSynchronize(f->stream);
     if (e != cudaSuccess) {
         delete f;

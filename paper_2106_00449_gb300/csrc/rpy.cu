@@ -899,9 +899,14 @@ void plan_mv_capacity(gdc_ctx* c) {
     c->sym_n_tiles = c->h_sym_tile_base.back();
     c->sym_n_jslots = c->h_sym_jbase.back();
     build_sym_items(c, 4);
-    // the symmetric double-float kernel: items of up to 8 source tiles (its per-pair work is
-    // ~8x the FP32 kernel's, so fewer, longer items balance as well)
-    build_sym_list(c, GDC_DFS_WIDTH, c->h_dfs_items, c->h_dfs_row_nk, c->dfs_kmax);
+    // the symmetric double-float kernel: items of GDC_DFS_WIDTH source tiles, so that with 3
+    // or 4 resident blocks per SM the last wave of long items stays full; wider in
+    // suspensions of more than 64 x GDC_DFS_WIDTH tiles, which keeps the target-side slots
+    // at 64 per blob (each wave is then a small part of the launch anyway)
+    int tmax = 1;
+    for (int s = 0; s < c->S; ++s)
+        tmax = std::max(tmax, (int)((c->h_blob_off[s + 1] - c->h_blob_off[s] + GDC_SYM_TILE - 1) / GDC_SYM_TILE));
+    build_sym_list(c, std::max(GDC_DFS_WIDTH, (tmax + 63) / 64), c->h_dfs_items, c->h_dfs_row_nk, c->dfs_kmax);
     c->dfs_n_items = (int)c->h_dfs_items.size();
 }
 
