@@ -22,7 +22,7 @@
 //   * averaging reads the velocity packed per point (one 16-byte load) and takes one warp per
 //     blob, each lane a fixed x offset and every (32 / width)-th row of the blob's box (at
 //     most 31 points per side); each lane sums its points of a z-plane in FP32 and the
-//     planes in FP64, and the lanes are added in a fixed order.
+//     planes with FP32 compensation, and the lanes are added in FP64 in a fixed order.
 #include <algorithm>
 #include <cmath>
 #include <new>
@@ -182,9 +182,14 @@ constexpr int SP_CHUNK = 512;    // blobs staged in shared memory per round
 // and every blob that can reach them lies in the 27 cells around it.  Those blobs are staged in shared memory (cells in a fixed order, blobs in
 // ascending index; rounds of SP_CHUNK) as FP32 offsets from the cell's corner, nearest image
 // to the cell's centre, and each thread sums them for its grid points with the minimum image
-// in FP32.  Deterministic, no atomics on the grid.
-template <int PT>   // grid points a thread keeps per round (cells with more points take several rounds)
-__global__ void __launch_bounds__(128) k_fcm_spread(int N, double h, double L, int nc, const double4_32a* __restrict__ pw,
+// in FP32.  Deterministic, no atomics on the grid.  With at least 4 cells per side every
+// staged offset is within 2 cell widths of the cell, less than L/2 from any of its grid
+// points, so the per-pair minimum image is the identity and WRAP = false drops it.  The image
+// of a staged blob is chosen with a multiplication by 1/L (an FP64 division per coordinate
+// there would make the FP64 pipe, 1/64 of the FP32 rate on this GPU, the kernel's limit).
+template <int PT, bool WRAP>   // PT: grid points a thread keeps per round
+__global__ void __launch_bounds__(128) k_fcm_spread(int N, double h, double L, double invL, double w, int nc,
+                                                    const double4_32a* __restrict__ pw,
                                                     const int* __restrict__ cnt, const int* __restrict__ start,
                                                     const int* __restrict__ list, const double* __restrict__ lam,
                                                     float R2, float inv2s2, float norm, float2* __restrict__ f,
@@ -192,15 +197,14 @@ __global__ void __launch_bounds__(128) k_fcm_spread(int N, double h, double L, i
     __shared__ float4 sp[SP_CHUNK];
     __shared__ float4 sl[SP_CHUNK];
     __shared__ int c_start[27], c_off[28];
+    __shared__ float base_off[3];   // offset of the cell's first grid point from its corner
+    __shared__ double corner[3];    // the cell's corner (w = L / nc, the cell width)
     const int b = blockIdx.x;
     const int c3[3] = {b % nc, (b / nc) % nc, b / (nc * nc)};
-    const double w = L / nc;
     int g0[3], gn[3];
-    double corner[3];
     for (int d = 0; d < 3; ++d) {
         g0[d] = (c3[d] * N + nc - 1) / nc;                  // first i with floor(i nc / N) = c
         gn[d] = ((c3[d] + 1) * N + nc - 1) / nc - g0[d];
-        corner[d] = c3[d] * w;
     }
     const int npts = gn[0] * gn[1] * gn[2];
     if (npts <= (int)blockIdx.y * PT * 128) return;   // whole block: no points in this chunk
@@ -214,13 +218,17 @@ __global__ void __launch_bounds__(128) k_fcm_spread(int N, double h, double L, i
         c_off[k + 1] = cnt[id];
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0) {   // the block's FP64 geometry, once (the FP64 pipe is slow)
         c_off[0] = 0;
         for (int k = 0; k < ncell; ++k) c_off[k + 1] += c_off[k];
+        for (int d = 0; d < 3; ++d) {
+            corner[d] = c3[d] * w;
+            base_off[d] = (float)(g0[d] * h - corner[d]);
+        }
     }
     __syncthreads();
     const int total = c_off[ncell];
-    const float Lf = (float)L, hL = 0.5f * Lf;
+    const float Lf = (float)L, hL = 0.5f * Lf, hf = (float)h;
     const double mid = 0.5 * w;
     {
         const int p0 = blockIdx.y * PT * 128;   // this block's chunk of the cell's grid points
@@ -233,11 +241,13 @@ __global__ void __launch_bounds__(128) k_fcm_spread(int N, double h, double L, i
             gi[q] = -1;
             gx[q] = gy[q] = gz[q] = 0.f;
             if (pt < npts) {
-                const int ix = g0[0] + pt % gn[0], iy = g0[1] + (pt / gn[0]) % gn[1], iz = g0[2] + pt / (gn[0] * gn[1]);
-                gx[q] = (float)(ix * h - corner[0]);
-                gy[q] = (float)(iy * h - corner[1]);
-                gz[q] = (float)(iz * h - corner[2]);
-                gi[q] = ix + (long long)N * (iy + (long long)N * iz);
+                // in FP32 from the block's base: FP64 arithmetic per point would load the FP64
+                // pipe (1/64 of the FP32 rate) more than the pair loop loads the FP32 one
+                const int jx = pt % gn[0], jy = (pt / gn[0]) % gn[1], jz = pt / (gn[0] * gn[1]);
+                gx[q] = fmaf((float)jx, hf, base_off[0]);
+                gy[q] = fmaf((float)jy, hf, base_off[1]);
+                gz[q] = fmaf((float)jz, hf, base_off[2]);
+                gi[q] = (g0[0] + jx) + (long long)N * ((g0[1] + jy) + (long long)N * (g0[2] + jz));
             }
         }
         for (int s0 = 0; s0 < total; s0 += SP_CHUNK) {
@@ -250,9 +260,9 @@ __global__ void __launch_bounds__(128) k_fcm_spread(int N, double h, double L, i
                 const int j = list[c_start[k] + (e - c_off[k])];
                 const double4_32a p = pw[j];
                 double rx = p.x - corner[0], ry = p.y - corner[1], rz = p.z - corner[2];
-                rx -= L * rint((rx - mid) / L);
-                ry -= L * rint((ry - mid) / L);
-                rz -= L * rint((rz - mid) / L);
+                rx -= L * rint((rx - mid) * invL);
+                ry -= L * rint((ry - mid) * invL);
+                rz -= L * rint((rz - mid) * invL);
                 sp[t] = make_float4((float)rx, (float)ry, (float)rz, 0.f);
                 sl[t] = make_float4((float)lam[3LL * j], (float)lam[3LL * j + 1], (float)lam[3LL * j + 2], 0.f);
             }
@@ -262,9 +272,11 @@ __global__ void __launch_bounds__(128) k_fcm_spread(int N, double h, double L, i
 #pragma unroll
                 for (int q = 0; q < PT; ++q) {
                     float dx = gx[q] - pj.x, dy = gy[q] - pj.y, dz = gz[q] - pj.z;
-                    dx = dx > hL ? dx - Lf : (dx < -hL ? dx + Lf : dx);
-                    dy = dy > hL ? dy - Lf : (dy < -hL ? dy + Lf : dy);
-                    dz = dz > hL ? dz - Lf : (dz < -hL ? dz + Lf : dz);
+                    if (WRAP) {
+                        dx = dx > hL ? dx - Lf : (dx < -hL ? dx + Lf : dx);
+                        dy = dy > hL ? dy - Lf : (dy < -hL ? dy + Lf : dy);
+                        dz = dz > hL ? dz - Lf : (dz < -hL ? dz + Lf : dz);
+                    }
                     const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                     if (d2 <= R2) {
                         const float wt = norm * expf(-d2 * inv2s2);
@@ -568,20 +580,29 @@ __global__ void __launch_bounds__(128) k_fcm_average(int n, const double* __rest
     const int i = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (i >= n) return;
-    double p[3];
+    // the blob's box and its offset from the box's first grid point, formed by lane 0 and
+    // shared by shuffles: FP64 divisions on every lane would keep the FP64 pipe (1/64 of
+    // the FP32 rate) busier than the whole sum over the box
     int lo[3], cn[3];
+    float d0[3];
     for (int d = 0; d < 3; ++d) {
-        double x = r[3LL * i + d];
-        x -= L * floor(x / L);
-        if (!(x < L) || !(x >= 0.0)) x = 0.0;
-        p[d] = x;
-        lo[d] = (int)ceil((x - R_t) / h);
-        cn[d] = min(31, (int)floor((x + R_t) / h) - lo[d] + 1);
+        int l = 0, c = 0;
+        float o = 0.f;
+        if (lane == 0) {
+            double x = r[3LL * i + d];
+            x -= L * floor(x / L);
+            if (!(x < L) || !(x >= 0.0)) x = 0.0;
+            l = (int)ceil((x - R_t) / h);
+            c = min(31, (int)floor((x + R_t) / h) - l + 1);
+            o = (float)(l * h - x);   // magnitude below R_t + h: FP32 keeps it to ~1e-7 R_t
+        }
+        lo[d] = __shfl_sync(0xffffffffu, l, 0);
+        cn[d] = __shfl_sync(0xffffffffu, c, 0);
+        d0[d] = __shfl_sync(0xffffffffu, o, 0);
     }
-    // offsets from the blob to the first grid point of its box, then steps of h, in FP32
-    // (magnitudes below R_t + h, so FP32 keeps them to ~1e-7 R_t)
+    // offsets from the blob to the grid points of its box: the first one, then steps of h
     const float hf = (float)h, R2 = (float)(R_t * R_t);
-    const float d0x = (float)(lo[0] * h - p[0]), d0y = (float)(lo[1] * h - p[1]), d0z = (float)(lo[2] * h - p[2]);
+    const float d0x = d0[0], d0y = d0[1], d0z = d0[2];
     const int mask = N - 1;                          // N is a power of two
     const int rows = cn[0] <= 16 ? 32 / cn[0] : 1;   // box rows a warp covers per pass
     const int ox = lane % cn[0], oyr = lane / cn[0];
@@ -589,34 +610,47 @@ __global__ void __launch_bounds__(128) k_fcm_average(int n, const double* __rest
     const float dx = d0x + ox * hf;
     const float wx = expf(-dx * dx * inv2s2);
     const int ix = (lo[0] + ox) & mask;
-    double acc[3] = {0.0, 0.0, 0.0};
-    for (int oz = 0; oz < cn[2]; ++oz) {
-        const float dz = d0z + oz * hf;
+    // the planes' sums added with compensation (Kahan) in FP32: as accurate as FP64 for a
+    // box's at most 31 planes, without an FP32-to-FP64 conversion and FP64 add per plane
+    float acc[3] = {0.f, 0.f, 0.f}, cmp[3] = {0.f, 0.f, 0.f};
+    // integer offsets also kept as floats (exact), so no conversion per point
+    float foz = 0.f;
+    const float frows = (float)rows;
+    for (int oz = 0; oz < cn[2]; ++oz, foz += 1.f) {
+        const float dz = fmaf(foz, hf, d0z);
         const float wz = expf(-dz * dz * inv2s2) * wx;
         const float dxz = fmaf(dx, dx, dz * dz);
         const long long zoff = (long long)((lo[2] + oz) & mask) * N * N + ix;
         float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+        float foy = (float)oyr;
 #pragma unroll 4
-        for (int oy = oyr; oy < cn[1]; oy += rows) {
-            const float dy = d0y + oy * hf;
+        for (int oy = oyr; oy < cn[1]; oy += rows, foy += frows) {
+            const float dy = fmaf(foy, hf, d0y);
             if (on && fmaf(dy, dy, dxz) <= R2) {
                 const float wgt = expf(-dy * dy * inv2s2) * wz;
-                const float4 q = __ldg(u + zoff + (long long)((lo[1] + oy) & mask) * N);
+                const float4 q = __ldg(u + zoff + ((lo[1] + oy) & mask) * N);   // within a plane: int
                 a0 = fmaf(q.x, wgt, a0);
                 a1 = fmaf(q.y, wgt, a1);
                 a2 = fmaf(q.z, wgt, a2);
             }
         }
-        acc[0] += a0;
-        acc[1] += a1;
-        acc[2] += a2;
+        const float a[3] = {a0, a1, a2};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float y = a[c] - cmp[c], t = acc[c] + y;
+            cmp[c] = (t - acc[c]) - y;
+            acc[c] = t;
+        }
     }
-    for (int c = 0; c < 3; ++c)
-        for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_down_sync(0xffffffffu, acc[c], o);
+    double tot[3];
+    for (int c = 0; c < 3; ++c) {
+        tot[c] = (double)acc[c] - (double)cmp[c];
+        for (int o = 16; o > 0; o >>= 1) tot[c] += __shfl_down_sync(0xffffffffu, tot[c], o);
+    }
     if (lane == 0) {
-        v[3LL * i] = acc[0] * wscale;
-        v[3LL * i + 1] = acc[1] * wscale;
-        v[3LL * i + 2] = acc[2] * wscale;
+        v[3LL * i] = tot[0] * wscale;
+        v[3LL * i + 1] = tot[1] * wscale;
+        v[3LL * i + 2] = tot[2] * wscale;
     }
 }
 
@@ -761,8 +795,13 @@ gdc_status gdc_fcm_apply(gdc_fcm* f, int n, const double* r, const double* lambd
         const unsigned chunks = (unsigned)((side * side * side + 511) / 512);
         const float R2 = (float)(f->p.R_t * f->p.R_t), i2 = (float)(0.5 / s2);
         const float nrm = (float)std::pow(2.0 * 3.141592653589793 * s2, -1.5);
-        ++f->n_launch, k_fcm_spread<4><<<dim3((unsigned)nc3, chunks), 128, 0, f->stream>>>(
-            f->N, f->h, f->p.L, f->nc, f->pw, f->cnt, f->start, f->list, lambda, R2, i2, nrm, f->grid, f->NG);
+        ++f->n_launch;
+        if (f->nc >= 4)
+            k_fcm_spread<4, false><<<dim3((unsigned)nc3, chunks), 128, 0, f->stream>>>(
+                f->N, f->h, f->p.L, 1.0 / f->p.L, f->p.L / f->nc, f->nc, f->pw, f->cnt, f->start, f->list, lambda, R2, i2, nrm, f->grid, f->NG);
+        else
+            k_fcm_spread<4, true><<<dim3((unsigned)nc3, chunks), 128, 0, f->stream>>>(
+                f->N, f->h, f->p.L, 1.0 / f->p.L, f->p.L / f->nc, f->nc, f->pw, f->cnt, f->start, f->list, lambda, R2, i2, nrm, f->grid, f->NG);
     }
     // grids 0-1: FFT(f_x + i f_y), FFT(f_z); grids 2-3: the velocity's (u_x + i u_y, u_z)
     fft3(f, 0, 2, false);
