@@ -21,7 +21,8 @@ prints its mean time per call (CUDA events on the library's stream): rpy32 / rpy
 (one RPY product in FP32 / FP64 / double-float), saddle32, precond, forces32 (positions and
 pair forces), lanczos32 (one v-breve), solve32 (one FP32-mixed mobility solve), step32 (one
 gDC step, --graph 0|1), fcm_apply / fcm_brownian / fcm_average (fluctuating FCM of the
-workload's blobs in a periodic cube of its box side, --fcm-n grid points per side).  This is
+workload's blobs in a periodic cube of its box side, --fcm-n grid points per side), fma_peak
+(the FP32 FMA throughput probe, packed and scalar).  This is
 the command the ncu captures under profiles/ run: its kernels_before_timed_calls counts the
 library's kernels (all named k_*) launched before the timed calls, so `ncu -k regex:^k_ -s`
 that count starts at the first timed call.
@@ -397,6 +398,25 @@ def fcm_measure(g, torch, wl, ctx, N: int, reps: int = 3) -> dict:
     return out
 
 
+def fma_probe_measure(g, torch, stream, n_sm: int, iters: int = 2048, reps: int = 3):
+    """FP32 FMA throughput of the library's probe kernel (8 resident 256-thread blocks per SM,
+    8 independent chains per thread), packed f32x2 and scalar, CUDA events on `stream`."""
+    out = torch.empty(n_sm * 8 * 256, dtype=torch.float32, device=torch.device("cuda", torch.cuda.current_device()))
+    res = {"blocks": n_sm * 8, "threads_per_block": 256, "iters": iters,
+           "note": "8 independent chains of FP32 pairs per thread, nothing else in the loop: "
+                   "16 scalar FMAs, 8 packed f32x2 FMAs or 4 packed + 8 scalar per iteration; "
+                   "pair_kernel_frac_of_packed = the pair kernel's achieved TFLOP/s / packed_tflops"}
+    for mode, key in ((1, "packed_tflops"), (0, "scalar_tflops"), (2, "mixed_tflops")):
+        g.fma_probe(out, mode, iters, stream)          # warm-up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        flops = sum(g.fma_probe(out, mode, iters, stream) for _ in range(reps))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res[key] = flops / (e0.elapsed_time(e1) / 1000.0) / 1e12
+    return res
+
+
 def run_op(args) -> int:
     """One building block of the library, timed with CUDA events (see --op in the module doc)."""
     import numpy as np
@@ -405,6 +425,11 @@ def run_op(args) -> int:
     import paper_2106_00449_gb300 as g
     from synthetic import workloads as WL
 
+    if args.op == "fma_peak":
+        n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+        r = fma_probe_measure(g, torch, torch.cuda.current_stream(), n_sm, iters=args.reps * 1024)
+        print(json.dumps({"op": "fma_peak", **r}), flush=True)
+        return 0
     wl = WL.BY_NAME[args.workload]()
     if args.bodies:
         wl = wl.first_bodies(args.bodies)
@@ -574,6 +599,11 @@ def main(argv=None) -> int:
     avg_s = prof["rpy32_ms"] / max(prof["rpy32_launches"], 1) / 1000.0
     achieved_tf = FLOPS_PER_PAIR * prof["pairs_per_product"] / avg_s / 1e12 if avg_s > 0 else None
     kind = int(prof.get("pair_kernel", 1)) or 1
+    probe = fma_probe_measure(g, torch, stream, n_sm)
+    if probe and achieved_tf:
+        probe["pair_kernel_frac_of_packed"] = achieved_tf / probe["packed_tflops"]
+        probe["packed_frac_of_peak"] = probe["packed_tflops"] / peak_tf
+    roof_probe = {"fma_probe": probe} if probe else {}
     roof = {"bound": "alu", "kernel": PAIR_KERNELS[kind][4], "achieved": achieved_tf,
             "peak": peak_tf, "unit": "TFLOP/s", "frac": (achieved_tf / peak_tf) if achieved_tf else None,
             "traffic": captured_traffic(kind) if args.workload == "c3_65k" else None,   # captured at 65,520 blobs
@@ -596,6 +626,7 @@ def main(argv=None) -> int:
                            "symmetric kernel evaluates each unordered pair once for both blobs "
                            "(unique_pairs_per_launch), so it executes about 51/66 of those flops"),
             "unique_pairs_per_launch": prof.get("unique_pairs_per_product")}
+    roof.update(roof_probe)
     if clocks.get("sm_mhz") and achieved_tf:
         roof["frac_at_sampled_clock"] = achieved_tf / (n_sm * FP32_LANES_PER_SM * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
     line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,

@@ -399,6 +399,17 @@ typedef struct {
                                            symmetric one (chosen by the autotuner)        */
 } gdc_profile_info;
 
+/* FP32 FMA throughput probe (the measured denominator of the pair kernels' FP32 roofline):
+ * launches n_blocks blocks of 256 threads on `stream` (a cudaStream_t, NULL = default); each
+ * thread runs 8 independent chains of FP32 pairs, x <- x a + b, for `iters` iterations, as
+ * scalar FMAs (mode 0), packed fma.rn.f32x2 (mode 1, two FMAs per instruction, as the pair
+ * kernels use) or half and half (mode 2), and writes one float to out[block * 256 + thread]
+ * (device, n_blocks * 256 floats, caller-owned).  The three modes compute the same values.
+ * Work per launch: n_blocks * 256 * iters * 32 flops; the caller times it.
+ * GDC_ERR_INVALID_ARG for another mode, n_blocks < 1, iters < 1 or out == NULL;
+ * GDC_ERR_CUDA if the launch fails.  Asynchronous; needs no context. */
+gdc_status gdc_fma_probe(int mode, int n_blocks, int iters, float* out, void* stream);
+
 /* Reset the counters; enable != 0 also brackets every pair-kernel launch with
  * CUDA events recorded on the context's stream (events are created once). */
 gdc_status gdc_profile(gdc_ctx* ctx, int enable);

@@ -42,7 +42,7 @@ EXPORTS = [
     "gdc_brownian_slip", "gdc_lsq_velocity", "gdc_forces", "gdc_draw_normals", "gdc_saddle_offsets",
     "gdc_profile", "gdc_profile_read", "gdc_rpy_apply_noalloc", "gdc_debug_wait_polls",
     "gdc_fcm_workspace_bytes", "gdc_fcm_init", "gdc_fcm_apply", "gdc_fcm_brownian", "gdc_fcm_average",
-    "gdc_fcm_last_error", "gdc_fcm_launches", "gdc_fcm_destroy",
+    "gdc_fcm_last_error", "gdc_fcm_launches", "gdc_fcm_destroy", "gdc_fma_probe",
 ]
 
 NOALLOC_MAX_BLOBS = 16384   # GDC_NOALLOC_MAX_BLOBS of include/gdc.h
@@ -161,6 +161,7 @@ def load_library() -> ctypes.CDLL:
     lib.gdc_init.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(_Params), ctypes.c_int, ip, dp, ctypes.c_int, llp, ip,
                              dp, dp, vp, ctypes.c_size_t, vp]
     lib.gdc_destroy.restype = None
+    lib.gdc_fma_probe.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp]
     lib.gdc_destroy.argtypes = [vp]
     lib.gdc_last_error.restype = cp
     lib.gdc_last_error.argtypes = [vp]
@@ -525,6 +526,24 @@ def rpy_apply_noalloc(r, lam, a: float = 1.0, eta: float = 1.0, out=None, stream
     if st != 0:
         raise GdcError(st, lib.gdc_last_error(None).decode())
     return out
+
+
+def fma_probe(out, mode: int = 1, iters: int = 2048, stream=None) -> float:
+    """Launch the FP32 FMA throughput probe (gdc_fma_probe) over out.numel() // 256 blocks of
+    256 threads on `stream` (a torch.cuda.Stream or None for the current one): mode 0 scalar,
+    1 packed f32x2, 2 half and half.  Returns the flops the launch performs.  out: a float32
+    CUDA tensor the kernel writes."""
+    import torch
+    if out.dtype != torch.float32 or not out.is_cuda or out.numel() < 256:
+        raise ValueError("out must be a float32 CUDA tensor of at least 256 elements")
+    blocks = out.numel() // 256
+    st = (stream or torch.cuda.current_stream(out.device)).cuda_stream
+    with torch.cuda.device(out.device):
+        rc = load_library().gdc_fma_probe(int(mode), blocks, int(iters), ctypes.c_void_p(out.data_ptr()),
+                                          ctypes.c_void_p(st))
+    if rc != 0:
+        raise RuntimeError(f"gdc_fma_probe failed with status {rc}")
+    return float(blocks) * 256 * iters * 32
 
 
 def debug_wait_polls(polls: int) -> None:

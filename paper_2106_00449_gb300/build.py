@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgdc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "geometry.cu", "rpy.cu", "sym.cu", "body.cu", "krylov.cu", "cells.cu", "fcm.cu", "wall.cu", "dfsym.cu"]
+SOURCES = ["api.cu", "geometry.cu", "rpy.cu", "sym.cu", "body.cu", "krylov.cu", "cells.cu", "fcm.cu", "wall.cu", "dfsym.cu", "probe.cu"]
 
 
 def nvcc() -> str:

@@ -46,6 +46,24 @@ def test_rpy_sampled_rows_65k(lib, wl65, ctx65, prec):
     assert err < {0: 1e-12, 1: 1e-5, 2: 1e-11}[prec], err
 
 
+def test_rpy_sampled_rows_327k(lib):
+    """The 327,680-blob rod suspension (640 tiles of 512): the symmetric FP32 kernel and the
+    symmetric double-float kernel, whose work items widen to 10 source tiles beyond 128
+    tiles per suspension, on sampled rows."""
+    wl = WL.c5()
+    ctx = lib.context_from_workload(wl, precision=lib.FP32_MIXED, autotune=0, pair_kernel=2)
+    assert ctx.profile_read()["df_kernel"] == 4
+    rng = np.random.default_rng(23)
+    lam = rng.standard_normal(3 * wl.n_blobs)
+    r = _host(ctx.blob_positions()).reshape(-1, 3)
+    rows = np.concatenate([[0, 1, wl.n_blobs - 1], rng.choice(wl.n_blobs, 61, replace=False)])
+    ref = matfree.rpy_rows(r, lam.reshape(-1, 3), rows, 1.0, 1.0)
+    for prec, tol in ((1, 1e-5), (2, 1e-11)):
+        u = _host(ctx.rpy_apply(lam, prec)).reshape(-1, 3)
+        err = np.abs(u[rows] - ref).max() / np.abs(ref).max()
+        assert err < tol, (prec, err)
+
+
 def test_mobility_solve_65k(lib, wl65, ctx65):
     rng = np.random.default_rng(22)
     FT = np.zeros(6 * wl65.n_bodies)
