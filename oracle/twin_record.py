@@ -6,7 +6,10 @@ core once and prints one JSON line: the step's wall time, its RPY product count 
 time of one product measured separately, so that a bounded sample of products can later be
 converted into a step rate.
 
-    python -m oracle.twin_record [--workload c3_65k] [--seed 0]
+    python -m oracle.twin_record [--workload c3_65k] [--seed 0] [--products-only N]
+
+With --products-only N it times N full-size RPY products and no step (for workloads whose
+step takes hours on the host, such as the 327,680-blob c5).
 """
 from __future__ import annotations
 
@@ -30,6 +33,7 @@ def main(argv=None) -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="c3_65k")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--products-only", type=int, default=0)
     args = ap.parse_args(argv)
     wl = WL.BY_NAME[args.workload](seed=args.seed)
     lay = G.Layout(wl.templates, wl.body_tmpl)
@@ -37,6 +41,17 @@ def main(argv=None) -> int:
     W = philox.normals(1000, 0, 0, 0, 3 * lay.n_blobs)
     Wt = philox.normals(1000, 0, 0, 1, 6 * lay.n_bodies)
     r = G.blob_positions(lay, wl.Y, wl.q)
+    if args.products_only > 0:
+        ts = []
+        for _ in range(args.products_only):
+            t0 = time.perf_counter()
+            twin.rpy_product(r, W, p.a, p.eta)
+            ts.append(time.perf_counter() - t0)
+        t = sum(ts) / len(ts)
+        print(json.dumps({"workload": wl.name, "n_blobs": lay.n_blobs, "threads": twin.threads(),
+                          "products": len(ts), "product_seconds": t,
+                          "pair_evals_per_s": float(lay.n_blobs) ** 2 / t}), flush=True)
+        return 0
     t0 = time.perf_counter()
     twin.rpy_product(r, W, p.a, p.eta)
     t_prod = time.perf_counter() - t0
