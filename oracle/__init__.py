@@ -4,7 +4,7 @@ TEST INFRASTRUCTURE ONLY.  This package is a plain, slow, dense restatement
 of Westwood, Delmotte & Keaveny, "A generalised drift-correcting time
 integration scheme for Brownian suspensions of rigid particles with
 arbitrary shape" (arXiv 2106.00449), written in NumPy FP64 so that a reader
-can check it against the paper by eye.  It exists to judge the CUDA library
+can check it against the paper by eye.  It exists to check the CUDA library
 and is imported only by the tests, by ``__graft_entry__.smoke()`` and by the
 benchmark's CPU-baseline leg.  The library never imports, links or executes
 anything from here, and this package imports nothing from the library.
