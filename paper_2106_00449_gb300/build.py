@@ -23,8 +23,10 @@ def nvcc() -> str:
 
 
 # the pair kernels flush FP32 denormals (their operands are never denormal), which lets
-# rsqrtf map to the bare reciprocal-square-root unit operation
-PER_FILE = {"rpy.cu": ["-ftz=true"], "sym.cu": ["-ftz=true"]}
+# rsqrtf map to the bare reciprocal-square-root unit operation; so do the FCM kernels (their
+# Gaussians are 2^x with -21 < x <= 0 and their grid values are far from the denormal range),
+# where it lets exp2f map to the bare exponential unit operation
+PER_FILE = {"rpy.cu": ["-ftz=true"], "sym.cu": ["-ftz=true"], "fcm.cu": ["-ftz=true"]}
 
 
 def _compile(src: str, extra) -> str:

@@ -48,6 +48,8 @@ struct gdc_fcm {
     int* start = nullptr;
     int* fill = nullptr;
     int* list = nullptr;
+    float4* poff = nullptr;   // per list entry: the blob's offset from its cell's corner (FP32)
+    float4* plam = nullptr;   // per list entry: its lambda (FP32)
     int* scan = nullptr;
     bool have_field = false;
     unsigned long long n_launch = 0;
@@ -99,6 +101,8 @@ static size_t fcm_carve(gdc_fcm* f, void* base) {
     f->start = w.take<int>(nc3);
     f->fill = w.take<int>(nc3);
     f->list = w.take<int>(f->p.max_blobs);
+    f->poff = w.take<float4>(f->p.max_blobs);
+    f->plam = w.take<float4>(f->p.max_blobs);
     f->scan = w.take<int>(scan_scratch(nc3));
     return w.off + 256;
 }
@@ -174,6 +178,22 @@ __global__ void k_fcm_scatter(int n, const int* __restrict__ cell_of, const int*
 
 // ---- spreading (gather) -----------------------------------------------------------------
 
+// Per entry e of the cell-sorted blob list: the blob's offset from the corner of its own cell
+// (formed in FP64, rounded to FP32: a magnitude below the cell width) and its lambda in FP32,
+// so that spreading stages blobs without FP64 arithmetic.
+__global__ void k_fcm_stage_blobs(int n, double w, int nc, const int* __restrict__ list,
+                                  const int* __restrict__ cell_of, const double4_32a* __restrict__ pw,
+                                  const double* __restrict__ lam, float4* __restrict__ poff,
+                                  float4* __restrict__ plam) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const int j = list[e], id = cell_of[j];
+    const int cx = id % nc, cy = (id / nc) % nc, cz = id / (nc * nc);
+    const double4_32a p = pw[j];
+    poff[e] = make_float4((float)(p.x - cx * w), (float)(p.y - cy * w), (float)(p.z - cz * w), 0.f);
+    plam[e] = make_float4((float)lam[3LL * j], (float)lam[3LL * j + 1], (float)lam[3LL * j + 2], 0.f);
+}
+
 constexpr int SP_CHUNK = 512;    // blobs staged in shared memory per round
 
 // f(x_g) = sum of lambda_j Delta_j(x_g).  One block per binning cell (cells at least R_t wide)
@@ -192,7 +212,8 @@ __global__ void __launch_bounds__(128) k_fcm_spread(int N, double h, double L, d
                                                     const double4_32a* __restrict__ pw,
                                                     const int* __restrict__ cnt, const int* __restrict__ start,
                                                     const int* __restrict__ list, const double* __restrict__ lam,
-                                                    float R2, float inv2s2, float norm, float2* __restrict__ f,
+                                                    const float4* __restrict__ poff, const float4* __restrict__ plam,
+                                                    float R2, float l2s, float norm, float2* __restrict__ f,
                                                     long long NG) {
     __shared__ float4 sp[SP_CHUNK];
     __shared__ float4 sl[SP_CHUNK];
@@ -230,6 +251,7 @@ __global__ void __launch_bounds__(128) k_fcm_spread(int N, double h, double L, d
     const int total = c_off[ncell];
     const float Lf = (float)L, hL = 0.5f * Lf, hf = (float)h;
     const double mid = 0.5 * w;
+    const float wf = (float)w;
     {
         const int p0 = blockIdx.y * PT * 128;   // this block's chunk of the cell's grid points
         float gx[PT], gy[PT], gz[PT], ax[PT], ay[PT], az[PT];
@@ -255,16 +277,25 @@ __global__ void __launch_bounds__(128) k_fcm_spread(int N, double h, double L, d
             __syncthreads();
             for (int t = threadIdx.x; t < take; t += blockDim.x) {
                 const int e = s0 + t;
-                int k = 0;
-                while (c_off[k + 1] <= e) ++k;
-                const int j = list[c_start[k] + (e - c_off[k])];
-                const double4_32a p = pw[j];
-                double rx = p.x - corner[0], ry = p.y - corner[1], rz = p.z - corner[2];
-                rx -= L * rint((rx - mid) * invL);
-                ry -= L * rint((ry - mid) * invL);
-                rz -= L * rint((rz - mid) * invL);
-                sp[t] = make_float4((float)rx, (float)ry, (float)rz, 0.f);
-                sl[t] = make_float4((float)lam[3LL * j], (float)lam[3LL * j + 1], (float)lam[3LL * j + 2], 0.f);
+                int k = 0;   // the neighbour cell of entry e: c_off[k] <= e < c_off[k + 1]
+                for (int step = 16; step > 0; step >>= 1)
+                    if (k + step <= ncell - 1 && c_off[k + step] <= e) k += step;
+                const int pos = c_start[k] + (e - c_off[k]);
+                if (WRAP) {   // few cells per side: the image nearest the cell's centre, in FP64
+                    const int j = list[pos];
+                    const double4_32a p = pw[j];
+                    double rx = p.x - corner[0], ry = p.y - corner[1], rz = p.z - corner[2];
+                    rx -= L * rint((rx - mid) * invL);
+                    ry -= L * rint((ry - mid) * invL);
+                    rz -= L * rint((rz - mid) * invL);
+                    sp[t] = make_float4((float)rx, (float)ry, (float)rz, 0.f);
+                    sl[t] = make_float4((float)lam[3LL * j], (float)lam[3LL * j + 1], (float)lam[3LL * j + 2], 0.f);
+                } else {      // the neighbour cell's corner is o w from this cell's (o in {-1, 0, 1}^3)
+                    const float4 q = poff[pos];
+                    const float ox = (float)(k % 3 - 1), oy = (float)((k / 3) % 3 - 1), oz = (float)(k / 9 - 1);
+                    sp[t] = make_float4(fmaf(ox, wf, q.x), fmaf(oy, wf, q.y), fmaf(oz, wf, q.z), 0.f);
+                    sl[t] = plam[pos];
+                }
             }
             __syncthreads();
             for (int j = 0; j < take; ++j) {
@@ -279,7 +310,7 @@ __global__ void __launch_bounds__(128) k_fcm_spread(int N, double h, double L, d
                     }
                     const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                     if (d2 <= R2) {
-                        const float wt = norm * expf(-d2 * inv2s2);
+                        const float wt = norm * exp2f(-d2 * l2s);   // exp(-d2 / 2s^2)
                         ax[q] = fmaf(lj.x, wt, ax[q]);
                         ay[q] = fmaf(lj.y, wt, ay[q]);
                         az[q] = fmaf(lj.z, wt, az[q]);
@@ -575,7 +606,7 @@ __global__ void k_fcm_stress(long long NG, unsigned long long seed, unsigned own
 // ---- averaging ------------------------------------------------------------------------------
 
 __global__ void __launch_bounds__(128) k_fcm_average(int n, const double* __restrict__ r, double L, int N, double h,
-                                                     double R_t, float inv2s2, double wscale,
+                                                     double R_t, float l2s, double wscale,
                                                      const float4* __restrict__ u, double* __restrict__ v) {
     const int i = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
@@ -608,7 +639,7 @@ __global__ void __launch_bounds__(128) k_fcm_average(int n, const double* __rest
     const int ox = lane % cn[0], oyr = lane / cn[0];
     const bool on = oyr < rows;
     const float dx = d0x + ox * hf;
-    const float wx = expf(-dx * dx * inv2s2);
+    const float wx = exp2f(-dx * dx * l2s);   // exp(-dx^2 / 2s^2)
     const int ix = (lo[0] + ox) & mask;
     // the planes' sums added with compensation (Kahan) in FP32: as accurate as FP64 for a
     // box's at most 31 planes, without an FP32-to-FP64 conversion and FP64 add per plane
@@ -618,7 +649,7 @@ __global__ void __launch_bounds__(128) k_fcm_average(int n, const double* __rest
     const float frows = (float)rows;
     for (int oz = 0; oz < cn[2]; ++oz, foz += 1.f) {
         const float dz = fmaf(foz, hf, d0z);
-        const float wz = expf(-dz * dz * inv2s2) * wx;
+        const float wz = exp2f(-dz * dz * l2s) * wx;
         const float dxz = fmaf(dx, dx, dz * dz);
         const long long zoff = (long long)((lo[2] + oz) & mask) * N * N + ix;
         float a0 = 0.f, a1 = 0.f, a2 = 0.f;
@@ -627,7 +658,7 @@ __global__ void __launch_bounds__(128) k_fcm_average(int n, const double* __rest
         for (int oy = oyr; oy < cn[1]; oy += rows, foy += frows) {
             const float dy = fmaf(foy, hf, d0y);
             if (on && fmaf(dy, dy, dxz) <= R2) {
-                const float wgt = expf(-dy * dy * inv2s2) * wz;
+                const float wgt = exp2f(-dy * dy * l2s) * wz;
                 const float4 q = __ldg(u + zoff + ((lo[1] + oy) & mask) * N);   // within a plane: int
                 a0 = fmaf(q.x, wgt, a0);
                 a1 = fmaf(q.y, wgt, a1);
@@ -643,6 +674,7 @@ __global__ void __launch_bounds__(128) k_fcm_average(int n, const double* __rest
         }
     }
     double tot[3];
+#pragma unroll
     for (int c = 0; c < 3; ++c) {
         tot[c] = (double)acc[c] - (double)cmp[c];
         for (int o = 16; o > 0; o >>= 1) tot[c] += __shfl_down_sync(0xffffffffu, tot[c], o);
@@ -709,7 +741,8 @@ static void fcm_average_launch(gdc_fcm* f, int n, const double* r, int which, do
     const double s2 = f->p.sigma * f->p.sigma;
     const double norm = std::pow(2.0 * 3.141592653589793 * s2, -1.5);
     ++f->n_launch, k_fcm_average<<<ceil_div(32LL * n, 128), 128, 0, f->stream>>>(
-        n, r, f->p.L, f->N, f->h, f->p.R_t, (float)(0.5 / s2), norm * f->h * f->h * f->h, f->packed + which * f->NG, v);
+        n, r, f->p.L, f->N, f->h, f->p.R_t, (float)(0.5 / s2 * 1.4426950408889634), norm * f->h * f->h * f->h,
+        f->packed + which * f->NG, v);
 }
 
 // The grid of a gDC context with the FCM mobility (defaults: sigma = a/sqrt(pi), R_t = 3a).
@@ -788,20 +821,36 @@ gdc_status gdc_fcm_apply(gdc_fcm* f, int n, const double* r, const double* lambd
     scan_exclusive(f->stream, &f->n_launch, (int)nc3, f->cnt, f->start, f->scan);
     ++f->n_launch, k_fcm_scatter<<<ceil_div(n, 256), 256, 0, f->stream>>>(n, f->cell_of, f->start, f->fill, f->list);
     ++f->n_launch, k_cell_sort<<<ceil_div(nc3, 256), 256, 0, f->stream>>>((int)nc3, f->cnt, f->start, f->list);
+    ++f->n_launch, k_fcm_stage_blobs<<<ceil_div(n, 256), 256, 0, f->stream>>>(
+        n, f->p.L / f->nc, f->nc, f->list, f->cell_of, f->pw, lambda, f->poff, f->plam);
     const double s2 = f->p.sigma * f->p.sigma;
     {
-        // 4 grid points per thread, 512 per block; the largest binning cell has side^3 points
+        // 4 grid points per thread, 512 per block (2 and 256 when a cell has at most 256
+        // points, so that small cells leave fewer idle slots); the largest cell has side^3 points
         const long long side = (f->N + f->nc - 1) / f->nc;
-        const unsigned chunks = (unsigned)((side * side * side + 511) / 512);
-        const float R2 = (float)(f->p.R_t * f->p.R_t), i2 = (float)(0.5 / s2);
+        const int pt = side * side * side <= 256 ? 2 : 4;
+        const unsigned chunks = (unsigned)((side * side * side + 128 * pt - 1) / (128 * pt));
+        // the Gaussians as powers of 2: exp(-d^2 / 2s^2) = 2^(-d^2 l2s), l2s = log2(e) / (2 s^2)
+        const float R2 = (float)(f->p.R_t * f->p.R_t), i2 = (float)(0.5 / s2 * 1.4426950408889634);
         const float nrm = (float)std::pow(2.0 * 3.141592653589793 * s2, -1.5);
         ++f->n_launch;
-        if (f->nc >= 4)
-            k_fcm_spread<4, false><<<dim3((unsigned)nc3, chunks), 128, 0, f->stream>>>(
-                f->N, f->h, f->p.L, 1.0 / f->p.L, f->p.L / f->nc, f->nc, f->pw, f->cnt, f->start, f->list, lambda, R2, i2, nrm, f->grid, f->NG);
-        else
-            k_fcm_spread<4, true><<<dim3((unsigned)nc3, chunks), 128, 0, f->stream>>>(
-                f->N, f->h, f->p.L, 1.0 / f->p.L, f->p.L / f->nc, f->nc, f->pw, f->cnt, f->start, f->list, lambda, R2, i2, nrm, f->grid, f->NG);
+#define GDC_SPREAD(PT_, WRAP_)                                                                                      \
+    k_fcm_spread<PT_, WRAP_><<<dim3((unsigned)nc3, chunks), 128, 0, f->stream>>>(                                  \
+        f->N, f->h, f->p.L, 1.0 / f->p.L, f->p.L / f->nc, f->nc, f->pw, f->cnt, f->start, f->list, lambda, f->poff, \
+        f->plam, R2, i2, nrm, f->grid, f->NG)
+        const bool wrap = f->nc < 4;
+        if (pt == 2) {
+            if (wrap)
+                GDC_SPREAD(2, true);
+            else
+                GDC_SPREAD(2, false);
+        } else {
+            if (wrap)
+                GDC_SPREAD(4, true);
+            else
+                GDC_SPREAD(4, false);
+        }
+#undef GDC_SPREAD
     }
     // grids 0-1: FFT(f_x + i f_y), FFT(f_z); grids 2-3: the velocity's (u_x + i u_y, u_z)
     fft3(f, 0, 2, false);
