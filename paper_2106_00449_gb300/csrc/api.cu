@@ -220,6 +220,7 @@ static size_t carve(gdc_ctx* c, void* base) {
     c->tmpl_Minv = w.take<double>(c->h_minv_off[T]);
     c->tmpl_M = w.take<double>(c->h_minv_off[T]);
     c->tmpl_M32 = w.take<float>(c->h_minv_off[T]);
+    c->tmpl_Minv32 = w.take<float>(c->h_minv_off[T]);
     c->tmpl_G = w.take<double>(18 * nt);
     c->tmpl_N = w.take<double>(36 * T);
     c->tmpl_KtKp = w.take<double>(36 * T);

@@ -127,10 +127,16 @@ void launch_lsq(gdc_ctx* c, const double* vbrev, double* calV) {
 // LAB = false: the template's FP64 blocks in the body frame, applied to rotated vectors.
 // LAB = true (blobs above a wall): each body's own blocks in the lab frame (set up by
 // k_wall_blocks at every configuration), blob offsets d_i = r_i - Y_p, no rotation.
-template <bool LAB>
+// F32: the body's M^-1 product in FP32 (the template block rounded to FP32, four interleaved
+// FP32 partial sums per row added in FP64; the rest of the block solve stays FP64), for the
+// inner cycles of the FP32-mixed mobility solve, whose operator already carries FP32 rounding:
+// the preconditioner only has to be a fixed approximation, and the FP64 product there was
+// FP64-pipe bound (1/64 of the FP32 rate).
+template <bool LAB, bool F32 = false>
 __global__ void __launch_bounds__(128) k_precond(const long long* __restrict__ body_blob_off, const int* __restrict__ body_tmpl,
                                                  const int* __restrict__ tmpl_n, const int* __restrict__ tmpl_off,
                                                  const long long* __restrict__ minv_off, const double* __restrict__ Minv,
+                                                 const float* __restrict__ Minv32,
                                                  const double* __restrict__ Gt, const double* __restrict__ Nt,
                                                  const double* __restrict__ tmpl_xyz, const int* __restrict__ blob_gm,
                                                  const int* __restrict__ body_gm, const double* __restrict__ Rb,
@@ -146,6 +152,7 @@ __global__ void __launch_bounds__(128) k_precond(const long long* __restrict__ b
     double* av = sh + n3;      // n3
     double* misc = sh + 2 * n3;  // 32
     double* bl = misc + 32;      // LAB: blob offsets d (n3)
+    float* rho32 = reinterpret_cast<float*>(misc + 32);   // F32 (never with LAB): rho in FP32 (n3)
     const double ident[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
     const double* R = LAB ? ident : Rb + 9 * p;
     const long long i0 = body_blob_off[p];
@@ -158,6 +165,11 @@ __global__ void __launch_bounds__(128) k_precond(const long long* __restrict__ b
         rho[3 * b] = w[0];
         rho[3 * b + 1] = w[1];
         rho[3 * b + 2] = w[2];
+        if (F32) {
+            rho32[3 * b] = (float)w[0];
+            rho32[3 * b + 1] = (float)w[1];
+            rho32[3 * b + 2] = (float)w[2];
+        }
     }
     if (threadIdx.x == 0) {
         const long long o = body_gm[p];
@@ -173,11 +185,27 @@ __global__ void __launch_bounds__(128) k_precond(const long long* __restrict__ b
         misc[5] = w[2];
     }
     __syncthreads();
-    const double* Mi = Minv + (LAB ? blk_off[p] : minv_off[t]);
-    for (int row = threadIdx.x; row < n3; row += blockDim.x) {
-        double acc = 0.0;
-        for (int k = 0; k < n3; ++k) acc = fma(Mi[(long long)k * n3 + row], rho[k], acc);  // symmetric
-        av[row] = acc;
+    if (F32) {
+        const float* Mi = Minv32 + minv_off[t];
+        for (int row = threadIdx.x; row < n3; row += blockDim.x) {
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+            int k = 0;
+            for (; k + 3 < n3; k += 4) {   // symmetric: column-major reads are coalesced over rows
+                a0 = fmaf(Mi[(long long)k * n3 + row], rho32[k], a0);
+                a1 = fmaf(Mi[(long long)(k + 1) * n3 + row], rho32[k + 1], a1);
+                a2 = fmaf(Mi[(long long)(k + 2) * n3 + row], rho32[k + 2], a2);
+                a3 = fmaf(Mi[(long long)(k + 3) * n3 + row], rho32[k + 3], a3);
+            }
+            for (; k < n3; ++k) a0 = fmaf(Mi[(long long)k * n3 + row], rho32[k], a0);
+            av[row] = ((double)a0 + (double)a1) + ((double)a2 + (double)a3);
+        }
+    } else {
+        const double* Mi = Minv + (LAB ? blk_off[p] : minv_off[t]);
+        for (int row = threadIdx.x; row < n3; row += blockDim.x) {
+            double acc = 0.0;
+            for (int k = 0; k < n3; ++k) acc = fma(Mi[(long long)k * n3 + row], rho[k], acc);  // symmetric
+            av[row] = acc;
+        }
     }
     __syncthreads();
     if (threadIdx.x < 32) {
@@ -348,16 +376,20 @@ void launch_intra_body(gdc_ctx* c, const double* x, double* y, int gm) {
                                                                  c->tmpl_M, c->blob_gm, c->Rb, x, y, gm);
 }
 
-void launch_precond(gdc_ctx* c, const double* r, double* z) {
+void launch_precond(gdc_ctx* c, const double* r, double* z, bool fp32) {
     const size_t smem = (size_t)(3 * 3 * c->max_body_blobs + 32) * sizeof(double);
     if (c->p.wall)
         ++c->n_launch, k_precond<true><<<c->NB, 128, smem, c->stream>>>(
-            c->body_blob_off, c->body_tmpl, c->tmpl_n, c->tmpl_off, c->minv_off, c->blk_Minv, c->blk_G, c->blk_N,
+            c->body_blob_off, c->body_tmpl, c->tmpl_n, c->tmpl_off, c->minv_off, c->blk_Minv, nullptr, c->blk_G, c->blk_N,
             c->tmpl_xyz, c->blob_gm, c->body_gm, c->Rb, r, z, c->blk_off, c->r, c->Yc);
+    else if (fp32)
+        ++c->n_launch, k_precond<false, true><<<c->NB, 128, smem, c->stream>>>(
+            c->body_blob_off, c->body_tmpl, c->tmpl_n, c->tmpl_off, c->minv_off, c->tmpl_Minv, c->tmpl_Minv32, c->tmpl_G,
+            c->tmpl_N, c->tmpl_xyz, c->blob_gm, c->body_gm, c->Rb, r, z, nullptr, nullptr, nullptr);
     else
         ++c->n_launch, k_precond<false><<<c->NB, 128, smem, c->stream>>>(
-            c->body_blob_off, c->body_tmpl, c->tmpl_n, c->tmpl_off, c->minv_off, c->tmpl_Minv, c->tmpl_G, c->tmpl_N,
-            c->tmpl_xyz, c->blob_gm, c->body_gm, c->Rb, r, z, nullptr, nullptr, nullptr);
+            c->body_blob_off, c->body_tmpl, c->tmpl_n, c->tmpl_off, c->minv_off, c->tmpl_Minv, nullptr, c->tmpl_G,
+            c->tmpl_N, c->tmpl_xyz, c->blob_gm, c->body_gm, c->Rb, r, z, nullptr, nullptr, nullptr);
 }
 
 // ---- factors of the body blocks: block-preconditioned Lanczos (Sec. 4.1, Chow & Saad) ----
@@ -664,6 +696,7 @@ void launch_template_setup(gdc_ctx* c, const double* Mext) {
     const int gr = (int)std::min<long long>(ceil_div(nm, 256), 1024);
     ++c->n_launch, k_round_f32<<<gr, 256, 0, c->stream>>>(nm, c->tmpl_M, c->tmpl_M32);
     ++c->n_launch, k_round_f32<<<gr, 256, 0, c->stream>>>(nm, c->tmpl_X, c->tmpl_X32);
+    ++c->n_launch, k_round_f32<<<gr, 256, 0, c->stream>>>(nm, c->tmpl_Minv, c->tmpl_Minv32);
     ++c->n_launch, k_round_f32<<<gr, 256, 0, c->stream>>>(nm, c->tmpl_XT, c->tmpl_XT32);
 }
 

@@ -130,6 +130,7 @@ struct gdc_ctx {
     double *tmpl_xyz = 0, *tmpl_L = 0;
     double *tmpl_Minv = 0, *tmpl_G = 0, *tmpl_N = 0, *tmpl_KtKp = 0, *tmpl_work = 0, *tmpl_M = 0;
     float* tmpl_M32 = 0;          // tmpl_M rounded to FP32 (intra-body block of the FP32 products)
+    float* tmpl_Minv32 = 0;       // tmpl_Minv rounded to FP32 (preconditioner of the FP32 inner cycles)
     // factors of the template blocks M_t = L_t L_t^T for the block-preconditioned Lanczos
     // operator, each stored as F with (F-product)_i = sum_k F[k n3 + i] x_k (reads along rows):
     // tmpl_LT = L_t^T (products with L_t), tmpl_X = L_t^-1 (with L_t^-T), tmpl_XT = L_t^-T (with L_t^-1)
@@ -384,7 +385,7 @@ const char* noalloc_last_error();
 // body.cu
 void launch_body_KT(gdc_ctx* c, const double* x, int x_gm, double* y, int y_gm, double scale);
 void launch_lsq(gdc_ctx* c, const double* vbrev, double* calV);
-void launch_precond(gdc_ctx* c, const double* r, double* z);
+void launch_precond(gdc_ctx* c, const double* r, double* z, bool fp32 = false);
 void launch_intra_body(gdc_ctx* c, const double* x, double* y, int gm);
 void launch_intra_body32(gdc_ctx* c, const double* x, double* y, int gm);
 void launch_template_setup(gdc_ctx* c, const double* Mext = nullptr);   // Mext: given template blocks

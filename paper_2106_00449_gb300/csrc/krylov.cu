@@ -441,7 +441,7 @@ gdc_status gmres_solve(gdc_ctx* c, const double* b, double* x, gdc_solve_info* i
         int j = 0;
         for (; j < m; ++j) {
             double* Vj = c->gm_V + (long long)j * n;
-            launch_precond(c, Vj, c->gm_z);
+            launch_precond(c, Vj, c->gm_z, prec == GDC_FP32_MIXED);
             c->mv_active = c->gm_active;   // suspensions that have converged need no product
             saddle_op(c, prec, c->gm_z, c->gm_w);
             c->mv_active = nullptr;
@@ -472,7 +472,7 @@ gdc_status gmres_solve(gdc_ctx* c, const double* b, double* x, gdc_solve_info* i
         // x += P^-1 V y
         ++c->n_launch, k_gm_backsolve<<<ceil_div(c->S, 128), 128, 0, c->stream>>>(c->S, m, c->gm_H, c->gm_g, c->gm_j, c->gm_y, cols);
         ++c->n_launch, k_combine<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->gm_V, n, c->gm_j, c->gm_y, cols, nullptr, c->gm_w);
-        launch_precond(c, c->gm_w, c->gm_z);   // the correction e of this cycle
+        launch_precond(c, c->gm_w, c->gm_z, prec == GDC_FP32_MIXED);   // the correction e of this cycle
         ++c->n_launch, k_axpy_chunks<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, 1.0, c->gm_z, x);
         if (prec == GDC_FP32_MIXED && rmax <= GDC_RESID_UPDATE) {
             // r <- r - A e: the residual is already small, so A e is too, and the FP32 product's
@@ -1251,7 +1251,7 @@ void gmres_solve_graph(gdc_ctx* c, const double* b, double* x) {
         cap_while_begin(c, hi);
         const unsigned long long before_i = c->n_launch;
         {
-            launch_precond(c, c->gm_vcur, c->gm_z);
+            launch_precond(c, c->gm_vcur, c->gm_z, prec == GDC_FP32_MIXED);
             c->mv_active = c->gm_active;
             saddle_op(c, prec, c->gm_z, c->gm_w);
             c->mv_active = nullptr;
@@ -1274,7 +1274,7 @@ void gmres_solve_graph(gdc_ctx* c, const double* b, double* x) {
                                                                                   c->gm_y, cols);
         ++c->n_launch, k_combine<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->gm_V, n, c->gm_j, c->gm_y, cols,
                                                                      nullptr, c->gm_w);
-        launch_precond(c, c->gm_w, c->gm_z);   // the correction e of this cycle
+        launch_precond(c, c->gm_w, c->gm_z, prec == GDC_FP32_MIXED);   // the correction e of this cycle
         ++c->n_launch, k_axpy_chunks<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, 1.0, c->gm_z, x);
         // the residual: recomputed, r = b - A x (accurate product), or updated, r <- r - A e
         // (FP32 product of the small correction), as k_gm_check decided
