@@ -172,6 +172,30 @@ static const char* build_host_layout(gdc_ctx* c, const gdc_params* p, int n_temp
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
     c->device = dev;
     c->num_sms = sms;
+    // bodies per block of the factor products: as many as keep 8 blocks per SM busy (at most
+    // GDC_TB_MAX), fewer for large templates (40 KB of shared memory per block); below 4 per
+    // block the products keep one block per body (measured faster there: 2,520 bodies)
+    {
+        int B = 1;
+        while (B < GDC_TB_MAX && NB >= 2LL * B * 8 * sms) B *= 2;
+        c->tb_use = B >= 4;
+        std::vector<std::vector<int>> by_t(n_templates);
+        for (long long b = 0; b < NB; ++b) by_t[body_tmpl[b]].push_back((int)b);
+        c->h_tb_items.clear();
+        c->h_tb_bodies.clear();
+        c->tb_smem = 0;
+        for (int t = 0; t < n_templates; ++t) {
+            const int n3 = 3 * tmpl_nblobs[t];
+            const int bt = std::max(1, std::min(B, 2560 / n3));
+            for (size_t i = 0; i < by_t[t].size(); i += bt) {
+                const int cnt = (int)std::min<size_t>(bt, by_t[t].size() - i);
+                c->h_tb_items.push_back(make_int4(t, (int)c->h_tb_bodies.size() + (int)i, cnt, 0));
+                c->tb_smem = std::max(c->tb_smem, (size_t)cnt * n3 * 2 * sizeof(double));
+            }
+            c->h_tb_bodies.insert(c->h_tb_bodies.end(), by_t[t].begin(), by_t[t].end());
+        }
+        c->tb_n_items = (int)c->h_tb_items.size();
+    }
     plan_mv_capacity(c);
     setup_segments(c);
     c->h_blk_off.assign(NB + 1, 0);
@@ -208,6 +232,8 @@ static size_t carve(gdc_ctx* c, void* base) {
     c->body_blob_off = w.take<long long>(NB + 1);
     c->minv_off = w.take<long long>(T + 1);
     c->body_tmpl = w.take<int>(NB);
+    c->tb_items = w.take<int4>(NB);
+    c->tb_bodies = w.take<int>(NB);
     c->body_susp = w.take<int>(NB);
     c->blob_body = w.take<int>(NBL);
     c->blob_susp = w.take<int>(NBL);
@@ -386,6 +412,8 @@ static gdc_status upload_layout(gdc_ctx* c, const double* tmpl_xyz_centred) {
     chk(up(c, c->body_blob_off, c->h_body_blob_off.data(), NB + 1));
     chk(up(c, c->minv_off, c->h_minv_off.data(), T + 1));
     chk(up(c, c->body_tmpl, c->h_body_tmpl.data(), NB));
+    chk(up(c, c->tb_items, c->h_tb_items.data(), c->h_tb_items.size()));
+    chk(up(c, c->tb_bodies, c->h_tb_bodies.data(), c->h_tb_bodies.size()));
     chk(up(c, c->body_susp, c->h_body_susp.data(), NB));
     chk(up(c, c->blob_body, blob_body.data(), NBL));
     chk(up(c, c->blob_susp, blob_susp.data(), NBL));

@@ -470,13 +470,95 @@ __global__ void __launch_bounds__(128) k_body_tri(const long long* __restrict__ 
     }
 }
 
+// The same products for several bodies of one template per block (the bodies of item
+// (t, first, count) in `bodies`): each element of the template's factor, read once from L2,
+// serves all of them, where a block per body re-reads the factor body after body (at 36,121
+// bodies that is hundreds of MB per launch).  One accumulator per body and row.
+template <int MODE, typename T>
+__global__ void __launch_bounds__(128) k_body_tri_tb(const int4* __restrict__ items, const int* __restrict__ bodies,
+                                                     const long long* __restrict__ body_blob_off,
+                                                     const int* __restrict__ tmpl_n,
+                                                     const long long* __restrict__ minv_off, const T* __restrict__ F,
+                                                     const double* __restrict__ Rb, const double* __restrict__ x,
+                                                     const double* __restrict__ add, double* __restrict__ out) {
+    extern __shared__ double sh[];
+    const int4 it = items[blockIdx.x];
+    const int t = it.x, cnt = it.z;
+    const int n = tmpl_n[t], n3 = 3 * n;
+    double* res = sh;                                    // [cnt][n3]
+    T* in = reinterpret_cast<T*>(sh + (long long)cnt * n3);   // [cnt][n3]
+    for (int e = threadIdx.x; e < cnt * n; e += blockDim.x) {
+        const int u = e / n, b = e - u * n;
+        const int p = bodies[it.y + u];
+        const long long o = 3 * (body_blob_off[p] + b);
+        double v[3] = {x[o], x[o + 1], x[o + 2]};
+        if (MODE == TRI_LINV) {
+            double w[3];
+            rotT(Rb + 9 * p, v, w);
+            v[0] = w[0];
+            v[1] = w[1];
+            v[2] = w[2];
+        }
+        in[u * n3 + 3 * b] = (T)v[0];
+        in[u * n3 + 3 * b + 1] = (T)v[1];
+        in[u * n3 + 3 * b + 2] = (T)v[2];
+    }
+    __syncthreads();
+    const T* Ft = F + minv_off[t];
+    for (int i = threadIdx.x; i < n3; i += blockDim.x) {
+        const int k0 = MODE == TRI_LINV_T ? i : 0, k1 = MODE == TRI_LINV_T ? n3 : i + 1;
+        T a[GDC_TB_MAX];
+#pragma unroll
+        for (int u = 0; u < GDC_TB_MAX; ++u) a[u] = T(0);
+        for (int k = k0; k < k1; ++k) {
+            const T f = Ft[(long long)k * n3 + i];
+#pragma unroll
+            for (int u = 0; u < GDC_TB_MAX; ++u)
+                if (u < cnt) a[u] = fma(f, in[u * n3 + k], a[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < GDC_TB_MAX; ++u)
+            if (u < cnt) res[u * n3 + i] = (double)a[u];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < cnt * n; e += blockDim.x) {
+        const int u = e / n, b = e - u * n;
+        const int p = bodies[it.y + u];
+        double w[3] = {res[u * n3 + 3 * b], res[u * n3 + 3 * b + 1], res[u * n3 + 3 * b + 2]};
+        if (MODE != TRI_LINV) {
+            double v[3];
+            rot(Rb + 9 * p, w, v);
+            w[0] = v[0];
+            w[1] = v[1];
+            w[2] = v[2];
+        }
+        const long long o = 3 * (body_blob_off[p] + b);
+        if (add) {
+            w[0] += add[o];
+            w[1] += add[o + 1];
+            w[2] += add[o + 2];
+        }
+        out[o] = w[0];
+        out[o + 1] = w[1];
+        out[o + 2] = w[2];
+    }
+}
+
 void launch_body_tri(gdc_ctx* c, int mode, const double* x, const double* add, double* out, bool fp32) {
     const size_t smem = (size_t)(2 * 3 * c->max_body_blobs) * sizeof(double);
     const bool lab = c->p.wall != 0;
     const long long* off = lab ? c->blk_off : c->minv_off;
+    // lab-frame factors (above a wall) and fewer bodies: one block per body; many bodies:
+    // grouped by template
 #define GDC_TRI(MODE, LAB, T, F)                                                                                  \
-    k_body_tri<MODE, LAB, T><<<c->NB, 128, smem, c->stream>>>(c->body_blob_off, c->body_tmpl, c->tmpl_n, off, F, \
-                                                             c->Rb, x, add, out)
+    do {                                                                                                          \
+        if (LAB || !c->tb_use)                                                                                    \
+            k_body_tri<MODE, LAB, T><<<c->NB, 128, smem, c->stream>>>(c->body_blob_off, c->body_tmpl, c->tmpl_n,  \
+                                                                     off, F, c->Rb, x, add, out);                \
+        else                                                                                                      \
+            k_body_tri_tb<MODE, T><<<c->tb_n_items, 128, c->tb_smem, c->stream>>>(                               \
+                c->tb_items, c->tb_bodies, c->body_blob_off, c->tmpl_n, c->minv_off, F, c->Rb, x, add, out);     \
+    } while (0)
     ++c->n_launch;
     if (fp32 && !lab && mode == TRI_LINV_T)
         GDC_TRI(TRI_LINV_T, false, float, c->tmpl_X32);

@@ -29,6 +29,7 @@
 #define GDC_MAX_RESTART 100
 #define GDC_MAX_LANCZOS 128
 #define GDC_MAX_TMPL_BLOBS 340   // 3n <= 1020 rows of a template block
+#define GDC_TB_MAX 8             // bodies of one template per block in the factor products
 #define GDC_NEAR_CAP 32          // blobs closer than 2a listed per blob (beyond: a search of the suspension)
 #define GDC_NEAR_SRC 2048        // sources per block of the near-pair search
 #define GDC_SYM_TILE 512         // blobs per tile of the symmetric FP32 pair kernel
@@ -119,6 +120,15 @@ struct gdc_ctx {
     // host copies of the layout
     std::vector<long long> h_body_off, h_blob_off, h_gm_off, h_body_blob_off;
     std::vector<int> h_body_tmpl, h_tmpl_n, h_tmpl_off, h_body_susp;
+    // factor products of several bodies of one template per block (body.cu k_body_tri_tb):
+    // items (template, first entry in tb_bodies, count), bodies grouped by template
+    int4* tb_items = 0;
+    int* tb_bodies = 0;
+    int tb_n_items = 0;
+    bool tb_use = false;   // the grouped products replace one block per body
+    size_t tb_smem = 0;
+    std::vector<int4> h_tb_items;
+    std::vector<int> h_tb_bodies;
     std::vector<long long> h_minv_off;
     std::vector<double> h_tmpl_xyz, h_tmpl_L;
 

@@ -174,6 +174,28 @@ def test_brownian_slip_lanczos(lib, wl_mix, prec, precond):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
+def test_brownian_slip_many_bodies(lib, prec):
+    """About 6,300 bodies in 1,400 small suspensions, enough for the factor products of the
+    preconditioned Lanczos to group several bodies of one template per block: the roots of 40
+    sampled suspensions against the oracle's dense block-preconditioned root."""
+    wl = WL.batch_small(1400, seed=3, nmin=4, nmax=5)
+    assert wl.n_bodies >= 6000
+    tol = 1e-11 if prec == 0 else 1e-6
+    ctx = ctx_for(lib, wl, precision=prec, lanczos_tol=tol, lanczos_max_iter=128, kT=1.3, dt=0.02,
+                  lanczos_precond=1, autotune=0)
+    rng = np.random.default_rng(16)
+    W = rng.standard_normal(3 * wl.n_blobs)
+    vb = _host(ctx.brownian_slip(W)[0])
+    sl = blob_slices(wl)
+    for s in rng.choice(wl.n_susp, 40, replace=False):
+        lay, Y, q = susp_layout(wl, s)
+        r, M, K, B = dense_state(lay, Y, q)
+        a, b = sl[s]
+        ref = np.sqrt(2 * 1.3 / 0.02) * rigid.sqrtm_block(M, rigid.block_factor(lay, q, 1.0, 1.0)) @ W[3 * a:3 * b]
+        assert rel(vb[3 * a:3 * b], ref) < (1e-9 if prec == 0 else 2e-5), (s, rel(vb[3 * a:3 * b], ref))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
 def test_mobility_solve(lib, wl_mix, wl_rod, wl_batch, prec):
     for wl in (wl_mix, wl_rod, wl_batch):
         tol = 1e-12 if prec == 0 else 1e-6
