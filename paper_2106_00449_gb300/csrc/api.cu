@@ -173,7 +173,8 @@ static const char* build_host_layout(gdc_ctx* c, const gdc_params* p, int n_temp
     c->device = dev;
     c->num_sms = sms;
     // bodies per block of the factor products: as many as keep 8 blocks per SM busy (at most
-    // GDC_TB_MAX), fewer for large templates (40 KB of shared memory per block); below 4 per
+    // GDC_TB_MAX), fewer for large templates (at most 2,048 rows per block: 40 KB of shared
+    // memory in the factor products, 41 KB in the preconditioner); below 4 per
     // block the products keep one block per body (measured faster there: 2,520 bodies)
     {
         int B = 1;
@@ -184,13 +185,16 @@ static const char* build_host_layout(gdc_ctx* c, const gdc_params* p, int n_temp
         c->h_tb_items.clear();
         c->h_tb_bodies.clear();
         c->tb_smem = 0;
+        c->tb_precond_smem = 0;
         for (int t = 0; t < n_templates; ++t) {
             const int n3 = 3 * tmpl_nblobs[t];
-            const int bt = std::max(1, std::min(B, 2560 / n3));
+            const int bt = std::max(1, std::min(B, 2048 / n3));
             for (size_t i = 0; i < by_t[t].size(); i += bt) {
                 const int cnt = (int)std::min<size_t>(bt, by_t[t].size() - i);
                 c->h_tb_items.push_back(make_int4(t, (int)c->h_tb_bodies.size() + (int)i, cnt, 0));
                 c->tb_smem = std::max(c->tb_smem, (size_t)cnt * n3 * 2 * sizeof(double));
+                c->tb_precond_smem = std::max(c->tb_precond_smem,
+                                              (size_t)cnt * ((2 * n3 + 16) * sizeof(double) + n3 * sizeof(float)));
             }
             c->h_tb_bodies.insert(c->h_tb_bodies.end(), by_t[t].begin(), by_t[t].end());
         }

@@ -376,12 +376,154 @@ void launch_intra_body(gdc_ctx* c, const double* x, double* y, int gm) {
                                                                  c->tmpl_M, c->blob_gm, c->Rb, x, y, gm);
 }
 
+// The block preconditioner for several bodies of one template per block (the items of
+// k_body_tri_tb): the template's M^-1 product grouped, each element read once for all of the
+// block's bodies (FP32 when F32, one accumulator per body and row), then per body (a warp
+// each) the sums K^T (M^-1 rho), the 6 x 6 solve with N and the correction G V, as k_precond.
+template <bool F32>
+__global__ void __launch_bounds__(128) k_precond_tb(const int4* __restrict__ items, const int* __restrict__ bodies,
+                                                    const long long* __restrict__ body_blob_off,
+                                                    const int* __restrict__ tmpl_n, const int* __restrict__ tmpl_off,
+                                                    const long long* __restrict__ minv_off,
+                                                    const double* __restrict__ Minv, const float* __restrict__ Minv32,
+                                                    const double* __restrict__ Gt, const double* __restrict__ Nt,
+                                                    const double* __restrict__ tmpl_xyz, const int* __restrict__ blob_gm,
+                                                    const int* __restrict__ body_gm, const double* __restrict__ Rb,
+                                                    const double* __restrict__ rin, double* __restrict__ zout) {
+    extern __shared__ double sh[];
+    const int4 it = items[blockIdx.x];
+    const int t = it.x, cnt = it.z;
+    const int n = tmpl_n[t], n3 = 3 * n;
+    double* rho = sh;                                         // [cnt][n3]
+    double* av = rho + (long long)cnt * n3;                   // [cnt][n3]
+    double* misc = av + (long long)cnt * n3;                  // [cnt][16]: 0-5 body rows, 8-13 V
+    float* rho32 = reinterpret_cast<float*>(misc + 16 * cnt);   // [cnt][n3] (F32)
+    for (int e = threadIdx.x; e < cnt * n; e += blockDim.x) {
+        const int u = e / n, b = e - u * n;
+        const int p = bodies[it.y + u];
+        const long long o = blob_gm[body_blob_off[p] + b];
+        double v[3] = {rin[o], rin[o + 1], rin[o + 2]}, w[3];
+        rotT(Rb + 9 * p, v, w);
+        for (int a = 0; a < 3; ++a) {
+            rho[u * n3 + 3 * b + a] = w[a];
+            if (F32) rho32[u * n3 + 3 * b + a] = (float)w[a];
+        }
+    }
+    for (int e = threadIdx.x; e < 2 * cnt; e += blockDim.x) {
+        const int u = e >> 1, h = e & 1;
+        const int p = bodies[it.y + u];
+        const long long o = body_gm[p] + 3 * h;
+        double v[3] = {rin[o], rin[o + 1], rin[o + 2]}, w[3];
+        rotT(Rb + 9 * p, v, w);
+        misc[16 * u + 3 * h] = w[0];
+        misc[16 * u + 3 * h + 1] = w[1];
+        misc[16 * u + 3 * h + 2] = w[2];
+    }
+    __syncthreads();
+    const long long mo = minv_off[t];
+    for (int row = threadIdx.x; row < n3; row += blockDim.x) {   // symmetric: coalesced over rows
+        if (F32) {
+            float a[GDC_TB_MAX];
+#pragma unroll
+            for (int u = 0; u < GDC_TB_MAX; ++u) a[u] = 0.f;
+            for (int k = 0; k < n3; ++k) {
+                const float f = Minv32[mo + (long long)k * n3 + row];
+#pragma unroll
+                for (int u = 0; u < GDC_TB_MAX; ++u)
+                    if (u < cnt) a[u] = fmaf(f, rho32[u * n3 + k], a[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < GDC_TB_MAX; ++u)
+                if (u < cnt) av[u * n3 + row] = (double)a[u];
+        } else {
+            double a[GDC_TB_MAX];
+#pragma unroll
+            for (int u = 0; u < GDC_TB_MAX; ++u) a[u] = 0.0;
+            for (int k = 0; k < n3; ++k) {
+                const double f = Minv[mo + (long long)k * n3 + row];
+#pragma unroll
+                for (int u = 0; u < GDC_TB_MAX; ++u)
+                    if (u < cnt) a[u] = fma(f, rho[u * n3 + k], a[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < GDC_TB_MAX; ++u)
+                if (u < cnt) av[u * n3 + row] = a[u];
+        }
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const double* bx = tmpl_xyz + 3LL * tmpl_off[t];
+    for (int u = warp; u < cnt; u += blockDim.x >> 5) {
+        double g[6] = {0, 0, 0, 0, 0, 0};
+        for (int i = lane; i < n; i += 32) {
+            const double a0 = av[u * n3 + 3 * i], a1 = av[u * n3 + 3 * i + 1], a2 = av[u * n3 + 3 * i + 2];
+            const double d0 = bx[3 * i], d1 = bx[3 * i + 1], d2 = bx[3 * i + 2];
+            g[0] += a0;
+            g[1] += a1;
+            g[2] += a2;
+            g[3] += d1 * a2 - d2 * a1;
+            g[4] += d2 * a0 - d0 * a2;
+            g[5] += d0 * a1 - d1 * a0;
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) g[k] = warp_sum(g[k]);
+        if (lane == 0) {
+            const double* N = Nt + 36 * t;
+            for (int a = 0; a < 6; ++a) {
+                double acc = 0.0;
+                for (int k = 0; k < 6; ++k) acc += N[6 * a + k] * (misc[16 * u + k] + g[k]);
+                misc[16 * u + 8 + a] = -acc;
+            }
+        }
+    }
+    __syncthreads();
+    const double* Gtt = Gt + 18LL * tmpl_off[t];   // 3n x 6
+    for (int e = threadIdx.x; e < cnt * n; e += blockDim.x) {
+        const int u = e / n, b = e - u * n;
+        const int p = bodies[it.y + u];
+        double lb[3];
+        for (int a = 0; a < 3; ++a) {
+            const int row = 3 * b + a;
+            double acc = av[u * n3 + row];
+            for (int k = 0; k < 6; ++k) acc = fma(Gtt[6LL * row + k], misc[16 * u + 8 + k], acc);
+            lb[a] = acc;
+        }
+        double w[3];
+        rot(Rb + 9 * p, lb, w);
+        const long long o = blob_gm[body_blob_off[p] + b];
+        zout[o] = w[0];
+        zout[o + 1] = w[1];
+        zout[o + 2] = w[2];
+    }
+    for (int u = threadIdx.x; u < cnt; u += blockDim.x) {
+        const int p = bodies[it.y + u];
+        double w[3];
+        const long long o = body_gm[p];
+        rot(Rb + 9 * p, misc + 16 * u + 8, w);
+        zout[o] = w[0];
+        zout[o + 1] = w[1];
+        zout[o + 2] = w[2];
+        rot(Rb + 9 * p, misc + 16 * u + 11, w);
+        zout[o + 3] = w[0];
+        zout[o + 4] = w[1];
+        zout[o + 5] = w[2];
+    }
+}
+
 void launch_precond(gdc_ctx* c, const double* r, double* z, bool fp32) {
     const size_t smem = (size_t)(3 * 3 * c->max_body_blobs + 32) * sizeof(double);
     if (c->p.wall)
         ++c->n_launch, k_precond<true><<<c->NB, 128, smem, c->stream>>>(
             c->body_blob_off, c->body_tmpl, c->tmpl_n, c->tmpl_off, c->minv_off, c->blk_Minv, nullptr, c->blk_G, c->blk_N,
             c->tmpl_xyz, c->blob_gm, c->body_gm, c->Rb, r, z, c->blk_off, c->r, c->Yc);
+    else if (c->tb_use && fp32)   // many bodies: grouped by template
+        ++c->n_launch, k_precond_tb<true><<<c->tb_n_items, 128, c->tb_precond_smem, c->stream>>>(
+            c->tb_items, c->tb_bodies, c->body_blob_off, c->tmpl_n, c->tmpl_off, c->minv_off, c->tmpl_Minv,
+            c->tmpl_Minv32, c->tmpl_G, c->tmpl_N, c->tmpl_xyz, c->blob_gm, c->body_gm, c->Rb, r, z);
+    else if (c->tb_use)
+        ++c->n_launch, k_precond_tb<false><<<c->tb_n_items, 128, c->tb_precond_smem, c->stream>>>(
+            c->tb_items, c->tb_bodies, c->body_blob_off, c->tmpl_n, c->tmpl_off, c->minv_off, c->tmpl_Minv,
+            c->tmpl_Minv32, c->tmpl_G, c->tmpl_N, c->tmpl_xyz, c->blob_gm, c->body_gm, c->Rb, r, z);
     else if (fp32)
         ++c->n_launch, k_precond<false, true><<<c->NB, 128, smem, c->stream>>>(
             c->body_blob_off, c->body_tmpl, c->tmpl_n, c->tmpl_off, c->minv_off, c->tmpl_Minv, c->tmpl_Minv32, c->tmpl_G,

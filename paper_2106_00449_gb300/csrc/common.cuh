@@ -126,7 +126,7 @@ struct gdc_ctx {
     int* tb_bodies = 0;
     int tb_n_items = 0;
     bool tb_use = false;   // the grouped products replace one block per body
-    size_t tb_smem = 0;
+    size_t tb_smem = 0, tb_precond_smem = 0;
     std::vector<int4> h_tb_items;
     std::vector<int> h_tb_bodies;
     std::vector<long long> h_minv_off;

@@ -195,6 +195,61 @@ def test_brownian_slip_many_bodies(lib, prec):
         assert rel(vb[3 * a:3 * b], ref) < (1e-9 if prec == 0 else 2e-5), (s, rel(vb[3 * a:3 * b], ref))
 
 
+def test_precond_and_solve_many_bodies(lib):
+    """About 6,300 bodies, enough for the block preconditioner to group several bodies of one
+    template per block: its application against the oracle's per-body saddle solves on
+    sampled bodies, and mobility solves in FP64 and FP32-mixed (whose inner cycles apply the
+    template M^-1 in FP32) against the oracle's LU on sampled suspensions, with iteration
+    counts that show the FP32 preconditioner preconditions as well."""
+    wl = WL.batch_small(1400, seed=3, nmin=4, nmax=5)
+    rng = np.random.default_rng(17)
+    ctx = ctx_for(lib, wl, precision=0, gmres_tol=1e-12, gmres_max_iter=800, autotune=0)
+    n = int(ctx.saddle_off[-1])
+    rvec = rng.standard_normal(n)
+    z = _host(ctx.precond_apply(rvec))
+    picks = rng.choice(wl.n_susp, 30, replace=False)
+    for s in picks[:10]:
+        lay, Y, q = susp_layout(wl, s)
+        r, M, K, B = dense_state(lay, Y, q)
+        o = int(ctx.saddle_off[s])
+        nl = 3 * lay.n_blobs
+        for p in range(lay.n_bodies):
+            i0, i1 = lay.blob_off[p], lay.blob_off[p + 1]
+            Mp = M[3 * i0:3 * i1, 3 * i0:3 * i1]
+            Kp = K[3 * i0:3 * i1, 6 * p:6 * p + 6]
+            Bp = rigid.rigid_basis(Kp, 1)
+            rv = Bp @ (Bp.T @ rvec[o + nl + 6 * p:o + nl + 6 * p + 6])
+            lp, vp = rigid.saddle_solve(Mp, Kp, Bp, -rvec[o + 3 * i0:o + 3 * i1], -rv)
+            assert rel(z[o + 3 * i0:o + 3 * i1], lp) < 1e-10
+            assert rel(z[o + nl + 6 * p:o + nl + 6 * p + 6], vp) < 1e-10
+    FT = rng.standard_normal(6 * wl.n_bodies).reshape(-1, 6)
+    vb = rng.standard_normal(3 * wl.n_blobs)
+    # physical torques only: none on the collinear rods (their axial spin is not a DOF)
+    collinear = [np.linalg.matrix_rank(t - t.mean(0), tol=1e-9) <= 1 for t in wl.templates]
+    FT[np.array([collinear[t] for t in wl.body_tmpl]), 3:] = 0.0
+    FT = FT.reshape(-1)
+    iters = {}
+    for prec, tol, check in ((0, 1e-12, True), (0, 1e-6, False), (1, 1e-6, True)):
+        c2 = ctx_for(lib, wl, precision=prec, gmres_tol=tol, gmres_max_iter=800, autotune=0)
+        V, lam, info = c2.mobility_solve(FT, vb, want_lambda=True)
+        V, lam = _host(V), _host(lam)
+        assert info["converged"] and info["residual"] <= tol
+        iters[(prec, tol)] = info["iterations"]
+        if not check:
+            continue
+        sl = blob_slices(wl)
+        for s in picks:
+            lay, Y, q = susp_layout(wl, s)
+            r, M, K, B = dense_state(lay, Y, q)
+            a, b = sl[s]
+            o = int(wl.susp_body_off[s])
+            Fs = FT[6 * o:6 * o + 6 * lay.n_bodies]
+            ls, Vs = rigid.saddle_solve(M, K, B, vb[3 * a:3 * b], Fs)
+            assert rel(V[6 * o:6 * o + 6 * lay.n_bodies], Vs) < (1e-9 if prec == 0 else 1e-4)
+    # the FP32-mixed solve (FP32 preconditioner product) needs about the FP64 solve's iterations
+    assert iters[(1, 1e-6)] <= 1.25 * iters[(0, 1e-6)] + 3, iters
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_mobility_solve(lib, wl_mix, wl_rod, wl_batch, prec):
     for wl in (wl_mix, wl_rod, wl_batch):
