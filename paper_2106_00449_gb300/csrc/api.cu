@@ -180,6 +180,7 @@ static const char* build_host_layout(gdc_ctx* c, const gdc_params* p, int n_temp
         int B = 1;
         while (B < GDC_TB_MAX && NB >= 2LL * B * 8 * sms) B *= 2;
         c->tb_use = B >= 4;
+        c->lz_qbuf_on = n_susp > sms;   // the eigen-step's scratch: see krylov.cu
         std::vector<std::vector<int>> by_t(n_templates);
         for (long long b = 0; b < NB; ++b) by_t[body_tmpl[b]].push_back((int)b);
         c->h_tb_items.clear();
@@ -329,6 +330,7 @@ static size_t carve(gdc_ctx* c, void* base) {
     c->lz_c = w.take<double>(S * k);
     c->lz_lastk = w.take<int>(2 * S);
     c->lz_hint = w.take<int>(S);
+    c->lz_qbuf = w.take<double>(c->lz_qbuf_on ? (long long)S * lz_q_doubles(c->kmax) : 1);
     c->lz_h = w.take<double>(S * cols);
     c->lz_Wnorm = w.take<double>(S);
     c->lz_err = w.take<double>(S);

@@ -128,6 +128,8 @@ struct gdc_ctx {
     bool tb_use = false;   // the grouped products replace one block per body
     size_t tb_smem = 0, tb_precond_smem = 0;
     std::vector<int4> h_tb_items;
+    double* lz_qbuf = 0;     // the eigen-step's Q / refined-root scratch per suspension (global)
+    bool lz_qbuf_on = false; // more suspensions than SMs: the scratch in global memory, not shared
     std::vector<int> h_tb_bodies;
     std::vector<long long> h_minv_off;
     std::vector<double> h_tmpl_xyz, h_tmpl_L;
@@ -381,6 +383,7 @@ void build_sym_items(gdc_ctx* c, int width);
 void build_sym_list(const gdc_ctx* c, int width, std::vector<SymItem>& items, std::vector<int>& row_nk, int& kmax);
 // dfsym.cu
 gdc_status dfsym_init_attributes(gdc_ctx* c);
+long long lz_q_doubles(int kmax);   // krylov.cu
 void launch_rpy_df_sym_pairs(gdc_ctx* c);
 void launch_rpy_df_sym_epilogue(gdc_ctx* c, const double* x, double* y, int gm_layout);
 gdc_status sym_upload(gdc_ctx* c);

@@ -540,11 +540,24 @@ __host__ __device__ inline int lz_refine_doubles(int k) {
     return (k * ldk + 1) / 2 + 2 * k * ldk + 2 * k;
 }
 
-// Dynamic shared memory of k_lz_tridiag: four c vectors, then Q (FP64) or the scratch of the
-// refined root, whichever is larger.
-static size_t lz_tridiag_smem(int kmax) {
-    const int q = kmax * lz_ldq(kmax), r = lz_refine_doubles(std::min(kmax, GDC_LZ_REFINE_MAX));
-    return (size_t)4 * kmax * sizeof(double) + (size_t)std::max(q, r) * sizeof(double);
+__device__ inline long long lz_q_doubles_dev(int kmax) {
+    const int q = kmax * lz_ldq(kmax), r = lz_refine_doubles(kmax < GDC_LZ_REFINE_MAX ? kmax : GDC_LZ_REFINE_MAX);
+    return q > r ? q : r;
+}
+
+// Doubles of Q (FP64, or FP32 in half of them) or of the scratch of the refined root,
+// whichever is larger.
+long long lz_q_doubles(int kmax) {
+    return std::max(kmax * lz_ldq(kmax), lz_refine_doubles(std::min(kmax, GDC_LZ_REFINE_MAX)));
+}
+
+// Dynamic shared memory of k_lz_tridiag: four c vectors, then Q or the refined root's scratch
+// (132 KB at kmax = 128, one block per SM).  With more suspensions than SMs that area lives in
+// a per-suspension slice of global memory instead (c->lz_qbuf, cached in L1), so that several
+// suspensions' warps share an SM.
+static size_t lz_tridiag_smem(int kmax) { return (size_t)(4 * kmax + lz_q_doubles(kmax)) * sizeof(double); }
+static size_t lz_launch_smem(const gdc_ctx* c) {
+    return c->lz_qbuf_on ? (size_t)4 * c->kmax * sizeof(double) : lz_tridiag_smem(c->kmax);
 }
 
 // Givens rotation (c, s) with c x + s z = r, -s x + c z = 0.  FP32 (the stopping test at
@@ -760,7 +773,8 @@ __global__ void __launch_bounds__(32) k_lz_tridiag(int S, int j, const int* __re
                                                    int* __restrict__ active, int* __restrict__ kcount,
                                                    int* __restrict__ lastk, double* __restrict__ scal, double tol,
                                                    const int* __restrict__ fixed, int* __restrict__ hint, int kmax,
-                                                   const long long* __restrict__ susp_blob_off, int* __restrict__ status) {
+                                                   const long long* __restrict__ susp_blob_off, int* __restrict__ status,
+                                                   double* __restrict__ qbuf) {
     extern __shared__ __align__(16) unsigned char lz_smem[];
     const int s = blockIdx.x;
     const int lane = threadIdx.x;
@@ -799,7 +813,7 @@ __global__ void __launch_bounds__(32) k_lz_tridiag(int S, int j, const int* __re
     double* ck = cur + kmax;
     double* cm = ck + kmax;
     double* best = cm + kmax;
-    double* Q = best + kmax;
+    double* Q = qbuf ? qbuf + (long long)s * lz_q_doubles_dev(kmax) : best + kmax;
     const int ldq = lz_ldq(kmax);
     const bool check32 = !fixed_mode && tol >= 1e-5;   // FP32 stopping test, FP64 result
     if (!lz_sqrt_e1(al, be, k, wn, Q, ldq, cur, check32)) {
@@ -920,10 +934,10 @@ gdc_status lanczos_sqrt(gdc_ctx* c, const double* W, double* out, double scale, 
         ++c->n_launch, k_mupdate<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_V, n, j + 1, nullptr, c->gm_h2, cols, c->lz_w);
         ++c->n_launch, k_add_cols<<<c->S, 128, 0, c->stream>>>(j + 1, nullptr, c->lz_h, c->gm_h2, cols);
         seg_mdot(c, sg, c->lz_w, 0, 1, c->lz_w, c->gm_h2, cols);
-        ++c->n_launch, k_lz_tridiag<<<c->S, 32, lz_tridiag_smem(kmax), c->stream>>>(
+        ++c->n_launch, k_lz_tridiag<<<c->S, 32, lz_launch_smem(c), c->stream>>>(
             c->S, j, nullptr, c->lz_h, cols, c->gm_h2, c->lz_alpha, c->lz_beta, c->lz_Wnorm, c->lz_c, c->lz_err, c->lz_active,
             c->lz_k, c->lz_lastk, c->lz_scal, c->p.lanczos_tol, fixed_mode ? c->lz_fix : nullptr, c->lz_hint, kmax, c->susp_blob_off,
-            c->dev_status);
+            c->dev_status, c->lz_qbuf_on ? c->lz_qbuf : nullptr);
         ++c->n_launch, k_seg_scale<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_w, c->lz_scal,
                                                                        c->lz_V + (long long)(j + 1) * n);
         if ((st = sync_read(c, c->lz_active, act.data(), sizeof(int) * c->S)) != GDC_OK) return st;
@@ -1203,10 +1217,10 @@ void lanczos_sqrt_graph(gdc_ctx* c, const double* W, double* out, double scale, 
     ++c->n_launch, k_mupdate<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_V, n, 1, jd, c->gm_h2, cols, c->lz_w);
     ++c->n_launch, k_add_cols<<<c->S, 128, 0, c->stream>>>(1, jd, c->lz_h, c->gm_h2, cols);
     seg_mdot(c, sg, c->lz_w, 0, 1, c->lz_w, c->gm_h2, cols);
-    ++c->n_launch, k_lz_tridiag<<<c->S, 32, lz_tridiag_smem(kmax), c->stream>>>(
+    ++c->n_launch, k_lz_tridiag<<<c->S, 32, lz_launch_smem(c), c->stream>>>(
         c->S, 0, jd, c->lz_h, cols, c->gm_h2, c->lz_alpha, c->lz_beta, c->lz_Wnorm, c->lz_c, c->lz_err, c->lz_active,
         c->lz_k, c->lz_lastk, c->lz_scal, c->p.lanczos_tol, fixed_mode ? c->lz_fix : nullptr, c->lz_hint, kmax,
-        c->susp_blob_off, c->dev_status);
+        c->susp_blob_off, c->dev_status, c->lz_qbuf_on ? c->lz_qbuf : nullptr);
     ++c->n_launch, k_seg_scale_slot<<<sg.n_chunks, 256, 0, c->stream>>>(sg.chunks, c->lz_w, c->lz_scal, c->lz_V, n, jd,
                                                                         1, c->lz_vcur);
     ++c->n_launch, k_lz_next<<<1, 32, 0, c->stream>>>(c->S, c->lz_active, c->ctl, kmax, h);
