@@ -319,6 +319,29 @@ def boomerang_wall_leg(g, torch, WL, n_susp: int, steps: int = 20) -> dict:
     return out
 
 
+def c5_shear_leg(g, torch, WL, common, steps: int = 1) -> dict:
+    """The large FP32-mixed configuration: 16,384 rods of 20 blobs (327,680 blobs) in linear
+    shear, dt 0.002, the headline's tolerances; default kernels (no autotuning, to bound the
+    bench's time), one warm-up step (its graph capture), then `steps` steps by CUDA events."""
+    wl = WL.c5(seed=0)
+    ctx = g.context_from_workload(wl, precision=g.FP32_MIXED, rfd_delta=1e-3, autotune=0, **common)
+    ctx.step(1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(ctx.stream)
+    inf = ctx.step(steps)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1000.0
+    out = {"workload": WORKLOAD_C5, "n_blobs": wl.n_blobs, "steps": steps, "warmup": 1,
+           "steps_per_s": steps / t, "pair_evals_per_s": sum(i["pair_evals"] for i in inf) / t,
+           "lanczos_iters": [i["lanczos_iters"] for i in inf], "gmres_iters": [i["solve"]["iterations"] for i in inf],
+           "residual_max": max(i["solve"]["residual"] for i in inf),
+           "note": "one warm-up step only (a step takes ~10 s); default kernels, not autotuned"}
+    del ctx
+    return out
+
+
 def per_suspension_steps(g, torch, wl, common, rank):
     """The suspensions of a batch advanced one context per suspension, one after another.
 
@@ -504,6 +527,8 @@ def main(argv=None) -> int:
     ap.add_argument("--cpu-products", type=int, default=3, help="full-size twin products timed for cpu_baseline")
     ap.add_argument("--c4-suspensions", type=int, default=64,
                     help="suspensions of the c4 batching leg of the default run (0 = skip)")
+    ap.add_argument("--c5-steps", type=int, default=1,
+                    help="timed steps of the 327,680-blob c5 leg in the default run (0 = skip)")
     ap.add_argument("--wall-suspensions", type=int, default=36,
                     help="boomerang-above-a-wall suspensions of the default run's wall leg (0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -659,6 +684,8 @@ def main(argv=None) -> int:
         line["c4_batching"] = c4_batching(g, torch, WL, common, args.c4_suspensions)
     if args.workload == "c3_65k" and rank == 0 and world == 1 and args.wall_suspensions > 0:
         line["boomerang_wall"] = boomerang_wall_leg(g, torch, WL, args.wall_suspensions)
+    if args.workload == "c3_65k" and rank == 0 and world == 1 and args.c5_steps > 0:
+        line["c5_shear"] = c5_shear_leg(g, torch, WL, common, args.c5_steps)
     if args.workload != "c3_65k":
         if rank == 0:
             print(json.dumps(line), flush=True)
