@@ -586,3 +586,35 @@ def test_rpy32_ragged_suspension_sizes(lib, kernel):
         got = u[3 * off:3 * (off + n)]
         assert rel(got, ref) < 2e-6, (n, rel(got, ref))
         off += n
+
+
+def test_largest_template_bodies(lib):
+    """Bodies of the largest template the library takes (340 blobs: a 7 x 7 x 7 lattice of
+    blobs 2a apart without three corners; 1,020 rows per template block): products, the
+    block preconditioner, the preconditioned Lanczos root and a mobility solve in FP64
+    against the dense oracle, three such bodies in one suspension."""
+    g = np.arange(7) * 2.0
+    cube = np.array([[x, y, z] for x in g for y in g for z in g])[3:]
+    cube = cube - cube.mean(axis=0)
+    assert cube.shape == (340, 3)
+    rng = np.random.default_rng(31)
+    Y = np.array([[0.0, 0.0, 0.0], [25.0, 1.0, -2.0], [-3.0, 25.0, 4.0]])   # > 2 x 10.4a apart: no overlap
+    q = WL.random_unit_quaternions(rng, 3)
+    wl = WL.Workload("cubes340", [cube], np.zeros(3, dtype=np.int32), np.array([0, 3], dtype=np.int64), Y, q,
+                     dict(WL.c1().params), np.array([60.0]))
+    ctx = ctx_for(lib, wl, precision=0, lanczos_tol=1e-11, lanczos_max_iter=128, gmres_tol=1e-12,
+                  gmres_max_iter=800, kT=1.0, dt=0.01, lanczos_precond=1)
+    lay, Yl, ql = susp_layout(wl, 0)
+    r, M, K, B = dense_state(lay, Yl, ql)
+    lam = rng.standard_normal(3 * wl.n_blobs)
+    assert rel(_host(ctx.rpy_apply(lam, 0)), M @ lam) < 1e-12
+    assert rel(_host(ctx.rpy_apply(lam, 1)), M @ lam) < 2e-6
+    W = rng.standard_normal(3 * wl.n_blobs)
+    vb = _host(ctx.brownian_slip(W)[0])
+    ref = np.sqrt(2 * 1.0 / 0.01) * rigid.sqrtm_block(M, rigid.block_factor(lay, ql, 1.0, 1.0)) @ W
+    assert rel(vb, ref) < 1e-9
+    FT = rng.standard_normal(6 * wl.n_bodies)
+    V, lamv, info = ctx.mobility_solve(FT, W, want_lambda=True)
+    assert info["converged"]
+    ls, Vs = rigid.saddle_solve(M, K, B, W, FT)
+    assert rel(_host(V), Vs) < 1e-9
