@@ -618,3 +618,39 @@ def test_largest_template_bodies(lib):
     assert info["converged"]
     ls, Vs = rigid.saddle_solve(M, K, B, W, FT)
     assert rel(_host(V), Vs) < 1e-9
+
+
+def _degenerate_workload():
+    """Single blobs (3 DOF: no rotation moves a blob at its body's centre, L_p read as a),
+    2-blob dumbbells (5 DOF) and icosahedra in one suspension."""
+    from synthetic import shapes
+    rng = np.random.default_rng(41)
+    tmpl = [np.zeros((1, 3)), np.array([[-1.0, 0.0, 0.0], [1.0, 0.0, 0.0]]), shapes.icosahedron()]
+    bt = np.array([0, 0, 1, 1, 2, 0, 1, 2], dtype=np.int32)
+    Y = np.array([[0, 0, 0], [4.0, 0, 0], [0, 5.0, 0], [5.0, 5.0, 1.0], [-6.0, 0, 0], [0, -4.0, 2.0], [0, 0, 6.0],
+                  [7.0, -6.0, 0]])
+    q = WL.random_unit_quaternions(rng, len(bt))
+    return WL.Workload("degenerate", tmpl, bt, np.array([0, len(bt)], dtype=np.int64), Y, q, dict(WL.c1().params),
+                       np.array([20.0]))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_degenerate_bodies_step(lib, prec):
+    """One gDC step of single blobs, dumbbells and icosahedra against the oracle: positions,
+    the dumbbells' axes and the icosahedra's rotations (a single blob's orientation carries
+    no information)."""
+    wl = _degenerate_workload()
+    ctx, tr, info, Y1, q1, out = _step_case(lib, wl, prec)
+    assert info["solve"]["converged"]
+    (s, o, e, ora), = out
+    pos_err = np.abs(Y1 - ora["Y1"]).max() / np.abs(ora["Y1"]).max()
+    disp_err = rel(Y1 - wl.Y, ora["Y1"] - wl.Y)
+    ico = wl.body_tmpl == 2
+    dumb = wl.body_tmpl == 1
+    axis = lambda qq: np.array([G.rotation_matrix(x)[:, 0] for x in qq])
+    ax_err = np.abs(axis(q1[dumb]) - axis(ora["q1"][dumb])).max()
+    r_err = rot_err(q1[ico], ora["q1"][ico])
+    if prec == 0:
+        assert pos_err < 1e-11 and disp_err < 1e-6 and ax_err < 1e-9 and r_err < 1e-9, (pos_err, disp_err, ax_err, r_err)
+    else:
+        assert pos_err < 1e-5 and disp_err < 1e-3 and ax_err < 1e-5 and r_err < 1e-5, (pos_err, disp_err, ax_err, r_err)
