@@ -6,8 +6,9 @@
 // GB300 layout: the grid work is bandwidth-bound, so it runs in FP32 on complex float2 grids
 // of N^3 points, each holding two real fields as a + i b (their transforms are separated by
 // conjugate symmetry in the solve): 0-1 the force density, 2-3 its velocity, 4-6 the six
-// stress components, 7-8 the fluctuating velocity; the two velocities are then packed per
-// point (float4), and the fluctuating one is kept there for re-averaging.
+// stress components, 7-8 the fluctuating velocity.  The last inverse pass (along x) writes a
+// velocity packed per point (float4: x, y, z, 0) into one of two packed grids, deterministic
+// and fluctuating; the fluctuating one is kept there for re-averaging.
 //   * spreading is a gather: a block takes the grid points of one binning cell (cells at
 //     least R_t wide) and stages the blobs of the 27 cells around it (blobs in ascending
 //     index) in shared memory as FP32 offsets from the cell's corner; it is deterministic and
@@ -18,8 +19,10 @@
 //     written once per axis, along x in the x pass and P consecutive x at a time in the y and
 //     z passes;
 //   * the solve (projection, 1/(eta k^2), the spectral divergence of the stress and the 1/N^3
-//     of the inverse transform) is one pass over the modes;
-//   * averaging reads the velocity packed per point (one 16-byte load) and takes one warp per
+//     of the inverse transform): for M_FCM lambda it runs between the forward and inverse z
+//     passes in one launch (a block takes pencils with their mirrors, whose modes -k the split
+//     of the two real fields needs), for v-breve it is one pass over the modes;
+//   * averaging reads the packed velocity (one 16-byte load per point) and takes one warp per
 //     blob, each lane a fixed x offset and every (32 / width)-th row of the blob's box (at
 //     most 31 points per side); each lane sums its points of a z-plane in FP32 and the
 //     planes with FP32 compensation, and the lanes are added in FP64 in a fixed order.
@@ -131,6 +134,11 @@ __device__ __forceinline__ int fft_swz(int t) { return t ^ ((t >> 3) & 15); }
 static size_t fft_smem(int N, int TH) {
     const int P = 8 * TH / N;
     return (size_t)(P * fft_stride(N, P) + N) * sizeof(float2);
+}
+// two rows per pencil (k_fft_x_pack, k_fcm_zsolve) and the twiddle table
+static size_t fft_smem2(int N, int TH) {
+    const int P = 8 * TH / N;
+    return (size_t)(2 * P * fft_stride(N, P) + N) * sizeof(float2);
 }
 // Threads per block of the y and z passes for 256- and 512-point pencils (P consecutive x
 // per warp row: 4 x 8 bytes = 32-byte runs at 256 threads and N = 512, 64 at 512, 128 at
@@ -327,15 +335,6 @@ __global__ void __launch_bounds__(128) k_fcm_spread(int N, double h, double L, d
     }
 }
 
-// The three real parts of a velocity's complex grids packed per point (x, y, z, 0).
-// The velocity (x, y, z, 0) per point from its packed complex grids (u_x + i u_y, u_z).
-__global__ void k_fcm_pack(long long NG, const float2* __restrict__ u, float4* __restrict__ out) {
-    const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (g >= NG) return;
-    const float2 a = u[g];
-    out[g] = make_float4(a.x, a.y, u[NG + g].x, 0.f);
-}
-
 // ---- FFT: self-sorting (Stockham) passes of radix 8, then 4 or 2; one axis per launch ----
 //
 // INV = 0: X_k = sum_n x_n exp(-2 pi i k n / N); INV = 1: the same with +i, unscaled.
@@ -486,6 +485,42 @@ __global__ void __launch_bounds__(TH) k_fft(float2* __restrict__ data, long long
     for (int m = 0; m < 8; ++m) g[(long long)(i + m * T) * st] = x[m];
 }
 
+// The last inverse pass of a velocity, along x, with its packing: a block transforms P pencils
+// of both complex grids u (u_x + i u_y at g, u_z at NG + g), one after the other, and writes
+// the three real parts per point as (x, y, z, 0), the layout averaging gathers (one 16-byte
+// load per point).  Same pencils and threads as the x pass of k_fft; the first grid's result
+// waits in a second shared-memory row per pencil while the second is transformed.
+template <int LOGN>
+__global__ void __launch_bounds__(256, 4) k_fft_x_pack(const float2* __restrict__ u, long long NG,
+                                                    const float2* __restrict__ tw_g, float4* __restrict__ out) {
+    constexpr int TH = 256, N = 1 << LOGN, T = N / 8, P = TH / T, S = fft_stride(N, P);
+    extern __shared__ float2 sm[];
+    float2* park = sm + P * S + (threadIdx.x / T) * S;
+    float2* tw = sm + 2 * P * S;
+    for (int j = threadIdx.x; j < N / 2; j += TH) {
+        const float2 w = tw_g[j];
+        tw[j] = w;
+        tw[j + N / 2] = make_float2(-w.x, -w.y);
+    }
+    const int q = threadIdx.x / T, i = threadIdx.x % T;
+    const long long o = ((long long)blockIdx.x * P + q) << LOGN;
+    float2 x[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) x[m] = u[o + i + m * T];
+    __syncthreads();   // twiddle table complete
+    fft_passes<1, LOGN, 0>(x, sm + q * S, tw, i);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) park[i + m * T] = x[m];   // read back by this thread only
+#pragma unroll
+    for (int m = 0; m < 8; ++m) x[m] = u[NG + o + i + m * T];
+    fft_passes<1, LOGN, 0>(x, sm + q * S, tw, i);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        const float2 a = park[i + m * T];
+        out[o + i + m * T] = make_float4(a.x, a.y, x[m].x, 0.f);
+    }
+}
+
 // ---- Fourier-space solve ------------------------------------------------------------------
 
 struct Mode {
@@ -493,16 +528,21 @@ struct Mode {
     float kx, ky, kz, k2;
 };
 
-__device__ __forceinline__ Mode fcm_mode(long long g, int N, float kunit) {
+// The mode of grid indices (ix, iy, iz): its wave vector and whether it is kept (k != 0, no
+// Nyquist component).
+__device__ __forceinline__ Mode fcm_mode3(int ix, int iy, int iz, int N, float kunit) {
     const int half = N / 2;
-    const int ix = (int)(g % N), iy = (int)((g / N) % N), iz = (int)(g / ((long long)N * N));
     Mode m;
-    m.keep = g != 0 && ix != half && iy != half && iz != half;
+    m.keep = (ix | iy | iz) != 0 && ix != half && iy != half && iz != half;
     m.kx = kunit * (float)(ix < half ? ix : ix - N);
     m.ky = kunit * (float)(iy < half ? iy : iy - N);
     m.kz = kunit * (float)(iz < half ? iz : iz - N);
     m.k2 = m.kx * m.kx + m.ky * m.ky + m.kz * m.kz;
     return m;
+}
+
+__device__ __forceinline__ Mode fcm_mode(long long g, int N, float kunit) {
+    return fcm_mode3((int)(g % N), (int)((g / N) % N), (int)(g / ((long long)N * N)), N, kunit);
 }
 
 // u = (I - k k^T / k^2) f / (eta k^2) / N^3 for one mode (complex f components)
@@ -533,30 +573,102 @@ __device__ __forceinline__ void fcm_split(float2 zk, float2 zm, float2& A, float
 // A + i B for two transforms of real fields: the inverse transform gives a + i b.
 __device__ __forceinline__ float2 fcm_join(float2 A, float2 B) { return make_float2(A.x - B.y, A.y + B.x); }
 
-// f: FFT(f_x + i f_y), FFT(f_z); u: (u_x + i u_y, u_z) transforms, scaled for the inverse.
-__global__ void k_fcm_solve(long long NG, int N, float kunit, float scale_eta, const float2* __restrict__ f,
-                            float2* __restrict__ u) {
-    const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (g >= NG) return;
-    const Mode m = fcm_mode(g, N, kunit);
-    float2 o0 = make_float2(0.f, 0.f), o1 = o0;
-    if (m.keep) {   // kept modes come in pairs k, -k (no Nyquist component)
-        const long long gm = fcm_mirror(g, N);
-        float2 fx, fy, ux, uy, uz;
-        fcm_split(f[g], f[gm], fx, fy);
-        fcm_project(m, scale_eta, fx, fy, f[NG + g], ux, uy, uz);
-        o0 = fcm_join(ux, uy);
-        o1 = uz;
+// The z passes of both transforms with the solve between them, in one launch.  F holds
+// FFT_xy(f_x + i f_y) and FFT_xy(f_z) (x and y passes done), U receives the velocity's two grids
+// (u_x + i u_y, u_z) before their inverse x and y passes, scaled for the inverse.  Splitting
+// FFT(f_x + i f_y) into its two real fields needs the mode -k beside k, so a block takes H
+// pencils (x, y) of consecutive x from the rows y = 0 .. N/2 together with their mirror
+// pencils (-x, -y): per pencil it transforms both force grids along z, keeps the first
+// spectrum in shared memory in natural order (the partner pencil reads its mode -k_z there),
+// solves, and transforms the two velocity grids back along z.  The grids are read and written
+// once instead of three times (forward z pass, solve, inverse z pass).  In the rows y = 0 and
+// y = N/2 the pencils x > N/2 are the mirrors of N - x and come with them; the four pencils
+// with x, y in {0, N/2} are their own mirrors.
+template <int LOGN, int TH>
+__global__ void __launch_bounds__(TH) k_fcm_zsolve(const float2* __restrict__ F, float2* __restrict__ U, long long NG,
+                                                   const float2* __restrict__ tw_g, float kunit, float scale_eta) {
+    constexpr int N = 1 << LOGN, T = N / 8, P = TH / T, H = P / 2, S = fft_stride(N, P);
+    extern __shared__ float2 sm[];
+    float2* zr = sm + P * S;   // per pencil: its spectrum of f_x + i f_y, later its parked u_z
+    float2* tw = zr + P * S;   // exp(-2 pi i m / N), m = 0..N-1
+    for (int j = threadIdx.x; j < N / 2; j += TH) {
+        const float2 w = tw_g[j];
+        tw[j] = w;
+        tw[j + N / 2] = make_float2(-w.x, -w.y);
     }
-    u[g] = o0;
-    u[NG + g] = o1;
+    // pencil q of the block: slot q mod H (x consecutive), side 0 the slot's pencil, 1 its mirror
+    const int q = threadIdx.x % P, i = threadIdx.x / P, side = q / H;
+    const long long s = (long long)blockIdx.x * H + q % H;
+    const int sx = (int)(s & (N - 1)), sy = (int)(s >> LOGN);
+    const bool self = (sx == 0 || sx == N / 2) && (sy == 0 || sy == N / 2);
+    const bool slot = sy <= N / 2 && ((sy > 0 && sy < N / 2) || sx <= N / 2);
+    const bool run = slot && !(side == 1 && self);   // the mirror side of a self-mirrored pencil idles
+    const int px = side ? (N - sx) & (N - 1) : sx, py = side ? (N - sy) & (N - 1) : sy;
+    const int partner = self ? q : (side ? q - H : q + H);
+    const long long o = px + ((long long)py << LOGN), st = (long long)N * N;
+    float2* row = sm + q * S;
+    float2* zq = zr + q * S;
+    float2 x[8], z1[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) x[m] = run ? F[o + (long long)(i + m * T) * st] : make_float2(0.f, 0.f);
+    __syncthreads();   // twiddle table complete
+    fft_passes<0, LOGN, 0>(x, row, tw, i);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) zq[i + m * T] = x[m];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) z1[m] = run ? F[NG + o + (long long)(i + m * T) * st] : make_float2(0.f, 0.f);
+    fft_passes<0, LOGN, 0>(z1, row, tw, i);
+    __syncthreads();   // every pencil's spectrum of f_x + i f_y in shared memory
+    const float2* zp = zr + partner * S;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        const int kz = i + m * T;
+        const Mode md = fcm_mode3(px, py, kz, N, kunit);
+        float2 o0 = make_float2(0.f, 0.f), o1 = o0;
+        if (md.keep) {
+            float2 fx, fy, ux, uy, uz;
+            fcm_split(zq[kz], zp[(N - kz) & (N - 1)], fx, fy);
+            fcm_project(md, scale_eta, fx, fy, z1[m], ux, uy, uz);
+            o0 = fcm_join(ux, uy);
+            o1 = uz;
+        }
+        row[kz] = o0;   // the exchange row is free here: parked until the spectra are read
+        z1[m] = o1;
+    }
+    __syncthreads();   // the spectra are no longer read
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        zq[i + m * T] = z1[m];   // parked while u_x + i u_y is transformed
+        x[m] = row[i + m * T];
+    }
+    __syncthreads();   // the first inverse pass rewrites the row
+    fft_passes<1, LOGN, 0>(x, row, tw, i);
+    if (run) {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) U[o + (long long)(i + m * T) * st] = x[m];
+    }
+#pragma unroll
+    for (int m = 0; m < 8; ++m) z1[m] = zq[i + m * T];
+    fft_passes<1, LOGN, 0>(z1, row, tw, i);
+    if (run) {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) U[NG + o + (long long)(i + m * T) * st] = z1[m];
+    }
 }
+
+// Threads per block of k_fcm_zsolve (its shared memory: fft_smem2, 132-135 KB at 1024
+// threads: 16 pencils of 512 points or 32 of 256).
+#ifndef GDC_ZSOLVE_TH
+#define GDC_ZSOLVE_TH 1024
+#endif
+static int zsolve_threads(int N) { return N >= 256 ? GDC_ZSOLVE_TH : 256; }
 
 __device__ __forceinline__ float2 cadd3(float a, float2 x, float b, float2 y, float c, float2 z) {
     return make_float2(a * x.x + b * y.x + c * z.x, a * x.y + b * y.y + c * z.y);
 }
 
-// Z: FFT(W_xx + i W_yy), FFT(W_zz + i W_xy), FFT(W_xz + i W_yz); u as for k_fcm_solve.
+// Z: FFT(W_xx + i W_yy), FFT(W_zz + i W_xy), FFT(W_xz + i W_yz); u: the velocity's transforms
+// (u_x + i u_y, u_z), scaled for the inverse.
 __global__ void k_fcm_solve_stress(long long NG, int N, float kunit, float scale_eta, const float2* __restrict__ Z,
                                    float2* __restrict__ u) {
     const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -698,9 +810,10 @@ static gdc_status fcm_check(gdc_fcm* f, cudaError_t e, const char* what) {
     return fcm_fail(f, GDC_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-static void fft3(gdc_fcm* f, int slot, int ncomp, bool inverse) {
+// The transforms along the axes a0 .. a1 - 1 (0 x, 1 y, 2 z) of ncomp grids from slot on.
+static void fft3(gdc_fcm* f, int slot, int ncomp, bool inverse, int a0, int a1) {
     float2* d = f->grid + slot * f->NG;
-    for (int axis = 0; axis < 3; ++axis) {
+    for (int axis = a0; axis < a1; ++axis) {
         const int th = fft_threads(f->N, axis);
         const dim3 grid((unsigned)(f->NG / (8LL * th)), (unsigned)ncomp);   // N^2 pencils, 8 TH / N per block
         const size_t smem = fft_smem(f->N, th);
@@ -731,12 +844,47 @@ static void fft3(gdc_fcm* f, int slot, int ncomp, bool inverse) {
     }
 }
 
-// which = 0: the deterministic velocity, 1: the fluctuating one
-static void fcm_pack(gdc_fcm* f, int slot, int which) {
-    ++f->n_launch, k_fcm_pack<<<ceil_div(f->NG, 256), 256, 0, f->stream>>>(f->NG, f->grid + slot * f->NG,
-                                                                           f->packed + which * f->NG);
+// The inverse x pass of the velocity in grids slot, slot + 1, packed into packed grid which.
+static void fft_x_pack(gdc_fcm* f, int slot, int which) {
+    const size_t smem = fft_smem2(f->N, 256);
+    const unsigned blocks = (unsigned)(f->NG / (8LL * 256));
+    const float2* u = f->grid + slot * f->NG;
+    float4* out = f->packed + which * f->NG;
+#define GDC_XP(L) k_fft_x_pack<L><<<blocks, 256, smem, f->stream>>>(u, f->NG, f->tw, out)
+    ++f->n_launch;
+    switch (f->logN) {
+        case 4: GDC_XP(4); break;
+        case 5: GDC_XP(5); break;
+        case 6: GDC_XP(6); break;
+        case 7: GDC_XP(7); break;
+        case 8: GDC_XP(8); break;
+        default: GDC_XP(9);
+    }
+#undef GDC_XP
 }
 
+static void zsolve_launch(gdc_fcm* f) {
+    const int th = zsolve_threads(f->N), H = 4 * th / f->N;   // slots (pencil pairs) per block
+    const unsigned blocks = (unsigned)ceil_div((long long)f->N * (f->N / 2 + 1), H);
+    const size_t smem = fft_smem2(f->N, th);
+    const float kunit = (float)(2.0 * 3.141592653589793 / f->p.L);
+    const float se = (float)(1.0 / ((double)f->NG * f->p.eta));
+    const float2* F = f->grid;
+    float2* U = f->grid + 2 * f->NG;
+#define GDC_ZS(L, TH_) k_fcm_zsolve<L, TH_><<<blocks, TH_, smem, f->stream>>>(F, U, f->NG, f->tw, kunit, se)
+    ++f->n_launch;
+    switch (f->logN) {
+        case 4: GDC_ZS(4, 256); break;
+        case 5: GDC_ZS(5, 256); break;
+        case 6: GDC_ZS(6, 256); break;
+        case 7: GDC_ZS(7, 256); break;
+        case 8: GDC_ZS(8, GDC_ZSOLVE_TH); break;
+        default: GDC_ZS(9, GDC_ZSOLVE_TH);
+    }
+#undef GDC_ZS
+}
+
+// which = 0: the deterministic velocity, 1: the fluctuating one
 static void fcm_average_launch(gdc_fcm* f, int n, const double* r, int which, double* v) {
     const double s2 = f->p.sigma * f->p.sigma;
     const double norm = std::pow(2.0 * 3.141592653589793 * s2, -1.5);
@@ -801,6 +949,11 @@ gdc_status gdc_fcm_init(gdc_fcm** out, const gdc_fcm_params* params, void* works
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft<1, 8, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft<0, 9, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft<1, 9, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm);
+    const int zsm = (int)std::max(fft_smem2(256, GDC_ZSOLVE_TH), fft_smem2(512, GDC_ZSOLVE_TH));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fcm_zsolve<8, GDC_ZSOLVE_TH>, cudaFuncAttributeMaxDynamicSharedMemorySize, zsm);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fcm_zsolve<9, GDC_ZSOLVE_TH>, cudaFuncAttributeMaxDynamicSharedMemorySize, zsm);
     if (e == cudaSuccess) e = cudaStreamSynchronize(f->stream);
     if (e != cudaSuccess) {
         delete f;
@@ -852,13 +1005,13 @@ gdc_status gdc_fcm_apply(gdc_fcm* f, int n, const double* r, const double* lambd
         }
 #undef GDC_SPREAD
     }
-    // grids 0-1: FFT(f_x + i f_y), FFT(f_z); grids 2-3: the velocity's (u_x + i u_y, u_z)
-    fft3(f, 0, 2, false);
-    ++f->n_launch, k_fcm_solve<<<ceil_div(f->NG, 256), 256, 0, f->stream>>>(
-        f->NG, f->N, (float)(2.0 * 3.141592653589793 / f->p.L), (float)(1.0 / ((double)f->NG * f->p.eta)), f->grid,
-        f->grid + 2 * f->NG);
-    fft3(f, 2, 2, true);
-    fcm_pack(f, 2, 0);
+    // grids 0-1: FFT(f_x + i f_y), FFT(f_z) along x and y; the z passes and the solve in one
+    // launch into grids 2-3, the velocity's (u_x + i u_y, u_z); their inverse y pass, then the
+    // inverse x pass into packed grid 0
+    fft3(f, 0, 2, false, 0, 2);
+    zsolve_launch(f);
+    fft3(f, 2, 2, true, 1, 2);
+    fft_x_pack(f, 2, 0);
     fcm_average_launch(f, n, r, 0, u);
     gdc_status st = fcm_check(f, cudaGetLastError(), "FCM launch");
     if (st == GDC_OK) st = fcm_check(f, cudaStreamSynchronize(f->stream), "FCM product");
@@ -876,12 +1029,12 @@ gdc_status gdc_fcm_brownian(gdc_fcm* f, unsigned long long seed, unsigned int ow
     // grids 4-6: the stress, two real components per complex grid; grids 7-8: (u_x + i u_y, u_z)
     ++f->n_launch, k_fcm_stress<<<ceil_div(f->NG, 256), 256, 0, f->stream>>>(f->NG, seed, owner, step, (float)sd,
                                                                              (float)so, f->grid + 4 * f->NG);
-    fft3(f, 4, 3, false);
+    fft3(f, 4, 3, false, 0, 3);
     ++f->n_launch, k_fcm_solve_stress<<<ceil_div(f->NG, 256), 256, 0, f->stream>>>(
         f->NG, f->N, (float)(2.0 * 3.141592653589793 / f->p.L), (float)(1.0 / ((double)f->NG * f->p.eta)),
         f->grid + 4 * f->NG, f->grid + 7 * f->NG);
-    fft3(f, 7, 2, true);
-    fcm_pack(f, 7, 1);
+    fft3(f, 7, 2, true, 1, 3);
+    fft_x_pack(f, 7, 1);
     f->have_field = true;
     fcm_average_launch(f, n, r, 1, v);
     gdc_status st = fcm_check(f, cudaGetLastError(), "FCM launch");

@@ -45,11 +45,13 @@ def test_fcm_product_matches_oracle(lib, N, L, R_t, n):
     np.testing.assert_array_equal(_host(F.apply(r, lam)), u)
 
 
-def test_fcm_product_matches_oracle_at_512(lib):
-    """The 512-point transforms (8 pencils per block in the contiguous pass, the benchmark's
-    grid) against the oracle on a 512^3 grid (about 30 s of numpy FFTs on the host)."""
-    N, L, R_t, n = 512, 150.0, 3.0, 60
-    rng = np.random.default_rng(512)
+@pytest.mark.parametrize("N,L", [(256, 80.0), (512, 150.0)])
+def test_fcm_product_matches_oracle_large_grids(lib, N, L):
+    """The 256- and 512-point transforms (1,024-thread blocks in the strided passes and in the
+    fused z passes with the solve; 512^3 is the benchmark's grid) against the oracle (about
+    30 s of numpy FFTs on the host at 512^3)."""
+    R_t, n = 3.0, 60
+    rng = np.random.default_rng(N)
     r = rng.uniform(0.0, L, size=(n, 3))
     lam = rng.standard_normal((n, 3))
     F = lib.Fcm(N, L, SIGMA, R_t, max_blobs=n)
