@@ -23,9 +23,10 @@
 //     passes in one launch (a block takes pencils with their mirrors, whose modes -k the split
 //     of the two real fields needs), for v-breve it is one pass over the modes;
 //   * averaging reads the packed velocity (one 16-byte load per point) and takes one warp per
-//     blob, each lane a fixed x offset and every (32 / width)-th row of the blob's box (at
-//     most 31 points per side); each lane sums its points of a z-plane in FP32 and the
-//     planes with FP32 compensation, and the lanes are added in FP64 in a fixed order.
+//     blob; in each z-plane of the blob's box (at most 31 points per side) the rows that can
+//     meet the sphere are one run of points, x fastest, dealt to the lanes in turn; each lane
+//     sums its points of a plane in FP32 and the planes with FP32 compensation, and the lanes
+//     are added in FP64 in a fixed order.
 #include <algorithm>
 #include <cmath>
 #include <new>
@@ -584,8 +585,13 @@ __device__ __forceinline__ float2 fcm_join(float2 A, float2 B) { return make_flo
 // once instead of three times (forward z pass, solve, inverse z pass).  In the rows y = 0 and
 // y = N/2 the pencils x > N/2 are the mirrors of N - x and come with them; the four pencils
 // with x, y in {0, N/2} are their own mirrors.
+// blocks per SM the fused kernel is compiled for (512 threads at 2 blocks per SM measured
+// 9.89 ms per M_FCM lambda at 512^3 against 9.51 with 1,024 threads at 1)
+#ifndef GDC_ZSOLVE_MINB
+#define GDC_ZSOLVE_MINB 1
+#endif
 template <int LOGN, int TH>
-__global__ void __launch_bounds__(TH) k_fcm_zsolve(const float2* __restrict__ F, float2* __restrict__ U, long long NG,
+__global__ void __launch_bounds__(TH, GDC_ZSOLVE_MINB) k_fcm_zsolve(const float2* __restrict__ F, float2* __restrict__ U, long long NG,
                                                    const float2* __restrict__ tw_g, float kunit, float scale_eta) {
     constexpr int N = 1 << LOGN, T = N / 8, P = TH / T, H = P / 2, S = fft_stride(N, P);
     extern __shared__ float2 sm[];
@@ -728,6 +734,7 @@ __global__ void __launch_bounds__(128) k_fcm_average(int n, const double* __rest
     // the FP32 rate) busier than the whole sum over the box
     int lo[3], cn[3];
     float d0[3];
+#pragma unroll
     for (int d = 0; d < 3; ++d) {
         int l = 0, c = 0;
         float o = 0.f;
@@ -744,34 +751,39 @@ __global__ void __launch_bounds__(128) k_fcm_average(int n, const double* __rest
         d0[d] = __shfl_sync(0xffffffffu, o, 0);
     }
     // offsets from the blob to the grid points of its box: the first one, then steps of h
-    const float hf = (float)h, R2 = (float)(R_t * R_t);
+    const float hf = (float)h, ih = 1.0f / hf, R2 = (float)(R_t * R_t);
     const float d0x = d0[0], d0y = d0[1], d0z = d0[2];
-    const int mask = N - 1;                          // N is a power of two
-    const int rows = cn[0] <= 16 ? 32 / cn[0] : 1;   // box rows a warp covers per pass
-    const int ox = lane % cn[0], oyr = lane / cn[0];
-    const bool on = oyr < rows;
-    const float dx = d0x + ox * hf;
-    const float wx = exp2f(-dx * dx * l2s);   // exp(-dx^2 / 2s^2)
-    const int ix = (lo[0] + ox) & mask;
+    const int mask = N - 1;   // N is a power of two
+    const int cx = cn[0];
+    const float icx = 1.0f / (float)cx;
     // the planes' sums added with compensation (Kahan) in FP32: as accurate as FP64 for a
     // box's at most 31 planes, without an FP32-to-FP64 conversion and FP64 add per plane
     float acc[3] = {0.f, 0.f, 0.f}, cmp[3] = {0.f, 0.f, 0.f};
-    // integer offsets also kept as floats (exact), so no conversion per point
-    float foz = 0.f;
-    const float frows = (float)rows;
+    float foz = 0.f;   // the plane offset also kept as a float (exact)
     for (int oz = 0; oz < cn[2]; ++oz, foz += 1.f) {
-        const float dz = fmaf(foz, hf, d0z);
-        const float wz = exp2f(-dz * dz * l2s) * wx;
-        const float dxz = fmaf(dx, dx, dz * dz);
-        const long long zoff = (long long)((lo[2] + oz) & mask) * N * N + ix;
+        const float dz = fmaf(foz, hf, d0z), dz2 = dz * dz, rem = R2 - dz2;
+        if (rem < 0.f) continue;   // the plane misses the sphere (the same on every lane)
+        // the rows that can meet the sphere's disc in this plane (widened by 1% of a row
+        // against rounding; the point test decides), taken as one run of points, x fastest,
+        // so the lanes stay busy whatever the box width
+        const float sq = sqrtf(rem);
+        const int y0 = max(0, (int)ceilf((-sq - d0y) * ih - 0.01f));
+        const int y1 = min(cn[1] - 1, (int)floorf((sq - d0y) * ih + 0.01f));
+        const int npt = (y1 - y0 + 1) * cx;
+        const float wz = exp2f(-dz2 * l2s);   // exp(-dz^2 / 2s^2)
+        const long long zoff = (long long)((lo[2] + oz) & mask) * N * N;
         float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-        float foy = (float)oyr;
 #pragma unroll 4
-        for (int oy = oyr; oy < cn[1]; oy += rows, foy += frows) {
-            const float dy = fmaf(foy, hf, d0y);
-            if (on && fmaf(dy, dy, dxz) <= R2) {
-                const float wgt = exp2f(-dy * dy * l2s) * wz;
-                const float4 q = __ldg(u + zoff + ((lo[1] + oy) & mask) * N);   // within a plane: int
+        for (int p = lane; p < npt; p += 32) {
+            // p = (oy - y0) cx + ox; the FP32 quotient is exact (p < 1024, and p / cx lies at
+            // least 1 / (2 cx) away from an integer)
+            const int qy = (int)(((float)p + 0.5f) * icx);
+            const int ox = p - qy * cx, oy = y0 + qy;
+            const float dx = fmaf((float)ox, hf, d0x), dy = fmaf((float)oy, hf, d0y);
+            const float dxy = fmaf(dx, dx, dy * dy);
+            if (dxy + dz2 <= R2) {
+                const float wgt = exp2f(-dxy * l2s) * wz;
+                const float4 q = __ldg(u + zoff + ((lo[1] + oy) & mask) * N + ((lo[0] + ox) & mask));
                 a0 = fmaf(q.x, wgt, a0);
                 a1 = fmaf(q.y, wgt, a1);
                 a2 = fmaf(q.z, wgt, a2);
