@@ -203,15 +203,18 @@ __global__ void k_fcm_stage_blobs(int n, double w, int nc, const int* __restrict
     plam[e] = make_float4((float)lam[3LL * j], (float)lam[3LL * j + 1], (float)lam[3LL * j + 2], 0.f);
 }
 
-constexpr int SP_CHUNK = 512;    // blobs staged in shared memory per round
+constexpr int SP_CHUNK = 128;    // blob entries examined per round (one per thread)
 
 // f(x_g) = sum of lambda_j Delta_j(x_g).  One block per binning cell (cells at least R_t wide)
 // and chunk of 128 PT of its grid points (blockIdx.y): the cell's grid points are those with
 // floor(i nc / N) equal to its index on every axis (an exact integer partition of the grid),
-// and every blob that can reach them lies in the 27 cells around it.  Those blobs are staged in shared memory (cells in a fixed order, blobs in
-// ascending index; rounds of SP_CHUNK) as FP32 offsets from the cell's corner, nearest image
-// to the cell's centre, and each thread sums them for its grid points with the minimum image
-// in FP32.  Deterministic, no atomics on the grid.  With at least 4 cells per side every
+// and every blob that can reach them lies in the 27 cells around it.  Those blobs are taken in
+// a fixed order (cells in a fixed order, blobs in ascending index; rounds of SP_CHUNK) as FP32
+// offsets from the cell's corner, nearest image to the cell's centre; a blob farther than R_t
+// from the bounding box of the block's grid points is dropped (with at least 4 cells per side),
+// the others are staged in shared memory in the same order (a ballot scan), and each thread
+// sums them for its grid points with the minimum image in FP32.  A dropped blob misses every
+// point of the block, so the sums are those of the full list, term for term.  Deterministic, no atomics on the grid.  With at least 4 cells per side every
 // staged offset is within 2 cell widths of the cell, less than L/2 from any of its grid
 // points, so the per-pair minimum image is the identity and WRAP = false drops it.  The image
 // of a staged blob is chosen with a multiplication by 1/L (an FP64 division per coordinate
@@ -226,6 +229,7 @@ __global__ void __launch_bounds__(128) k_fcm_spread(int N, double h, double L, d
                                                     long long NG) {
     __shared__ float4 sp[SP_CHUNK];
     __shared__ float4 sl[SP_CHUNK];
+    __shared__ int wkept[SP_CHUNK / 32];
     __shared__ int c_start[27], c_off[28];
     __shared__ float base_off[3];   // offset of the cell's first grid point from its corner
     __shared__ double corner[3];    // the cell's corner (w = L / nc, the cell width)
@@ -281,11 +285,22 @@ __global__ void __launch_bounds__(128) k_fcm_spread(int N, double h, double L, d
                 gi[q] = (g0[0] + jx) + (long long)N * ((g0[1] + jy) + (long long)N * (g0[2] + jz));
             }
         }
+        // the bounding box of this block's grid points (whole x and y rows of the cell, the z
+        // layers of the chunk) in the frame of the cell's corner, and the squared reach beyond
+        // it, widened by 1e-4 against rounding (dropping is only ever conservative)
+        const int layer = gn[0] * gn[1];
+        const int zlo = p0 / layer, zhi = (min(p0 + PT * 128, npts) - 1) / layer;
+        const float bx0 = base_off[0], bx1 = fmaf((float)(gn[0] - 1), hf, base_off[0]);
+        const float by0 = base_off[1], by1 = fmaf((float)(gn[1] - 1), hf, base_off[1]);
+        const float bz0 = fmaf((float)zlo, hf, base_off[2]), bz1 = fmaf((float)zhi, hf, base_off[2]);
+        const float reach2 = R2 * 1.0001f;
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
         for (int s0 = 0; s0 < total; s0 += SP_CHUNK) {
-            const int take = min(SP_CHUNK, total - s0);
-            __syncthreads();
-            for (int t = threadIdx.x; t < take; t += blockDim.x) {
-                const int e = s0 + t;
+            const int e = s0 + (int)threadIdx.x;
+            bool keep = false;
+            float4 vp = make_float4(0.f, 0.f, 0.f, 0.f), vl = vp;
+            __syncthreads();   // the previous round's staged blobs are no longer read
+            if (e < total) {
                 int k = 0;   // the neighbour cell of entry e: c_off[k] <= e < c_off[k + 1]
                 for (int step = 16; step > 0; step >>= 1)
                     if (k + step <= ncell - 1 && c_off[k + step] <= e) k += step;
@@ -297,14 +312,35 @@ __global__ void __launch_bounds__(128) k_fcm_spread(int N, double h, double L, d
                     rx -= L * rint((rx - mid) * invL);
                     ry -= L * rint((ry - mid) * invL);
                     rz -= L * rint((rz - mid) * invL);
-                    sp[t] = make_float4((float)rx, (float)ry, (float)rz, 0.f);
-                    sl[t] = make_float4((float)lam[3LL * j], (float)lam[3LL * j + 1], (float)lam[3LL * j + 2], 0.f);
+                    vp = make_float4((float)rx, (float)ry, (float)rz, 0.f);
+                    vl = make_float4((float)lam[3LL * j], (float)lam[3LL * j + 1], (float)lam[3LL * j + 2], 0.f);
+                    keep = true;
                 } else {      // the neighbour cell's corner is o w from this cell's (o in {-1, 0, 1}^3)
                     const float4 q = poff[pos];
                     const float ox = (float)(k % 3 - 1), oy = (float)((k / 3) % 3 - 1), oz = (float)(k / 9 - 1);
-                    sp[t] = make_float4(fmaf(ox, wf, q.x), fmaf(oy, wf, q.y), fmaf(oz, wf, q.z), 0.f);
-                    sl[t] = plam[pos];
+                    vp = make_float4(fmaf(ox, wf, q.x), fmaf(oy, wf, q.y), fmaf(oz, wf, q.z), 0.f);
+                    vl = plam[pos];
+                    const float ex = fmaxf(fmaxf(bx0 - vp.x, vp.x - bx1), 0.f);
+                    const float ey = fmaxf(fmaxf(by0 - vp.y, vp.y - by1), 0.f);
+                    const float ez = fmaxf(fmaxf(bz0 - vp.z, vp.z - bz1), 0.f);
+                    keep = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) <= reach2;
                 }
+            }
+            // staged in entry order: the kept entries of lower warps, then of lower lanes
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            if (lane == 0) wkept[wid] = __popc(bal);
+            __syncthreads();
+            int base = 0, take = 0;
+#pragma unroll
+            for (int w2 = 0; w2 < SP_CHUNK / 32; ++w2) {
+                const int c = wkept[w2];
+                base += w2 < wid ? c : 0;
+                take += c;
+            }
+            if (keep) {
+                const int at = base + __popc(bal & ((1u << lane) - 1u));
+                sp[at] = vp;
+                sl[at] = vl;
             }
             __syncthreads();
             for (int j = 0; j < take; ++j) {
