@@ -414,7 +414,8 @@ def fcm_measure(g, torch, wl, ctx, N: int, reps: int = 3) -> dict:
                                "as in Sec. 6.2 (the FP32 grid's rounding, a few 1e-7 of the operator, sets the floor)"}
     fctx.close()
     del fctx
-    out["note"] = ("M_FCM lambda, v-breve = J L^-1 D W (stress draw + 6 forward and 3 inverse 3-D FFTs) and the "
+    out["note"] = ("M_FCM lambda (3-D FFTs of 2 complex grids forward and back, each grid carrying two real "
+                   "fields), v-breve = J L^-1 D W (stress draw, 3 complex grids forward, 2 back) and the "
                    "re-averaging J u-breve at the same positions; CUDA events on the library stream, each call "
                    "ending with a synchronisation; the grids (14 GB at 512^3) exceed L2")
     torch.cuda.empty_cache()
