@@ -9,10 +9,10 @@
 // stress components, 7-8 the fluctuating velocity.  The last inverse pass (along x) writes a
 // velocity packed per point (float4: x, y, z, 0) into one of two packed grids, deterministic
 // and fluctuating; the fluctuating one is kept there for re-averaging.
-//   * spreading is a gather: a block takes the grid points of one binning cell (cells at
-//     least R_t wide) and stages the blobs of the 27 cells around it (blobs in ascending
-//     index) in shared memory as FP32 offsets from the cell's corner; it is deterministic and
-//     needs no atomics on the grid;
+//   * spreading is a gather: a block takes grid points of one binning cell (cells at least
+//     R_t wide) and stages the blobs of the 27 cells around it that can reach them (blobs in
+//     ascending index) in shared memory as FP32 offsets from the cell's corner; it is
+//     deterministic and needs no atomics on the grid;
 //   * the 3-D FFT is one launch per axis of self-sorting (Stockham) passes of radix 8 (then
 //     4 or 2) with 8 points of a pencil per thread in registers, exchanged through shared
 //     memory between passes (two exchanges for 512-point pencils); points are read once and
